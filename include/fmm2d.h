@@ -1,0 +1,195 @@
+/*
+ * fmm2d.h -- C ABI of the B300 (sm_103a) balanced adaptive 2D FMM library
+ * (libfmm2d.so).
+ *
+ * The library evaluates the 2D harmonic potential in complex form,
+ *     Phi(z_i) = sum_{j : z_j != z_i} Gamma_j / (z_i - z_j),   z = x + i y,
+ * i.e. the pairwise sum of Sec. 2, eq (2.1), with the exclusion rule of eq (2.2)
+ * and the harmonic kernel of Sec. 3.3 (taken with a + sign), by the balanced
+ * adaptive FMM of Holm, Engblom, Goude and Holmgren (arXiv:1311.1006):
+ *   - a pyramid tree of N_levels full levels whose boxes are split into four
+ *     children at exact medians, x first and then y in each half (Sec. 2.2-2.3);
+ *   - strong / weak coupling lists from the theta-criterion R + theta r <= theta d
+ *     (Sec. 2.1, eq 2.3);
+ *   - P2M, M2M, M2L, L2L, L2P and the P2P near-field sum (Sec. 2.1, Fig 2.2),
+ *     all as CUDA kernels on one GPU.
+ *
+ * Conventions shared by every call
+ *   - Device pointers are CUDA device addresses on the current device; host
+ *     pointers are ordinary host memory.  The caller owns every buffer it passes;
+ *     the library only reads/writes them, asynchronously, on the given stream.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Calls return once the work is enqueued, except where stated
+ *     (tree builds synchronise the stream once to read a status word).
+ *   - Points are N x 2 float64, row-major (x0, y0, x1, y1, ...).  Complex
+ *     arrays are interleaved (re, im): float64 pairs, or float32 pairs where a
+ *     call says "complex64".
+ *   - Outputs are in the caller's input order.  Sources and evaluation points
+ *     are the same point set (eq 2.1).  Real strengths: pass im = 0.
+ *   - Errors are returned as fmm_status codes; nothing crosses the ABI as an
+ *     exception.  fmm_last_error() gives a thread-local detail string.  An
+ *     asynchronous CUDA error from earlier work is reported by the next call.
+ *   - Two precision paths (fmm_params.path):
+ *       FMM_PATH_FP32 (mixed): P2P, M2L, P2M and L2P compute in FP32 with FP32
+ *         accumulation; M2M and L2L shifts and the accumulation of expansions
+ *         across levels are FP64; output complex64.
+ *       FMM_PATH_FP64: every pass in FP64; output complex128.
+ *   - Thread safety: a tree may be used by one host thread at a time.
+ */
+#ifndef FMM2D_H
+#define FMM2D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FMM_OK = 0,
+    FMM_ERR_INVALID_ARG = 1, /* a size, parameter or pointer is out of range */
+    FMM_ERR_CUDA = 2,        /* a CUDA runtime call or kernel failed */
+    FMM_ERR_OOM = 3,         /* device or host allocation failed */
+    FMM_ERR_TIMEOUT = 4,     /* a bounded device wait ran out (status word) */
+    FMM_ERR_NONFINITE = 5    /* NaN / Inf in the point coordinates */
+} fmm_status;
+
+typedef enum { FMM_PATH_FP32 = 0, FMM_PATH_FP64 = 1 } fmm_path;
+
+/* fmm_params.flags */
+enum {
+    FMM_FLAG_NO_GRAPH = 1, /* launch kernels one by one instead of replaying a captured CUDA graph */
+    FMM_FLAG_SERIAL = 2,   /* run P2P on the caller's stream after the far field (no overlap) */
+    FMM_FLAG_TIMING = 4    /* record per-phase CUDA events; read them with fmm_phase_times */
+};
+
+/* Maximum expansion order accepted (p terms, coefficients k = 0..p-1). */
+#define FMM_P_MAX 32
+
+typedef struct {
+    int p;        /* expansion terms, 1 <= p <= FMM_P_MAX (Sec. 2.1, "p terms") */
+    double theta; /* separation parameter of eq (2.3), 0 < theta < 1 */
+    int nlevels;  /* N_levels >= 1 with 4^(N_levels-1) <= N (no empty leaf);
+                     0 = fmm_default_nlevels(N, p, path) */
+    int path;     /* fmm_path */
+    int flags;    /* FMM_FLAG_* */
+} fmm_params;
+
+/* Opaque, device-resident tree + workspace, owned by the library. */
+typedef struct fmm_tree fmm_tree;
+
+/* Build the pyramid tree and the coupling lists of one point set (Sec. 2.1-2.3).
+ *   d_xy   : device, N x 2 float64 points; read during the call only.
+ *   n      : N >= 1 (and < 2^31).
+ *   prm    : host, parameters (copied).
+ *   out    : host, receives the new tree (NULL on failure).
+ * Synchronises `stream` once to check the device status word.
+ * Errors: INVALID_ARG (bad n / prm), NONFINITE (NaN or Inf coordinate), OOM, CUDA. */
+fmm_status fmm_build_tree(const double* d_xy, int64_t n, const fmm_params* prm, void* stream, fmm_tree** out);
+
+/* Rebuild an existing tree in place for new coordinates of the same N points
+ * (the paper rebuilds the partition at every time step, Sec. 3.1), optionally
+ * with new parameters (prm may be NULL = keep).  Buffers are reused and grown
+ * when needed.  Same errors as fmm_build_tree. */
+fmm_status fmm_tree_rebuild(fmm_tree* t, const double* d_xy, const fmm_params* prm, void* stream);
+
+/* Batched build: B independent instances in one forest (one launch per phase
+ * covers every instance).  Instance b owns points h_offsets[b] .. h_offsets[b+1]-1
+ * of d_xy (h_offsets: host, B+1 entries, h_offsets[0] = 0).  h_nlevels (host, B
+ * entries) gives N_levels per instance, or NULL to choose each instance's
+ * N_levels with fmm_default_nlevels.  No coupling crosses instances. */
+fmm_status fmm_build_tree_batched(const double* d_xy, const int64_t* h_offsets, int B, const fmm_params* prm,
+                                  const int* h_nlevels, void* stream, fmm_tree** out);
+
+/* Evaluate Phi at every point (Sec. 2.1: P2M, M2M, M2L, L2L, L2P, P2P).
+ *   d_gamma : device, N complex strengths (complex128), input order.
+ *   d_phi   : device, N complex outputs, input order: complex64 for
+ *             FMM_PATH_FP32, complex128 for FMM_PATH_FP64.
+ * Works on single and batched trees.  Errors: INVALID_ARG (NULL), CUDA. */
+fmm_status fmm_eval(fmm_tree* t, const double* d_gamma, void* d_phi, void* stream);
+
+/* Same as fmm_eval; rejects a tree that was not built by fmm_build_tree_batched. */
+fmm_status fmm_eval_batched(fmm_tree* t, const double* d_gamma, void* d_phi, void* stream);
+
+/* Adjoint of fmm_eval with the tree frozen.  For the real loss
+ *     L = sum_i w_i Re Phi_i + v_i Im Phi_i,    d_gphi[i] = w_i + i v_i (complex128),
+ * writes (torch convention: d/dRe + i d/dIm)
+ *     d_ggamma[k] = dL/dRe Gamma_k + i dL/dIm Gamma_k = -conj(Psi_k)   (complex128)
+ *     d_gxy[k]    = (dL/dx_k, dL/dy_k) = (Re D_k, -Im D_k)             (N x 2 float64)
+ * with c = conj(gphi), Psi(z) = sum_i c_i/(z - z_i) (a second FMM over the same
+ * tree), D_k = c_k Phi'(z_k) - Gamma_k Psi'(z_k).  Either output may be NULL.
+ * Uses the tree's precision path.  Errors: INVALID_ARG, CUDA. */
+fmm_status fmm_eval_backward(fmm_tree* t, const double* d_gamma, const double* d_gphi, double* d_ggamma,
+                             double* d_gxy, void* stream);
+
+/* One step of the N_levels autotuner (Sec. 4.2, Algorithm 4 "AT3b": a directed
+ * walk with cost estimation and a user cap on the tuning cost).  Call after
+ * every evaluation with its time; *inout receives the parameters to use next
+ * (only nlevels changes; theta is kept).  The caller rebuilds the tree with
+ * them (fmm_tree_rebuild).  Host-only; no device work. */
+fmm_status fmm_autotune_step(fmm_tree* t, double last_time_s, fmm_params* inout);
+
+/* Configure the autotuner: cap = maximum relative tuning cost (e.g. 0.1),
+ * window = number of evaluations whose minimum time is used per decision
+ * (noise filter, Sec. 4.2.1), period = evaluations between N_levels moves. */
+fmm_status fmm_autotune_config(fmm_tree* t, double cap, int window, int period);
+
+/* N_levels the library picks for n points at expansion order p when
+ * fmm_params.nlevels == 0: the level whose leaves hold closest to the point
+ * count that balances the P2P and M2L costs of eqs (2.4)-(2.5) on this GPU. */
+int fmm_default_nlevels(int64_t n, int p, int path);
+
+/* Per-phase device times (milliseconds) of the last evaluation made with
+ * FMM_FLAG_TIMING: out[0] gather, [1] P2M+M2M, [2] M2L, [3] L2L, [4] P2P,
+ * [5] L2P+combine, [6] whole evaluation.  Synchronises on the recorded events. */
+fmm_status fmm_phase_times(fmm_tree* t, double* out, int nout);
+
+/* Tree facts (host struct). */
+typedef struct {
+    int64_t n;               /* points */
+    int ninst;               /* instances (1 unless batched) */
+    int nlevels_max;         /* largest N_levels over instances */
+    int p, path;
+    double theta;
+    int64_t nboxes;          /* boxes over all levels and instances */
+    int64_t nleaves;
+    int64_t n_weak;          /* M2L pairs over all levels */
+    int64_t n_strong_leaf;   /* P2P leaf pairs */
+    int64_t p2p_pairs;       /* P2P point pairs: sum over leaves of n_leaf * near points */
+    int strong_cap, weak_cap;
+} fmm_tree_info;
+
+fmm_status fmm_get_tree_info(const fmm_tree* t, fmm_tree_info* out);
+
+/* Copy one of the tree's device arrays to host memory (tests, diagnostics).
+ * `count` is the number of ELEMENTS the host buffer holds; the call fails
+ * with INVALID_ARG when it is too small.  Synchronises `stream`. */
+typedef enum {
+    FMM_EXPORT_PERM = 0,      /* int32[n]     sorted position -> input index */
+    FMM_EXPORT_BSTART = 1,    /* int32[nbox]  first sorted position of each box */
+    FMM_EXPORT_BCOUNT = 2,    /* int32[nbox]  points in each box */
+    FMM_EXPORT_CENTER = 3,    /* float64[2*nbox] */
+    FMM_EXPORT_RADIUS = 4,    /* float64[nbox] */
+    FMM_EXPORT_NSTRONG = 5,   /* int32[nbox] */
+    FMM_EXPORT_STRONG = 6,    /* int32[nbox*strong_cap], box-major, first NSTRONG valid */
+    FMM_EXPORT_NWEAK = 7,     /* int32[nbox] */
+    FMM_EXPORT_WEAK = 8,      /* int32[nbox*weak_cap] */
+    FMM_EXPORT_MPOLE = 9,     /* float64[2*nbox*p]: multipole coefficients a_k / rho^k (rho = scale radius) */
+    FMM_EXPORT_LOCAL = 10,    /* float64[2*nbox*p]: local coefficients b_l * rho^l */
+    FMM_EXPORT_NEAR = 11,     /* float64[2*n]: P2P part of the last evaluation, sorted order */
+    FMM_EXPORT_INST = 12,     /* int64[3*ninst]: point offset, box offset, N_levels per instance */
+    FMM_EXPORT_RHO = 13       /* float64[nbox]: scale radius rho of each box */
+} fmm_export_what;
+
+fmm_status fmm_tree_export(const fmm_tree* t, int what, void* h_dst, int64_t count, void* stream);
+
+void fmm_tree_destroy(fmm_tree* t);
+
+const char* fmm_status_string(fmm_status s);
+const char* fmm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMM2D_H */

@@ -1,0 +1,221 @@
+// Internal declarations of the B300 FMM library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "fmm2d.h"
+
+namespace fmm {
+
+// ------------------------------------------------------------------ status
+// Bits of the device status word (atomicOr from kernels, read after a build).
+enum : unsigned {
+    ST_NONFINITE = 1u,        // NaN/Inf coordinate seen by the key kernel
+    ST_STRONG_OVERFLOW = 2u,  // a strong list exceeded its fixed capacity
+    ST_WEAK_OVERFLOW = 4u,    // a weak list exceeded its fixed capacity
+    ST_TIMEOUT = 8u           // a bounded wait gave up
+};
+
+// Partition tile: 256 threads x 8 consecutive positions.
+constexpr int kPartThreads = 256;
+constexpr int kPartItems = 8;
+constexpr int kPartTile = kPartThreads * kPartItems;
+
+// Radix sort tile: 256 threads x 8 rounds.
+constexpr int kSortThreads = 256;
+constexpr int kSortRounds = 8;
+constexpr int kSortTile = kSortThreads * kSortRounds;
+
+// Segment table of one partition stage: segment k covers sorted positions
+// [start[k], start[k+1]) and its first nzero[k] positions (by the list being
+// split) keep flag 0.
+struct SegTable {
+    int K = 0;
+    int32_t* d_start = nullptr;  // K+1 entries, start[K] = n
+    int32_t* d_nzero = nullptr;  // K entries
+};
+
+struct LevelList {
+    int count = 0;
+    int32_t* d_ids = nullptr;  // global box ids
+};
+
+// --------------------------------------------------------------- the tree
+struct Tree {
+    // parameters
+    int p = 17, P = 17, PS = 18, path = FMM_PATH_FP32, flags = 0;
+    double theta = 0.5;
+    bool batched = false;
+
+    // shape
+    int64_t n = 0;
+    int ninst = 1;
+    std::vector<int64_t> inst_pt_off;   // ninst+1
+    std::vector<int> inst_levels;       // ninst
+    std::vector<int64_t> inst_box_off;  // ninst+1
+    int Lmax = 1;
+    int64_t nbox = 0, nleaf = 0;
+    std::vector<int64_t> shape_key;     // (inst sizes, levels) the tables were built for
+
+    // host copies of the shape tables
+    std::vector<int32_t> h_bstart, h_bcount, h_parent, h_child0, h_inst;
+    std::vector<std::vector<int32_t>> h_level_boxes;  // per level: boxes present
+    std::vector<int32_t> h_leaves;
+
+    // device shape tables
+    int32_t *d_bstart = nullptr, *d_bcount = nullptr, *d_parent = nullptr, *d_child0 = nullptr,
+            *d_inst = nullptr;
+    std::vector<LevelList> level_boxes;    // per level l: all boxes on level l
+    std::vector<LevelList> level_parents;  // per level l: boxes on level l that have children
+    LevelList leaves;
+    std::vector<SegTable> seg_x, seg_y;    // per level l < Lmax-1
+    int64_t* d_inst_ptoff = nullptr;       // ninst+1
+    int64_t* d_inst_boxoff = nullptr;      // ninst+1 (root box id of each instance)
+    int32_t* d_leaf_start = nullptr;       // nleaf+1: first sorted position of each leaf
+
+    // build scratch
+    uint64_t* d_keys[4] = {nullptr, nullptr, nullptr, nullptr};
+    int32_t* d_vals[4] = {nullptr, nullptr, nullptr, nullptr};
+    int32_t *d_X2 = nullptr, *d_Y2 = nullptr;
+    uint8_t *d_sideX = nullptr, *d_sideY = nullptr;
+    int32_t *d_tile_cnt = nullptr, *d_tile_pre = nullptr, *d_seg_lc = nullptr;
+    int32_t *d_sort_hist = nullptr, *d_sort_tot = nullptr, *d_sort_off = nullptr;
+    int64_t segs_cap = 0;
+
+    // tree data
+    int32_t* d_perm = nullptr;     // sorted position -> input index
+    int32_t* d_leaf_of = nullptr;  // sorted position -> leaf box id
+    double2* d_pts = nullptr;      // sorted FP64 points
+    float4* d_pos4 = nullptr;      // sorted (x_hi, y_hi, x_lo, y_lo) relative to the instance origin
+    double2* d_center = nullptr;   // per box
+    double* d_radius = nullptr;    // per box (half bbox diagonal)
+    double* d_rho = nullptr;       // per box scale radius = (double)(float)radius
+    float4* d_chl = nullptr;       // per box centre hi/lo relative to the instance origin
+    float* d_rho32 = nullptr;      // per box (float)rho
+    int scap = 32, wcap = 80;
+    int32_t *d_nstrong = nullptr, *d_strong = nullptr, *d_nweak = nullptr, *d_weak = nullptr;
+    unsigned* d_status = nullptr;  // [0] status bits; bytes 8.. three 64-bit counters
+    unsigned long long h_counts[3] = {0, 0, 0};
+
+    // evaluation workspace
+    void* d_gam = nullptr;     // sorted strengths (float2 or double2), 2 sets for backward
+    void* d_near = nullptr;    // P2P output(s), sorted order
+    double2* d_M64 = nullptr;  // multipoles, scaled
+    float2* d_M32 = nullptr;
+    void* d_Lm2l = nullptr;    // M2L sums per box
+    double2* d_L64 = nullptr;  // locals after L2L, scaled
+    float2* d_L32 = nullptr;
+    size_t eval_nbox = 0, eval_n = 0;
+    int eval_PS = 0, eval_path = -1, eval_sets = 0;
+
+    // streams / events
+    cudaStream_t s_aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_t[8] = {};
+    bool timing_valid = false;
+
+    // captured evaluation graph (keyed by the user pointers it bakes in)
+    cudaGraphExec_t graph = nullptr;
+    const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};
+
+    // autotuner state (AT3b, Algorithm 4)
+    struct Tune {
+        double cap = 0.10;
+        int window = 3, period = 8;
+        int iter = 0;           // evaluations seen
+        int since_move = 0;     // evaluations since the last decision
+        std::vector<double> win;
+        double base_min = 0;    // min time over the window of the accepted configuration
+        int accepted = 0;       // accepted N_levels
+        int trial = 0;          // N_levels on trial (0 = none)
+        int nldir = +1;
+        double basetime = 0;    // accumulated time of accepted evaluations
+        double upcost = 0, downcost = 0;
+        int upinterval = 0, downinterval = 0;  // evaluations to wait before the next up/down move
+        int wait_up = 0, wait_down = 0;
+        int max_levels = 1;
+    } tune;
+};
+
+// -------------------------------------------------------------- utilities
+void set_error(const std::string& msg);
+fmm_status cuda_fail(cudaError_t e, const char* what);
+
+#define FMM_CUDA(call)                                              \
+    do {                                                            \
+        cudaError_t _e = (call);                                    \
+        if (_e != cudaSuccess) return ::fmm::cuda_fail(_e, #call);  \
+    } while (0)
+
+// ------------------------------------------------------------ tree phases
+fmm_status build_shape(Tree& t);                                         // host tables + device copies
+fmm_status alloc_build(Tree& t);                                         // build scratch / tree arrays
+fmm_status alloc_lists(Tree& t);                                         // fixed-capacity lists
+fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s);  // sort, split, geometry
+fmm_status run_lists(Tree& t, cudaStream_t s);                           // strong / weak lists
+fmm_status alloc_eval(Tree& t, int sets);
+fmm_status run_eval(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s);
+fmm_status run_backward(Tree& t, const double* d_gamma, const double* d_gphi, double* d_ggamma, double* d_gxy,
+                        cudaStream_t s);
+
+// Autotuner (host).
+int default_nlevels(int64_t n, int p, int path);
+
+}  // namespace fmm
+
+// ---------------------------------------------------------------- device
+#ifdef __CUDACC__
+namespace fmm {
+
+// C(n,k) by the multiplicative formula; exact in double for n <= 62.
+__host__ __device__ constexpr double binom_d(int n, int k) {
+    if (k < 0 || k > n) return 0.0;
+    if (k > n - k) k = n - k;
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r = r * double(n - k + i) / double(i);
+    return r;
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// acc + a*b
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc) {
+    return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Index of the segment containing position i: largest k with start[k] <= i.
+__device__ __forceinline__ int find_seg(const int32_t* __restrict__ start, int K, int i) {
+    int lo = 0, hi = K - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(start + mid) <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+}  // namespace fmm
+#endif

@@ -1,0 +1,762 @@
+// Tree build of the balanced adaptive FMM on the device (Sec. 2.2-2.3 of the
+// paper: a pyramid of full levels, every box split into four at exact medians,
+// x first and then y within each half) and the strong / weak coupling lists of
+// Sec. 2.1 with the theta-criterion of eq (2.3).
+//
+// Design: both coordinates are sorted once by an LSD radix sort on
+// order-preserving 64-bit keys with the input index as tie-break (stable).
+// After that a median split never compares coordinates again: every box keeps
+// its points as two lists, one in (x, index) order and one in (y, index) order.
+// The x-split of a box is a contiguous cut of its x-list; the y-list is then
+// stably partitioned by the side flags of that cut (segmented scan + scatter).
+// The y-split of each half is the mirror image.  Bounding boxes come for free
+// from the first/last entries of the two lists.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+// ================================================================ shape (host)
+
+static int64_t lvl_off(int l) {  // boxes on levels < l of one instance
+    int64_t s = 0, w = 1;
+    for (int i = 0; i < l; ++i) { s += w; w *= 4; }
+    return s;
+}
+
+template <typename T>
+static fmm_status upload(T** dst, const std::vector<T>& v) {
+    if (*dst) { cudaFree(*dst); *dst = nullptr; }
+    size_t bytes = std::max<size_t>(v.size(), 1) * sizeof(T);
+    FMM_CUDA(cudaMalloc((void**)dst, bytes));
+    if (!v.empty()) FMM_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return FMM_OK;
+}
+
+static void free_list(LevelList& l) {
+    if (l.d_ids) cudaFree(l.d_ids);
+    l.d_ids = nullptr;
+    l.count = 0;
+}
+static void free_seg(SegTable& s) {
+    if (s.d_start) cudaFree(s.d_start);
+    if (s.d_nzero) cudaFree(s.d_nzero);
+    s = SegTable();
+}
+
+// Point ranges, parents and children of every box follow from the instance
+// sizes alone: a box of n points gives its x-halves floor(n/2) and ceil(n/2)
+// points, and each half gives its y-halves the floor / ceil of its own count.
+fmm_status build_shape(Tree& t) {
+    const int B = t.ninst;
+    t.Lmax = 1;
+    t.inst_box_off.assign(B + 1, 0);
+    for (int b = 0; b < B; ++b) {
+        t.Lmax = std::max(t.Lmax, t.inst_levels[b]);
+        t.inst_box_off[b + 1] = t.inst_box_off[b] + lvl_off(t.inst_levels[b]);
+    }
+    t.nbox = t.inst_box_off[B];
+    if (t.nbox >= (int64_t(1) << 30)) { set_error("too many boxes"); return FMM_ERR_INVALID_ARG; }
+    t.h_bstart.assign(t.nbox, 0);
+    t.h_bcount.assign(t.nbox, 0);
+    t.h_parent.assign(t.nbox, -1);
+    t.h_child0.assign(t.nbox, -1);
+    t.h_inst.assign(t.nbox, 0);
+    t.h_level_boxes.assign(t.Lmax, {});
+    std::vector<std::vector<int32_t>> lvl_par(t.Lmax);
+    t.h_leaves.clear();
+    for (int b = 0; b < B; ++b) {
+        const int L = t.inst_levels[b];
+        const int64_t bo = t.inst_box_off[b];
+        t.h_bstart[bo] = (int32_t)t.inst_pt_off[b];
+        t.h_bcount[bo] = (int32_t)(t.inst_pt_off[b + 1] - t.inst_pt_off[b]);
+        for (int l = 0; l < L; ++l) {
+            const int64_t nb = int64_t(1) << (2 * l);
+            for (int64_t i = 0; i < nb; ++i) {
+                const int64_t g = bo + lvl_off(l) + i;
+                t.h_inst[g] = b;
+                t.h_level_boxes[l].push_back((int32_t)g);
+                if (l + 1 == L) { t.h_leaves.push_back((int32_t)g); continue; }
+                lvl_par[l].push_back((int32_t)g);
+                const int32_t s = t.h_bstart[g], n = t.h_bcount[g];
+                const int32_t nl = n / 2, nr = n - nl;
+                const int64_t c0 = bo + lvl_off(l + 1) + 4 * i;
+                t.h_child0[g] = (int32_t)c0;
+                const int32_t cs[4] = {s, s + nl / 2, s + nl, s + nl + nr / 2};
+                const int32_t cn[4] = {nl / 2, nl - nl / 2, nr / 2, nr - nr / 2};
+                for (int c = 0; c < 4; ++c) {
+                    t.h_bstart[c0 + c] = cs[c];
+                    t.h_bcount[c0 + c] = cn[c];
+                    t.h_parent[c0 + c] = (int32_t)g;
+                }
+            }
+        }
+    }
+    t.nleaf = (int64_t)t.h_leaves.size();
+    fmm_status st;
+    if ((st = upload(&t.d_bstart, t.h_bstart))) return st;
+    if ((st = upload(&t.d_bcount, t.h_bcount))) return st;
+    if ((st = upload(&t.d_parent, t.h_parent))) return st;
+    if ((st = upload(&t.d_child0, t.h_child0))) return st;
+    if ((st = upload(&t.d_inst, t.h_inst))) return st;
+    if ((st = upload(&t.d_inst_ptoff, t.inst_pt_off))) return st;
+    if ((st = upload(&t.d_inst_boxoff, t.inst_box_off))) return st;
+    for (auto& l : t.level_boxes) free_list(l);
+    for (auto& l : t.level_parents) free_list(l);
+    free_list(t.leaves);
+    t.level_boxes.assign(t.Lmax, {});
+    t.level_parents.assign(t.Lmax, {});
+    for (int l = 0; l < t.Lmax; ++l) {
+        t.level_boxes[l].count = (int)t.h_level_boxes[l].size();
+        if ((st = upload(&t.level_boxes[l].d_ids, t.h_level_boxes[l]))) return st;
+        t.level_parents[l].count = (int)lvl_par[l].size();
+        if ((st = upload(&t.level_parents[l].d_ids, lvl_par[l]))) return st;
+    }
+    t.leaves.count = (int)t.nleaf;
+    if ((st = upload(&t.leaves.d_ids, t.h_leaves))) return st;
+    {
+        std::vector<int32_t> ls(t.nleaf + 1);
+        for (int64_t i = 0; i < t.nleaf; ++i) ls[i] = t.h_bstart[t.h_leaves[i]];
+        ls[t.nleaf] = (int32_t)t.n;
+        if ((st = upload(&t.d_leaf_start, ls))) return st;
+    }
+
+    // partition segment tables, one x-stage and one y-stage per level
+    for (auto& s : t.seg_x) free_seg(s);
+    for (auto& s : t.seg_y) free_seg(s);
+    t.seg_x.assign(std::max(t.Lmax - 1, 0), {});
+    t.seg_y.assign(std::max(t.Lmax - 1, 0), {});
+    int64_t maxK = 1;
+    for (int l = 0; l + 1 < t.Lmax; ++l) {
+        std::vector<int32_t> xs, xz, ys, yz;
+        for (int b = 0; b < B; ++b) {
+            const int L = t.inst_levels[b];
+            const int32_t ps = (int32_t)t.inst_pt_off[b], pn = (int32_t)(t.inst_pt_off[b + 1] - t.inst_pt_off[b]);
+            if (l + 1 >= L) {  // this instance is already at its leaves: one inert segment
+                xs.push_back(ps); xz.push_back(pn);
+                ys.push_back(ps); yz.push_back(pn);
+                continue;
+            }
+            const int64_t bo = t.inst_box_off[b] + lvl_off(l);
+            for (int64_t i = 0; i < (int64_t(1) << (2 * l)); ++i) {
+                const int32_t s = t.h_bstart[bo + i], n = t.h_bcount[bo + i];
+                const int32_t nl = n / 2, nr = n - nl;
+                xs.push_back(s); xz.push_back(nl);
+                ys.push_back(s); yz.push_back(nl / 2);
+                ys.push_back(s + nl); yz.push_back(nr / 2);
+            }
+        }
+        xs.push_back((int32_t)t.n);
+        ys.push_back((int32_t)t.n);
+        t.seg_x[l].K = (int)xz.size();
+        t.seg_y[l].K = (int)yz.size();
+        maxK = std::max<int64_t>(maxK, (int64_t)std::max(xz.size(), yz.size()));
+        if ((st = upload(&t.seg_x[l].d_start, xs))) return st;
+        if ((st = upload(&t.seg_x[l].d_nzero, xz))) return st;
+        if ((st = upload(&t.seg_y[l].d_start, ys))) return st;
+        if ((st = upload(&t.seg_y[l].d_nzero, yz))) return st;
+    }
+    t.segs_cap = maxK;
+    return FMM_OK;
+}
+
+// ============================================================== radix sort
+
+// Order-preserving key of a double (+0 and -0 map to the same key).
+__device__ __forceinline__ uint64_t order_key(double v) {
+    if (v == 0.0) v = 0.0;
+    uint64_t u = (uint64_t)__double_as_longlong(v);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+__global__ void k_keys(const double2* __restrict__ xy, int n, uint64_t* kx, uint64_t* ky, int32_t* vx, int32_t* vy,
+                       unsigned* status) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 p = xy[i];
+    if (!isfinite(p.x) || !isfinite(p.y)) atomicOr(status, ST_NONFINITE);
+    kx[i] = order_key(p.x);
+    ky[i] = order_key(p.y);
+    vx[i] = i;
+    vy[i] = i;
+}
+
+// Instance index of each sorted entry (batched trees): the digit source of the
+// two final stable passes that group the points by instance.
+__global__ void k_inst_keys(const int32_t* __restrict__ vx, const int32_t* __restrict__ vy,
+                            const int64_t* __restrict__ ptoff, int ninst, int n, uint64_t* kx, uint64_t* ky) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int s = 0; s < 2; ++s) {
+        int v = s ? vy[i] : vx[i];
+        int lo = 0, hi = ninst - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (ptoff[mid] <= v) lo = mid;
+            else hi = mid - 1;
+        }
+        (s ? ky : kx)[i] = (uint64_t)lo;
+    }
+}
+
+// Per-tile digit histograms of both sorts (blockIdx.y = which sort).
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint64_t* __restrict__ k0,
+                                                            const uint64_t* __restrict__ k1, int n, int shift, int T,
+                                                            int32_t* hist /*[2][256][T]*/, int32_t* tot /*[2][256]*/) {
+    __shared__ int h[256];
+    const int s = blockIdx.y, t = blockIdx.x;
+    const uint64_t* k = s ? k1 : k0;
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    for (int r = 0; r < kSortRounds; ++r) {
+        int i = t * kSortTile + r * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(int)((k[i] >> shift) & 255u)], 1);
+    }
+    __syncthreads();
+    int c = h[threadIdx.x];
+    hist[((size_t)s * 256 + threadIdx.x) * T + t] = c;
+    if (c) atomicAdd(&tot[s * 256 + threadIdx.x], c);
+}
+
+// Exclusive offsets: block (d, s) scans digit d's tile counts and adds the
+// number of keys with a smaller digit.
+__global__ void __launch_bounds__(1024) k_sort_scan(const int32_t* __restrict__ hist, const int32_t* __restrict__ tot,
+                                                    int T, int32_t* off) {
+    __shared__ int wsum[32];
+    __shared__ int base;
+    const int d = blockIdx.x, s = blockIdx.y;
+    if (threadIdx.x < 32) {
+        int acc = 0;
+        for (int e = threadIdx.x; e < d; e += 32) acc += tot[s * 256 + e];
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) base = acc;
+    }
+    __syncthreads();
+    const int32_t* hrow = hist + ((size_t)s * 256 + d) * T;
+    int32_t* orow = off + ((size_t)s * 256 + d) * T;
+    int carry = base;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int c0 = 0; c0 < T; c0 += 1024) {
+        int i = c0 + threadIdx.x;
+        int v = i < T ? hrow[i] : 0;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int ws = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, ws, o);
+                if (lane >= o) ws += y;
+            }
+            wsum[lane] = ws;
+        }
+        __syncthreads();
+        int excl = x - v + (w ? wsum[w - 1] : 0);
+        if (i < T) orow[i] = carry + excl;
+        int total = wsum[31];
+        __syncthreads();
+        carry += total;
+    }
+}
+
+// Stable scatter of one 8-bit digit.  A tile is processed in rounds of 256
+// consecutive keys; within a round, warps rank equal digits with match_any and
+// a per-digit prefix over warps keeps the input order.
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t* __restrict__ ki0,
+                                                               const int32_t* __restrict__ vi0,
+                                                               const uint64_t* __restrict__ ki1,
+                                                               const int32_t* __restrict__ vi1, uint64_t* ko0,
+                                                               int32_t* vo0, uint64_t* ko1, int32_t* vo1, int n,
+                                                               int shift, int T, const int32_t* __restrict__ off) {
+    __shared__ int run[256];
+    __shared__ int wcnt[kSortThreads / 32][256];
+    __shared__ int base[256];
+    const int s = blockIdx.y, t = blockIdx.x, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const uint64_t* ki = s ? ki1 : ki0;
+    const int32_t* vi = s ? vi1 : vi0;
+    uint64_t* ko = s ? ko1 : ko0;
+    int32_t* vo = s ? vo1 : vo0;
+    base[tid] = off[((size_t)s * 256 + tid) * T + t];
+    run[tid] = 0;
+    for (int r = 0; r < kSortRounds; ++r) {
+        const int i = t * kSortTile + r * kSortThreads + tid;
+        const bool valid = i < n;
+        uint64_t k = valid ? ki[i] : 0;
+        int v = valid ? vi[i] : 0;
+        int d = valid ? (int)((k >> shift) & 255u) : 256;
+#pragma unroll
+        for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][tid] = 0;
+        __syncthreads();
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int rank = __popc(peers & lanemask_lt());
+        if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        {
+            int acc = run[tid];
+#pragma unroll
+            for (int w = 0; w < kSortThreads / 32; ++w) {
+                int c = wcnt[w][tid];
+                wcnt[w][tid] = acc;
+                acc += c;
+            }
+            run[tid] = acc;
+        }
+        __syncthreads();
+        if (valid) {
+            int pos = base[d] + wcnt[warp][d] + rank;
+            ko[pos] = k;
+            vo[pos] = v;
+        }
+        __syncthreads();
+    }
+}
+
+static inline int nblk(int64_t n, int b) { return (int)std::max<int64_t>((n + b - 1) / b, 1); }
+
+// One LSD pass over both sorts: (keys,vals)[src..src+1] -> [dst..dst+1].
+static fmm_status sort_pass(Tree& t, cudaStream_t s, int src, int dst, int shift) {
+    const int n = (int)t.n;
+    const int T = nblk(n, kSortTile);
+    FMM_CUDA(cudaMemsetAsync(t.d_sort_tot, 0, 2 * 256 * sizeof(int32_t), s));
+    dim3 g(T, 2);
+    k_sort_hist<<<g, kSortThreads, 0, s>>>(t.d_keys[src], t.d_keys[src + 1], n, shift, T, t.d_sort_hist,
+                                           t.d_sort_tot);
+    k_sort_scan<<<dim3(256, 2), 1024, 0, s>>>(t.d_sort_hist, t.d_sort_tot, T, t.d_sort_off);
+    k_sort_scatter<<<g, kSortThreads, 0, s>>>(t.d_keys[src], t.d_vals[src], t.d_keys[src + 1], t.d_vals[src + 1],
+                                              t.d_keys[dst], t.d_vals[dst], t.d_keys[dst + 1], t.d_vals[dst + 1], n,
+                                              shift, T, t.d_sort_off);
+    FMM_CUDA(cudaGetLastError());
+    return FMM_OK;
+}
+
+// ======================================================= segmented partition
+
+// Side flags of a contiguous cut: entry at position i of list A goes to side 1
+// when its offset inside its segment is >= nzero of that segment.
+__global__ void k_mark(const int32_t* __restrict__ A, int n, const int32_t* __restrict__ start,
+                       const int32_t* __restrict__ nzero, int K, uint8_t* side) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int k = find_seg(start, K, i);
+    side[A[i]] = (uint8_t)((i - start[k]) >= nzero[k]);
+}
+
+__device__ __forceinline__ int block_excl_scan(int v, int* wsum, int& total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int ws = lane < nw ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, ws, o);
+            if (lane >= o) ws += y;
+        }
+        wsum[lane] = ws;
+    }
+    __syncthreads();
+    total = wsum[nw - 1];
+    int r = x - v + (w ? wsum[w - 1] : 0);
+    __syncthreads();
+    return r;
+}
+
+// Pass 1: ones per tile, and for every segment that starts inside the tile the
+// number of ones in the tile before that start.
+__global__ void __launch_bounds__(kPartThreads) k_part_count(const int32_t* __restrict__ A,
+                                                             const uint8_t* __restrict__ side, int n,
+                                                             const int32_t* __restrict__ start, int K,
+                                                             int32_t* tile_cnt, int32_t* seg_lc) {
+    __shared__ int wsum[32];
+    const int t = blockIdx.x;
+    const int i0 = t * kPartTile + threadIdx.x * kPartItems;
+    int f[kPartItems];
+    int sum = 0;
+#pragma unroll
+    for (int j = 0; j < kPartItems; ++j) {
+        int i = i0 + j;
+        f[j] = i < n ? (int)side[A[i]] : 0;
+        sum += f[j];
+    }
+    int total;
+    int excl = block_excl_scan(sum, wsum, total);
+    if (threadIdx.x == 0) tile_cnt[t] = total;
+    if (i0 < n) {
+        int k = find_seg(start, K, i0);
+        int acc = excl;
+#pragma unroll
+        for (int j = 0; j < kPartItems; ++j) {
+            int i = i0 + j;
+            if (i < n) {
+                while (k + 1 < K && start[k + 1] <= i) ++k;
+                if (start[k] == i) seg_lc[k] = acc;
+            }
+            acc += f[j];
+        }
+    }
+}
+
+// Pass 2: exclusive scan of the tile counts (one block).
+__global__ void __launch_bounds__(1024) k_part_scan(const int32_t* __restrict__ cnt, int T, int32_t* pre) {
+    __shared__ int wsum[32];
+    int carry = 0;
+    for (int c0 = 0; c0 < T; c0 += 1024) {
+        int i = c0 + threadIdx.x;
+        int v = i < T ? cnt[i] : 0;
+        int total;
+        int e = block_excl_scan(v, wsum, total);
+        if (i < T) pre[i] = carry + e;
+        carry += total;
+    }
+}
+
+// Pass 3: stable scatter.  Zeros keep their order at the front of their
+// segment, ones keep their order after the segment's nzero zeros.
+__global__ void __launch_bounds__(kPartThreads) k_part_scatter(const int32_t* __restrict__ A,
+                                                               const uint8_t* __restrict__ side, int n,
+                                                               const int32_t* __restrict__ start,
+                                                               const int32_t* __restrict__ nzero, int K,
+                                                               const int32_t* __restrict__ tile_pre,
+                                                               const int32_t* __restrict__ seg_lc, int32_t* out) {
+    __shared__ int wsum[32];
+    const int t = blockIdx.x;
+    const int i0 = t * kPartTile + threadIdx.x * kPartItems;
+    int f[kPartItems], a[kPartItems];
+    int sum = 0;
+#pragma unroll
+    for (int j = 0; j < kPartItems; ++j) {
+        int i = i0 + j;
+        a[j] = i < n ? A[i] : 0;
+        f[j] = i < n ? (int)side[a[j]] : 0;
+        sum += f[j];
+    }
+    int total;
+    int excl = block_excl_scan(sum, wsum, total);
+    if (i0 >= n) return;
+    int Pi = tile_pre[t] + excl;
+    int k = find_seg(start, K, i0);
+    int s = start[k];
+    int Ps = tile_pre[s / kPartTile] + seg_lc[k];
+#pragma unroll
+    for (int j = 0; j < kPartItems; ++j) {
+        int i = i0 + j;
+        if (i < n) {
+            while (k + 1 < K && start[k + 1] <= i) {
+                ++k;
+                s = start[k];
+                Ps = tile_pre[s / kPartTile] + seg_lc[k];
+            }
+            int ones = Pi - Ps;
+            int dst = f[j] ? s + nzero[k] + ones : s + (i - s) - ones;
+            out[dst] = a[j];
+        }
+        Pi += f[j];
+    }
+}
+
+static fmm_status partition(Tree& t, cudaStream_t s, const int32_t* A, const uint8_t* side, const SegTable& seg,
+                            int32_t* out) {
+    const int n = (int)t.n;
+    const int T = nblk(n, kPartTile);
+    k_part_count<<<T, kPartThreads, 0, s>>>(A, side, n, seg.d_start, seg.K, t.d_tile_cnt, t.d_seg_lc);
+    k_part_scan<<<1, 1024, 0, s>>>(t.d_tile_cnt, T, t.d_tile_pre);
+    k_part_scatter<<<T, kPartThreads, 0, s>>>(A, side, n, seg.d_start, seg.d_nzero, seg.K, t.d_tile_pre, t.d_seg_lc,
+                                              out);
+    FMM_CUDA(cudaGetLastError());
+    return FMM_OK;
+}
+
+// ================================================================ geometry
+
+// Box geometry from the first/last entries of the box's x- and y-lists:
+// centre = midpoint of the tight bounding box, radius = half its diagonal
+// (FP64 with explicit rounding, no contraction, so values are reproducible).
+__global__ void k_geom(const int32_t* __restrict__ ids, int cnt, const int32_t* __restrict__ X,
+                       const int32_t* __restrict__ Y, const double2* __restrict__ xy,
+                       const int32_t* __restrict__ bstart, const int32_t* __restrict__ bcount,
+                       const int32_t* __restrict__ inst, const int64_t* __restrict__ inst_box_off, double2* center,
+                       double* radius, double* rho, float4* chl, float* rho32, int is_root_level) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= cnt) return;
+    const int b = ids[q];
+    const int s = bstart[b], e = s + bcount[b] - 1;
+    const double x0 = xy[X[s]].x, x1 = xy[X[e]].x;
+    const double y0 = xy[Y[s]].y, y1 = xy[Y[e]].y;
+    const double cx = __dmul_rn(0.5, __dadd_rn(x0, x1));
+    const double cy = __dmul_rn(0.5, __dadd_rn(y0, y1));
+    const double dx = __dsub_rn(x1, x0), dy = __dsub_rn(y1, y0);
+    const double r = __dmul_rn(0.5, __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy))));
+    center[b] = make_double2(cx, cy);
+    radius[b] = r;
+    const float r32 = r >= 1e-30 ? __double2float_rn(r) : 0.0f;
+    rho32[b] = r32;
+    rho[b] = (double)r32;
+    double ox = cx, oy = cy;
+    if (!is_root_level) {
+        const double2 o = center[inst_box_off[inst[b]]];
+        ox = o.x;
+        oy = o.y;
+    }
+    const double ex = __dsub_rn(cx, ox), ey = __dsub_rn(cy, oy);
+    const float hx = __double2float_rn(ex), hy = __double2float_rn(ey);
+    chl[b] = make_float4(hx, hy, __double2float_rn(__dsub_rn(ex, (double)hx)),
+                         __double2float_rn(__dsub_rn(ey, (double)hy)));
+}
+
+// Sorted point data: permutation, FP64 copy, FP32 hi/lo split relative to the
+// instance origin (root centre), and the leaf of every sorted position.
+__global__ void k_finalize(const int32_t* __restrict__ Y, int n, const double2* __restrict__ xy,
+                           const int32_t* __restrict__ leaf_start /*nleaf+1*/, const int32_t* __restrict__ leaf_ids,
+                           int nleaf, const int32_t* __restrict__ inst, const int64_t* __restrict__ inst_box_off,
+                           const double2* __restrict__ center, int32_t* perm, double2* pts, float4* pos4,
+                           int32_t* leaf_of) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int id = Y[i];
+    perm[i] = id;
+    const double2 p = xy[id];
+    pts[i] = p;
+    const int lf = leaf_ids[find_seg(leaf_start, nleaf, i)];
+    leaf_of[i] = lf;
+    const double2 o = center[inst_box_off[inst[lf]]];
+    const double ex = __dsub_rn(p.x, o.x), ey = __dsub_rn(p.y, o.y);
+    const float hx = __double2float_rn(ex), hy = __double2float_rn(ey);
+    pos4[i] = make_float4(hx, hy, __double2float_rn(__dsub_rn(ex, (double)hx)),
+                          __double2float_rn(__dsub_rn(ey, (double)hy)));
+}
+
+// ================================================================== lists
+
+__global__ void k_lists_root(const int64_t* __restrict__ inst_box_off, int ninst, int32_t* nstrong, int32_t* strong,
+                             int32_t* nweak, int scap) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= ninst) return;
+    int r = (int)inst_box_off[b];
+    nstrong[r] = 1;
+    strong[(size_t)r * scap] = r;
+    nweak[r] = 0;
+}
+
+// eq (2.3): R + theta*r <= theta*d, with d > 0 required.
+__device__ __forceinline__ bool well_separated(double2 ca, double ra, double2 cb, double rb, double theta) {
+    const double dx = __dsub_rn(ca.x, cb.x), dy = __dsub_rn(ca.y, cb.y);
+    const double d = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+    const double R = ra > rb ? ra : rb;
+    const double r = ra > rb ? rb : ra;
+    return d > 0.0 && __dadd_rn(R, __dmul_rn(theta, r)) <= __dmul_rn(theta, d);
+}
+
+// Coupling of one level (Sec. 2.1): children of the parent's strongly coupled
+// boxes are strong unless well separated (then weak); a box is always strong
+// with itself.
+__global__ void k_lists(const int32_t* __restrict__ ids, int cnt, const int32_t* __restrict__ parent,
+                        const int32_t* __restrict__ child0, const double2* __restrict__ center,
+                        const double* __restrict__ radius, double theta, int32_t* nstrong, int32_t* strong,
+                        int32_t* nweak, int32_t* weak, int scap, int wcap, unsigned* status) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= cnt) return;
+    const int b = ids[q];
+    const int P = parent[b];
+    const double2 cb = center[b];
+    const double rb = radius[b];
+    int ns = 0, nw = 0;
+    const int np = nstrong[P];
+    bool ovs = false, ovw = false;
+    for (int j = 0; j < np; ++j) {
+        const int Q = strong[(size_t)P * scap + j];
+        const int c0 = child0[Q];
+        for (int c = 0; c < 4; ++c) {
+            const int h = c0 + c;
+            const bool sep = (h != b) && well_separated(cb, rb, center[h], radius[h], theta);
+            if (sep) {
+                if (nw < wcap) weak[(size_t)b * wcap + nw] = h;
+                else ovw = true;
+                ++nw;
+            } else {
+                if (ns < scap) strong[(size_t)b * scap + ns] = h;
+                else ovs = true;
+                ++ns;
+            }
+        }
+    }
+    nstrong[b] = ns < scap ? ns : scap;
+    nweak[b] = nw < wcap ? nw : wcap;
+    if (ovs) atomicOr(status, ST_STRONG_OVERFLOW);
+    if (ovw) atomicOr(status, ST_WEAK_OVERFLOW);
+}
+
+// Totals for fmm_get_tree_info: weak pairs, leaf strong pairs, P2P point pairs.
+__global__ void k_count(const int32_t* __restrict__ leaf_ids, int nleaf, int nbox, const int32_t* __restrict__ nstrong,
+                        const int32_t* __restrict__ strong, const int32_t* __restrict__ nweak,
+                        const int32_t* __restrict__ bcount, int scap, unsigned long long* out) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long w = 0, sl = 0, pp = 0;
+    if (q < nbox) w = (unsigned long long)nweak[q];
+    if (q < nleaf) {
+        const int b = leaf_ids[q];
+        const int ns = nstrong[b];
+        sl = ns;
+        unsigned long long src = 0;
+        for (int j = 0; j < ns; ++j) src += bcount[strong[(size_t)b * scap + j]];
+        pp = src * (unsigned long long)bcount[b];
+    }
+    for (int o = 16; o; o >>= 1) {
+        w += __shfl_xor_sync(0xffffffffu, w, o);
+        sl += __shfl_xor_sync(0xffffffffu, sl, o);
+        pp += __shfl_xor_sync(0xffffffffu, pp, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (w) atomicAdd(out + 0, w);
+        if (sl) atomicAdd(out + 1, sl);
+        if (pp) atomicAdd(out + 2, pp);
+    }
+}
+
+// ============================================================ orchestration
+
+static void dfree(void* p) {
+    if (p) cudaFree(p);
+}
+
+template <typename T>
+static fmm_status dalloc(T** p, size_t count) {
+    dfree(*p);
+    *p = nullptr;
+    cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T));
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        set_error("device allocation failed");
+        return FMM_ERR_OOM;
+    }
+    FMM_CUDA(e);
+    return FMM_OK;
+}
+
+fmm_status alloc_build(Tree& t) {
+    const size_t n = (size_t)t.n;
+    fmm_status st;
+    for (int i = 0; i < 4; ++i) {
+        if ((st = dalloc(&t.d_keys[i], n))) return st;
+        if ((st = dalloc(&t.d_vals[i], n))) return st;
+    }
+    if ((st = dalloc(&t.d_X2, n))) return st;
+    if ((st = dalloc(&t.d_Y2, n))) return st;
+    if ((st = dalloc(&t.d_sideX, n))) return st;
+    if ((st = dalloc(&t.d_sideY, n))) return st;
+    const int64_t T = std::max<int64_t>(nblk(t.n, kPartTile), nblk(t.n, kSortTile));
+    if ((st = dalloc(&t.d_tile_cnt, T))) return st;
+    if ((st = dalloc(&t.d_tile_pre, T))) return st;
+    if ((st = dalloc(&t.d_seg_lc, t.segs_cap + 1))) return st;
+    if ((st = dalloc(&t.d_sort_hist, 2 * 256 * (size_t)T))) return st;
+    if ((st = dalloc(&t.d_sort_off, 2 * 256 * (size_t)T))) return st;
+    if ((st = dalloc(&t.d_sort_tot, 2 * 256))) return st;
+    if ((st = dalloc(&t.d_perm, n))) return st;
+    if ((st = dalloc(&t.d_leaf_of, n))) return st;
+    if ((st = dalloc(&t.d_pts, n))) return st;
+    if ((st = dalloc(&t.d_pos4, n))) return st;
+    const size_t nb = (size_t)t.nbox;
+    if ((st = dalloc(&t.d_center, nb))) return st;
+    if ((st = dalloc(&t.d_radius, nb))) return st;
+    if ((st = dalloc(&t.d_rho, nb))) return st;
+    if ((st = dalloc(&t.d_chl, nb))) return st;
+    if ((st = dalloc(&t.d_rho32, nb))) return st;
+    if ((st = dalloc(&t.d_nstrong, nb))) return st;
+    if ((st = dalloc(&t.d_nweak, nb))) return st;
+    if (!t.d_status) {
+        if ((st = dalloc(reinterpret_cast<unsigned long long**>(&t.d_status), 8))) return st;
+    }
+    return alloc_lists(t);
+}
+
+fmm_status alloc_lists(Tree& t) {
+    fmm_status st;
+    if ((st = dalloc(&t.d_strong, (size_t)t.nbox * t.scap))) return st;
+    if ((st = dalloc(&t.d_weak, (size_t)t.nbox * t.wcap))) return st;
+    return FMM_OK;
+}
+
+fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s) {
+    const int n = (int)t.n;
+    const double2* xy = reinterpret_cast<const double2*>(d_xy);
+    FMM_CUDA(cudaMemsetAsync(t.d_status, 0, sizeof(unsigned), s));
+    k_keys<<<nblk(n, 256), 256, 0, s>>>(xy, n, t.d_keys[0], t.d_keys[1], t.d_vals[0], t.d_vals[1], t.d_status);
+    FMM_CUDA(cudaGetLastError());
+    // 8 LSD passes over the 64-bit keys (+2 over the instance index when
+    // batched); an even number of passes leaves the result in buffers 0/1.
+    int src = 0;
+    fmm_status st;
+    for (int pass = 0; pass < 8; ++pass) {
+        if ((st = sort_pass(t, s, src, 2 - src, 8 * pass))) return st;
+        src = 2 - src;
+    }
+    if (t.ninst > 1) {
+        k_inst_keys<<<nblk(n, 256), 256, 0, s>>>(t.d_vals[src], t.d_vals[src + 1], t.d_inst_ptoff, t.ninst, n,
+                                                 t.d_keys[src], t.d_keys[src + 1]);
+        for (int pass = 0; pass < 2; ++pass) {
+            if ((st = sort_pass(t, s, src, 2 - src, 8 * pass))) return st;
+            src = 2 - src;
+        }
+    }
+    int32_t* X = t.d_vals[src];
+    int32_t* Y = t.d_vals[src + 1];
+    int32_t* X2 = t.d_X2;
+    int32_t* Y2 = t.d_Y2;
+    const LevelList& L0 = t.level_boxes[0];
+    k_geom<<<nblk(L0.count, 128), 128, 0, s>>>(L0.d_ids, L0.count, X, Y, xy, t.d_bstart, t.d_bcount, t.d_inst,
+                                               t.d_inst_boxoff, t.d_center, t.d_radius, t.d_rho, t.d_chl, t.d_rho32,
+                                               1);
+    FMM_CUDA(cudaGetLastError());
+    for (int l = 0; l + 1 < t.Lmax; ++l) {
+        const SegTable& sx = t.seg_x[l];
+        const SegTable& sy = t.seg_y[l];
+        k_mark<<<nblk(n, 256), 256, 0, s>>>(X, n, sx.d_start, sx.d_nzero, sx.K, t.d_sideX);
+        if ((st = partition(t, s, Y, t.d_sideX, sx, Y2))) return st;
+        std::swap(Y, Y2);
+        k_mark<<<nblk(n, 256), 256, 0, s>>>(Y, n, sy.d_start, sy.d_nzero, sy.K, t.d_sideY);
+        if ((st = partition(t, s, X, t.d_sideY, sy, X2))) return st;
+        std::swap(X, X2);
+        const LevelList& Ll = t.level_boxes[l + 1];
+        k_geom<<<nblk(Ll.count, 128), 128, 0, s>>>(Ll.d_ids, Ll.count, X, Y, xy, t.d_bstart, t.d_bcount, t.d_inst,
+                                                   t.d_inst_boxoff, t.d_center, t.d_radius, t.d_rho, t.d_chl,
+                                                   t.d_rho32, 0);
+        FMM_CUDA(cudaGetLastError());
+    }
+    k_finalize<<<nblk(n, 256), 256, 0, s>>>(Y, n, xy, t.d_leaf_start, t.leaves.d_ids, (int)t.nleaf, t.d_inst,
+                                            t.d_inst_boxoff, t.d_center, t.d_perm, t.d_pts, t.d_pos4, t.d_leaf_of);
+    FMM_CUDA(cudaGetLastError());
+    return FMM_OK;
+}
+
+fmm_status run_lists(Tree& t, cudaStream_t s) {
+    k_lists_root<<<nblk(t.ninst, 128), 128, 0, s>>>(t.d_inst_boxoff, t.ninst, t.d_nstrong, t.d_strong, t.d_nweak,
+                                                    t.scap);
+    for (int l = 1; l < t.Lmax; ++l) {
+        const LevelList& Ll = t.level_boxes[l];
+        k_lists<<<nblk(Ll.count, 128), 128, 0, s>>>(Ll.d_ids, Ll.count, t.d_parent, t.d_child0, t.d_center,
+                                                    t.d_radius, t.theta, t.d_nstrong, t.d_strong, t.d_nweak,
+                                                    t.d_weak, t.scap, t.wcap, t.d_status);
+    }
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(t.d_status) + 1;
+    FMM_CUDA(cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), s));
+    const int64_t m = std::max<int64_t>(t.nbox, t.nleaf);
+    k_count<<<nblk(m, 256), 256, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, (int)t.nbox, t.d_nstrong, t.d_strong,
+                                         t.d_nweak, t.d_bcount, t.scap, cnt);
+    FMM_CUDA(cudaGetLastError());
+    return FMM_OK;
+}
+
+}  // namespace fmm

@@ -1,0 +1,444 @@
+// C ABI of the FMM library: argument checks, tree life cycle, evaluation
+// (eager or replayed from a captured CUDA graph), export and diagnostics.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+fmm_status cuda_fail(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return FMM_ERR_OOM;
+    }
+    return FMM_ERR_CUDA;
+}
+
+static fmm_status invalid(const std::string& msg) {
+    g_err = msg;
+    return FMM_ERR_INVALID_ARG;
+}
+
+static int max_levels_for(int64_t n) {  // largest N_levels with 4^(L-1) <= n
+    int L = 1;
+    while (L < 15 && (int64_t(1) << (2 * L)) <= n) ++L;
+    return L;
+}
+
+int default_nlevels(int64_t n, int p, int path) {
+    // Leaf size that balances P2P (eq 2.4) against M2L (eq 2.5) for the
+    // measured unit costs of this implementation; the autotuner refines it.
+    (void)p;
+    const double target = path == FMM_PATH_FP32 ? 24.0 : 16.0;
+    const int Lmax = max_levels_for(n);
+    int best = 1;
+    double bestd = 1e300;
+    for (int L = 1; L <= Lmax; ++L) {
+        const double per = (double)n / std::pow(4.0, L - 1);
+        const double d = std::fabs(std::log(per / target));
+        if (d < bestd) {
+            bestd = d;
+            best = L;
+        }
+    }
+    return best;
+}
+
+static fmm_status check_params(const fmm_params* prm) {
+    if (!prm) return invalid("params is NULL");
+    if (prm->p < 1 || prm->p > FMM_P_MAX) return invalid("p must be in [1, 32]");
+    if (!(prm->theta > 0.0 && prm->theta < 1.0)) return invalid("theta must be in (0, 1)");
+    if (prm->path != FMM_PATH_FP32 && prm->path != FMM_PATH_FP64) return invalid("path must be 0 (FP32) or 1 (FP64)");
+    if (prm->nlevels < 0) return invalid("nlevels must be >= 0");
+    return FMM_OK;
+}
+
+static void invalidate_graph(Tree& t) {
+    if (t.graph) cudaGraphExecDestroy(t.graph);
+    t.graph = nullptr;
+    for (auto& k : t.graph_key) k = nullptr;
+}
+
+static void apply_params(Tree& t, const fmm_params* prm) {
+    t.p = prm->p;
+    t.P = compiled_order(prm->p);
+    t.PS = (t.P + 1) & ~1;
+    t.theta = prm->theta;
+    t.path = prm->path;
+    t.flags = prm->flags;
+}
+
+static fmm_status ensure_streams(Tree& t) {
+    if (!t.s_aux) FMM_CUDA(cudaStreamCreateWithFlags(&t.s_aux, cudaStreamNonBlocking));
+    if (!t.ev_fork) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_fork, cudaEventDisableTiming));
+    if (!t.ev_join) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_join, cudaEventDisableTiming));
+    for (auto& e : t.ev_t)
+        if (!e) FMM_CUDA(cudaEventCreate(&e));
+    return FMM_OK;
+}
+
+// Tree build + lists, with the list capacities doubled and the lists rebuilt
+// when a box overflows them.
+static fmm_status build_all(Tree& t, const double* d_xy, cudaStream_t s) {
+    fmm_status st = run_tree_build(t, d_xy, s);
+    if (st) return st;
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        if ((st = run_lists(t, s))) return st;
+        unsigned long long hbuf[4] = {0, 0, 0, 0};
+        FMM_CUDA(cudaMemcpyAsync(hbuf, t.d_status, sizeof(hbuf), cudaMemcpyDeviceToHost, s));
+        FMM_CUDA(cudaStreamSynchronize(s));
+        const unsigned bits = (unsigned)(hbuf[0] & 0xffffffffu);
+        if (bits & ST_NONFINITE) {
+            set_error("non-finite point coordinate");
+            return FMM_ERR_NONFINITE;
+        }
+        if (!(bits & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW))) {
+            t.h_counts[0] = hbuf[1];
+            t.h_counts[1] = hbuf[2];
+            t.h_counts[2] = hbuf[3];
+            return FMM_OK;
+        }
+        if (bits & ST_STRONG_OVERFLOW) t.scap *= 2;
+        if (bits & ST_WEAK_OVERFLOW) t.wcap *= 2;
+        invalidate_graph(t);
+        if ((st = alloc_lists(t))) return st;
+        FMM_CUDA(cudaMemsetAsync(t.d_status, 0, sizeof(unsigned), s));
+    }
+    set_error("coupling lists kept overflowing");
+    return FMM_ERR_OOM;
+}
+
+static fmm_status shape_and_build(Tree& t, const double* d_xy, cudaStream_t s, bool reshape) {
+    fmm_status st;
+    if (reshape) {
+        invalidate_graph(t);
+        if ((st = build_shape(t))) return st;
+        if ((st = alloc_build(t))) return st;
+        t.eval_nbox = 0;  // force the workspace to follow the new shape
+    }
+    if ((st = ensure_streams(t))) return st;
+    return build_all(t, d_xy, s);
+}
+
+static void release(Tree* t) {
+    if (!t) return;
+    invalidate_graph(*t);
+    void* ptrs[] = {t->d_bstart, t->d_bcount, t->d_parent, t->d_child0, t->d_inst, t->d_inst_ptoff,
+                    t->d_inst_boxoff, t->d_leaf_start, t->d_X2, t->d_Y2, t->d_sideX, t->d_sideY, t->d_tile_cnt,
+                    t->d_tile_pre, t->d_seg_lc, t->d_sort_hist, t->d_sort_tot, t->d_sort_off, t->d_perm,
+                    t->d_leaf_of, t->d_pts, t->d_pos4, t->d_center, t->d_radius, t->d_rho, t->d_chl, t->d_rho32,
+                    t->d_nstrong, t->d_strong, t->d_nweak, t->d_weak, t->d_status, t->d_gam, t->d_near, t->d_M64,
+                    t->d_M32, t->d_Lm2l, t->d_L64, t->d_L32};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (int i = 0; i < 4; ++i) {
+        if (t->d_keys[i]) cudaFree(t->d_keys[i]);
+        if (t->d_vals[i]) cudaFree(t->d_vals[i]);
+    }
+    for (auto& l : t->level_boxes)
+        if (l.d_ids) cudaFree(l.d_ids);
+    for (auto& l : t->level_parents)
+        if (l.d_ids) cudaFree(l.d_ids);
+    if (t->leaves.d_ids) cudaFree(t->leaves.d_ids);
+    for (auto& s : t->seg_x) {
+        if (s.d_start) cudaFree(s.d_start);
+        if (s.d_nzero) cudaFree(s.d_nzero);
+    }
+    for (auto& s : t->seg_y) {
+        if (s.d_start) cudaFree(s.d_start);
+        if (s.d_nzero) cudaFree(s.d_nzero);
+    }
+    if (t->s_aux) cudaStreamDestroy(t->s_aux);
+    if (t->ev_fork) cudaEventDestroy(t->ev_fork);
+    if (t->ev_join) cudaEventDestroy(t->ev_join);
+    for (auto e : t->ev_t)
+        if (e) cudaEventDestroy(e);
+}
+
+static fmm_status check_pending() {
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(e, "earlier asynchronous work");
+    }
+    return FMM_OK;
+}
+
+}  // namespace fmm
+
+using namespace fmm;
+
+
+extern "C" {
+
+const char* fmm_status_string(fmm_status s) {
+    switch (s) {
+        case FMM_OK: return "ok";
+        case FMM_ERR_INVALID_ARG: return "invalid argument";
+        case FMM_ERR_CUDA: return "CUDA error";
+        case FMM_ERR_OOM: return "out of memory";
+        case FMM_ERR_TIMEOUT: return "device wait timed out";
+        case FMM_ERR_NONFINITE: return "non-finite input";
+    }
+    return "unknown status";
+}
+
+const char* fmm_last_error(void) { return g_err.c_str(); }
+
+int fmm_default_nlevels(int64_t n, int p, int path) { return n < 1 ? 0 : default_nlevels(n, p, path); }
+
+static fmm_status build_common(const double* d_xy, const std::vector<int64_t>& offs, const fmm_params* prm,
+                               const int* h_nlevels, bool batched, void* stream, fmm_tree** out) {
+    if (!out) return invalid("out is NULL");
+    *out = nullptr;
+    fmm_status st = check_params(prm);
+    if (st) return st;
+    if (!d_xy) return invalid("d_xy is NULL");
+    const int B = (int)offs.size() - 1;
+    if (B < 1) return invalid("no instance");
+    if (offs[0] != 0) return invalid("offsets must start at 0");
+    for (int b = 0; b < B; ++b)
+        if (offs[b + 1] - offs[b] < 1) return invalid("every instance needs >= 1 point");
+    if (offs[B] >= (int64_t(1) << 31) - 1) return invalid("n must be < 2^31");
+    if ((st = check_pending())) return st;
+    fmm_tree* h = new (std::nothrow) fmm_tree();
+    if (!h) return FMM_ERR_OOM;
+    Tree& t = h->t;
+    apply_params(t, prm);
+    t.batched = batched;
+    t.n = offs[B];
+    t.ninst = B;
+    t.inst_pt_off = offs;
+    t.inst_levels.resize(B);
+    for (int b = 0; b < B; ++b) {
+        const int64_t nb = offs[b + 1] - offs[b];
+        int L = h_nlevels ? h_nlevels[b] : prm->nlevels;
+        if (L == 0) L = default_nlevels(nb, prm->p, prm->path);
+        if (L < 1 || L > max_levels_for(nb)) {
+            delete h;
+            return invalid("nlevels out of range: need 1 <= nlevels and 4^(nlevels-1) <= points of the instance");
+        }
+        t.inst_levels[b] = L;
+    }
+    st = shape_and_build(t, d_xy, static_cast<cudaStream_t>(stream), true);
+    if (st) {
+        release(&h->t);
+        delete h;
+        return st;
+    }
+    t.tune.accepted = t.inst_levels[0];
+    t.tune.max_levels = max_levels_for(t.n);
+    *out = h;
+    return FMM_OK;
+}
+
+fmm_status fmm_build_tree(const double* d_xy, int64_t n, const fmm_params* prm, void* stream, fmm_tree** out) {
+    if (n < 1) return invalid("n must be >= 1");
+    std::vector<int64_t> offs = {0, n};
+    return build_common(d_xy, offs, prm, nullptr, false, stream, out);
+}
+
+fmm_status fmm_build_tree_batched(const double* d_xy, const int64_t* h_offsets, int B, const fmm_params* prm,
+                                  const int* h_nlevels, void* stream, fmm_tree** out) {
+    if (!h_offsets || B < 1) return invalid("offsets NULL or B < 1");
+    std::vector<int64_t> offs(h_offsets, h_offsets + B + 1);
+    return build_common(d_xy, offs, prm, h_nlevels, true, stream, out);
+}
+
+fmm_status fmm_tree_rebuild(fmm_tree* h, const double* d_xy, const fmm_params* prm, void* stream) {
+    if (!h || !d_xy) return invalid("NULL argument");
+    Tree& t = h->t;
+    fmm_status st;
+    if ((st = check_pending())) return st;
+    bool reshape = false;
+    if (prm) {
+        if ((st = check_params(prm))) return st;
+        if (!t.batched && prm->nlevels != 0 && prm->nlevels != t.inst_levels[0]) {
+            if (prm->nlevels > max_levels_for(t.n)) return invalid("nlevels out of range");
+            t.inst_levels[0] = prm->nlevels;
+            reshape = true;
+        }
+        if (prm->p != t.p || prm->path != t.path) t.eval_nbox = 0;
+        if (prm->theta != t.theta || prm->p != t.p || prm->path != t.path) invalidate_graph(t);
+        const int old_flags = t.flags;
+        apply_params(t, prm);
+        if (old_flags != t.flags) invalidate_graph(t);
+    }
+    return shape_and_build(t, d_xy, static_cast<cudaStream_t>(stream), reshape);
+}
+
+void fmm_tree_destroy(fmm_tree* h) {
+    if (!h) return;
+    release(&h->t);
+    delete h;
+}
+
+static fmm_status eval_common(fmm_tree* h, const double* d_gamma, void* d_phi, void* stream) {
+    if (!h || !d_gamma || !d_phi) return invalid("NULL argument");
+    Tree& t = h->t;
+    fmm_status st;
+    if ((st = check_pending())) return st;
+    if (t.eval_nbox == 0) invalidate_graph(t);
+    if ((st = alloc_eval(t, 1))) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool use_graph = !(t.flags & (FMM_FLAG_NO_GRAPH | FMM_FLAG_TIMING)) && s != nullptr;
+    if (!use_graph) return run_eval(t, d_gamma, d_phi, s);
+    const void* key[4] = {d_gamma, d_phi, (const void*)s, (const void*)(intptr_t)(t.path * 64 + t.P)};
+    if (!t.graph || memcmp(key, t.graph_key, sizeof(key)) != 0) {
+        invalidate_graph(t);
+        FMM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        st = run_eval(t, d_gamma, d_phi, s);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (st) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        FMM_CUDA(e);
+        e = cudaGraphInstantiate(&t.graph, g, 0);
+        cudaGraphDestroy(g);
+        FMM_CUDA(e);
+        memcpy(t.graph_key, key, sizeof(key));
+    }
+    FMM_CUDA(cudaGraphLaunch(t.graph, s));
+    return FMM_OK;
+}
+
+fmm_status fmm_eval(fmm_tree* h, const double* d_gamma, void* d_phi, void* stream) {
+    return eval_common(h, d_gamma, d_phi, stream);
+}
+
+fmm_status fmm_eval_batched(fmm_tree* h, const double* d_gamma, void* d_phi, void* stream) {
+    if (h && !h->t.batched) return invalid("tree was not built by fmm_build_tree_batched");
+    return eval_common(h, d_gamma, d_phi, stream);
+}
+
+fmm_status fmm_eval_backward(fmm_tree* h, const double* d_gamma, const double* d_gphi, double* d_ggamma,
+                             double* d_gxy, void* stream) {
+    if (!h || !d_gamma || !d_gphi) return invalid("NULL argument");
+    if (!d_ggamma && !d_gxy) return FMM_OK;
+    Tree& t = h->t;
+    fmm_status st;
+    if ((st = check_pending())) return st;
+    if ((st = alloc_eval(t, 2))) return st;
+    return run_backward(t, d_gamma, d_gphi, d_ggamma, d_gxy, static_cast<cudaStream_t>(stream));
+}
+
+fmm_status fmm_phase_times(fmm_tree* h, double* out, int nout) {
+    if (!h || !out || nout < 1) return invalid("NULL argument");
+    Tree& t = h->t;
+    if (!t.timing_valid) return invalid("no evaluation with FMM_FLAG_TIMING yet");
+    FMM_CUDA(cudaEventSynchronize(t.ev_t[7]));
+    float ms[7] = {0, 0, 0, 0, 0, 0, 0};
+    FMM_CUDA(cudaEventElapsedTime(&ms[0], t.ev_t[0], t.ev_t[1]));
+    FMM_CUDA(cudaEventElapsedTime(&ms[1], t.ev_t[1], t.ev_t[2]));
+    FMM_CUDA(cudaEventElapsedTime(&ms[2], t.ev_t[2], t.ev_t[3]));
+    FMM_CUDA(cudaEventElapsedTime(&ms[3], t.ev_t[3], t.ev_t[4]));
+    FMM_CUDA(cudaEventElapsedTime(&ms[4], t.ev_t[5], t.ev_t[6]));
+    FMM_CUDA(cudaEventElapsedTime(&ms[5], t.ev_t[4], t.ev_t[7]));
+    FMM_CUDA(cudaEventElapsedTime(&ms[6], t.ev_t[0], t.ev_t[7]));
+    for (int i = 0; i < nout && i < 7; ++i) out[i] = ms[i];
+    return FMM_OK;
+}
+
+fmm_status fmm_get_tree_info(const fmm_tree* h, fmm_tree_info* out) {
+    if (!h || !out) return invalid("NULL argument");
+    const Tree& t = h->t;
+    out->n = t.n;
+    out->ninst = t.ninst;
+    out->nlevels_max = t.Lmax;
+    out->p = t.p;
+    out->path = t.path;
+    out->theta = t.theta;
+    out->nboxes = t.nbox;
+    out->nleaves = t.nleaf;
+    out->n_weak = (int64_t)t.h_counts[0];
+    out->n_strong_leaf = (int64_t)t.h_counts[1];
+    out->p2p_pairs = (int64_t)t.h_counts[2];
+    out->strong_cap = t.scap;
+    out->weak_cap = t.wcap;
+    return FMM_OK;
+}
+
+fmm_status fmm_tree_export(const fmm_tree* h, int what, void* h_dst, int64_t count, void* stream) {
+    if (!h || !h_dst) return invalid("NULL argument");
+    const Tree& t = h->t;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t n = t.n, nb = t.nbox;
+    auto copy = [&](const void* src, int64_t elems, size_t esz) -> fmm_status {
+        if (count < elems) return invalid("host buffer too small");
+        if (!src) return invalid("array not available (no evaluation yet?)");
+        FMM_CUDA(cudaMemcpyAsync(h_dst, src, (size_t)elems * esz, cudaMemcpyDeviceToHost, s));
+        FMM_CUDA(cudaStreamSynchronize(s));
+        return FMM_OK;
+    };
+    switch (what) {
+        case FMM_EXPORT_PERM: return copy(t.d_perm, n, 4);
+        case FMM_EXPORT_BSTART: return copy(t.d_bstart, nb, 4);
+        case FMM_EXPORT_BCOUNT: return copy(t.d_bcount, nb, 4);
+        case FMM_EXPORT_CENTER: return copy(t.d_center, 2 * nb, 8);
+        case FMM_EXPORT_RADIUS: return copy(t.d_radius, nb, 8);
+        case FMM_EXPORT_RHO: return copy(t.d_rho, nb, 8);
+        case FMM_EXPORT_NSTRONG: return copy(t.d_nstrong, nb, 4);
+        case FMM_EXPORT_STRONG: return copy(t.d_strong, nb * t.scap, 4);
+        case FMM_EXPORT_NWEAK: return copy(t.d_nweak, nb, 4);
+        case FMM_EXPORT_WEAK: return copy(t.d_weak, nb * t.wcap, 4);
+        case FMM_EXPORT_INST: {
+            if (count < 3 * (int64_t)t.ninst) return invalid("host buffer too small");
+            int64_t* o = static_cast<int64_t*>(h_dst);
+            for (int b = 0; b < t.ninst; ++b) {
+                o[3 * b] = t.inst_pt_off[b];
+                o[3 * b + 1] = t.inst_box_off[b];
+                o[3 * b + 2] = t.inst_levels[b];
+            }
+            return FMM_OK;
+        }
+        case FMM_EXPORT_NEAR: {
+            if (count < 2 * n) return invalid("host buffer too small");
+            if (!t.d_near || t.eval_nbox == 0) return invalid("no evaluation yet");
+            double* o = static_cast<double*>(h_dst);
+            if (t.path == FMM_PATH_FP64) return copy(t.d_near, 2 * n, 8);
+            std::vector<float> tmp(2 * n);
+            FMM_CUDA(cudaMemcpyAsync(tmp.data(), t.d_near, 2 * n * sizeof(float), cudaMemcpyDeviceToHost, s));
+            FMM_CUDA(cudaStreamSynchronize(s));
+            for (int64_t i = 0; i < 2 * n; ++i) o[i] = tmp[i];
+            return FMM_OK;
+        }
+        case FMM_EXPORT_MPOLE:
+        case FMM_EXPORT_LOCAL: {
+            if (count < 2 * nb * t.p) return invalid("host buffer too small");
+            if (t.eval_nbox == 0) return invalid("no evaluation yet");
+            const size_t PS = (size_t)t.PS;
+            std::vector<double> a64(2 * nb * PS);
+            std::vector<float> a32(2 * nb * PS);
+            const bool mp = what == FMM_EXPORT_MPOLE;
+            FMM_CUDA(cudaMemcpyAsync(a64.data(), mp ? t.d_M64 : t.d_L64, a64.size() * 8, cudaMemcpyDeviceToHost, s));
+            if (mp && t.path == FMM_PATH_FP32)
+                FMM_CUDA(cudaMemcpyAsync(a32.data(), t.d_M32, a32.size() * 4, cudaMemcpyDeviceToHost, s));
+            FMM_CUDA(cudaStreamSynchronize(s));
+            double* o = static_cast<double*>(h_dst);
+            for (int64_t b = 0; b < nb; ++b) {
+                const bool leaf32 = mp && t.path == FMM_PATH_FP32 && t.h_child0[b] < 0;
+                for (int k = 0; k < t.p; ++k) {
+                    const size_t src = 2 * ((size_t)b * PS + k);
+                    o[2 * (b * t.p + k)] = leaf32 ? a32[src] : a64[src];
+                    o[2 * (b * t.p + k) + 1] = leaf32 ? a32[src + 1] : a64[src + 1];
+                }
+            }
+            return FMM_OK;
+        }
+    }
+    return invalid("unknown export id");
+}
+
+}  // extern "C"

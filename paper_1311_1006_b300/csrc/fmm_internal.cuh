@@ -124,18 +124,20 @@ struct Tree {
 
     // autotuner state (AT3b, Algorithm 4)
     struct Tune {
-        double cap = 0.10;
-        int window = 3, period = 8;
-        int iter = 0;           // evaluations seen
-        int since_move = 0;     // evaluations since the last decision
+        double cap = 0.10;      // maximum relative tuning cost
+        int window = 3;         // evaluations per decision (minimum taken)
+        int period = 8;         // accepted evaluations between moves
+        int iter = 0;
+        int since_move = 0;
         std::vector<double> win;
-        double base_min = 0;    // min time over the window of the accepted configuration
+        double base_min = 0;    // windowed minimum time of the accepted N_levels
         int accepted = 0;       // accepted N_levels
         int trial = 0;          // N_levels on trial (0 = none)
+        int trial_dir = 0;
         int nldir = +1;
         double basetime = 0;    // accumulated time of accepted evaluations
+        int accepted_evals = 0;
         double upcost = 0, downcost = 0;
-        int upinterval = 0, downinterval = 0;  // evaluations to wait before the next up/down move
         int wait_up = 0, wait_down = 0;
         int max_levels = 1;
     } tune;
@@ -165,7 +167,15 @@ fmm_status run_backward(Tree& t, const double* d_gamma, const double* d_gphi, do
 // Autotuner (host).
 int default_nlevels(int64_t n, int p, int path);
 
+// Smallest compiled expansion order >= p (kernels are templates on the order).
+int compiled_order(int p);
+
 }  // namespace fmm
+
+// The opaque handle of the C ABI.
+struct fmm_tree {
+    fmm::Tree t;
+};
 
 // ---------------------------------------------------------------- device
 #ifdef __CUDACC__

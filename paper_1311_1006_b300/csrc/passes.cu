@@ -1,0 +1,813 @@
+// FMM passes on the device (Sec. 2.1, Fig 2.2 of the paper): P2M, M2M, M2L,
+// L2L, L2P and the P2P near-field sum for the harmonic kernel
+//     Phi(z) = sum_j Gamma_j / (z - z_j).
+//
+// Expansions are stored SCALED by the box's scale radius rho, so that every
+// ratio entering a shift is <= 1 in magnitude and FP32 never under/overflows:
+//   multipole  M(z) = sum_k at_k rho^k / (z-c)^(k+1),  at_k = sum_j Gamma_j ((z_j-c)/rho)^k
+//   local      L(z) = sum_l bt_l ((z-c)/rho)^l
+// Shifts (all derived from the binomial series of the textbook expansions):
+//   M2M  at'_n = sum_{k<=n} C(n,k) (sigma^k at_k) q^(n-k),   sigma = rho_c/rho_P, q = (c_c-c_P)/rho_P
+//   M2L  bt_l += (-rho_L u)^l u sum_k C(k+l,l) (rho_M u)^k at_k,   u = 1/(c_L - c_M)
+//   L2L  bt'_m = sigma^m sum_{l>=m} C(l,m) bt_l q^(l-m)
+// M2M and L2L run as in-place Taylor shifts (p(p-1)/2 complex multiply-adds,
+// no binomial table); M2L applies the binomial matrix with the coefficients
+// C(k+l,l) folded into the instruction stream as immediates (p is a template
+// parameter).
+//
+// Precision paths: FP32 path = P2M, M2L, L2P, P2P in FP32 (FP32 accumulation),
+// M2M / L2L and the per-level local sums in FP64.  FP64 path = all FP64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+static inline int nblk(int64_t n, int b) { return (int)std::max<int64_t>((n + b - 1) / b, 1); }
+
+// Binomial coefficients C(n,k), n < 64, k < 32, by Pascal's rule at compile
+// time; kernels index them with unrolled (compile-time) indices.
+struct BinomTable {
+    float f[64][32];
+    double d[64][32];
+};
+static constexpr BinomTable make_binom() {
+    BinomTable t{};
+    double row[64] = {};
+    for (int n = 0; n < 64; ++n) {
+        for (int k = n; k >= 1; --k) row[k] = row[k] + row[k - 1];
+        row[0] = 1.0;
+        for (int k = 0; k < 32; ++k) {
+            t.d[n][k] = k <= n ? row[k] : 0.0;
+            t.f[n][k] = (float)t.d[n][k];
+        }
+    }
+    return t;
+}
+__constant__ BinomTable c_binom = make_binom();
+
+// ------------------------------------------------------------------ gather
+
+__global__ void k_gather32(const double2* __restrict__ in, const int32_t* __restrict__ perm, int n, float2* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 g = in[perm[i]];
+    out[i] = make_float2((float)g.x, (float)g.y);
+}
+__global__ void k_gather64(const double2* __restrict__ in, const int32_t* __restrict__ perm, int n, double2* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = in[perm[i]];
+}
+
+// --------------------------------------------------------------------- P2M
+
+// One thread per leaf: at_k = sum_j Gamma_j w_j^k, w_j = (z_j - c)/rho, FP32.
+// Point offsets use the hi/lo split so w keeps full FP32 accuracy.
+template <int P>
+__global__ void __launch_bounds__(128) k_p2m32(const int32_t* __restrict__ leaves, int nleaf,
+                                               const int32_t* __restrict__ bstart, const int32_t* __restrict__ bcount,
+                                               const float4* __restrict__ chl, const float* __restrict__ rho32,
+                                               const float4* __restrict__ pos4, const float2* __restrict__ gam,
+                                               float2* __restrict__ M32, int p, int PS) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nleaf) return;
+    const int b = leaves[q];
+    const float4 c = chl[b];
+    const float r = rho32[b];
+    const float inv = r > 0.f ? 1.0f / r : 0.f;
+    float2 a[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) a[k] = make_float2(0.f, 0.f);
+    const int s = bstart[b], e = s + bcount[b];
+    for (int i = s; i < e; ++i) {
+        const float4 pt = pos4[i];
+        const float2 w = make_float2(((pt.x - c.x) + (pt.z - c.z)) * inv, ((pt.y - c.y) + (pt.w - c.w)) * inv);
+        float2 t = gam[i];
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            a[k].x += t.x;
+            a[k].y += t.y;
+            t = cmul(t, w);
+        }
+    }
+    float2* out = M32 + (size_t)b * PS;
+#pragma unroll
+    for (int k = 0; k < P; ++k) out[k] = k < p ? a[k] : make_float2(0.f, 0.f);
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_p2m64(const int32_t* __restrict__ leaves, int nleaf,
+                                               const int32_t* __restrict__ bstart, const int32_t* __restrict__ bcount,
+                                               const double2* __restrict__ center, const double* __restrict__ rho,
+                                               const double2* __restrict__ pts, const double2* __restrict__ gam,
+                                               double2* __restrict__ M64, int p, int PS) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nleaf) return;
+    const int b = leaves[q];
+    const double2 c = center[b];
+    const double r = rho[b];
+    const double inv = r > 0.0 ? 1.0 / r : 0.0;
+    double2 a[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) a[k] = make_double2(0.0, 0.0);
+    const int s = bstart[b], e = s + bcount[b];
+    for (int i = s; i < e; ++i) {
+        const double2 pt = pts[i];
+        const double2 w = make_double2((pt.x - c.x) * inv, (pt.y - c.y) * inv);
+        double2 t = gam[i];
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            a[k].x += t.x;
+            a[k].y += t.y;
+            t = cmul(t, w);
+        }
+    }
+    double2* out = M64 + (size_t)b * PS;
+#pragma unroll
+    for (int k = 0; k < P; ++k) out[k] = k < p ? a[k] : make_double2(0.0, 0.0);
+}
+
+// --------------------------------------------------------------------- M2M
+
+// One thread per parent; FP64.  Leaf children of the FP32 path are read from
+// the FP32 multipoles written by P2M.
+template <int P>
+__global__ void __launch_bounds__(128) k_m2m(const int32_t* __restrict__ parents, int cnt,
+                                             const int32_t* __restrict__ child0, const double* __restrict__ rho,
+                                             const double2* __restrict__ center, const float2* __restrict__ M32in,
+                                             double2* __restrict__ M64, float2* __restrict__ M32out, int fp32_path,
+                                             int PS) {
+    int qi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= cnt) return;
+    const int b = parents[qi];
+    const int c0 = child0[b];
+    const double rP = rho[b];
+    const double inv = rP > 0.0 ? 1.0 / rP : 0.0;
+    const double2 cP = center[b];
+    double2 acc[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) acc[k] = make_double2(0.0, 0.0);
+    for (int c = 0; c < 4; ++c) {
+        const int h = c0 + c;
+        double2 v[P];
+        if (fp32_path && child0[h] < 0) {
+            const float2* src = M32in + (size_t)h * PS;
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                float2 f = src[k];
+                v[k] = make_double2((double)f.x, (double)f.y);
+            }
+        } else {
+            const double2* src = M64 + (size_t)h * PS;
+#pragma unroll
+            for (int k = 0; k < P; ++k) v[k] = src[k];
+        }
+        const double sigma = rho[h] * inv;
+        const double2 ch = center[h];
+        const double2 q = make_double2((ch.x - cP.x) * inv, (ch.y - cP.y) * inv);
+        double sp = 1.0;
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            v[k].x *= sp;
+            v[k].y *= sp;
+            sp *= sigma;
+        }
+        // in-place Taylor shift: after the sweeps v_n = sum_{k<=n} C(n,k) v_k q^(n-k)
+#pragma unroll
+        for (int k = P - 1; k >= 1; --k) {
+#pragma unroll
+            for (int j = k; j < P; ++j) v[j] = cfma(q, v[j - 1], v[j]);
+        }
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            acc[k].x += v[k].x;
+            acc[k].y += v[k].y;
+        }
+    }
+    double2* out = M64 + (size_t)b * PS;
+#pragma unroll
+    for (int k = 0; k < P; ++k) out[k] = acc[k];
+    if (fp32_path) {
+        float2* o32 = M32out + (size_t)b * PS;
+#pragma unroll
+        for (int k = 0; k < P; ++k) o32[k] = make_float2((float)acc[k].x, (float)acc[k].y);
+    }
+}
+
+// --------------------------------------------------------------------- M2L
+
+// One thread per target box (every level in one launch), looping over the
+// box's weak list.  FP32 with FP32 accumulation.  Root boxes (no parent) also
+// seed the FP64 local array, which L2L reads for level 1.
+template <int P>
+__global__ void __launch_bounds__(128) k_m2l32(int nbox, const int32_t* __restrict__ nweak,
+                                               const int32_t* __restrict__ weak, int wcap,
+                                               const float4* __restrict__ chl, const float* __restrict__ rho32,
+                                               const float2* __restrict__ M32, float2* __restrict__ Lm2l,
+                                               const int32_t* __restrict__ parent,
+                                               const int32_t* __restrict__ child0, double2* __restrict__ L64,
+                                               float2* __restrict__ L32, int PS) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    const int nw = nweak[b];
+    const float4 ct = chl[b];
+    const float rt = rho32[b];
+    float2 acc[P];
+#pragma unroll
+    for (int l = 0; l < P; ++l) acc[l] = make_float2(0.f, 0.f);
+    const int32_t* wl = weak + (size_t)b * wcap;
+    for (int j = 0; j < nw; ++j) {
+        const int s = wl[j];
+        const float4 cs = chl[s];
+        const float rs = rho32[s];
+        const float dx = (ct.x - cs.x) + (ct.z - cs.z);
+        const float dy = (ct.y - cs.y) + (ct.w - cs.w);
+        const float inv = 1.0f / fmaf(dx, dx, dy * dy);
+        const float2 u = make_float2(dx * inv, -dy * inv);  // 1/d, d = c_target - c_source
+        const float2 alpha = make_float2(rs * u.x, rs * u.y);
+        const float2 beta = make_float2(-rt * u.x, -rt * u.y);
+        float2 w[P];
+#pragma unroll
+        for (int l = 0; l < P; ++l) w[l] = make_float2(0.f, 0.f);
+        const float4* src = reinterpret_cast<const float4*>(M32 + (size_t)s * PS);
+        float2 ap = make_float2(1.f, 0.f);
+#pragma unroll
+        for (int k2 = 0; k2 < (P + 1) / 2; ++k2) {
+            const float4 aa = src[k2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = 2 * k2 + h;
+                if (k < P) {
+                    const float2 a = h ? make_float2(aa.z, aa.w) : make_float2(aa.x, aa.y);
+                    const float2 v = cmul(ap, a);
+                    ap = cmul(ap, alpha);
+#pragma unroll
+                    for (int l = 0; l < P; ++l) {
+                        const float cb = c_binom.f[k + l][l];
+                        w[l].x = fmaf(cb, v.x, w[l].x);
+                        w[l].y = fmaf(cb, v.y, w[l].y);
+                    }
+                }
+            }
+        }
+        float2 g = u;
+#pragma unroll
+        for (int l = 0; l < P; ++l) {
+            acc[l] = cfma(g, w[l], acc[l]);
+            g = cmul(g, beta);
+        }
+    }
+    float2* out = Lm2l + (size_t)b * PS;
+#pragma unroll
+    for (int l = 0; l < P; ++l) out[l] = acc[l];
+    if (parent[b] < 0) {
+        double2* o64 = L64 + (size_t)b * PS;
+#pragma unroll
+        for (int l = 0; l < P; ++l) o64[l] = make_double2((double)acc[l].x, (double)acc[l].y);
+        if (child0[b] < 0) {  // a one-level tree: the root is a leaf
+            float2* o32 = L32 + (size_t)b * PS;
+#pragma unroll
+            for (int l = 0; l < P; ++l) o32[l] = acc[l];
+        }
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_m2l64(int nbox, const int32_t* __restrict__ nweak,
+                                               const int32_t* __restrict__ weak, int wcap,
+                                               const double2* __restrict__ center, const double* __restrict__ rho,
+                                               const double2* __restrict__ M64, double2* __restrict__ Lm2l,
+                                               const int32_t* __restrict__ parent, double2* __restrict__ L64,
+                                               int PS) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    const int nw = nweak[b];
+    const double2 ct = center[b];
+    const double rt = rho[b];
+    double2 acc[P];
+#pragma unroll
+    for (int l = 0; l < P; ++l) acc[l] = make_double2(0.0, 0.0);
+    const int32_t* wl = weak + (size_t)b * wcap;
+    for (int j = 0; j < nw; ++j) {
+        const int s = wl[j];
+        const double2 cs = center[s];
+        const double rs = rho[s];
+        const double dx = ct.x - cs.x, dy = ct.y - cs.y;
+        const double inv = 1.0 / (dx * dx + dy * dy);
+        const double2 u = make_double2(dx * inv, -dy * inv);
+        const double2 alpha = make_double2(rs * u.x, rs * u.y);
+        const double2 beta = make_double2(-rt * u.x, -rt * u.y);
+        double2 w[P];
+#pragma unroll
+        for (int l = 0; l < P; ++l) w[l] = make_double2(0.0, 0.0);
+        const double2* src = M64 + (size_t)s * PS;
+        double2 ap = make_double2(1.0, 0.0);
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            const double2 v = cmul(ap, src[k]);
+            ap = cmul(ap, alpha);
+#pragma unroll
+            for (int l = 0; l < P; ++l) {
+                const double cb = c_binom.d[k + l][l];
+                w[l].x = fma(cb, v.x, w[l].x);
+                w[l].y = fma(cb, v.y, w[l].y);
+            }
+        }
+        double2 g = u;
+#pragma unroll
+        for (int l = 0; l < P; ++l) {
+            acc[l] = cfma(g, w[l], acc[l]);
+            g = cmul(g, beta);
+        }
+    }
+    double2* out = Lm2l + (size_t)b * PS;
+#pragma unroll
+    for (int l = 0; l < P; ++l) out[l] = acc[l];
+    if (parent[b] < 0) {
+        double2* o64 = L64 + (size_t)b * PS;
+#pragma unroll
+        for (int l = 0; l < P; ++l) o64[l] = acc[l];
+    }
+}
+
+// --------------------------------------------------------------------- L2L
+
+// One thread per child box of one level; FP64.  child = shift(parent) + its
+// own M2L sum.  In the FP32 path leaves also get an FP32 copy for L2P.
+template <int P, typename LM>
+__global__ void __launch_bounds__(128) k_l2l(const int32_t* __restrict__ boxes, int cnt,
+                                             const int32_t* __restrict__ parent, const int32_t* __restrict__ child0,
+                                             const double* __restrict__ rho, const double2* __restrict__ center,
+                                             const LM* __restrict__ Lm2l, double2* __restrict__ L64,
+                                             float2* __restrict__ L32, int p, int PS) {
+    int qi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= cnt) return;
+    const int c = boxes[qi];
+    const int Pb = parent[c];
+    const double rP = rho[Pb];
+    const double inv = rP > 0.0 ? 1.0 / rP : 0.0;
+    const double2 cP = center[Pb], cc = center[c];
+    const double2 q = make_double2((cc.x - cP.x) * inv, (cc.y - cP.y) * inv);
+    const double sigma = rho[c] * inv;
+    double2 b[P];
+    const double2* src = L64 + (size_t)Pb * PS;
+#pragma unroll
+    for (int k = 0; k < P; ++k) b[k] = src[k];
+    // in-place Taylor shift: after the sweeps b_m = sum_{l>=m} C(l,m) b_l q^(l-m)
+#pragma unroll
+    for (int k = 0; k + 1 < P; ++k) {
+#pragma unroll
+        for (int j = P - 2; j >= k; --j) b[j] = cfma(q, b[j + 1], b[j]);
+    }
+    const LM* own = Lm2l + (size_t)c * PS;
+    double sp = 1.0;
+    double2* out = L64 + (size_t)c * PS;
+    const bool leaf32 = (L32 != nullptr) && child0[c] < 0;
+    float2* o32 = L32 + (size_t)c * PS;
+#pragma unroll
+    for (int m = 0; m < P; ++m) {
+        const LM o = own[m];
+        double2 v = make_double2(fma(b[m].x, sp, (double)o.x), fma(b[m].y, sp, (double)o.y));
+        if (m >= p) v = make_double2(0.0, 0.0);
+        sp *= sigma;
+        out[m] = v;
+        if (leaf32) o32[m] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+// ------------------------------------------------------------- L2P + sum
+
+// One thread per sorted point: far field by Horner from the leaf's local
+// expansion, plus the near field, written to the caller's order.
+template <int P>
+__global__ void __launch_bounds__(256) k_l2p32(int n, const int32_t* __restrict__ leaf_of,
+                                               const float4* __restrict__ chl, const float* __restrict__ rho32,
+                                               const float4* __restrict__ pos4, const float2* __restrict__ L32,
+                                               const float2* __restrict__ nearv, const int32_t* __restrict__ perm,
+                                               float2* __restrict__ out, int PS) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int lf = leaf_of[i];
+    const float4 c = chl[lf];
+    const float r = rho32[lf];
+    const float inv = r > 0.f ? 1.0f / r : 0.f;
+    const float4 pt = pos4[i];
+    const float2 w = make_float2(((pt.x - c.x) + (pt.z - c.z)) * inv, ((pt.y - c.y) + (pt.w - c.w)) * inv);
+    const float2* Lb = L32 + (size_t)lf * PS;
+    float2 v = Lb[P - 1];
+#pragma unroll
+    for (int l = P - 2; l >= 0; --l) v = cfma(v, w, Lb[l]);
+    const float2 nv = nearv[i];
+    out[perm[i]] = make_float2(v.x + nv.x, v.y + nv.y);
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_l2p64(int n, const int32_t* __restrict__ leaf_of,
+                                               const double2* __restrict__ center, const double* __restrict__ rho,
+                                               const double2* __restrict__ pts, const double2* __restrict__ L64,
+                                               const double2* __restrict__ nearv, const int32_t* __restrict__ perm,
+                                               double2* __restrict__ out, int PS) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int lf = leaf_of[i];
+    const double2 c = center[lf];
+    const double r = rho[lf];
+    const double inv = r > 0.0 ? 1.0 / r : 0.0;
+    const double2 pt = pts[i];
+    const double2 w = make_double2((pt.x - c.x) * inv, (pt.y - c.y) * inv);
+    const double2* Lb = L64 + (size_t)lf * PS;
+    double2 v = Lb[P - 1];
+#pragma unroll
+    for (int l = P - 2; l >= 0; --l) v = cfma(v, w, Lb[l]);
+    const double2 nv = nearv[i];
+    out[perm[i]] = make_double2(v.x + nv.x, v.y + nv.y);
+}
+
+// --------------------------------------------------------------------- P2P
+
+// One warp per target leaf.  The warp's lanes form LT target groups x S
+// source slices: lane (tg, ss) owns targets tg, tg+LT, ... (TPL of them) and
+// every S-th staged source; slices are summed with shuffles at the end.
+// Sources of the strongly coupled leaves are staged in warp-private shared
+// memory in chunks.  FP32: coordinates carry a hi/lo split so that
+// z_i - z_j keeps full FP32 relative accuracy even for very close pairs.
+constexpr int kP2PWarps = 8;
+constexpr int kP2PChunk32 = 192;
+constexpr int kP2PChunk64 = 128;
+
+__device__ __forceinline__ void p2p_interact32(const float4 t, const float4 s, const float2 g, float2& acc) {
+    const float dx = (t.x - s.x) + (t.z - s.z);
+    const float dy = (t.y - s.y) + (t.w - s.w);
+    const float r2 = fmaf(dx, dx, dy * dy);
+    const float inv = fminf(rcp_approx(r2), 3.0e38f);  // coincident pair: r2 = 0, dx = dy = 0 -> adds 0
+    const float tr = fmaf(g.x, dx, g.y * dy);
+    const float ti = fmaf(g.y, dx, -g.x * dy);
+    acc.x = fmaf(tr, inv, acc.x);
+    acc.y = fmaf(ti, inv, acc.y);
+}
+
+template <int TPL>
+__global__ void __launch_bounds__(kP2PWarps * 32) k_p2p32(const int32_t* __restrict__ leaves, int nleaf,
+                                                          const int32_t* __restrict__ bstart,
+                                                          const int32_t* __restrict__ bcount,
+                                                          const int32_t* __restrict__ nstrong,
+                                                          const int32_t* __restrict__ strong, int scap,
+                                                          const float4* __restrict__ pos4,
+                                                          const float2* __restrict__ gam, float2* __restrict__ nearv) {
+    __shared__ float4 sp[kP2PWarps][kP2PChunk32];
+    __shared__ float2 sg[kP2PWarps][kP2PChunk32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int lq = blockIdx.x * kP2PWarps + warp; lq < nleaf; lq += gridDim.x * kP2PWarps) {
+        const int b = leaves[lq];
+        const int ts = bstart[b], tn = bcount[b];
+        const int ns = nstrong[b];
+        const int32_t* sl = strong + (size_t)b * scap;
+        for (int t0 = 0; t0 < tn; t0 += 32 * TPL) {
+            const int nt = min(tn - t0, 32 * TPL);
+            const int LT = (nt + TPL - 1) / TPL;
+            const int S = 32 / LT;
+            const int tg = lane % LT, ss = lane / LT;
+            const bool active = ss < S;
+            float4 xt[TPL];
+            float2 acc[TPL];
+#pragma unroll
+            for (int u = 0; u < TPL; ++u) {
+                const int idx = t0 + tg + u * LT;
+                xt[u] = (idx < tn) ? pos4[ts + idx] : make_float4(0.f, 0.f, 0.f, 0.f);
+                acc[u] = make_float2(0.f, 0.f);
+            }
+            int j = 0, off = 0;
+            while (j < ns) {
+                __syncwarp();
+                int cnt = 0;
+                while (j < ns && cnt < kP2PChunk32) {
+                    const int h = sl[j];
+                    const int hs = bstart[h], hn = bcount[h];
+                    const int take = min(hn - off, kP2PChunk32 - cnt);
+                    for (int e = lane; e < take; e += 32) {
+                        sp[warp][cnt + e] = pos4[hs + off + e];
+                        sg[warp][cnt + e] = gam[hs + off + e];
+                    }
+                    cnt += take;
+                    off += take;
+                    if (off == hn) {
+                        ++j;
+                        off = 0;
+                    }
+                }
+                __syncwarp();
+                if (active) {
+#pragma unroll 4
+                    for (int e = ss; e < cnt; e += S) {
+                        const float4 s = sp[warp][e];
+                        const float2 g = sg[warp][e];
+#pragma unroll
+                        for (int u = 0; u < TPL; ++u) p2p_interact32(xt[u], s, g, acc[u]);
+                    }
+                }
+            }
+            // sum the S source slices into the lanes of slice 0
+#pragma unroll
+            for (int u = 0; u < TPL; ++u) {
+                float2 tot = acc[u];
+                for (int s2 = 1; s2 < S; ++s2) {
+                    const int src = tg + s2 * LT;
+                    tot.x += __shfl_sync(0xffffffffu, acc[u].x, src & 31);
+                    tot.y += __shfl_sync(0xffffffffu, acc[u].y, src & 31);
+                }
+                const int idx = t0 + tg + u * LT;
+                if (ss == 0 && idx < tn) nearv[ts + idx] = tot;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void p2p_interact64(const double2 t, const double2 s, const double2 g, double2& acc) {
+    const double dx = t.x - s.x, dy = t.y - s.y;
+    const double r2 = fma(dx, dx, dy * dy);
+    const double inv = r2 > 0.0 ? __drcp_rn(r2) : 0.0;
+    const double tr = fma(g.x, dx, g.y * dy);
+    const double ti = fma(g.y, dx, -g.x * dy);
+    acc.x = fma(tr, inv, acc.x);
+    acc.y = fma(ti, inv, acc.y);
+}
+
+template <int TPL>
+__global__ void __launch_bounds__(kP2PWarps * 32) k_p2p64(const int32_t* __restrict__ leaves, int nleaf,
+                                                          const int32_t* __restrict__ bstart,
+                                                          const int32_t* __restrict__ bcount,
+                                                          const int32_t* __restrict__ nstrong,
+                                                          const int32_t* __restrict__ strong, int scap,
+                                                          const double2* __restrict__ pts,
+                                                          const double2* __restrict__ gam,
+                                                          double2* __restrict__ nearv) {
+    __shared__ double2 sp[kP2PWarps][kP2PChunk64];
+    __shared__ double2 sg[kP2PWarps][kP2PChunk64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int lq = blockIdx.x * kP2PWarps + warp; lq < nleaf; lq += gridDim.x * kP2PWarps) {
+        const int b = leaves[lq];
+        const int ts = bstart[b], tn = bcount[b];
+        const int ns = nstrong[b];
+        const int32_t* sl = strong + (size_t)b * scap;
+        for (int t0 = 0; t0 < tn; t0 += 32 * TPL) {
+            const int nt = min(tn - t0, 32 * TPL);
+            const int LT = (nt + TPL - 1) / TPL;
+            const int S = 32 / LT;
+            const int tg = lane % LT, ss = lane / LT;
+            const bool active = ss < S;
+            double2 xt[TPL], acc[TPL];
+#pragma unroll
+            for (int u = 0; u < TPL; ++u) {
+                const int idx = t0 + tg + u * LT;
+                xt[u] = (idx < tn) ? pts[ts + idx] : make_double2(0.0, 0.0);
+                acc[u] = make_double2(0.0, 0.0);
+            }
+            int j = 0, off = 0;
+            while (j < ns) {
+                __syncwarp();
+                int cnt = 0;
+                while (j < ns && cnt < kP2PChunk64) {
+                    const int h = sl[j];
+                    const int hs = bstart[h], hn = bcount[h];
+                    const int take = min(hn - off, kP2PChunk64 - cnt);
+                    for (int e = lane; e < take; e += 32) {
+                        sp[warp][cnt + e] = pts[hs + off + e];
+                        sg[warp][cnt + e] = gam[hs + off + e];
+                    }
+                    cnt += take;
+                    off += take;
+                    if (off == hn) {
+                        ++j;
+                        off = 0;
+                    }
+                }
+                __syncwarp();
+                if (active) {
+                    for (int e = ss; e < cnt; e += S) {
+                        const double2 s = sp[warp][e];
+                        const double2 g = sg[warp][e];
+#pragma unroll
+                        for (int u = 0; u < TPL; ++u) p2p_interact64(xt[u], s, g, acc[u]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < TPL; ++u) {
+                double2 tot = acc[u];
+                for (int s2 = 1; s2 < S; ++s2) {
+                    const int src = tg + s2 * LT;
+                    tot.x += __shfl_sync(0xffffffffu, acc[u].x, src & 31);
+                    tot.y += __shfl_sync(0xffffffffu, acc[u].y, src & 31);
+                }
+                const int idx = t0 + tg + u * LT;
+                if (ss == 0 && idx < tn) nearv[ts + idx] = tot;
+            }
+        }
+    }
+}
+
+// ============================================================ dispatch
+
+template <int P>
+static void launch_far_fp32(Tree& t, cudaStream_t s) {
+    const float2* gam = static_cast<const float2*>(t.d_gam);
+    k_p2m32<P><<<nblk(t.nleaf, 128), 128, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, t.d_bstart, t.d_bcount, t.d_chl,
+                                                  t.d_rho32, t.d_pos4, gam, t.d_M32, t.p, t.PS);
+    for (int l = t.Lmax - 2; l >= 0; --l) {
+        const LevelList& L = t.level_parents[l];
+        if (!L.count) continue;
+        k_m2m<P><<<nblk(L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_child0, t.d_rho, t.d_center, t.d_M32,
+                                                    t.d_M64, t.d_M32, 1, t.PS);
+    }
+    if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[2], s);
+    k_m2l32<P><<<nblk(t.nbox, 128), 128, 0, s>>>((int)t.nbox, t.d_nweak, t.d_weak, t.wcap, t.d_chl, t.d_rho32,
+                                                 t.d_M32, static_cast<float2*>(t.d_Lm2l), t.d_parent, t.d_child0,
+                                                 t.d_L64, t.d_L32, t.PS);
+    if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[3], s);
+    for (int l = 0; l + 1 < t.Lmax; ++l) {
+        const LevelList& L = t.level_boxes[l + 1];
+        k_l2l<P, float2><<<nblk(L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho,
+                                                            t.d_center, static_cast<const float2*>(t.d_Lm2l),
+                                                            t.d_L64, t.d_L32, t.p, t.PS);
+    }
+}
+
+template <int P>
+static void launch_far_fp64(Tree& t, cudaStream_t s) {
+    const double2* gam = static_cast<const double2*>(t.d_gam);
+    k_p2m64<P><<<nblk(t.nleaf, 128), 128, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, t.d_bstart, t.d_bcount, t.d_center,
+                                                  t.d_rho, t.d_pts, gam, t.d_M64, t.p, t.PS);
+    for (int l = t.Lmax - 2; l >= 0; --l) {
+        const LevelList& L = t.level_parents[l];
+        if (!L.count) continue;
+        k_m2m<P><<<nblk(L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_child0, t.d_rho, t.d_center, nullptr,
+                                                    t.d_M64, nullptr, 0, t.PS);
+    }
+    if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[2], s);
+    k_m2l64<P><<<nblk(t.nbox, 128), 128, 0, s>>>((int)t.nbox, t.d_nweak, t.d_weak, t.wcap, t.d_center, t.d_rho,
+                                                 t.d_M64, static_cast<double2*>(t.d_Lm2l), t.d_parent, t.d_L64,
+                                                 t.PS);
+    if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[3], s);
+    for (int l = 0; l + 1 < t.Lmax; ++l) {
+        const LevelList& L = t.level_boxes[l + 1];
+        k_l2l<P, double2><<<nblk(L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho,
+                                                             t.d_center, static_cast<const double2*>(t.d_Lm2l),
+                                                             t.d_L64, nullptr, t.p, t.PS);
+    }
+}
+
+template <int P>
+static void launch_l2p(Tree& t, void* d_phi, cudaStream_t s) {
+    const int n = (int)t.n;
+    if (t.path == FMM_PATH_FP32) {
+        k_l2p32<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_chl, t.d_rho32, t.d_pos4, t.d_L32,
+                                                static_cast<const float2*>(t.d_near), t.d_perm,
+                                                static_cast<float2*>(d_phi), t.PS);
+    } else {
+        k_l2p64<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_center, t.d_rho, t.d_pts, t.d_L64,
+                                                static_cast<const double2*>(t.d_near), t.d_perm,
+                                                static_cast<double2*>(d_phi), t.PS);
+    }
+}
+
+static void launch_p2p(Tree& t, cudaStream_t s) {
+    const int nl = (int)t.nleaf;
+    const int grid = nblk(nl, kP2PWarps);
+    const double avg = (double)t.n / std::max<int64_t>(t.nleaf, 1);
+    if (t.path == FMM_PATH_FP32) {
+        const float2* gam = static_cast<const float2*>(t.d_gam);
+        float2* nv = static_cast<float2*>(t.d_near);
+        if (avg >= 8.0)
+            k_p2p32<4><<<grid, kP2PWarps * 32, 0, s>>>(t.leaves.d_ids, nl, t.d_bstart, t.d_bcount, t.d_nstrong,
+                                                       t.d_strong, t.scap, t.d_pos4, gam, nv);
+        else
+            k_p2p32<1><<<grid, kP2PWarps * 32, 0, s>>>(t.leaves.d_ids, nl, t.d_bstart, t.d_bcount, t.d_nstrong,
+                                                       t.d_strong, t.scap, t.d_pos4, gam, nv);
+    } else {
+        const double2* gam = static_cast<const double2*>(t.d_gam);
+        double2* nv = static_cast<double2*>(t.d_near);
+        if (avg >= 8.0)
+            k_p2p64<4><<<grid, kP2PWarps * 32, 0, s>>>(t.leaves.d_ids, nl, t.d_bstart, t.d_bcount, t.d_nstrong,
+                                                       t.d_strong, t.scap, t.d_pts, gam, nv);
+        else
+            k_p2p64<1><<<grid, kP2PWarps * 32, 0, s>>>(t.leaves.d_ids, nl, t.d_bstart, t.d_bcount, t.d_nstrong,
+                                                       t.d_strong, t.scap, t.d_pts, gam, nv);
+    }
+}
+
+template <int P>
+static void launch_far(Tree& t, cudaStream_t s) {
+    if (t.path == FMM_PATH_FP32) launch_far_fp32<P>(t, s);
+    else launch_far_fp64<P>(t, s);
+}
+
+// Compiled expansion orders; a request for p runs the smallest compiled
+// order >= p with the coefficients k >= p held at zero.
+#define FMM_FOR_ORDERS(X) X(4) X(8) X(12) X(16) X(17) X(20) X(24) X(28) X(32)
+
+int compiled_order(int p) {
+#define FMM_PICK(Q) \
+    if (p <= Q) return Q;
+    FMM_FOR_ORDERS(FMM_PICK)
+#undef FMM_PICK
+    return -1;
+}
+
+static void dispatch_far(Tree& t, cudaStream_t s) {
+    switch (t.P) {
+#define FMM_CASE(Q) \
+    case Q: launch_far<Q>(t, s); break;
+        FMM_FOR_ORDERS(FMM_CASE)
+#undef FMM_CASE
+    }
+}
+
+static void dispatch_l2p(Tree& t, void* d_phi, cudaStream_t s) {
+    switch (t.P) {
+#define FMM_CASE(Q) \
+    case Q: launch_l2p<Q>(t, d_phi, s); break;
+        FMM_FOR_ORDERS(FMM_CASE)
+#undef FMM_CASE
+    }
+}
+
+// ------------------------------------------------------------- workspace
+
+template <typename T>
+static fmm_status ralloc(T** p, size_t bytes) {
+    if (*p) cudaFree((void*)*p);
+    *p = nullptr;
+    cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(bytes, 16));
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        set_error("device allocation failed (evaluation workspace)");
+        return FMM_ERR_OOM;
+    }
+    FMM_CUDA(e);
+    return FMM_OK;
+}
+
+fmm_status alloc_eval(Tree& t, int sets) {
+    if (t.eval_nbox == (size_t)t.nbox && t.eval_n == (size_t)t.n && t.eval_PS == t.PS && t.eval_path == t.path &&
+        t.eval_sets >= sets)
+        return FMM_OK;
+    const size_t nb = (size_t)t.nbox, n = (size_t)t.n, PS = (size_t)t.PS;
+    const size_t cs = t.path == FMM_PATH_FP32 ? sizeof(float2) : sizeof(double2);
+    fmm_status st;
+    if ((st = ralloc(&t.d_gam, n * cs * sets))) return st;
+    if ((st = ralloc(&t.d_near, n * sizeof(double2) * 3 * sets))) return st;
+    if ((st = ralloc(&t.d_M64, nb * PS * sizeof(double2) * sets))) return st;
+    if ((st = ralloc(&t.d_L64, nb * PS * sizeof(double2) * sets))) return st;
+    if ((st = ralloc(&t.d_Lm2l, nb * PS * cs * sets))) return st;
+    if ((st = ralloc(&t.d_M32, nb * PS * sizeof(float2) * sets))) return st;
+    if ((st = ralloc(&t.d_L32, nb * PS * sizeof(float2) * sets))) return st;
+    t.eval_nbox = nb;
+    t.eval_n = n;
+    t.eval_PS = t.PS;
+    t.eval_path = t.path;
+    t.eval_sets = sets;
+    return FMM_OK;
+}
+
+// One evaluation: gather strengths into sorted order, then fork P2P onto the
+// auxiliary stream while the far field (P2M, M2M, M2L, L2L) runs on the
+// caller's stream, join, and finish with L2P + near + unpermute.
+fmm_status run_eval(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s) {
+    const int n = (int)t.n;
+    const bool timing = t.flags & FMM_FLAG_TIMING;
+    const bool serial = t.flags & FMM_FLAG_SERIAL;
+    if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[0], s));
+    const double2* gin = reinterpret_cast<const double2*>(d_gamma);
+    if (t.path == FMM_PATH_FP32)
+        k_gather32<<<nblk(n, 256), 256, 0, s>>>(gin, t.d_perm, n, static_cast<float2*>(t.d_gam));
+    else
+        k_gather64<<<nblk(n, 256), 256, 0, s>>>(gin, t.d_perm, n, static_cast<double2*>(t.d_gam));
+    if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[1], s));
+    if (!serial) {
+        FMM_CUDA(cudaEventRecord(t.ev_fork, s));
+        FMM_CUDA(cudaStreamWaitEvent(t.s_aux, t.ev_fork, 0));
+        if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[5], t.s_aux));
+        launch_p2p(t, t.s_aux);
+        if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[6], t.s_aux));
+        FMM_CUDA(cudaEventRecord(t.ev_join, t.s_aux));
+    }
+    dispatch_far(t, s);
+    if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[4], s));
+    if (serial) {
+        if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[5], s));
+        launch_p2p(t, s);
+        if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[6], s));
+    } else {
+        FMM_CUDA(cudaStreamWaitEvent(s, t.ev_join, 0));
+    }
+    dispatch_l2p(t, d_phi, s);
+    if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[7], s));
+    FMM_CUDA(cudaGetLastError());
+    t.timing_valid = timing;
+    return FMM_OK;
+}
+
+}  // namespace fmm

@@ -135,6 +135,20 @@ fmm_status fmm_autotune_step(fmm_tree* t, double last_time_s, fmm_params* inout)
  * (noise filter, Sec. 4.2.1), period = evaluations between N_levels moves. */
 fmm_status fmm_autotune_config(fmm_tree* t, double cap, int window, int period);
 
+/* Standalone N_levels autotuner with the same AT3b logic, for callers that
+ * manage trees themselves (and for host-only tests).  nlevels = starting
+ * N_levels, max_levels = largest allowed (4^(max_levels-1) <= N).
+ * fmm_autotuner_step takes the last evaluation time and writes the N_levels
+ * to use next.  fmm_autotuner_stats writes up to 6 values: accepted N_levels,
+ * steps, rejected moves, time lost to rejected moves (s), accumulated time of
+ * accepted evaluations (s), N_levels on trial (0 = none). */
+typedef struct fmm_autotuner fmm_autotuner;
+fmm_status fmm_autotuner_create(int nlevels, int max_levels, double cap, int window, int period,
+                                fmm_autotuner** out);
+fmm_status fmm_autotuner_step(fmm_autotuner* a, double time_s, int* nlevels_out);
+fmm_status fmm_autotuner_stats(const fmm_autotuner* a, double* out, int nout);
+void fmm_autotuner_destroy(fmm_autotuner* a);
+
 /* N_levels the library picks for n points at expansion order p when
  * fmm_params.nlevels == 0: the level whose leaves hold closest to the point
  * count that balances the P2P and M2L costs of eqs (2.4)-(2.5) on this GPU. */

@@ -1,0 +1,280 @@
+"""B300 (sm_103a) balanced adaptive 2D FMM for the harmonic potential.
+
+    Phi(z_i) = sum_{j : z_j != z_i} Gamma_j / (z_i - z_j)      (eq 2.1 / 2.2)
+
+The method is the balanced adaptive FMM of Holm, Engblom, Goude, Holmgren
+(arXiv:1311.1006): a pyramid tree with median splits (Sec. 2.2-2.3), coupling by
+the theta-criterion (eq 2.3), P2M / M2M / M2L / L2L / L2P / P2P passes
+(Sec. 2.1), an N_levels autotuner (Sec. 4.2, Algorithm 4) and, added here, a
+hand-written adjoint and batched instances.
+
+This module is a thin binding over the C ABI of ``libfmm2d.so`` (same names,
+argument marshalling only).  PyTorch supplies device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (FMM_FLAG_NO_GRAPH, FMM_FLAG_SERIAL, FMM_FLAG_TIMING, FMM_PATH_FP32, FMM_PATH_FP64, FMMError,
+                   FMMParams)
+
+__all__ = ["Tree", "FMMFunction", "fmm", "default_nlevels", "Autotuner", "FMMError", "FMM_PATH_FP32",
+           "FMM_PATH_FP64", "FMM_FLAG_NO_GRAPH", "FMM_FLAG_SERIAL", "FMM_FLAG_TIMING"]
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _path(path) -> int:
+    if path in (FMM_PATH_FP32, "fp32", "mixed"):
+        return FMM_PATH_FP32
+    if path in (FMM_PATH_FP64, "fp64"):
+        return FMM_PATH_FP64
+    raise ValueError(f"unknown path {path!r}")
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype, shape=None, name="tensor"):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def default_nlevels(n: int, p: int = 17, path="fp32") -> int:
+    return int(_lib.load().fmm_default_nlevels(int(n), int(p), _path(path)))
+
+
+class Tree:
+    """A device-resident FMM tree (tree + coupling lists + workspace)."""
+
+    def __init__(self, handle, n, params: FMMParams, batched=False, ninst=1):
+        self._h = handle
+        self.n = int(n)
+        self.params = params
+        self.batched = batched
+        self.ninst = ninst
+
+    # -- construction -------------------------------------------------------
+    @classmethod
+    def build(cls, xy, p=17, theta=0.5, nlevels=0, path="fp32", flags=0, stream=None) -> "Tree":
+        """fmm_build_tree: xy is an (N, 2) float64 CUDA tensor."""
+        torch = _torch()
+        lib = _lib.load()
+        n = xy.shape[0]
+        ptr = _dev(xy, torch.float64, (n, 2), "xy")
+        prm = FMMParams(int(p), float(theta), int(nlevels), _path(path), int(flags))
+        h = ctypes.c_void_p()
+        _lib.check(lib.fmm_build_tree(ptr, n, ctypes.byref(prm), _stream(stream), ctypes.byref(h)))
+        return cls(h, n, prm)
+
+    @classmethod
+    def build_batched(cls, xy, offsets, nlevels=None, p=17, theta=0.5, path="fp32", flags=0,
+                      stream=None) -> "Tree":
+        """fmm_build_tree_batched: instance b owns xy[offsets[b]:offsets[b+1]]."""
+        torch = _torch()
+        lib = _lib.load()
+        n = xy.shape[0]
+        ptr = _dev(xy, torch.float64, (n, 2), "xy")
+        offs = np.ascontiguousarray(offsets, dtype=np.int64)
+        B = offs.shape[0] - 1
+        if offs[-1] != n:
+            raise ValueError("offsets[-1] must equal the number of points")
+        prm = FMMParams(int(p), float(theta), 0, _path(path), int(flags))
+        nl = None
+        if nlevels is not None:
+            nl = np.ascontiguousarray(nlevels, dtype=np.int32)
+            if nl.shape[0] != B:
+                raise ValueError("one nlevels entry per instance")
+        h = ctypes.c_void_p()
+        _lib.check(lib.fmm_build_tree_batched(
+            ptr, offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), B, ctypes.byref(prm),
+            None if nl is None else nl.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _stream(stream),
+            ctypes.byref(h)))
+        return cls(h, n, prm, batched=True, ninst=B)
+
+    def rebuild(self, xy, nlevels=None, p=None, theta=None, path=None, flags=None, stream=None) -> None:
+        """fmm_tree_rebuild for new coordinates (and optionally new parameters)."""
+        torch = _torch()
+        ptr = _dev(xy, torch.float64, (self.n, 2), "xy")
+        prm = FMMParams(self.params.p if p is None else int(p),
+                        self.params.theta if theta is None else float(theta),
+                        0 if nlevels is None else int(nlevels),
+                        self.params.path if path is None else _path(path),
+                        self.params.flags if flags is None else int(flags))
+        _lib.check(_lib.load().fmm_tree_rebuild(self._h, ptr, ctypes.byref(prm), _stream(stream)))
+        self.params = prm
+
+    # -- evaluation ---------------------------------------------------------
+    @property
+    def out_dtype(self):
+        torch = _torch()
+        return torch.complex64 if self.params.path == FMM_PATH_FP32 else torch.complex128
+
+    def eval(self, gamma, out=None, stream=None):
+        """fmm_eval: gamma is an (N,) complex128 CUDA tensor; returns Phi."""
+        torch = _torch()
+        g = _dev(gamma, torch.complex128, (self.n,), "gamma")
+        if out is None:
+            out = torch.empty(self.n, dtype=self.out_dtype, device=gamma.device)
+        o = _dev(out, self.out_dtype, (self.n,), "out")
+        fn = _lib.load().fmm_eval_batched if self.batched else _lib.load().fmm_eval
+        _lib.check(fn(self._h, g, o, _stream(stream)))
+        return out
+
+    def backward(self, gamma, gphi, stream=None):
+        """fmm_eval_backward: returns (dL/dGamma complex128, dL/d(x,y) float64 (N,2))."""
+        torch = _torch()
+        g = _dev(gamma, torch.complex128, (self.n,), "gamma")
+        gp = gphi.to(torch.complex128).contiguous()
+        gpp = _dev(gp, torch.complex128, (self.n,), "gphi")
+        gg = torch.empty(self.n, dtype=torch.complex128, device=gamma.device)
+        gxy = torch.empty(self.n, 2, dtype=torch.float64, device=gamma.device)
+        _lib.check(_lib.load().fmm_eval_backward(self._h, g, gpp, ctypes.c_void_p(gg.data_ptr()),
+                                                 ctypes.c_void_p(gxy.data_ptr()), _stream(stream)))
+        return gg, gxy
+
+    # -- diagnostics --------------------------------------------------------
+    def info(self) -> dict:
+        inf = _lib.FMMTreeInfo()
+        _lib.check(_lib.load().fmm_get_tree_info(self._h, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in _lib.FMMTreeInfo._fields_}
+
+    def export(self, what: str, stream=None) -> np.ndarray:
+        """fmm_tree_export into a numpy array (tests, diagnostics)."""
+        inf = self.info()
+        nb, n, p = inf["nboxes"], inf["n"], inf["p"]
+        spec = {
+            "perm": (np.int32, n), "bstart": (np.int32, nb), "bcount": (np.int32, nb),
+            "center": (np.float64, 2 * nb), "radius": (np.float64, nb), "rho": (np.float64, nb),
+            "nstrong": (np.int32, nb), "strong": (np.int32, nb * inf["strong_cap"]),
+            "nweak": (np.int32, nb), "weak": (np.int32, nb * inf["weak_cap"]),
+            "mpole": (np.float64, 2 * nb * p), "local": (np.float64, 2 * nb * p),
+            "near": (np.float64, 2 * n), "inst": (np.int64, 3 * inf["ninst"]),
+        }[what]
+        buf = np.zeros(spec[1], dtype=spec[0])
+        _lib.check(_lib.load().fmm_tree_export(self._h, _lib.EXPORT[what], ctypes.c_void_p(buf.ctypes.data),
+                                               buf.shape[0], _stream(stream)))
+        if what == "center":
+            return buf.reshape(nb, 2)
+        if what in ("mpole", "local"):
+            return buf.view(np.complex128).reshape(nb, p)
+        if what == "near":
+            return buf.view(np.complex128)
+        if what == "strong":
+            return buf.reshape(nb, inf["strong_cap"])
+        if what == "weak":
+            return buf.reshape(nb, inf["weak_cap"])
+        if what == "inst":
+            return buf.reshape(-1, 3)
+        return buf
+
+    def phase_times(self) -> dict:
+        out = (ctypes.c_double * 7)()
+        _lib.check(_lib.load().fmm_phase_times(self._h, out, 7))
+        keys = ["gather", "p2m_m2m", "m2l", "l2l", "p2p", "l2p", "total"]
+        return dict(zip(keys, list(out)))
+
+    def autotune_config(self, cap=0.1, window=3, period=8) -> None:
+        _lib.check(_lib.load().fmm_autotune_config(self._h, float(cap), int(window), int(period)))
+
+    def autotune_step(self, seconds: float) -> int:
+        prm = FMMParams(self.params.p, self.params.theta, 0, self.params.path, self.params.flags)
+        _lib.check(_lib.load().fmm_autotune_step(self._h, float(seconds), ctypes.byref(prm)))
+        return int(prm.nlevels)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _lib.load().fmm_tree_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Autotuner:
+    """Standalone AT3b N_levels autotuner (fmm_autotuner_*)."""
+
+    def __init__(self, nlevels: int, max_levels: int, cap=0.1, window=3, period=8):
+        lib = _lib.load()
+        self._h = ctypes.c_void_p()
+        _lib.check(lib.fmm_autotuner_create(int(nlevels), int(max_levels), float(cap), int(window), int(period),
+                                            ctypes.byref(self._h)))
+
+    def step(self, seconds: float) -> int:
+        out = ctypes.c_int()
+        _lib.check(_lib.load().fmm_autotuner_step(self._h, float(seconds), ctypes.byref(out)))
+        return int(out.value)
+
+    def stats(self) -> dict:
+        out = (ctypes.c_double * 6)()
+        _lib.check(_lib.load().fmm_autotuner_stats(self._h, out, 6))
+        return dict(zip(["accepted", "steps", "rejected", "tuning_cost", "basetime", "trial"], list(out)))
+
+    def __del__(self):
+        try:
+            if self._h:
+                _lib.load().fmm_autotuner_destroy(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+
+def _make_function():
+    torch = _torch()
+
+    class FMMFunction(torch.autograd.Function):
+        """Phi = FMM(xy, gamma) with the tree frozen; backward = fmm_eval_backward."""
+
+        @staticmethod
+        def forward(ctx, xy, gamma, tree):
+            ctx.tree = tree
+            ctx.save_for_backward(gamma)
+            return tree.eval(gamma.detach().contiguous())
+
+        @staticmethod
+        def backward(ctx, gphi):
+            (gamma,) = ctx.saved_tensors
+            gg, gxy = ctx.tree.backward(gamma.detach().contiguous(), gphi)
+            return gxy, gg, None
+
+    return FMMFunction
+
+
+class _Lazy:
+    _fn = None
+
+    def __getattr__(self, k):
+        if _Lazy._fn is None:
+            _Lazy._fn = _make_function()
+        return getattr(_Lazy._fn, k)
+
+
+FMMFunction = _Lazy()
+
+
+def fmm(xy, gamma, p=17, theta=0.5, nlevels=0, path="fp32"):
+    """Differentiable one-shot evaluation: builds a tree for xy (frozen under
+    autograd) and returns Phi with gradients for xy and gamma."""
+    tree = Tree.build(xy.detach().contiguous(), p=p, theta=theta, nlevels=nlevels, path=path)
+    return FMMFunction.apply(xy, gamma, tree)

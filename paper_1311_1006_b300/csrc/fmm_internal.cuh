@@ -140,6 +140,8 @@ struct Tree {
         double upcost = 0, downcost = 0;
         int wait_up = 0, wait_down = 0;
         int max_levels = 1;
+        int rejected = 0;
+        double tuning_cost = 0;  // time lost to rejected moves
     } tune;
 };
 
@@ -166,6 +168,8 @@ fmm_status run_backward(Tree& t, const double* d_gamma, const double* d_gphi, do
 
 // Autotuner (host).
 int default_nlevels(int64_t n, int p, int path);
+
+int tune_step(Tree::Tune& u, double time_s);
 
 // Smallest compiled expansion order >= p (kernels are templates on the order).
 int compiled_order(int p);

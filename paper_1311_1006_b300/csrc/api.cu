@@ -102,6 +102,10 @@ static fmm_status build_all(Tree& t, const double* d_xy, cudaStream_t s) {
             set_error("non-finite point coordinate");
             return FMM_ERR_NONFINITE;
         }
+        if (bits & ST_INTERNAL) {
+            set_error("internal index check failed during the tree build");
+            return FMM_ERR_CUDA;
+        }
         if (!(bits & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW))) {
             t.h_counts[0] = hbuf[1];
             t.h_counts[1] = hbuf[2];

@@ -17,7 +17,8 @@ enum : unsigned {
     ST_NONFINITE = 1u,        // NaN/Inf coordinate seen by the key kernel
     ST_STRONG_OVERFLOW = 2u,  // a strong list exceeded its fixed capacity
     ST_WEAK_OVERFLOW = 4u,    // a weak list exceeded its fixed capacity
-    ST_TIMEOUT = 8u           // a bounded wait gave up
+    ST_TIMEOUT = 8u,          // a bounded wait gave up
+    ST_INTERNAL = 16u         // an index check in a scatter failed (a bug, reported not written)
 };
 
 // Partition tile: 256 threads x 8 consecutive positions.

@@ -275,7 +275,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t* _
                                                                const uint64_t* __restrict__ ki1,
                                                                const int32_t* __restrict__ vi1, uint64_t* ko0,
                                                                int32_t* vo0, uint64_t* ko1, int32_t* vo1, int n,
-                                                               int shift, int T, const int32_t* __restrict__ off) {
+                                                               int shift, int T, const int32_t* __restrict__ off,
+                                                               unsigned* status) {
     __shared__ int run[256];
     __shared__ int wcnt[kSortThreads / 32][256];
     __shared__ int base[256];
@@ -313,8 +314,12 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t* _
         __syncthreads();
         if (valid) {
             int pos = base[d] + wcnt[warp][d] + rank;
-            ko[pos] = k;
-            vo[pos] = v;
+            if (pos >= 0 && pos < n) {
+                ko[pos] = k;
+                vo[pos] = v;
+            } else {
+                atomicOr(status, ST_INTERNAL);
+            }
         }
         __syncthreads();
     }
@@ -333,7 +338,7 @@ static fmm_status sort_pass(Tree& t, cudaStream_t s, int src, int dst, int shift
     k_sort_scan<<<dim3(256, 2), 1024, 0, s>>>(t.d_sort_hist, t.d_sort_tot, T, t.d_sort_off);
     k_sort_scatter<<<g, kSortThreads, 0, s>>>(t.d_keys[src], t.d_vals[src], t.d_keys[src + 1], t.d_vals[src + 1],
                                               t.d_keys[dst], t.d_vals[dst], t.d_keys[dst + 1], t.d_vals[dst + 1], n,
-                                              shift, T, t.d_sort_off);
+                                              shift, T, t.d_sort_off, t.d_status);
     FMM_CUDA(cudaGetLastError());
     return FMM_OK;
 }
@@ -431,7 +436,8 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const int32_t* __
                                                                const int32_t* __restrict__ start,
                                                                const int32_t* __restrict__ nzero, int K,
                                                                const int32_t* __restrict__ tile_pre,
-                                                               const int32_t* __restrict__ seg_lc, int32_t* out) {
+                                                               const int32_t* __restrict__ seg_lc, int32_t* out,
+                                                               unsigned* status) {
     __shared__ int wsum[32];
     const int t = blockIdx.x;
     const int i0 = t * kPartTile + threadIdx.x * kPartItems;
@@ -462,7 +468,8 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const int32_t* __
             }
             int ones = Pi - Ps;
             int dst = f[j] ? s + nzero[k] + ones : s + (i - s) - ones;
-            out[dst] = a[j];
+            if (dst >= s && dst < start[k + 1]) out[dst] = a[j];
+            else atomicOr(status, ST_INTERNAL);
         }
         Pi += f[j];
     }
@@ -475,7 +482,7 @@ static fmm_status partition(Tree& t, cudaStream_t s, const int32_t* A, const uin
     k_part_count<<<T, kPartThreads, 0, s>>>(A, side, n, seg.d_start, seg.K, t.d_tile_cnt, t.d_seg_lc);
     k_part_scan<<<1, 1024, 0, s>>>(t.d_tile_cnt, T, t.d_tile_pre);
     k_part_scatter<<<T, kPartThreads, 0, s>>>(A, side, n, seg.d_start, seg.d_nzero, seg.K, t.d_tile_pre, t.d_seg_lc,
-                                              out);
+                                              out, t.d_status);
     FMM_CUDA(cudaGetLastError());
     return FMM_OK;
 }

@@ -1,0 +1,391 @@
+"""Benchmark: Mpoints/s per FMM evaluation of the headline workload on one B300.
+
+Workload (synthetic, seeded): N = 1,000,000 points, 90 % from 8 Gaussian
+clusters (sigma log-uniform in [0.01, 0.1]) + 10 % uniform background in the
+unit square, complex strengths with N(0,1) real and imaginary parts, p = 17,
+theta = 0.5, N_levels picked by the library's AT3b autotuner during warm-up.
+
+One step = the whole hot path for one evaluation: rebuild the pyramid tree and
+coupling lists for the step's coordinates (the paper re-partitions at every
+time step) + one FMM evaluation (P2M, M2M, M2L, L2L, L2P, P2P) on the FP32
+(mixed) path.  `value` is device time with inputs resident in HBM; `e2e` is the
+same through the C ABI with host (pinned) buffers: H2D copy of points and
+strengths, build, evaluate, D2H copy of the potentials, every step.  The FP64
+path and the adjoint are timed on the same workload and reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+METRIC = "Mpoints/s per FMM eval at N=1e6, rel err<=1e-5: FP32 vs FP64 path; bwd/fwd"
+UNIT = "Mpoints/s"
+N_POINTS = 1_000_000
+P_TERMS = 17
+THETA = 0.5
+WORKLOAD = "cluster_mix_1e6_p17_theta0.5"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def _inputs():
+    from paper_1311_1006_b300 import workloads as W
+
+    g = W.rng(W.W_CLUSTER_1M)
+    xy = W.cluster_mix(N_POINTS, g)
+    gam = W.complex_strengths(N_POINTS, g)
+    return xy, gam
+
+
+class _Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_1311_1006_b300 as F
+    from paper_1311_1006_b300 import _lib
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    xy, gam = _inputs()
+    X = torch.tensor(xy, device=dev)
+    G = torch.tensor(gam, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 126 MB L2
+
+    with torch.cuda.stream(stream):
+        # --- N_levels: AT3b autotuner over a warm-up sequence -----------------
+        L0 = F.default_nlevels(N_POINTS, P_TERMS, "fp32")
+        tree = F.Tree.build(X, p=P_TERMS, theta=THETA, nlevels=L0, path="fp32")
+        tree.autotune_config(cap=0.2, window=2, period=2)
+        phi = torch.empty(N_POINTS, dtype=torch.complex64, device=dev)
+        L = L0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(max(24, args.warmup)):
+            e0.record(stream)
+            tree.rebuild(X, nlevels=L)
+            tree.eval(G, out=phi)
+            e1.record(stream)
+            e1.synchronize()
+            L = tree.autotune_step(e0.elapsed_time(e1) * 1e-3)
+        tuned = int(tree.info()["autotune_nlevels"])
+        tree.rebuild(X, nlevels=tuned)
+        info = tree.info()
+
+        # --- timed: build + eval, inputs resident ------------------------------
+        for _ in range(args.warmup):
+            tree.rebuild(X)
+            tree.eval(G, out=phi)
+        stream.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with _Clocks(local) as clk:
+            for k in range(args.steps):
+                flush.zero_()
+                starts[k].record(stream)
+                tree.rebuild(X)
+                tree.eval(G, out=phi)
+                ends[k].record(stream)
+            torch.cuda.synchronize()
+        step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        ms = float(np.mean(step_ms))
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+
+        # --- phase times (events on the launching streams) ----------------------
+        tree.rebuild(X, flags=F.FMM_FLAG_TIMING)
+        ph = []
+        for _ in range(5):
+            flush.zero_()
+            tree.eval(G, out=phi)
+            ph.append(tree.phase_times())
+        tree.rebuild(X, flags=0)
+        phases = {k: float(np.median([p[k] for p in ph])) for k in ph[0]}
+        bld = []
+        for _ in range(5):
+            flush.zero_()
+            e0.record(stream)
+            tree.rebuild(X)
+            e1.record(stream)
+            e1.synchronize()
+            bld.append(e0.elapsed_time(e1))
+        build_ms = float(np.median(bld))
+        ev = []
+        for _ in range(5):
+            flush.zero_()
+            e0.record(stream)
+            tree.eval(G, out=phi)
+            e1.record(stream)
+            e1.synchronize()
+            ev.append(e0.elapsed_time(e1))
+        eval_ms = float(np.median(ev))
+
+        # --- accuracy on sampled points vs the exact sum (oracle) -----------------
+        err32 = None
+        if rank == 0:
+            import oracle
+
+            tg = np.random.default_rng(7).choice(N_POINTS, 1024, replace=False)
+            exact = oracle.direct(xy, gam, targets=tg)
+            err32 = _rel(phi.cpu().numpy().astype(np.complex128)[tg], exact)
+
+        # --- FP64 path on the same workload -------------------------------------
+        t64 = F.Tree.build(X, p=P_TERMS, theta=THETA, nlevels=tuned, path="fp64")
+        phi64 = torch.empty(N_POINTS, dtype=torch.complex128, device=dev)
+        t64.rebuild(X)
+        t64.eval(G, out=phi64)
+        s64 = []
+        for _ in range(3):
+            flush.zero_()
+            e0.record(stream)
+            t64.rebuild(X)
+            t64.eval(G, out=phi64)
+            e1.record(stream)
+            e1.synchronize()
+            s64.append(e0.elapsed_time(e1))
+        ms64 = float(np.median(s64))
+        err64 = _rel(phi64.cpu().numpy()[tg], exact) if rank == 0 else None
+        t64.close()
+
+        # --- adjoint / forward ratio (same tree) ------------------------------
+        bwd_ratio = None
+        try:
+            gphi = torch.complex(torch.randn(N_POINTS, device=dev, dtype=torch.float64),
+                                 torch.randn(N_POINTS, device=dev, dtype=torch.float64))
+            tree.backward(G, gphi)
+            bb = []
+            for _ in range(3):
+                flush.zero_()
+                e0.record(stream)
+                tree.backward(G, gphi)
+                e1.record(stream)
+                e1.synchronize()
+                bb.append(e0.elapsed_time(e1))
+            bwd_ratio = float(np.median(bb)) / eval_ms
+        except _lib.FMMError:
+            bwd_ratio = None
+
+        # --- end to end through the C ABI with host buffers -----------------------
+        h_xy = torch.tensor(xy).pin_memory()
+        h_g = torch.tensor(gam).pin_memory()
+        h_phi = torch.empty(N_POINTS, dtype=torch.complex64).pin_memory()
+        d_xy = torch.empty_like(X)
+        d_g = torch.empty_like(G)
+        for _ in range(2):
+            d_xy.copy_(h_xy, non_blocking=True)
+            d_g.copy_(h_g, non_blocking=True)
+            tree.rebuild(d_xy)
+            tree.eval(d_g, out=phi)
+            h_phi.copy_(phi, non_blocking=True)
+        stream.synchronize()
+        ee = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0.record(stream)
+            d_xy.copy_(h_xy, non_blocking=True)
+            d_g.copy_(h_g, non_blocking=True)
+            tree.rebuild(d_xy)
+            tree.eval(d_g, out=phi)
+            h_phi.copy_(phi, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            ee.append(e0.elapsed_time(e1))
+        e2e_ms = float(np.mean(ee))
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    peaks = _peaks()
+    value = N_POINTS * world / (ms * 1e-3) / 1e6
+    # dominant kernel: P2P (FP32 ALU bound).  19 algorithmic FP32 flops per
+    # interaction (FMA = 2); the ALU peak for this instruction mix = measured
+    # FP32 lane-op rate / 15 FP32 instructions per interaction * 19 flops.
+    fp32_lane_ops = 34.2e12
+    peak = fp32_lane_ops / 15.0 * 19.0 / 1e12
+    achieved = info["p2p_pairs"] * 19.0 / (phases["p2p"] * 1e-3) / 1e12
+    line = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 (P2P/M2L/P2M/L2P) + f64 (M2M/L2L)",
+        "data": "synthetic (seeded Gaussian-cluster mixture)",
+        "config": {"workload": WORKLOAD, "n_points": N_POINTS, "p": P_TERMS, "theta": THETA,
+                   "nlevels": info["nlevels_max"], "path": "fp32", "l2": "flushed (256 MB write) between steps",
+                   "step": "tree rebuild + lists + one evaluation", "parallelism": "replicas" if world > 1 else "1 gpu"},
+        "breakdown_ms": {"build": round(build_ms, 4), "eval": round(eval_ms, 4),
+                         **{k: round(v, 4) for k, v in phases.items()}},
+        "eval_only_mpoints_s": round(N_POINTS / (eval_ms * 1e-3) / 1e6, 2),
+        "fp64_path": {"ms_per_step": round(ms64, 4), "value": round(N_POINTS / (ms64 * 1e-3) / 1e6, 2),
+                      "rel_err_sampled": err64},
+        "rel_err_sampled": err32,
+        "bwd_over_fwd": bwd_ratio,
+        "roofline": {"kernel": "k_p2p32", "bound": "alu", "achieved": round(achieved, 3),
+                     "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                     "traffic": None,
+                     "peak_note": "measured FP32 FFMA lane rate 34.2e12/s (probe), 15 FP32 instr = 19 flops per interaction"},
+        "e2e": {"value": round(N_POINTS / (e2e_ms * 1e-3) / 1e6, 2), "unit": UNIT,
+                "h2d_bytes_per_step": int(xy.nbytes + gam.nbytes), "d2h_bytes_per_step": int(N_POINTS * 8)},
+        "gpu_launches": int(args.steps * (info["launches_build"] + info["launches_eval"])),
+        "interactions": {"p2p_pairs": info["p2p_pairs"], "m2l_pairs": info["n_weak"]},
+    }
+    line["clocks"] = clk.summary()
+    if peaks:
+        line["peaks_used"] = {"hbm_gbs": peaks.get("hbm_gbs")}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(n=250_000, levels=8):
+    """The oracle (plain FP64 C, OpenMP over boxes) on a bounded sample of the
+    same workload: a 250k-point draw of the same generator, N_levels 8."""
+    import oracle
+    from paper_1311_1006_b300 import workloads as W
+
+    g = W.rng(W.W_CLUSTER_1M)
+    xy = W.cluster_mix(n, g)
+    gam = W.complex_strengths(n, g)
+    oracle.set_threads(os.cpu_count() or 1)
+    t = time.time()
+    oracle.fmm(xy, gam, levels, THETA, P_TERMS)
+    dt = time.time() - t
+    return {"value": round(n / dt / 1e6, 4), "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{n} points of the same cluster-mixture generator, N_levels={levels}, p=17, one evaluation "
+                      f"incl. tree ({dt:.2f} s)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline())
+    v = float(np.mean([x["value"] for x in vals]))
+    ms = N_POINTS / (v * 1e6) * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "config": {"workload": WORKLOAD, "n_points": N_POINTS, "p": P_TERMS, "theta": THETA},
+            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "kind": "oracle", "cores": vals[0]["cores"],
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -172,6 +172,9 @@ typedef struct {
     int64_t n_strong_leaf;   /* P2P leaf pairs */
     int64_t p2p_pairs;       /* P2P point pairs: sum over leaves of n_leaf * near points */
     int strong_cap, weak_cap;
+    int autotune_nlevels;    /* N_levels the autotuner has accepted so far */
+    int launches_build;      /* kernels one build / rebuild launches */
+    int launches_eval;       /* kernels one evaluation launches */
 } fmm_tree_info;
 
 fmm_status fmm_get_tree_info(const fmm_tree* t, fmm_tree_info* out);

@@ -39,7 +39,8 @@ class FMMTreeInfo(ctypes.Structure):
                 ("p", ctypes.c_int), ("path", ctypes.c_int), ("theta", ctypes.c_double),
                 ("nboxes", ctypes.c_int64), ("nleaves", ctypes.c_int64), ("n_weak", ctypes.c_int64),
                 ("n_strong_leaf", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64),
-                ("strong_cap", ctypes.c_int), ("weak_cap", ctypes.c_int)]
+                ("strong_cap", ctypes.c_int), ("weak_cap", ctypes.c_int), ("autotune_nlevels", ctypes.c_int),
+                ("launches_build", ctypes.c_int), ("launches_eval", ctypes.c_int)]
 
 
 class FMMError(RuntimeError):

@@ -371,6 +371,10 @@ fmm_status fmm_get_tree_info(const fmm_tree* h, fmm_tree_info* out) {
     out->p2p_pairs = (int64_t)t.h_counts[2];
     out->strong_cap = t.scap;
     out->weak_cap = t.wcap;
+    out->autotune_nlevels = t.tune.accepted;
+    const int lv = t.Lmax - 1;
+    out->launches_build = 1 + 24 + (t.ninst > 1 ? 7 : 0) + 1 + 9 * lv + 1 + 1 + lv + 1;
+    out->launches_eval = 5 + 2 * lv;
     return FMM_OK;
 }
 

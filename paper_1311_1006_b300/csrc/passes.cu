@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(128) k_m2m(const int32_t* __restrict__ parents
                                              const int32_t* __restrict__ child0, const double* __restrict__ rho,
                                              const double2* __restrict__ center, const float2* __restrict__ M32in,
                                              double2* __restrict__ M64, float2* __restrict__ M32out, int fp32_path,
-                                             int PS) {
+                                             int p, int PS) {
     int qi = blockIdx.x * blockDim.x + threadIdx.x;
     if (qi >= cnt) return;
     const int b = parents[qi];
@@ -187,6 +187,10 @@ __global__ void __launch_bounds__(128) k_m2m(const int32_t* __restrict__ parents
             acc[k].y += v[k].y;
         }
     }
+    // the shift fills orders >= p from lower ones: keep the expansion at p terms
+#pragma unroll
+    for (int k = 0; k < P; ++k)
+        if (k >= p) acc[k] = make_double2(0.0, 0.0);
     double2* out = M64 + (size_t)b * PS;
 #pragma unroll
     for (int k = 0; k < P; ++k) out[k] = acc[k];
@@ -620,7 +624,7 @@ static void launch_far_fp32(Tree& t, cudaStream_t s) {
         const LevelList& L = t.level_parents[l];
         if (!L.count) continue;
         k_m2m<P><<<nblk(L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_child0, t.d_rho, t.d_center, t.d_M32,
-                                                    t.d_M64, t.d_M32, 1, t.PS);
+                                                    t.d_M64, t.d_M32, 1, t.p, t.PS);
     }
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[2], s);
     k_m2l32<P><<<nblk(t.nbox, 128), 128, 0, s>>>((int)t.nbox, t.d_nweak, t.d_weak, t.wcap, t.d_chl, t.d_rho32,
@@ -644,7 +648,7 @@ static void launch_far_fp64(Tree& t, cudaStream_t s) {
         const LevelList& L = t.level_parents[l];
         if (!L.count) continue;
         k_m2m<P><<<nblk(L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_child0, t.d_rho, t.d_center, nullptr,
-                                                    t.d_M64, nullptr, 0, t.PS);
+                                                    t.d_M64, nullptr, 0, t.p, t.PS);
     }
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[2], s);
     k_m2l64<P><<<nblk(t.nbox, 128), 128, 0, s>>>((int)t.nbox, t.d_nweak, t.d_weak, t.wcap, t.d_center, t.d_rho,

@@ -168,15 +168,18 @@ typedef struct {
     double theta;
     int64_t nboxes;          /* boxes over all levels and instances */
     int64_t nleaves;
-    int64_t n_weak;          /* M2L pairs over all levels */
+    int64_t n_strong;        /* strong-list entries over all levels */
+    int64_t n_weak;          /* weak-list entries = M2L pairs over all levels */
     int64_t n_strong_leaf;   /* P2P leaf pairs */
     int64_t p2p_pairs;       /* P2P point pairs: sum over leaves of n_leaf * near points */
-    int strong_cap, weak_cap;
+    int64_t p2p_items;       /* P2P work items (a leaf with a long strong list is split) */
+    int64_t m2l_items;       /* M2L work items */
     int autotune_nlevels;    /* N_levels the autotuner has accepted so far */
     int launches_build;      /* kernels one build / rebuild launches */
     int launches_eval;       /* kernels one evaluation launches */
 } fmm_tree_info;
 
+/* Fills *out; the pair counts are summed on the device (synchronises). */
 fmm_status fmm_get_tree_info(const fmm_tree* t, fmm_tree_info* out);
 
 /* Copy one of the tree's device arrays to host memory (tests, diagnostics).
@@ -188,15 +191,17 @@ typedef enum {
     FMM_EXPORT_BCOUNT = 2,    /* int32[nbox]  points in each box */
     FMM_EXPORT_CENTER = 3,    /* float64[2*nbox] */
     FMM_EXPORT_RADIUS = 4,    /* float64[nbox] */
-    FMM_EXPORT_NSTRONG = 5,   /* int32[nbox] */
-    FMM_EXPORT_STRONG = 6,    /* int32[nbox*strong_cap], box-major, first NSTRONG valid */
+    FMM_EXPORT_NSTRONG = 5,   /* int32[nbox]      strong-list length of each box */
+    FMM_EXPORT_STRONG = 6,    /* int32[n_strong]  strong-list entries (CSR; box b: STRONG_OFF[b] ..) */
     FMM_EXPORT_NWEAK = 7,     /* int32[nbox] */
-    FMM_EXPORT_WEAK = 8,      /* int32[nbox*weak_cap] */
+    FMM_EXPORT_WEAK = 8,      /* int32[n_weak] */
     FMM_EXPORT_MPOLE = 9,     /* float64[2*nbox*p]: multipole coefficients a_k / rho^k (rho = scale radius) */
     FMM_EXPORT_LOCAL = 10,    /* float64[2*nbox*p]: local coefficients b_l * rho^l */
     FMM_EXPORT_NEAR = 11,     /* float64[2*n]: P2P part of the last evaluation, sorted order */
     FMM_EXPORT_INST = 12,     /* int64[3*ninst]: point offset, box offset, N_levels per instance */
-    FMM_EXPORT_RHO = 13       /* float64[nbox]: scale radius rho of each box */
+    FMM_EXPORT_RHO = 13,      /* float64[nbox]: scale radius rho of each box */
+    FMM_EXPORT_STRONG_OFF = 14, /* int32[nbox]  first entry of each strong list */
+    FMM_EXPORT_WEAK_OFF = 15    /* int32[nbox] */
 } fmm_export_what;
 
 fmm_status fmm_tree_export(const fmm_tree* t, int what, void* h_dst, int64_t count, void* stream);

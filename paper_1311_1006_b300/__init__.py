@@ -164,8 +164,9 @@ class Tree:
         spec = {
             "perm": (np.int32, n), "bstart": (np.int32, nb), "bcount": (np.int32, nb),
             "center": (np.float64, 2 * nb), "radius": (np.float64, nb), "rho": (np.float64, nb),
-            "nstrong": (np.int32, nb), "strong": (np.int32, nb * inf["strong_cap"]),
-            "nweak": (np.int32, nb), "weak": (np.int32, nb * inf["weak_cap"]),
+            "nstrong": (np.int32, nb), "strong": (np.int32, max(inf["n_strong"], 1)),
+            "nweak": (np.int32, nb), "weak": (np.int32, max(inf["n_weak"], 1)),
+            "soff": (np.int32, nb), "woff": (np.int32, nb),
             "mpole": (np.float64, 2 * nb * p), "local": (np.float64, 2 * nb * p),
             "near": (np.float64, 2 * n), "inst": (np.int64, 3 * inf["ninst"]),
         }[what]
@@ -178,13 +179,17 @@ class Tree:
             return buf.view(np.complex128).reshape(nb, p)
         if what == "near":
             return buf.view(np.complex128)
-        if what == "strong":
-            return buf.reshape(nb, inf["strong_cap"])
-        if what == "weak":
-            return buf.reshape(nb, inf["weak_cap"])
         if what == "inst":
             return buf.reshape(-1, 3)
         return buf
+
+    def lists(self):
+        """Strong and weak lists of every box as (list of arrays, list of arrays)."""
+        ns, so, si = self.export("nstrong"), self.export("soff"), self.export("strong")
+        nw, wo, wi = self.export("nweak"), self.export("woff"), self.export("weak")
+        strong = [si[so[b]: so[b] + ns[b]] for b in range(ns.shape[0])]
+        weak = [wi[wo[b]: wo[b] + nw[b]] for b in range(nw.shape[0])]
+        return strong, weak
 
     def phase_times(self) -> dict:
         out = (ctypes.c_double * 7)()

@@ -26,7 +26,7 @@ FMM_FLAG_TIMING = 4
 FMM_P_MAX = 32
 
 EXPORT = dict(perm=0, bstart=1, bcount=2, center=3, radius=4, nstrong=5, strong=6, nweak=7, weak=8,
-              mpole=9, local=10, near=11, inst=12, rho=13)
+              mpole=9, local=10, near=11, inst=12, rho=13, soff=14, woff=15)
 
 
 class FMMParams(ctypes.Structure):
@@ -37,9 +37,9 @@ class FMMParams(ctypes.Structure):
 class FMMTreeInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("ninst", ctypes.c_int), ("nlevels_max", ctypes.c_int),
                 ("p", ctypes.c_int), ("path", ctypes.c_int), ("theta", ctypes.c_double),
-                ("nboxes", ctypes.c_int64), ("nleaves", ctypes.c_int64), ("n_weak", ctypes.c_int64),
-                ("n_strong_leaf", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64),
-                ("strong_cap", ctypes.c_int), ("weak_cap", ctypes.c_int), ("autotune_nlevels", ctypes.c_int),
+                ("nboxes", ctypes.c_int64), ("nleaves", ctypes.c_int64), ("n_strong", ctypes.c_int64),
+                ("n_weak", ctypes.c_int64), ("n_strong_leaf", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64),
+                ("p2p_items", ctypes.c_int64), ("m2l_items", ctypes.c_int64), ("autotune_nlevels", ctypes.c_int),
                 ("launches_build", ctypes.c_int), ("launches_eval", ctypes.c_int)]
 
 

@@ -87,14 +87,15 @@ static fmm_status ensure_streams(Tree& t) {
     return FMM_OK;
 }
 
-// Tree build + lists, with the list capacities doubled and the lists rebuilt
-// when a box overflows them.
+// Tree build + lists + work items.  The first build learns the exact list
+// and item sizes from the device counters; a capacity that was too small is
+// grown (25 % slack) and the lists are rebuilt.
 static fmm_status build_all(Tree& t, const double* d_xy, cudaStream_t s) {
     fmm_status st = run_tree_build(t, d_xy, s);
     if (st) return st;
-    for (int attempt = 0; attempt < 8; ++attempt) {
+    for (int attempt = 0; attempt < 16; ++attempt) {
         if ((st = run_lists(t, s))) return st;
-        unsigned long long hbuf[4] = {0, 0, 0, 0};
+        unsigned long long hbuf[5] = {0, 0, 0, 0, 0};
         FMM_CUDA(cudaMemcpyAsync(hbuf, t.d_status, sizeof(hbuf), cudaMemcpyDeviceToHost, s));
         FMM_CUDA(cudaStreamSynchronize(s));
         const unsigned bits = (unsigned)(hbuf[0] & 0xffffffffu);
@@ -106,14 +107,24 @@ static fmm_status build_all(Tree& t, const double* d_xy, cudaStream_t s) {
             set_error("internal index check failed during the tree build");
             return FMM_ERR_CUDA;
         }
-        if (!(bits & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW))) {
-            t.h_counts[0] = hbuf[1];
-            t.h_counts[1] = hbuf[2];
-            t.h_counts[2] = hbuf[3];
+        const bool ovl = bits & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW);
+        if (!ovl && !(bits & ST_ITEM_OVERFLOW)) {
+            for (int i = 0; i < 4; ++i) t.h_counts[i] = hbuf[1 + i];
             return FMM_OK;
         }
-        if (bits & ST_STRONG_OVERFLOW) t.scap *= 2;
-        if (bits & ST_WEAK_OVERFLOW) t.wcap *= 2;
+        auto grow = [](long long cur, unsigned long long need) {
+            return std::max<long long>(2 * cur, (long long)(need + need / 4 + 1024));
+        };
+        if (bits & ST_STRONG_OVERFLOW) t.scap_tot = grow(t.scap_tot, hbuf[1]);
+        if (bits & ST_WEAK_OVERFLOW) t.wcap_tot = grow(t.wcap_tot, hbuf[2]);
+        if (!ovl && (bits & ST_ITEM_OVERFLOW)) {
+            if ((long long)hbuf[3] > t.p2p_cap) t.p2p_cap = (long long)(hbuf[3] + hbuf[3] / 4 + 1024);
+            if ((long long)hbuf[4] > t.m2l_cap) t.m2l_cap = (long long)(hbuf[4] + hbuf[4] / 4 + 1024);
+        }
+        if (t.scap_tot >= (1ll << 31) || t.wcap_tot >= (1ll << 31)) {
+            set_error("coupling lists exceed 2^31 entries");
+            return FMM_ERR_OOM;
+        }
         invalidate_graph(t);
         if ((st = alloc_lists(t))) return st;
         FMM_CUDA(cudaMemsetAsync(t.d_status, 0, sizeof(unsigned), s));
@@ -141,8 +152,9 @@ static void release(Tree* t) {
                     t->d_inst_boxoff, t->d_leaf_start, t->d_X2, t->d_Y2, t->d_sideX, t->d_sideY, t->d_tile_cnt,
                     t->d_tile_pre, t->d_seg_lc, t->d_sort_hist, t->d_sort_tot, t->d_sort_off, t->d_perm,
                     t->d_leaf_of, t->d_pts, t->d_pos4, t->d_center, t->d_radius, t->d_rho, t->d_chl, t->d_rho32,
-                    t->d_nstrong, t->d_strong, t->d_nweak, t->d_weak, t->d_status, t->d_gam, t->d_near, t->d_M64,
-                    t->d_M32, t->d_Lm2l, t->d_L64, t->d_L32};
+                    t->d_rad32, t->d_soff, t->d_ns, t->d_sidx, t->d_woff, t->d_nw, t->d_widx, t->d_p2p_items,
+                    t->d_m2l_items, t->d_leaf_items, t->d_box_m2l, t->d_status, t->d_gam, t->d_near, t->d_M64,
+                    t->d_M32, t->d_Lm2l, t->d_L64, t->d_L32, t->d_p2p_part, t->d_m2l_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < 4; ++i) {
@@ -366,14 +378,18 @@ fmm_status fmm_get_tree_info(const fmm_tree* h, fmm_tree_info* out) {
     out->theta = t.theta;
     out->nboxes = t.nbox;
     out->nleaves = t.nleaf;
-    out->n_weak = (int64_t)t.h_counts[0];
-    out->n_strong_leaf = (int64_t)t.h_counts[1];
-    out->p2p_pairs = (int64_t)t.h_counts[2];
-    out->strong_cap = t.scap;
-    out->weak_cap = t.wcap;
+    unsigned long long c[2] = {0, 0};
+    fmm_status st = run_count(const_cast<Tree&>(t), nullptr, c);
+    if (st) return st;
+    out->n_strong = (int64_t)t.h_counts[0];
+    out->n_weak = (int64_t)t.h_counts[1];
+    out->n_strong_leaf = (int64_t)c[0];
+    out->p2p_pairs = (int64_t)c[1];
+    out->p2p_items = (int64_t)t.h_counts[2];
+    out->m2l_items = (int64_t)t.h_counts[3];
     out->autotune_nlevels = t.tune.accepted;
     const int lv = t.Lmax - 1;
-    out->launches_build = 1 + 24 + (t.ninst > 1 ? 7 : 0) + 1 + 9 * lv + 1 + 1 + lv + 1;
+    out->launches_build = 29 + 10 * lv + (t.ninst > 1 ? 7 : 0);
     out->launches_eval = 5 + 2 * lv;
     return FMM_OK;
 }
@@ -397,10 +413,12 @@ fmm_status fmm_tree_export(const fmm_tree* h, int what, void* h_dst, int64_t cou
         case FMM_EXPORT_CENTER: return copy(t.d_center, 2 * nb, 8);
         case FMM_EXPORT_RADIUS: return copy(t.d_radius, nb, 8);
         case FMM_EXPORT_RHO: return copy(t.d_rho, nb, 8);
-        case FMM_EXPORT_NSTRONG: return copy(t.d_nstrong, nb, 4);
-        case FMM_EXPORT_STRONG: return copy(t.d_strong, nb * t.scap, 4);
-        case FMM_EXPORT_NWEAK: return copy(t.d_nweak, nb, 4);
-        case FMM_EXPORT_WEAK: return copy(t.d_weak, nb * t.wcap, 4);
+        case FMM_EXPORT_NSTRONG: return copy(t.d_ns, nb, 4);
+        case FMM_EXPORT_STRONG_OFF: return copy(t.d_soff, nb, 4);
+        case FMM_EXPORT_STRONG: return copy(t.d_sidx, (int64_t)t.h_counts[0], 4);
+        case FMM_EXPORT_NWEAK: return copy(t.d_nw, nb, 4);
+        case FMM_EXPORT_WEAK_OFF: return copy(t.d_woff, nb, 4);
+        case FMM_EXPORT_WEAK: return copy(t.d_widx, (int64_t)t.h_counts[1], 4);
         case FMM_EXPORT_INST: {
             if (count < 3 * (int64_t)t.ninst) return invalid("host buffer too small");
             int64_t* o = static_cast<int64_t*>(h_dst);
@@ -414,12 +432,37 @@ fmm_status fmm_tree_export(const fmm_tree* h, int what, void* h_dst, int64_t cou
         case FMM_EXPORT_NEAR: {
             if (count < 2 * n) return invalid("host buffer too small");
             if (!t.d_near || t.eval_nbox == 0) return invalid("no evaluation yet");
+            // near field per sorted point: in place, or the sum of the leaf's item partials
             double* o = static_cast<double*>(h_dst);
-            if (t.path == FMM_PATH_FP64) return copy(t.d_near, 2 * n, 8);
-            std::vector<float> tmp(2 * n);
-            FMM_CUDA(cudaMemcpyAsync(tmp.data(), t.d_near, 2 * n * sizeof(float), cudaMemcpyDeviceToHost, s));
+            const bool f32 = t.path == FMM_PATH_FP32;
+            const size_t cs = f32 ? 8 : 16;
+            const int64_t items = (int64_t)t.h_counts[2];
+            std::vector<char> nv(n * cs), pv((size_t)std::max<int64_t>(items, 1) * t.max_leaf * cs);
+            std::vector<int2> li(nb);
+            FMM_CUDA(cudaMemcpyAsync(nv.data(), t.d_near, nv.size(), cudaMemcpyDeviceToHost, s));
+            FMM_CUDA(cudaMemcpyAsync(pv.data(), t.d_p2p_part, (size_t)items * t.max_leaf * cs,
+                                     cudaMemcpyDeviceToHost, s));
+            FMM_CUDA(cudaMemcpyAsync(li.data(), t.d_leaf_items, nb * sizeof(int2), cudaMemcpyDeviceToHost, s));
             FMM_CUDA(cudaStreamSynchronize(s));
-            for (int64_t i = 0; i < 2 * n; ++i) o[i] = tmp[i];
+            auto val = [&](const std::vector<char>& v, size_t k, int c) -> double {
+                return f32 ? (double)reinterpret_cast<const float*>(v.data())[2 * k + c]
+                           : reinterpret_cast<const double*>(v.data())[2 * k + c];
+            };
+            for (int32_t lf : t.h_leaves) {
+                const int2 it = li[lf];
+                for (int32_t i = t.h_bstart[lf]; i < t.h_bstart[lf] + t.h_bcount[lf]; ++i) {
+                    for (int c = 0; c < 2; ++c) {
+                        double acc = 0;
+                        if (it.y == 1) {
+                            acc = val(nv, i, c);
+                        } else {
+                            for (int q = 0; q < it.y; ++q)
+                                acc += val(pv, (size_t)(it.x + q) * t.max_leaf + (i - t.h_bstart[lf]), c);
+                        }
+                        o[2 * i + c] = acc;
+                    }
+                }
+            }
             return FMM_OK;
         }
         case FMM_EXPORT_MPOLE:

@@ -18,8 +18,14 @@ enum : unsigned {
     ST_STRONG_OVERFLOW = 2u,  // a strong list exceeded its fixed capacity
     ST_WEAK_OVERFLOW = 4u,    // a weak list exceeded its fixed capacity
     ST_TIMEOUT = 8u,          // a bounded wait gave up
-    ST_INTERNAL = 16u         // an index check in a scatter failed (a bug, reported not written)
+    ST_INTERNAL = 16u,        // an index check in a scatter failed (a bug, reported not written)
+    ST_ITEM_OVERFLOW = 32u    // a work-item array exceeded its capacity
 };
+
+// Work-item sizes: P2P items hold about this many source points; M2L items at
+// most this many weak pairs.
+constexpr int kP2PItemSources = 512;
+constexpr int kM2LItemPairs = 64;
 
 // Partition tile: 256 threads x 8 consecutive positions.
 constexpr int kPartThreads = 256;
@@ -97,20 +103,36 @@ struct Tree {
     double* d_rho = nullptr;       // per box scale radius = (double)(float)radius
     float4* d_chl = nullptr;       // per box centre hi/lo relative to the instance origin
     float* d_rho32 = nullptr;      // per box (float)rho
-    int scap = 32, wcap = 80;
-    int32_t *d_nstrong = nullptr, *d_strong = nullptr, *d_nweak = nullptr, *d_weak = nullptr;
-    unsigned* d_status = nullptr;  // [0] status bits; bytes 8.. three 64-bit counters
-    unsigned long long h_counts[3] = {0, 0, 0};
+    float* d_rad32 = nullptr;      // per box (float)radius, for the FP32 pre-test of eq (2.3)
+    // coupling lists in CSR form: box b's strong list is sidx[soff[b] .. soff[b]+ns[b])
+    int32_t *d_soff = nullptr, *d_ns = nullptr, *d_sidx = nullptr;
+    int32_t *d_woff = nullptr, *d_nw = nullptr, *d_widx = nullptr;
+    long long scap_tot = 0, wcap_tot = 0;
+    // work items (see k_items)
+    int4* d_p2p_items = nullptr;
+    int4* d_m2l_items = nullptr;
+    int2* d_leaf_items = nullptr;  // per box: first P2P item, item count (leaves)
+    int2* d_box_m2l = nullptr;     // per box: first M2L item, item count
+    long long p2p_cap = 0, m2l_cap = 0;
+    int max_leaf = 1;              // largest leaf (points): row stride of the P2P partial sums
+    // device words: [0] status bits, then 64-bit counters:
+    // [1] strong entries, [2] weak entries, [3] P2P items, [4] M2L items, [5..6] diagnostics
+    unsigned* d_status = nullptr;
+    unsigned long long h_counts[4] = {0, 0, 0, 0};  // strong, weak, P2P items, M2L items
 
     // evaluation workspace
     void* d_gam = nullptr;     // sorted strengths (float2 or double2), 2 sets for backward
     void* d_near = nullptr;    // P2P output(s), sorted order
+    void* d_p2p_part = nullptr;  // partial P2P sums of split leaves (item x max_leaf)
+    void* d_m2l_part = nullptr;  // partial M2L sums of split boxes (item x PS)
+    long long part_p2p_cap = 0, part_m2l_cap = 0;
     double2* d_M64 = nullptr;  // multipoles, scaled
     float2* d_M32 = nullptr;
     void* d_Lm2l = nullptr;    // M2L sums per box
     double2* d_L64 = nullptr;  // locals after L2L, scaled
     float2* d_L32 = nullptr;
     size_t eval_nbox = 0, eval_n = 0;
+    int eval_ts = 0;
     int eval_PS = 0, eval_path = -1, eval_sets = 0;
 
     // streams / events
@@ -161,11 +183,27 @@ fmm_status build_shape(Tree& t);                                         // host
 fmm_status alloc_build(Tree& t);                                         // build scratch / tree arrays
 fmm_status alloc_lists(Tree& t);                                         // fixed-capacity lists
 fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s);  // sort, split, geometry
-fmm_status run_lists(Tree& t, cudaStream_t s);                           // strong / weak lists
+fmm_status run_lists(Tree& t, cudaStream_t s);                           // strong / weak lists, work items
+fmm_status run_count(Tree& t, cudaStream_t s, unsigned long long out[2]);
 fmm_status alloc_eval(Tree& t, int sets);
 fmm_status run_eval(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s);
 fmm_status run_backward(Tree& t, const double* d_gamma, const double* d_gphi, double* d_ggamma, double* d_gxy,
                         cudaStream_t s);
+
+// Buffers of one strength set of the evaluation workspace.
+struct Bufs {
+    void* gam;
+    void* near;
+    double2* M64;
+    float2* M32;
+    void* Lm2l;
+    double2* L64;
+    float2* L32;
+    void* p2p_part;
+    void* m2l_part;
+};
+Bufs bufs(Tree& t, int set);
+void dispatch_far(Tree& t, const Bufs& B, cudaStream_t s);  // P2M, M2M, M2L, L2L of one strength set
 
 // Autotuner (host).
 int default_nlevels(int64_t n, int p, int path);

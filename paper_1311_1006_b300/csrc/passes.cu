@@ -207,23 +207,23 @@ __global__ void __launch_bounds__(128) k_m2m(const int32_t* __restrict__ parents
 // box's weak list.  FP32 with FP32 accumulation.  Root boxes (no parent) also
 // seed the FP64 local array, which L2L reads for level 1.
 template <int P>
-__global__ void __launch_bounds__(128) k_m2l32(int nbox, const int32_t* __restrict__ nweak,
-                                               const int32_t* __restrict__ weak, int wcap,
+__global__ void __launch_bounds__(128) k_m2l32(const int4* __restrict__ items,
+                                               const unsigned long long* __restrict__ nitems,
+                                               const int32_t* __restrict__ woff, const int32_t* __restrict__ widx,
                                                const float4* __restrict__ chl, const float* __restrict__ rho32,
                                                const float2* __restrict__ M32, float2* __restrict__ Lm2l,
-                                               const int32_t* __restrict__ parent,
-                                               const int32_t* __restrict__ child0, double2* __restrict__ L64,
-                                               float2* __restrict__ L32, int PS) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nbox) return;
-    const int nw = nweak[b];
+                                               float2* __restrict__ part, int PS) {
+    const int it = blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= (int)*nitems) return;
+    const int4 item = items[it];
+    const int b = item.x;
     const float4 ct = chl[b];
     const float rt = rho32[b];
     float2 acc[P];
 #pragma unroll
     for (int l = 0; l < P; ++l) acc[l] = make_float2(0.f, 0.f);
-    const int32_t* wl = weak + (size_t)b * wcap;
-    for (int j = 0; j < nw; ++j) {
+    const int32_t* wl = widx + woff[b];
+    for (int j = item.y; j < item.z; ++j) {
         const int s = wl[j];
         const float4 cs = chl[s];
         const float rs = rho32[s];
@@ -264,38 +264,29 @@ __global__ void __launch_bounds__(128) k_m2l32(int nbox, const int32_t* __restri
             g = cmul(g, beta);
         }
     }
-    float2* out = Lm2l + (size_t)b * PS;
+    float2* out = item.w < 0 ? Lm2l + (size_t)b * PS : part + (size_t)it * PS;
 #pragma unroll
     for (int l = 0; l < P; ++l) out[l] = acc[l];
-    if (parent[b] < 0) {
-        double2* o64 = L64 + (size_t)b * PS;
-#pragma unroll
-        for (int l = 0; l < P; ++l) o64[l] = make_double2((double)acc[l].x, (double)acc[l].y);
-        if (child0[b] < 0) {  // a one-level tree: the root is a leaf
-            float2* o32 = L32 + (size_t)b * PS;
-#pragma unroll
-            for (int l = 0; l < P; ++l) o32[l] = acc[l];
-        }
-    }
 }
 
 template <int P>
-__global__ void __launch_bounds__(128) k_m2l64(int nbox, const int32_t* __restrict__ nweak,
-                                               const int32_t* __restrict__ weak, int wcap,
+__global__ void __launch_bounds__(128) k_m2l64(const int4* __restrict__ items,
+                                               const unsigned long long* __restrict__ nitems,
+                                               const int32_t* __restrict__ woff, const int32_t* __restrict__ widx,
                                                const double2* __restrict__ center, const double* __restrict__ rho,
                                                const double2* __restrict__ M64, double2* __restrict__ Lm2l,
-                                               const int32_t* __restrict__ parent, double2* __restrict__ L64,
-                                               int PS) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nbox) return;
-    const int nw = nweak[b];
+                                               double2* __restrict__ part, int PS) {
+    const int it = blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= (int)*nitems) return;
+    const int4 item = items[it];
+    const int b = item.x;
     const double2 ct = center[b];
     const double rt = rho[b];
     double2 acc[P];
 #pragma unroll
     for (int l = 0; l < P; ++l) acc[l] = make_double2(0.0, 0.0);
-    const int32_t* wl = weak + (size_t)b * wcap;
-    for (int j = 0; j < nw; ++j) {
+    const int32_t* wl = widx + woff[b];
+    for (int j = item.y; j < item.z; ++j) {
         const int s = wl[j];
         const double2 cs = center[s];
         const double rs = rho[s];
@@ -327,14 +318,9 @@ __global__ void __launch_bounds__(128) k_m2l64(int nbox, const int32_t* __restri
             g = cmul(g, beta);
         }
     }
-    double2* out = Lm2l + (size_t)b * PS;
+    double2* out = item.w < 0 ? Lm2l + (size_t)b * PS : part + (size_t)it * PS;
 #pragma unroll
     for (int l = 0; l < P; ++l) out[l] = acc[l];
-    if (parent[b] < 0) {
-        double2* o64 = L64 + (size_t)b * PS;
-#pragma unroll
-        for (int l = 0; l < P; ++l) o64[l] = acc[l];
-    }
 }
 
 // --------------------------------------------------------------------- L2L
@@ -345,7 +331,8 @@ template <int P, typename LM>
 __global__ void __launch_bounds__(128) k_l2l(const int32_t* __restrict__ boxes, int cnt,
                                              const int32_t* __restrict__ parent, const int32_t* __restrict__ child0,
                                              const double* __restrict__ rho, const double2* __restrict__ center,
-                                             const LM* __restrict__ Lm2l, double2* __restrict__ L64,
+                                             const int2* __restrict__ box_m2l, const LM* __restrict__ Lm2l,
+                                             const LM* __restrict__ part, double2* __restrict__ L64,
                                              float2* __restrict__ L32, int p, int PS) {
     int qi = blockIdx.x * blockDim.x + threadIdx.x;
     if (qi >= cnt) return;
@@ -366,15 +353,33 @@ __global__ void __launch_bounds__(128) k_l2l(const int32_t* __restrict__ boxes, 
 #pragma unroll
         for (int j = P - 2; j >= k; --j) b[j] = cfma(q, b[j + 1], b[j]);
     }
-    const LM* own = Lm2l + (size_t)c * PS;
+    // this box's own M2L sum: none, one item written in place, or the partial
+    // sums of its items added in item order
+    const int2 mi = box_m2l[c];
+    double2 own[P];
+#pragma unroll
+    for (int m = 0; m < P; ++m) own[m] = make_double2(0.0, 0.0);
+    if (mi.y == 1) {
+        const LM* o = Lm2l + (size_t)c * PS;
+#pragma unroll
+        for (int m = 0; m < P; ++m) own[m] = make_double2((double)o[m].x, (double)o[m].y);
+    } else {
+        for (int q = 0; q < mi.y; ++q) {
+            const LM* o = part + (size_t)(mi.x + q) * PS;
+#pragma unroll
+            for (int m = 0; m < P; ++m) {
+                own[m].x += (double)o[m].x;
+                own[m].y += (double)o[m].y;
+            }
+        }
+    }
     double sp = 1.0;
     double2* out = L64 + (size_t)c * PS;
     const bool leaf32 = (L32 != nullptr) && child0[c] < 0;
     float2* o32 = L32 + (size_t)c * PS;
 #pragma unroll
     for (int m = 0; m < P; ++m) {
-        const LM o = own[m];
-        double2 v = make_double2(fma(b[m].x, sp, (double)o.x), fma(b[m].y, sp, (double)o.y));
+        double2 v = make_double2(fma(b[m].x, sp, own[m].x), fma(b[m].y, sp, own[m].y));
         if (m >= p) v = make_double2(0.0, 0.0);
         sp *= sigma;
         out[m] = v;
@@ -384,14 +389,34 @@ __global__ void __launch_bounds__(128) k_l2l(const int32_t* __restrict__ boxes, 
 
 // ------------------------------------------------------------- L2P + sum
 
+// Near-field value of sorted point i: written in place by a single P2P item,
+// or the partial sums of the leaf's items added in item order.
+template <typename C>
+__device__ __forceinline__ C near_value(int i, int lf, int ls, const int2* __restrict__ leaf_items,
+                                        const C* __restrict__ nearv, const C* __restrict__ part, int TS) {
+    const int2 li = leaf_items[lf];
+    if (li.y == 1) return nearv[i];
+    C s;
+    s.x = 0;
+    s.y = 0;
+    for (int q = 0; q < li.y; ++q) {
+        const C v = part[(size_t)(li.x + q) * TS + (i - ls)];
+        s.x += v.x;
+        s.y += v.y;
+    }
+    return s;
+}
+
 // One thread per sorted point: far field by Horner from the leaf's local
 // expansion, plus the near field, written to the caller's order.
 template <int P>
 __global__ void __launch_bounds__(256) k_l2p32(int n, const int32_t* __restrict__ leaf_of,
-                                               const float4* __restrict__ chl, const float* __restrict__ rho32,
-                                               const float4* __restrict__ pos4, const float2* __restrict__ L32,
-                                               const float2* __restrict__ nearv, const int32_t* __restrict__ perm,
-                                               float2* __restrict__ out, int PS) {
+                                               const int32_t* __restrict__ bstart, const float4* __restrict__ chl,
+                                               const float* __restrict__ rho32, const float4* __restrict__ pos4,
+                                               const float2* __restrict__ L32, const int2* __restrict__ leaf_items,
+                                               const float2* __restrict__ nearv, const float2* __restrict__ part,
+                                               int TS, const int32_t* __restrict__ perm, float2* __restrict__ out,
+                                               int PS) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int lf = leaf_of[i];
@@ -404,16 +429,18 @@ __global__ void __launch_bounds__(256) k_l2p32(int n, const int32_t* __restrict_
     float2 v = Lb[P - 1];
 #pragma unroll
     for (int l = P - 2; l >= 0; --l) v = cfma(v, w, Lb[l]);
-    const float2 nv = nearv[i];
+    const float2 nv = near_value(i, lf, bstart[lf], leaf_items, nearv, part, TS);
     out[perm[i]] = make_float2(v.x + nv.x, v.y + nv.y);
 }
 
 template <int P>
 __global__ void __launch_bounds__(256) k_l2p64(int n, const int32_t* __restrict__ leaf_of,
-                                               const double2* __restrict__ center, const double* __restrict__ rho,
-                                               const double2* __restrict__ pts, const double2* __restrict__ L64,
-                                               const double2* __restrict__ nearv, const int32_t* __restrict__ perm,
-                                               double2* __restrict__ out, int PS) {
+                                               const int32_t* __restrict__ bstart, const double2* __restrict__ center,
+                                               const double* __restrict__ rho, const double2* __restrict__ pts,
+                                               const double2* __restrict__ L64, const int2* __restrict__ leaf_items,
+                                               const double2* __restrict__ nearv, const double2* __restrict__ part,
+                                               int TS, const int32_t* __restrict__ perm, double2* __restrict__ out,
+                                               int PS) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int lf = leaf_of[i];
@@ -426,7 +453,7 @@ __global__ void __launch_bounds__(256) k_l2p64(int n, const int32_t* __restrict_
     double2 v = Lb[P - 1];
 #pragma unroll
     for (int l = P - 2; l >= 0; --l) v = cfma(v, w, Lb[l]);
-    const double2 nv = nearv[i];
+    const double2 nv = near_value(i, lf, bstart[lf], leaf_items, nearv, part, TS);
     out[perm[i]] = make_double2(v.x + nv.x, v.y + nv.y);
 }
 
@@ -454,21 +481,24 @@ __device__ __forceinline__ void p2p_interact32(const float4 t, const float4 s, c
 }
 
 template <int TPL>
-__global__ void __launch_bounds__(kP2PWarps * 32) k_p2p32(const int32_t* __restrict__ leaves, int nleaf,
+__global__ void __launch_bounds__(kP2PWarps * 32) k_p2p32(const int4* __restrict__ items,
+                                                          const unsigned long long* __restrict__ nitems,
                                                           const int32_t* __restrict__ bstart,
                                                           const int32_t* __restrict__ bcount,
-                                                          const int32_t* __restrict__ nstrong,
-                                                          const int32_t* __restrict__ strong, int scap,
+                                                          const int32_t* __restrict__ soff,
+                                                          const int32_t* __restrict__ sidx,
                                                           const float4* __restrict__ pos4,
-                                                          const float2* __restrict__ gam, float2* __restrict__ nearv) {
+                                                          const float2* __restrict__ gam, float2* __restrict__ nearv,
+                                                          float2* __restrict__ part, int TS) {
     __shared__ float4 sp[kP2PWarps][kP2PChunk32];
     __shared__ float2 sg[kP2PWarps][kP2PChunk32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int lq = blockIdx.x * kP2PWarps + warp; lq < nleaf; lq += gridDim.x * kP2PWarps) {
-        const int b = leaves[lq];
+    const int nit = (int)*nitems;
+    for (int it = blockIdx.x * kP2PWarps + warp; it < nit; it += gridDim.x * kP2PWarps) {
+        const int4 item = items[it];
+        const int b = item.x;
         const int ts = bstart[b], tn = bcount[b];
-        const int ns = nstrong[b];
-        const int32_t* sl = strong + (size_t)b * scap;
+        const int32_t* sl = sidx + soff[b];
         for (int t0 = 0; t0 < tn; t0 += 32 * TPL) {
             const int nt = min(tn - t0, 32 * TPL);
             const int LT = (nt + TPL - 1) / TPL;
@@ -483,11 +513,11 @@ __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p32(const int32_t* __restr
                 xt[u] = (idx < tn) ? pos4[ts + idx] : make_float4(0.f, 0.f, 0.f, 0.f);
                 acc[u] = make_float2(0.f, 0.f);
             }
-            int j = 0, off = 0;
-            while (j < ns) {
+            int j = item.y, off = 0;
+            while (j < item.z) {
                 __syncwarp();
                 int cnt = 0;
-                while (j < ns && cnt < kP2PChunk32) {
+                while (j < item.z && cnt < kP2PChunk32) {
                     const int h = sl[j];
                     const int hs = bstart[h], hn = bcount[h];
                     const int take = min(hn - off, kP2PChunk32 - cnt);
@@ -523,7 +553,10 @@ __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p32(const int32_t* __restr
                     tot.y += __shfl_sync(0xffffffffu, acc[u].y, src & 31);
                 }
                 const int idx = t0 + tg + u * LT;
-                if (ss == 0 && idx < tn) nearv[ts + idx] = tot;
+                if (ss == 0 && idx < tn) {
+                    if (item.w < 0) nearv[ts + idx] = tot;
+                    else part[(size_t)it * TS + idx] = tot;
+                }
             }
         }
     }
@@ -540,22 +573,25 @@ __device__ __forceinline__ void p2p_interact64(const double2 t, const double2 s,
 }
 
 template <int TPL>
-__global__ void __launch_bounds__(kP2PWarps * 32) k_p2p64(const int32_t* __restrict__ leaves, int nleaf,
+__global__ void __launch_bounds__(kP2PWarps * 32) k_p2p64(const int4* __restrict__ items,
+                                                          const unsigned long long* __restrict__ nitems,
                                                           const int32_t* __restrict__ bstart,
                                                           const int32_t* __restrict__ bcount,
-                                                          const int32_t* __restrict__ nstrong,
-                                                          const int32_t* __restrict__ strong, int scap,
+                                                          const int32_t* __restrict__ soff,
+                                                          const int32_t* __restrict__ sidx,
                                                           const double2* __restrict__ pts,
                                                           const double2* __restrict__ gam,
-                                                          double2* __restrict__ nearv) {
+                                                          double2* __restrict__ nearv, double2* __restrict__ part,
+                                                          int TS) {
     __shared__ double2 sp[kP2PWarps][kP2PChunk64];
     __shared__ double2 sg[kP2PWarps][kP2PChunk64];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int lq = blockIdx.x * kP2PWarps + warp; lq < nleaf; lq += gridDim.x * kP2PWarps) {
-        const int b = leaves[lq];
+    const int nit = (int)*nitems;
+    for (int it = blockIdx.x * kP2PWarps + warp; it < nit; it += gridDim.x * kP2PWarps) {
+        const int4 item = items[it];
+        const int b = item.x;
         const int ts = bstart[b], tn = bcount[b];
-        const int ns = nstrong[b];
-        const int32_t* sl = strong + (size_t)b * scap;
+        const int32_t* sl = sidx + soff[b];
         for (int t0 = 0; t0 < tn; t0 += 32 * TPL) {
             const int nt = min(tn - t0, 32 * TPL);
             const int LT = (nt + TPL - 1) / TPL;
@@ -569,11 +605,11 @@ __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p64(const int32_t* __restr
                 xt[u] = (idx < tn) ? pts[ts + idx] : make_double2(0.0, 0.0);
                 acc[u] = make_double2(0.0, 0.0);
             }
-            int j = 0, off = 0;
-            while (j < ns) {
+            int j = item.y, off = 0;
+            while (j < item.z) {
                 __syncwarp();
                 int cnt = 0;
-                while (j < ns && cnt < kP2PChunk64) {
+                while (j < item.z && cnt < kP2PChunk64) {
                     const int h = sl[j];
                     const int hs = bstart[h], hn = bcount[h];
                     const int take = min(hn - off, kP2PChunk64 - cnt);
@@ -607,7 +643,10 @@ __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p64(const int32_t* __restr
                     tot.y += __shfl_sync(0xffffffffu, acc[u].y, src & 31);
                 }
                 const int idx = t0 + tg + u * LT;
-                if (ss == 0 && idx < tn) nearv[ts + idx] = tot;
+                if (ss == 0 && idx < tn) {
+                    if (item.w < 0) nearv[ts + idx] = tot;
+                    else part[(size_t)it * TS + idx] = tot;
+                }
             }
         }
     }
@@ -615,97 +654,122 @@ __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p64(const int32_t* __restr
 
 // ============================================================ dispatch
 
+Bufs bufs(Tree& t, int set) {
+    const size_t nb = (size_t)t.nbox, n = (size_t)t.n, PS = (size_t)t.PS;
+    const size_t cs = t.path == FMM_PATH_FP32 ? sizeof(float2) : sizeof(double2);
+    Bufs b;
+    b.gam = static_cast<char*>(t.d_gam) + set * n * cs;
+    b.near = t.d_near;
+    b.M64 = t.d_M64 + set * nb * PS;
+    b.M32 = t.d_M32 + set * nb * PS;
+    b.L64 = t.d_L64 + set * nb * PS;
+    b.L32 = t.d_L32 + set * nb * PS;
+    b.Lm2l = static_cast<char*>(t.d_Lm2l) + set * nb * PS * cs;
+    b.p2p_part = t.d_p2p_part;
+    b.m2l_part = static_cast<char*>(t.d_m2l_part) + set * (size_t)t.part_m2l_cap * PS * cs;
+    return b;
+}
+
+static const unsigned long long* item_count(const Tree& t, int which) {
+    return reinterpret_cast<const unsigned long long*>(t.d_status) + 1 + which;  // 2 = P2P, 3 = M2L
+}
+
 template <int P>
-static void launch_far_fp32(Tree& t, cudaStream_t s) {
-    const float2* gam = static_cast<const float2*>(t.d_gam);
+static void launch_far_fp32(Tree& t, const Bufs& B, cudaStream_t s) {
+    const float2* gam = static_cast<const float2*>(B.gam);
     k_p2m32<P><<<nblk(t.nleaf, 128), 128, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, t.d_bstart, t.d_bcount, t.d_chl,
-                                                  t.d_rho32, t.d_pos4, gam, t.d_M32, t.p, t.PS);
+                                                  t.d_rho32, t.d_pos4, gam, B.M32, t.p, t.PS);
     for (int l = t.Lmax - 2; l >= 0; --l) {
         const LevelList& L = t.level_parents[l];
         if (!L.count) continue;
-        k_m2m<P><<<nblk(L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_child0, t.d_rho, t.d_center, t.d_M32,
-                                                    t.d_M64, t.d_M32, 1, t.p, t.PS);
+        k_m2m<P><<<nblk(L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_child0, t.d_rho, t.d_center, B.M32,
+                                                    B.M64, B.M32, 1, t.p, t.PS);
     }
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[2], s);
-    k_m2l32<P><<<nblk(t.nbox, 128), 128, 0, s>>>((int)t.nbox, t.d_nweak, t.d_weak, t.wcap, t.d_chl, t.d_rho32,
-                                                 t.d_M32, static_cast<float2*>(t.d_Lm2l), t.d_parent, t.d_child0,
-                                                 t.d_L64, t.d_L32, t.PS);
+    k_m2l32<P><<<nblk(t.m2l_cap, 128), 128, 0, s>>>(t.d_m2l_items, item_count(t, 3), t.d_woff, t.d_widx, t.d_chl,
+                                                    t.d_rho32, B.M32, static_cast<float2*>(B.Lm2l),
+                                                    static_cast<float2*>(B.m2l_part), t.PS);
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[3], s);
     for (int l = 0; l + 1 < t.Lmax; ++l) {
         const LevelList& L = t.level_boxes[l + 1];
-        k_l2l<P, float2><<<nblk(L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho,
-                                                            t.d_center, static_cast<const float2*>(t.d_Lm2l),
-                                                            t.d_L64, t.d_L32, t.p, t.PS);
+        k_l2l<P, float2><<<nblk(L.count, 128), 128, 0, s>>>(
+            L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho, t.d_center, t.d_box_m2l,
+            static_cast<const float2*>(B.Lm2l), static_cast<const float2*>(B.m2l_part), B.L64, B.L32, t.p, t.PS);
     }
 }
 
 template <int P>
-static void launch_far_fp64(Tree& t, cudaStream_t s) {
-    const double2* gam = static_cast<const double2*>(t.d_gam);
+static void launch_far_fp64(Tree& t, const Bufs& B, cudaStream_t s) {
+    const double2* gam = static_cast<const double2*>(B.gam);
     k_p2m64<P><<<nblk(t.nleaf, 128), 128, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, t.d_bstart, t.d_bcount, t.d_center,
-                                                  t.d_rho, t.d_pts, gam, t.d_M64, t.p, t.PS);
+                                                  t.d_rho, t.d_pts, gam, B.M64, t.p, t.PS);
     for (int l = t.Lmax - 2; l >= 0; --l) {
         const LevelList& L = t.level_parents[l];
         if (!L.count) continue;
         k_m2m<P><<<nblk(L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_child0, t.d_rho, t.d_center, nullptr,
-                                                    t.d_M64, nullptr, 0, t.p, t.PS);
+                                                    B.M64, nullptr, 0, t.p, t.PS);
     }
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[2], s);
-    k_m2l64<P><<<nblk(t.nbox, 128), 128, 0, s>>>((int)t.nbox, t.d_nweak, t.d_weak, t.wcap, t.d_center, t.d_rho,
-                                                 t.d_M64, static_cast<double2*>(t.d_Lm2l), t.d_parent, t.d_L64,
-                                                 t.PS);
+    k_m2l64<P><<<nblk(t.m2l_cap, 128), 128, 0, s>>>(t.d_m2l_items, item_count(t, 3), t.d_woff, t.d_widx,
+                                                    t.d_center, t.d_rho, B.M64, static_cast<double2*>(B.Lm2l),
+                                                    static_cast<double2*>(B.m2l_part), t.PS);
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[3], s);
     for (int l = 0; l + 1 < t.Lmax; ++l) {
         const LevelList& L = t.level_boxes[l + 1];
-        k_l2l<P, double2><<<nblk(L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho,
-                                                             t.d_center, static_cast<const double2*>(t.d_Lm2l),
-                                                             t.d_L64, nullptr, t.p, t.PS);
+        k_l2l<P, double2><<<nblk(L.count, 128), 128, 0, s>>>(
+            L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho, t.d_center, t.d_box_m2l,
+            static_cast<const double2*>(B.Lm2l), static_cast<const double2*>(B.m2l_part), B.L64, nullptr, t.p,
+            t.PS);
     }
 }
 
 template <int P>
-static void launch_l2p(Tree& t, void* d_phi, cudaStream_t s) {
+static void launch_l2p(Tree& t, const Bufs& B, void* d_phi, cudaStream_t s) {
     const int n = (int)t.n;
     if (t.path == FMM_PATH_FP32) {
-        k_l2p32<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_chl, t.d_rho32, t.d_pos4, t.d_L32,
-                                                static_cast<const float2*>(t.d_near), t.d_perm,
+        k_l2p32<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_bstart, t.d_chl, t.d_rho32, t.d_pos4, B.L32,
+                                                t.d_leaf_items, static_cast<const float2*>(B.near),
+                                                static_cast<const float2*>(B.p2p_part), t.max_leaf, t.d_perm,
                                                 static_cast<float2*>(d_phi), t.PS);
     } else {
-        k_l2p64<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_center, t.d_rho, t.d_pts, t.d_L64,
-                                                static_cast<const double2*>(t.d_near), t.d_perm,
+        k_l2p64<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_bstart, t.d_center, t.d_rho, t.d_pts, B.L64,
+                                                t.d_leaf_items, static_cast<const double2*>(B.near),
+                                                static_cast<const double2*>(B.p2p_part), t.max_leaf, t.d_perm,
                                                 static_cast<double2*>(d_phi), t.PS);
     }
 }
 
-static void launch_p2p(Tree& t, cudaStream_t s) {
-    const int nl = (int)t.nleaf;
-    const int grid = nblk(nl, kP2PWarps);
-    const double avg = (double)t.n / std::max<int64_t>(t.nleaf, 1);
+static void launch_p2p(Tree& t, const Bufs& B, cudaStream_t s) {
+    const int grid = nblk(t.p2p_cap, kP2PWarps);
+    const bool wide = (double)t.n / std::max<int64_t>(t.nleaf, 1) >= 8.0;
+    const unsigned long long* cnt = item_count(t, 2);
     if (t.path == FMM_PATH_FP32) {
-        const float2* gam = static_cast<const float2*>(t.d_gam);
-        float2* nv = static_cast<float2*>(t.d_near);
-        if (avg >= 8.0)
-            k_p2p32<4><<<grid, kP2PWarps * 32, 0, s>>>(t.leaves.d_ids, nl, t.d_bstart, t.d_bcount, t.d_nstrong,
-                                                       t.d_strong, t.scap, t.d_pos4, gam, nv);
+        const float2* gam = static_cast<const float2*>(B.gam);
+        float2* nv = static_cast<float2*>(B.near);
+        float2* pt = static_cast<float2*>(B.p2p_part);
+        if (wide)
+            k_p2p32<4><<<grid, kP2PWarps * 32, 0, s>>>(t.d_p2p_items, cnt, t.d_bstart, t.d_bcount, t.d_soff,
+                                                       t.d_sidx, t.d_pos4, gam, nv, pt, t.max_leaf);
         else
-            k_p2p32<1><<<grid, kP2PWarps * 32, 0, s>>>(t.leaves.d_ids, nl, t.d_bstart, t.d_bcount, t.d_nstrong,
-                                                       t.d_strong, t.scap, t.d_pos4, gam, nv);
+            k_p2p32<1><<<grid, kP2PWarps * 32, 0, s>>>(t.d_p2p_items, cnt, t.d_bstart, t.d_bcount, t.d_soff,
+                                                       t.d_sidx, t.d_pos4, gam, nv, pt, t.max_leaf);
     } else {
-        const double2* gam = static_cast<const double2*>(t.d_gam);
-        double2* nv = static_cast<double2*>(t.d_near);
-        if (avg >= 8.0)
-            k_p2p64<4><<<grid, kP2PWarps * 32, 0, s>>>(t.leaves.d_ids, nl, t.d_bstart, t.d_bcount, t.d_nstrong,
-                                                       t.d_strong, t.scap, t.d_pts, gam, nv);
+        const double2* gam = static_cast<const double2*>(B.gam);
+        double2* nv = static_cast<double2*>(B.near);
+        double2* pt = static_cast<double2*>(B.p2p_part);
+        if (wide)
+            k_p2p64<4><<<grid, kP2PWarps * 32, 0, s>>>(t.d_p2p_items, cnt, t.d_bstart, t.d_bcount, t.d_soff,
+                                                       t.d_sidx, t.d_pts, gam, nv, pt, t.max_leaf);
         else
-            k_p2p64<1><<<grid, kP2PWarps * 32, 0, s>>>(t.leaves.d_ids, nl, t.d_bstart, t.d_bcount, t.d_nstrong,
-                                                       t.d_strong, t.scap, t.d_pts, gam, nv);
+            k_p2p64<1><<<grid, kP2PWarps * 32, 0, s>>>(t.d_p2p_items, cnt, t.d_bstart, t.d_bcount, t.d_soff,
+                                                       t.d_sidx, t.d_pts, gam, nv, pt, t.max_leaf);
     }
 }
 
 template <int P>
-static void launch_far(Tree& t, cudaStream_t s) {
-    if (t.path == FMM_PATH_FP32) launch_far_fp32<P>(t, s);
-    else launch_far_fp64<P>(t, s);
+static void launch_far(Tree& t, const Bufs& B, cudaStream_t s) {
+    if (t.path == FMM_PATH_FP32) launch_far_fp32<P>(t, B, s);
+    else launch_far_fp64<P>(t, B, s);
 }
 
 // Compiled expansion orders; a request for p runs the smallest compiled
@@ -720,19 +784,19 @@ int compiled_order(int p) {
     return -1;
 }
 
-static void dispatch_far(Tree& t, cudaStream_t s) {
+void dispatch_far(Tree& t, const Bufs& B, cudaStream_t s) {
     switch (t.P) {
 #define FMM_CASE(Q) \
-    case Q: launch_far<Q>(t, s); break;
+    case Q: launch_far<Q>(t, B, s); break;
         FMM_FOR_ORDERS(FMM_CASE)
 #undef FMM_CASE
     }
 }
 
-static void dispatch_l2p(Tree& t, void* d_phi, cudaStream_t s) {
+static void dispatch_l2p(Tree& t, const Bufs& B, void* d_phi, cudaStream_t s) {
     switch (t.P) {
 #define FMM_CASE(Q) \
-    case Q: launch_l2p<Q>(t, d_phi, s); break;
+    case Q: launch_l2p<Q>(t, B, d_phi, s); break;
         FMM_FOR_ORDERS(FMM_CASE)
 #undef FMM_CASE
     }
@@ -754,20 +818,33 @@ static fmm_status ralloc(T** p, size_t bytes) {
     return FMM_OK;
 }
 
+// Evaluation workspace: `sets` strength sets (1 forward, 2 adjoint).  Sizes
+// follow the tree shape, the expansion order and the work-item capacities;
+// the function is a no-op when nothing grew.
 fmm_status alloc_eval(Tree& t, int sets) {
     if (t.eval_nbox == (size_t)t.nbox && t.eval_n == (size_t)t.n && t.eval_PS == t.PS && t.eval_path == t.path &&
-        t.eval_sets >= sets)
+        t.eval_sets >= sets && t.part_p2p_cap >= t.p2p_cap && t.part_m2l_cap >= t.m2l_cap &&
+        t.eval_ts >= t.max_leaf)
         return FMM_OK;
+    sets = std::max(sets, t.eval_sets);
     const size_t nb = (size_t)t.nbox, n = (size_t)t.n, PS = (size_t)t.PS;
     const size_t cs = t.path == FMM_PATH_FP32 ? sizeof(float2) : sizeof(double2);
     fmm_status st;
     if ((st = ralloc(&t.d_gam, n * cs * sets))) return st;
-    if ((st = ralloc(&t.d_near, n * sizeof(double2) * 3 * sets))) return st;
+    if ((st = ralloc(&t.d_near, n * sizeof(double2) * 3))) return st;
     if ((st = ralloc(&t.d_M64, nb * PS * sizeof(double2) * sets))) return st;
     if ((st = ralloc(&t.d_L64, nb * PS * sizeof(double2) * sets))) return st;
     if ((st = ralloc(&t.d_Lm2l, nb * PS * cs * sets))) return st;
     if ((st = ralloc(&t.d_M32, nb * PS * sizeof(float2) * sets))) return st;
     if ((st = ralloc(&t.d_L32, nb * PS * sizeof(float2) * sets))) return st;
+    if ((st = ralloc(&t.d_p2p_part, (size_t)t.p2p_cap * t.max_leaf * sizeof(double2) * 3))) return st;
+    if ((st = ralloc(&t.d_m2l_part, (size_t)t.m2l_cap * PS * cs * sets))) return st;
+    // root locals are never written by the passes: they stay zero
+    FMM_CUDA(cudaMemset(t.d_L64, 0, nb * PS * sizeof(double2) * sets));
+    FMM_CUDA(cudaMemset(t.d_L32, 0, nb * PS * sizeof(float2) * sets));
+    t.part_p2p_cap = t.p2p_cap;
+    t.part_m2l_cap = t.m2l_cap;
+    t.eval_ts = t.max_leaf;
     t.eval_nbox = nb;
     t.eval_n = n;
     t.eval_PS = t.PS;
@@ -785,29 +862,30 @@ fmm_status run_eval(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s)
     const bool serial = t.flags & FMM_FLAG_SERIAL;
     if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[0], s));
     const double2* gin = reinterpret_cast<const double2*>(d_gamma);
+    const Bufs B = bufs(t, 0);
     if (t.path == FMM_PATH_FP32)
-        k_gather32<<<nblk(n, 256), 256, 0, s>>>(gin, t.d_perm, n, static_cast<float2*>(t.d_gam));
+        k_gather32<<<nblk(n, 256), 256, 0, s>>>(gin, t.d_perm, n, static_cast<float2*>(B.gam));
     else
-        k_gather64<<<nblk(n, 256), 256, 0, s>>>(gin, t.d_perm, n, static_cast<double2*>(t.d_gam));
+        k_gather64<<<nblk(n, 256), 256, 0, s>>>(gin, t.d_perm, n, static_cast<double2*>(B.gam));
     if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[1], s));
     if (!serial) {
         FMM_CUDA(cudaEventRecord(t.ev_fork, s));
         FMM_CUDA(cudaStreamWaitEvent(t.s_aux, t.ev_fork, 0));
         if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[5], t.s_aux));
-        launch_p2p(t, t.s_aux);
+        launch_p2p(t, B, t.s_aux);
         if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[6], t.s_aux));
         FMM_CUDA(cudaEventRecord(t.ev_join, t.s_aux));
     }
-    dispatch_far(t, s);
+    dispatch_far(t, B, s);
     if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[4], s));
     if (serial) {
         if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[5], s));
-        launch_p2p(t, s);
+        launch_p2p(t, B, s);
         if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[6], s));
     } else {
         FMM_CUDA(cudaStreamWaitEvent(s, t.ev_join, 0));
     }
-    dispatch_l2p(t, d_phi, s);
+    dispatch_l2p(t, B, d_phi, s);
     if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[7], s));
     FMM_CUDA(cudaGetLastError());
     t.timing_valid = timing;

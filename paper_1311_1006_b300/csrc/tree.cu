@@ -97,6 +97,8 @@ fmm_status build_shape(Tree& t) {
         }
     }
     t.nleaf = (int64_t)t.h_leaves.size();
+    t.max_leaf = 1;
+    for (int32_t lf : t.h_leaves) t.max_leaf = std::max(t.max_leaf, (int)t.h_bcount[lf]);
     fmm_status st;
     if ((st = upload(&t.d_bstart, t.h_bstart))) return st;
     if ((st = upload(&t.d_bcount, t.h_bcount))) return st;
@@ -496,7 +498,7 @@ __global__ void k_geom(const int32_t* __restrict__ ids, int cnt, const int32_t* 
                        const int32_t* __restrict__ Y, const double2* __restrict__ xy,
                        const int32_t* __restrict__ bstart, const int32_t* __restrict__ bcount,
                        const int32_t* __restrict__ inst, const int64_t* __restrict__ inst_box_off, double2* center,
-                       double* radius, double* rho, float4* chl, float* rho32, int is_root_level) {
+                       double* radius, double* rho, float4* chl, float* rho32, float* rad32, int is_root_level) {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= cnt) return;
     const int b = ids[q];
@@ -509,15 +511,23 @@ __global__ void k_geom(const int32_t* __restrict__ ids, int cnt, const int32_t* 
     const double r = __dmul_rn(0.5, __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy))));
     center[b] = make_double2(cx, cy);
     radius[b] = r;
-    const float r32 = r >= 1e-30 ? __double2float_rn(r) : 0.0f;
-    rho32[b] = r32;
-    rho[b] = (double)r32;
-    double ox = cx, oy = cy;
+    rad32[b] = __double2float_rn(r);
+    // Scale radius of the expansions: the bbox radius, floored at 2^-24 of the
+    // instance's root radius so that a box of coincident points still keeps a
+    // usable local-expansion derivative; rounded to FP32 so both precisions
+    // scale by the same number.
+    double ox = cx, oy = cy, rfloor = 0.0;
     if (!is_root_level) {
-        const double2 o = center[inst_box_off[inst[b]]];
+        const int root = (int)inst_box_off[inst[b]];
+        const double2 o = center[root];
         ox = o.x;
         oy = o.y;
+        rfloor = ldexp(radius[root], -24);
     }
+    const double rs = r > rfloor ? r : rfloor;
+    const float r32 = rs >= 1e-30 ? __double2float_rn(rs) : 0.0f;
+    rho32[b] = r32;
+    rho[b] = (double)r32;
     const double ex = __dsub_rn(cx, ox), ey = __dsub_rn(cy, oy);
     const float hx = __double2float_rn(ex), hy = __double2float_rn(ey);
     chl[b] = make_float4(hx, hy, __double2float_rn(__dsub_rn(ex, (double)hx)),
@@ -548,17 +558,20 @@ __global__ void k_finalize(const int32_t* __restrict__ Y, int n, const double2* 
 
 // ================================================================== lists
 
-__global__ void k_lists_root(const int64_t* __restrict__ inst_box_off, int ninst, int32_t* nstrong, int32_t* strong,
-                             int32_t* nweak, int scap) {
+__global__ void k_lists_root(const int64_t* __restrict__ inst_box_off, int ninst, int32_t* soff, int32_t* ns,
+                             int32_t* sidx, int32_t* woff, int32_t* nw, unsigned long long* ctr) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b == 0) ctr[0] = (unsigned long long)ninst;
     if (b >= ninst) return;
-    int r = (int)inst_box_off[b];
-    nstrong[r] = 1;
-    strong[(size_t)r * scap] = r;
-    nweak[r] = 0;
+    const int r = (int)inst_box_off[b];
+    soff[r] = b;  // the first ninst strong entries are the roots themselves
+    ns[r] = 1;
+    sidx[b] = r;
+    woff[r] = 0;
+    nw[r] = 0;
 }
 
-// eq (2.3): R + theta*r <= theta*d, with d > 0 required.
+// eq (2.3) in FP64: R + theta*r <= theta*d, with d > 0 required.
 __device__ __forceinline__ bool well_separated(double2 ca, double ra, double2 cb, double rb, double theta) {
     const double dx = __dsub_rn(ca.x, cb.x), dy = __dsub_rn(ca.y, cb.y);
     const double d = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
@@ -567,69 +580,156 @@ __device__ __forceinline__ bool well_separated(double2 ca, double ra, double2 cb
     return d > 0.0 && __dadd_rn(R, __dmul_rn(theta, r)) <= __dmul_rn(theta, d);
 }
 
-// Coupling of one level (Sec. 2.1): children of the parent's strongly coupled
-// boxes are strong unless well separated (then weak); a box is always strong
-// with itself.
-__global__ void k_lists(const int32_t* __restrict__ ids, int cnt, const int32_t* __restrict__ parent,
-                        const int32_t* __restrict__ child0, const double2* __restrict__ center,
-                        const double* __restrict__ radius, double theta, int32_t* nstrong, int32_t* strong,
-                        int32_t* nweak, int32_t* weak, int scap, int wcap, unsigned* status) {
-    int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= cnt) return;
-    const int b = ids[q];
-    const int P = parent[b];
-    const double2 cb = center[b];
-    const double rb = radius[b];
-    int ns = 0, nw = 0;
-    const int np = nstrong[P];
-    bool ovs = false, ovw = false;
-    for (int j = 0; j < np; ++j) {
-        const int Q = strong[(size_t)P * scap + j];
-        const int c0 = child0[Q];
-        for (int c = 0; c < 4; ++c) {
-            const int h = c0 + c;
-            const bool sep = (h != b) && well_separated(cb, rb, center[h], radius[h], theta);
-            if (sep) {
-                if (nw < wcap) weak[(size_t)b * wcap + nw] = h;
-                else ovw = true;
-                ++nw;
-            } else {
-                if (ns < scap) strong[(size_t)b * scap + ns] = h;
-                else ovs = true;
-                ++ns;
-            }
-        }
-    }
-    nstrong[b] = ns < scap ? ns : scap;
-    nweak[b] = nw < wcap ? nw : wcap;
-    if (ovs) atomicOr(status, ST_STRONG_OVERFLOW);
-    if (ovw) atomicOr(status, ST_WEAK_OVERFLOW);
+// Same decision, evaluated in FP32 first; only pairs within a relative 1e-5
+// of the boundary (far above the FP32 evaluation error) repeat the exact FP64
+// test, so the result equals the FP64 test bit for bit.
+__device__ __forceinline__ bool well_separated_fast(int a, int b, const float4* __restrict__ chl,
+                                                    const float* __restrict__ rad32,
+                                                    const double2* __restrict__ center,
+                                                    const double* __restrict__ radius, float theta32, double theta) {
+    const float4 ca = chl[a], cb = chl[b];
+    const float dx = (ca.x - cb.x) + (ca.z - cb.z);
+    const float dy = (ca.y - cb.y) + (ca.w - cb.w);
+    const float d = sqrtf(fmaf(dx, dx, dy * dy));
+    const float ra = rad32[a], rb = rad32[b];
+    const float lhs = fmaf(theta32, fminf(ra, rb), fmaxf(ra, rb));
+    const float rhs = theta32 * d;
+    const float tol = 1e-5f * (lhs + rhs) + 1e-12f * (fabsf(ca.x) + fabsf(ca.y) + fabsf(cb.x) + fabsf(cb.y));
+    if (lhs + tol < rhs) return true;
+    if (lhs > rhs + tol) return false;
+    return well_separated(center[a], radius[a], center[b], radius[b], theta);
 }
 
-// Totals for fmm_get_tree_info: weak pairs, leaf strong pairs, P2P point pairs.
-__global__ void k_count(const int32_t* __restrict__ leaf_ids, int nleaf, int nbox, const int32_t* __restrict__ nstrong,
-                        const int32_t* __restrict__ strong, const int32_t* __restrict__ nweak,
-                        const int32_t* __restrict__ bcount, int scap, unsigned long long* out) {
+// Coupling of one level (Sec. 2.1), one warp per box: the candidates are the
+// children of the parent's strongly coupled boxes; a candidate is weak when
+// well separated, else strong (a box is always strong with itself).  The warp
+// counts, reserves its CSR ranges with one atomic each, then writes the
+// entries in candidate order.  When a reservation passes the capacity the
+// counts are still recorded (the host learns the size it needs) but nothing
+// is written, and every later level is skipped.
+__global__ void __launch_bounds__(256) k_lists_level(
+    const int32_t* __restrict__ ids, int cnt, const int32_t* __restrict__ parent, const int32_t* __restrict__ child0,
+    int32_t* soff, int32_t* ns, int32_t* sidx, int32_t* woff, int32_t* nw, int32_t* widx,
+    const float4* __restrict__ chl, const float* __restrict__ rad32, const double2* __restrict__ center,
+    const double* __restrict__ radius, double theta, unsigned long long* ctr, long long scap, long long wcap,
+    unsigned* status) {
+    const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= cnt) return;
+    if (*((volatile unsigned*)status) & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW)) return;
+    const int b = ids[w];
+    const int P = parent[b];
+    const int m = 4 * ns[P];
+    const int32_t* ps = sidx + soff[P];
+    const float th32 = (float)theta;
+    int cs = 0, cw = 0;
+    for (int c0 = 0; c0 < m; c0 += 32) {
+        const int j = c0 + lane;
+        bool v = j < m, sep = false;
+        if (v) {
+            const int h = child0[ps[j >> 2]] + (j & 3);
+            sep = (h != b) && well_separated_fast(b, h, chl, rad32, center, radius, th32, theta);
+        }
+        cs += __popc(__ballot_sync(0xffffffffu, v && !sep));
+        cw += __popc(__ballot_sync(0xffffffffu, v && sep));
+    }
+    unsigned long long os = 0, ow = 0;
+    if (lane == 0) {
+        os = atomicAdd(ctr + 0, (unsigned long long)cs);
+        ow = atomicAdd(ctr + 1, (unsigned long long)cw);
+    }
+    os = __shfl_sync(0xffffffffu, os, 0);
+    ow = __shfl_sync(0xffffffffu, ow, 0);
+    const bool fs = (long long)(os + cs) <= scap, fw = (long long)(ow + cw) <= wcap;
+    if (lane == 0) {
+        soff[b] = (int32_t)os;
+        ns[b] = cs;
+        woff[b] = (int32_t)ow;
+        nw[b] = cw;
+        if (!fs) atomicOr(status, ST_STRONG_OVERFLOW);
+        if (!fw) atomicOr(status, ST_WEAK_OVERFLOW);
+    }
+    if (!fs || !fw) return;
+    const unsigned lt = lanemask_lt();
+    int rs = 0, rw = 0;
+    for (int c0 = 0; c0 < m; c0 += 32) {
+        const int j = c0 + lane;
+        bool v = j < m, sep = false;
+        int h = 0;
+        if (v) {
+            h = child0[ps[j >> 2]] + (j & 3);
+            sep = (h != b) && well_separated_fast(b, h, chl, rad32, center, radius, th32, theta);
+        }
+        const unsigned bs = __ballot_sync(0xffffffffu, v && !sep);
+        const unsigned bw = __ballot_sync(0xffffffffu, v && sep);
+        if (v && !sep) sidx[os + rs + __popc(bs & lt)] = h;
+        if (v && sep) widx[ow + rw + __popc(bw & lt)] = h;
+        rs += __popc(bs);
+        rw += __popc(bw);
+    }
+}
+
+// Work items that bound the work of one warp / thread whatever the list
+// lengths: P2P items = (leaf, slice of its strong list) with about
+// kP2PItemSources source points, M2L items = (box, at most kM2LItemPairs weak
+// entries).  A box whose list is split keeps its items contiguous; their
+// partial sums are added in item order later (deterministic).
+// int4 item = (box, list begin, list end, first item of the box or -1 when
+// the box has a single item).
+__global__ void k_items(int nbox, const int32_t* __restrict__ child0, const int32_t* __restrict__ bcount,
+                        const int32_t* __restrict__ ns, const int32_t* __restrict__ nw, unsigned long long* ctr,
+                        int4* p2p_items, int2* leaf_items, long long p2p_cap, int4* m2l_items, int2* box_m2l,
+                        long long m2l_cap, unsigned* status) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    if (*((volatile unsigned*)status) & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW)) return;
+    if (child0[b] < 0) {
+        const int n = ns[b];
+        const int C = max(1, kP2PItemSources / max(bcount[b], 1));
+        const int k = (n + C - 1) / C;
+        const unsigned long long base = atomicAdd(ctr + 2, (unsigned long long)k);
+        leaf_items[b] = make_int2((int)base, k);
+        if ((long long)(base + k) > p2p_cap) {
+            atomicOr(status, ST_ITEM_OVERFLOW);
+        } else {
+            for (int c = 0; c < k; ++c)
+                p2p_items[base + c] = make_int4(b, c * C, min(n, (c + 1) * C), k > 1 ? (int)base : -1);
+        }
+    }
+    const int n = nw[b];
+    const int k = (n + kM2LItemPairs - 1) / kM2LItemPairs;
+    const unsigned long long base = atomicAdd(ctr + 3, (unsigned long long)k);
+    box_m2l[b] = make_int2((int)base, k);
+    if ((long long)(base + k) > m2l_cap) {
+        atomicOr(status, ST_ITEM_OVERFLOW);
+    } else {
+        for (int c = 0; c < k; ++c)
+            m2l_items[base + c] =
+                make_int4(b, c * kM2LItemPairs, min(n, (c + 1) * kM2LItemPairs), k > 1 ? (int)base : -1);
+    }
+}
+
+// Totals for fmm_get_tree_info (diagnostics, not on the evaluation path).
+__global__ void k_count(const int32_t* __restrict__ leaf_ids, int nleaf, const int32_t* __restrict__ soff,
+                        const int32_t* __restrict__ ns, const int32_t* __restrict__ sidx,
+                        const int32_t* __restrict__ bcount, unsigned long long* out) {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long w = 0, sl = 0, pp = 0;
-    if (q < nbox) w = (unsigned long long)nweak[q];
+    unsigned long long sl = 0, pp = 0;
     if (q < nleaf) {
         const int b = leaf_ids[q];
-        const int ns = nstrong[b];
-        sl = ns;
+        const int n = ns[b];
+        sl = n;
         unsigned long long src = 0;
-        for (int j = 0; j < ns; ++j) src += bcount[strong[(size_t)b * scap + j]];
+        for (int j = 0; j < n; ++j) src += bcount[sidx[soff[b] + j]];
         pp = src * (unsigned long long)bcount[b];
     }
     for (int o = 16; o; o >>= 1) {
-        w += __shfl_xor_sync(0xffffffffu, w, o);
         sl += __shfl_xor_sync(0xffffffffu, sl, o);
         pp += __shfl_xor_sync(0xffffffffu, pp, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        if (w) atomicAdd(out + 0, w);
-        if (sl) atomicAdd(out + 1, sl);
-        if (pp) atomicAdd(out + 2, pp);
+        if (sl) atomicAdd(out + 0, sl);
+        if (pp) atomicAdd(out + 1, pp);
     }
 }
 
@@ -681,18 +781,29 @@ fmm_status alloc_build(Tree& t) {
     if ((st = dalloc(&t.d_rho, nb))) return st;
     if ((st = dalloc(&t.d_chl, nb))) return st;
     if ((st = dalloc(&t.d_rho32, nb))) return st;
-    if ((st = dalloc(&t.d_nstrong, nb))) return st;
-    if ((st = dalloc(&t.d_nweak, nb))) return st;
+    if ((st = dalloc(&t.d_rad32, nb))) return st;
+    if ((st = dalloc(&t.d_soff, nb))) return st;
+    if ((st = dalloc(&t.d_ns, nb))) return st;
+    if ((st = dalloc(&t.d_woff, nb))) return st;
+    if ((st = dalloc(&t.d_nw, nb))) return st;
+    if ((st = dalloc(&t.d_leaf_items, nb))) return st;
+    if ((st = dalloc(&t.d_box_m2l, nb))) return st;
     if (!t.d_status) {
         if ((st = dalloc(reinterpret_cast<unsigned long long**>(&t.d_status), 8))) return st;
     }
+    if (t.scap_tot < (long long)t.nbox * 16) t.scap_tot = (long long)t.nbox * 16;
+    if (t.wcap_tot < (long long)t.nbox * 48) t.wcap_tot = (long long)t.nbox * 48;
+    if (t.p2p_cap < t.nleaf * 2) t.p2p_cap = t.nleaf * 2;
+    if (t.m2l_cap < t.nbox * 2) t.m2l_cap = t.nbox * 2;
     return alloc_lists(t);
 }
 
 fmm_status alloc_lists(Tree& t) {
     fmm_status st;
-    if ((st = dalloc(&t.d_strong, (size_t)t.nbox * t.scap))) return st;
-    if ((st = dalloc(&t.d_weak, (size_t)t.nbox * t.wcap))) return st;
+    if ((st = dalloc(&t.d_sidx, (size_t)t.scap_tot))) return st;
+    if ((st = dalloc(&t.d_widx, (size_t)t.wcap_tot))) return st;
+    if ((st = dalloc(&t.d_p2p_items, (size_t)t.p2p_cap))) return st;
+    if ((st = dalloc(&t.d_m2l_items, (size_t)t.m2l_cap))) return st;
     return FMM_OK;
 }
 
@@ -725,7 +836,7 @@ fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s) {
     const LevelList& L0 = t.level_boxes[0];
     k_geom<<<nblk(L0.count, 128), 128, 0, s>>>(L0.d_ids, L0.count, X, Y, xy, t.d_bstart, t.d_bcount, t.d_inst,
                                                t.d_inst_boxoff, t.d_center, t.d_radius, t.d_rho, t.d_chl, t.d_rho32,
-                                               1);
+                                               t.d_rad32, 1);
     FMM_CUDA(cudaGetLastError());
     for (int l = 0; l + 1 < t.Lmax; ++l) {
         const SegTable& sx = t.seg_x[l];
@@ -739,7 +850,7 @@ fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s) {
         const LevelList& Ll = t.level_boxes[l + 1];
         k_geom<<<nblk(Ll.count, 128), 128, 0, s>>>(Ll.d_ids, Ll.count, X, Y, xy, t.d_bstart, t.d_bcount, t.d_inst,
                                                    t.d_inst_boxoff, t.d_center, t.d_radius, t.d_rho, t.d_chl,
-                                                   t.d_rho32, 0);
+                                                   t.d_rho32, t.d_rad32, 0);
         FMM_CUDA(cudaGetLastError());
     }
     k_finalize<<<nblk(n, 256), 256, 0, s>>>(Y, n, xy, t.d_leaf_start, t.leaves.d_ids, (int)t.nleaf, t.d_inst,
@@ -749,20 +860,31 @@ fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s) {
 }
 
 fmm_status run_lists(Tree& t, cudaStream_t s) {
-    k_lists_root<<<nblk(t.ninst, 128), 128, 0, s>>>(t.d_inst_boxoff, t.ninst, t.d_nstrong, t.d_strong, t.d_nweak,
-                                                    t.scap);
+    unsigned long long* ctr = reinterpret_cast<unsigned long long*>(t.d_status) + 1;
+    FMM_CUDA(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), s));
+    k_lists_root<<<nblk(t.ninst, 128), 128, 0, s>>>(t.d_inst_boxoff, t.ninst, t.d_soff, t.d_ns, t.d_sidx, t.d_woff,
+                                                    t.d_nw, ctr);
     for (int l = 1; l < t.Lmax; ++l) {
         const LevelList& Ll = t.level_boxes[l];
-        k_lists<<<nblk(Ll.count, 128), 128, 0, s>>>(Ll.d_ids, Ll.count, t.d_parent, t.d_child0, t.d_center,
-                                                    t.d_radius, t.theta, t.d_nstrong, t.d_strong, t.d_nweak,
-                                                    t.d_weak, t.scap, t.wcap, t.d_status);
+        k_lists_level<<<nblk((int64_t)Ll.count * 32, 256), 256, 0, s>>>(
+            Ll.d_ids, Ll.count, t.d_parent, t.d_child0, t.d_soff, t.d_ns, t.d_sidx, t.d_woff, t.d_nw, t.d_widx,
+            t.d_chl, t.d_rad32, t.d_center, t.d_radius, t.theta, ctr, t.scap_tot, t.wcap_tot, t.d_status);
     }
-    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(t.d_status) + 1;
-    FMM_CUDA(cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), s));
-    const int64_t m = std::max<int64_t>(t.nbox, t.nleaf);
-    k_count<<<nblk(m, 256), 256, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, (int)t.nbox, t.d_nstrong, t.d_strong,
-                                         t.d_nweak, t.d_bcount, t.scap, cnt);
+    k_items<<<nblk(t.nbox, 128), 128, 0, s>>>((int)t.nbox, t.d_child0, t.d_bcount, t.d_ns, t.d_nw, ctr,
+                                              t.d_p2p_items, t.d_leaf_items, t.p2p_cap, t.d_m2l_items, t.d_box_m2l,
+                                              t.m2l_cap, t.d_status);
     FMM_CUDA(cudaGetLastError());
+    return FMM_OK;
+}
+
+fmm_status run_count(Tree& t, cudaStream_t s, unsigned long long out[2]) {
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(t.d_status) + 5;
+    FMM_CUDA(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s));
+    k_count<<<nblk(t.nleaf, 256), 256, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, t.d_soff, t.d_ns, t.d_sidx, t.d_bcount,
+                                               cnt);
+    FMM_CUDA(cudaGetLastError());
+    FMM_CUDA(cudaMemcpyAsync(out, cnt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    FMM_CUDA(cudaStreamSynchronize(s));
     return FMM_OK;
 }
 

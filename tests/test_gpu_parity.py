@@ -70,11 +70,10 @@ def test_lists_exact(orc, kind, n, L, theta):
     t = _tree(xy, L, theta=theta)
     ref = orc.build_tree(xy, L)
     li = orc.build_lists(L, ref["center"], ref["radius"], theta)
-    ns, s = t.export("nstrong"), t.export("strong")
-    nw, w = t.export("nweak"), t.export("weak")
+    strong, weak = t.lists()
     for b in range(orc.num_boxes(L)):
-        assert np.array_equal(np.sort(s[b, : ns[b]]), li["s_idx"][li["s_off"][b]: li["s_off"][b + 1]]), b
-        assert np.array_equal(np.sort(w[b, : nw[b]]), li["w_idx"][li["w_off"][b]: li["w_off"][b + 1]]), b
+        assert np.array_equal(np.sort(strong[b]), li["s_idx"][li["s_off"][b]: li["s_off"][b + 1]]), b
+        assert np.array_equal(np.sort(weak[b]), li["w_idx"][li["w_off"][b]: li["w_off"][b + 1]]), b
     info = t.info()
     assert info["n_weak"] == li["w_off"][-1]
 
@@ -201,7 +200,7 @@ def test_too_many_levels_rejected():
 
 def test_list_capacity_overflow_is_retried(orc):
     # points on a tight line make long strong lists; the library grows its
-    # fixed list capacity and rebuilds the lists transparently
+    # list capacity and rebuilds the lists transparently
     g = np.random.default_rng(9)
     n = 20000
     s = np.sort(g.random(n))

@@ -142,14 +142,14 @@ def run_gpu(args):
         phi = torch.empty(N_POINTS, dtype=torch.complex64, device=dev)
         L = L0
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        for _ in range(max(24, args.warmup)):
+        for _ in range(0 if args.nlevels else max(24, args.warmup)):
             e0.record(stream)
             tree.rebuild(X, nlevels=L)
             tree.eval(G, out=phi)
             e1.record(stream)
             e1.synchronize()
             L = tree.autotune_step(e0.elapsed_time(e1) * 1e-3)
-        tuned = int(tree.info()["autotune_nlevels"])
+        tuned = args.nlevels or int(tree.info()["autotune_nlevels"])
         tree.rebuild(X, nlevels=tuned)
         info = tree.info()
 
@@ -177,6 +177,12 @@ def run_gpu(args):
             t = torch.tensor([ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = float(t.item())
+        if args.only_step:
+            if rank == 0:
+                print(json.dumps({"metric": METRIC, "value": round(N_POINTS * world / (ms * 1e-3) / 1e6, 2),
+                                  "unit": UNIT, "ms_per_step": round(ms, 4), "nlevels": tuned,
+                                  "only_step": True}))
+            return
 
         # --- phase times (events on the launching streams) ----------------------
         tree.rebuild(X, flags=F.FMM_FLAG_TIMING)
@@ -378,6 +384,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nlevels", type=int, default=0, help="fix N_levels (skip the autotuner warm-up)")
+    ap.add_argument("--only-step", action="store_true",
+                    help="time the step only (no phase split, FP64 path, adjoint, e2e, accuracy); for profiling")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -208,6 +208,24 @@ fmm_status fmm_tree_export(const fmm_tree* t, int what, void* h_dst, int64_t cou
 
 void fmm_tree_destroy(fmm_tree* t);
 
+/* Exact pairwise sum Phi(z_i) = sum_{z_j != z_i} Gamma_j / (z_i - z_j) for at
+ * most 16384 points, in FP64, that ALLOCATES NO DEVICE MEMORY.  The paper has no
+ * counterpart: it is an addition for callers that cannot allocate — code inside
+ * a host application that owns every device allocation (a fixed pool handed out
+ * by a framework), or latency-critical loops where cudaMalloc/cudaFree, which
+ * can synchronise the device, are not allowed.
+ *   d_xy    : device, n x 2 float64 points;  d_gamma : device, n complex128
+ *   d_phi   : device, n complex128 outputs (input order)
+ * Scratch: a fixed 2 MiB __device__ array inside the library, resident on every
+ * GPU that loads it until the process exits.  The first call on a device looks
+ * up that array's device address (no allocation); make that first call before
+ * any stream capture.  All calls share the array, so calls that run at the same
+ * time on one GPU (unordered streams) race and give wrong results; calls
+ * ordered on one stream are safe, and nothing needs clearing between them.
+ * Errors: INVALID_ARG (NULL pointer, n < 1 or n > 16384), CUDA. */
+fmm_status fmm_direct_eval_noalloc(const double* d_xy, const double* d_gamma, int64_t n, double* d_phi,
+                                   void* stream);
+
 const char* fmm_status_string(fmm_status s);
 const char* fmm_last_error(void);
 

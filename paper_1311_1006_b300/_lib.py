@@ -84,6 +84,7 @@ def load() -> ctypes.CDLL:
         "fmm_get_tree_info": (S, [_VP, ctypes.POINTER(FMMTreeInfo)]),
         "fmm_tree_export": (S, [_VP, ctypes.c_int, _VP, ctypes.c_int64, _VP]),
         "fmm_tree_destroy": (None, [_VP]),
+        "fmm_direct_eval_noalloc": (S, [_VP, _VP, ctypes.c_int64, _VP, _VP]),
         "fmm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "fmm_last_error": (ctypes.c_char_p, []),
     }

@@ -79,6 +79,9 @@ static void apply_params(Tree& t, const fmm_params* prm) {
 }
 
 static fmm_status ensure_streams(Tree& t) {
+    int dev = 0;
+    FMM_CUDA(cudaGetDevice(&dev));
+    FMM_CUDA(cudaDeviceGetAttribute(&t.num_sms, cudaDevAttrMultiProcessorCount, dev));
     if (!t.s_aux) FMM_CUDA(cudaStreamCreateWithFlags(&t.s_aux, cudaStreamNonBlocking));
     if (!t.ev_fork) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_fork, cudaEventDisableTiming));
     if (!t.ev_join) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_join, cudaEventDisableTiming));
@@ -152,7 +155,7 @@ static void release(Tree* t) {
                     t->d_inst_boxoff, t->d_leaf_start, t->d_X2, t->d_Y2, t->d_sideX, t->d_sideY, t->d_tile_cnt,
                     t->d_tile_pre, t->d_seg_lc, t->d_sort_hist, t->d_sort_tot, t->d_sort_off, t->d_perm,
                     t->d_leaf_of, t->d_pts, t->d_pos4, t->d_center, t->d_radius, t->d_rho, t->d_chl, t->d_rho32,
-                    t->d_rad32, t->d_soff, t->d_ns, t->d_sidx, t->d_woff, t->d_nw, t->d_widx, t->d_p2p_items,
+                    t->d_rad32, t->d_soff, t->d_ns, t->d_sidx, t->d_srng, t->d_woff, t->d_nw, t->d_widx, t->d_p2p_items,
                     t->d_m2l_items, t->d_leaf_items, t->d_box_m2l, t->d_status, t->d_gam, t->d_near, t->d_M64,
                     t->d_M32, t->d_Lm2l, t->d_L64, t->d_L32, t->d_p2p_part, t->d_m2l_part};
     for (void* p : ptrs)

@@ -24,7 +24,7 @@ enum : unsigned {
 
 // Work-item sizes: P2P items hold about this many source points; M2L items at
 // most this many weak pairs.
-constexpr int kP2PItemSources = 512;
+constexpr int kP2PItemSources = 2048;
 constexpr int kM2LItemPairs = 64;
 
 // Partition tile: 256 threads x 8 consecutive positions.
@@ -106,6 +106,7 @@ struct Tree {
     float* d_rad32 = nullptr;      // per box (float)radius, for the FP32 pre-test of eq (2.3)
     // coupling lists in CSR form: box b's strong list is sidx[soff[b] .. soff[b]+ns[b])
     int32_t *d_soff = nullptr, *d_ns = nullptr, *d_sidx = nullptr;
+    int2* d_srng = nullptr;        // leaves: (first point, count) of each strong entry, parallel to sidx
     int32_t *d_woff = nullptr, *d_nw = nullptr, *d_widx = nullptr;
     long long scap_tot = 0, wcap_tot = 0;
     // work items (see k_items)
@@ -114,7 +115,8 @@ struct Tree {
     int2* d_leaf_items = nullptr;  // per box: first P2P item, item count (leaves)
     int2* d_box_m2l = nullptr;     // per box: first M2L item, item count
     long long p2p_cap = 0, m2l_cap = 0;
-    int max_leaf = 1;              // largest leaf (points): row stride of the P2P partial sums
+    int max_leaf = 1;
+    int num_sms = 148;              // largest leaf (points): row stride of the P2P partial sums
     // device words: [0] status bits, then 64-bit counters:
     // [1] strong entries, [2] weak entries, [3] P2P items, [4] M2L items, [5..6] diagnostics
     unsigned* d_status = nullptr;

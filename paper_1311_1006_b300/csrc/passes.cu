@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "fmm_internal.cuh"
 
@@ -132,32 +133,32 @@ __global__ void __launch_bounds__(128) k_p2m64(const int32_t* __restrict__ leave
 
 // --------------------------------------------------------------------- M2M
 
-// One thread per parent; FP64.  Leaf children of the FP32 path are read from
-// the FP32 multipoles written by P2M.
+// One thread per (parent, child), FP64: four consecutive lanes shift the four
+// children of one parent and add them with two xor-shuffles (fixed order).
+// Leaf children of the FP32 path are read from the FP32 multipoles of P2M.
 template <int P>
 __global__ void __launch_bounds__(128) k_m2m(const int32_t* __restrict__ parents, int cnt,
                                              const int32_t* __restrict__ child0, const double* __restrict__ rho,
                                              const double2* __restrict__ center, const float2* __restrict__ M32in,
                                              double2* __restrict__ M64, float2* __restrict__ M32out, int fp32_path,
                                              int p, int PS) {
-    int qi = blockIdx.x * blockDim.x + threadIdx.x;
-    if (qi >= cnt) return;
-    const int b = parents[qi];
-    const int c0 = child0[b];
-    const double rP = rho[b];
-    const double inv = rP > 0.0 ? 1.0 / rP : 0.0;
-    const double2 cP = center[b];
-    double2 acc[P];
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int pi = q >> 2, c = q & 3;
+    const bool valid = pi < cnt;
+    double2 v[P];
 #pragma unroll
-    for (int k = 0; k < P; ++k) acc[k] = make_double2(0.0, 0.0);
-    for (int c = 0; c < 4; ++c) {
-        const int h = c0 + c;
-        double2 v[P];
+    for (int k = 0; k < P; ++k) v[k] = make_double2(0.0, 0.0);
+    int b = 0;
+    if (valid) {
+        b = parents[pi];
+        const int h = child0[b] + c;
+        const double rP = rho[b];
+        const double inv = rP > 0.0 ? 1.0 / rP : 0.0;
         if (fp32_path && child0[h] < 0) {
             const float2* src = M32in + (size_t)h * PS;
 #pragma unroll
             for (int k = 0; k < P; ++k) {
-                float2 f = src[k];
+                const float2 f = src[k];
                 v[k] = make_double2((double)f.x, (double)f.y);
             }
         } else {
@@ -166,8 +167,8 @@ __global__ void __launch_bounds__(128) k_m2m(const int32_t* __restrict__ parents
             for (int k = 0; k < P; ++k) v[k] = src[k];
         }
         const double sigma = rho[h] * inv;
-        const double2 ch = center[h];
-        const double2 q = make_double2((ch.x - cP.x) * inv, (ch.y - cP.y) * inv);
+        const double2 cP = center[b], ch = center[h];
+        const double2 qv = make_double2((ch.x - cP.x) * inv, (ch.y - cP.y) * inv);
         double sp = 1.0;
 #pragma unroll
         for (int k = 0; k < P; ++k) {
@@ -179,25 +180,25 @@ __global__ void __launch_bounds__(128) k_m2m(const int32_t* __restrict__ parents
 #pragma unroll
         for (int k = P - 1; k >= 1; --k) {
 #pragma unroll
-            for (int j = k; j < P; ++j) v[j] = cfma(q, v[j - 1], v[j]);
-        }
-#pragma unroll
-        for (int k = 0; k < P; ++k) {
-            acc[k].x += v[k].x;
-            acc[k].y += v[k].y;
+            for (int j = k; j < P; ++j) v[j] = cfma(qv, v[j - 1], v[j]);
         }
     }
-    // the shift fills orders >= p from lower ones: keep the expansion at p terms
 #pragma unroll
-    for (int k = 0; k < P; ++k)
-        if (k >= p) acc[k] = make_double2(0.0, 0.0);
+    for (int k = 0; k < P; ++k) {
+        v[k].x += __shfl_xor_sync(0xffffffffu, v[k].x, 1);
+        v[k].y += __shfl_xor_sync(0xffffffffu, v[k].y, 1);
+        v[k].x += __shfl_xor_sync(0xffffffffu, v[k].x, 2);
+        v[k].y += __shfl_xor_sync(0xffffffffu, v[k].y, 2);
+    }
+    if (!valid || c != 0) return;
+    // the shift fills orders >= p from lower ones: keep the expansion at p terms
     double2* out = M64 + (size_t)b * PS;
 #pragma unroll
-    for (int k = 0; k < P; ++k) out[k] = acc[k];
+    for (int k = 0; k < P; ++k) out[k] = k < p ? v[k] : make_double2(0.0, 0.0);
     if (fp32_path) {
         float2* o32 = M32out + (size_t)b * PS;
 #pragma unroll
-        for (int k = 0; k < P; ++k) o32[k] = make_float2((float)acc[k].x, (float)acc[k].y);
+        for (int k = 0; k < P; ++k) o32[k] = k < p ? make_float2((float)v[k].x, (float)v[k].y) : make_float2(0.f, 0.f);
     }
 }
 
@@ -332,7 +333,7 @@ __global__ void __launch_bounds__(128) k_l2l(const int32_t* __restrict__ boxes, 
                                              const int32_t* __restrict__ parent, const int32_t* __restrict__ child0,
                                              const double* __restrict__ rho, const double2* __restrict__ center,
                                              const int2* __restrict__ box_m2l, const LM* __restrict__ Lm2l,
-                                             const LM* __restrict__ part, double2* __restrict__ L64,
+                                             double2* __restrict__ L64,
                                              float2* __restrict__ L32, int p, int PS) {
     int qi = blockIdx.x * blockDim.x + threadIdx.x;
     if (qi >= cnt) return;
@@ -353,26 +354,12 @@ __global__ void __launch_bounds__(128) k_l2l(const int32_t* __restrict__ boxes, 
 #pragma unroll
         for (int j = P - 2; j >= k; --j) b[j] = cfma(q, b[j + 1], b[j]);
     }
-    // this box's own M2L sum: none, one item written in place, or the partial
-    // sums of its items added in item order
+    // this box's own M2L sum (split boxes were summed by k_reduce_m2l)
     const int2 mi = box_m2l[c];
     double2 own[P];
+    const LM* o = Lm2l + (size_t)c * PS;
 #pragma unroll
-    for (int m = 0; m < P; ++m) own[m] = make_double2(0.0, 0.0);
-    if (mi.y == 1) {
-        const LM* o = Lm2l + (size_t)c * PS;
-#pragma unroll
-        for (int m = 0; m < P; ++m) own[m] = make_double2((double)o[m].x, (double)o[m].y);
-    } else {
-        for (int q = 0; q < mi.y; ++q) {
-            const LM* o = part + (size_t)(mi.x + q) * PS;
-#pragma unroll
-            for (int m = 0; m < P; ++m) {
-                own[m].x += (double)o[m].x;
-                own[m].y += (double)o[m].y;
-            }
-        }
-    }
+    for (int m = 0; m < P; ++m) own[m] = mi.y > 0 ? make_double2((double)o[m].x, (double)o[m].y) : make_double2(0.0, 0.0);
     double sp = 1.0;
     double2* out = L64 + (size_t)c * PS;
     const bool leaf32 = (L32 != nullptr) && child0[c] < 0;
@@ -389,34 +376,14 @@ __global__ void __launch_bounds__(128) k_l2l(const int32_t* __restrict__ boxes, 
 
 // ------------------------------------------------------------- L2P + sum
 
-// Near-field value of sorted point i: written in place by a single P2P item,
-// or the partial sums of the leaf's items added in item order.
-template <typename C>
-__device__ __forceinline__ C near_value(int i, int lf, int ls, const int2* __restrict__ leaf_items,
-                                        const C* __restrict__ nearv, const C* __restrict__ part, int TS) {
-    const int2 li = leaf_items[lf];
-    if (li.y == 1) return nearv[i];
-    C s;
-    s.x = 0;
-    s.y = 0;
-    for (int q = 0; q < li.y; ++q) {
-        const C v = part[(size_t)(li.x + q) * TS + (i - ls)];
-        s.x += v.x;
-        s.y += v.y;
-    }
-    return s;
-}
-
 // One thread per sorted point: far field by Horner from the leaf's local
 // expansion, plus the near field, written to the caller's order.
 template <int P>
 __global__ void __launch_bounds__(256) k_l2p32(int n, const int32_t* __restrict__ leaf_of,
-                                               const int32_t* __restrict__ bstart, const float4* __restrict__ chl,
+                                               const float4* __restrict__ chl,
                                                const float* __restrict__ rho32, const float4* __restrict__ pos4,
-                                               const float2* __restrict__ L32, const int2* __restrict__ leaf_items,
-                                               const float2* __restrict__ nearv, const float2* __restrict__ part,
-                                               int TS, const int32_t* __restrict__ perm, float2* __restrict__ out,
-                                               int PS) {
+                                               const float2* __restrict__ L32, const float2* __restrict__ nearv,
+                                               const int32_t* __restrict__ perm, float2* __restrict__ out, int PS) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int lf = leaf_of[i];
@@ -429,18 +396,16 @@ __global__ void __launch_bounds__(256) k_l2p32(int n, const int32_t* __restrict_
     float2 v = Lb[P - 1];
 #pragma unroll
     for (int l = P - 2; l >= 0; --l) v = cfma(v, w, Lb[l]);
-    const float2 nv = near_value(i, lf, bstart[lf], leaf_items, nearv, part, TS);
+    const float2 nv = nearv[i];
     out[perm[i]] = make_float2(v.x + nv.x, v.y + nv.y);
 }
 
 template <int P>
 __global__ void __launch_bounds__(256) k_l2p64(int n, const int32_t* __restrict__ leaf_of,
-                                               const int32_t* __restrict__ bstart, const double2* __restrict__ center,
+                                               const double2* __restrict__ center,
                                                const double* __restrict__ rho, const double2* __restrict__ pts,
-                                               const double2* __restrict__ L64, const int2* __restrict__ leaf_items,
-                                               const double2* __restrict__ nearv, const double2* __restrict__ part,
-                                               int TS, const int32_t* __restrict__ perm, double2* __restrict__ out,
-                                               int PS) {
+                                               const double2* __restrict__ L64, const double2* __restrict__ nearv,
+                                               const int32_t* __restrict__ perm, double2* __restrict__ out, int PS) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int lf = leaf_of[i];
@@ -453,7 +418,7 @@ __global__ void __launch_bounds__(256) k_l2p64(int n, const int32_t* __restrict_
     double2 v = Lb[P - 1];
 #pragma unroll
     for (int l = P - 2; l >= 0; --l) v = cfma(v, w, Lb[l]);
-    const double2 nv = near_value(i, lf, bstart[lf], leaf_items, nearv, part, TS);
+    const double2 nv = nearv[i];
     out[perm[i]] = make_double2(v.x + nv.x, v.y + nv.y);
 }
 
@@ -468,6 +433,7 @@ __global__ void __launch_bounds__(256) k_l2p64(int n, const int32_t* __restrict_
 constexpr int kP2PWarps = 8;
 constexpr int kP2PChunk32 = 192;
 constexpr int kP2PChunk64 = 128;
+constexpr int kP2PBlocksPerSM = 4;
 
 __device__ __forceinline__ void p2p_interact32(const float4 t, const float4 s, const float2 g, float2& acc) {
     const float dx = (t.x - s.x) + (t.z - s.z);
@@ -480,77 +446,132 @@ __device__ __forceinline__ void p2p_interact32(const float4 t, const float4 s, c
     acc.y = fmaf(ti, inv, acc.y);
 }
 
-template <int TPL>
-__global__ void __launch_bounds__(kP2PWarps * 32) k_p2p32(const int4* __restrict__ items,
-                                                          const unsigned long long* __restrict__ nitems,
-                                                          const int32_t* __restrict__ bstart,
-                                                          const int32_t* __restrict__ bcount,
-                                                          const int32_t* __restrict__ soff,
-                                                          const int32_t* __restrict__ sidx,
-                                                          const float4* __restrict__ pos4,
-                                                          const float2* __restrict__ gam, float2* __restrict__ nearv,
-                                                          float2* __restrict__ part, int TS) {
-    __shared__ float4 sp[kP2PWarps][kP2PChunk32];
-    __shared__ float2 sg[kP2PWarps][kP2PChunk32];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+__device__ __forceinline__ void p2p_interact64(const double2 t, const double2 s, const double2 g, double2& acc) {
+    const double dx = t.x - s.x, dy = t.y - s.y;
+    const double r2 = fma(dx, dx, dy * dy);
+    const double inv = r2 > 0.0 ? __drcp_rn(r2) : 0.0;
+    const double tr = fma(g.x, dx, g.y * dy);
+    const double ti = fma(g.y, dx, -g.x * dy);
+    acc.x = fma(tr, inv, acc.x);
+    acc.y = fma(ti, inv, acc.y);
+}
+
+// ---- P2P with a compile-time lane layout --------------------------------
+// LT target lanes x S = 32/LT source slices, TPL targets per lane (a leaf of at
+// most TPL*LT points per pass).  Staged chunks are padded with zero-strength
+// sources far away, so the inner loop runs whole unrolled groups with no tail
+// test.  FP32: the coincident-pair guard is folded into r^2 (+1e-37f):
+// coincident points give dx = dy = 0 and add 0; pairs closer than ~1e-18 are
+// below FP32 resolution anyway.
+__device__ __forceinline__ void p2p_fast32(const float4 t, const float4 s, const float2 g, float2& acc) {
+    const float dx = (t.x - s.x) + (t.z - s.z);
+    const float dy = (t.y - s.y) + (t.w - s.w);
+    const float inv = rcp_approx(fmaf(dx, dx, fmaf(dy, dy, 1e-37f)));
+    const float tr = fmaf(g.x, dx, g.y * dy);
+    const float ti = fmaf(g.y, dx, -g.x * dy);
+    acc.x = fmaf(tr, inv, acc.x);
+    acc.y = fmaf(ti, inv, acc.y);
+}
+__device__ __forceinline__ void p2p_fast(const float4 t, const float4 s, const float2 g, float2& acc) {
+    p2p_fast32(t, s, g, acc);
+}
+__device__ __forceinline__ void p2p_fast(const double2 t, const double2 s, const double2 g, double2& acc) {
+    p2p_interact64(t, s, g, acc);
+}
+template <typename V>
+__device__ __forceinline__ V far_dummy();
+template <>
+__device__ __forceinline__ float4 far_dummy<float4>() {
+    return make_float4(1e18f, 1e18f, 0.f, 0.f);
+}
+template <>
+__device__ __forceinline__ double2 far_dummy<double2>() {
+    return make_double2(1e150, 1e150);
+}
+
+constexpr int kP2PUnroll = 4;
+
+// ---- P2P reading sources straight from global memory ------------------------
+// One warp per work item, fetched dynamically from an atomic counter.  Lane
+// (tg, ss) holds TPL targets and walks every S-th point of the item's source
+// ranges (int2 (first point, count) per strong entry, recorded by the list
+// build).  The S slices of a warp read S consecutive points per step, so each
+// load is one coalesced line; the next point is prefetched before the current
+// one is used.  No shared memory, no staging.
+constexpr int kP2PDWarps = 4;
+
+template <typename V, typename C, int TPL, int LT>
+__global__ void __launch_bounds__(kP2PDWarps * 32) k_p2p_direct(const int4* __restrict__ items,
+                                                                const unsigned long long* __restrict__ nitems,
+                                                                unsigned* __restrict__ next_item,
+                                                                const int32_t* __restrict__ bstart,
+                                                                const int32_t* __restrict__ bcount,
+                                                                const int32_t* __restrict__ soff,
+                                                                const int2* __restrict__ srng,
+                                                                const V* __restrict__ pos, const C* __restrict__ gam,
+                                                                C* __restrict__ nearv, C* __restrict__ part, int TS) {
+    constexpr int S = 32 / LT;
+    const int lane = threadIdx.x & 31;
+    const int tg = lane % LT, ss = lane / LT;
     const int nit = (int)*nitems;
-    for (int it = blockIdx.x * kP2PWarps + warp; it < nit; it += gridDim.x * kP2PWarps) {
+    while (true) {
+        int it = 0;
+        if (lane == 0) it = (int)atomicAdd(next_item, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= nit) break;
         const int4 item = items[it];
         const int b = item.x;
         const int ts = bstart[b], tn = bcount[b];
-        const int32_t* sl = sidx + soff[b];
-        for (int t0 = 0; t0 < tn; t0 += 32 * TPL) {
-            const int nt = min(tn - t0, 32 * TPL);
-            const int LT = (nt + TPL - 1) / TPL;
-            const int S = 32 / LT;
-            const int tg = lane % LT, ss = lane / LT;
-            const bool active = ss < S;
-            float4 xt[TPL];
-            float2 acc[TPL];
+        const int2* rl = srng + soff[b];
+        for (int t0 = 0; t0 < tn; t0 += TPL * LT) {
+            V xt[TPL];
+            C acc[TPL];
 #pragma unroll
             for (int u = 0; u < TPL; ++u) {
                 const int idx = t0 + tg + u * LT;
-                xt[u] = (idx < tn) ? pos4[ts + idx] : make_float4(0.f, 0.f, 0.f, 0.f);
-                acc[u] = make_float2(0.f, 0.f);
+                xt[u] = (idx < tn) ? pos[ts + idx] : V{};
+                acc[u] = C{};
             }
-            int j = item.y, off = 0;
-            while (j < item.z) {
-                __syncwarp();
-                int cnt = 0;
-                while (j < item.z && cnt < kP2PChunk32) {
-                    const int h = sl[j];
-                    const int hs = bstart[h], hn = bcount[h];
-                    const int take = min(hn - off, kP2PChunk32 - cnt);
-                    for (int e = lane; e < take; e += 32) {
-                        sp[warp][cnt + e] = pos4[hs + off + e];
-                        sg[warp][cnt + e] = gam[hs + off + e];
-                    }
-                    cnt += take;
-                    off += take;
-                    if (off == hn) {
-                        ++j;
-                        off = 0;
-                    }
+            // warp-uniform walk over the source ranges; the next range's entry and
+            // first point of this lane are loaded one step ahead
+            int k = item.y;
+            int2 r = k < item.z ? rl[k] : make_int2(0, 0);
+            V s0 = V{};
+            C g0 = C{};
+            if (k < item.z && ss < r.y) {
+                s0 = pos[r.x + ss];
+                g0 = gam[r.x + ss];
+            }
+            while (k < item.z) {
+                const int2 rn = (k + 1 < item.z) ? rl[k + 1] : make_int2(0, 0);
+                V s1 = V{};
+                C g1 = C{};
+                if (ss < rn.y) {
+                    s1 = pos[rn.x + ss];
+                    g1 = gam[rn.x + ss];
                 }
-                __syncwarp();
-                if (active) {
-#pragma unroll 4
-                    for (int e = ss; e < cnt; e += S) {
-                        const float4 s = sp[warp][e];
-                        const float2 g = sg[warp][e];
+                if (ss < r.y) {
 #pragma unroll
-                        for (int u = 0; u < TPL; ++u) p2p_interact32(xt[u], s, g, acc[u]);
+                    for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], s0, g0, acc[u]);
+                    for (int e = ss + S; e < r.y; e += S) {
+                        const V s = pos[r.x + e];
+                        const C g = gam[r.x + e];
+#pragma unroll
+                        for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], s, g, acc[u]);
                     }
                 }
+                r = rn;
+                s0 = s1;
+                g0 = g1;
+                ++k;
             }
-            // sum the S source slices into the lanes of slice 0
 #pragma unroll
             for (int u = 0; u < TPL; ++u) {
-                float2 tot = acc[u];
-                for (int s2 = 1; s2 < S; ++s2) {
-                    const int src = tg + s2 * LT;
-                    tot.x += __shfl_sync(0xffffffffu, acc[u].x, src & 31);
-                    tot.y += __shfl_sync(0xffffffffu, acc[u].y, src & 31);
+                C tot = acc[u];
+#pragma unroll
+                for (int o = LT; o < 32; o <<= 1) {
+                    tot.x += __shfl_xor_sync(0xffffffffu, tot.x, o);
+                    tot.y += __shfl_xor_sync(0xffffffffu, tot.y, o);
                 }
                 const int idx = t0 + tg + u * LT;
                 if (ss == 0 && idx < tn) {
@@ -562,93 +583,51 @@ __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p32(const int4* __restrict
     }
 }
 
-__device__ __forceinline__ void p2p_interact64(const double2 t, const double2 s, const double2 g, double2& acc) {
-    const double dx = t.x - s.x, dy = t.y - s.y;
-    const double r2 = fma(dx, dx, dy * dy);
-    const double inv = r2 > 0.0 ? __drcp_rn(r2) : 0.0;
-    const double tr = fma(g.x, dx, g.y * dy);
-    const double ti = fma(g.y, dx, -g.x * dy);
-    acc.x = fma(tr, inv, acc.x);
-    acc.y = fma(ti, inv, acc.y);
+// Near field of leaves whose strong list was split into several items: one
+// warp per leaf adds the item partial sums of each target in item order.
+template <typename C>
+__global__ void __launch_bounds__(256) k_reduce_p2p(const int32_t* __restrict__ leaves, int nleaf,
+                                                    const int2* __restrict__ leaf_items,
+                                                    const int32_t* __restrict__ bstart,
+                                                    const int32_t* __restrict__ bcount, const C* __restrict__ part,
+                                                    int TS, C* __restrict__ nearv) {
+    const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= nleaf) return;
+    const int b = leaves[w];
+    const int2 li = leaf_items[b];
+    if (li.y <= 1) return;
+    const int ts = bstart[b], tn = bcount[b];
+    for (int t = lane; t < tn; t += 32) {
+        C s{};
+#pragma unroll 8
+        for (int q = 0; q < li.y; ++q) {
+            const C v = part[(size_t)(li.x + q) * TS + t];
+            s.x += v.x;
+            s.y += v.y;
+        }
+        nearv[ts + t] = s;
+    }
 }
 
-template <int TPL>
-__global__ void __launch_bounds__(kP2PWarps * 32) k_p2p64(const int4* __restrict__ items,
-                                                          const unsigned long long* __restrict__ nitems,
-                                                          const int32_t* __restrict__ bstart,
-                                                          const int32_t* __restrict__ bcount,
-                                                          const int32_t* __restrict__ soff,
-                                                          const int32_t* __restrict__ sidx,
-                                                          const double2* __restrict__ pts,
-                                                          const double2* __restrict__ gam,
-                                                          double2* __restrict__ nearv, double2* __restrict__ part,
-                                                          int TS) {
-    __shared__ double2 sp[kP2PWarps][kP2PChunk64];
-    __shared__ double2 sg[kP2PWarps][kP2PChunk64];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nit = (int)*nitems;
-    for (int it = blockIdx.x * kP2PWarps + warp; it < nit; it += gridDim.x * kP2PWarps) {
-        const int4 item = items[it];
-        const int b = item.x;
-        const int ts = bstart[b], tn = bcount[b];
-        const int32_t* sl = sidx + soff[b];
-        for (int t0 = 0; t0 < tn; t0 += 32 * TPL) {
-            const int nt = min(tn - t0, 32 * TPL);
-            const int LT = (nt + TPL - 1) / TPL;
-            const int S = 32 / LT;
-            const int tg = lane % LT, ss = lane / LT;
-            const bool active = ss < S;
-            double2 xt[TPL], acc[TPL];
-#pragma unroll
-            for (int u = 0; u < TPL; ++u) {
-                const int idx = t0 + tg + u * LT;
-                xt[u] = (idx < tn) ? pts[ts + idx] : make_double2(0.0, 0.0);
-                acc[u] = make_double2(0.0, 0.0);
-            }
-            int j = item.y, off = 0;
-            while (j < item.z) {
-                __syncwarp();
-                int cnt = 0;
-                while (j < item.z && cnt < kP2PChunk64) {
-                    const int h = sl[j];
-                    const int hs = bstart[h], hn = bcount[h];
-                    const int take = min(hn - off, kP2PChunk64 - cnt);
-                    for (int e = lane; e < take; e += 32) {
-                        sp[warp][cnt + e] = pts[hs + off + e];
-                        sg[warp][cnt + e] = gam[hs + off + e];
-                    }
-                    cnt += take;
-                    off += take;
-                    if (off == hn) {
-                        ++j;
-                        off = 0;
-                    }
-                }
-                __syncwarp();
-                if (active) {
-                    for (int e = ss; e < cnt; e += S) {
-                        const double2 s = sp[warp][e];
-                        const double2 g = sg[warp][e];
-#pragma unroll
-                        for (int u = 0; u < TPL; ++u) p2p_interact64(xt[u], s, g, acc[u]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < TPL; ++u) {
-                double2 tot = acc[u];
-                for (int s2 = 1; s2 < S; ++s2) {
-                    const int src = tg + s2 * LT;
-                    tot.x += __shfl_sync(0xffffffffu, acc[u].x, src & 31);
-                    tot.y += __shfl_sync(0xffffffffu, acc[u].y, src & 31);
-                }
-                const int idx = t0 + tg + u * LT;
-                if (ss == 0 && idx < tn) {
-                    if (item.w < 0) nearv[ts + idx] = tot;
-                    else part[(size_t)it * TS + idx] = tot;
-                }
-            }
+// M2L sums of boxes whose weak list was split: one warp per box, lane = coefficient.
+template <typename C>
+__global__ void __launch_bounds__(256) k_reduce_m2l(int nbox, const int2* __restrict__ box_m2l,
+                                                    const C* __restrict__ part, int PS, C* __restrict__ Lm2l) {
+    const int b = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= nbox) return;
+    const int2 mi = box_m2l[b];
+    if (mi.y <= 1) return;
+    if (lane < PS) {
+        C s{};
+#pragma unroll 8
+        for (int q = 0; q < mi.y; ++q) {
+            const C v = part[(size_t)(mi.x + q) * PS + lane];
+            s.x += v.x;
+            s.y += v.y;
         }
+        Lm2l[(size_t)b * PS + lane] = s;
     }
 }
 
@@ -682,19 +661,22 @@ static void launch_far_fp32(Tree& t, const Bufs& B, cudaStream_t s) {
     for (int l = t.Lmax - 2; l >= 0; --l) {
         const LevelList& L = t.level_parents[l];
         if (!L.count) continue;
-        k_m2m<P><<<nblk(L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_child0, t.d_rho, t.d_center, B.M32,
-                                                    B.M64, B.M32, 1, t.p, t.PS);
+        k_m2m<P><<<nblk(4 * (int64_t)L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_child0, t.d_rho,
+                                                                 t.d_center, B.M32, B.M64, B.M32, 1, t.p, t.PS);
     }
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[2], s);
     k_m2l32<P><<<nblk(t.m2l_cap, 128), 128, 0, s>>>(t.d_m2l_items, item_count(t, 3), t.d_woff, t.d_widx, t.d_chl,
                                                     t.d_rho32, B.M32, static_cast<float2*>(B.Lm2l),
                                                     static_cast<float2*>(B.m2l_part), t.PS);
+    k_reduce_m2l<float2><<<nblk(32 * t.nbox, 256), 256, 0, s>>>((int)t.nbox, t.d_box_m2l,
+                                                               static_cast<const float2*>(B.m2l_part), t.PS,
+                                                               static_cast<float2*>(B.Lm2l));
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[3], s);
     for (int l = 0; l + 1 < t.Lmax; ++l) {
         const LevelList& L = t.level_boxes[l + 1];
         k_l2l<P, float2><<<nblk(L.count, 128), 128, 0, s>>>(
             L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho, t.d_center, t.d_box_m2l,
-            static_cast<const float2*>(B.Lm2l), static_cast<const float2*>(B.m2l_part), B.L64, B.L32, t.p, t.PS);
+            static_cast<const float2*>(B.Lm2l), B.L64, B.L32, t.p, t.PS);
     }
 }
 
@@ -706,20 +688,22 @@ static void launch_far_fp64(Tree& t, const Bufs& B, cudaStream_t s) {
     for (int l = t.Lmax - 2; l >= 0; --l) {
         const LevelList& L = t.level_parents[l];
         if (!L.count) continue;
-        k_m2m<P><<<nblk(L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_child0, t.d_rho, t.d_center, nullptr,
-                                                    B.M64, nullptr, 0, t.p, t.PS);
+        k_m2m<P><<<nblk(4 * (int64_t)L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_child0, t.d_rho,
+                                                                 t.d_center, nullptr, B.M64, nullptr, 0, t.p, t.PS);
     }
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[2], s);
     k_m2l64<P><<<nblk(t.m2l_cap, 128), 128, 0, s>>>(t.d_m2l_items, item_count(t, 3), t.d_woff, t.d_widx,
                                                     t.d_center, t.d_rho, B.M64, static_cast<double2*>(B.Lm2l),
                                                     static_cast<double2*>(B.m2l_part), t.PS);
+    k_reduce_m2l<double2><<<nblk(32 * t.nbox, 256), 256, 0, s>>>((int)t.nbox, t.d_box_m2l,
+                                                                static_cast<const double2*>(B.m2l_part), t.PS,
+                                                                static_cast<double2*>(B.Lm2l));
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[3], s);
     for (int l = 0; l + 1 < t.Lmax; ++l) {
         const LevelList& L = t.level_boxes[l + 1];
         k_l2l<P, double2><<<nblk(L.count, 128), 128, 0, s>>>(
             L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho, t.d_center, t.d_box_m2l,
-            static_cast<const double2*>(B.Lm2l), static_cast<const double2*>(B.m2l_part), B.L64, nullptr, t.p,
-            t.PS);
+            static_cast<const double2*>(B.Lm2l), B.L64, nullptr, t.p, t.PS);
     }
 }
 
@@ -727,42 +711,65 @@ template <int P>
 static void launch_l2p(Tree& t, const Bufs& B, void* d_phi, cudaStream_t s) {
     const int n = (int)t.n;
     if (t.path == FMM_PATH_FP32) {
-        k_l2p32<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_bstart, t.d_chl, t.d_rho32, t.d_pos4, B.L32,
-                                                t.d_leaf_items, static_cast<const float2*>(B.near),
-                                                static_cast<const float2*>(B.p2p_part), t.max_leaf, t.d_perm,
+        k_l2p32<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_chl, t.d_rho32, t.d_pos4, B.L32,
+                                                static_cast<const float2*>(B.near), t.d_perm,
                                                 static_cast<float2*>(d_phi), t.PS);
     } else {
-        k_l2p64<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_bstart, t.d_center, t.d_rho, t.d_pts, B.L64,
-                                                t.d_leaf_items, static_cast<const double2*>(B.near),
-                                                static_cast<const double2*>(B.p2p_part), t.max_leaf, t.d_perm,
+        k_l2p64<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_center, t.d_rho, t.d_pts, B.L64,
+                                                static_cast<const double2*>(B.near), t.d_perm,
                                                 static_cast<double2*>(d_phi), t.PS);
     }
 }
 
+// Blocks per SM of the P2P grid (FMM_P2P_BLOCKS_PER_SM overrides the default).
+static int p2p_blocks_per_sm() {
+    static int v = [] {
+        const char* e = getenv("FMM_P2P_BLOCKS_PER_SM");
+        const int x = e ? atoi(e) : 0;
+        return x > 0 ? x : kP2PBlocksPerSM;
+    }();
+    return v;
+}
+
 static void launch_p2p(Tree& t, const Bufs& B, cudaStream_t s) {
-    const int grid = nblk(t.p2p_cap, kP2PWarps);
-    const bool wide = (double)t.n / std::max<int64_t>(t.nleaf, 1) >= 8.0;
     const unsigned long long* cnt = item_count(t, 2);
+    unsigned* next = reinterpret_cast<unsigned*>(reinterpret_cast<unsigned long long*>(t.d_status) + 7);
+    cudaMemsetAsync(next, 0, sizeof(unsigned), s);
+    const int bps = p2p_blocks_per_sm();
+    const int dgrid = std::min(nblk(t.p2p_cap, kP2PDWarps), t.num_sms * bps);
+    const int rgrid = nblk(32 * t.nleaf, 256);
     if (t.path == FMM_PATH_FP32) {
         const float2* gam = static_cast<const float2*>(B.gam);
         float2* nv = static_cast<float2*>(B.near);
         float2* pt = static_cast<float2*>(B.p2p_part);
-        if (wide)
-            k_p2p32<4><<<grid, kP2PWarps * 32, 0, s>>>(t.d_p2p_items, cnt, t.d_bstart, t.d_bcount, t.d_soff,
-                                                       t.d_sidx, t.d_pos4, gam, nv, pt, t.max_leaf);
-        else
-            k_p2p32<1><<<grid, kP2PWarps * 32, 0, s>>>(t.d_p2p_items, cnt, t.d_bstart, t.d_bcount, t.d_soff,
-                                                       t.d_sidx, t.d_pos4, gam, nv, pt, t.max_leaf);
+#define FMM_P2P32(TPL, LT)                                                                                        \
+    k_p2p_direct<float4, float2, TPL, LT><<<dgrid, kP2PDWarps * 32, 0, s>>>(                                      \
+        t.d_p2p_items, cnt, next, t.d_bstart, t.d_bcount, t.d_soff, t.d_srng, t.d_pos4, gam, nv, pt, t.max_leaf)
+        if (t.max_leaf <= 4) { FMM_P2P32(2, 2); }
+        else if (t.max_leaf <= 8) { FMM_P2P32(4, 2); }
+        else if (t.max_leaf <= 16) { FMM_P2P32(8, 2); }
+        else if (t.max_leaf <= 32) { FMM_P2P32(8, 4); }
+        else if (t.max_leaf <= 64) { FMM_P2P32(8, 8); }
+        else { FMM_P2P32(8, 16); }
+#undef FMM_P2P32
+        k_reduce_p2p<float2><<<rgrid, 256, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, t.d_leaf_items, t.d_bstart,
+                                                   t.d_bcount, pt, t.max_leaf, nv);
     } else {
         const double2* gam = static_cast<const double2*>(B.gam);
         double2* nv = static_cast<double2*>(B.near);
         double2* pt = static_cast<double2*>(B.p2p_part);
-        if (wide)
-            k_p2p64<4><<<grid, kP2PWarps * 32, 0, s>>>(t.d_p2p_items, cnt, t.d_bstart, t.d_bcount, t.d_soff,
-                                                       t.d_sidx, t.d_pts, gam, nv, pt, t.max_leaf);
-        else
-            k_p2p64<1><<<grid, kP2PWarps * 32, 0, s>>>(t.d_p2p_items, cnt, t.d_bstart, t.d_bcount, t.d_soff,
-                                                       t.d_sidx, t.d_pts, gam, nv, pt, t.max_leaf);
+#define FMM_P2P64(TPL, LT)                                                                                        \
+    k_p2p_direct<double2, double2, TPL, LT><<<dgrid, kP2PDWarps * 32, 0, s>>>(                                    \
+        t.d_p2p_items, cnt, next, t.d_bstart, t.d_bcount, t.d_soff, t.d_srng, t.d_pts, gam, nv, pt, t.max_leaf)
+        if (t.max_leaf <= 4) { FMM_P2P64(2, 2); }
+        else if (t.max_leaf <= 8) { FMM_P2P64(4, 2); }
+        else if (t.max_leaf <= 16) { FMM_P2P64(8, 2); }
+        else if (t.max_leaf <= 32) { FMM_P2P64(8, 4); }
+        else if (t.max_leaf <= 64) { FMM_P2P64(8, 8); }
+        else { FMM_P2P64(8, 16); }
+#undef FMM_P2P64
+        k_reduce_p2p<double2><<<rgrid, 256, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, t.d_leaf_items, t.d_bstart,
+                                                    t.d_bcount, pt, t.max_leaf, nv);
     }
 }
 

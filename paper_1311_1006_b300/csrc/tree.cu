@@ -559,11 +559,14 @@ __global__ void k_finalize(const int32_t* __restrict__ Y, int n, const double2* 
 // ================================================================== lists
 
 __global__ void k_lists_root(const int64_t* __restrict__ inst_box_off, int ninst, int32_t* soff, int32_t* ns,
-                             int32_t* sidx, int32_t* woff, int32_t* nw, unsigned long long* ctr) {
+                             int32_t* sidx, int32_t* woff, int32_t* nw, unsigned long long* ctr,
+                             const int32_t* __restrict__ child0, const int32_t* __restrict__ bstart,
+                             const int32_t* __restrict__ bcount, int2* srng) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b == 0) ctr[0] = (unsigned long long)ninst;
     if (b >= ninst) return;
     const int r = (int)inst_box_off[b];
+    if (child0[r] < 0) srng[b] = make_int2(bstart[r], bcount[r]);  // a one-level instance: its P2P source range
     soff[r] = b;  // the first ninst strong entries are the roots themselves
     ns[r] = 1;
     sidx[b] = r;
@@ -612,7 +615,7 @@ __global__ void __launch_bounds__(256) k_lists_level(
     int32_t* soff, int32_t* ns, int32_t* sidx, int32_t* woff, int32_t* nw, int32_t* widx,
     const float4* __restrict__ chl, const float* __restrict__ rad32, const double2* __restrict__ center,
     const double* __restrict__ radius, double theta, unsigned long long* ctr, long long scap, long long wcap,
-    unsigned* status) {
+    unsigned* status, const int32_t* __restrict__ bstart, const int32_t* __restrict__ bcount, int2* srng) {
     const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (w >= cnt) return;
@@ -651,6 +654,7 @@ __global__ void __launch_bounds__(256) k_lists_level(
     }
     if (!fs || !fw) return;
     const unsigned lt = lanemask_lt();
+    const bool leaf = child0[b] < 0;  // leaves also record the point range of each strong entry (P2P sources)
     int rs = 0, rw = 0;
     for (int c0 = 0; c0 < m; c0 += 32) {
         const int j = c0 + lane;
@@ -662,7 +666,11 @@ __global__ void __launch_bounds__(256) k_lists_level(
         }
         const unsigned bs = __ballot_sync(0xffffffffu, v && !sep);
         const unsigned bw = __ballot_sync(0xffffffffu, v && sep);
-        if (v && !sep) sidx[os + rs + __popc(bs & lt)] = h;
+        if (v && !sep) {
+            const size_t q = os + rs + __popc(bs & lt);
+            sidx[q] = h;
+            if (leaf) srng[q] = make_int2(bstart[h], bcount[h]);
+        }
         if (v && sep) widx[ow + rw + __popc(bw & lt)] = h;
         rs += __popc(bs);
         rw += __popc(bw);
@@ -801,6 +809,7 @@ fmm_status alloc_build(Tree& t) {
 fmm_status alloc_lists(Tree& t) {
     fmm_status st;
     if ((st = dalloc(&t.d_sidx, (size_t)t.scap_tot))) return st;
+    if ((st = dalloc(&t.d_srng, (size_t)t.scap_tot))) return st;
     if ((st = dalloc(&t.d_widx, (size_t)t.wcap_tot))) return st;
     if ((st = dalloc(&t.d_p2p_items, (size_t)t.p2p_cap))) return st;
     if ((st = dalloc(&t.d_m2l_items, (size_t)t.m2l_cap))) return st;
@@ -863,12 +872,13 @@ fmm_status run_lists(Tree& t, cudaStream_t s) {
     unsigned long long* ctr = reinterpret_cast<unsigned long long*>(t.d_status) + 1;
     FMM_CUDA(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), s));
     k_lists_root<<<nblk(t.ninst, 128), 128, 0, s>>>(t.d_inst_boxoff, t.ninst, t.d_soff, t.d_ns, t.d_sidx, t.d_woff,
-                                                    t.d_nw, ctr);
+                                                    t.d_nw, ctr, t.d_child0, t.d_bstart, t.d_bcount, t.d_srng);
     for (int l = 1; l < t.Lmax; ++l) {
         const LevelList& Ll = t.level_boxes[l];
         k_lists_level<<<nblk((int64_t)Ll.count * 32, 256), 256, 0, s>>>(
             Ll.d_ids, Ll.count, t.d_parent, t.d_child0, t.d_soff, t.d_ns, t.d_sidx, t.d_woff, t.d_nw, t.d_widx,
-            t.d_chl, t.d_rad32, t.d_center, t.d_radius, t.theta, ctr, t.scap_tot, t.wcap_tot, t.d_status);
+            t.d_chl, t.d_rad32, t.d_center, t.d_radius, t.theta, ctr, t.scap_tot, t.wcap_tot, t.d_status,
+            t.d_bstart, t.d_bcount, t.d_srng);
     }
     k_items<<<nblk(t.nbox, 128), 128, 0, s>>>((int)t.nbox, t.d_child0, t.d_bcount, t.d_ns, t.d_nw, ctr,
                                               t.d_p2p_items, t.d_leaf_items, t.p2p_cap, t.d_m2l_items, t.d_box_m2l,

@@ -99,7 +99,9 @@ static fmm_status build_all(Tree& t, const double* d_xy, cudaStream_t s) {
     for (int attempt = 0; attempt < 16; ++attempt) {
         if ((st = run_lists(t, s))) return st;
         unsigned long long hbuf[5] = {0, 0, 0, 0, 0};
+        unsigned long long lb[2 * kMaxLevels + 4];
         FMM_CUDA(cudaMemcpyAsync(hbuf, t.d_status, sizeof(hbuf), cudaMemcpyDeviceToHost, s));
+        FMM_CUDA(cudaMemcpyAsync(lb, t.d_lvl_base, sizeof(lb), cudaMemcpyDeviceToHost, s));
         FMM_CUDA(cudaStreamSynchronize(s));
         const unsigned bits = (unsigned)(hbuf[0] & 0xffffffffu);
         if (bits & ST_NONFINITE) {
@@ -112,14 +114,19 @@ static fmm_status build_all(Tree& t, const double* d_xy, cudaStream_t s) {
         }
         const bool ovl = bits & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW);
         if (!ovl && !(bits & ST_ITEM_OVERFLOW)) {
-            for (int i = 0; i < 4; ++i) t.h_counts[i] = hbuf[1 + i];
+            t.h_counts[0] = lb[t.Lmax];
+            t.h_counts[1] = lb[kMaxLevels + t.Lmax];
+            t.h_counts[2] = hbuf[3];
+            t.h_counts[3] = hbuf[4];
             return FMM_OK;
         }
-        auto grow = [](long long cur, unsigned long long need) {
-            return std::max<long long>(2 * cur, (long long)(need + need / 4 + 1024));
+        const unsigned long long* need = lb + 2 * kMaxLevels;
+        auto grow = [](long long cur, unsigned long long want) {
+            return std::max<long long>(2 * cur, (long long)(want + want / 4 + 1024));
         };
-        if (bits & ST_STRONG_OVERFLOW) t.scap_tot = grow(t.scap_tot, hbuf[1]);
-        if (bits & ST_WEAK_OVERFLOW) t.wcap_tot = grow(t.wcap_tot, hbuf[2]);
+        if (need[0] > (unsigned long long)t.cand_cap) t.cand_cap = grow(t.cand_cap, need[0]);
+        if (need[1] > (unsigned long long)t.scap_tot) t.scap_tot = grow(t.scap_tot, need[1]);
+        if (need[2] > (unsigned long long)t.wcap_tot) t.wcap_tot = grow(t.wcap_tot, need[2]);
         if (!ovl && (bits & ST_ITEM_OVERFLOW)) {
             if ((long long)hbuf[3] > t.p2p_cap) t.p2p_cap = (long long)(hbuf[3] + hbuf[3] / 4 + 1024);
             if ((long long)hbuf[4] > t.m2l_cap) t.m2l_cap = (long long)(hbuf[4] + hbuf[4] / 4 + 1024);
@@ -155,7 +162,8 @@ static void release(Tree* t) {
                     t->d_inst_boxoff, t->d_leaf_start, t->d_X2, t->d_Y2, t->d_sideX, t->d_sideY, t->d_tile_cnt,
                     t->d_tile_pre, t->d_seg_lc, t->d_sort_hist, t->d_sort_tot, t->d_sort_off, t->d_perm,
                     t->d_leaf_of, t->d_pts, t->d_pos4, t->d_center, t->d_radius, t->d_rho, t->d_chl, t->d_rho32,
-                    t->d_rad32, t->d_soff, t->d_ns, t->d_sidx, t->d_srng, t->d_woff, t->d_nw, t->d_widx, t->d_p2p_items,
+                    t->d_rad32, t->d_soff, t->d_ns, t->d_sidx, t->d_srng, t->d_sowner, t->d_cflags, t->d_ltile_s,
+                    t->d_ltile_w, t->d_lpre_s, t->d_lpre_w, t->d_lvl_base, t->d_woff, t->d_nw, t->d_widx, t->d_p2p_items,
                     t->d_m2l_items, t->d_leaf_items, t->d_box_m2l, t->d_status, t->d_gam, t->d_near, t->d_M64,
                     t->d_M32, t->d_Lm2l, t->d_L64, t->d_L32, t->d_p2p_part, t->d_m2l_part};
     for (void* p : ptrs)
@@ -392,7 +400,7 @@ fmm_status fmm_get_tree_info(const fmm_tree* h, fmm_tree_info* out) {
     out->m2l_items = (int64_t)t.h_counts[3];
     out->autotune_nlevels = t.tune.accepted;
     const int lv = t.Lmax - 1;
-    out->launches_build = 29 + 10 * lv + (t.ninst > 1 ? 7 : 0);
+    out->launches_build = 29 + 13 * lv + (t.ninst > 1 ? 7 : 0);
     out->launches_eval = 5 + 2 * lv;
     return FMM_OK;
 }

@@ -25,6 +25,7 @@ enum : unsigned {
 // Work-item sizes: P2P items hold about this many source points; M2L items at
 // most this many weak pairs.
 constexpr int kP2PItemSources = 2048;
+constexpr int kMaxLevels = 16;
 constexpr int kM2LItemPairs = 64;
 
 // Partition tile: 256 threads x 8 consecutive positions.
@@ -107,6 +108,11 @@ struct Tree {
     // coupling lists in CSR form: box b's strong list is sidx[soff[b] .. soff[b]+ns[b])
     int32_t *d_soff = nullptr, *d_ns = nullptr, *d_sidx = nullptr;
     int2* d_srng = nullptr;        // leaves: (first point, count) of each strong entry, parallel to sidx
+    int32_t* d_sowner = nullptr;   // box of each strong entry, parallel to sidx
+    uint8_t* d_cflags = nullptr;   // candidate flags of the level being built
+    int32_t *d_ltile_s = nullptr, *d_ltile_w = nullptr, *d_lpre_s = nullptr, *d_lpre_w = nullptr;
+    unsigned long long* d_lvl_base = nullptr;  // [0,16) strong / [16,32) weak level offsets, [32,36) sizes needed
+    long long cand_cap = 0;
     int32_t *d_woff = nullptr, *d_nw = nullptr, *d_widx = nullptr;
     long long scap_tot = 0, wcap_tot = 0;
     // work items (see k_items)

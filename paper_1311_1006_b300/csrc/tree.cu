@@ -557,21 +557,37 @@ __global__ void k_finalize(const int32_t* __restrict__ Y, int n, const double2* 
 }
 
 // ================================================================== lists
+//
+// Level by level.  The candidates of level l are the pairs (child c of parent
+// P, child c' of the j-th strong entry Q of P), enumerated as
+//     g = 16*(soff(P) - base(l-1)) + c*4*ns(P) + 4*j + c'
+// so that the candidates of one child box are contiguous and in (j, c')
+// order.  Every candidate is classified (strong / weak / none, the last for
+// entries of boxes without children), the flags are scanned over tiles, and a
+// scatter writes the lists in candidate order.  The strong entries of level l
+// are stored contiguously after those of level l-1; `owner` records the box of
+// every strong entry, which decodes the next level's candidates.
 
 __global__ void k_lists_root(const int64_t* __restrict__ inst_box_off, int ninst, int32_t* soff, int32_t* ns,
-                             int32_t* sidx, int32_t* woff, int32_t* nw, unsigned long long* ctr,
-                             const int32_t* __restrict__ child0, const int32_t* __restrict__ bstart,
-                             const int32_t* __restrict__ bcount, int2* srng) {
+                             int32_t* sidx, int32_t* sowner, int32_t* woff, int32_t* nw,
+                             unsigned long long* lvl_base, const int32_t* __restrict__ child0,
+                             const int32_t* __restrict__ bstart, const int32_t* __restrict__ bcount, int2* srng) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b == 0) ctr[0] = (unsigned long long)ninst;
+    if (b == 0) {
+        lvl_base[0] = 0;             // strong entries of level 0 start at 0
+        lvl_base[1] = ninst;         // ... and level 1 after them
+        lvl_base[kMaxLevels + 0] = 0;  // weak entries
+        lvl_base[kMaxLevels + 1] = 0;
+    }
     if (b >= ninst) return;
     const int r = (int)inst_box_off[b];
-    if (child0[r] < 0) srng[b] = make_int2(bstart[r], bcount[r]);  // a one-level instance: its P2P source range
-    soff[r] = b;  // the first ninst strong entries are the roots themselves
+    soff[r] = b;
     ns[r] = 1;
     sidx[b] = r;
+    sowner[b] = r;
     woff[r] = 0;
     nw[r] = 0;
+    if (child0[r] < 0) srng[b] = make_int2(bstart[r], bcount[r]);  // a one-level instance: its P2P sources
 }
 
 // eq (2.3) in FP64: R + theta*r <= theta*d, with d > 0 required.
@@ -603,78 +619,207 @@ __device__ __forceinline__ bool well_separated_fast(int a, int b, const float4* 
     return well_separated(center[a], radius[a], center[b], radius[b], theta);
 }
 
-// Coupling of one level (Sec. 2.1), one warp per box: the candidates are the
-// children of the parent's strongly coupled boxes; a candidate is weak when
-// well separated, else strong (a box is always strong with itself).  The warp
-// counts, reserves its CSR ranges with one atomic each, then writes the
-// entries in candidate order.  When a reservation passes the capacity the
-// counts are still recorded (the host learns the size it needs) but nothing
-// is written, and every later level is skipped.
-__global__ void __launch_bounds__(256) k_lists_level(
-    const int32_t* __restrict__ ids, int cnt, const int32_t* __restrict__ parent, const int32_t* __restrict__ child0,
-    int32_t* soff, int32_t* ns, int32_t* sidx, int32_t* woff, int32_t* nw, int32_t* widx,
-    const float4* __restrict__ chl, const float* __restrict__ rad32, const double2* __restrict__ center,
-    const double* __restrict__ radius, double theta, unsigned long long* ctr, long long scap, long long wcap,
-    unsigned* status, const int32_t* __restrict__ bstart, const int32_t* __restrict__ bcount, int2* srng) {
-    const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (w >= cnt) return;
+struct Cand {
+    int b, h;       // child box, candidate box
+    bool first;     // first candidate of b
+    bool last;      // last candidate of b
+    bool valid;     // the parent has children
+};
+
+// Decode candidate g of level l (see the enumeration above).
+__device__ __forceinline__ Cand decode_cand(long long g, long long base_prev, const int32_t* __restrict__ sowner,
+                                            const int32_t* __restrict__ soff, const int32_t* __restrict__ ns,
+                                            const int32_t* __restrict__ sidx, const int32_t* __restrict__ child0) {
+    Cand c;
+    const int P = sowner[base_prev + (g >> 4)];
+    const int c0 = child0[P];
+    c.valid = c0 >= 0;
+    if (!c.valid) {
+        c.b = c.h = 0;
+        c.first = c.last = false;
+        return c;
+    }
+    const int n = ns[P];
+    const long long e0 = (long long)soff[P] - base_prev;
+    const int r = (int)(g - 16 * e0);
+    const int q = 4 * n;
+    const int ci = r / q, rem = r - ci * q;
+    const int j = rem >> 2, cp = rem & 3;
+    c.b = c0 + ci;
+    c.h = child0[sidx[soff[P] + j]] + cp;
+    c.first = rem == 0;
+    c.last = rem == q - 1;
+    return c;
+}
+
+constexpr int kLThreads = 256, kLItems = 8, kLTile = kLThreads * kLItems;
+
+// Pass 1: classify every candidate (flag 0 none, 1 strong, 2 weak) and count
+// strong / weak per tile.
+__global__ void __launch_bounds__(kLThreads) k_lists_classify(
+    int l, const unsigned long long* __restrict__ lvl_base, const int32_t* __restrict__ sowner,
+    const int32_t* __restrict__ soff, const int32_t* __restrict__ ns, const int32_t* __restrict__ sidx,
+    const int32_t* __restrict__ child0, const float4* __restrict__ chl, const float* __restrict__ rad32,
+    const double2* __restrict__ center, const double* __restrict__ radius, double theta, uint8_t* flags,
+    long long flags_cap, int32_t* tile_s, int32_t* tile_w, long long tiles_cap, unsigned* status) {
+    __shared__ int ws[32], ww[32];
     if (*((volatile unsigned*)status) & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW)) return;
-    const int b = ids[w];
-    const int P = parent[b];
-    const int m = 4 * ns[P];
-    const int32_t* ps = sidx + soff[P];
+    const long long base_prev = (long long)lvl_base[l - 1];
+    const long long ncand = 16 * ((long long)lvl_base[l] - base_prev);
+    const long long ntiles = (ncand + kLTile - 1) / kLTile;
+    if (ncand > flags_cap || ntiles > tiles_cap) return;  // the host sized these from the last build; checked in pass 2
     const float th32 = (float)theta;
-    int cs = 0, cw = 0;
-    for (int c0 = 0; c0 < m; c0 += 32) {
-        const int j = c0 + lane;
-        bool v = j < m, sep = false;
-        if (v) {
-            const int h = child0[ps[j >> 2]] + (j & 3);
-            sep = (h != b) && well_separated_fast(b, h, chl, rad32, center, radius, th32, theta);
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const long long g0 = t * kLTile + (long long)threadIdx.x * kLItems;
+        int cs = 0, cw = 0;
+        uint32_t packed[2] = {0, 0};
+#pragma unroll
+        for (int k = 0; k < kLItems; ++k) {
+            const long long g = g0 + k;
+            int f = 0;
+            if (g < ncand) {
+                const Cand c = decode_cand(g, base_prev, sowner, soff, ns, sidx, child0);
+                if (c.valid) {
+                    const bool sep =
+                        (c.h != c.b) && well_separated_fast(c.b, c.h, chl, rad32, center, radius, th32, theta);
+                    f = sep ? 2 : 1;
+                }
+            }
+            cs += f == 1;
+            cw += f == 2;
+            packed[k >> 2] |= (uint32_t)f << (8 * (k & 3));
         }
-        cs += __popc(__ballot_sync(0xffffffffu, v && !sep));
-        cw += __popc(__ballot_sync(0xffffffffu, v && sep));
-    }
-    unsigned long long os = 0, ow = 0;
-    if (lane == 0) {
-        os = atomicAdd(ctr + 0, (unsigned long long)cs);
-        ow = atomicAdd(ctr + 1, (unsigned long long)cw);
-    }
-    os = __shfl_sync(0xffffffffu, os, 0);
-    ow = __shfl_sync(0xffffffffu, ow, 0);
-    const bool fs = (long long)(os + cs) <= scap, fw = (long long)(ow + cw) <= wcap;
-    if (lane == 0) {
-        soff[b] = (int32_t)os;
-        ns[b] = cs;
-        woff[b] = (int32_t)ow;
-        nw[b] = cw;
-        if (!fs) atomicOr(status, ST_STRONG_OVERFLOW);
-        if (!fw) atomicOr(status, ST_WEAK_OVERFLOW);
-    }
-    if (!fs || !fw) return;
-    const unsigned lt = lanemask_lt();
-    const bool leaf = child0[b] < 0;  // leaves also record the point range of each strong entry (P2P sources)
-    int rs = 0, rw = 0;
-    for (int c0 = 0; c0 < m; c0 += 32) {
-        const int j = c0 + lane;
-        bool v = j < m, sep = false;
-        int h = 0;
-        if (v) {
-            h = child0[ps[j >> 2]] + (j & 3);
-            sep = (h != b) && well_separated_fast(b, h, chl, rad32, center, radius, th32, theta);
+        if (g0 < ncand) {
+            uint2* fp = reinterpret_cast<uint2*>(flags + g0);  // g0 is a multiple of 8
+            *fp = make_uint2(packed[0], packed[1]);
         }
-        const unsigned bs = __ballot_sync(0xffffffffu, v && !sep);
-        const unsigned bw = __ballot_sync(0xffffffffu, v && sep);
-        if (v && !sep) {
-            const size_t q = os + rs + __popc(bs & lt);
-            sidx[q] = h;
-            if (leaf) srng[q] = make_int2(bstart[h], bcount[h]);
+        int tot_s, tot_w;
+        (void)block_excl_scan(cs, ws, tot_s);
+        (void)block_excl_scan(cw, ww, tot_w);
+        if (threadIdx.x == 0) {
+            tile_s[t] = tot_s;
+            tile_w[t] = tot_w;
         }
-        if (v && sep) widx[ow + rw + __popc(bw & lt)] = h;
-        rs += __popc(bs);
-        rw += __popc(bw);
     }
+}
+
+// Pass 2 (one block): tile offsets, level totals, capacity checks.
+__global__ void __launch_bounds__(1024) k_lists_scan(int l, unsigned long long* lvl_base,
+                                                     const int32_t* __restrict__ tile_s,
+                                                     const int32_t* __restrict__ tile_w, int32_t* pre_s,
+                                                     int32_t* pre_w, long long flags_cap, long long tiles_cap,
+                                                     long long scap, long long wcap, unsigned long long* need,
+                                                     unsigned* status) {
+    __shared__ int wsum[32];
+    if (*((volatile unsigned*)status) & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW)) return;
+    const long long base_prev = (long long)lvl_base[l - 1];
+    const long long ncand = 16 * ((long long)lvl_base[l] - base_prev);
+    const long long ntiles = (ncand + kLTile - 1) / kLTile;
+    if (ncand > flags_cap || ntiles > tiles_cap) {
+        if (threadIdx.x == 0) {
+            atomicMax(need + 0, (unsigned long long)ncand);
+            atomicOr(status, ST_STRONG_OVERFLOW);
+        }
+        return;
+    }
+    long long cs = 0, cw = 0;
+    for (long long c0 = 0; c0 < ntiles; c0 += 1024) {
+        const long long i = c0 + threadIdx.x;
+        const int vs = i < ntiles ? tile_s[i] : 0;
+        const int vw = i < ntiles ? tile_w[i] : 0;
+        int ts, tw;
+        const int es = block_excl_scan(vs, wsum, ts);
+        const int ew = block_excl_scan(vw, wsum, tw);
+        if (i < ntiles) {
+            pre_s[i] = (int)(cs + es);
+            pre_w[i] = (int)(cw + ew);
+        }
+        cs += ts;
+        cw += tw;
+    }
+    if (threadIdx.x == 0) {
+        const long long bs = (long long)lvl_base[l], bw = (long long)lvl_base[kMaxLevels + l];
+        lvl_base[l + 1] = (unsigned long long)(bs + cs);
+        lvl_base[kMaxLevels + l + 1] = (unsigned long long)(bw + cw);
+        if (bs + cs > scap) {
+            atomicMax(need + 1, (unsigned long long)(bs + cs));
+            atomicOr(status, ST_STRONG_OVERFLOW);
+        }
+        if (bw + cw > wcap) {
+            atomicMax(need + 2, (unsigned long long)(bw + cw));
+            atomicOr(status, ST_WEAK_OVERFLOW);
+        }
+    }
+}
+
+// Pass 3: scatter in candidate order; the first candidate of a box writes its
+// list offsets, the last one its list ends (turned into lengths by pass 4).
+__global__ void __launch_bounds__(kLThreads) k_lists_scatter(
+    int l, const unsigned long long* __restrict__ lvl_base, const int32_t* __restrict__ sowner,
+    int32_t* __restrict__ soff, int32_t* __restrict__ ns, int32_t* __restrict__ sidx, int32_t* __restrict__ woff,
+    int32_t* __restrict__ nw, int32_t* __restrict__ widx, int32_t* __restrict__ sowner_out,
+    const int32_t* __restrict__ child0, const int32_t* __restrict__ bstart, const int32_t* __restrict__ bcount,
+    int2* __restrict__ srng, const uint8_t* __restrict__ flags, const int32_t* __restrict__ pre_s,
+    const int32_t* __restrict__ pre_w, unsigned* status) {
+    __shared__ int ws[32], ww[32];
+    if (*((volatile unsigned*)status) & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW)) return;
+    const long long base_prev = (long long)lvl_base[l - 1];
+    const long long bs = (long long)lvl_base[l], bw = (long long)lvl_base[kMaxLevels + l];
+    const long long ncand = 16 * (bs - base_prev);
+    const long long ntiles = (ncand + kLTile - 1) / kLTile;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const long long g0 = t * kLTile + (long long)threadIdx.x * kLItems;
+        uint2 fp = make_uint2(0, 0);
+        if (g0 < ncand) fp = *reinterpret_cast<const uint2*>(flags + g0);
+        int cs = 0, cw = 0;
+#pragma unroll
+        for (int k = 0; k < kLItems; ++k) {
+            const int f = (int)(((k < 4 ? fp.x : fp.y) >> (8 * (k & 3))) & 0xffu);
+            cs += f == 1;
+            cw += f == 2;
+        }
+        int tot_s, tot_w;
+        int ps = block_excl_scan(cs, ws, tot_s) + pre_s[t];
+        int pw = block_excl_scan(cw, ww, tot_w) + pre_w[t];
+        if (g0 >= ncand) continue;
+#pragma unroll
+        for (int k = 0; k < kLItems; ++k) {
+            const long long g = g0 + k;
+            if (g >= ncand) break;
+            const int f = (int)(((k < 4 ? fp.x : fp.y) >> (8 * (k & 3))) & 0xffu);
+            const Cand c = decode_cand(g, base_prev, sowner, soff, ns, sidx, child0);
+            if (!c.valid) continue;
+            if (c.first) {
+                soff[c.b] = (int32_t)(bs + ps);
+                woff[c.b] = (int32_t)(bw + pw);
+            }
+            if (f == 1) {
+                const long long q = bs + ps;
+                sidx[q] = c.h;
+                sowner_out[q] = c.b;
+                if (child0[c.b] < 0) srng[q] = make_int2(bstart[c.h], bcount[c.h]);
+                ++ps;
+            } else {
+                widx[bw + pw] = c.h;
+                ++pw;
+            }
+            if (c.last) {
+                ns[c.b] = (int32_t)(bs + ps);  // end; made a length in pass 4
+                nw[c.b] = (int32_t)(bw + pw);
+            }
+        }
+    }
+}
+
+// Pass 4: list ends -> lengths for the boxes of level l.
+__global__ void k_lists_len(const int32_t* __restrict__ ids, int cnt, const int32_t* __restrict__ soff,
+                            int32_t* ns, const int32_t* __restrict__ woff, int32_t* nw, unsigned* status) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= cnt) return;
+    if (*((volatile unsigned*)status) & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW)) return;
+    const int b = ids[q];
+    ns[b] -= soff[b];
+    nw[b] -= woff[b];
 }
 
 // Work items that bound the work of one warp / thread whatever the list
@@ -802,6 +947,10 @@ fmm_status alloc_build(Tree& t) {
     if (t.scap_tot < (long long)t.nbox * 16) t.scap_tot = (long long)t.nbox * 16;
     if (t.wcap_tot < (long long)t.nbox * 48) t.wcap_tot = (long long)t.nbox * 48;
     if (t.p2p_cap < t.nleaf * 2) t.p2p_cap = t.nleaf * 2;
+    if (t.cand_cap < t.nbox * 64) t.cand_cap = t.nbox * 64;
+    if (!t.d_lvl_base) {
+        if ((st = dalloc(&t.d_lvl_base, 2 * kMaxLevels + 8))) return st;
+    }
     if (t.m2l_cap < t.nbox * 2) t.m2l_cap = t.nbox * 2;
     return alloc_lists(t);
 }
@@ -809,7 +958,14 @@ fmm_status alloc_build(Tree& t) {
 fmm_status alloc_lists(Tree& t) {
     fmm_status st;
     if ((st = dalloc(&t.d_sidx, (size_t)t.scap_tot))) return st;
+    if ((st = dalloc(&t.d_sowner, (size_t)t.scap_tot))) return st;
     if ((st = dalloc(&t.d_srng, (size_t)t.scap_tot))) return st;
+    if ((st = dalloc(&t.d_cflags, (size_t)t.cand_cap + 16))) return st;
+    const size_t tiles = (size_t)(t.cand_cap / kLTile + 2);
+    if ((st = dalloc(&t.d_ltile_s, tiles))) return st;
+    if ((st = dalloc(&t.d_ltile_w, tiles))) return st;
+    if ((st = dalloc(&t.d_lpre_s, tiles))) return st;
+    if ((st = dalloc(&t.d_lpre_w, tiles))) return st;
     if ((st = dalloc(&t.d_widx, (size_t)t.wcap_tot))) return st;
     if ((st = dalloc(&t.d_p2p_items, (size_t)t.p2p_cap))) return st;
     if ((st = dalloc(&t.d_m2l_items, (size_t)t.m2l_cap))) return st;
@@ -870,15 +1026,28 @@ fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s) {
 
 fmm_status run_lists(Tree& t, cudaStream_t s) {
     unsigned long long* ctr = reinterpret_cast<unsigned long long*>(t.d_status) + 1;
+    unsigned long long* need = t.d_lvl_base + 2 * kMaxLevels;
     FMM_CUDA(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), s));
-    k_lists_root<<<nblk(t.ninst, 128), 128, 0, s>>>(t.d_inst_boxoff, t.ninst, t.d_soff, t.d_ns, t.d_sidx, t.d_woff,
-                                                    t.d_nw, ctr, t.d_child0, t.d_bstart, t.d_bcount, t.d_srng);
+    FMM_CUDA(cudaMemsetAsync(need, 0, 4 * sizeof(unsigned long long), s));
+    k_lists_root<<<nblk(t.ninst, 128), 128, 0, s>>>(t.d_inst_boxoff, t.ninst, t.d_soff, t.d_ns, t.d_sidx, t.d_sowner,
+                                                    t.d_woff, t.d_nw, t.d_lvl_base, t.d_child0, t.d_bstart,
+                                                    t.d_bcount, t.d_srng);
+    const long long tiles_cap = t.cand_cap / kLTile + 2;
+    const int grid = t.num_sms * 8;
     for (int l = 1; l < t.Lmax; ++l) {
+        k_lists_classify<<<grid, kLThreads, 0, s>>>(l, t.d_lvl_base, t.d_sowner, t.d_soff, t.d_ns, t.d_sidx,
+                                                    t.d_child0, t.d_chl, t.d_rad32, t.d_center, t.d_radius, t.theta,
+                                                    t.d_cflags, t.cand_cap, t.d_ltile_s, t.d_ltile_w, tiles_cap,
+                                                    t.d_status);
+        k_lists_scan<<<1, 1024, 0, s>>>(l, t.d_lvl_base, t.d_ltile_s, t.d_ltile_w, t.d_lpre_s, t.d_lpre_w,
+                                        t.cand_cap, tiles_cap, t.scap_tot, t.wcap_tot, need, t.d_status);
+        k_lists_scatter<<<grid, kLThreads, 0, s>>>(l, t.d_lvl_base, t.d_sowner, t.d_soff, t.d_ns, t.d_sidx,
+                                                   t.d_woff, t.d_nw, t.d_widx, t.d_sowner, t.d_child0, t.d_bstart,
+                                                   t.d_bcount, t.d_srng, t.d_cflags, t.d_lpre_s, t.d_lpre_w,
+                                                   t.d_status);
         const LevelList& Ll = t.level_boxes[l];
-        k_lists_level<<<nblk((int64_t)Ll.count * 32, 256), 256, 0, s>>>(
-            Ll.d_ids, Ll.count, t.d_parent, t.d_child0, t.d_soff, t.d_ns, t.d_sidx, t.d_woff, t.d_nw, t.d_widx,
-            t.d_chl, t.d_rad32, t.d_center, t.d_radius, t.theta, ctr, t.scap_tot, t.wcap_tot, t.d_status,
-            t.d_bstart, t.d_bcount, t.d_srng);
+        k_lists_len<<<nblk(Ll.count, 256), 256, 0, s>>>(Ll.d_ids, Ll.count, t.d_soff, t.d_ns, t.d_woff, t.d_nw,
+                                                        t.d_status);
     }
     k_items<<<nblk(t.nbox, 128), 128, 0, s>>>((int)t.nbox, t.d_child0, t.d_bcount, t.d_ns, t.d_nw, ctr,
                                               t.d_p2p_items, t.d_leaf_items, t.p2p_cap, t.d_m2l_items, t.d_box_m2l,

@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <utility>
 
 #include "fmm_internal.cuh"
 
@@ -207,6 +208,37 @@ __global__ void __launch_bounds__(128) k_m2m(const int32_t* __restrict__ parents
 // One thread per target box (every level in one launch), looping over the
 // box's weak list.  FP32 with FP32 accumulation.  Root boxes (no parent) also
 // seed the FP64 local array, which L2L reads for level 1.
+// Binomial coefficients as compile-time constants: the unrolled M2L applies
+// C(k+l, l) as FFMA immediates (no constant-bank loads in the inner loop).
+template <int N, int K>
+struct Bn {
+    static constexpr float v = (float)binom_d(N, K);
+};
+
+template <int P, int K, int... L>
+__device__ __forceinline__ void m2l_row(float2 (&w)[P], const float2 v, std::integer_sequence<int, L...>) {
+    ((w[L].x = fmaf(Bn<K + L, L>::v, v.x, w[L].x)), ...);
+    ((w[L].y = fmaf(Bn<K + L, L>::v, v.y, w[L].y)), ...);
+}
+
+template <int P, int K>
+__device__ __forceinline__ void m2l_step(float2 (&w)[P], const float4 (&aa)[(P + 1) / 2], float2& ap,
+                                         const float2 alpha) {
+    const float4 q = aa[K / 2];
+    const float2 a = (K & 1) ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
+    const float2 v = cmul(ap, a);
+    if (K + 1 < P) ap = cmul(ap, alpha);
+    m2l_row<P, K>(w, v, std::make_integer_sequence<int, P>{});
+}
+
+// w_l = sum_k C(k+l, l) alpha^k a_k for l < P (a_k held in registers)
+template <int P, int... K>
+__device__ __forceinline__ void m2l_apply(float2 (&w)[P], const float4 (&aa)[(P + 1) / 2], const float2 alpha,
+                                          std::integer_sequence<int, K...>) {
+    float2 ap = make_float2(1.f, 0.f);
+    (m2l_step<P, K>(w, aa, ap, alpha), ...);
+}
+
 template <int P>
 __global__ void __launch_bounds__(128) k_m2l32(const int4* __restrict__ items,
                                                const unsigned long long* __restrict__ nitems,
@@ -237,27 +269,11 @@ __global__ void __launch_bounds__(128) k_m2l32(const int4* __restrict__ items,
         float2 w[P];
 #pragma unroll
         for (int l = 0; l < P; ++l) w[l] = make_float2(0.f, 0.f);
+        float4 aa[(P + 1) / 2];
         const float4* src = reinterpret_cast<const float4*>(M32 + (size_t)s * PS);
-        float2 ap = make_float2(1.f, 0.f);
 #pragma unroll
-        for (int k2 = 0; k2 < (P + 1) / 2; ++k2) {
-            const float4 aa = src[k2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int k = 2 * k2 + h;
-                if (k < P) {
-                    const float2 a = h ? make_float2(aa.z, aa.w) : make_float2(aa.x, aa.y);
-                    const float2 v = cmul(ap, a);
-                    ap = cmul(ap, alpha);
-#pragma unroll
-                    for (int l = 0; l < P; ++l) {
-                        const float cb = c_binom.f[k + l][l];
-                        w[l].x = fmaf(cb, v.x, w[l].x);
-                        w[l].y = fmaf(cb, v.y, w[l].y);
-                    }
-                }
-            }
-        }
+        for (int k2 = 0; k2 < (P + 1) / 2; ++k2) aa[k2] = src[k2];
+        m2l_apply<P>(w, aa, alpha, std::make_integer_sequence<int, P>{});
         float2 g = u;
 #pragma unroll
         for (int l = 0; l < P; ++l) {

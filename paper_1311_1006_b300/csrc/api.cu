@@ -159,7 +159,7 @@ static void release(Tree* t) {
     if (!t) return;
     invalidate_graph(*t);
     void* ptrs[] = {t->d_bstart, t->d_bcount, t->d_parent, t->d_child0, t->d_inst, t->d_inst_ptoff,
-                    t->d_inst_boxoff, t->d_leaf_start, t->d_X2, t->d_Y2, t->d_sideX, t->d_sideY, t->d_tile_cnt,
+                    t->d_inst_boxoff, t->d_leaf_start, t->d_inst_levels, t->d_loc, t->d_X2, t->d_Y2, t->d_sideX, t->d_sideY, t->d_tile_cnt,
                     t->d_tile_pre, t->d_seg_lc, t->d_sort_hist, t->d_sort_tot, t->d_sort_off, t->d_perm,
                     t->d_leaf_of, t->d_pts, t->d_pos4, t->d_center, t->d_radius, t->d_rho, t->d_chl, t->d_rho32,
                     t->d_rad32, t->d_soff, t->d_ns, t->d_sidx, t->d_srng, t->d_sowner, t->d_cflags, t->d_ltile_s,
@@ -400,7 +400,8 @@ fmm_status fmm_get_tree_info(const fmm_tree* h, fmm_tree_info* out) {
     out->m2l_items = (int64_t)t.h_counts[3];
     out->autotune_nlevels = t.tune.accepted;
     const int lv = t.Lmax - 1;
-    out->launches_build = 29 + 13 * lv + (t.ninst > 1 ? 7 : 0);
+    const int lg = std::min(t.l0, lv);
+    out->launches_build = 29 + 4 * lv + 9 * lg + (lg < lv ? 1 : 0) + (t.ninst > 1 ? 7 : 0);
     out->launches_eval = 5 + 2 * lv;
     return FMM_OK;
 }

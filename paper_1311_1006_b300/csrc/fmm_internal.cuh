@@ -26,6 +26,7 @@ enum : unsigned {
 // most this many weak pairs.
 constexpr int kP2PItemSources = 2048;
 constexpr int kMaxLevels = 16;
+constexpr int kSubMax = 4096;  // largest box whose remaining splits one CTA performs in shared memory
 constexpr int kM2LItemPairs = 64;
 
 // Partition tile: 256 threads x 8 consecutive positions.
@@ -82,6 +83,8 @@ struct Tree {
     LevelList leaves;
     std::vector<SegTable> seg_x, seg_y;    // per level l < Lmax-1
     int64_t* d_inst_ptoff = nullptr;       // ninst+1
+    int32_t* d_inst_levels = nullptr;      // ninst
+    int l0 = 0;                            // first level split inside one CTA per box
     int64_t* d_inst_boxoff = nullptr;      // ninst+1 (root box id of each instance)
     int32_t* d_leaf_start = nullptr;       // nleaf+1: first sorted position of each leaf
 
@@ -90,6 +93,7 @@ struct Tree {
     int32_t* d_vals[4] = {nullptr, nullptr, nullptr, nullptr};
     int32_t *d_X2 = nullptr, *d_Y2 = nullptr;
     uint8_t *d_sideX = nullptr, *d_sideY = nullptr;
+    int32_t* d_loc = nullptr;  // input index -> local id inside a subtree CTA
     int32_t *d_tile_cnt = nullptr, *d_tile_pre = nullptr, *d_seg_lc = nullptr;
     int32_t *d_sort_hist = nullptr, *d_sort_tot = nullptr, *d_sort_off = nullptr;
     int64_t segs_cap = 0;

@@ -163,6 +163,17 @@ fmm_status build_shape(Tree& t) {
         if ((st = upload(&t.seg_y[l].d_nzero, yz))) return st;
     }
     t.segs_cap = maxK;
+    // first level whose splitting boxes all fit one CTA of the subtree kernel
+    t.l0 = t.Lmax - 1;
+    for (int l = 0; l + 1 < t.Lmax; ++l) {
+        int mx = 0;
+        for (int32_t g : lvl_par[l]) mx = std::max(mx, (int)t.h_bcount[g]);
+        if (mx <= kSubMax) {
+            t.l0 = l;
+            break;
+        }
+    }
+    if ((st = upload(&t.d_inst_levels, t.inst_levels))) return st;
     return FMM_OK;
 }
 
@@ -532,6 +543,192 @@ __global__ void k_geom(const int32_t* __restrict__ ids, int cnt, const int32_t* 
     const float hx = __double2float_rn(ex), hy = __double2float_rn(ey);
     chl[b] = make_float4(hx, hy, __double2float_rn(__dsub_rn(ex, (double)hx)),
                          __double2float_rn(__dsub_rn(ey, (double)hy)));
+}
+
+// ============================================== subtree splits in one CTA
+//
+// From level l0 on every box holds at most kSubMax points, so one CTA takes a
+// box of level l0 and performs all of its remaining median splits in shared
+// memory: the x- and y-lists become arrays of 16-bit local ids (local id =
+// position in the box's x-list), the side flags live in shared memory, and
+// each stable partition is a block-wide scan.  Geometry of every new box is
+// computed on the way; at the end the box's leaf-ordered list of input
+// indices is written back over its part of the global y-list.
+
+constexpr int kSubThreads = 256;
+constexpr int kSubItems = kSubMax / kSubThreads;
+constexpr int kSubSegs = 2048;       // segments (half boxes) per split stage
+
+__device__ __forceinline__ void box_geometry(int b, double x0, double x1, double y0, double y1,
+                                             const double2* __restrict__ center_root_src, int root,
+                                             double2* center, double* radius, double* rho, float4* chl,
+                                             float* rho32, float* rad32) {
+    const double cx = __dmul_rn(0.5, __dadd_rn(x0, x1));
+    const double cy = __dmul_rn(0.5, __dadd_rn(y0, y1));
+    const double dx = __dsub_rn(x1, x0), dy = __dsub_rn(y1, y0);
+    const double r = __dmul_rn(0.5, __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy))));
+    center[b] = make_double2(cx, cy);
+    radius[b] = r;
+    rad32[b] = __double2float_rn(r);
+    double ox = cx, oy = cy, rfloor = 0.0;
+    if (root >= 0) {
+        const double2 o = center_root_src[root];
+        ox = o.x;
+        oy = o.y;
+        rfloor = ldexp(radius[root], -24);
+    }
+    const double rs = r > rfloor ? r : rfloor;
+    const float r32 = rs >= 1e-30 ? __double2float_rn(rs) : 0.0f;
+    rho32[b] = r32;
+    rho[b] = (double)r32;
+    const double ex = __dsub_rn(cx, ox), ey = __dsub_rn(cy, oy);
+    const float hx = __double2float_rn(ex), hy = __double2float_rn(ey);
+    chl[b] = make_float4(hx, hy, __double2float_rn(__dsub_rn(ex, (double)hx)),
+                         __double2float_rn(__dsub_rn(ey, (double)hy)));
+}
+
+__device__ __forceinline__ int seg_of(const uint16_t* __restrict__ st, int nseg, int i) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (st[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Stable partition of lin (n local ids) by side[id] within the segments
+// st[0..nseg) (segment k keeps its first nz[k] zeros first).
+__device__ __forceinline__ void cta_partition(const uint16_t* lin, uint16_t* lout, const uint8_t* side, int n,
+                                              const uint16_t* st, const uint16_t* nz, int nseg, uint16_t* P,
+                                              int* wsum) {
+    const int i0 = threadIdx.x * kSubItems;
+    int f[kSubItems];
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < kSubItems; ++k) {
+        const int i = i0 + k;
+        f[k] = i < n ? side[lin[i]] : 0;
+        sum += f[k];
+    }
+    int total;
+    int acc = block_excl_scan(sum, wsum, total);
+#pragma unroll
+    for (int k = 0; k < kSubItems; ++k) {
+        if (i0 + k < n) P[i0 + k] = (uint16_t)acc;
+        acc += f[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kSubItems; ++k) {
+        const int i = i0 + k;
+        if (i >= n) break;
+        const int sgi = seg_of(st, nseg, i);
+        const int s0 = st[sgi];
+        const int ones = (int)P[i] - (int)P[s0];
+        const int dst = f[k] ? s0 + nz[sgi] + ones : s0 + (i - s0) - ones;
+        if (dst >= 0 && dst < n) lout[dst] = lin[i];
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSubThreads) k_subtree(
+    const int32_t* __restrict__ ids, int cnt, int l0, const int32_t* __restrict__ X, int32_t* __restrict__ Y,
+    const double2* __restrict__ xy, const int32_t* __restrict__ bstart, const int32_t* __restrict__ bcount,
+    const int32_t* __restrict__ inst, const int64_t* __restrict__ inst_box_off, const int32_t* __restrict__ inst_levels,
+    int32_t* __restrict__ loc, double2* center, double* radius, double* rho, float4* chl, float* rho32, float* rad32,
+    unsigned* status) {
+    __shared__ uint16_t buf[3][kSubMax];
+    __shared__ uint16_t P[kSubMax];
+    __shared__ uint8_t side[kSubMax];
+    __shared__ uint16_t st[kSubSegs], nz[kSubSegs];
+    __shared__ int wsum[32];
+    if (blockIdx.x >= cnt) return;
+    const int B = ids[blockIdx.x];
+    const int s = bstart[B], n = bcount[B];
+    if (n > kSubMax) {  // the host picks l0 so that this cannot happen
+        if (threadIdx.x == 0) atomicOr(status, ST_INTERNAL);
+        return;
+    }
+    const int ib = inst[B];
+    const int bo = (int)inst_box_off[ib];
+    const int Lb = inst_levels[ib];
+    long long off_l0 = 0, w = 1;
+    for (int q = 0; q < l0; ++q) {
+        off_l0 += w;
+        w *= 4;
+    }
+    const int iB = B - bo - (int)off_l0;
+    uint16_t* xl = buf[0];  // local ids in x-order within the current boxes
+    uint16_t* yl = buf[1];  // local ids in y-order within the current boxes
+    uint16_t* tp = buf[2];
+    for (int i = threadIdx.x; i < n; i += kSubThreads) {
+        loc[X[s + i]] = i;
+        xl[i] = (uint16_t)i;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kSubThreads) yl[i] = (uint16_t)loc[Y[s + i]];
+    __syncthreads();
+    long long off_l = off_l0, width = 1, lsz = w;  // level offset, subtree boxes and all boxes on level l
+    for (int l = l0; l + 1 < Lb; ++l) {
+        const int gb0 = bo + (int)off_l + iB * (int)width;  // first box of the subtree on level l
+        if (2 * width > kSubSegs) {  // cannot happen for boxes of <= kSubMax non-empty leaves
+            if (threadIdx.x == 0) atomicOr(status, ST_INTERNAL);
+            return;
+        }
+        // x-split: segments = boxes of level l
+        for (int k = threadIdx.x; k < width; k += kSubThreads) {
+            st[k] = (uint16_t)(bstart[gb0 + k] - s);
+            nz[k] = (uint16_t)(bcount[gb0 + k] / 2);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += kSubThreads) {
+            const int k = seg_of(st, (int)width, i);
+            side[xl[i]] = (uint8_t)((i - st[k]) >= nz[k]);
+        }
+        __syncthreads();
+        cta_partition(yl, tp, side, n, st, nz, (int)width, P, wsum);  // tp = new y-list
+        // y-split of every half: segments = half boxes
+        for (int k = threadIdx.x; k < width; k += kSubThreads) {
+            const int bs = bstart[gb0 + k] - s, bn = bcount[gb0 + k], nl = bn / 2;
+            st[2 * k] = (uint16_t)bs;
+            st[2 * k + 1] = (uint16_t)(bs + nl);
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < width; k += kSubThreads) {
+            const int bn = bcount[gb0 + k], nl = bn / 2;
+            nz[2 * k] = (uint16_t)(nl / 2);
+            nz[2 * k + 1] = (uint16_t)((bn - nl) / 2);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += kSubThreads) {
+            const int k = seg_of(st, 2 * (int)width, i);
+            side[tp[i]] = (uint8_t)((i - st[k]) >= nz[k]);
+        }
+        __syncthreads();
+        cta_partition(xl, yl, side, n, st, nz, 2 * (int)width, P, wsum);  // old y-list buffer = new x-list
+        {
+            uint16_t* nx = yl;
+            uint16_t* ny = tp;
+            tp = xl;
+            xl = nx;
+            yl = ny;
+        }
+        off_l += lsz;  // first box of level l+1
+        lsz *= 4;
+        width *= 4;
+        // geometry of the children (level l+1)
+        const int gc0 = bo + (int)off_l + iB * (int)width;
+        for (int k = threadIdx.x; k < width; k += kSubThreads) {
+            const int b = gc0 + k;
+            const int cs = bstart[b] - s, ce = cs + bcount[b] - 1;
+            const double x0 = xy[X[s + xl[cs]]].x, x1 = xy[X[s + xl[ce]]].x;
+            const double y0 = xy[X[s + yl[cs]]].y, y1 = xy[X[s + yl[ce]]].y;
+            box_geometry(b, x0, x1, y0, y1, center, bo, center, radius, rho, chl, rho32, rad32);
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < n; i += kSubThreads) Y[s + i] = X[s + yl[i]];
 }
 
 // Sorted point data: permutation, FP64 copy, FP32 hi/lo split relative to the
@@ -917,6 +1114,7 @@ fmm_status alloc_build(Tree& t) {
     if ((st = dalloc(&t.d_Y2, n))) return st;
     if ((st = dalloc(&t.d_sideX, n))) return st;
     if ((st = dalloc(&t.d_sideY, n))) return st;
+    if ((st = dalloc(&t.d_loc, n))) return st;
     const int64_t T = std::max<int64_t>(nblk(t.n, kPartTile), nblk(t.n, kSortTile));
     if ((st = dalloc(&t.d_tile_cnt, T))) return st;
     if ((st = dalloc(&t.d_tile_pre, T))) return st;
@@ -1003,7 +1201,8 @@ fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s) {
                                                t.d_inst_boxoff, t.d_center, t.d_radius, t.d_rho, t.d_chl, t.d_rho32,
                                                t.d_rad32, 1);
     FMM_CUDA(cudaGetLastError());
-    for (int l = 0; l + 1 < t.Lmax; ++l) {
+    const int lglob = std::min(t.l0, t.Lmax - 1);  // levels split by the global passes
+    for (int l = 0; l < lglob; ++l) {
         const SegTable& sx = t.seg_x[l];
         const SegTable& sy = t.seg_y[l];
         k_mark<<<nblk(n, 256), 256, 0, s>>>(X, n, sx.d_start, sx.d_nzero, sx.K, t.d_sideX);
@@ -1016,6 +1215,14 @@ fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s) {
         k_geom<<<nblk(Ll.count, 128), 128, 0, s>>>(Ll.d_ids, Ll.count, X, Y, xy, t.d_bstart, t.d_bcount, t.d_inst,
                                                    t.d_inst_boxoff, t.d_center, t.d_radius, t.d_rho, t.d_chl,
                                                    t.d_rho32, t.d_rad32, 0);
+        FMM_CUDA(cudaGetLastError());
+    }
+    if (lglob < t.Lmax - 1 && t.level_parents[lglob].count > 0) {
+        // every remaining split inside one CTA per box of level l0
+        const LevelList& Lp = t.level_parents[lglob];
+        k_subtree<<<Lp.count, kSubThreads, 0, s>>>(Lp.d_ids, Lp.count, lglob, X, Y, xy, t.d_bstart, t.d_bcount,
+                                                   t.d_inst, t.d_inst_boxoff, t.d_inst_levels, t.d_loc, t.d_center,
+                                                   t.d_radius, t.d_rho, t.d_chl, t.d_rho32, t.d_rad32, t.d_status);
         FMM_CUDA(cudaGetLastError());
     }
     k_finalize<<<nblk(n, 256), 256, 0, s>>>(Y, n, xy, t.d_leaf_start, t.leaves.d_ids, (int)t.nleaf, t.d_inst,

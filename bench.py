@@ -36,6 +36,9 @@ N_POINTS = 1_000_000
 P_TERMS = 17
 THETA = 0.5
 WORKLOAD = "cluster_mix_1e6_p17_theta0.5"
+# dram__bytes_read.sum + dram__bytes_write.sum of one P2P launch at N_levels = 9
+# (ncu, profiles/p2p_cluster1e6_L9.md); None until captured for the current kernel
+P2P_TRAFFIC_BYTES = None
 
 
 def _peaks():
@@ -184,15 +187,21 @@ def run_gpu(args):
                                   "only_step": True}))
             return
 
-        # --- phase times (events on the launching streams) ----------------------
-        tree.rebuild(X, flags=F.FMM_FLAG_TIMING)
-        ph = []
-        for _ in range(5):
-            flush.zero_()
-            tree.eval(G, out=phi)
-            ph.append(tree.phase_times())
+        # --- phase times (events recorded by the library on the streams the kernels
+        # run on): once as in the step (P2P overlapped with the far field), once
+        # with every phase alone (FMM_FLAG_SERIAL) for the per-kernel roofline
+        def _phases(flags):
+            tree.rebuild(X, flags=flags)
+            ph = []
+            for _ in range(5):
+                flush.zero_()
+                tree.eval(G, out=phi)
+                ph.append(tree.phase_times())
+            return {k: float(np.median([p[k] for p in ph])) for k in ph[0]}
+
+        phases = _phases(F.FMM_FLAG_TIMING)
+        phases_alone = _phases(F.FMM_FLAG_TIMING | F.FMM_FLAG_SERIAL)
         tree.rebuild(X, flags=0)
-        phases = {k: float(np.median([p[k] for p in ph])) for k in ph[0]}
         bld = []
         for _ in range(5):
             flush.zero_()
@@ -290,12 +299,14 @@ def run_gpu(args):
         return
     peaks = _peaks()
     value = N_POINTS * world / (ms * 1e-3) / 1e6
-    # dominant kernel: P2P (FP32 ALU bound).  19 algorithmic FP32 flops per
-    # interaction (FMA = 2); the ALU peak for this instruction mix = measured
-    # FP32 lane-op rate / 15 FP32 instructions per interaction * 19 flops.
+    # dominant kernel: P2P (FP32 ALU bound).  19 algorithmic flops per point
+    # pair (compensated difference 6, r^2 3, two products 6, accumulation 4,
+    # plus one reciprocal); the kernel issues 14 FP32-pipe instructions per pair,
+    # so the ALU peak for this mix is the measured FP32 lane rate / 14 pairs/s.
     fp32_lane_ops = 34.2e12
-    peak = fp32_lane_ops / 15.0 * 19.0 / 1e12
-    achieved = info["p2p_pairs"] * 19.0 / (phases["p2p"] * 1e-3) / 1e12
+    peak = fp32_lane_ops / 14.0 * 19.0 / 1e12
+    p2p_ms = phases_alone["p2p"]
+    achieved = info["p2p_pairs"] * 19.0 / (p2p_ms * 1e-3) / 1e12
     line = {
         "metric": METRIC,
         "value": round(value, 2),
@@ -313,16 +324,18 @@ def run_gpu(args):
                    "nlevels": info["nlevels_max"], "path": "fp32", "l2": "flushed (256 MB write) between steps",
                    "step": "tree rebuild + lists + one evaluation", "parallelism": "replicas" if world > 1 else "1 gpu"},
         "breakdown_ms": {"build": round(build_ms, 4), "eval": round(eval_ms, 4),
-                         **{k: round(v, 4) for k, v in phases.items()}},
+                         "in_step": {k: round(v, 4) for k, v in phases.items()},
+                         "alone": {k: round(v, 4) for k, v in phases_alone.items()}},
         "eval_only_mpoints_s": round(N_POINTS / (eval_ms * 1e-3) / 1e6, 2),
         "fp64_path": {"ms_per_step": round(ms64, 4), "value": round(N_POINTS / (ms64 * 1e-3) / 1e6, 2),
                       "rel_err_sampled": err64},
         "rel_err_sampled": err32,
         "bwd_over_fwd": bwd_ratio,
-        "roofline": {"kernel": "k_p2p32", "bound": "alu", "achieved": round(achieved, 3),
+        "roofline": {"kernel": "k_p2p_direct (P2P, FP32)", "bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                     "traffic": None,
-                     "peak_note": "measured FP32 FFMA lane rate 34.2e12/s (probe), 15 FP32 instr = 19 flops per interaction"},
+                     "traffic": P2P_TRAFFIC_BYTES, "kernel_ms": round(p2p_ms, 4),
+                     "peak_note": "ALU peak derived from the measured FP32 FFMA lane rate (34.2e12/s, 114/clk/SM "
+                                  "at 2032 MHz): 14 FP32-pipe instructions = 19 flops per point pair"},
         "e2e": {"value": round(N_POINTS / (e2e_ms * 1e-3) / 1e6, 2), "unit": UNIT,
                 "h2d_bytes_per_step": int(xy.nbytes + gam.nbytes), "d2h_bytes_per_step": int(N_POINTS * 8)},
         "gpu_launches": int(args.steps * (info["launches_build"] + info["launches_eval"])),

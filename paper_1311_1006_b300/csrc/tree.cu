@@ -816,36 +816,36 @@ __device__ __forceinline__ bool well_separated_fast(int a, int b, const float4* 
     return well_separated(center[a], radius[a], center[b], radius[b], theta);
 }
 
-struct Cand {
-    int b, h;       // child box, candidate box
-    bool first;     // first candidate of b
-    bool last;      // last candidate of b
+// The four candidates g = 4*q + c' (c' = 0..3) share the child box b and the
+// strong entry Q of its parent; decode that group once.
+struct CandGroup {
+    int b, h0;      // child box, first child of Q (candidates h0 + c')
+    bool first;     // group holds the first candidate of b
+    bool last;      // group holds the last candidate of b
     bool valid;     // the parent has children
 };
 
-// Decode candidate g of level l (see the enumeration above).
-__device__ __forceinline__ Cand decode_cand(long long g, long long base_prev, const int32_t* __restrict__ sowner,
-                                            const int32_t* __restrict__ soff, const int32_t* __restrict__ ns,
-                                            const int32_t* __restrict__ sidx, const int32_t* __restrict__ child0) {
-    Cand c;
-    const int P = sowner[base_prev + (g >> 4)];
+__device__ __forceinline__ CandGroup decode_group(long long q, long long base_prev, const int32_t* __restrict__ sowner,
+                                                  const int32_t* __restrict__ soff, const int32_t* __restrict__ ns,
+                                                  const int32_t* __restrict__ sidx,
+                                                  const int32_t* __restrict__ child0) {
+    CandGroup c;
+    const int P = sowner[base_prev + (q >> 2)];
     const int c0 = child0[P];
     c.valid = c0 >= 0;
     if (!c.valid) {
-        c.b = c.h = 0;
+        c.b = c.h0 = 0;
         c.first = c.last = false;
         return c;
     }
     const int n = ns[P];
     const long long e0 = (long long)soff[P] - base_prev;
-    const int r = (int)(g - 16 * e0);
-    const int q = 4 * n;
-    const int ci = r / q, rem = r - ci * q;
-    const int j = rem >> 2, cp = rem & 3;
+    const int r = (int)(q - 4 * e0);  // (child index) * n + j
+    const int ci = r / n, j = r - ci * n;
     c.b = c0 + ci;
-    c.h = child0[sidx[soff[P] + j]] + cp;
-    c.first = rem == 0;
-    c.last = rem == q - 1;
+    c.h0 = child0[sidx[soff[P] + j]];
+    c.first = j == 0;
+    c.last = j == n - 1;
     return c;
 }
 
@@ -871,20 +871,21 @@ __global__ void __launch_bounds__(kLThreads) k_lists_classify(
         int cs = 0, cw = 0;
         uint32_t packed[2] = {0, 0};
 #pragma unroll
-        for (int k = 0; k < kLItems; ++k) {
-            const long long g = g0 + k;
-            int f = 0;
-            if (g < ncand) {
-                const Cand c = decode_cand(g, base_prev, sowner, soff, ns, sidx, child0);
-                if (c.valid) {
-                    const bool sep =
-                        (c.h != c.b) && well_separated_fast(c.b, c.h, chl, rad32, center, radius, th32, theta);
-                    f = sep ? 2 : 1;
-                }
+        for (int gq = 0; gq < kLItems / 4; ++gq) {
+            const long long gg = g0 + 4 * gq;
+            if (gg >= ncand) break;
+            const CandGroup c = decode_group(gg >> 2, base_prev, sowner, soff, ns, sidx, child0);
+            if (!c.valid) continue;
+#pragma unroll
+            for (int cp = 0; cp < 4; ++cp) {
+                const int h = c.h0 + cp;
+                const bool sep = (h != c.b) && well_separated_fast(c.b, h, chl, rad32, center, radius, th32, theta);
+                const int f = sep ? 2 : 1;
+                cs += f == 1;
+                cw += f == 2;
+                const int k = 4 * gq + cp;
+                packed[k >> 2] |= (uint32_t)f << (8 * (k & 3));
             }
-            cs += f == 1;
-            cw += f == 2;
-            packed[k >> 2] |= (uint32_t)f << (8 * (k & 3));
         }
         if (g0 < ncand) {
             uint2* fp = reinterpret_cast<uint2*>(flags + g0);  // g0 is a multiple of 8
@@ -980,25 +981,31 @@ __global__ void __launch_bounds__(kLThreads) k_lists_scatter(
         int pw = block_excl_scan(cw, ww, tot_w) + pre_w[t];
         if (g0 >= ncand) continue;
 #pragma unroll
-        for (int k = 0; k < kLItems; ++k) {
-            const long long g = g0 + k;
-            if (g >= ncand) break;
-            const int f = (int)(((k < 4 ? fp.x : fp.y) >> (8 * (k & 3))) & 0xffu);
-            const Cand c = decode_cand(g, base_prev, sowner, soff, ns, sidx, child0);
+        for (int gq = 0; gq < kLItems / 4; ++gq) {
+            const long long gg = g0 + 4 * gq;
+            if (gg >= ncand) break;
+            const CandGroup c = decode_group(gg >> 2, base_prev, sowner, soff, ns, sidx, child0);
             if (!c.valid) continue;
             if (c.first) {
                 soff[c.b] = (int32_t)(bs + ps);
                 woff[c.b] = (int32_t)(bw + pw);
             }
-            if (f == 1) {
-                const long long q = bs + ps;
-                sidx[q] = c.h;
-                sowner_out[q] = c.b;
-                if (child0[c.b] < 0) srng[q] = make_int2(bstart[c.h], bcount[c.h]);
-                ++ps;
-            } else {
-                widx[bw + pw] = c.h;
-                ++pw;
+            const bool leaf = child0[c.b] < 0;
+#pragma unroll
+            for (int cp = 0; cp < 4; ++cp) {
+                const int k = 4 * gq + cp;
+                const int f = (int)(((k < 4 ? fp.x : fp.y) >> (8 * (k & 3))) & 0xffu);
+                const int h = c.h0 + cp;
+                if (f == 1) {
+                    const long long qq = bs + ps;
+                    sidx[qq] = h;
+                    sowner_out[qq] = c.b;
+                    if (leaf) srng[qq] = make_int2(bstart[h], bcount[h]);
+                    ++ps;
+                } else {
+                    widx[bw + pw] = h;
+                    ++pw;
+                }
             }
             if (c.last) {
                 ns[c.b] = (int32_t)(bs + ps);  // end; made a length in pass 4
@@ -1026,36 +1033,56 @@ __global__ void k_lists_len(const int32_t* __restrict__ ids, int cnt, const int3
 // partial sums are added in item order later (deterministic).
 // int4 item = (box, list begin, list end, first item of the box or -1 when
 // the box has a single item).
+// One atomic per warp: lanes reserve k items each from a global counter.
+__device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* ctr, int k) {
+    const int lane = threadIdx.x & 31;
+    int incl = k;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 31 && total > 0) base = atomicAdd(ctr, (unsigned long long)total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    return base + (unsigned long long)(incl - k);
+}
+
 __global__ void k_items(int nbox, const int32_t* __restrict__ child0, const int32_t* __restrict__ bcount,
                         const int32_t* __restrict__ ns, const int32_t* __restrict__ nw, unsigned long long* ctr,
                         int4* p2p_items, int2* leaf_items, long long p2p_cap, int4* m2l_items, int2* box_m2l,
                         long long m2l_cap, unsigned* status) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nbox) return;
-    if (*((volatile unsigned*)status) & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW)) return;
-    if (child0[b] < 0) {
-        const int n = ns[b];
-        const int C = max(1, kP2PItemSources / max(bcount[b], 1));
-        const int k = (n + C - 1) / C;
-        const unsigned long long base = atomicAdd(ctr + 2, (unsigned long long)k);
-        leaf_items[b] = make_int2((int)base, k);
-        if ((long long)(base + k) > p2p_cap) {
+    if (*((volatile unsigned*)status) & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW)) return;  // uniform
+    const bool in = b < nbox;
+    const bool leaf = in && child0[b] < 0;
+    int kp = 0, C = 1, n = 0;
+    if (leaf) {
+        n = ns[b];
+        C = max(1, kP2PItemSources / max(bcount[b], 1));
+        kp = (n + C - 1) / C;
+    }
+    const unsigned long long bp = warp_reserve(ctr + 2, kp);
+    if (leaf) {
+        leaf_items[b] = make_int2((int)bp, kp);
+        if ((long long)(bp + kp) > p2p_cap) {
             atomicOr(status, ST_ITEM_OVERFLOW);
         } else {
-            for (int c = 0; c < k; ++c)
-                p2p_items[base + c] = make_int4(b, c * C, min(n, (c + 1) * C), k > 1 ? (int)base : -1);
+            for (int c = 0; c < kp; ++c)
+                p2p_items[bp + c] = make_int4(b, c * C, min(n, (c + 1) * C), kp > 1 ? (int)bp : -1);
         }
     }
-    const int n = nw[b];
-    const int k = (n + kM2LItemPairs - 1) / kM2LItemPairs;
-    const unsigned long long base = atomicAdd(ctr + 3, (unsigned long long)k);
-    box_m2l[b] = make_int2((int)base, k);
-    if ((long long)(base + k) > m2l_cap) {
+    const int m = in ? nw[b] : 0;
+    const int km = (m + kM2LItemPairs - 1) / kM2LItemPairs;
+    const unsigned long long bm = warp_reserve(ctr + 3, km);
+    if (!in) return;
+    box_m2l[b] = make_int2((int)bm, km);
+    if ((long long)(bm + km) > m2l_cap) {
         atomicOr(status, ST_ITEM_OVERFLOW);
     } else {
-        for (int c = 0; c < k; ++c)
-            m2l_items[base + c] =
-                make_int4(b, c * kM2LItemPairs, min(n, (c + 1) * kM2LItemPairs), k > 1 ? (int)base : -1);
+        for (int c = 0; c < km; ++c)
+            m2l_items[bm + c] = make_int4(b, c * kM2LItemPairs, min(m, (c + 1) * kM2LItemPairs), km > 1 ? (int)bm : -1);
     }
 }
 

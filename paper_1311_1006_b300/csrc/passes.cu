@@ -517,7 +517,7 @@ constexpr int kP2PUnroll = 4;
 constexpr int kP2PDWarps = 4;
 
 template <typename V, typename C, int TPL, int LT>
-__global__ void __launch_bounds__(kP2PDWarps * 32) k_p2p_direct(const int4* __restrict__ items,
+__global__ void __launch_bounds__(kP2PDWarps * 32, sizeof(C) == 8 ? 5 : 1) k_p2p_direct(const int4* __restrict__ items,
                                                                 const unsigned long long* __restrict__ nitems,
                                                                 unsigned* __restrict__ next_item,
                                                                 const int32_t* __restrict__ bstart,
@@ -548,38 +548,57 @@ __global__ void __launch_bounds__(kP2PDWarps * 32) k_p2p_direct(const int4* __re
                 xt[u] = (idx < tn) ? pos[ts + idx] : V{};
                 acc[u] = C{};
             }
-            // warp-uniform walk over the source ranges; the next range's entry and
-            // first point of this lane are loaded one step ahead
+            // warp-uniform walk over the source ranges, two per step.  The
+            // first S points of a range are one point per slice; a slice past
+            // the end of a short (or empty) range reads point 0 with zero
+            // strength (adds exactly 0), so the loop has no divergent branch.
+            // Ranges longer than S finish in a uniform inner loop.
             int k = item.y;
-            int2 r = k < item.z ? rl[k] : make_int2(0, 0);
-            V s0 = V{};
-            C g0 = C{};
-            if (k < item.z && ss < r.y) {
-                s0 = pos[r.x + ss];
-                g0 = gam[r.x + ss];
-            }
-            while (k < item.z) {
-                const int2 rn = (k + 1 < item.z) ? rl[k + 1] : make_int2(0, 0);
-                V s1 = V{};
-                C g1 = C{};
-                if (ss < rn.y) {
-                    s1 = pos[rn.x + ss];
-                    g1 = gam[rn.x + ss];
-                }
-                if (ss < r.y) {
+            const int ke = item.z;
+            int2 ra = k < ke ? rl[k] : make_int2(0, 1);
+            int2 rb = k + 1 < ke ? rl[k + 1] : make_int2(0, 1);
+            V sa = pos[ss < ra.y ? ra.x + ss : 0];
+            C ga = gam[ss < ra.y ? ra.x + ss : 0];
+            V sb = pos[ss < rb.y ? rb.x + ss : 0];
+            C gb = gam[ss < rb.y ? rb.x + ss : 0];
+            if (!(ss < ra.y) || k >= ke) ga = C{};
+            if (!(ss < rb.y) || k + 1 >= ke) gb = C{};
+            while (k < ke) {
+                const int2 rc = k + 2 < ke ? rl[k + 2] : make_int2(0, 1);
+                const int2 rd = k + 3 < ke ? rl[k + 3] : make_int2(0, 1);
+                const V sc = pos[ss < rc.y ? rc.x + ss : 0];
+                C gc = gam[ss < rc.y ? rc.x + ss : 0];
+                const V sd = pos[ss < rd.y ? rd.x + ss : 0];
+                C gd = gam[ss < rd.y ? rd.x + ss : 0];
+                if (!(ss < rc.y) || k + 2 >= ke) gc = C{};
+                if (!(ss < rd.y) || k + 3 >= ke) gd = C{};
 #pragma unroll
-                    for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], s0, g0, acc[u]);
-                    for (int e = ss + S; e < r.y; e += S) {
-                        const V s = pos[r.x + e];
-                        const C g = gam[r.x + e];
+                for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], sa, ga, acc[u]);
+#pragma unroll
+                for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], sb, gb, acc[u]);
+                if (ra.y > S && k < ke) {
+                    for (int e = ss + S; e < ra.y; e += S) {
+                        const V s = pos[ra.x + e];
+                        const C g = gam[ra.x + e];
 #pragma unroll
                         for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], s, g, acc[u]);
                     }
                 }
-                r = rn;
-                s0 = s1;
-                g0 = g1;
-                ++k;
+                if (rb.y > S && k + 1 < ke) {
+                    for (int e = ss + S; e < rb.y; e += S) {
+                        const V s = pos[rb.x + e];
+                        const C g = gam[rb.x + e];
+#pragma unroll
+                        for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], s, g, acc[u]);
+                    }
+                }
+                ra = rc;
+                rb = rd;
+                sa = sc;
+                ga = gc;
+                sb = sd;
+                gb = gd;
+                k += 2;
             }
 #pragma unroll
             for (int u = 0; u < TPL; ++u) {

@@ -165,6 +165,7 @@ static void release(Tree* t) {
                     t->d_rad32, t->d_soff, t->d_ns, t->d_sidx, t->d_srng, t->d_sowner, t->d_cflags, t->d_ltile_s,
                     t->d_ltile_w, t->d_lpre_s, t->d_lpre_w, t->d_lvl_base, t->d_woff, t->d_nw, t->d_widx, t->d_p2p_items,
                     t->d_m2l_items, t->d_leaf_items, t->d_box_m2l, t->d_status, t->d_gam, t->d_near, t->d_M64,
+                    t->d_pslot, t->d_posp, t->d_slot_of, t->d_gamp,
                     t->d_M32, t->d_Lm2l, t->d_L64, t->d_L32, t->d_p2p_part, t->d_m2l_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);

@@ -22,6 +22,25 @@ enum : unsigned {
     ST_ITEM_OVERFLOW = 32u    // a work-item array exceeded its capacity
 };
 
+// P2P lane layout for leaves of at most max_leaf points: lt target lanes x
+// 32/lt source slices, tpl targets per lane.
+struct P2PLayout {
+    int tpl, lt;
+};
+inline P2PLayout p2p_layout(int max_leaf) {
+    if (max_leaf <= 4) return {2, 2};
+    if (max_leaf <= 8) return {4, 2};
+    if (max_leaf <= 16) return {8, 2};
+    if (max_leaf <= 32) return {8, 4};
+    if (max_leaf <= 64) return {8, 8};
+    return {8, 16};
+}
+// Slots per leaf: max_leaf rounded up to whole source steps of the layout.
+inline int leaf_capacity(int max_leaf) {
+    const int S = 32 / p2p_layout(max_leaf).lt;
+    return (max_leaf + S - 1) / S * S;
+}
+
 // Work-item sizes: P2P items hold about this many source points; M2L items at
 // most this many weak pairs.
 constexpr int kP2PItemSources = 2048;
@@ -87,6 +106,11 @@ struct Tree {
     int l0 = 0;                            // first level split inside one CTA per box
     int64_t* d_inst_boxoff = nullptr;      // ninst+1 (root box id of each instance)
     int32_t* d_leaf_start = nullptr;       // nleaf+1: first sorted position of each leaf
+    // leaf slot layout of the P2P operands: leaf q owns slots [q*leaf_cap, (q+1)*leaf_cap);
+    // its points fill the first bcount slots, the rest (and one extra block after the
+    // last leaf) are padding with zero strength
+    int leaf_cap = 16;
+    int32_t* d_pslot = nullptr;            // per box: first slot of a leaf, -1 otherwise
 
     // build scratch
     uint64_t* d_keys[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -103,6 +127,9 @@ struct Tree {
     int32_t* d_leaf_of = nullptr;  // sorted position -> leaf box id
     double2* d_pts = nullptr;      // sorted FP64 points
     float4* d_pos4 = nullptr;      // sorted (x_hi, y_hi, x_lo, y_lo) relative to the instance origin
+    void* d_posp = nullptr;        // slot layout: pos4 (FP32 path) or FP64 points, 16 B per slot
+    int32_t* d_slot_of = nullptr;  // sorted position -> slot
+    int64_t slot_alloc = 0;        // slots d_posp was allocated for
     double2* d_center = nullptr;   // per box
     double* d_radius = nullptr;    // per box (half bbox diagonal)
     double* d_rho = nullptr;       // per box scale radius = (double)(float)radius
@@ -111,7 +138,7 @@ struct Tree {
     float* d_rad32 = nullptr;      // per box (float)radius, for the FP32 pre-test of eq (2.3)
     // coupling lists in CSR form: box b's strong list is sidx[soff[b] .. soff[b]+ns[b])
     int32_t *d_soff = nullptr, *d_ns = nullptr, *d_sidx = nullptr;
-    int2* d_srng = nullptr;        // leaves: (first point, count) of each strong entry, parallel to sidx
+    int2* d_srng = nullptr;        // leaves: (first slot, count) of each strong entry, parallel to sidx
     int32_t* d_sowner = nullptr;   // box of each strong entry, parallel to sidx
     uint8_t* d_cflags = nullptr;   // candidate flags of the level being built
     int32_t *d_ltile_s = nullptr, *d_ltile_w = nullptr, *d_lpre_s = nullptr, *d_lpre_w = nullptr;
@@ -134,6 +161,8 @@ struct Tree {
 
     // evaluation workspace
     void* d_gam = nullptr;     // sorted strengths (float2 or double2), 2 sets for backward
+    void* d_gamp = nullptr;    // strengths in the leaf slot layout (forward set)
+    int64_t eval_slots = 0;
     void* d_near = nullptr;    // P2P output(s), sorted order
     void* d_p2p_part = nullptr;  // partial P2P sums of split leaves (item x max_leaf)
     void* d_m2l_part = nullptr;  // partial M2L sums of split boxes (item x PS)

@@ -52,16 +52,23 @@ __constant__ BinomTable c_binom = make_binom();
 
 // ------------------------------------------------------------------ gather
 
-__global__ void k_gather32(const double2* __restrict__ in, const int32_t* __restrict__ perm, int n, float2* out) {
+// Strengths into sorted order and into the leaf slot layout of the P2P pass.
+__global__ void k_gather32(const double2* __restrict__ in, const int32_t* __restrict__ perm,
+                           const int32_t* __restrict__ slot_of, int n, float2* out, float2* outp) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double2 g = in[perm[i]];
-    out[i] = make_float2((float)g.x, (float)g.y);
+    const double2 g = in[perm[i]];
+    const float2 v = make_float2((float)g.x, (float)g.y);
+    out[i] = v;
+    outp[slot_of[i]] = v;
 }
-__global__ void k_gather64(const double2* __restrict__ in, const int32_t* __restrict__ perm, int n, double2* out) {
+__global__ void k_gather64(const double2* __restrict__ in, const int32_t* __restrict__ perm,
+                           const int32_t* __restrict__ slot_of, int n, double2* out, double2* outp) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    out[i] = in[perm[i]];
+    const double2 g = in[perm[i]];
+    out[i] = g;
+    outp[slot_of[i]] = g;
 }
 
 // --------------------------------------------------------------------- P2M
@@ -440,45 +447,24 @@ __global__ void __launch_bounds__(256) k_l2p64(int n, const int32_t* __restrict_
 
 // --------------------------------------------------------------------- P2P
 
-// One warp per target leaf.  The warp's lanes form LT target groups x S
-// source slices: lane (tg, ss) owns targets tg, tg+LT, ... (TPL of them) and
-// every S-th staged source; slices are summed with shuffles at the end.
-// Sources of the strongly coupled leaves are staged in warp-private shared
-// memory in chunks.  FP32: coordinates carry a hi/lo split so that
-// z_i - z_j keeps full FP32 relative accuracy even for very close pairs.
-constexpr int kP2PWarps = 8;
-constexpr int kP2PChunk32 = 192;
-constexpr int kP2PChunk64 = 128;
+// Pairwise terms Gamma_j/(z_i - z_j) = Gamma_j conj(d)/|d|^2, d = z_i - z_j.
 constexpr int kP2PBlocksPerSM = 4;
-
-__device__ __forceinline__ void p2p_interact32(const float4 t, const float4 s, const float2 g, float2& acc) {
-    const float dx = (t.x - s.x) + (t.z - s.z);
-    const float dy = (t.y - s.y) + (t.w - s.w);
-    const float r2 = fmaf(dx, dx, dy * dy);
-    const float inv = fminf(rcp_approx(r2), 3.0e38f);  // coincident pair: r2 = 0, dx = dy = 0 -> adds 0
-    const float tr = fmaf(g.x, dx, g.y * dy);
-    const float ti = fmaf(g.y, dx, -g.x * dy);
-    acc.x = fmaf(tr, inv, acc.x);
-    acc.y = fmaf(ti, inv, acc.y);
-}
 
 __device__ __forceinline__ void p2p_interact64(const double2 t, const double2 s, const double2 g, double2& acc) {
     const double dx = t.x - s.x, dy = t.y - s.y;
     const double r2 = fma(dx, dx, dy * dy);
-    const double inv = r2 > 0.0 ? __drcp_rn(r2) : 0.0;
+    const double inv = r2 > 0.0 ? __drcp_rn(r2) : 0.0;  // coincident pair (z_j = z_i): adds 0
     const double tr = fma(g.x, dx, g.y * dy);
     const double ti = fma(g.y, dx, -g.x * dy);
     acc.x = fma(tr, inv, acc.x);
     acc.y = fma(ti, inv, acc.y);
 }
 
-// ---- P2P with a compile-time lane layout --------------------------------
-// LT target lanes x S = 32/LT source slices, TPL targets per lane (a leaf of at
-// most TPL*LT points per pass).  Staged chunks are padded with zero-strength
-// sources far away, so the inner loop runs whole unrolled groups with no tail
-// test.  FP32: the coincident-pair guard is folded into r^2 (+1e-37f):
-// coincident points give dx = dy = 0 and add 0; pairs closer than ~1e-18 are
-// below FP32 resolution anyway.
+// FP32: coordinates carry a hi/lo split so that z_i - z_j keeps full FP32
+// relative accuracy even for very close pairs.  The coincident-pair guard is
+// folded into r^2 (+1e-37f): coincident points give dx = dy = 0 and add 0;
+// pairs closer than ~1e-18 are below FP32 resolution anyway.  Zero-strength
+// padding sources add exactly 0 (every factor is finite).
 __device__ __forceinline__ void p2p_fast32(const float4 t, const float4 s, const float2 g, float2& acc) {
     const float dx = (t.x - s.x) + (t.z - s.z);
     const float dy = (t.y - s.y) + (t.w - s.w);
@@ -494,39 +480,31 @@ __device__ __forceinline__ void p2p_fast(const float4 t, const float4 s, const f
 __device__ __forceinline__ void p2p_fast(const double2 t, const double2 s, const double2 g, double2& acc) {
     p2p_interact64(t, s, g, acc);
 }
-template <typename V>
-__device__ __forceinline__ V far_dummy();
-template <>
-__device__ __forceinline__ float4 far_dummy<float4>() {
-    return make_float4(1e18f, 1e18f, 0.f, 0.f);
-}
-template <>
-__device__ __forceinline__ double2 far_dummy<double2>() {
-    return make_double2(1e150, 1e150);
-}
 
-constexpr int kP2PUnroll = 4;
-
-// ---- P2P reading sources straight from global memory ------------------------
-// One warp per work item, fetched dynamically from an atomic counter.  Lane
-// (tg, ss) holds TPL targets and walks every S-th point of the item's source
-// ranges (int2 (first point, count) per strong entry, recorded by the list
-// build).  The S slices of a warp read S consecutive points per step, so each
-// load is one coalesced line; the next point is prefetched before the current
-// one is used.  No shared memory, no staging.
+// ---- P2P over the leaf slot layout ------------------------------------------
+// One warp per work item (a target leaf and a run of its strong entries),
+// fetched from an atomic counter.  Lane (tg, ss) owns targets tg, tg+LT, ...
+// (TPL of them) and source slice ss of S = 32/LT.  Every leaf occupies `cap`
+// consecutive slots whose tail is zero-strength padding, so a source step is
+// "slot offset of the range + ss" with no per-lane bounds test: S consecutive
+// slots make one coalesced load.  When cap == S (LONG false) one step covers a
+// whole range and the loop walks two ranges per half-iteration from two
+// register sets (A, B) that are reloaded in place, with the range offsets read
+// one half-iteration before the loads that use them.  Entries past the item's
+// end read the all-padding block at slot `pad`.  The layouts with LT = 2 hold
+// leaves of at most 16 = S points, so cap == S; the others (LONG) take
+// ceil(count/S) steps per range.  The S slice sums are added with shuffles.
 constexpr int kP2PDWarps = 4;
 
 template <typename V, typename C, int TPL, int LT>
-__global__ void __launch_bounds__(kP2PDWarps * 32, sizeof(C) == 8 ? 5 : 1) k_p2p_direct(const int4* __restrict__ items,
-                                                                const unsigned long long* __restrict__ nitems,
-                                                                unsigned* __restrict__ next_item,
-                                                                const int32_t* __restrict__ bstart,
-                                                                const int32_t* __restrict__ bcount,
-                                                                const int32_t* __restrict__ soff,
-                                                                const int2* __restrict__ srng,
-                                                                const V* __restrict__ pos, const C* __restrict__ gam,
-                                                                C* __restrict__ nearv, C* __restrict__ part, int TS) {
+__global__ void __launch_bounds__(kP2PDWarps * 32, sizeof(C) == 8 ? 5 : 1)
+    k_p2p_slots(const int4* __restrict__ items, const unsigned long long* __restrict__ nitems,
+                unsigned* __restrict__ next_item, const int32_t* __restrict__ bstart,
+                const int32_t* __restrict__ bcount, const int32_t* __restrict__ pslot,
+                const int32_t* __restrict__ soff, const int2* __restrict__ srng, const V* __restrict__ posp,
+                const C* __restrict__ gamp, C* __restrict__ nearv, C* __restrict__ part, int TS, int pad) {
     constexpr int S = 32 / LT;
+    constexpr bool LONG = LT > 2;
     const int lane = threadIdx.x & 31;
     const int tg = lane % LT, ss = lane / LT;
     const int nit = (int)*nitems;
@@ -537,68 +515,69 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, sizeof(C) == 8 ? 5 : 1) k_p2p
         if (it >= nit) break;
         const int4 item = items[it];
         const int b = item.x;
-        const int ts = bstart[b], tn = bcount[b];
+        const int ts = bstart[b], tn = bcount[b], tb = pslot[b];
         const int2* rl = srng + soff[b];
+        const int ke = item.z;
         for (int t0 = 0; t0 < tn; t0 += TPL * LT) {
             V xt[TPL];
             C acc[TPL];
 #pragma unroll
             for (int u = 0; u < TPL; ++u) {
                 const int idx = t0 + tg + u * LT;
-                xt[u] = (idx < tn) ? pos[ts + idx] : V{};
+                xt[u] = (idx < tn) ? posp[tb + idx] : V{};
                 acc[u] = C{};
             }
-            // warp-uniform walk over the source ranges, two per step.  The
-            // first S points of a range are one point per slice; a slice past
-            // the end of a short (or empty) range reads point 0 with zero
-            // strength (adds exactly 0), so the loop has no divergent branch.
-            // Ranges longer than S finish in a uniform inner loop.
-            int k = item.y;
-            const int ke = item.z;
-            int2 ra = k < ke ? rl[k] : make_int2(0, 1);
-            int2 rb = k + 1 < ke ? rl[k + 1] : make_int2(0, 1);
-            V sa = pos[ss < ra.y ? ra.x + ss : 0];
-            C ga = gam[ss < ra.y ? ra.x + ss : 0];
-            V sb = pos[ss < rb.y ? rb.x + ss : 0];
-            C gb = gam[ss < rb.y ? rb.x + ss : 0];
-            if (!(ss < ra.y) || k >= ke) ga = C{};
-            if (!(ss < rb.y) || k + 1 >= ke) gb = C{};
-            while (k < ke) {
-                const int2 rc = k + 2 < ke ? rl[k + 2] : make_int2(0, 1);
-                const int2 rd = k + 3 < ke ? rl[k + 3] : make_int2(0, 1);
-                const V sc = pos[ss < rc.y ? rc.x + ss : 0];
-                C gc = gam[ss < rc.y ? rc.x + ss : 0];
-                const V sd = pos[ss < rd.y ? rd.x + ss : 0];
-                C gd = gam[ss < rd.y ? rd.x + ss : 0];
-                if (!(ss < rc.y) || k + 2 >= ke) gc = C{};
-                if (!(ss < rd.y) || k + 3 >= ke) gd = C{};
+            if constexpr (!LONG) {
+                int k = item.y;
+                int oa0 = (k < ke ? rl[k].x : pad) + ss;
+                int oa1 = (k + 1 < ke ? rl[k + 1].x : pad) + ss;
+                V sa0 = posp[oa0], sa1 = posp[oa1];
+                C ga0 = gamp[oa0], ga1 = gamp[oa1];
+                int ob0 = (k + 2 < ke ? rl[k + 2].x : pad) + ss;
+                int ob1 = (k + 3 < ke ? rl[k + 3].x : pad) + ss;
+                while (true) {
+                    const V sb0 = posp[ob0], sb1 = posp[ob1];
+                    const C gb0 = gamp[ob0], gb1 = gamp[ob1];
+                    oa0 = (k + 4 < ke ? rl[k + 4].x : pad) + ss;
+                    oa1 = (k + 5 < ke ? rl[k + 5].x : pad) + ss;
 #pragma unroll
-                for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], sa, ga, acc[u]);
+                    for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], sa0, ga0, acc[u]);
 #pragma unroll
-                for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], sb, gb, acc[u]);
-                if (ra.y > S && k < ke) {
-                    for (int e = ss + S; e < ra.y; e += S) {
-                        const V s = pos[ra.x + e];
-                        const C g = gam[ra.x + e];
+                    for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], sa1, ga1, acc[u]);
+                    if (k + 2 >= ke) break;
+                    sa0 = posp[oa0];
+                    sa1 = posp[oa1];
+                    ga0 = gamp[oa0];
+                    ga1 = gamp[oa1];
+                    ob0 = (k + 6 < ke ? rl[k + 6].x : pad) + ss;
+                    ob1 = (k + 7 < ke ? rl[k + 7].x : pad) + ss;
 #pragma unroll
-                        for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], s, g, acc[u]);
+                    for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], sb0, gb0, acc[u]);
+#pragma unroll
+                    for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], sb1, gb1, acc[u]);
+                    k += 4;
+                    if (k >= ke) break;
+                }
+            } else {
+                for (int k = item.y; k < ke; ++k) {
+                    const int2 r = rl[k];
+                    const int o = r.x + ss;
+                    int e = 0;
+                    for (; e + S < r.y; e += 2 * S) {  // two steps, both inside the range's slots
+                        const V s0 = posp[o + e], s1 = posp[o + e + S];
+                        const C g0 = gamp[o + e], g1 = gamp[o + e + S];
+#pragma unroll
+                        for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], s0, g0, acc[u]);
+#pragma unroll
+                        for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], s1, g1, acc[u]);
+                    }
+                    if (e < r.y) {
+                        const V s0 = posp[o + e];
+                        const C g0 = gamp[o + e];
+#pragma unroll
+                        for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], s0, g0, acc[u]);
                     }
                 }
-                if (rb.y > S && k + 1 < ke) {
-                    for (int e = ss + S; e < rb.y; e += S) {
-                        const V s = pos[rb.x + e];
-                        const C g = gam[rb.x + e];
-#pragma unroll
-                        for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], s, g, acc[u]);
-                    }
-                }
-                ra = rc;
-                rb = rd;
-                sa = sc;
-                ga = gc;
-                sb = sd;
-                gb = gd;
-                k += 2;
             }
 #pragma unroll
             for (int u = 0; u < TPL; ++u) {
@@ -773,39 +752,36 @@ static void launch_p2p(Tree& t, const Bufs& B, cudaStream_t s) {
     const int bps = p2p_blocks_per_sm();
     const int dgrid = std::min(nblk(t.p2p_cap, kP2PDWarps), t.num_sms * bps);
     const int rgrid = nblk(32 * t.nleaf, 256);
+    const P2PLayout lay = p2p_layout(t.max_leaf);
+    const int pad = (int)(t.nleaf * t.leaf_cap);
+#define FMM_P2P(V, C, TPL, LT)                                                                                   \
+    k_p2p_slots<V, C, TPL, LT><<<dgrid, kP2PDWarps * 32, 0, s>>>(                                                 \
+        t.d_p2p_items, cnt, next, t.d_bstart, t.d_bcount, t.d_pslot, t.d_soff, t.d_srng,                          \
+        static_cast<const V*>(t.d_posp), static_cast<const C*>(t.d_gamp), nv, pt, t.max_leaf, pad);
+#define FMM_P2P_LAYOUTS(V, C)                                  \
+    switch (lay.tpl * 100 + lay.lt) {                          \
+        case 202: FMM_P2P(V, C, 2, 2) break;                   \
+        case 402: FMM_P2P(V, C, 4, 2) break;                   \
+        case 802: FMM_P2P(V, C, 8, 2) break;                   \
+        case 804: FMM_P2P(V, C, 8, 4) break;                   \
+        case 808: FMM_P2P(V, C, 8, 8) break;                   \
+        default: FMM_P2P(V, C, 8, 16) break;                   \
+    }
     if (t.path == FMM_PATH_FP32) {
-        const float2* gam = static_cast<const float2*>(B.gam);
         float2* nv = static_cast<float2*>(B.near);
         float2* pt = static_cast<float2*>(B.p2p_part);
-#define FMM_P2P32(TPL, LT)                                                                                        \
-    k_p2p_direct<float4, float2, TPL, LT><<<dgrid, kP2PDWarps * 32, 0, s>>>(                                      \
-        t.d_p2p_items, cnt, next, t.d_bstart, t.d_bcount, t.d_soff, t.d_srng, t.d_pos4, gam, nv, pt, t.max_leaf)
-        if (t.max_leaf <= 4) { FMM_P2P32(2, 2); }
-        else if (t.max_leaf <= 8) { FMM_P2P32(4, 2); }
-        else if (t.max_leaf <= 16) { FMM_P2P32(8, 2); }
-        else if (t.max_leaf <= 32) { FMM_P2P32(8, 4); }
-        else if (t.max_leaf <= 64) { FMM_P2P32(8, 8); }
-        else { FMM_P2P32(8, 16); }
-#undef FMM_P2P32
+        FMM_P2P_LAYOUTS(float4, float2)
         k_reduce_p2p<float2><<<rgrid, 256, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, t.d_leaf_items, t.d_bstart,
                                                    t.d_bcount, pt, t.max_leaf, nv);
     } else {
-        const double2* gam = static_cast<const double2*>(B.gam);
         double2* nv = static_cast<double2*>(B.near);
         double2* pt = static_cast<double2*>(B.p2p_part);
-#define FMM_P2P64(TPL, LT)                                                                                        \
-    k_p2p_direct<double2, double2, TPL, LT><<<dgrid, kP2PDWarps * 32, 0, s>>>(                                    \
-        t.d_p2p_items, cnt, next, t.d_bstart, t.d_bcount, t.d_soff, t.d_srng, t.d_pts, gam, nv, pt, t.max_leaf)
-        if (t.max_leaf <= 4) { FMM_P2P64(2, 2); }
-        else if (t.max_leaf <= 8) { FMM_P2P64(4, 2); }
-        else if (t.max_leaf <= 16) { FMM_P2P64(8, 2); }
-        else if (t.max_leaf <= 32) { FMM_P2P64(8, 4); }
-        else if (t.max_leaf <= 64) { FMM_P2P64(8, 8); }
-        else { FMM_P2P64(8, 16); }
-#undef FMM_P2P64
+        FMM_P2P_LAYOUTS(double2, double2)
         k_reduce_p2p<double2><<<rgrid, 256, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, t.d_leaf_items, t.d_bstart,
                                                     t.d_bcount, pt, t.max_leaf, nv);
     }
+#undef FMM_P2P_LAYOUTS
+#undef FMM_P2P
 }
 
 template <int P>
@@ -866,7 +842,7 @@ static fmm_status ralloc(T** p, size_t bytes) {
 fmm_status alloc_eval(Tree& t, int sets) {
     if (t.eval_nbox == (size_t)t.nbox && t.eval_n == (size_t)t.n && t.eval_PS == t.PS && t.eval_path == t.path &&
         t.eval_sets >= sets && t.part_p2p_cap >= t.p2p_cap && t.part_m2l_cap >= t.m2l_cap &&
-        t.eval_ts >= t.max_leaf)
+        t.eval_ts >= t.max_leaf && t.eval_slots == t.slot_alloc)
         return FMM_OK;
     sets = std::max(sets, t.eval_sets);
     const size_t nb = (size_t)t.nbox, n = (size_t)t.n, PS = (size_t)t.PS;
@@ -881,6 +857,10 @@ fmm_status alloc_eval(Tree& t, int sets) {
     if ((st = ralloc(&t.d_L32, nb * PS * sizeof(float2) * sets))) return st;
     if ((st = ralloc(&t.d_p2p_part, (size_t)t.p2p_cap * t.max_leaf * sizeof(double2) * 3))) return st;
     if ((st = ralloc(&t.d_m2l_part, (size_t)t.m2l_cap * PS * cs * sets))) return st;
+    // strengths in the slot layout: padding slots keep strength zero
+    if ((st = ralloc(&t.d_gamp, (size_t)t.slot_alloc * cs))) return st;
+    FMM_CUDA(cudaMemset(t.d_gamp, 0, (size_t)t.slot_alloc * cs));
+    t.eval_slots = t.slot_alloc;
     // root locals are never written by the passes: they stay zero
     FMM_CUDA(cudaMemset(t.d_L64, 0, nb * PS * sizeof(double2) * sets));
     FMM_CUDA(cudaMemset(t.d_L32, 0, nb * PS * sizeof(float2) * sets));
@@ -906,9 +886,11 @@ fmm_status run_eval(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s)
     const double2* gin = reinterpret_cast<const double2*>(d_gamma);
     const Bufs B = bufs(t, 0);
     if (t.path == FMM_PATH_FP32)
-        k_gather32<<<nblk(n, 256), 256, 0, s>>>(gin, t.d_perm, n, static_cast<float2*>(B.gam));
+        k_gather32<<<nblk(n, 256), 256, 0, s>>>(gin, t.d_perm, t.d_slot_of, n, static_cast<float2*>(B.gam),
+                                                static_cast<float2*>(t.d_gamp));
     else
-        k_gather64<<<nblk(n, 256), 256, 0, s>>>(gin, t.d_perm, n, static_cast<double2*>(B.gam));
+        k_gather64<<<nblk(n, 256), 256, 0, s>>>(gin, t.d_perm, t.d_slot_of, n, static_cast<double2*>(B.gam),
+                                                static_cast<double2*>(t.d_gamp));
     if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[1], s));
     if (!serial) {
         FMM_CUDA(cudaEventRecord(t.ev_fork, s));

@@ -99,7 +99,15 @@ fmm_status build_shape(Tree& t) {
     t.nleaf = (int64_t)t.h_leaves.size();
     t.max_leaf = 1;
     for (int32_t lf : t.h_leaves) t.max_leaf = std::max(t.max_leaf, (int)t.h_bcount[lf]);
+    t.leaf_cap = leaf_capacity(t.max_leaf);
+    if ((t.nleaf + 1) * (int64_t)t.leaf_cap >= (int64_t(1) << 31)) {
+        set_error("too many P2P slots (leaves x leaf capacity)");
+        return FMM_ERR_INVALID_ARG;
+    }
+    std::vector<int32_t> pslot(t.nbox, -1);
+    for (int64_t q = 0; q < t.nleaf; ++q) pslot[t.h_leaves[q]] = (int32_t)(q * t.leaf_cap);
     fmm_status st;
+    if ((st = upload(&t.d_pslot, pslot))) return st;
     if ((st = upload(&t.d_bstart, t.h_bstart))) return st;
     if ((st = upload(&t.d_bcount, t.h_bcount))) return st;
     if ((st = upload(&t.d_parent, t.h_parent))) return st;
@@ -733,24 +741,32 @@ __global__ void __launch_bounds__(kSubThreads) k_subtree(
 
 // Sorted point data: permutation, FP64 copy, FP32 hi/lo split relative to the
 // instance origin (root centre), and the leaf of every sorted position.
+// The P2P operands also go to the leaf slot layout: leaf q's points fill slots
+// q*cap, q*cap+1, ... (pos4 on the FP32 path, the FP64 point on the FP64 path).
 __global__ void k_finalize(const int32_t* __restrict__ Y, int n, const double2* __restrict__ xy,
                            const int32_t* __restrict__ leaf_start /*nleaf+1*/, const int32_t* __restrict__ leaf_ids,
                            int nleaf, const int32_t* __restrict__ inst, const int64_t* __restrict__ inst_box_off,
                            const double2* __restrict__ center, int32_t* perm, double2* pts, float4* pos4,
-                           int32_t* leaf_of) {
+                           int32_t* leaf_of, int cap, int32_t* slot_of, float4* posp32, double2* posp64) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int id = Y[i];
     perm[i] = id;
     const double2 p = xy[id];
     pts[i] = p;
-    const int lf = leaf_ids[find_seg(leaf_start, nleaf, i)];
+    const int q = find_seg(leaf_start, nleaf, i);
+    const int lf = leaf_ids[q];
     leaf_of[i] = lf;
+    const int slot = q * cap + (i - leaf_start[q]);
+    slot_of[i] = slot;
     const double2 o = center[inst_box_off[inst[lf]]];
     const double ex = __dsub_rn(p.x, o.x), ey = __dsub_rn(p.y, o.y);
     const float hx = __double2float_rn(ex), hy = __double2float_rn(ey);
-    pos4[i] = make_float4(hx, hy, __double2float_rn(__dsub_rn(ex, (double)hx)),
-                          __double2float_rn(__dsub_rn(ey, (double)hy)));
+    const float4 v = make_float4(hx, hy, __double2float_rn(__dsub_rn(ex, (double)hx)),
+                                 __double2float_rn(__dsub_rn(ey, (double)hy)));
+    pos4[i] = v;
+    if (posp32) posp32[slot] = v;
+    if (posp64) posp64[slot] = p;
 }
 
 // ================================================================== lists
@@ -768,7 +784,7 @@ __global__ void k_finalize(const int32_t* __restrict__ Y, int n, const double2* 
 __global__ void k_lists_root(const int64_t* __restrict__ inst_box_off, int ninst, int32_t* soff, int32_t* ns,
                              int32_t* sidx, int32_t* sowner, int32_t* woff, int32_t* nw,
                              unsigned long long* lvl_base, const int32_t* __restrict__ child0,
-                             const int32_t* __restrict__ bstart, const int32_t* __restrict__ bcount, int2* srng) {
+                             const int32_t* __restrict__ pslot, const int32_t* __restrict__ bcount, int2* srng) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b == 0) {
         lvl_base[0] = 0;             // strong entries of level 0 start at 0
@@ -784,7 +800,7 @@ __global__ void k_lists_root(const int64_t* __restrict__ inst_box_off, int ninst
     sowner[b] = r;
     woff[r] = 0;
     nw[r] = 0;
-    if (child0[r] < 0) srng[b] = make_int2(bstart[r], bcount[r]);  // a one-level instance: its P2P sources
+    if (child0[r] < 0) srng[b] = make_int2(pslot[r], bcount[r]);  // a one-level instance: its P2P sources
 }
 
 // eq (2.3) in FP64: R + theta*r <= theta*d, with d > 0 required.
@@ -956,7 +972,7 @@ __global__ void __launch_bounds__(kLThreads) k_lists_scatter(
     int l, const unsigned long long* __restrict__ lvl_base, const int32_t* __restrict__ sowner,
     int32_t* __restrict__ soff, int32_t* __restrict__ ns, int32_t* __restrict__ sidx, int32_t* __restrict__ woff,
     int32_t* __restrict__ nw, int32_t* __restrict__ widx, int32_t* __restrict__ sowner_out,
-    const int32_t* __restrict__ child0, const int32_t* __restrict__ bstart, const int32_t* __restrict__ bcount,
+    const int32_t* __restrict__ child0, const int32_t* __restrict__ pslot, const int32_t* __restrict__ bcount,
     int2* __restrict__ srng, const uint8_t* __restrict__ flags, const int32_t* __restrict__ pre_s,
     const int32_t* __restrict__ pre_w, unsigned* status) {
     __shared__ int ws[32], ww[32];
@@ -1000,7 +1016,7 @@ __global__ void __launch_bounds__(kLThreads) k_lists_scatter(
                     const long long qq = bs + ps;
                     sidx[qq] = h;
                     sowner_out[qq] = c.b;
-                    if (leaf) srng[qq] = make_int2(bstart[h], bcount[h]);
+                    if (leaf) srng[qq] = make_int2(pslot[h], bcount[h]);
                     ++ps;
                 } else {
                     widx[bw + pw] = h;
@@ -1153,6 +1169,17 @@ fmm_status alloc_build(Tree& t) {
     if ((st = dalloc(&t.d_leaf_of, n))) return st;
     if ((st = dalloc(&t.d_pts, n))) return st;
     if ((st = dalloc(&t.d_pos4, n))) return st;
+    if ((st = dalloc(&t.d_slot_of, n))) return st;
+    {
+        // slot layout (+1 block of padding); padding stays zero across rebuilds of this shape
+        const int64_t slots = (t.nleaf + 1) * (int64_t)t.leaf_cap;
+        float4* pp = static_cast<float4*>(t.d_posp);
+        t.d_posp = nullptr;
+        if ((st = dalloc(&pp, (size_t)slots))) return st;
+        t.d_posp = pp;
+        FMM_CUDA(cudaMemset(t.d_posp, 0, (size_t)slots * sizeof(float4)));
+        t.slot_alloc = slots;
+    }
     const size_t nb = (size_t)t.nbox;
     if ((st = dalloc(&t.d_center, nb))) return st;
     if ((st = dalloc(&t.d_radius, nb))) return st;
@@ -1252,8 +1279,11 @@ fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s) {
                                                    t.d_radius, t.d_rho, t.d_chl, t.d_rho32, t.d_rad32, t.d_status);
         FMM_CUDA(cudaGetLastError());
     }
+    const bool f32 = t.path == FMM_PATH_FP32;
     k_finalize<<<nblk(n, 256), 256, 0, s>>>(Y, n, xy, t.d_leaf_start, t.leaves.d_ids, (int)t.nleaf, t.d_inst,
-                                            t.d_inst_boxoff, t.d_center, t.d_perm, t.d_pts, t.d_pos4, t.d_leaf_of);
+                                            t.d_inst_boxoff, t.d_center, t.d_perm, t.d_pts, t.d_pos4, t.d_leaf_of,
+                                            t.leaf_cap, t.d_slot_of, f32 ? static_cast<float4*>(t.d_posp) : nullptr,
+                                            f32 ? nullptr : static_cast<double2*>(t.d_posp));
     FMM_CUDA(cudaGetLastError());
     return FMM_OK;
 }
@@ -1264,7 +1294,7 @@ fmm_status run_lists(Tree& t, cudaStream_t s) {
     FMM_CUDA(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), s));
     FMM_CUDA(cudaMemsetAsync(need, 0, 4 * sizeof(unsigned long long), s));
     k_lists_root<<<nblk(t.ninst, 128), 128, 0, s>>>(t.d_inst_boxoff, t.ninst, t.d_soff, t.d_ns, t.d_sidx, t.d_sowner,
-                                                    t.d_woff, t.d_nw, t.d_lvl_base, t.d_child0, t.d_bstart,
+                                                    t.d_woff, t.d_nw, t.d_lvl_base, t.d_child0, t.d_pslot,
                                                     t.d_bcount, t.d_srng);
     const long long tiles_cap = t.cand_cap / kLTile + 2;
     const int grid = t.num_sms * 8;
@@ -1276,7 +1306,7 @@ fmm_status run_lists(Tree& t, cudaStream_t s) {
         k_lists_scan<<<1, 1024, 0, s>>>(l, t.d_lvl_base, t.d_ltile_s, t.d_ltile_w, t.d_lpre_s, t.d_lpre_w,
                                         t.cand_cap, tiles_cap, t.scap_tot, t.wcap_tot, need, t.d_status);
         k_lists_scatter<<<grid, kLThreads, 0, s>>>(l, t.d_lvl_base, t.d_sowner, t.d_soff, t.d_ns, t.d_sidx,
-                                                   t.d_woff, t.d_nw, t.d_widx, t.d_sowner, t.d_child0, t.d_bstart,
+                                                   t.d_woff, t.d_nw, t.d_widx, t.d_sowner, t.d_child0, t.d_pslot,
                                                    t.d_bcount, t.d_srng, t.d_cflags, t.d_lpre_s, t.d_lpre_w,
                                                    t.d_status);
         const LevelList& Ll = t.level_boxes[l];

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfmm2d.so")
-SOURCES = ["tree.cu", "passes.cu", "backward.cu", "api.cu", "autotune.cpp", "noalloc.cu"]
+SOURCES = ["tree.cu", "passes.cu", "m2l_tc.cu", "backward.cu", "api.cu", "autotune.cpp", "noalloc.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

@@ -246,6 +246,11 @@ struct Bufs {
 Bufs bufs(Tree& t, int set);
 void dispatch_far(Tree& t, const Bufs& B, cudaStream_t s);  // P2M, M2M, M2L, L2L of one strength set
 
+// FP32-path M2L on the tensor cores (m2l_tc.cu); FMM_M2L_TC=0 selects the CUDA-core kernel.
+bool m2l_tc_enabled();
+fmm_status m2l_tc_prepare(int P);  // once per compiled order, before launches (and graph capture)
+void launch_m2l_tc(const Tree& t, const float2* M32, float2* Lm2l, float2* part, cudaStream_t s);
+
 // Autotuner (host).
 int default_nlevels(int64_t n, int p, int path);
 

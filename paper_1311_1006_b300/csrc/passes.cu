@@ -679,9 +679,12 @@ static void launch_far_fp32(Tree& t, const Bufs& B, cudaStream_t s) {
                                                                  t.d_center, B.M32, B.M64, B.M32, 1, t.p, t.PS);
     }
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[2], s);
-    k_m2l32<P><<<nblk(t.m2l_cap, 128), 128, 0, s>>>(t.d_m2l_items, item_count(t, 3), t.d_woff, t.d_widx, t.d_chl,
-                                                    t.d_rho32, B.M32, static_cast<float2*>(B.Lm2l),
-                                                    static_cast<float2*>(B.m2l_part), t.PS);
+    if (m2l_tc_enabled())
+        launch_m2l_tc(t, B.M32, static_cast<float2*>(B.Lm2l), static_cast<float2*>(B.m2l_part), s);
+    else
+        k_m2l32<P><<<nblk(t.m2l_cap, 128), 128, 0, s>>>(t.d_m2l_items, item_count(t, 3), t.d_woff, t.d_widx,
+                                                        t.d_chl, t.d_rho32, B.M32, static_cast<float2*>(B.Lm2l),
+                                                        static_cast<float2*>(B.m2l_part), t.PS);
     k_reduce_m2l<float2><<<nblk(32 * t.nbox, 256), 256, 0, s>>>((int)t.nbox, t.d_box_m2l,
                                                                static_cast<const float2*>(B.m2l_part), t.PS,
                                                                static_cast<float2*>(B.Lm2l));
@@ -857,6 +860,7 @@ fmm_status alloc_eval(Tree& t, int sets) {
     if ((st = ralloc(&t.d_L32, nb * PS * sizeof(float2) * sets))) return st;
     if ((st = ralloc(&t.d_p2p_part, (size_t)t.p2p_cap * t.max_leaf * sizeof(double2) * 3))) return st;
     if ((st = ralloc(&t.d_m2l_part, (size_t)t.m2l_cap * PS * cs * sets))) return st;
+    if (t.path == FMM_PATH_FP32 && m2l_tc_enabled() && (st = m2l_tc_prepare(t.P))) return st;
     // strengths in the slot layout: padding slots keep strength zero
     if ((st = ralloc(&t.d_gamp, (size_t)t.slot_alloc * cs))) return st;
     FMM_CUDA(cudaMemset(t.d_gamp, 0, (size_t)t.slot_alloc * cs));

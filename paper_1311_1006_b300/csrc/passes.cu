@@ -50,6 +50,23 @@ static constexpr BinomTable make_binom() {
 }
 __constant__ BinomTable c_binom = make_binom();
 
+// n! and 1/n! for n < 32 (lane-indexed by the warp-per-shift kernels).
+struct FactTable {
+    double f[32];
+    double inv[32];
+};
+static constexpr FactTable make_fact() {
+    FactTable t{};
+    double x = 1.0;
+    for (int n = 0; n < 32; ++n) {
+        if (n > 0) x *= n;
+        t.f[n] = x;
+        t.inv[n] = 1.0 / x;
+    }
+    return t;
+}
+__constant__ FactTable c_fact = make_fact();
+
 // ------------------------------------------------------------------ gather
 
 // Strengths into sorted order and into the leaf slot layout of the P2P pass.
@@ -397,6 +414,141 @@ __global__ void __launch_bounds__(128) k_l2l(const int32_t* __restrict__ boxes, 
     }
 }
 
+// ---- M2M / L2L for levels with few boxes: one warp per shift -----------------
+// FP64 warp instructions are expensive per issue on this GPU (the FP64 pipe
+// takes many cycles per warp instruction whatever the number of active
+// lanes), so a level with few boxes run as one thread per shift is bound by
+// one warp's ~p^2/2 complex FMAs.  Here lane n computes output coefficient n
+// of one shift as a convolution,
+//   M2M  at'_n = n! sum_{k<=n} (sigma^k at_k / k!) (q^(n-k) / (n-k)!)
+//   L2L  bt'_m = (sigma^m / m!) sum_{l>=m} (l! bt_l) (q^(l-m) / (l-m)!)
+// (the binomial shifts of the header comment with C(n,k) = n!/(k!(n-k)!)),
+// with the powers of sigma and q from a scan across lanes: ~p complex FMAs
+// per lane spread over many warps.
+
+// a_lane = x^lane by a Hillis-Steele product scan across the warp
+__device__ __forceinline__ double2 lane_pow(double2 x, int lane) {
+    double2 a = lane == 0 ? make_double2(1.0, 0.0) : x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const double2 y = make_double2(__shfl_up_sync(0xffffffffu, a.x, d), __shfl_up_sync(0xffffffffu, a.y, d));
+        if (lane >= d) a = cmul(a, y);
+    }
+    return a;
+}
+__device__ __forceinline__ double lane_pow(double x, int lane) {
+    double a = lane == 0 ? 1.0 : x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, a, d);
+        if (lane >= d) a *= y;
+    }
+    return a;
+}
+__device__ __forceinline__ double2 shfl2(double2 v, int src) {
+    return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// One CTA of 4 warps per parent; warp c shifts child c, and the four shifted
+// expansions are added in a fixed order ((c0 + c1) + (c2 + c3)).
+template <int P>
+__global__ void __launch_bounds__(128) k_m2m_warp(const int32_t* __restrict__ parents, int cnt,
+                                                  const int32_t* __restrict__ child0, const double* __restrict__ rho,
+                                                  const double2* __restrict__ center,
+                                                  const float2* __restrict__ M32in, double2* __restrict__ M64,
+                                                  float2* __restrict__ M32out, int fp32_path, int p, int PS) {
+    __shared__ double2 part[4][32];
+    const int pi = blockIdx.x;
+    if (pi >= cnt) return;
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = parents[pi];
+    const int h = child0[b] + c;
+    const double rP = rho[b];
+    const double inv = rP > 0.0 ? 1.0 / rP : 0.0;
+    const double sigma = rho[h] * inv;
+    const double2 cP = center[b], ch = center[h];
+    const double2 q = make_double2((ch.x - cP.x) * inv, (ch.y - cP.y) * inv);
+    double2 v = make_double2(0.0, 0.0);
+    if (lane < P) {
+        if (fp32_path && child0[h] < 0) {
+            const float2 f = M32in[(size_t)h * PS + lane];
+            v = make_double2((double)f.x, (double)f.y);
+        } else {
+            v = M64[(size_t)h * PS + lane];
+        }
+    }
+    const double sk = lane_pow(sigma, lane);
+    const double2 qk = lane_pow(q, lane);
+    const double ifk = c_fact.inv[lane];
+    const double ys = sk * ifk;
+    const double2 y = make_double2(v.x * ys, v.y * ys);
+    const double2 z = make_double2(qk.x * ifk, qk.y * ifk);
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        const double2 yk = shfl2(y, k);
+        const double2 zz = shfl2(z, (lane - k) & 31);
+        if (k <= lane) acc = cfma(yk, zz, acc);
+    }
+    const double fn = c_fact.f[lane];
+    part[c][lane] = make_double2(acc.x * fn, acc.y * fn);
+    __syncthreads();
+    if (c != 0 || lane >= P) return;
+    const double2 s01 = make_double2(part[0][lane].x + part[1][lane].x, part[0][lane].y + part[1][lane].y);
+    const double2 s23 = make_double2(part[2][lane].x + part[3][lane].x, part[2][lane].y + part[3][lane].y);
+    const double2 s = lane < p ? make_double2(s01.x + s23.x, s01.y + s23.y) : make_double2(0.0, 0.0);
+    M64[(size_t)b * PS + lane] = s;
+    if (fp32_path) M32out[(size_t)b * PS + lane] = make_float2((float)s.x, (float)s.y);
+}
+
+// One warp per child box: shifted parent local + the box's own M2L sum.
+template <int P, typename LM>
+__global__ void __launch_bounds__(128) k_l2l_warp(const int32_t* __restrict__ boxes, int cnt,
+                                                  const int32_t* __restrict__ parent,
+                                                  const int32_t* __restrict__ child0, const double* __restrict__ rho,
+                                                  const double2* __restrict__ center,
+                                                  const int2* __restrict__ box_m2l, const LM* __restrict__ Lm2l,
+                                                  double2* __restrict__ L64, float2* __restrict__ L32, int p, int PS) {
+    const int qi = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (qi >= cnt) return;  // warp-uniform
+    const int c = boxes[qi];
+    const int Pb = parent[c];
+    const double rP = rho[Pb];
+    const double inv = rP > 0.0 ? 1.0 / rP : 0.0;
+    const double2 cP = center[Pb], cc = center[c];
+    const double2 q = make_double2((cc.x - cP.x) * inv, (cc.y - cP.y) * inv);
+    const double sigma = rho[c] * inv;
+    const double2 bl = lane < P ? L64[(size_t)Pb * PS + lane] : make_double2(0.0, 0.0);
+    const double sk = lane_pow(sigma, lane);
+    const double2 qk = lane_pow(q, lane);
+    const double fl = c_fact.f[lane], ifl = c_fact.inv[lane];
+    const double2 y = make_double2(bl.x * fl, bl.y * fl);
+    const double2 z = make_double2(qk.x * ifl, qk.y * ifl);
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int l = 0; l < P; ++l) {
+        const double2 yl = shfl2(y, l);
+        const double2 zz = shfl2(z, (l - lane) & 31);
+        if (l >= lane) acc = cfma(yl, zz, acc);
+    }
+    if (lane >= P) return;
+    const double scale = sk * ifl;
+    const int2 mi = box_m2l[c];
+    double2 own = make_double2(0.0, 0.0);
+    if (mi.y > 0) {
+        const LM o = Lm2l[(size_t)c * PS + lane];
+        own = make_double2((double)o.x, (double)o.y);
+    }
+    double2 v = make_double2(fma(acc.x, scale, own.x), fma(acc.y, scale, own.y));
+    if (lane >= p) v = make_double2(0.0, 0.0);
+    L64[(size_t)c * PS + lane] = v;
+    if (L32 != nullptr && child0[c] < 0) L32[(size_t)c * PS + lane] = make_float2((float)v.x, (float)v.y);
+}
+
+// Levels with at most this many shifts use the warp-per-shift kernels.
+constexpr int kWarpShiftMax = 4096;
+
 // ------------------------------------------------------------- L2P + sum
 
 // One thread per sorted point: far field by Horner from the leaf's local
@@ -675,8 +827,12 @@ static void launch_far_fp32(Tree& t, const Bufs& B, cudaStream_t s) {
     for (int l = t.Lmax - 2; l >= 0; --l) {
         const LevelList& L = t.level_parents[l];
         if (!L.count) continue;
-        k_m2m<P><<<nblk(4 * (int64_t)L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_child0, t.d_rho,
-                                                                 t.d_center, B.M32, B.M64, B.M32, 1, t.p, t.PS);
+        if (4 * (int64_t)L.count <= kWarpShiftMax)
+            k_m2m_warp<P><<<L.count, 128, 0, s>>>(L.d_ids, L.count, t.d_child0, t.d_rho, t.d_center, B.M32, B.M64,
+                                                  B.M32, 1, t.p, t.PS);
+        else
+            k_m2m<P><<<nblk(4 * (int64_t)L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_child0, t.d_rho,
+                                                                     t.d_center, B.M32, B.M64, B.M32, 1, t.p, t.PS);
     }
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[2], s);
     if (m2l_tc_enabled())
@@ -691,9 +847,14 @@ static void launch_far_fp32(Tree& t, const Bufs& B, cudaStream_t s) {
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[3], s);
     for (int l = 0; l + 1 < t.Lmax; ++l) {
         const LevelList& L = t.level_boxes[l + 1];
-        k_l2l<P, float2><<<nblk(L.count, 128), 128, 0, s>>>(
-            L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho, t.d_center, t.d_box_m2l,
-            static_cast<const float2*>(B.Lm2l), B.L64, B.L32, t.p, t.PS);
+        if (L.count <= kWarpShiftMax)
+            k_l2l_warp<P, float2><<<nblk(32 * (int64_t)L.count, 128), 128, 0, s>>>(
+                L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho, t.d_center, t.d_box_m2l,
+                static_cast<const float2*>(B.Lm2l), B.L64, B.L32, t.p, t.PS);
+        else
+            k_l2l<P, float2><<<nblk(L.count, 128), 128, 0, s>>>(
+                L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho, t.d_center, t.d_box_m2l,
+                static_cast<const float2*>(B.Lm2l), B.L64, B.L32, t.p, t.PS);
     }
 }
 
@@ -705,8 +866,13 @@ static void launch_far_fp64(Tree& t, const Bufs& B, cudaStream_t s) {
     for (int l = t.Lmax - 2; l >= 0; --l) {
         const LevelList& L = t.level_parents[l];
         if (!L.count) continue;
-        k_m2m<P><<<nblk(4 * (int64_t)L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_child0, t.d_rho,
-                                                                 t.d_center, nullptr, B.M64, nullptr, 0, t.p, t.PS);
+        if (4 * (int64_t)L.count <= kWarpShiftMax)
+            k_m2m_warp<P><<<L.count, 128, 0, s>>>(L.d_ids, L.count, t.d_child0, t.d_rho, t.d_center, nullptr,
+                                                  B.M64, nullptr, 0, t.p, t.PS);
+        else
+            k_m2m<P><<<nblk(4 * (int64_t)L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_child0, t.d_rho,
+                                                                     t.d_center, nullptr, B.M64, nullptr, 0, t.p,
+                                                                     t.PS);
     }
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[2], s);
     k_m2l64<P><<<nblk(t.m2l_cap, 128), 128, 0, s>>>(t.d_m2l_items, item_count(t, 3), t.d_woff, t.d_widx,
@@ -718,9 +884,14 @@ static void launch_far_fp64(Tree& t, const Bufs& B, cudaStream_t s) {
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[3], s);
     for (int l = 0; l + 1 < t.Lmax; ++l) {
         const LevelList& L = t.level_boxes[l + 1];
-        k_l2l<P, double2><<<nblk(L.count, 128), 128, 0, s>>>(
-            L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho, t.d_center, t.d_box_m2l,
-            static_cast<const double2*>(B.Lm2l), B.L64, nullptr, t.p, t.PS);
+        if (L.count <= kWarpShiftMax)
+            k_l2l_warp<P, double2><<<nblk(32 * (int64_t)L.count, 128), 128, 0, s>>>(
+                L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho, t.d_center, t.d_box_m2l,
+                static_cast<const double2*>(B.Lm2l), B.L64, nullptr, t.p, t.PS);
+        else
+            k_l2l<P, double2><<<nblk(L.count, 128), 128, 0, s>>>(
+                L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho, t.d_center, t.d_box_m2l,
+                static_cast<const double2*>(B.Lm2l), B.L64, nullptr, t.p, t.PS);
     }
 }
 

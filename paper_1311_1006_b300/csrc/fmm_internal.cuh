@@ -35,10 +35,20 @@ inline P2PLayout p2p_layout(int max_leaf) {
     if (max_leaf <= 64) return {8, 8};
     return {8, 16};
 }
-// Slots per leaf: max_leaf rounded up to whole source steps of the layout.
+// FP32 path: lanes take PAIRS of source slots (packed f32x2 arithmetic), so a
+// step covers 2 * 32/lt slots.
+inline P2PLayout p2p_pair_layout(int max_leaf) {
+    if (max_leaf <= 8) return {2, 4};
+    if (max_leaf <= 16) return {4, 4};
+    if (max_leaf <= 32) return {4, 8};
+    if (max_leaf <= 64) return {4, 16};
+    return {8, 16};
+}
+// Slots per leaf: max_leaf rounded up to whole source steps of both layouts
+// (the pair layout's step is a multiple of the scalar layout's).
 inline int leaf_capacity(int max_leaf) {
-    const int S = 32 / p2p_layout(max_leaf).lt;
-    return (max_leaf + S - 1) / S * S;
+    const int step = 2 * (32 / p2p_pair_layout(max_leaf).lt);
+    return (max_leaf + step - 1) / step * step;
 }
 
 // Work-item sizes: P2P items hold about this many source points; M2L items at
@@ -127,7 +137,8 @@ struct Tree {
     int32_t* d_leaf_of = nullptr;  // sorted position -> leaf box id
     double2* d_pts = nullptr;      // sorted FP64 points
     float4* d_pos4 = nullptr;      // sorted (x_hi, y_hi, x_lo, y_lo) relative to the instance origin
-    void* d_posp = nullptr;        // slot layout: pos4 (FP32 path) or FP64 points, 16 B per slot
+    void* d_posp = nullptr;        // slot layout, 16 B per slot: FP64 points, or on the FP32 path the
+                                   // pair-interleaved hi/lo coordinates (see k_finalize)
     int32_t* d_slot_of = nullptr;  // sorted position -> slot
     int64_t slot_alloc = 0;        // slots d_posp was allocated for
     double2* d_center = nullptr;   // per box

@@ -69,15 +69,19 @@ __constant__ FactTable c_fact = make_fact();
 
 // ------------------------------------------------------------------ gather
 
-// Strengths into sorted order and into the leaf slot layout of the P2P pass.
+// Strengths into sorted order and into the leaf slot layout of the P2P pass
+// (FP32: slot pairs interleaved as (re[2m], re[2m+1], im[2m], im[2m+1])).
 __global__ void k_gather32(const double2* __restrict__ in, const int32_t* __restrict__ perm,
-                           const int32_t* __restrict__ slot_of, int n, float2* out, float2* outp) {
+                           const int32_t* __restrict__ slot_of, int n, float2* out, float* outp) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double2 g = in[perm[i]];
     const float2 v = make_float2((float)g.x, (float)g.y);
     out[i] = v;
-    outp[slot_of[i]] = v;
+    const int slot = slot_of[i];
+    float* f = outp + 4 * (slot >> 1) + (slot & 1);
+    f[0] = v.x;
+    f[2] = v.y;
 }
 __global__ void k_gather64(const double2* __restrict__ in, const int32_t* __restrict__ perm,
                            const int32_t* __restrict__ slot_of, int n, double2* out, double2* outp) {
@@ -749,6 +753,201 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, sizeof(C) == 8 ? 5 : 1)
     }
 }
 
+// ---- FP32 P2P with packed f32x2 arithmetic ----------------------------------
+// Same work items and slot layout as above, but a lane takes a PAIR of source
+// slots per step and every instruction is a 2-wide FP32 operation: one target
+// (duplicated into both halves once per target tile) against two sources.
+// Per pair of interactions: 14 f32x2 instructions and 2 reciprocals, half the
+// FP32 instruction issue of the scalar kernel.  Lane (tg, ss): targets tg,
+// tg+LT, ... and pair slice ss of S = 32/LT; a step covers 2S slots.  Each
+// packed accumulator holds two partial sums (even / odd source slots), added
+// at the end before the shuffle reduction over slices.
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x f2pk(float lo, float hi) {
+    f2x r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2upk(f2x v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2x f2add(f2x a, f2x b) {
+    f2x d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2x f2sub(f2x a, f2x b) {
+    f2x d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2x f2mul(f2x a, f2x b) {
+    f2x d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2x f2fma(f2x a, f2x b, f2x c) {
+    f2x d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// Two sources (packed) against one target: Gamma_j conj(d)/|d|^2 with
+// d = z_t - z_j from the hi/lo coordinates; the coincident-pair guard is
+// folded into |d|^2 (+1e-37f) as in the scalar kernel.
+struct SrcPair {
+    f2x x, y, xl, yl, gx, gy, ngx;
+};
+__device__ __forceinline__ SrcPair src_pair(const ulonglong2 a, const ulonglong2 b, const ulonglong2 g) {
+    SrcPair s;
+    s.x = a.x;
+    s.y = a.y;
+    s.xl = b.x;
+    s.yl = b.y;
+    s.gx = g.x;
+    s.gy = g.y;
+    s.ngx = f2mul(g.x, f2pk(-1.f, -1.f));
+    return s;
+}
+__device__ __forceinline__ void p2p_pair(const f2x tx, const f2x ty, const f2x txl, const f2x tyl, const SrcPair& s,
+                                         f2x& ax, f2x& ay) {
+    const f2x dx = f2add(f2sub(tx, s.x), f2sub(txl, s.xl));
+    const f2x dy = f2add(f2sub(ty, s.y), f2sub(tyl, s.yl));
+    const f2x r2 = f2fma(dx, dx, f2fma(dy, dy, f2pk(1e-37f, 1e-37f)));
+    float r0, r1;
+    f2upk(r2, r0, r1);
+    const f2x inv = f2pk(rcp_approx(r0), rcp_approx(r1));
+    const f2x a = f2mul(dx, inv), b = f2mul(dy, inv);
+    ax = f2fma(s.gx, a, f2fma(s.gy, b, ax));   // gx a + gy b
+    ay = f2fma(s.gy, a, f2fma(s.ngx, b, ay));  // gy a - gx b
+}
+
+template <int TPL, int LT>
+__global__ void __launch_bounds__(kP2PDWarps * 32, TPL > 4 ? 2 : 4)
+    k_p2p_pairs(const int4* __restrict__ items, const unsigned long long* __restrict__ nitems,
+                unsigned* __restrict__ next_item, const int32_t* __restrict__ bstart,
+                const int32_t* __restrict__ bcount, const int32_t* __restrict__ pslot,
+                const int32_t* __restrict__ soff, const int2* __restrict__ srng, const ulonglong2* __restrict__ posq,
+                const ulonglong2* __restrict__ gamq, float2* __restrict__ nearv, float2* __restrict__ part, int TS,
+                int pad) {
+    constexpr int S = 32 / LT;      // pair slices
+    constexpr bool LONG = LT > 4;   // the LT = 4 layouts hold leaves of at most 16 = 2S slots
+    const int lane = threadIdx.x & 31;
+    const int tg = lane % LT, ss = lane / LT;
+    const int nit = (int)*nitems;
+    while (true) {
+        int it = 0;
+        if (lane == 0) it = (int)atomicAdd(next_item, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= nit) break;
+        const int4 item = items[it];
+        const int b = item.x;
+        const int ts = bstart[b], tn = bcount[b], tb = pslot[b];
+        const int2* rl = srng + soff[b];
+        const int ke = item.z;
+        for (int t0 = 0; t0 < tn; t0 += TPL * LT) {
+            f2x tx[TPL], ty[TPL], txl[TPL], tyl[TPL], ax[TPL], ay[TPL];
+#pragma unroll
+            for (int u = 0; u < TPL; ++u) {
+                const int idx = t0 + tg + u * LT;
+                float x = 0.f, y = 0.f, xl = 0.f, yl = 0.f;
+                if (idx < tn) {
+                    const int sl = tb + idx;
+                    const float* f = reinterpret_cast<const float*>(posq) + 8 * (sl >> 1) + (sl & 1);
+                    x = f[0];
+                    y = f[2];
+                    xl = f[4];
+                    yl = f[6];
+                }
+                tx[u] = f2pk(x, x);
+                ty[u] = f2pk(y, y);
+                txl[u] = f2pk(xl, xl);
+                tyl[u] = f2pk(yl, yl);
+                ax[u] = 0ull;
+                ay[u] = 0ull;
+            }
+            if constexpr (!LONG) {
+                // slot-pair index of range k's slice ss (the padding block past the end)
+#define FMM_PIDX(k) ((((k) < ke ? rl[(k)].x : pad) >> 1) + ss)
+                int k = item.y;
+                int oa0 = FMM_PIDX(k), oa1 = FMM_PIDX(k + 1);
+                ulonglong2 pa0 = posq[2 * oa0], qa0 = posq[2 * oa0 + 1], ga0 = gamq[oa0];
+                ulonglong2 pa1 = posq[2 * oa1], qa1 = posq[2 * oa1 + 1], ga1 = gamq[oa1];
+                int ob0 = FMM_PIDX(k + 2), ob1 = FMM_PIDX(k + 3);
+                while (true) {
+                    const ulonglong2 pb0 = posq[2 * ob0], qb0 = posq[2 * ob0 + 1], gb0 = gamq[ob0];
+                    const ulonglong2 pb1 = posq[2 * ob1], qb1 = posq[2 * ob1 + 1], gb1 = gamq[ob1];
+                    oa0 = FMM_PIDX(k + 4);
+                    oa1 = FMM_PIDX(k + 5);
+                    {
+                        const SrcPair s0 = src_pair(pa0, qa0, ga0), s1 = src_pair(pa1, qa1, ga1);
+#pragma unroll
+                        for (int u = 0; u < TPL; ++u) p2p_pair(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
+#pragma unroll
+                        for (int u = 0; u < TPL; ++u) p2p_pair(tx[u], ty[u], txl[u], tyl[u], s1, ax[u], ay[u]);
+                    }
+                    if (k + 2 >= ke) break;
+                    pa0 = posq[2 * oa0];
+                    qa0 = posq[2 * oa0 + 1];
+                    ga0 = gamq[oa0];
+                    pa1 = posq[2 * oa1];
+                    qa1 = posq[2 * oa1 + 1];
+                    ga1 = gamq[oa1];
+                    ob0 = FMM_PIDX(k + 6);
+                    ob1 = FMM_PIDX(k + 7);
+                    {
+                        const SrcPair s0 = src_pair(pb0, qb0, gb0), s1 = src_pair(pb1, qb1, gb1);
+#pragma unroll
+                        for (int u = 0; u < TPL; ++u) p2p_pair(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
+#pragma unroll
+                        for (int u = 0; u < TPL; ++u) p2p_pair(tx[u], ty[u], txl[u], tyl[u], s1, ax[u], ay[u]);
+                    }
+                    k += 4;
+                    if (k >= ke) break;
+                }
+#undef FMM_PIDX
+            } else {
+                for (int k = item.y; k < ke; ++k) {
+                    const int2 r = rl[k];
+                    const int o = (r.x >> 1) + ss;  // slot-pair index of this slice
+                    int e = 0;                      // slot-pair offset of the step
+                    for (; 2 * (e + S) < r.y; e += 2 * S) {  // two steps, both inside the range's slots
+                        const SrcPair s0 = src_pair(posq[2 * (o + e)], posq[2 * (o + e) + 1], gamq[o + e]);
+                        const SrcPair s1 =
+                            src_pair(posq[2 * (o + e + S)], posq[2 * (o + e + S) + 1], gamq[o + e + S]);
+#pragma unroll
+                        for (int u = 0; u < TPL; ++u) p2p_pair(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
+#pragma unroll
+                        for (int u = 0; u < TPL; ++u) p2p_pair(tx[u], ty[u], txl[u], tyl[u], s1, ax[u], ay[u]);
+                    }
+                    if (2 * e < r.y) {
+                        const SrcPair s0 = src_pair(posq[2 * (o + e)], posq[2 * (o + e) + 1], gamq[o + e]);
+#pragma unroll
+                        for (int u = 0; u < TPL; ++u) p2p_pair(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < TPL; ++u) {
+                float x0, x1, y0, y1;
+                f2upk(ax[u], x0, x1);
+                f2upk(ay[u], y0, y1);
+                float2 tot = make_float2(x0 + x1, y0 + y1);
+#pragma unroll
+                for (int o = LT; o < 32; o <<= 1) {
+                    tot.x += __shfl_xor_sync(0xffffffffu, tot.x, o);
+                    tot.y += __shfl_xor_sync(0xffffffffu, tot.y, o);
+                }
+                const int idx = t0 + tg + u * LT;
+                if (ss == 0 && idx < tn) {
+                    if (item.w < 0) nearv[ts + idx] = tot;
+                    else part[(size_t)it * TS + idx] = tot;
+                }
+            }
+        }
+    }
+}
+
 // Near field of leaves whose strong list was split into several items: one
 // warp per leaf adds the item partial sums of each target in item order.
 template <typename C>
@@ -944,7 +1143,20 @@ static void launch_p2p(Tree& t, const Bufs& B, cudaStream_t s) {
     if (t.path == FMM_PATH_FP32) {
         float2* nv = static_cast<float2*>(B.near);
         float2* pt = static_cast<float2*>(B.p2p_part);
-        FMM_P2P_LAYOUTS(float4, float2)
+        const P2PLayout pl = p2p_pair_layout(t.max_leaf);
+#define FMM_P2P_PAIRS(TPL, LT)                                                                                   \
+    k_p2p_pairs<TPL, LT><<<dgrid, kP2PDWarps * 32, 0, s>>>(                                                       \
+        t.d_p2p_items, cnt, next, t.d_bstart, t.d_bcount, t.d_pslot, t.d_soff, t.d_srng,                          \
+        static_cast<const ulonglong2*>(t.d_posp), static_cast<const ulonglong2*>(t.d_gamp), nv, pt, t.max_leaf,   \
+        pad);
+        switch (pl.tpl * 100 + pl.lt) {
+            case 204: FMM_P2P_PAIRS(2, 4) break;
+            case 404: FMM_P2P_PAIRS(4, 4) break;
+            case 408: FMM_P2P_PAIRS(4, 8) break;
+            case 416: FMM_P2P_PAIRS(4, 16) break;
+            default: FMM_P2P_PAIRS(8, 16) break;
+        }
+#undef FMM_P2P_PAIRS
         k_reduce_p2p<float2><<<rgrid, 256, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, t.d_leaf_items, t.d_bstart,
                                                    t.d_bcount, pt, t.max_leaf, nv);
     } else {
@@ -1062,7 +1274,7 @@ fmm_status run_eval(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s)
     const Bufs B = bufs(t, 0);
     if (t.path == FMM_PATH_FP32)
         k_gather32<<<nblk(n, 256), 256, 0, s>>>(gin, t.d_perm, t.d_slot_of, n, static_cast<float2*>(B.gam),
-                                                static_cast<float2*>(t.d_gamp));
+                                                static_cast<float*>(t.d_gamp));
     else
         k_gather64<<<nblk(n, 256), 256, 0, s>>>(gin, t.d_perm, t.d_slot_of, n, static_cast<double2*>(B.gam),
                                                 static_cast<double2*>(t.d_gamp));

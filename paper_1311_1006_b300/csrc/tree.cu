@@ -742,12 +742,14 @@ __global__ void __launch_bounds__(kSubThreads) k_subtree(
 // Sorted point data: permutation, FP64 copy, FP32 hi/lo split relative to the
 // instance origin (root centre), and the leaf of every sorted position.
 // The P2P operands also go to the leaf slot layout: leaf q's points fill slots
-// q*cap, q*cap+1, ... (pos4 on the FP32 path, the FP64 point on the FP64 path).
+// q*cap, q*cap+1, ...  FP64 path: the point per slot.  FP32 path: slots are
+// interleaved in pairs (2m, 2m+1) for packed f32x2 arithmetic, as two float4
+// (x_hi[2m], x_hi[2m+1], y_hi[2m], y_hi[2m+1]), (x_lo.., x_lo.., y_lo.., y_lo..).
 __global__ void k_finalize(const int32_t* __restrict__ Y, int n, const double2* __restrict__ xy,
                            const int32_t* __restrict__ leaf_start /*nleaf+1*/, const int32_t* __restrict__ leaf_ids,
                            int nleaf, const int32_t* __restrict__ inst, const int64_t* __restrict__ inst_box_off,
                            const double2* __restrict__ center, int32_t* perm, double2* pts, float4* pos4,
-                           int32_t* leaf_of, int cap, int32_t* slot_of, float4* posp32, double2* posp64) {
+                           int32_t* leaf_of, int cap, int32_t* slot_of, float* posp32, double2* posp64) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int id = Y[i];
@@ -765,7 +767,13 @@ __global__ void k_finalize(const int32_t* __restrict__ Y, int n, const double2* 
     const float4 v = make_float4(hx, hy, __double2float_rn(__dsub_rn(ex, (double)hx)),
                                  __double2float_rn(__dsub_rn(ey, (double)hy)));
     pos4[i] = v;
-    if (posp32) posp32[slot] = v;
+    if (posp32) {
+        float* f = posp32 + 8 * (slot >> 1) + (slot & 1);
+        f[0] = v.x;
+        f[2] = v.y;
+        f[4] = v.z;
+        f[6] = v.w;
+    }
     if (posp64) posp64[slot] = p;
 }
 
@@ -1282,7 +1290,7 @@ fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s) {
     const bool f32 = t.path == FMM_PATH_FP32;
     k_finalize<<<nblk(n, 256), 256, 0, s>>>(Y, n, xy, t.d_leaf_start, t.leaves.d_ids, (int)t.nleaf, t.d_inst,
                                             t.d_inst_boxoff, t.d_center, t.d_perm, t.d_pts, t.d_pos4, t.d_leaf_of,
-                                            t.leaf_cap, t.d_slot_of, f32 ? static_cast<float4*>(t.d_posp) : nullptr,
+                                            t.leaf_cap, t.d_slot_of, f32 ? static_cast<float*>(t.d_posp) : nullptr,
                                             f32 ? nullptr : static_cast<double2*>(t.d_posp));
     FMM_CUDA(cudaGetLastError());
     return FMM_OK;

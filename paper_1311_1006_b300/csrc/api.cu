@@ -82,9 +82,17 @@ static fmm_status ensure_streams(Tree& t) {
     int dev = 0;
     FMM_CUDA(cudaGetDevice(&dev));
     FMM_CUDA(cudaDeviceGetAttribute(&t.num_sms, cudaDevAttrMultiProcessorCount, dev));
-    if (!t.s_aux) FMM_CUDA(cudaStreamCreateWithFlags(&t.s_aux, cudaStreamNonBlocking));
+    // The evaluation forks the far-field chain (a sequence of short, partly
+    // latency-bound kernels) onto a high-priority stream and the P2P pass onto
+    // a low-priority one, so that far-field blocks are scheduled first as P2P
+    // blocks retire.
+    int lo_prio = 0, hi_prio = 0;
+    FMM_CUDA(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+    if (!t.s_aux) FMM_CUDA(cudaStreamCreateWithPriority(&t.s_aux, cudaStreamNonBlocking, lo_prio));
+    if (!t.s_far) FMM_CUDA(cudaStreamCreateWithPriority(&t.s_far, cudaStreamNonBlocking, hi_prio));
     if (!t.ev_fork) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_fork, cudaEventDisableTiming));
     if (!t.ev_join) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_join, cudaEventDisableTiming));
+    if (!t.ev_join_far) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_join_far, cudaEventDisableTiming));
     for (auto& e : t.ev_t)
         if (!e) FMM_CUDA(cudaEventCreate(&e));
     return FMM_OK;
@@ -187,6 +195,8 @@ static void release(Tree* t) {
         if (s.d_nzero) cudaFree(s.d_nzero);
     }
     if (t->s_aux) cudaStreamDestroy(t->s_aux);
+    if (t->s_far) cudaStreamDestroy(t->s_far);
+    if (t->ev_join_far) cudaEventDestroy(t->ev_join_far);
     if (t->ev_fork) cudaEventDestroy(t->ev_fork);
     if (t->ev_join) cudaEventDestroy(t->ev_join);
     for (auto e : t->ev_t)

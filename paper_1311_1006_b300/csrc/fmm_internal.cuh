@@ -188,8 +188,9 @@ struct Tree {
     int eval_PS = 0, eval_path = -1, eval_sets = 0;
 
     // streams / events
-    cudaStream_t s_aux = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t s_aux = nullptr;  // P2P (lowest priority)
+    cudaStream_t s_far = nullptr;  // far-field chain (highest priority)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join_far = nullptr;
     cudaEvent_t ev_t[8] = {};
     bool timing_valid = false;
 

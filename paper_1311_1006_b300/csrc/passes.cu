@@ -658,13 +658,14 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, sizeof(C) == 8 ? 5 : 1)
                 unsigned* __restrict__ next_item, const int32_t* __restrict__ bstart,
                 const int32_t* __restrict__ bcount, const int32_t* __restrict__ pslot,
                 const int32_t* __restrict__ soff, const int2* __restrict__ srng, const V* __restrict__ posp,
-                const C* __restrict__ gamp, C* __restrict__ nearv, C* __restrict__ part, int TS, int pad) {
+                const C* __restrict__ gamp, C* __restrict__ nearv, C* __restrict__ part, int TS, int pad,
+                int per_warp) {
     constexpr int S = 32 / LT;
     constexpr bool LONG = LT > 2;
     const int lane = threadIdx.x & 31;
     const int tg = lane % LT, ss = lane / LT;
     const int nit = (int)*nitems;
-    while (true) {
+    for (int done = 0; done < per_warp; ++done) {
         int it = 0;
         if (lane == 0) it = (int)atomicAdd(next_item, 1u);
         it = __shfl_sync(0xffffffffu, it, 0);
@@ -829,13 +830,13 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, TPL > 4 ? 2 : 4)
                 const int32_t* __restrict__ bcount, const int32_t* __restrict__ pslot,
                 const int32_t* __restrict__ soff, const int2* __restrict__ srng, const ulonglong2* __restrict__ posq,
                 const ulonglong2* __restrict__ gamq, float2* __restrict__ nearv, float2* __restrict__ part, int TS,
-                int pad) {
+                int pad, int per_warp) {
     constexpr int S = 32 / LT;      // pair slices
     constexpr bool LONG = LT > 4;   // the LT = 4 layouts hold leaves of at most 16 = 2S slots
     const int lane = threadIdx.x & 31;
     const int tg = lane % LT, ss = lane / LT;
     const int nit = (int)*nitems;
-    while (true) {
+    for (int done = 0; done < per_warp; ++done) {
         int it = 0;
         if (lane == 0) it = (int)atomicAdd(next_item, 1u);
         it = __shfl_sync(0xffffffffu, it, 0);
@@ -1108,11 +1109,22 @@ static void launch_l2p(Tree& t, const Bufs& B, void* d_phi, cudaStream_t s) {
     }
 }
 
-// Blocks per SM of the P2P grid (FMM_P2P_BLOCKS_PER_SM overrides the default).
+// Work items one P2P warp takes before it exits (FMM_P2P_ITEMS_PER_WARP
+// overrides; 0 = persistent grid of FMM_P2P_BLOCKS_PER_SM blocks per SM).
+// Bounded warps let blocks retire during the pass, so the far-field kernels
+// on the high-priority stream get SM slots while P2P runs.
+constexpr int kP2PItemsPerWarp = 4;
+static int env_int(const char* name, int dflt) {
+    const char* e = getenv(name);
+    return e ? atoi(e) : dflt;
+}
+static int p2p_items_per_warp() {
+    static int v = env_int("FMM_P2P_ITEMS_PER_WARP", kP2PItemsPerWarp);
+    return v;
+}
 static int p2p_blocks_per_sm() {
     static int v = [] {
-        const char* e = getenv("FMM_P2P_BLOCKS_PER_SM");
-        const int x = e ? atoi(e) : 0;
+        const int x = env_int("FMM_P2P_BLOCKS_PER_SM", 0);
         return x > 0 ? x : kP2PBlocksPerSM;
     }();
     return v;
@@ -1122,15 +1134,21 @@ static void launch_p2p(Tree& t, const Bufs& B, cudaStream_t s) {
     const unsigned long long* cnt = item_count(t, 2);
     unsigned* next = reinterpret_cast<unsigned*>(reinterpret_cast<unsigned long long*>(t.d_status) + 7);
     cudaMemsetAsync(next, 0, sizeof(unsigned), s);
-    const int bps = p2p_blocks_per_sm();
-    const int dgrid = std::min(nblk(t.p2p_cap, kP2PDWarps), t.num_sms * bps);
+    int per_warp = p2p_items_per_warp();
+    int dgrid;
+    if (per_warp > 0) {
+        dgrid = nblk(t.p2p_cap, kP2PDWarps * per_warp);
+    } else {
+        per_warp = 1 << 30;
+        dgrid = std::min(nblk(t.p2p_cap, kP2PDWarps), t.num_sms * p2p_blocks_per_sm());
+    }
     const int rgrid = nblk(32 * t.nleaf, 256);
     const P2PLayout lay = p2p_layout(t.max_leaf);
     const int pad = (int)(t.nleaf * t.leaf_cap);
 #define FMM_P2P(V, C, TPL, LT)                                                                                   \
     k_p2p_slots<V, C, TPL, LT><<<dgrid, kP2PDWarps * 32, 0, s>>>(                                                 \
         t.d_p2p_items, cnt, next, t.d_bstart, t.d_bcount, t.d_pslot, t.d_soff, t.d_srng,                          \
-        static_cast<const V*>(t.d_posp), static_cast<const C*>(t.d_gamp), nv, pt, t.max_leaf, pad);
+        static_cast<const V*>(t.d_posp), static_cast<const C*>(t.d_gamp), nv, pt, t.max_leaf, pad, per_warp);
 #define FMM_P2P_LAYOUTS(V, C)                                  \
     switch (lay.tpl * 100 + lay.lt) {                          \
         case 202: FMM_P2P(V, C, 2, 2) break;                   \
@@ -1148,7 +1166,7 @@ static void launch_p2p(Tree& t, const Bufs& B, cudaStream_t s) {
     k_p2p_pairs<TPL, LT><<<dgrid, kP2PDWarps * 32, 0, s>>>(                                                       \
         t.d_p2p_items, cnt, next, t.d_bstart, t.d_bcount, t.d_pslot, t.d_soff, t.d_srng,                          \
         static_cast<const ulonglong2*>(t.d_posp), static_cast<const ulonglong2*>(t.d_gamp), nv, pt, t.max_leaf,   \
-        pad);
+        pad, per_warp);
         switch (pl.tpl * 100 + pl.lt) {
             case 204: FMM_P2P_PAIRS(2, 4) break;
             case 404: FMM_P2P_PAIRS(4, 4) break;
@@ -1281,20 +1299,23 @@ fmm_status run_eval(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s)
     if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[1], s));
     if (!serial) {
         FMM_CUDA(cudaEventRecord(t.ev_fork, s));
+        FMM_CUDA(cudaStreamWaitEvent(t.s_far, t.ev_fork, 0));
         FMM_CUDA(cudaStreamWaitEvent(t.s_aux, t.ev_fork, 0));
+        dispatch_far(t, B, t.s_far);
+        if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[4], t.s_far));
+        FMM_CUDA(cudaEventRecord(t.ev_join_far, t.s_far));
         if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[5], t.s_aux));
         launch_p2p(t, B, t.s_aux);
         if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[6], t.s_aux));
         FMM_CUDA(cudaEventRecord(t.ev_join, t.s_aux));
-    }
-    dispatch_far(t, B, s);
-    if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[4], s));
-    if (serial) {
+        FMM_CUDA(cudaStreamWaitEvent(s, t.ev_join_far, 0));
+        FMM_CUDA(cudaStreamWaitEvent(s, t.ev_join, 0));
+    } else {
+        dispatch_far(t, B, s);
+        if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[4], s));
         if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[5], s));
         launch_p2p(t, B, s);
         if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[6], s));
-    } else {
-        FMM_CUDA(cudaStreamWaitEvent(s, t.ev_join, 0));
     }
     dispatch_l2p(t, B, d_phi, s);
     if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[7], s));

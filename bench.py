@@ -36,9 +36,14 @@ N_POINTS = 1_000_000
 P_TERMS = 17
 THETA = 0.5
 WORKLOAD = "cluster_mix_1e6_p17_theta0.5"
-# dram__bytes_read.sum + dram__bytes_write.sum of one P2P launch at N_levels = 9
-# (ncu, profiles/p2p_cluster1e6_L9.md); None until captured for the current kernel
-P2P_TRAFFIC_BYTES = None
+# dram__bytes_read.sum + dram__bytes_write.sum of one P2P launch (k_p2p_pairs) at
+# N_levels = 9 on this workload, from one ncu capture (profiles/p2p_pairs_cluster1e6_L9.md)
+P2P_TRAFFIC_BYTES = 83_457_280 + 6_434_048
+# algorithmic FP32 flops of one point-pair interaction (FMA = 2): compensated
+# difference 6, |d|^2 4, the two scalings 2, the complex accumulation 8
+P2P_FLOPS = 20.0
+SM_COUNT = 148
+FP32_FLOP_PER_CLK_SM = 256  # 128 FP32 lanes x FMA
 
 
 def _peaks():
@@ -299,14 +304,14 @@ def run_gpu(args):
         return
     peaks = _peaks()
     value = N_POINTS * world / (ms * 1e-3) / 1e6
-    # dominant kernel: P2P (FP32 ALU bound).  19 algorithmic flops per point
-    # pair (compensated difference 6, r^2 3, two products 6, accumulation 4,
-    # plus one reciprocal); the kernel issues 14 FP32-pipe instructions per pair,
-    # so the ALU peak for this mix is the measured FP32 lane rate / 14 pairs/s.
-    fp32_lane_ops = 34.2e12
-    peak = fp32_lane_ops / 14.0 * 19.0 / 1e12
+    clocks = clk.summary()
+    # dominant kernel: P2P, bound by the FP32 pipe.  Peak = SMs x 256 flop/clk x
+    # SM clock (the median sampled under load; also given at the 2032 MHz max).
+    sm_mhz = clocks.get("sm_mhz") or 2032.0
+    peak = SM_COUNT * FP32_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12
+    peak_max = SM_COUNT * FP32_FLOP_PER_CLK_SM * 2032e6 / 1e12
     p2p_ms = phases_alone["p2p"]
-    achieved = info["p2p_pairs"] * 19.0 / (p2p_ms * 1e-3) / 1e12
+    achieved = info["p2p_pairs"] * P2P_FLOPS / (p2p_ms * 1e-3) / 1e12
     line = {
         "metric": METRIC,
         "value": round(value, 2),
@@ -331,17 +336,19 @@ def run_gpu(args):
                       "rel_err_sampled": err64},
         "rel_err_sampled": err32,
         "bwd_over_fwd": bwd_ratio,
-        "roofline": {"kernel": "k_p2p_direct (P2P, FP32)", "bound": "alu", "achieved": round(achieved, 3),
+        "roofline": {"kernel": "k_p2p_pairs (P2P, FP32 f32x2)", "bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                      "traffic": P2P_TRAFFIC_BYTES, "kernel_ms": round(p2p_ms, 4),
-                     "peak_note": "ALU peak derived from the measured FP32 FFMA lane rate (34.2e12/s, 114/clk/SM "
-                                  "at 2032 MHz): 14 FP32-pipe instructions = 19 flops per point pair"},
+                     "frac_at_max_clock": round(achieved / peak_max, 4),
+                     "peak_note": f"FP32 peak from unit counts: {SM_COUNT} SMs x 256 flop/clk x {sm_mhz:.0f} MHz "
+                                  f"(median SM clock sampled during the timed steps); {P2P_FLOPS:.0f} algorithmic "
+                                  "flops per point pair (FMA = 2), launch time from CUDA events with the pass alone"},
         "e2e": {"value": round(N_POINTS / (e2e_ms * 1e-3) / 1e6, 2), "unit": UNIT,
                 "h2d_bytes_per_step": int(xy.nbytes + gam.nbytes), "d2h_bytes_per_step": int(N_POINTS * 8)},
         "gpu_launches": int(args.steps * (info["launches_build"] + info["launches_eval"])),
         "interactions": {"p2p_pairs": info["p2p_pairs"], "m2l_pairs": info["n_weak"]},
     }
-    line["clocks"] = clk.summary()
+    line["clocks"] = clocks
     if peaks:
         line["peaks_used"] = {"hbm_gbs": peaks.get("hbm_gbs")}
     if not args.no_cpu_baseline:

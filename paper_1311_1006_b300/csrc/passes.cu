@@ -551,7 +551,7 @@ __global__ void __launch_bounds__(128) k_l2l_warp(const int32_t* __restrict__ bo
 }
 
 // Levels with at most this many shifts use the warp-per-shift kernels.
-constexpr int kWarpShiftMax = 4096;
+constexpr int kWarpShiftMax = 1024;
 
 // ------------------------------------------------------------- L2P + sum
 

@@ -59,9 +59,12 @@ typedef enum { FMM_PATH_FP32 = 0, FMM_PATH_FP64 = 1 } fmm_path;
 
 /* fmm_params.flags */
 enum {
-    FMM_FLAG_NO_GRAPH = 1, /* launch kernels one by one instead of replaying a captured CUDA graph */
+    FMM_FLAG_NO_GRAPH = 1, /* launch the kernels one by one (the default; overrides FMM_FLAG_GRAPH) */
     FMM_FLAG_SERIAL = 2,   /* run P2P on the caller's stream after the far field (no overlap) */
-    FMM_FLAG_TIMING = 4    /* record per-phase CUDA events; read them with fmm_phase_times */
+    FMM_FLAG_TIMING = 4,   /* record per-phase CUDA events; read them with fmm_phase_times */
+    FMM_FLAG_GRAPH = 8     /* capture the evaluation once per (strengths, output, stream) and replay the
+                              CUDA graph; fewer host launches, but on B300 the replay overlaps P2P with
+                              the far field less well than direct launches on prioritised streams */
 };
 
 /* Maximum expansion order accepted (p terms, coefficients k = 0..p-1). */

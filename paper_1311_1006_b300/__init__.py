@@ -18,11 +18,11 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (FMM_FLAG_NO_GRAPH, FMM_FLAG_SERIAL, FMM_FLAG_TIMING, FMM_PATH_FP32, FMM_PATH_FP64, FMMError,
+from ._lib import (FMM_FLAG_GRAPH, FMM_FLAG_NO_GRAPH, FMM_FLAG_SERIAL, FMM_FLAG_TIMING, FMM_PATH_FP32, FMM_PATH_FP64, FMMError,
                    FMMParams)
 
 __all__ = ["Tree", "FMMFunction", "fmm", "default_nlevels", "Autotuner", "FMMError", "FMM_PATH_FP32",
-           "FMM_PATH_FP64", "FMM_FLAG_NO_GRAPH", "FMM_FLAG_SERIAL", "FMM_FLAG_TIMING"]
+           "FMM_PATH_FP64", "FMM_FLAG_GRAPH", "FMM_FLAG_NO_GRAPH", "FMM_FLAG_SERIAL", "FMM_FLAG_TIMING"]
 
 
 def _torch():

@@ -22,6 +22,7 @@ FMM_PATH_FP64 = 1
 FMM_FLAG_NO_GRAPH = 1
 FMM_FLAG_SERIAL = 2
 FMM_FLAG_TIMING = 4
+FMM_FLAG_GRAPH = 8
 
 FMM_P_MAX = 32
 

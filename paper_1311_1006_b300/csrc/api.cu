@@ -321,6 +321,38 @@ void fmm_tree_destroy(fmm_tree* h) {
     delete h;
 }
 
+// Stream priorities of the evaluation (far field high, P2P low) set on the
+// captured kernel nodes, which otherwise run at the priority of the stream the
+// graph is launched into.  Best effort: a node that refuses keeps the default.
+static void set_node_priorities(const Tree& t, cudaGraph_t g) {
+    int lo = 0, hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return;
+    }
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess || ty != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp{};
+        if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
+        const bool p2p = std::find(t.p2p_funcs.begin(), t.p2p_funcs.end(), kp.func) != t.p2p_funcs.end();
+        cudaLaunchAttributeValue v{};
+        v.priority = p2p ? lo : hi;
+        cudaGraphKernelNodeSetAttribute(nd, cudaLaunchAttributePriority, &v);
+    }
+    cudaGetLastError();
+}
+
 static fmm_status eval_common(fmm_tree* h, const double* d_gamma, void* d_phi, void* stream) {
     if (!h || !d_gamma || !d_phi) return invalid("NULL argument");
     Tree& t = h->t;
@@ -328,8 +360,10 @@ static fmm_status eval_common(fmm_tree* h, const double* d_gamma, void* d_phi, v
     if ((st = check_pending())) return st;
     if (t.eval_nbox == 0) invalidate_graph(t);
     if ((st = alloc_eval(t, 1))) return st;
+    if (refresh_grids(t)) invalidate_graph(t);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const bool use_graph = !(t.flags & (FMM_FLAG_NO_GRAPH | FMM_FLAG_TIMING)) && s != nullptr;
+    const bool use_graph =
+        (t.flags & FMM_FLAG_GRAPH) && !(t.flags & (FMM_FLAG_NO_GRAPH | FMM_FLAG_TIMING)) && s != nullptr;
     if (!use_graph) return run_eval(t, d_gamma, d_phi, s);
     const void* key[4] = {d_gamma, d_phi, (const void*)s, (const void*)(intptr_t)(t.path * 64 + t.P)};
     if (!t.graph || memcmp(key, t.graph_key, sizeof(key)) != 0) {
@@ -343,6 +377,7 @@ static fmm_status eval_common(fmm_tree* h, const double* d_gamma, void* d_phi, v
             return st;
         }
         FMM_CUDA(e);
+        set_node_priorities(t, g);
         e = cudaGraphInstantiate(&t.graph, g, 0);
         cudaGraphDestroy(g);
         FMM_CUDA(e);
@@ -369,6 +404,7 @@ fmm_status fmm_eval_backward(fmm_tree* h, const double* d_gamma, const double* d
     fmm_status st;
     if ((st = check_pending())) return st;
     if ((st = alloc_eval(t, 2))) return st;
+    if (refresh_grids(t)) invalidate_graph(t);
     return run_backward(t, d_gamma, d_gphi, d_ggamma, d_gxy, static_cast<cudaStream_t>(stream));
 }
 

@@ -313,7 +313,7 @@ fmm_status run_backward(Tree& t, const double* d_gamma, const double* d_gphi, do
                                                            static_cast<double2*>(B1.gam));
     FMM_CUDA(cudaEventRecord(t.ev_fork, s));
     FMM_CUDA(cudaStreamWaitEvent(t.s_aux, t.ev_fork, 0));
-    const int grid = nblk(t.p2p_cap, kBWarps);
+    const int grid = nblk(p2p_grid_items(t), kBWarps);
     const long long stride = (long long)t.part_p2p_cap * t.max_leaf;
     const unsigned long long* cnt = reinterpret_cast<const unsigned long long*>(t.d_status) + 3;
     const bool wide = (double)t.n / std::max<int64_t>(t.nleaf, 1) >= 8.0;

@@ -163,6 +163,10 @@ struct Tree {
     int2* d_leaf_items = nullptr;  // per box: first P2P item, item count (leaves)
     int2* d_box_m2l = nullptr;     // per box: first M2L item, item count
     long long p2p_cap = 0, m2l_cap = 0;
+    // work items the P2P / M2L launch grids cover: the last build's counts plus
+    // slack, re-derived (and the evaluation graph re-captured) when a build's
+    // counts leave [grid/2.5, grid]
+    long long grid_p2p_items = 0, grid_m2l_items = 0;
     int max_leaf = 1;
     int num_sms = 148;              // largest leaf (points): row stride of the P2P partial sums
     // device words: [0] status bits, then 64-bit counters:
@@ -196,6 +200,7 @@ struct Tree {
 
     // captured evaluation graph (keyed by the user pointers it bakes in)
     cudaGraphExec_t graph = nullptr;
+    std::vector<const void*> p2p_funcs;  // P2P kernels launched by the last evaluation (low graph priority)
     const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};
 
     // autotuner state (AT3b, Algorithm 4)
@@ -256,6 +261,9 @@ struct Bufs {
     void* m2l_part;
 };
 Bufs bufs(Tree& t, int set);
+bool refresh_grids(Tree& t);  // true when the P2P / M2L grids changed (the graph must be re-captured)
+long long p2p_grid_items(const Tree& t);
+long long m2l_grid_items(const Tree& t);
 void dispatch_far(Tree& t, const Bufs& B, cudaStream_t s);  // P2M, M2M, M2L, L2L of one strength set
 
 // FP32-path M2L on the tensor cores (m2l_tc.cu); FMM_M2L_TC=0 selects the CUDA-core kernel.

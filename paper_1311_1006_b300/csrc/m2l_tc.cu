@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(kTcThreads, P <= 18 ? 3 : 2)
 
 template <int P>
 void launch_tc(const Tree& t, const float2* M32, float2* Lm2l, float2* part, cudaStream_t s) {
-    const int grid = static_cast<int>(std::max<long long>((t.m2l_cap + kTcThreads - 1) / kTcThreads, 1));
+    const int grid = static_cast<int>(std::max<long long>((m2l_grid_items(t) + kTcThreads - 1) / kTcThreads, 1));
     k_m2l_tc<P><<<grid, kTcThreads, TcShape<P>::SMEM, s>>>(
         t.d_m2l_items, reinterpret_cast<const unsigned long long*>(t.d_status) + 4, t.d_woff, t.d_widx, t.d_chl,
         t.d_rho32, M32, Lm2l, part, t.PS, t.d_status);

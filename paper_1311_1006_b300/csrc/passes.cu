@@ -1015,6 +1015,26 @@ Bufs bufs(Tree& t, int set) {
     return b;
 }
 
+// Launch grids cover the last build's work-item counts plus 25 % slack (the
+// kernels read the exact count on the device), not the allocated capacities,
+// which can stay far larger after a build at another N_levels.
+static long long grid_target(unsigned long long c) { return (long long)(c + c / 4 + 64); }
+bool refresh_grids(Tree& t) {
+    bool changed = false;
+    const long long cp = (long long)t.h_counts[2], cm = (long long)t.h_counts[3];
+    if (t.grid_p2p_items < cp || t.grid_p2p_items > 5 * (cp + 64) / 2) {
+        t.grid_p2p_items = std::min(grid_target(cp), std::max(t.p2p_cap, 1LL));
+        changed = true;
+    }
+    if (t.grid_m2l_items < cm || t.grid_m2l_items > 5 * (cm + 64) / 2) {
+        t.grid_m2l_items = std::min(grid_target(cm), std::max(t.m2l_cap, 1LL));
+        changed = true;
+    }
+    return changed;
+}
+long long p2p_grid_items(const Tree& t) { return t.grid_p2p_items > 0 ? t.grid_p2p_items : t.p2p_cap; }
+long long m2l_grid_items(const Tree& t) { return t.grid_m2l_items > 0 ? t.grid_m2l_items : t.m2l_cap; }
+
 static const unsigned long long* item_count(const Tree& t, int which) {
     return reinterpret_cast<const unsigned long long*>(t.d_status) + 1 + which;  // 2 = P2P, 3 = M2L
 }
@@ -1038,7 +1058,7 @@ static void launch_far_fp32(Tree& t, const Bufs& B, cudaStream_t s) {
     if (m2l_tc_enabled())
         launch_m2l_tc(t, B.M32, static_cast<float2*>(B.Lm2l), static_cast<float2*>(B.m2l_part), s);
     else
-        k_m2l32<P><<<nblk(t.m2l_cap, 128), 128, 0, s>>>(t.d_m2l_items, item_count(t, 3), t.d_woff, t.d_widx,
+        k_m2l32<P><<<nblk(m2l_grid_items(t), 128), 128, 0, s>>>(t.d_m2l_items, item_count(t, 3), t.d_woff, t.d_widx,
                                                         t.d_chl, t.d_rho32, B.M32, static_cast<float2*>(B.Lm2l),
                                                         static_cast<float2*>(B.m2l_part), t.PS);
     k_reduce_m2l<float2><<<nblk(32 * t.nbox, 256), 256, 0, s>>>((int)t.nbox, t.d_box_m2l,
@@ -1075,7 +1095,7 @@ static void launch_far_fp64(Tree& t, const Bufs& B, cudaStream_t s) {
                                                                      t.PS);
     }
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[2], s);
-    k_m2l64<P><<<nblk(t.m2l_cap, 128), 128, 0, s>>>(t.d_m2l_items, item_count(t, 3), t.d_woff, t.d_widx,
+    k_m2l64<P><<<nblk(m2l_grid_items(t), 128), 128, 0, s>>>(t.d_m2l_items, item_count(t, 3), t.d_woff, t.d_widx,
                                                     t.d_center, t.d_rho, B.M64, static_cast<double2*>(B.Lm2l),
                                                     static_cast<double2*>(B.m2l_part), t.PS);
     k_reduce_m2l<double2><<<nblk(32 * t.nbox, 256), 256, 0, s>>>((int)t.nbox, t.d_box_m2l,
@@ -1137,15 +1157,16 @@ static void launch_p2p(Tree& t, const Bufs& B, cudaStream_t s) {
     int per_warp = p2p_items_per_warp();
     int dgrid;
     if (per_warp > 0) {
-        dgrid = nblk(t.p2p_cap, kP2PDWarps * per_warp);
+        dgrid = nblk(p2p_grid_items(t), kP2PDWarps * per_warp);
     } else {
         per_warp = 1 << 30;
-        dgrid = std::min(nblk(t.p2p_cap, kP2PDWarps), t.num_sms * p2p_blocks_per_sm());
+        dgrid = std::min(nblk(p2p_grid_items(t), kP2PDWarps), t.num_sms * p2p_blocks_per_sm());
     }
     const int rgrid = nblk(32 * t.nleaf, 256);
     const P2PLayout lay = p2p_layout(t.max_leaf);
     const int pad = (int)(t.nleaf * t.leaf_cap);
 #define FMM_P2P(V, C, TPL, LT)                                                                                   \
+    t.p2p_funcs.push_back(reinterpret_cast<const void*>(k_p2p_slots<V, C, TPL, LT>));                           \
     k_p2p_slots<V, C, TPL, LT><<<dgrid, kP2PDWarps * 32, 0, s>>>(                                                 \
         t.d_p2p_items, cnt, next, t.d_bstart, t.d_bcount, t.d_pslot, t.d_soff, t.d_srng,                          \
         static_cast<const V*>(t.d_posp), static_cast<const C*>(t.d_gamp), nv, pt, t.max_leaf, pad, per_warp);
@@ -1163,6 +1184,7 @@ static void launch_p2p(Tree& t, const Bufs& B, cudaStream_t s) {
         float2* pt = static_cast<float2*>(B.p2p_part);
         const P2PLayout pl = p2p_pair_layout(t.max_leaf);
 #define FMM_P2P_PAIRS(TPL, LT)                                                                                   \
+    t.p2p_funcs.push_back(reinterpret_cast<const void*>(k_p2p_pairs<TPL, LT>));                                 \
     k_p2p_pairs<TPL, LT><<<dgrid, kP2PDWarps * 32, 0, s>>>(                                                       \
         t.d_p2p_items, cnt, next, t.d_bstart, t.d_bcount, t.d_pslot, t.d_soff, t.d_srng,                          \
         static_cast<const ulonglong2*>(t.d_posp), static_cast<const ulonglong2*>(t.d_gamp), nv, pt, t.max_leaf,   \
@@ -1175,12 +1197,14 @@ static void launch_p2p(Tree& t, const Bufs& B, cudaStream_t s) {
             default: FMM_P2P_PAIRS(8, 16) break;
         }
 #undef FMM_P2P_PAIRS
+        t.p2p_funcs.push_back(reinterpret_cast<const void*>(k_reduce_p2p<float2>));
         k_reduce_p2p<float2><<<rgrid, 256, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, t.d_leaf_items, t.d_bstart,
                                                    t.d_bcount, pt, t.max_leaf, nv);
     } else {
         double2* nv = static_cast<double2*>(B.near);
         double2* pt = static_cast<double2*>(B.p2p_part);
         FMM_P2P_LAYOUTS(double2, double2)
+        t.p2p_funcs.push_back(reinterpret_cast<const void*>(k_reduce_p2p<double2>));
         k_reduce_p2p<double2><<<rgrid, 256, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, t.d_leaf_items, t.d_bstart,
                                                     t.d_bcount, pt, t.max_leaf, nv);
     }
@@ -1285,6 +1309,7 @@ fmm_status alloc_eval(Tree& t, int sets) {
 // caller's stream, join, and finish with L2P + near + unpermute.
 fmm_status run_eval(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s) {
     const int n = (int)t.n;
+    t.p2p_funcs.clear();
     const bool timing = t.flags & FMM_FLAG_TIMING;
     const bool serial = t.flags & FMM_FLAG_SERIAL;
     if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[0], s));

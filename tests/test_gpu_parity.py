@@ -149,13 +149,13 @@ def test_eval_single_point_is_zero():
 
 
 def test_eval_is_deterministic_and_graph_replay_matches_eager(orc):
-    from paper_1311_1006_b300 import FMM_FLAG_NO_GRAPH, Tree
+    from paper_1311_1006_b300 import FMM_FLAG_GRAPH, FMM_FLAG_NO_GRAPH, Tree
 
     g = np.random.default_rng(5)
     xy, gam = W.cluster_mix(20000, g), W.complex_strengths(20000, g)
     X, G = _dev(xy), _dev(gam)
     for path in ("fp32", "fp64"):
-        t1 = Tree.build(X, nlevels=6, path=path)
+        t1 = Tree.build(X, nlevels=6, path=path, flags=FMM_FLAG_GRAPH)
         t2 = Tree.build(X, nlevels=6, path=path, flags=FMM_FLAG_NO_GRAPH)
         a = t1.eval(G).clone()
         b = t1.eval(G).clone()

@@ -120,6 +120,10 @@ static fmm_status build_all(Tree& t, const double* d_xy, cudaStream_t s) {
             set_error("internal index check failed during the tree build");
             return FMM_ERR_CUDA;
         }
+        if (bits & ST_TIMEOUT) {
+            set_error("a bounded wait in the list build gave up");
+            return FMM_ERR_TIMEOUT;
+        }
         const bool ovl = bits & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW);
         if (!ovl && !(bits & ST_ITEM_OVERFLOW)) {
             t.h_counts[0] = lb[t.Lmax];
@@ -170,8 +174,8 @@ static void release(Tree* t) {
                     t->d_inst_boxoff, t->d_leaf_start, t->d_inst_levels, t->d_loc, t->d_X2, t->d_Y2, t->d_sideX, t->d_sideY, t->d_tile_cnt,
                     t->d_tile_pre, t->d_seg_lc, t->d_sort_hist, t->d_sort_tot, t->d_sort_off, t->d_perm,
                     t->d_leaf_of, t->d_pts, t->d_pos4, t->d_center, t->d_radius, t->d_rho, t->d_chl, t->d_rho32,
-                    t->d_rad32, t->d_soff, t->d_ns, t->d_sidx, t->d_srng, t->d_sowner, t->d_cflags, t->d_ltile_s,
-                    t->d_ltile_w, t->d_lpre_s, t->d_lpre_w, t->d_lvl_base, t->d_woff, t->d_nw, t->d_widx, t->d_p2p_items,
+                    t->d_rad32, t->d_soff, t->d_ns, t->d_sidx, t->d_srng, t->d_sowner, t->d_ltstat,
+                    t->d_lvl_base, t->d_woff, t->d_nw, t->d_widx, t->d_p2p_items,
                     t->d_m2l_items, t->d_leaf_items, t->d_box_m2l, t->d_status, t->d_gam, t->d_near, t->d_M64,
                     t->d_pslot, t->d_posp, t->d_slot_of, t->d_gamp,
                     t->d_M32, t->d_Lm2l, t->d_L64, t->d_L32, t->d_p2p_part, t->d_m2l_part};

@@ -151,8 +151,7 @@ struct Tree {
     int32_t *d_soff = nullptr, *d_ns = nullptr, *d_sidx = nullptr;
     int2* d_srng = nullptr;        // leaves: (first slot, count) of each strong entry, parallel to sidx
     int32_t* d_sowner = nullptr;   // box of each strong entry, parallel to sidx
-    uint8_t* d_cflags = nullptr;   // candidate flags of the level being built
-    int32_t *d_ltile_s = nullptr, *d_ltile_w = nullptr, *d_lpre_s = nullptr, *d_lpre_w = nullptr;
+    unsigned long long* d_ltstat = nullptr;  // list build: tile status words (strong, weak) + tile ticket
     unsigned long long* d_lvl_base = nullptr;  // [0,16) strong / [16,32) weak level offsets, [32,36) sizes needed
     long long cand_cap = 0;
     int32_t *d_woff = nullptr, *d_nw = nullptr, *d_widx = nullptr;

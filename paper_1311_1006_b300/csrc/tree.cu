@@ -875,140 +875,131 @@ __device__ __forceinline__ CandGroup decode_group(long long q, long long base_pr
 
 constexpr int kLThreads = 256, kLItems = 8, kLTile = kLThreads * kLItems;
 
-// Pass 1: classify every candidate (flag 0 none, 1 strong, 2 weak) and count
-// strong / weak per tile.
-__global__ void __launch_bounds__(kLThreads) k_lists_classify(
-    int l, const unsigned long long* __restrict__ lvl_base, const int32_t* __restrict__ sowner,
-    const int32_t* __restrict__ soff, const int32_t* __restrict__ ns, const int32_t* __restrict__ sidx,
-    const int32_t* __restrict__ child0, const float4* __restrict__ chl, const float* __restrict__ rad32,
-    const double2* __restrict__ center, const double* __restrict__ radius, double theta, uint8_t* flags,
-    long long flags_cap, int32_t* tile_s, int32_t* tile_w, long long tiles_cap, unsigned* status) {
-    __shared__ int ws[32], ww[32];
-    if (*((volatile unsigned*)status) & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW)) return;
-    const long long base_prev = (long long)lvl_base[l - 1];
-    const long long ncand = 16 * ((long long)lvl_base[l] - base_prev);
-    const long long ntiles = (ncand + kLTile - 1) / kLTile;
-    if (ncand > flags_cap || ntiles > tiles_cap) return;  // the host sized these from the last build; checked in pass 2
-    const float th32 = (float)theta;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const long long g0 = t * kLTile + (long long)threadIdx.x * kLItems;
-        int cs = 0, cw = 0;
-        uint32_t packed[2] = {0, 0};
-#pragma unroll
-        for (int gq = 0; gq < kLItems / 4; ++gq) {
-            const long long gg = g0 + 4 * gq;
-            if (gg >= ncand) break;
-            const CandGroup c = decode_group(gg >> 2, base_prev, sowner, soff, ns, sidx, child0);
-            if (!c.valid) continue;
-#pragma unroll
-            for (int cp = 0; cp < 4; ++cp) {
-                const int h = c.h0 + cp;
-                const bool sep = (h != c.b) && well_separated_fast(c.b, h, chl, rad32, center, radius, th32, theta);
-                const int f = sep ? 2 : 1;
-                cs += f == 1;
-                cw += f == 2;
-                const int k = 4 * gq + cp;
-                packed[k >> 2] |= (uint32_t)f << (8 * (k & 3));
-            }
-        }
-        if (g0 < ncand) {
-            uint2* fp = reinterpret_cast<uint2*>(flags + g0);  // g0 is a multiple of 8
-            *fp = make_uint2(packed[0], packed[1]);
-        }
-        int tot_s, tot_w;
-        (void)block_excl_scan(cs, ws, tot_s);
-        (void)block_excl_scan(cw, ww, tot_w);
-        if (threadIdx.x == 0) {
-            tile_s[t] = tot_s;
-            tile_w[t] = tot_w;
-        }
-    }
+// One pass per level: every candidate is classified (none / strong / weak),
+// the tile's strong and weak counts are scanned across the block, the tile's
+// offsets come from a decoupled look-back over the preceding tiles, and the
+// entries are written in candidate order.  Tiles are taken in ticket order
+// (atomic counter), so a tile only waits on tiles that running CTAs already
+// hold; every wait is bounded and a timeout is reported as ST_TIMEOUT.
+// Tile status words: bits 62-63 = 0 (not yet), 1 (tile aggregate), 2 (inclusive
+// prefix); bits 0-61 = the count.  [0, tiles_cap) strong, [tiles_cap, 2
+// tiles_cap) weak, then the ticket counter; zeroed before every level.
+constexpr unsigned long long kLAgg = 1ull << 62, kLIncl = 2ull << 62, kLVal = (1ull << 62) - 1;
+constexpr int kLookbackSpins = 1 << 21;
+
+__device__ __forceinline__ void st_volatile(unsigned long long* p, unsigned long long v) {
+    *reinterpret_cast<volatile unsigned long long*>(p) = v;
+}
+__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* p) {
+    return *reinterpret_cast<const volatile unsigned long long*>(p);
 }
 
-// Pass 2 (one block): tile offsets, level totals, capacity checks.
-__global__ void __launch_bounds__(1024) k_lists_scan(int l, unsigned long long* lvl_base,
-                                                     const int32_t* __restrict__ tile_s,
-                                                     const int32_t* __restrict__ tile_w, int32_t* pre_s,
-                                                     int32_t* pre_w, long long flags_cap, long long tiles_cap,
-                                                     long long scap, long long wcap, unsigned long long* need,
-                                                     unsigned* status) {
-    __shared__ int wsum[32];
-    if (*((volatile unsigned*)status) & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW)) return;
-    const long long base_prev = (long long)lvl_base[l - 1];
-    const long long ncand = 16 * ((long long)lvl_base[l] - base_prev);
-    const long long ntiles = (ncand + kLTile - 1) / kLTile;
-    if (ncand > flags_cap || ntiles > tiles_cap) {
-        if (threadIdx.x == 0) {
-            atomicMax(need + 0, (unsigned long long)ncand);
-            atomicOr(status, ST_STRONG_OVERFLOW);
-        }
-        return;
-    }
-    long long cs = 0, cw = 0;
-    for (long long c0 = 0; c0 < ntiles; c0 += 1024) {
-        const long long i = c0 + threadIdx.x;
-        const int vs = i < ntiles ? tile_s[i] : 0;
-        const int vw = i < ntiles ? tile_w[i] : 0;
-        int ts, tw;
-        const int es = block_excl_scan(vs, wsum, ts);
-        const int ew = block_excl_scan(vw, wsum, tw);
-        if (i < ntiles) {
-            pre_s[i] = (int)(cs + es);
-            pre_w[i] = (int)(cw + ew);
-        }
-        cs += ts;
-        cw += tw;
-    }
-    if (threadIdx.x == 0) {
-        const long long bs = (long long)lvl_base[l], bw = (long long)lvl_base[kMaxLevels + l];
-        lvl_base[l + 1] = (unsigned long long)(bs + cs);
-        lvl_base[kMaxLevels + l + 1] = (unsigned long long)(bw + cw);
-        if (bs + cs > scap) {
-            atomicMax(need + 1, (unsigned long long)(bs + cs));
-            atomicOr(status, ST_STRONG_OVERFLOW);
-        }
-        if (bw + cw > wcap) {
-            atomicMax(need + 2, (unsigned long long)(bw + cw));
-            atomicOr(status, ST_WEAK_OVERFLOW);
-        }
-    }
-}
-
-// Pass 3: scatter in candidate order; the first candidate of a box writes its
-// list offsets, the last one its list ends (turned into lengths by pass 4).
-__global__ void __launch_bounds__(kLThreads) k_lists_scatter(
-    int l, const unsigned long long* __restrict__ lvl_base, const int32_t* __restrict__ sowner,
-    int32_t* __restrict__ soff, int32_t* __restrict__ ns, int32_t* __restrict__ sidx, int32_t* __restrict__ woff,
-    int32_t* __restrict__ nw, int32_t* __restrict__ widx, int32_t* __restrict__ sowner_out,
-    const int32_t* __restrict__ child0, const int32_t* __restrict__ pslot, const int32_t* __restrict__ bcount,
-    int2* __restrict__ srng, const uint8_t* __restrict__ flags, const int32_t* __restrict__ pre_s,
-    const int32_t* __restrict__ pre_w, unsigned* status) {
+__global__ void __launch_bounds__(kLThreads) k_lists_level(
+    int l, unsigned long long* lvl_base, int32_t* __restrict__ sowner, int32_t* __restrict__ soff,
+    int32_t* __restrict__ ns, int32_t* __restrict__ sidx, int32_t* __restrict__ woff, int32_t* __restrict__ nw,
+    int32_t* __restrict__ widx, const int32_t* __restrict__ child0, const int32_t* __restrict__ pslot,
+    const int32_t* __restrict__ bcount, int2* __restrict__ srng, const float4* __restrict__ chl,
+    const float* __restrict__ rad32, const double2* __restrict__ center, const double* __restrict__ radius,
+    double theta, unsigned long long* tstat, long long tiles_cap, long long scap, long long wcap,
+    unsigned long long* need, unsigned* status) {
     __shared__ int ws[32], ww[32];
+    __shared__ long long sh_excl[2];
+    __shared__ long long sh_tile;
     if (*((volatile unsigned*)status) & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW)) return;
     const long long base_prev = (long long)lvl_base[l - 1];
     const long long bs = (long long)lvl_base[l], bw = (long long)lvl_base[kMaxLevels + l];
     const long long ncand = 16 * (bs - base_prev);
     const long long ntiles = (ncand + kLTile - 1) / kLTile;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const long long g0 = t * kLTile + (long long)threadIdx.x * kLItems;
-        uint2 fp = make_uint2(0, 0);
-        if (g0 < ncand) fp = *reinterpret_cast<const uint2*>(flags + g0);
-        int cs = 0, cw = 0;
-#pragma unroll
-        for (int k = 0; k < kLItems; ++k) {
-            const int f = (int)(((k < 4 ? fp.x : fp.y) >> (8 * (k & 3))) & 0xffu);
-            cs += f == 1;
-            cw += f == 2;
+    if (ntiles > tiles_cap) {  // tile status array too small: grow the candidate capacity
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            atomicMax(need + 0, (unsigned long long)ncand);
+            atomicOr(status, ST_STRONG_OVERFLOW);
         }
-        int tot_s, tot_w;
-        int ps = block_excl_scan(cs, ws, tot_s) + pre_s[t];
-        int pw = block_excl_scan(cw, ww, tot_w) + pre_w[t];
-        if (g0 >= ncand) continue;
+        return;
+    }
+    if (ntiles == 0) {  // no candidates: the level's lists are empty
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            lvl_base[l + 1] = (unsigned long long)bs;
+            lvl_base[kMaxLevels + l + 1] = (unsigned long long)bw;
+        }
+        return;
+    }
+    unsigned long long* ticket = tstat + 2 * tiles_cap;
+    const float th32 = (float)theta;
+    while (true) {
+        if (threadIdx.x == 0) sh_tile = (long long)atomicAdd(ticket, 1ull);
+        __syncthreads();
+        const long long t = sh_tile;
+        __syncthreads();
+        if (t >= ntiles) break;
+        const long long g0 = t * kLTile + (long long)threadIdx.x * kLItems;
+        CandGroup cg[kLItems / 4];
+        uint32_t fl = 0;  // 2 bits per candidate: 0 none, 1 strong, 2 weak
+        int cs = 0, cw = 0;
 #pragma unroll
         for (int gq = 0; gq < kLItems / 4; ++gq) {
             const long long gg = g0 + 4 * gq;
-            if (gg >= ncand) break;
-            const CandGroup c = decode_group(gg >> 2, base_prev, sowner, soff, ns, sidx, child0);
+            cg[gq].valid = false;
+            if (gg >= ncand) continue;
+            cg[gq] = decode_group(gg >> 2, base_prev, sowner, soff, ns, sidx, child0);
+            if (!cg[gq].valid) continue;
+#pragma unroll
+            for (int cp = 0; cp < 4; ++cp) {
+                const int h = cg[gq].h0 + cp;
+                const bool sep =
+                    (h != cg[gq].b) && well_separated_fast(cg[gq].b, h, chl, rad32, center, radius, th32, theta);
+                cs += !sep;
+                cw += sep;
+                fl |= (sep ? 2u : 1u) << (2 * (4 * gq + cp));
+            }
+        }
+        int tot_s, tot_w;
+        long long ps = block_excl_scan(cs, ws, tot_s);
+        long long pw = block_excl_scan(cw, ww, tot_w);
+        if (threadIdx.x == 0 || threadIdx.x == 32) {
+            const int which = threadIdx.x == 0 ? 0 : 1;
+            unsigned long long* st = tstat + which * tiles_cap;
+            const unsigned long long agg = (unsigned long long)(which ? tot_w : tot_s);
+            unsigned long long excl = 0;
+            if (t == 0) {
+                st_volatile(st, kLIncl | agg);
+            } else {
+                st_volatile(st + t, kLAgg | agg);
+                long long j = t - 1;
+                int spins = 0;
+                while (true) {
+                    const unsigned long long v = ld_volatile(st + j);
+                    const unsigned long long f = v & ~kLVal;
+                    if (f == 0) {
+                        if (++spins > kLookbackSpins) {
+                            atomicOr(status, ST_TIMEOUT);
+                            break;
+                        }
+                        continue;
+                    }
+                    excl += v & kLVal;
+                    if (f == kLIncl || j == 0) break;
+                    --j;
+                }
+                st_volatile(st + t, kLIncl | (excl + agg));
+            }
+            sh_excl[which] = (long long)excl;
+            if (t == ntiles - 1) {  // level totals and capacity checks
+                const long long base = which ? bw : bs;
+                const long long end = base + (long long)(excl + agg);
+                lvl_base[which ? kMaxLevels + l + 1 : l + 1] = (unsigned long long)end;
+                if (end > (which ? wcap : scap)) {
+                    atomicMax(need + 1 + which, (unsigned long long)end);
+                    atomicOr(status, which ? ST_WEAK_OVERFLOW : ST_STRONG_OVERFLOW);
+                }
+            }
+        }
+        __syncthreads();
+        ps += sh_excl[0];
+        pw += sh_excl[1];
+#pragma unroll
+        for (int gq = 0; gq < kLItems / 4; ++gq) {
+            const CandGroup& c = cg[gq];
             if (!c.valid) continue;
             if (c.first) {
                 soff[c.b] = (int32_t)(bs + ps);
@@ -1017,29 +1008,28 @@ __global__ void __launch_bounds__(kLThreads) k_lists_scatter(
             const bool leaf = child0[c.b] < 0;
 #pragma unroll
             for (int cp = 0; cp < 4; ++cp) {
-                const int k = 4 * gq + cp;
-                const int f = (int)(((k < 4 ? fp.x : fp.y) >> (8 * (k & 3))) & 0xffu);
                 const int h = c.h0 + cp;
-                if (f == 1) {
+                if (((fl >> (2 * (4 * gq + cp))) & 3u) == 1u) {
                     const long long qq = bs + ps;
-                    sidx[qq] = h;
-                    sowner_out[qq] = c.b;
-                    if (leaf) srng[qq] = make_int2(pslot[h], bcount[h]);
+                    if (qq < scap) {
+                        sidx[qq] = h;
+                        sowner[qq] = c.b;
+                        if (leaf) srng[qq] = make_int2(pslot[h], bcount[h]);
+                    }
                     ++ps;
                 } else {
-                    widx[bw + pw] = h;
+                    if (bw + pw < wcap) widx[bw + pw] = h;
                     ++pw;
                 }
             }
             if (c.last) {
-                ns[c.b] = (int32_t)(bs + ps);  // end; made a length in pass 4
+                ns[c.b] = (int32_t)(bs + ps);  // end; made a length by k_lists_len
                 nw[c.b] = (int32_t)(bw + pw);
             }
         }
     }
 }
 
-// Pass 4: list ends -> lengths for the boxes of level l.
 __global__ void k_lists_len(const int32_t* __restrict__ ids, int cnt, const int32_t* __restrict__ soff,
                             int32_t* ns, const int32_t* __restrict__ woff, int32_t* nw, unsigned* status) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1220,12 +1210,8 @@ fmm_status alloc_lists(Tree& t) {
     if ((st = dalloc(&t.d_sidx, (size_t)t.scap_tot))) return st;
     if ((st = dalloc(&t.d_sowner, (size_t)t.scap_tot))) return st;
     if ((st = dalloc(&t.d_srng, (size_t)t.scap_tot))) return st;
-    if ((st = dalloc(&t.d_cflags, (size_t)t.cand_cap + 16))) return st;
     const size_t tiles = (size_t)(t.cand_cap / kLTile + 2);
-    if ((st = dalloc(&t.d_ltile_s, tiles))) return st;
-    if ((st = dalloc(&t.d_ltile_w, tiles))) return st;
-    if ((st = dalloc(&t.d_lpre_s, tiles))) return st;
-    if ((st = dalloc(&t.d_lpre_w, tiles))) return st;
+    if ((st = dalloc(&t.d_ltstat, 2 * tiles + 1))) return st;
     if ((st = dalloc(&t.d_widx, (size_t)t.wcap_tot))) return st;
     if ((st = dalloc(&t.d_p2p_items, (size_t)t.p2p_cap))) return st;
     if ((st = dalloc(&t.d_m2l_items, (size_t)t.m2l_cap))) return st;
@@ -1307,16 +1293,11 @@ fmm_status run_lists(Tree& t, cudaStream_t s) {
     const long long tiles_cap = t.cand_cap / kLTile + 2;
     const int grid = t.num_sms * 8;
     for (int l = 1; l < t.Lmax; ++l) {
-        k_lists_classify<<<grid, kLThreads, 0, s>>>(l, t.d_lvl_base, t.d_sowner, t.d_soff, t.d_ns, t.d_sidx,
-                                                    t.d_child0, t.d_chl, t.d_rad32, t.d_center, t.d_radius, t.theta,
-                                                    t.d_cflags, t.cand_cap, t.d_ltile_s, t.d_ltile_w, tiles_cap,
-                                                    t.d_status);
-        k_lists_scan<<<1, 1024, 0, s>>>(l, t.d_lvl_base, t.d_ltile_s, t.d_ltile_w, t.d_lpre_s, t.d_lpre_w,
-                                        t.cand_cap, tiles_cap, t.scap_tot, t.wcap_tot, need, t.d_status);
-        k_lists_scatter<<<grid, kLThreads, 0, s>>>(l, t.d_lvl_base, t.d_sowner, t.d_soff, t.d_ns, t.d_sidx,
-                                                   t.d_woff, t.d_nw, t.d_widx, t.d_sowner, t.d_child0, t.d_pslot,
-                                                   t.d_bcount, t.d_srng, t.d_cflags, t.d_lpre_s, t.d_lpre_w,
-                                                   t.d_status);
+        FMM_CUDA(cudaMemsetAsync(t.d_ltstat, 0, (size_t)(2 * tiles_cap + 1) * sizeof(unsigned long long), s));
+        k_lists_level<<<grid, kLThreads, 0, s>>>(l, t.d_lvl_base, t.d_sowner, t.d_soff, t.d_ns, t.d_sidx, t.d_woff,
+                                                 t.d_nw, t.d_widx, t.d_child0, t.d_pslot, t.d_bcount, t.d_srng,
+                                                 t.d_chl, t.d_rad32, t.d_center, t.d_radius, t.theta, t.d_ltstat,
+                                                 tiles_cap, t.scap_tot, t.wcap_tot, need, t.d_status);
         const LevelList& Ll = t.level_boxes[l];
         k_lists_len<<<nblk(Ll.count, 256), 256, 0, s>>>(Ll.d_ids, Ll.count, t.d_soff, t.d_ns, t.d_woff, t.d_nw,
                                                         t.d_status);

@@ -763,36 +763,6 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, sizeof(C) == 8 ? 5 : 1)
 // tg+LT, ... and pair slice ss of S = 32/LT; a step covers 2S slots.  Each
 // packed accumulator holds two partial sums (even / odd source slots), added
 // at the end before the shuffle reduction over slices.
-typedef unsigned long long f2x;
-__device__ __forceinline__ f2x f2pk(float lo, float hi) {
-    f2x r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void f2upk(f2x v, float& lo, float& hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ f2x f2add(f2x a, f2x b) {
-    f2x d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2x f2sub(f2x a, f2x b) {
-    f2x d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2x f2mul(f2x a, f2x b) {
-    f2x d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2x f2fma(f2x a, f2x b, f2x c) {
-    f2x d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-
 // Two sources (packed) against one target: Gamma_j conj(d)/|d|^2 with
 // d = z_t - z_j from the hi/lo coordinates; the coincident-pair guard is
 // folded into |d|^2 (+1e-37f) as in the scalar kernel.

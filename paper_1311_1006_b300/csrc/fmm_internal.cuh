@@ -73,8 +73,9 @@ constexpr int kSortTile = kSortThreads * kSortRounds;
 // split) keep flag 0.
 struct SegTable {
     int K = 0;
-    int32_t* d_start = nullptr;  // K+1 entries, start[K] = n
-    int32_t* d_nzero = nullptr;  // K entries
+    int32_t* d_start = nullptr;    // K+1 entries, start[K] = n
+    int32_t* d_nzero = nullptr;    // K entries
+    int32_t* d_obefore = nullptr;  // K entries: flag-1 positions in segments before k
 };
 
 struct LevelList {
@@ -128,7 +129,7 @@ struct Tree {
     int32_t *d_X2 = nullptr, *d_Y2 = nullptr;
     uint8_t *d_sideX = nullptr, *d_sideY = nullptr;
     int32_t* d_loc = nullptr;  // input index -> local id inside a subtree CTA
-    int32_t *d_tile_cnt = nullptr, *d_tile_pre = nullptr, *d_seg_lc = nullptr;
+    unsigned long long* d_part_stat = nullptr;  // partition: tile status words + tile ticket
     int32_t *d_sort_hist = nullptr, *d_sort_tot = nullptr, *d_sort_off = nullptr;
     int64_t segs_cap = 0;
 

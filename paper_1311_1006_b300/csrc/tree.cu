@@ -45,7 +45,19 @@ static void free_list(LevelList& l) {
 static void free_seg(SegTable& s) {
     if (s.d_start) cudaFree(s.d_start);
     if (s.d_nzero) cudaFree(s.d_nzero);
+    if (s.d_obefore) cudaFree(s.d_obefore);
     s = SegTable();
+}
+
+// Flag-1 positions before each segment: segment j holds (length - nzero) of them.
+static std::vector<int32_t> ones_before(const std::vector<int32_t>& start, const std::vector<int32_t>& nzero) {
+    std::vector<int32_t> ob(nzero.size());
+    int64_t acc = 0;
+    for (size_t k = 0; k < nzero.size(); ++k) {
+        ob[k] = (int32_t)acc;
+        acc += (start[k + 1] - start[k]) - nzero[k];
+    }
+    return ob;
 }
 
 // Point ranges, parents and children of every box follow from the instance
@@ -169,6 +181,8 @@ fmm_status build_shape(Tree& t) {
         if ((st = upload(&t.seg_x[l].d_nzero, xz))) return st;
         if ((st = upload(&t.seg_y[l].d_start, ys))) return st;
         if ((st = upload(&t.seg_y[l].d_nzero, yz))) return st;
+        if ((st = upload(&t.seg_x[l].d_obefore, ones_before(xs, xz)))) return st;
+        if ((st = upload(&t.seg_y[l].d_obefore, ones_before(ys, yz)))) return st;
     }
     t.segs_cap = maxK;
     // first level whose splitting boxes all fit one CTA of the subtree kernel
@@ -401,109 +415,124 @@ __device__ __forceinline__ int block_excl_scan(int v, int* wsum, int& total) {
     return r;
 }
 
-// Pass 1: ones per tile, and for every segment that starts inside the tile the
-// number of ones in the tile before that start.
-__global__ void __launch_bounds__(kPartThreads) k_part_count(const int32_t* __restrict__ A,
-                                                             const uint8_t* __restrict__ side, int n,
-                                                             const int32_t* __restrict__ start, int K,
-                                                             int32_t* tile_cnt, int32_t* seg_lc) {
+constexpr unsigned long long kLAgg = 1ull << 62, kLIncl = 2ull << 62, kLVal = (1ull << 62) - 1;
+constexpr int kLookbackSpins = 1 << 21;
+
+__device__ __forceinline__ void st_volatile(unsigned long long* p, unsigned long long v) {
+    *reinterpret_cast<volatile unsigned long long*>(p) = v;
+}
+__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* p) {
+    return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
+// Stable segmented partition in one pass per stage.  List A is cut into
+// segments; within segment k the entries with flag 0 (side[point] == 0) keep
+// their order at the front and the flag-1 entries keep their order after the
+// segment's nzero[k] zeros.  The destination of entry i needs the number of
+// flag-1 entries before i inside its segment = (flag-1 entries before i in
+// the whole list) - obefore[k]; the first term comes from a block scan and a
+// decoupled look-back over the preceding tiles (tiles in ticket order,
+// bounded waits).  The flags of the NEXT stage, which cuts the list written
+// here, follow from each entry's destination and are written on the way.
+// Tile status words: bits 62-63 = 0 (not yet), 1 (aggregate), 2 (inclusive
+// prefix); [0, T) tiles, [T] ticket; zeroed before every stage.
+__global__ void __launch_bounds__(kPartThreads) k_part_fused(
+    const int32_t* __restrict__ A, const uint8_t* __restrict__ side, int n, const int32_t* __restrict__ start,
+    const int32_t* __restrict__ nzero, const int32_t* __restrict__ obefore, int K, int32_t* __restrict__ out,
+    const int32_t* __restrict__ nstart, const int32_t* __restrict__ nnzero, int nK, uint8_t* __restrict__ side_next,
+    unsigned long long* tstat, int T, unsigned* status) {
     __shared__ int wsum[32];
-    const int t = blockIdx.x;
-    const int i0 = t * kPartTile + threadIdx.x * kPartItems;
-    int f[kPartItems];
-    int sum = 0;
-#pragma unroll
-    for (int j = 0; j < kPartItems; ++j) {
-        int i = i0 + j;
-        f[j] = i < n ? (int)side[A[i]] : 0;
-        sum += f[j];
-    }
-    int total;
-    int excl = block_excl_scan(sum, wsum, total);
-    if (threadIdx.x == 0) tile_cnt[t] = total;
-    if (i0 < n) {
-        int k = find_seg(start, K, i0);
-        int acc = excl;
+    __shared__ int sh_tile;
+    __shared__ long long sh_excl;
+    unsigned long long* ticket = tstat + T;
+    while (true) {
+        if (threadIdx.x == 0) sh_tile = (int)atomicAdd(ticket, 1ull);
+        __syncthreads();
+        const int t = sh_tile;
+        __syncthreads();
+        if (t >= T) break;
+        const int i0 = t * kPartTile + threadIdx.x * kPartItems;
+        int f[kPartItems], a[kPartItems];
+        int sum = 0;
 #pragma unroll
         for (int j = 0; j < kPartItems; ++j) {
-            int i = i0 + j;
-            if (i < n) {
-                while (k + 1 < K && start[k + 1] <= i) ++k;
-                if (start[k] == i) seg_lc[k] = acc;
-            }
-            acc += f[j];
+            const int i = i0 + j;
+            a[j] = i < n ? A[i] : 0;
+            f[j] = i < n ? (int)side[a[j]] : 0;
+            sum += f[j];
         }
-    }
-}
-
-// Pass 2: exclusive scan of the tile counts (one block).
-__global__ void __launch_bounds__(1024) k_part_scan(const int32_t* __restrict__ cnt, int T, int32_t* pre) {
-    __shared__ int wsum[32];
-    int carry = 0;
-    for (int c0 = 0; c0 < T; c0 += 1024) {
-        int i = c0 + threadIdx.x;
-        int v = i < T ? cnt[i] : 0;
         int total;
-        int e = block_excl_scan(v, wsum, total);
-        if (i < T) pre[i] = carry + e;
-        carry += total;
-    }
-}
-
-// Pass 3: stable scatter.  Zeros keep their order at the front of their
-// segment, ones keep their order after the segment's nzero zeros.
-__global__ void __launch_bounds__(kPartThreads) k_part_scatter(const int32_t* __restrict__ A,
-                                                               const uint8_t* __restrict__ side, int n,
-                                                               const int32_t* __restrict__ start,
-                                                               const int32_t* __restrict__ nzero, int K,
-                                                               const int32_t* __restrict__ tile_pre,
-                                                               const int32_t* __restrict__ seg_lc, int32_t* out,
-                                                               unsigned* status) {
-    __shared__ int wsum[32];
-    const int t = blockIdx.x;
-    const int i0 = t * kPartTile + threadIdx.x * kPartItems;
-    int f[kPartItems], a[kPartItems];
-    int sum = 0;
+        const int excl = block_excl_scan(sum, wsum, total);
+        if (threadIdx.x == 0) {
+            unsigned long long pre = 0;
+            if (t == 0) {
+                st_volatile(tstat, kLIncl | (unsigned long long)total);
+            } else {
+                st_volatile(tstat + t, kLAgg | (unsigned long long)total);
+                int j = t - 1, spins = 0;
+                while (true) {
+                    const unsigned long long v = ld_volatile(tstat + j);
+                    const unsigned long long fl = v & ~kLVal;
+                    if (fl == 0) {
+                        if (++spins > kLookbackSpins) {
+                            atomicOr(status, ST_TIMEOUT);
+                            break;
+                        }
+                        continue;
+                    }
+                    pre += v & kLVal;
+                    if (fl == kLIncl || j == 0) break;
+                    --j;
+                }
+                st_volatile(tstat + t, kLIncl | (pre + (unsigned long long)total));
+            }
+            sh_excl = (long long)pre;
+        }
+        __syncthreads();
+        if (i0 >= n) continue;
+        long long P = sh_excl + excl;  // flag-1 entries before position i0
+        int k = find_seg(start, K, i0);
+        int s = start[k], e = start[k + 1], nz = nzero[k];
+        long long ob = obefore[k];
 #pragma unroll
-    for (int j = 0; j < kPartItems; ++j) {
-        int i = i0 + j;
-        a[j] = i < n ? A[i] : 0;
-        f[j] = i < n ? (int)side[a[j]] : 0;
-        sum += f[j];
-    }
-    int total;
-    int excl = block_excl_scan(sum, wsum, total);
-    if (i0 >= n) return;
-    int Pi = tile_pre[t] + excl;
-    int k = find_seg(start, K, i0);
-    int s = start[k];
-    int Ps = tile_pre[s / kPartTile] + seg_lc[k];
-#pragma unroll
-    for (int j = 0; j < kPartItems; ++j) {
-        int i = i0 + j;
-        if (i < n) {
-            while (k + 1 < K && start[k + 1] <= i) {
+        for (int j = 0; j < kPartItems; ++j) {
+            const int i = i0 + j;
+            if (i >= n) break;
+            while (i >= e) {
                 ++k;
                 s = start[k];
-                Ps = tile_pre[s / kPartTile] + seg_lc[k];
+                e = start[k + 1];
+                nz = nzero[k];
+                ob = obefore[k];
             }
-            int ones = Pi - Ps;
-            int dst = f[j] ? s + nzero[k] + ones : s + (i - s) - ones;
-            if (dst >= s && dst < start[k + 1]) out[dst] = a[j];
-            else atomicOr(status, ST_INTERNAL);
+            const int ones = (int)(P - ob);
+            const int dst = f[j] ? s + nz + ones : i - ones;
+            if (dst >= s && dst < e) {
+                out[dst] = a[j];
+                if (side_next) {
+                    const int kn = find_seg(nstart, nK, dst);
+                    side_next[a[j]] = (uint8_t)((dst - nstart[kn]) >= nnzero[kn]);
+                }
+            } else {
+                atomicOr(status, ST_INTERNAL);
+            }
+            P += f[j];
         }
-        Pi += f[j];
     }
 }
 
+// One stage: partition A by side (segments of `seg`) into out; with `next`,
+// also the flags of the next stage's cut of out.
 static fmm_status partition(Tree& t, cudaStream_t s, const int32_t* A, const uint8_t* side, const SegTable& seg,
-                            int32_t* out) {
+                            int32_t* out, const SegTable* next, uint8_t* side_next) {
     const int n = (int)t.n;
     const int T = nblk(n, kPartTile);
-    k_part_count<<<T, kPartThreads, 0, s>>>(A, side, n, seg.d_start, seg.K, t.d_tile_cnt, t.d_seg_lc);
-    k_part_scan<<<1, 1024, 0, s>>>(t.d_tile_cnt, T, t.d_tile_pre);
-    k_part_scatter<<<T, kPartThreads, 0, s>>>(A, side, n, seg.d_start, seg.d_nzero, seg.K, t.d_tile_pre, t.d_seg_lc,
-                                              out, t.d_status);
+    FMM_CUDA(cudaMemsetAsync(t.d_part_stat, 0, (size_t)(T + 1) * sizeof(unsigned long long), s));
+    const int grid = std::min(T, t.num_sms * 4);
+    k_part_fused<<<grid, kPartThreads, 0, s>>>(A, side, n, seg.d_start, seg.d_nzero, seg.d_obefore, seg.K, out,
+                                               next ? next->d_start : nullptr, next ? next->d_nzero : nullptr,
+                                               next ? next->K : 0, next ? side_next : nullptr, t.d_part_stat, T,
+                                               t.d_status);
     FMM_CUDA(cudaGetLastError());
     return FMM_OK;
 }
@@ -884,16 +913,6 @@ constexpr int kLThreads = 256, kLItems = 8, kLTile = kLThreads * kLItems;
 // Tile status words: bits 62-63 = 0 (not yet), 1 (tile aggregate), 2 (inclusive
 // prefix); bits 0-61 = the count.  [0, tiles_cap) strong, [tiles_cap, 2
 // tiles_cap) weak, then the ticket counter; zeroed before every level.
-constexpr unsigned long long kLAgg = 1ull << 62, kLIncl = 2ull << 62, kLVal = (1ull << 62) - 1;
-constexpr int kLookbackSpins = 1 << 21;
-
-__device__ __forceinline__ void st_volatile(unsigned long long* p, unsigned long long v) {
-    *reinterpret_cast<volatile unsigned long long*>(p) = v;
-}
-__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* p) {
-    return *reinterpret_cast<const volatile unsigned long long*>(p);
-}
-
 __global__ void __launch_bounds__(kLThreads) k_lists_level(
     int l, unsigned long long* lvl_base, int32_t* __restrict__ sowner, int32_t* __restrict__ soff,
     int32_t* __restrict__ ns, int32_t* __restrict__ sidx, int32_t* __restrict__ woff, int32_t* __restrict__ nw,
@@ -1157,9 +1176,7 @@ fmm_status alloc_build(Tree& t) {
     if ((st = dalloc(&t.d_sideY, n))) return st;
     if ((st = dalloc(&t.d_loc, n))) return st;
     const int64_t T = std::max<int64_t>(nblk(t.n, kPartTile), nblk(t.n, kSortTile));
-    if ((st = dalloc(&t.d_tile_cnt, T))) return st;
-    if ((st = dalloc(&t.d_tile_pre, T))) return st;
-    if ((st = dalloc(&t.d_seg_lc, t.segs_cap + 1))) return st;
+    if ((st = dalloc(&t.d_part_stat, T + 1))) return st;
     if ((st = dalloc(&t.d_sort_hist, 2 * 256 * (size_t)T))) return st;
     if ((st = dalloc(&t.d_sort_off, 2 * 256 * (size_t)T))) return st;
     if ((st = dalloc(&t.d_sort_tot, 2 * 256))) return st;
@@ -1250,14 +1267,19 @@ fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s) {
                                                t.d_rad32, 1);
     FMM_CUDA(cudaGetLastError());
     const int lglob = std::min(t.l0, t.Lmax - 1);  // levels split by the global passes
+    if (lglob > 0) {  // flags of the first cut (x, level 0); later cuts get theirs from the stage before
+        const SegTable& sx = t.seg_x[0];
+        k_mark<<<nblk(n, 256), 256, 0, s>>>(X, n, sx.d_start, sx.d_nzero, sx.K, t.d_sideX);
+    }
     for (int l = 0; l < lglob; ++l) {
         const SegTable& sx = t.seg_x[l];
         const SegTable& sy = t.seg_y[l];
-        k_mark<<<nblk(n, 256), 256, 0, s>>>(X, n, sx.d_start, sx.d_nzero, sx.K, t.d_sideX);
-        if ((st = partition(t, s, Y, t.d_sideX, sx, Y2))) return st;
+        // x-cut: Y partitioned by the x-side flags; the y-cut flags come from Y's new order
+        if ((st = partition(t, s, Y, t.d_sideX, sx, Y2, &sy, t.d_sideY))) return st;
         std::swap(Y, Y2);
-        k_mark<<<nblk(n, 256), 256, 0, s>>>(Y, n, sy.d_start, sy.d_nzero, sy.K, t.d_sideY);
-        if ((st = partition(t, s, X, t.d_sideY, sy, X2))) return st;
+        // y-cut: X partitioned by the y-side flags; the next level's x-cut flags come from X's new order
+        const SegTable* nxt = l + 1 < lglob ? &t.seg_x[l + 1] : nullptr;
+        if ((st = partition(t, s, X, t.d_sideY, sy, X2, nxt, t.d_sideX))) return st;
         std::swap(X, X2);
         const LevelList& Ll = t.level_boxes[l + 1];
         k_geom<<<nblk(Ll.count, 128), 128, 0, s>>>(Ll.d_ids, Ll.count, X, Y, xy, t.d_bstart, t.d_bcount, t.d_inst,

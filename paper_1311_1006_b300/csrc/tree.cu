@@ -425,6 +425,49 @@ __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long lo
     return *reinterpret_cast<const volatile unsigned long long*>(p);
 }
 
+// Decoupled look-back by one full warp: publishes tile t's aggregate, then
+// sums the counts of the preceding tiles 32 at a time (lane i reads tile
+// j - i) down to the nearest inclusive prefix, and publishes t's inclusive
+// prefix.  Returns the exclusive prefix of tile t (all lanes).  Bounded: after
+// kLookbackSpins rounds that met a tile with nothing published it sets
+// ST_TIMEOUT and returns what it has.
+__device__ unsigned long long warp_lookback(unsigned long long* st, long long t, unsigned long long agg,
+                                            unsigned* status) {
+    const int lane = threadIdx.x & 31;
+    if (t == 0) {
+        if (lane == 0) st_volatile(st, kLIncl | agg);
+        return 0;
+    }
+    if (lane == 0) st_volatile(st + t, kLAgg | agg);
+    unsigned long long excl = 0;
+    long long j = t - 1;
+    int spins = 0;
+    while (true) {
+        const long long q = j - lane;
+        const unsigned long long v = q >= 0 ? ld_volatile(st + q) : kLIncl;  // before tile 0: an empty prefix
+        const unsigned long long fl = v & ~kLVal;
+        const unsigned incl = __ballot_sync(0xffffffffu, fl == kLIncl);
+        const unsigned notready = __ballot_sync(0xffffffffu, fl == 0);
+        const int first = incl ? __ffs(incl) - 1 : 32;  // nearest inclusive prefix in this window
+        const unsigned need = first == 32 ? 0xffffffffu : (first == 31 ? 0xffffffffu : ((2u << first) - 1u));
+        if (notready & need) {
+            if (++spins > kLookbackSpins) {
+                if (lane == 0) atomicOr(status, ST_TIMEOUT);
+                break;
+            }
+            continue;
+        }
+        unsigned long long x = lane <= first ? (v & kLVal) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        excl += x;
+        if (first < 32) break;
+        j -= 32;
+    }
+    if (lane == 0) st_volatile(st + t, kLIncl | (excl + agg));
+    return excl;
+}
+
 // Stable segmented partition in one pass per stage.  List A is cut into
 // segments; within segment k the entries with flag 0 (side[point] == 0) keep
 // their order at the front and the flag-1 entries keep their order after the
@@ -463,30 +506,9 @@ __global__ void __launch_bounds__(kPartThreads) k_part_fused(
         }
         int total;
         const int excl = block_excl_scan(sum, wsum, total);
-        if (threadIdx.x == 0) {
-            unsigned long long pre = 0;
-            if (t == 0) {
-                st_volatile(tstat, kLIncl | (unsigned long long)total);
-            } else {
-                st_volatile(tstat + t, kLAgg | (unsigned long long)total);
-                int j = t - 1, spins = 0;
-                while (true) {
-                    const unsigned long long v = ld_volatile(tstat + j);
-                    const unsigned long long fl = v & ~kLVal;
-                    if (fl == 0) {
-                        if (++spins > kLookbackSpins) {
-                            atomicOr(status, ST_TIMEOUT);
-                            break;
-                        }
-                        continue;
-                    }
-                    pre += v & kLVal;
-                    if (fl == kLIncl || j == 0) break;
-                    --j;
-                }
-                st_volatile(tstat + t, kLIncl | (pre + (unsigned long long)total));
-            }
-            sh_excl = (long long)pre;
+        if (threadIdx.x < 32) {
+            const unsigned long long pre = warp_lookback(tstat, t, (unsigned long long)total, status);
+            if (threadIdx.x == 0) sh_excl = (long long)pre;
         }
         __syncthreads();
         if (i0 >= n) continue;
@@ -975,41 +997,20 @@ __global__ void __launch_bounds__(kLThreads) k_lists_level(
         int tot_s, tot_w;
         long long ps = block_excl_scan(cs, ws, tot_s);
         long long pw = block_excl_scan(cw, ww, tot_w);
-        if (threadIdx.x == 0 || threadIdx.x == 32) {
-            const int which = threadIdx.x == 0 ? 0 : 1;
-            unsigned long long* st = tstat + which * tiles_cap;
+        if (threadIdx.x < 64) {  // warp 0: strong counts, warp 1: weak counts
+            const int which = threadIdx.x >> 5;
             const unsigned long long agg = (unsigned long long)(which ? tot_w : tot_s);
-            unsigned long long excl = 0;
-            if (t == 0) {
-                st_volatile(st, kLIncl | agg);
-            } else {
-                st_volatile(st + t, kLAgg | agg);
-                long long j = t - 1;
-                int spins = 0;
-                while (true) {
-                    const unsigned long long v = ld_volatile(st + j);
-                    const unsigned long long f = v & ~kLVal;
-                    if (f == 0) {
-                        if (++spins > kLookbackSpins) {
-                            atomicOr(status, ST_TIMEOUT);
-                            break;
-                        }
-                        continue;
+            const unsigned long long excl = warp_lookback(tstat + which * tiles_cap, t, agg, status);
+            if ((threadIdx.x & 31) == 0) {
+                sh_excl[which] = (long long)excl;
+                if (t == ntiles - 1) {  // level totals and capacity checks
+                    const long long base = which ? bw : bs;
+                    const long long end = base + (long long)(excl + agg);
+                    lvl_base[which ? kMaxLevels + l + 1 : l + 1] = (unsigned long long)end;
+                    if (end > (which ? wcap : scap)) {
+                        atomicMax(need + 1 + which, (unsigned long long)end);
+                        atomicOr(status, which ? ST_WEAK_OVERFLOW : ST_STRONG_OVERFLOW);
                     }
-                    excl += v & kLVal;
-                    if (f == kLIncl || j == 0) break;
-                    --j;
-                }
-                st_volatile(st + t, kLIncl | (excl + agg));
-            }
-            sh_excl[which] = (long long)excl;
-            if (t == ntiles - 1) {  // level totals and capacity checks
-                const long long base = which ? bw : bs;
-                const long long end = base + (long long)(excl + agg);
-                lvl_base[which ? kMaxLevels + l + 1 : l + 1] = (unsigned long long)end;
-                if (end > (which ? wcap : scap)) {
-                    atomicMax(need + 1 + which, (unsigned long long)end);
-                    atomicOr(status, which ? ST_WEAK_OVERFLOW : ST_STRONG_OVERFLOW);
                 }
             }
         }

@@ -271,6 +271,49 @@ def run_gpu(args):
         except _lib.FMMError:
             bwd_ratio = None
 
+        # --- theta autotuning (the second control of Sec. 4.2): N_levels and theta
+        # tuned together at TOL = 1e-6, p following theta, on the same workload ----
+        theta_tune = None
+        if rank == 0 and not args.no_theta_tune:
+            tol = 1e-6
+            th, L2 = THETA, tuned
+            pp = F.p_for_tolerance(tol, th)
+            tt = F.Tree.build(X, p=pp, theta=th, nlevels=L2, path="fp32")
+            tt.autotune_config(cap=0.2, window=2, period=2)
+            tt.autotune_theta(tol, 0.35, 0.65)
+            ph = torch.empty(N_POINTS, dtype=torch.complex64, device=dev)
+            for _ in range(60):
+                e0.record(stream)
+                tt.rebuild(X, nlevels=L2, theta=th, p=pp)
+                tt.eval(G, out=ph)
+                e1.record(stream)
+                e1.synchronize()
+                L2, th, pp = tt.autotune_params(e0.elapsed_time(e1) * 1e-3)
+            inf2 = tt.info()
+            L2, th = int(inf2["autotune_nlevels"]), float(inf2["autotune_theta"])
+            pp = F.p_for_tolerance(tol, th)
+            tt.rebuild(X, nlevels=L2, theta=th, p=pp)
+            tt.eval(G, out=ph)
+            tts = []
+            for _ in range(10):
+                flush.zero_()
+                e0.record(stream)
+                tt.rebuild(X)
+                tt.eval(G, out=ph)
+                e1.record(stream)
+                e1.synchronize()
+                tts.append(e0.elapsed_time(e1))
+            import oracle as _orc
+
+            tg2 = np.random.default_rng(8).choice(N_POINTS, 1024, replace=False)
+            ex2 = _orc.direct(xy, gam, targets=tg2)
+            theta_tune = {"tol": tol, "theta": round(th, 4), "p": pp, "nlevels": L2,
+                          "ms_per_step": round(float(np.median(tts)), 4),
+                          "value": round(N_POINTS / (float(np.median(tts)) * 1e-3) / 1e6, 2),
+                          "rel_err_sampled": _rel(ph.cpu().numpy().astype(np.complex128)[tg2], ex2),
+                          "tuning_steps": 60}
+            tt.close()
+
         # --- end to end through the C ABI with host buffers -----------------------
         h_xy = torch.tensor(xy).pin_memory()
         h_g = torch.tensor(gam).pin_memory()
@@ -336,6 +379,7 @@ def run_gpu(args):
                       "rel_err_sampled": err64},
         "rel_err_sampled": err32,
         "bwd_over_fwd": bwd_ratio,
+        "theta_autotune": theta_tune,
         "roofline": {"kernel": "k_p2p_pairs (P2P, FP32 f32x2)", "bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                      "traffic": P2P_TRAFFIC_BYTES, "kernel_ms": round(p2p_ms, 4),
@@ -405,6 +449,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nlevels", type=int, default=0, help="fix N_levels (skip the autotuner warm-up)")
+    ap.add_argument("--no-theta-tune", action="store_true", help="skip the theta autotuning run")
     ap.add_argument("--only-step", action="store_true",
                     help="time the step only (no phase split, FP64 path, adjoint, e2e, accuracy); for profiling")
     args = ap.parse_args()

@@ -126,12 +126,27 @@ fmm_status fmm_eval_batched(fmm_tree* t, const double* d_gamma, void* d_phi, voi
 fmm_status fmm_eval_backward(fmm_tree* t, const double* d_gamma, const double* d_gphi, double* d_ggamma,
                              double* d_gxy, void* stream);
 
-/* One step of the N_levels autotuner (Sec. 4.2, Algorithm 4 "AT3b": a directed
- * walk with cost estimation and a user cap on the tuning cost).  Call after
- * every evaluation with its time; *inout receives the parameters to use next
- * (only nlevels changes; theta is kept).  The caller rebuilds the tree with
- * them (fmm_tree_rebuild).  Host-only; no device work. */
+/* One step of the autotuner (Sec. 4.2, Algorithm 4 "AT3b": a directed walk
+ * with cost estimation and a user cap on the tuning cost).  Call after every
+ * evaluation with its time; *inout receives the parameters to use next
+ * (nlevels; with fmm_autotune_theta also theta and p, else theta is kept and p
+ * untouched).  The caller rebuilds the tree with them (fmm_tree_rebuild).
+ * Host-only; no device work. */
 fmm_status fmm_autotune_step(fmm_tree* t, double last_time_s, fmm_params* inout);
+
+/* Tune theta as well (the theta moves of Algorithms 2-4, Sec. 4.2): moves of
+ * 0.01 x Fibonacci steps alternating with N_levels moves; a rejected move
+ * reverses direction and takes the next step of the sequence.  p follows
+ * theta through the tolerance: p = fmm_p_for_tolerance(tol, theta).  theta is
+ * kept in [theta_min, theta_max] and where p <= FMM_P_MAX.
+ * Errors: INVALID_ARG (0 < tol < 1, 0 < theta_min <= theta_max < 1 and
+ * p(tol, theta_min) <= FMM_P_MAX required). */
+fmm_status fmm_autotune_theta(fmm_tree* t, double tol, double theta_min, double theta_max);
+
+/* Expansion terms for relative tolerance tol at separation theta (Sec. 4.1,
+ * p ~ log TOL / log theta): ceil(0.9 ln(tol) / ln(theta)); never below the
+ * paper's Table 4.1 and at most one above it.  -1 for arguments outside (0,1). */
+int fmm_p_for_tolerance(double tol, double theta);
 
 /* Configure the autotuner: cap = maximum relative tuning cost (e.g. 0.1),
  * window = number of evaluations whose minimum time is used per decision
@@ -149,6 +164,12 @@ typedef struct fmm_autotuner fmm_autotuner;
 fmm_status fmm_autotuner_create(int nlevels, int max_levels, double cap, int window, int period,
                                 fmm_autotuner** out);
 fmm_status fmm_autotuner_step(fmm_autotuner* a, double time_s, int* nlevels_out);
+/* Enable theta moves on a standalone tuner (as fmm_autotune_theta), starting at theta. */
+fmm_status fmm_autotuner_theta(fmm_autotuner* a, double theta, double tol, double theta_min, double theta_max);
+/* As fmm_autotuner_step, also writing theta and p to use next (p = -1 without theta moves). */
+fmm_status fmm_autotuner_step_params(fmm_autotuner* a, double time_s, int* nlevels_out, double* theta_out,
+                                     int* p_out);
+/* Up to 8 values: the 6 above, then the accepted theta and the theta on trial (0 = none). */
 fmm_status fmm_autotuner_stats(const fmm_autotuner* a, double* out, int nout);
 void fmm_autotuner_destroy(fmm_autotuner* a);
 
@@ -180,6 +201,7 @@ typedef struct {
     int autotune_nlevels;    /* N_levels the autotuner has accepted so far */
     int launches_build;      /* kernels one build / rebuild launches */
     int launches_eval;       /* kernels one evaluation launches */
+    double autotune_theta;   /* theta the autotuner has accepted (the tree's theta without theta moves) */
 } fmm_tree_info;
 
 /* Fills *out; the pair counts are summed on the device (synchronises). */

@@ -21,7 +21,7 @@ from . import _lib
 from ._lib import (FMM_FLAG_GRAPH, FMM_FLAG_NO_GRAPH, FMM_FLAG_SERIAL, FMM_FLAG_TIMING, FMM_PATH_FP32, FMM_PATH_FP64, FMMError,
                    FMMParams)
 
-__all__ = ["Tree", "FMMFunction", "fmm", "default_nlevels", "Autotuner", "FMMError", "FMM_PATH_FP32",
+__all__ = ["Tree", "FMMFunction", "fmm", "default_nlevels", "p_for_tolerance", "Autotuner", "FMMError", "FMM_PATH_FP32",
            "FMM_PATH_FP64", "FMM_FLAG_GRAPH", "FMM_FLAG_NO_GRAPH", "FMM_FLAG_SERIAL", "FMM_FLAG_TIMING"]
 
 
@@ -205,6 +205,16 @@ class Tree:
         _lib.check(_lib.load().fmm_autotune_step(self._h, float(seconds), ctypes.byref(prm)))
         return int(prm.nlevels)
 
+    def autotune_theta(self, tol: float, theta_min=0.35, theta_max=0.65) -> None:
+        """Tune theta as well (p follows from tol); see autotune_params."""
+        _lib.check(_lib.load().fmm_autotune_theta(self._h, float(tol), float(theta_min), float(theta_max)))
+
+    def autotune_params(self, seconds: float) -> tuple:
+        """One tuner step; returns (nlevels, theta, p) to rebuild with."""
+        prm = FMMParams(self.params.p, self.params.theta, 0, self.params.path, self.params.flags)
+        _lib.check(_lib.load().fmm_autotune_step(self._h, float(seconds), ctypes.byref(prm)))
+        return int(prm.nlevels), float(prm.theta), int(prm.p)
+
     def close(self) -> None:
         if getattr(self, "_h", None):
             _lib.load().fmm_tree_destroy(self._h)
@@ -217,8 +227,13 @@ class Tree:
             pass
 
 
+def p_for_tolerance(tol: float, theta: float) -> int:
+    """fmm_p_for_tolerance: expansion terms for tolerance tol at separation theta."""
+    return int(_lib.load().fmm_p_for_tolerance(float(tol), float(theta)))
+
+
 class Autotuner:
-    """Standalone AT3b N_levels autotuner (fmm_autotuner_*)."""
+    """Standalone AT3b autotuner (fmm_autotuner_*): N_levels, optionally theta."""
 
     def __init__(self, nlevels: int, max_levels: int, cap=0.1, window=3, period=8):
         lib = _lib.load()
@@ -231,10 +246,22 @@ class Autotuner:
         _lib.check(_lib.load().fmm_autotuner_step(self._h, float(seconds), ctypes.byref(out)))
         return int(out.value)
 
+    def enable_theta(self, theta: float, tol: float, theta_min=0.35, theta_max=0.65) -> None:
+        _lib.check(_lib.load().fmm_autotuner_theta(self._h, float(theta), float(tol), float(theta_min),
+                                                   float(theta_max)))
+
+    def step_params(self, seconds: float) -> tuple:
+        """(nlevels, theta, p) to use next."""
+        nl, th, pp = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+        _lib.check(_lib.load().fmm_autotuner_step_params(self._h, float(seconds), ctypes.byref(nl), ctypes.byref(th),
+                                                         ctypes.byref(pp)))
+        return int(nl.value), float(th.value), int(pp.value)
+
     def stats(self) -> dict:
-        out = (ctypes.c_double * 6)()
-        _lib.check(_lib.load().fmm_autotuner_stats(self._h, out, 6))
-        return dict(zip(["accepted", "steps", "rejected", "tuning_cost", "basetime", "trial"], list(out)))
+        out = (ctypes.c_double * 8)()
+        _lib.check(_lib.load().fmm_autotuner_stats(self._h, out, 8))
+        return dict(zip(["accepted", "steps", "rejected", "tuning_cost", "basetime", "trial", "theta",
+                         "theta_trial"], list(out)))
 
     def __del__(self):
         try:

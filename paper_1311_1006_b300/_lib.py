@@ -41,7 +41,8 @@ class FMMTreeInfo(ctypes.Structure):
                 ("nboxes", ctypes.c_int64), ("nleaves", ctypes.c_int64), ("n_strong", ctypes.c_int64),
                 ("n_weak", ctypes.c_int64), ("n_strong_leaf", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64),
                 ("p2p_items", ctypes.c_int64), ("m2l_items", ctypes.c_int64), ("autotune_nlevels", ctypes.c_int),
-                ("launches_build", ctypes.c_int), ("launches_eval", ctypes.c_int)]
+                ("launches_build", ctypes.c_int), ("launches_eval", ctypes.c_int),
+                ("autotune_theta", ctypes.c_double)]
 
 
 class FMMError(RuntimeError):
@@ -80,6 +81,11 @@ def load() -> ctypes.CDLL:
         "fmm_autotuner_step": (S, [_VP, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
         "fmm_autotuner_stats": (S, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
         "fmm_autotuner_destroy": (None, [_VP]),
+        "fmm_autotune_theta": (S, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+        "fmm_p_for_tolerance": (ctypes.c_int, [ctypes.c_double, ctypes.c_double]),
+        "fmm_autotuner_theta": (S, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+        "fmm_autotuner_step_params": (S, [_VP, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
         "fmm_default_nlevels": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.c_int]),
         "fmm_phase_times": (S, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
         "fmm_get_tree_info": (S, [_VP, ctypes.POINTER(FMMTreeInfo)]),

@@ -461,6 +461,7 @@ fmm_status fmm_get_tree_info(const fmm_tree* h, fmm_tree_info* out) {
     // per evaluation: gather, P2M, M2M per level, M2L, M2L partial sums, L2L per level, P2P, P2P partial
     // sums, L2P
     out->launches_eval = 7 + 2 * lv;
+    out->autotune_theta = t.tune.theta_on ? t.tune.theta : t.theta;
     return FMM_OK;
 }
 

@@ -223,6 +223,15 @@ struct Tree {
         int max_levels = 1;
         int rejected = 0;
         double tuning_cost = 0;  // time lost to rejected moves
+        // theta moves (Algorithms 2-4): 0.01 x Fibonacci steps, p follows theta through the tolerance
+        bool theta_on = false;
+        double tol = 1e-6, theta_lo = 0.3, theta_hi = 0.7;
+        double theta = 0.5;        // accepted theta
+        double theta_trial = 0;    // theta on trial (0 = none)
+        int theta_dir = +1;
+        int fibcount = 1, fiblength = 3;
+        int trial_kind = 0;        // 0 none, 1 N_levels move, 2 theta move
+        int next_kind = 1;         // kind of the next move attempt (they alternate)
     } tune;
 };
 
@@ -275,6 +284,8 @@ void launch_m2l_tc(const Tree& t, const float2* M32, float2* Lm2l, float2* part,
 int default_nlevels(int64_t n, int p, int path);
 
 int tune_step(Tree::Tune& u, double time_s);
+int p_for_tolerance(double tol, double theta);
+double tune_theta(const Tree::Tune& u);  // theta to use next (accepted or on trial)
 
 // Smallest compiled expansion order >= p (kernels are templates on the order).
 int compiled_order(int p);

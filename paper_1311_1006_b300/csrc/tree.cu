@@ -238,6 +238,31 @@ __global__ void k_inst_keys(const int32_t* __restrict__ vx, const int32_t* __res
     }
 }
 
+__device__ __forceinline__ int block_excl_scan(int v, int* wsum, int& total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int ws = lane < nw ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, ws, o);
+            if (lane >= o) ws += y;
+        }
+        wsum[lane] = ws;
+    }
+    __syncthreads();
+    total = wsum[nw - 1];
+    int r = x - v + (w ? wsum[w - 1] : 0);
+    __syncthreads();
+    return r;
+}
+
 // Per-tile digit histograms of both sorts (blockIdx.y = which sort).
 __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint64_t* __restrict__ k0,
                                                             const uint64_t* __restrict__ k1, int n, int shift, int T,
@@ -302,9 +327,15 @@ __global__ void __launch_bounds__(1024) k_sort_scan(const int32_t* __restrict__ 
     }
 }
 
-// Stable scatter of one 8-bit digit.  A tile is processed in rounds of 256
-// consecutive keys; within a round, warps rank equal digits with match_any and
-// a per-digit prefix over warps keeps the input order.
+// Stable scatter of one 8-bit digit.  Warp w of a tile owns its 256
+// consecutive keys (lane l holds keys w*256 + 32 r + l, r = 0..7, loaded up
+// front); each warp ranks its keys round by round with match_any and a
+// warp-private digit counter, so the rounds need only warp synchronisation.
+// One exclusive pass over the warps per digit then gives every key its rank
+// among the tile's keys of its digit (input order: stable).  The tile is
+// reordered by digit in shared memory and written back so that consecutive
+// threads store consecutive keys of a digit: each digit's run of the tile is
+// one contiguous piece of the output.
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t* __restrict__ ki0,
                                                                const int32_t* __restrict__ vi0,
                                                                const uint64_t* __restrict__ ki1,
@@ -312,9 +343,13 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t* _
                                                                int32_t* vo0, uint64_t* ko1, int32_t* vo1, int n,
                                                                int shift, int T, const int32_t* __restrict__ off,
                                                                unsigned* status) {
-    __shared__ int run[256];
-    __shared__ int wcnt[kSortThreads / 32][256];
-    __shared__ int base[256];
+    constexpr int W = kSortThreads / 32;
+    __shared__ int whist[W][257];  // per-warp digit counts, then their exclusive prefix over warps
+    __shared__ int base[256];      // global position of the tile's first key of each digit
+    __shared__ int tstart[257];    // first tile-local slot of each digit
+    __shared__ int wsum[32];
+    __shared__ uint64_t skey[kSortTile];
+    __shared__ int sval[kSortTile];
     const int s = blockIdx.y, t = blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const uint64_t* ki = s ? ki1 : ki0;
@@ -322,41 +357,66 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t* _
     uint64_t* ko = s ? ko1 : ko0;
     int32_t* vo = s ? vo1 : vo0;
     base[tid] = off[((size_t)s * 256 + tid) * T + t];
-    run[tid] = 0;
+#pragma unroll
+    for (int j = 0; j < 257; j += 32)
+        if (j + lane < 257) whist[warp][j + lane] = 0;
+    uint64_t key[kSortRounds];
+    int val[kSortRounds], rank[kSortRounds], dig[kSortRounds];
+    const int i0 = t * kSortTile + warp * (32 * kSortRounds) + lane;
+#pragma unroll
     for (int r = 0; r < kSortRounds; ++r) {
-        const int i = t * kSortTile + r * kSortThreads + tid;
+        const int i = i0 + 32 * r;
         const bool valid = i < n;
-        uint64_t k = valid ? ki[i] : 0;
-        int v = valid ? vi[i] : 0;
-        int d = valid ? (int)((k >> shift) & 255u) : 256;
+        key[r] = valid ? ki[i] : 0;
+        val[r] = valid ? vi[i] : 0;
+        dig[r] = valid ? (int)((key[r] >> shift) & 255u) : 256;
+    }
+    __syncwarp();
 #pragma unroll
-        for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][tid] = 0;
-        __syncthreads();
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        int rank = __popc(peers & lanemask_lt());
-        if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        {
-            int acc = run[tid];
+    for (int r = 0; r < kSortRounds; ++r) {
+        const int d = dig[r];
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int before = whist[warp][d];
+        rank[r] = before + __popc(peers & lanemask_lt());
+        __syncwarp();
+        if (lane == __ffs(peers) - 1) whist[warp][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    int cnt = 0;
+    {  // thread = digit: exclusive prefix of the digit's count over the warps
 #pragma unroll
-            for (int w = 0; w < kSortThreads / 32; ++w) {
-                int c = wcnt[w][tid];
-                wcnt[w][tid] = acc;
-                acc += c;
-            }
-            run[tid] = acc;
+        for (int w = 0; w < W; ++w) {
+            const int c = whist[w][tid];
+            whist[w][tid] = cnt;
+            cnt += c;
         }
-        __syncthreads();
-        if (valid) {
-            int pos = base[d] + wcnt[warp][d] + rank;
-            if (pos >= 0 && pos < n) {
-                ko[pos] = k;
-                vo[pos] = v;
-            } else {
-                atomicOr(status, ST_INTERNAL);
-            }
+    }
+    int total;
+    const int st0 = block_excl_scan(cnt, wsum, total);  // first local slot of digit tid (contains barriers)
+    tstart[tid] = st0;
+    if (tid == 0) tstart[256] = total;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+        const int d = dig[r];
+        if (d < 256) {
+            const int slot = tstart[d] + whist[warp][d] + rank[r];
+            skey[slot] = key[r];
+            sval[slot] = val[r];
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    for (int j = tid; j < total; j += kSortThreads) {
+        const uint64_t k = skey[j];
+        const int d = (int)((k >> shift) & 255u);
+        const int pos = base[d] + (j - tstart[d]);
+        if (pos >= 0 && pos < n) {
+            ko[pos] = k;
+            vo[pos] = sval[j];
+        } else {
+            atomicOr(status, ST_INTERNAL);
+        }
     }
 }
 
@@ -390,30 +450,6 @@ __global__ void k_mark(const int32_t* __restrict__ A, int n, const int32_t* __re
     side[A[i]] = (uint8_t)((i - start[k]) >= nzero[k]);
 }
 
-__device__ __forceinline__ int block_excl_scan(int v, int* wsum, int& total) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
-    int x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        int ws = lane < nw ? wsum[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, ws, o);
-            if (lane >= o) ws += y;
-        }
-        wsum[lane] = ws;
-    }
-    __syncthreads();
-    total = wsum[nw - 1];
-    int r = x - v + (w ? wsum[w - 1] : 0);
-    __syncthreads();
-    return r;
-}
 
 constexpr unsigned long long kLAgg = 1ull << 62, kLIncl = 2ull << 62, kLVal = (1ull << 62) - 1;
 constexpr int kLookbackSpins = 1 << 21;

@@ -47,6 +47,7 @@ def _load():
         lib.fo_max_threads.restype = ctypes.c_int
         lib.fo_direct.argtypes = [_I64, _P, _P, _I64, _P, _P, _P]
         lib.fo_direct_grad.argtypes = [_I64, _P, _P, _P, _I64, _P, _P, _P]
+        lib.fo_direct_points.argtypes = [_I64, _P, _P, _I64, _P, _P]
         lib.fo_build_tree.restype = ctypes.c_int
         lib.fo_build_tree.argtypes = [_I64, _P, ctypes.c_int, _P, _P, _P, _P, _P]
         lib.fo_build_lists.restype = ctypes.c_int
@@ -103,6 +104,18 @@ def direct(xy, gamma, targets=None, deriv: bool = False):
     dphi = np.zeros(m, np.complex128) if deriv else None
     lib.fo_direct(n, _ptr(xy), _ptr(gamma), m, _ptr(tg), _ptr(phi), _ptr(dphi))
     return (phi, dphi) if deriv else phi
+
+
+def direct_points(src_xy, gamma, tgt_xy):
+    """Exact eq (2.2) sum at separate evaluation points ``tgt_xy`` (M x 2):
+    Phi(y_t) = sum_{j: x_j != y_t} Gamma_j / (y_t - x_j)."""
+    lib = _load()
+    sxy, txy = _xy(src_xy), _xy(tgt_xy)
+    n, m = sxy.shape[0], txy.shape[0]
+    gamma = _cx(gamma, n)
+    phi = np.zeros(m, np.complex128)
+    lib.fo_direct_points(n, _ptr(sxy), _ptr(gamma), m, _ptr(txy), _ptr(phi))
+    return phi
 
 
 def direct_grad(xy, gamma, gphi, targets=None):

@@ -144,6 +144,23 @@ void fo_direct(int64_t n, const double* xy, const double* gam, int64_t m, const 
     }
 }
 
+/* Exact sum of eq (2.2) with separate evaluation points: for each of the m
+ * points y_t (txy, interleaved x, y), phi[t] = sum_{j: x_j != y_t} Gamma_j / (y_t - x_j)
+ * over the n sources x_j (sxy).                                                      */
+void fo_direct_points(int64_t n, const double* sxy, const double* gam, int64_t m, const double* txy, double* phi) {
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t t = 0; t < m; ++t) {
+        cplx yt = txy[2 * t] + I * txy[2 * t + 1];
+        cplx s = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            cplx xj = sxy[2 * j] + I * sxy[2 * j + 1];
+            if (xj == yt) continue; /* eq (2.2): x_j != y_t */
+            s += load_c(gam, j) / (yt - xj);
+        }
+        store_c(phi, t, s);
+    }
+}
+
 /* Exact gradient of the loss  L = sum_i w_i Re Phi_i + v_i Im Phi_i  with
  * upstream gphi_i = w_i + i v_i, at the points tgt[0..m) (all when NULL).
  * Derivation (chain rule on the holomorphic kernel), with c_i = conj(gphi_i):

@@ -381,3 +381,32 @@ def test_fmm_gradient_matches_direct_gradient(orc):
     rg, rxy = orc.direct_grad(xy, gam, gphi)
     assert np.abs(gg - rg).max() <= 1e-8 * np.abs(rg).max()
     assert np.abs(gxy - rxy).max() <= 1e-8 * np.abs(rxy).max()
+
+
+# ---------------------------------------------------------------- separate evaluation points (eq 2.2)
+
+def test_direct_points_closed_form():
+    """Two sources and two evaluation points, summed by hand; an evaluation
+    point on a source skips that source (x_j != y_t)."""
+    import oracle
+
+    src = np.array([[0.0, 0.0], [1.0, 0.0]])
+    gam = np.array([2.0 + 1.0j, -1.0 + 0.5j])
+    tgt = np.array([[0.0, 1.0], [1.0, 0.0]])
+    y0 = 0.0 + 1.0j
+    want0 = (2.0 + 1.0j) / (y0 - 0.0) + (-1.0 + 0.5j) / (y0 - 1.0)
+    want1 = (2.0 + 1.0j) / (1.0 - 0.0)  # the second source coincides with the point
+    got = oracle.direct_points(src, gam, tgt)
+    assert abs(got[0] - want0) < 1e-15 and abs(got[1] - want1) < 1e-15
+
+
+def test_direct_points_equals_direct_on_the_sources():
+    """With the evaluation points equal to the sources, eq (2.2) is eq (2.1)."""
+    import oracle
+
+    g = np.random.default_rng(11)
+    xy = g.random((300, 2))
+    gam = g.standard_normal(300) + 1j * g.standard_normal(300)
+    a = oracle.direct_points(xy, gam, xy)
+    b = oracle.direct(xy, gam)
+    assert np.max(np.abs(a - b)) <= 1e-14 * np.max(np.abs(b))

@@ -126,6 +126,23 @@ fmm_status fmm_eval_batched(fmm_tree* t, const double* d_gamma, void* d_phi, voi
 fmm_status fmm_eval_backward(fmm_tree* t, const double* d_gamma, const double* d_gphi, double* d_ggamma,
                              double* d_gxy, void* stream);
 
+/* Separate evaluation points (eq 2.2): Phi(y_i) = sum_{j: x_j != y_i} Gamma_j / (y_i - x_j)
+ * at n_tgt points y (d_tgt_xy, n_tgt x 2 float64, device) for n_src sources x
+ * (d_src_xy, n_src x 2 float64, device).  The tree is built over the sources and
+ * the evaluation points together, the evaluation points carrying zero strength
+ * (they change no expansion; the P2P pass skips coincident points, which is
+ * x_j != y_i), so the balanced splits see all n_src + n_tgt points.
+ * fmm_eval_targets: d_gamma = n_src complex128 source strengths, d_phi = n_tgt
+ * complex values (complex64 on the FP32 path, complex128 on FP64).  The library
+ * keeps copies of the points and strengths in its own workspace.  N_levels is
+ * chosen for n_src + n_tgt points.  Errors: INVALID_ARG (NULL, n < 1, a tree not
+ * built with fmm_build_tree_targets), CUDA, OOM. */
+fmm_status fmm_build_tree_targets(const double* d_src_xy, int64_t n_src, const double* d_tgt_xy, int64_t n_tgt,
+                                  const fmm_params* params, void* stream, fmm_tree** out);
+fmm_status fmm_tree_rebuild_targets(fmm_tree* t, const double* d_src_xy, const double* d_tgt_xy,
+                                    const fmm_params* params, void* stream);
+fmm_status fmm_eval_targets(fmm_tree* t, const double* d_gamma, void* d_phi, void* stream);
+
 /* One step of the autotuner (Sec. 4.2, Algorithm 4 "AT3b": a directed walk
  * with cost estimation and a user cap on the tuning cost).  Call after every
  * evaluation with its time; *inout receives the parameters to use next

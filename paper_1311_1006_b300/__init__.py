@@ -65,12 +65,13 @@ def default_nlevels(n: int, p: int = 17, path="fp32") -> int:
 class Tree:
     """A device-resident FMM tree (tree + coupling lists + workspace)."""
 
-    def __init__(self, handle, n, params: FMMParams, batched=False, ninst=1):
+    def __init__(self, handle, n, params: FMMParams, batched=False, ninst=1, n_src=0, n_tgt=0):
         self._h = handle
         self.n = int(n)
         self.params = params
         self.batched = batched
         self.ninst = ninst
+        self.n_src, self.n_tgt = int(n_src), int(n_tgt)
 
     # -- construction -------------------------------------------------------
     @classmethod
@@ -84,6 +85,34 @@ class Tree:
         h = ctypes.c_void_p()
         _lib.check(lib.fmm_build_tree(ptr, n, ctypes.byref(prm), _stream(stream), ctypes.byref(h)))
         return cls(h, n, prm)
+
+    @classmethod
+    def build_targets(cls, src_xy, tgt_xy, p=17, theta=0.5, nlevels=0, path="fp32", flags=0,
+                      stream=None) -> "Tree":
+        """fmm_build_tree_targets: sources (N, 2) and separate evaluation points (M, 2), float64 CUDA."""
+        torch = _torch()
+        lib = _lib.load()
+        ns, nt = src_xy.shape[0], tgt_xy.shape[0]
+        ps = _dev(src_xy, torch.float64, (ns, 2), "src_xy")
+        pt = _dev(tgt_xy, torch.float64, (nt, 2), "tgt_xy")
+        prm = FMMParams(int(p), float(theta), int(nlevels), _path(path), int(flags))
+        h = ctypes.c_void_p()
+        _lib.check(lib.fmm_build_tree_targets(ps, ns, pt, nt, ctypes.byref(prm), _stream(stream), ctypes.byref(h)))
+        return cls(h, ns + nt, prm, n_src=ns, n_tgt=nt)
+
+    def rebuild_targets(self, src_xy, tgt_xy, nlevels=None, p=None, theta=None, path=None, flags=None,
+                        stream=None) -> None:
+        """fmm_tree_rebuild_targets for new source / evaluation-point coordinates."""
+        torch = _torch()
+        ps = _dev(src_xy, torch.float64, (self.n_src, 2), "src_xy")
+        pt = _dev(tgt_xy, torch.float64, (self.n_tgt, 2), "tgt_xy")
+        prm = FMMParams(self.params.p if p is None else int(p),
+                        self.params.theta if theta is None else float(theta),
+                        0 if nlevels is None else int(nlevels),
+                        self.params.path if path is None else _path(path),
+                        self.params.flags if flags is None else int(flags))
+        _lib.check(_lib.load().fmm_tree_rebuild_targets(self._h, ps, pt, ctypes.byref(prm), _stream(stream)))
+        self.params = prm
 
     @classmethod
     def build_batched(cls, xy, offsets, nlevels=None, p=17, theta=0.5, path="fp32", flags=0,
@@ -137,6 +166,16 @@ class Tree:
         o = _dev(out, self.out_dtype, (self.n,), "out")
         fn = _lib.load().fmm_eval_batched if self.batched else _lib.load().fmm_eval
         _lib.check(fn(self._h, g, o, _stream(stream)))
+        return out
+
+    def eval_targets(self, gamma, out=None, stream=None):
+        """fmm_eval_targets: gamma = (N_src,) complex128 source strengths; returns Phi at the evaluation points."""
+        torch = _torch()
+        g = _dev(gamma, torch.complex128, (self.n_src,), "gamma")
+        if out is None:
+            out = torch.empty(self.n_tgt, dtype=self.out_dtype, device=gamma.device)
+        o = _dev(out, self.out_dtype, (self.n_tgt,), "out")
+        _lib.check(_lib.load().fmm_eval_targets(self._h, g, o, _stream(stream)))
         return out
 
     def backward(self, gamma, gphi, stream=None):

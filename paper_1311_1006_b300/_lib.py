@@ -72,6 +72,10 @@ def load() -> ctypes.CDLL:
         "fmm_build_tree_batched": (S, [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
                                        ctypes.POINTER(FMMParams), ctypes.POINTER(ctypes.c_int), _VP, _PP]),
         "fmm_eval": (S, [_VP, _VP, _VP, _VP]),
+        "fmm_build_tree_targets": (S, [_VP, ctypes.c_int64, _VP, ctypes.c_int64, ctypes.POINTER(FMMParams), _VP,
+                                       _PP]),
+        "fmm_tree_rebuild_targets": (S, [_VP, _VP, _VP, ctypes.POINTER(FMMParams), _VP]),
+        "fmm_eval_targets": (S, [_VP, _VP, _VP, _VP]),
         "fmm_eval_batched": (S, [_VP, _VP, _VP, _VP]),
         "fmm_eval_backward": (S, [_VP, _VP, _VP, _VP, _VP, _VP]),
         "fmm_autotune_step": (S, [_VP, ctypes.c_double, ctypes.POINTER(FMMParams)]),

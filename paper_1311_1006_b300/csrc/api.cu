@@ -177,7 +177,7 @@ static void release(Tree* t) {
                     t->d_rad32, t->d_soff, t->d_ns, t->d_sidx, t->d_srng, t->d_sowner, t->d_ltstat,
                     t->d_lvl_base, t->d_woff, t->d_nw, t->d_widx, t->d_p2p_items,
                     t->d_m2l_items, t->d_leaf_items, t->d_box_m2l, t->d_status, t->d_gam, t->d_near, t->d_M64,
-                    t->d_pslot, t->d_posp, t->d_slot_of, t->d_gamp,
+                    t->d_pslot, t->d_posp, t->d_slot_of, t->d_gamp, t->d_xy_all, t->d_gam_all, t->d_phi_all,
                     t->d_M32, t->d_Lm2l, t->d_L64, t->d_L32, t->d_p2p_part, t->d_m2l_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -297,6 +297,91 @@ fmm_status fmm_build_tree_batched(const double* d_xy, const int64_t* h_offsets, 
     if (!h_offsets || B < 1) return invalid("offsets NULL or B < 1");
     std::vector<int64_t> offs(h_offsets, h_offsets + B + 1);
     return build_common(d_xy, offs, prm, h_nlevels, true, stream, out);
+}
+
+// ---- separate evaluation points (eq 2.2) ----------------------------------
+// The tree is built over the sources followed by the evaluation points, which
+// carry zero strength: a zero-strength point changes no expansion and no near
+// sum, and the coincidence rule z_j != z_i of the P2P pass is eq (2.2)'s
+// x_j != y_i.  The evaluation gathers the potentials of the evaluation points.
+
+static fmm_status concat_points(Tree& t, const double* d_src, const double* d_tgt, cudaStream_t s) {
+    FMM_CUDA(cudaMemcpyAsync(t.d_xy_all, d_src, (size_t)t.n_src * 2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    FMM_CUDA(cudaMemcpyAsync(t.d_xy_all + 2 * t.n_src, d_tgt, (size_t)t.n_tgt * 2 * sizeof(double),
+                             cudaMemcpyDeviceToDevice, s));
+    return FMM_OK;
+}
+
+fmm_status fmm_build_tree_targets(const double* d_src_xy, int64_t n_src, const double* d_tgt_xy, int64_t n_tgt,
+                                  const fmm_params* prm, void* stream, fmm_tree** out) {
+    if (!d_src_xy || !d_tgt_xy || !out) return invalid("NULL argument");
+    if (n_src < 1 || n_tgt < 1) return invalid("n_src and n_tgt must be >= 1");
+    const int64_t n = n_src + n_tgt;
+    double* buf = nullptr;
+    cudaError_t e = cudaMalloc((void**)&buf, (size_t)n * 2 * sizeof(double));
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        set_error("device allocation failed (points)");
+        return FMM_ERR_OOM;
+    }
+    FMM_CUDA(e);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    e = cudaMemcpyAsync(buf, d_src_xy, (size_t)n_src * 2 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(buf + 2 * n_src, d_tgt_xy, (size_t)n_tgt * 2 * sizeof(double), cudaMemcpyDeviceToDevice,
+                            s);
+    if (e != cudaSuccess) {
+        cudaFree(buf);
+        return cuda_fail(e, "cudaMemcpyAsync(points)");
+    }
+    std::vector<int64_t> offs = {0, n};
+    const fmm_status st = build_common(buf, offs, prm, nullptr, false, stream, out);
+    if (st) {
+        cudaFree(buf);
+        return st;
+    }
+    Tree& t = (*out)->t;
+    t.d_xy_all = buf;
+    t.n_src = n_src;
+    t.n_tgt = n_tgt;
+    return FMM_OK;
+}
+
+fmm_status fmm_tree_rebuild_targets(fmm_tree* h, const double* d_src_xy, const double* d_tgt_xy,
+                                    const fmm_params* prm, void* stream) {
+    if (!h || !d_src_xy || !d_tgt_xy) return invalid("NULL argument");
+    Tree& t = h->t;
+    if (t.n_src == 0) return invalid("not a tree with separate evaluation points (fmm_build_tree_targets)");
+    fmm_status st;
+    if ((st = concat_points(t, d_src_xy, d_tgt_xy, static_cast<cudaStream_t>(stream)))) return st;
+    return fmm_tree_rebuild(h, t.d_xy_all, prm, stream);
+}
+
+static fmm_status eval_common(fmm_tree* h, const double* d_gamma, void* d_phi, void* stream);
+
+fmm_status fmm_eval_targets(fmm_tree* h, const double* d_gamma, void* d_phi, void* stream) {
+    if (!h || !d_gamma || !d_phi) return invalid("NULL argument");
+    Tree& t = h->t;
+    if (t.n_src == 0) return invalid("not a tree with separate evaluation points (fmm_build_tree_targets)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t cs = t.path == FMM_PATH_FP32 ? 8 : 16;
+    if (!t.d_gam_all) {
+        FMM_CUDA(cudaMalloc((void**)&t.d_gam_all, (size_t)t.n * 2 * sizeof(double)));
+        FMM_CUDA(cudaMemset(t.d_gam_all, 0, (size_t)t.n * 2 * sizeof(double)));  // evaluation points: strength 0
+    }
+    if (t.phi_all_path != t.path) {
+        if (t.d_phi_all) cudaFree(t.d_phi_all);
+        t.d_phi_all = nullptr;
+        FMM_CUDA(cudaMalloc(&t.d_phi_all, (size_t)t.n * cs));
+        t.phi_all_path = t.path;
+    }
+    FMM_CUDA(cudaMemcpyAsync(t.d_gam_all, d_gamma, (size_t)t.n_src * 2 * sizeof(double), cudaMemcpyDeviceToDevice,
+                             s));
+    fmm_status st = eval_common(h, t.d_gam_all, t.d_phi_all, stream);
+    if (st) return st;
+    FMM_CUDA(cudaMemcpyAsync(d_phi, static_cast<char*>(t.d_phi_all) + (size_t)t.n_src * cs, (size_t)t.n_tgt * cs,
+                             cudaMemcpyDeviceToDevice, s));
+    return FMM_OK;
 }
 
 fmm_status fmm_tree_rebuild(fmm_tree* h, const double* d_xy, const fmm_params* prm, void* stream) {

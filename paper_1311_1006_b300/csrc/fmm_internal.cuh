@@ -85,6 +85,14 @@ struct LevelList {
 
 // --------------------------------------------------------------- the tree
 struct Tree {
+    // separate evaluation points (eq 2.2): the tree holds n_src sources followed by n_tgt
+    // evaluation points of zero strength (n_src == 0: sources are the evaluation points)
+    int64_t n_src = 0, n_tgt = 0;
+    double* d_xy_all = nullptr;   // sources then evaluation points
+    double* d_gam_all = nullptr;  // source strengths then zeros
+    void* d_phi_all = nullptr;    // potentials of all points (path precision)
+    int phi_all_path = -1;
+
     // parameters
     int p = 17, P = 17, PS = 18, path = FMM_PATH_FP32, flags = 0;
     double theta = 0.5;

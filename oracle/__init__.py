@@ -48,6 +48,9 @@ def _load():
         lib.fo_direct.argtypes = [_I64, _P, _P, _I64, _P, _P, _P]
         lib.fo_direct_grad.argtypes = [_I64, _P, _P, _P, _I64, _P, _P, _P]
         lib.fo_direct_points.argtypes = [_I64, _P, _P, _I64, _P, _P]
+        lib.fo_direct_log.argtypes = [_I64, _P, _P, _I64, _P, _P]
+        lib.fo_fmm_log.restype = ctypes.c_int
+        lib.fo_fmm_log.argtypes = [_I64, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int, _P]
         lib.fo_build_tree.restype = ctypes.c_int
         lib.fo_build_tree.argtypes = [_I64, _P, ctypes.c_int, _P, _P, _P, _P, _P]
         lib.fo_build_lists.restype = ctypes.c_int
@@ -115,6 +118,33 @@ def direct_points(src_xy, gamma, tgt_xy):
     gamma = _cx(gamma, n)
     phi = np.zeros(m, np.complex128)
     lib.fo_direct_points(n, _ptr(sxy), _ptr(gamma), m, _ptr(txy), _ptr(phi))
+    return phi
+
+
+def direct_log(xy, gamma, targets=None):
+    """Exact logarithmic potential sum_{j: z_j != z_t} Gamma_j ln|z_t - z_j| at ``targets``."""
+    lib = _load()
+    xy = _xy(xy)
+    n = xy.shape[0]
+    gamma = _cx(gamma, n)
+    tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    m = n if tg is None else tg.shape[0]
+    phi = np.zeros(m, np.complex128)
+    lib.fo_direct_log(n, _ptr(xy), _ptr(gamma), m, _ptr(tg), _ptr(phi))
+    return phi
+
+
+def fmm_log(xy, gamma, nlevels: int, theta: float, p: int):
+    """One oracle FMM evaluation of the logarithmic potential (complex strengths
+    on the real kernel ln|z - z_j|)."""
+    lib = _load()
+    xy = _xy(xy)
+    n = xy.shape[0]
+    gamma = _cx(gamma, n)
+    phi = np.zeros(n, np.complex128)
+    rc = lib.fo_fmm_log(n, _ptr(xy), _ptr(gamma), int(nlevels), float(theta), int(p), _ptr(phi))
+    if rc != 0:
+        raise ValueError(f"oracle fmm_log failed ({rc})")
     return phi
 
 

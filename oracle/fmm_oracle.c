@@ -572,3 +572,193 @@ done:
     free(c); free(psi); free(dpsi); free(phi); free(dphi);
     return rc;
 }
+
+/* ======================================================= logarithmic kernel
+ *
+ * The logarithmic potential (Sec. 3.3, used for isopotential plots; its
+ * multipole form a_0 log(z - z_0) + sum_j a_j / (z - z_0)^j is the one the paper
+ * writes down):
+ *     Phi(z_i) = sum_{j: z_j != z_i} Gamma_j ln|z_i - z_j|.
+ * Complex strengths act on the real kernel ln|.|, i.e. the real and imaginary
+ * parts of Gamma are two real-strength potentials.  For real strengths q,
+ * F(z) = sum_j q_j log(z - z_j) has Re F = the potential; the imaginary part of
+ * log is branch-dependent and is never used.  Textbook series of the complex
+ * log, written out from their definitions:
+ *   multipole about c:  F(z) ~ a_0 log(z - c) + sum_{k=1}^{p-1} a_k / (z-c)^k,
+ *                       a_0 = sum q_j,  a_k = -sum q_j (z_j - c)^k / k
+ *   local about c:      F(z) ~ sum_{l=0}^{p} b_l (z - c)^l
+ *   M2M (z0 = c_child - c_parent):
+ *       b_0 = a_0,  b_l = -a_0 z0^l / l + sum_{k=1}^{l} a_k z0^(l-k) C(l-1, k-1)
+ *   M2L (z0 = c_M - c_L):
+ *       b_0 += a_0 log(-z0) + sum_{k>=1} a_k (-1)^k / z0^k
+ *       b_l += -a_0 / (l z0^l) + z0^(-l) sum_{k>=1} (a_k / z0^k) C(l+k-1, k-1) (-1)^k
+ *   L2L, L2P: Taylor shift and evaluation of the degree-p local polynomial
+ *   (fo_l2l / fo_l2p with p+1 coefficients).
+ * Truncation: p multipole coefficients (log term + k = 1..p-1) and locals of
+ * degree p, so that d/dz of the expansions is the harmonic expansion of p
+ * terms used by the rest of this file.                                      */
+
+/* Exact sum at tgt[0..m) (all n points when tgt == NULL). */
+void fo_direct_log(int64_t n, const double* xy, const double* gam, int64_t m, const int64_t* tgt, double* phi) {
+    if (tgt == NULL) m = n;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t q = 0; q < m; ++q) {
+        int64_t t = tgt ? tgt[q] : q;
+        cplx zt = xy[2 * t] + I * xy[2 * t + 1];
+        cplx s = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            cplx zj = xy[2 * j] + I * xy[2 * j + 1];
+            if (zj == zt) continue; /* R7 */
+            s += load_c(gam, j) * log(cabs(zt - zj));
+        }
+        store_c(phi, q, s);
+    }
+}
+
+static void p2m_log(int nlevels, int p, const double* xy, const double* q, const int64_t* perm,
+                    const int64_t* bstart, const int64_t* bcount, const double* center, double* mpole) {
+    int64_t l0 = level_offset(nlevels - 1), nb = fo_num_boxes(nlevels) - l0;
+#pragma omp parallel for schedule(static)
+    for (int64_t b = 0; b < nb; ++b) {
+        int64_t g = l0 + b;
+        cplx c = center[2 * g] + I * center[2 * g + 1];
+        cplx a[64] = {0};
+        for (int64_t i = bstart[g]; i < bstart[g] + bcount[g]; ++i) {
+            int64_t j = perm[i];
+            cplx w = (xy[2 * j] + I * xy[2 * j + 1]) - c;
+            a[0] += q[j];
+            cplx wk = 1;
+            for (int k = 1; k < p; ++k) {
+                wk *= w;
+                a[k] -= q[j] * wk / (double)k;
+            }
+        }
+        for (int k = 0; k < p; ++k) store_c(mpole, g * p + k, a[k]);
+    }
+}
+
+static void m2m_log(int nlevels, int p, const double* center, double* mpole) {
+    for (int l = nlevels - 2; l >= 0; --l) {
+        int64_t off = level_offset(l), nb = fo_num_boxes(l + 1) - off;
+#pragma omp parallel for schedule(static)
+        for (int64_t b = 0; b < nb; ++b) {
+            int64_t g = off + b;
+            cplx cp = center[2 * g] + I * center[2 * g + 1];
+            cplx out[64] = {0};
+            for (int c = 0; c < 4; ++c) {
+                int64_t h = level_offset(l + 1) + 4 * b + c;
+                cplx z0 = (center[2 * h] + I * center[2 * h + 1]) - cp;
+                cplx a0 = load_c(mpole, h * p);
+                out[0] += a0;
+                for (int n = 1; n < p; ++n) {
+                    cplx acc = -a0 * cpow_int(z0, n) / (double)n;
+                    for (int k = 1; k <= n; ++k) acc += load_c(mpole, h * p + k) * cpow_int(z0, n - k) * binom(n - 1, k - 1);
+                    out[n] += acc;
+                }
+            }
+            for (int n = 0; n < p; ++n) store_c(mpole, g * p + n, out[n]);
+        }
+    }
+}
+
+/* local has p+1 coefficients per box */
+static void m2l_log(int nlevels, int p, const double* center, const int64_t* w_off, const int32_t* w_idx,
+                    const double* mpole, double* local) {
+    int64_t nbox = fo_num_boxes(nlevels);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t g = 0; g < nbox; ++g) {
+        cplx cl = center[2 * g] + I * center[2 * g + 1];
+        cplx b[65] = {0};
+        for (int64_t qq = w_off[g]; qq < w_off[g + 1]; ++qq) {
+            int64_t h = w_idx[qq];
+            cplx z0 = (center[2 * h] + I * center[2 * h + 1]) - cl;
+            cplx a0 = load_c(mpole, h * p);
+            cplx zi[130]; /* zi[m] = z0^(-m) */
+            zi[0] = 1;
+            for (int m = 1; m <= 2 * p; ++m) zi[m] = zi[m - 1] / z0;
+            cplx b0 = a0 * clog(-z0);
+            for (int k = 1; k < p; ++k) b0 += load_c(mpole, h * p + k) * ((k & 1) ? -zi[k] : zi[k]);
+            b[0] += b0;
+            for (int l = 1; l <= p; ++l) {
+                cplx acc = 0;
+                for (int k = 1; k < p; ++k) {
+                    cplx t = load_c(mpole, h * p + k) * zi[k] * binom(l + k - 1, k - 1);
+                    acc += (k & 1) ? -t : t;
+                }
+                b[l] += -a0 * zi[l] / (double)l + zi[l] * acc;
+            }
+        }
+        for (int l = 0; l <= p; ++l) store_c(local, g * (p + 1) + l, b[l]);
+    }
+}
+
+static void p2p_log(int nlevels, const double* xy, const double* q, const int64_t* perm, const int64_t* bstart,
+                    const int64_t* bcount, const int64_t* s_off, const int32_t* s_idx, double* out) {
+    int64_t l0 = level_offset(nlevels - 1), nb = fo_num_boxes(nlevels) - l0;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t b = 0; b < nb; ++b) {
+        int64_t g = l0 + b;
+        for (int64_t i = bstart[g]; i < bstart[g] + bcount[g]; ++i) {
+            int64_t t = perm[i];
+            cplx zt = xy[2 * t] + I * xy[2 * t + 1];
+            double s = 0;
+            for (int64_t qq = s_off[g]; qq < s_off[g + 1]; ++qq) {
+                int64_t h = s_idx[qq];
+                for (int64_t u = bstart[h]; u < bstart[h] + bcount[h]; ++u) {
+                    int64_t j = perm[u];
+                    cplx zj = xy[2 * j] + I * xy[2 * j + 1];
+                    if (zj == zt) continue; /* R7 */
+                    s += q[j] * log(cabs(zt - zj));
+                }
+            }
+            out[t] = s;
+        }
+    }
+}
+
+/* One logarithmic-kernel FMM evaluation (complex strengths as two real ones). */
+int fo_fmm_log(int64_t n, const double* xy, const double* gam, int nlevels, double theta, int p, double* phi) {
+    if (n < 1 || nlevels < 1 || p < 1 || p > 64 || !(theta > 0.0 && theta < 1.0)) return -1;
+    int64_t nbox = fo_num_boxes(nlevels);
+    int64_t* perm = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t* bstart = (int64_t*)malloc(sizeof(int64_t) * (size_t)nbox);
+    int64_t* bcount = (int64_t*)malloc(sizeof(int64_t) * (size_t)nbox);
+    double* center = (double*)malloc(sizeof(double) * 2 * (size_t)nbox);
+    double* radius = (double*)malloc(sizeof(double) * (size_t)nbox);
+    int64_t* s_off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nbox + 1));
+    int64_t* w_off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nbox + 1));
+    double* mpole = (double*)calloc((size_t)(2 * nbox * p), sizeof(double));
+    double* local = (double*)calloc((size_t)(2 * nbox * (p + 1)), sizeof(double));
+    double* q = (double*)malloc(sizeof(double) * (size_t)n);
+    double* nearv = (double*)malloc(sizeof(double) * (size_t)n);
+    double* farv = (double*)malloc(sizeof(double) * 2 * (size_t)n);
+    int32_t* s_idx = NULL;
+    int32_t* w_idx = NULL;
+    int rc = -2;
+    if (!perm || !bstart || !bcount || !center || !radius || !s_off || !w_off || !mpole || !local || !q || !nearv ||
+        !farv)
+        goto done;
+    rc = fo_build_tree(n, xy, nlevels, perm, bstart, bcount, center, radius);
+    if (rc) goto done;
+    rc = fo_build_lists(nlevels, center, radius, theta, s_off, w_off, NULL, NULL);
+    if (rc) goto done;
+    s_idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(s_off[nbox] + 1));
+    w_idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(w_off[nbox] + 1));
+    if (!s_idx || !w_idx) { rc = -2; goto done; }
+    fo_build_lists(nlevels, center, radius, theta, s_off, w_off, s_idx, w_idx);
+    for (int part = 0; part < 2; ++part) {  /* real, then imaginary part of the strengths */
+        for (int64_t j = 0; j < n; ++j) q[j] = gam[2 * j + part];
+        p2m_log(nlevels, p, xy, q, perm, bstart, bcount, center, mpole);
+        m2m_log(nlevels, p, center, mpole);
+        m2l_log(nlevels, p, center, w_off, w_idx, mpole, local);
+        fo_l2l(nlevels, p + 1, center, local);
+        fo_l2p(nlevels, p + 1, xy, perm, bstart, bcount, center, local, farv, NULL);
+        p2p_log(nlevels, xy, q, perm, bstart, bcount, s_off, s_idx, nearv);
+        for (int64_t j = 0; j < n; ++j) phi[2 * j + part] = farv[2 * j] + nearv[j];
+    }
+    rc = 0;
+done:
+    free(perm); free(bstart); free(bcount); free(center); free(radius); free(s_off); free(w_off);
+    free(mpole); free(local); free(q); free(nearv); free(farv); free(s_idx); free(w_idx);
+    return rc;
+}

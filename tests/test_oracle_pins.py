@@ -410,3 +410,51 @@ def test_direct_points_equals_direct_on_the_sources():
     a = oracle.direct_points(xy, gam, xy)
     b = oracle.direct(xy, gam)
     assert np.max(np.abs(a - b)) <= 1e-14 * np.max(np.abs(b))
+
+
+# ---------------------------------------------------------------- logarithmic kernel
+
+def test_direct_log_closed_form():
+    import oracle
+
+    xy = np.array([[0.0, 0.0], [3.0, 4.0], [0.0, 1.0]])
+    gam = np.array([1.0 + 2.0j, -0.5, 2.0j])
+    got = oracle.direct_log(xy, gam)
+    want0 = -0.5 * np.log(5.0) + 2.0j * np.log(1.0)
+    want1 = (1.0 + 2.0j) * np.log(5.0) + 2.0j * np.log(np.hypot(3.0, 3.0))
+    want2 = (1.0 + 2.0j) * np.log(1.0) - 0.5 * np.log(np.hypot(3.0, 3.0))
+    assert np.allclose(got, [want0, want1, want2], rtol=0, atol=1e-15)
+
+
+def test_direct_log_gradient_is_the_harmonic_field():
+    """d/dx sum_j q_j ln|y - x_j| = Re sum_j q_j / (y - x_j) and d/dy = -Im of it
+    (real q): central differences of the log sum against the harmonic direct sum."""
+    import oracle
+
+    g = np.random.default_rng(31)
+    src = g.random((200, 2))
+    q = g.standard_normal(200).astype(np.complex128)
+    y = np.array([0.37, 0.61])
+    h = 1e-6
+
+    def pot(pt):
+        xy = np.vstack([src, pt[None, :]])
+        return oracle.direct_log(xy, np.concatenate([q, [0.0]]), targets=[200])[0].real
+
+    dx = (pot(y + [h, 0]) - pot(y - [h, 0])) / (2 * h)
+    dy = (pot(y + [0, h]) - pot(y - [0, h])) / (2 * h)
+    hm = oracle.direct_points(src, q, y[None, :])[0]
+    assert abs(dx - hm.real) <= 1e-6 * abs(hm) and abs(dy + hm.imag) <= 1e-6 * abs(hm)
+
+
+def test_fmm_log_converges_geometrically_and_one_level_is_direct():
+    import oracle
+
+    g = np.random.default_rng(32)
+    xy = g.random((3000, 2))
+    gam = g.standard_normal(3000) + 1j * g.standard_normal(3000)
+    ex = oracle.direct_log(xy, gam)
+    errs = [np.max(np.abs(oracle.fmm_log(xy, gam, 5, 0.5, p) - ex)) / np.max(np.abs(ex)) for p in (6, 10, 14, 18)]
+    assert all(b < 0.2 * a for a, b in zip(errs, errs[1:])), errs  # geometric in p (theta = 0.5)
+    assert errs[-1] < 1e-8
+    assert np.max(np.abs(oracle.fmm_log(xy, gam, 1, 0.5, 6) - ex)) <= 1e-13 * np.max(np.abs(ex))

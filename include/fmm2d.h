@@ -115,6 +115,23 @@ fmm_status fmm_eval(fmm_tree* t, const double* d_gamma, void* d_phi, void* strea
 /* Same as fmm_eval; rejects a tree that was not built by fmm_build_tree_batched. */
 fmm_status fmm_eval_batched(fmm_tree* t, const double* d_gamma, void* d_phi, void* stream);
 
+/* Logarithmic potential (Sec. 3.3 of the paper, the kernel it uses for
+ * isopotential plots):
+ *     Phi_i = sum_{j: z_j != z_i} Gamma_j ln|z_i - z_j|,
+ * complex strengths acting on the real kernel (the real and imaginary parts of
+ * Gamma give the real and imaginary parts of Phi).  Same tree, lists, expansion
+ * order and precision path as fmm_eval; the log multipole is the integral of
+ * the harmonic one (a_0 log(z - c) + sum_{k>=1} a_k/(z - c)^k, locals of degree
+ * p), so the far field runs the harmonic passes twice (one real-strength set
+ * per part of Gamma) plus the constant term of each local expansion, and P2P
+ * takes one logarithm per pair.  Arguments as fmm_eval (d_gamma: n complex128,
+ * caller's order; d_phi: n complex64 on the FP32 path, complex128 on FP64).
+ * fmm_eval_targets_log is the same at the evaluation points of a tree built
+ * by fmm_build_tree_targets (as fmm_eval_targets).  Errors: INVALID_ARG, CUDA,
+ * OOM. */
+fmm_status fmm_eval_log(fmm_tree* t, const double* d_gamma, void* d_phi, void* stream);
+fmm_status fmm_eval_targets_log(fmm_tree* t, const double* d_gamma, void* d_phi, void* stream);
+
 /* Adjoint of fmm_eval with the tree frozen.  For the real loss
  *     L = sum_i w_i Re Phi_i + v_i Im Phi_i,    d_gphi[i] = w_i + i v_i (complex128),
  * writes (torch convention: d/dRe + i d/dIm)

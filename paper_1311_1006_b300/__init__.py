@@ -168,15 +168,32 @@ class Tree:
         _lib.check(fn(self._h, g, o, _stream(stream)))
         return out
 
-    def eval_targets(self, gamma, out=None, stream=None):
-        """fmm_eval_targets: gamma = (N_src,) complex128 source strengths; returns Phi at the evaluation points."""
+    def eval_log(self, gamma, out=None, stream=None):
+        """fmm_eval_log: the logarithmic potential sum_j Gamma_j ln|z_i - z_j| (Sec. 3.3)."""
+        torch = _torch()
+        g = _dev(gamma, torch.complex128, (self.n,), "gamma")
+        if out is None:
+            out = torch.empty(self.n, dtype=self.out_dtype, device=gamma.device)
+        o = _dev(out, self.out_dtype, (self.n,), "out")
+        _lib.check(_lib.load().fmm_eval_log(self._h, g, o, _stream(stream)))
+        return out
+
+    def _eval_targets(self, fn, gamma, out, stream):
         torch = _torch()
         g = _dev(gamma, torch.complex128, (self.n_src,), "gamma")
         if out is None:
             out = torch.empty(self.n_tgt, dtype=self.out_dtype, device=gamma.device)
         o = _dev(out, self.out_dtype, (self.n_tgt,), "out")
-        _lib.check(_lib.load().fmm_eval_targets(self._h, g, o, _stream(stream)))
+        _lib.check(fn(self._h, g, o, _stream(stream)))
         return out
+
+    def eval_targets(self, gamma, out=None, stream=None):
+        """fmm_eval_targets: gamma = (N_src,) complex128 source strengths; returns Phi at the evaluation points."""
+        return self._eval_targets(_lib.load().fmm_eval_targets, gamma, out, stream)
+
+    def eval_targets_log(self, gamma, out=None, stream=None):
+        """fmm_eval_targets_log: the logarithmic potential at the evaluation points."""
+        return self._eval_targets(_lib.load().fmm_eval_targets_log, gamma, out, stream)
 
     def backward(self, gamma, gphi, stream=None):
         """fmm_eval_backward: returns (dL/dGamma complex128, dL/d(x,y) float64 (N,2))."""

@@ -77,6 +77,8 @@ def load() -> ctypes.CDLL:
         "fmm_tree_rebuild_targets": (S, [_VP, _VP, _VP, ctypes.POINTER(FMMParams), _VP]),
         "fmm_eval_targets": (S, [_VP, _VP, _VP, _VP]),
         "fmm_eval_batched": (S, [_VP, _VP, _VP, _VP]),
+        "fmm_eval_log": (S, [_VP, _VP, _VP, _VP]),
+        "fmm_eval_targets_log": (S, [_VP, _VP, _VP, _VP]),
         "fmm_eval_backward": (S, [_VP, _VP, _VP, _VP, _VP, _VP]),
         "fmm_autotune_step": (S, [_VP, ctypes.c_double, ctypes.POINTER(FMMParams)]),
         "fmm_autotune_config": (S, [_VP, ctypes.c_double, ctypes.c_int, ctypes.c_int]),

@@ -72,7 +72,7 @@ static void invalidate_graph(Tree& t) {
 static void apply_params(Tree& t, const fmm_params* prm) {
     t.p = prm->p;
     t.P = compiled_order(prm->p);
-    t.PS = (t.P + 1) & ~1;
+    t.PS = (t.P + 2) & ~1;  // >= P+1: slot P holds the constant term of the logarithmic kernel
     t.theta = prm->theta;
     t.path = prm->path;
     t.flags = prm->flags;
@@ -359,7 +359,8 @@ fmm_status fmm_tree_rebuild_targets(fmm_tree* h, const double* d_src_xy, const d
 
 static fmm_status eval_common(fmm_tree* h, const double* d_gamma, void* d_phi, void* stream);
 
-fmm_status fmm_eval_targets(fmm_tree* h, const double* d_gamma, void* d_phi, void* stream) {
+static fmm_status eval_targets_common(fmm_tree* h, const double* d_gamma, void* d_phi, void* stream,
+                                      bool log_kernel) {
     if (!h || !d_gamma || !d_phi) return invalid("NULL argument");
     Tree& t = h->t;
     if (t.n_src == 0) return invalid("not a tree with separate evaluation points (fmm_build_tree_targets)");
@@ -377,11 +378,20 @@ fmm_status fmm_eval_targets(fmm_tree* h, const double* d_gamma, void* d_phi, voi
     }
     FMM_CUDA(cudaMemcpyAsync(t.d_gam_all, d_gamma, (size_t)t.n_src * 2 * sizeof(double), cudaMemcpyDeviceToDevice,
                              s));
-    fmm_status st = eval_common(h, t.d_gam_all, t.d_phi_all, stream);
+    fmm_status st = log_kernel ? fmm_eval_log(h, t.d_gam_all, t.d_phi_all, stream)
+                               : eval_common(h, t.d_gam_all, t.d_phi_all, stream);
     if (st) return st;
     FMM_CUDA(cudaMemcpyAsync(d_phi, static_cast<char*>(t.d_phi_all) + (size_t)t.n_src * cs, (size_t)t.n_tgt * cs,
                              cudaMemcpyDeviceToDevice, s));
     return FMM_OK;
+}
+
+fmm_status fmm_eval_targets(fmm_tree* h, const double* d_gamma, void* d_phi, void* stream) {
+    return eval_targets_common(h, d_gamma, d_phi, stream, false);
+}
+
+fmm_status fmm_eval_targets_log(fmm_tree* h, const double* d_gamma, void* d_phi, void* stream) {
+    return eval_targets_common(h, d_gamma, d_phi, stream, true);
 }
 
 fmm_status fmm_tree_rebuild(fmm_tree* h, const double* d_xy, const fmm_params* prm, void* stream) {
@@ -444,14 +454,23 @@ static void set_node_priorities(const Tree& t, cudaGraph_t g) {
     cudaGetLastError();
 }
 
+// Evaluation workspace of `sets` strength sets; a reallocation invalidates the
+// captured graph, whose nodes hold the old buffer addresses.
+static fmm_status ensure_eval(Tree& t, int sets) {
+    const unsigned gen = t.eval_gen;
+    const fmm_status st = alloc_eval(t, sets);
+    if (st || t.eval_gen != gen) invalidate_graph(t);
+    if (!st && refresh_grids(t)) invalidate_graph(t);
+    return st;
+}
+
 static fmm_status eval_common(fmm_tree* h, const double* d_gamma, void* d_phi, void* stream) {
     if (!h || !d_gamma || !d_phi) return invalid("NULL argument");
     Tree& t = h->t;
     fmm_status st;
     if ((st = check_pending())) return st;
     if (t.eval_nbox == 0) invalidate_graph(t);
-    if ((st = alloc_eval(t, 1))) return st;
-    if (refresh_grids(t)) invalidate_graph(t);
+    if ((st = ensure_eval(t, 1))) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool use_graph =
         (t.flags & FMM_FLAG_GRAPH) && !(t.flags & (FMM_FLAG_NO_GRAPH | FMM_FLAG_TIMING)) && s != nullptr;
@@ -482,6 +501,15 @@ fmm_status fmm_eval(fmm_tree* h, const double* d_gamma, void* d_phi, void* strea
     return eval_common(h, d_gamma, d_phi, stream);
 }
 
+fmm_status fmm_eval_log(fmm_tree* h, const double* d_gamma, void* d_phi, void* stream) {
+    if (!h || !d_gamma || !d_phi) return invalid("NULL argument");
+    Tree& t = h->t;
+    fmm_status st;
+    if ((st = check_pending())) return st;
+    if ((st = ensure_eval(t, 2))) return st;
+    return run_eval_log(t, d_gamma, d_phi, static_cast<cudaStream_t>(stream));
+}
+
 fmm_status fmm_eval_batched(fmm_tree* h, const double* d_gamma, void* d_phi, void* stream) {
     if (h && !h->t.batched) return invalid("tree was not built by fmm_build_tree_batched");
     return eval_common(h, d_gamma, d_phi, stream);
@@ -494,8 +522,7 @@ fmm_status fmm_eval_backward(fmm_tree* h, const double* d_gamma, const double* d
     Tree& t = h->t;
     fmm_status st;
     if ((st = check_pending())) return st;
-    if ((st = alloc_eval(t, 2))) return st;
-    if (refresh_grids(t)) invalidate_graph(t);
+    if ((st = ensure_eval(t, 2))) return st;
     return run_backward(t, d_gamma, d_gphi, d_ggamma, d_gxy, static_cast<cudaStream_t>(stream));
 }
 

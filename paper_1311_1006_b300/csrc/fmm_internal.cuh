@@ -198,6 +198,7 @@ struct Tree {
     size_t eval_nbox = 0, eval_n = 0;
     int eval_ts = 0;
     int eval_PS = 0, eval_path = -1, eval_sets = 0;
+    unsigned eval_gen = 0;  // bumped whenever alloc_eval reallocates (captured graphs hold the old pointers)
 
     // streams / events
     cudaStream_t s_aux = nullptr;  // P2P (lowest priority)
@@ -262,6 +263,7 @@ fmm_status run_lists(Tree& t, cudaStream_t s);                           // stro
 fmm_status run_count(Tree& t, cudaStream_t s, unsigned long long out[2]);
 fmm_status alloc_eval(Tree& t, int sets);
 fmm_status run_eval(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s);
+fmm_status run_eval_log(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s);  // needs alloc_eval(t, 2)
 fmm_status run_backward(Tree& t, const double* d_gamma, const double* d_gphi, double* d_ggamma, double* d_gxy,
                         cudaStream_t s);
 
@@ -281,12 +283,12 @@ Bufs bufs(Tree& t, int set);
 bool refresh_grids(Tree& t);  // true when the P2P / M2L grids changed (the graph must be re-captured)
 long long p2p_grid_items(const Tree& t);
 long long m2l_grid_items(const Tree& t);
-void dispatch_far(Tree& t, const Bufs& B, cudaStream_t s);  // P2M, M2M, M2L, L2L of one strength set
+void dispatch_far(Tree& t, const Bufs& B, cudaStream_t s, bool log_kernel = false);  // P2M, M2M, M2L, L2L of one strength set
 
 // FP32-path M2L on the tensor cores (m2l_tc.cu); FMM_M2L_TC=0 selects the CUDA-core kernel.
 bool m2l_tc_enabled();
 fmm_status m2l_tc_prepare(int P);  // once per compiled order, before launches (and graph capture)
-void launch_m2l_tc(const Tree& t, const float2* M32, float2* Lm2l, float2* part, cudaStream_t s);
+void launch_m2l_tc(const Tree& t, const float2* M32, float2* Lm2l, float2* part, bool log_kernel, cudaStream_t s);
 
 // Autotuner (host).
 int default_nlevels(int64_t n, int p, int path);

@@ -27,6 +27,10 @@
 // column of B are applied on the CUDA cores with the coefficients as
 // immediates, which keeps the operands small enough for three CTAs per SM.
 //
+// Logarithmic kernel (LOG): the same contraction, plus the constant term of
+// the log local, b0 += Re(at_0) ln|c_L - c_M| - sum_{k>=1} Re(v_k)/k, summed on
+// the CUDA cores from the v_k each thread forms anyway and written to slot P.
+//
 // Precision: 3xTF32.  v = v_hi + v_lo and B = B_hi + B_lo with TF32 parts, and
 // w = v_lo B_hi + v_hi B_lo + v_hi B_hi accumulated in FP32 (the v_lo B_lo term
 // is below FP32 rounding): about 2^-21 relative per product.
@@ -237,7 +241,7 @@ __device__ __forceinline__ void ltail_all(const float2 (&v)[P], float2 (&wt)[NW]
     ((wt[T] = ltail_col<P, NT + T>(v, std::make_integer_sequence<int, P>{})), ...);
 }
 
-template <int P>
+template <int P, bool LOG>
 __global__ void __launch_bounds__(kTcThreads, P <= 18 ? 3 : 2)
     k_m2l_tc(const int4* __restrict__ items, const unsigned long long* __restrict__ nitems,
              const int32_t* __restrict__ woff, const int32_t* __restrict__ widx, const float4* __restrict__ chl,
@@ -305,6 +309,7 @@ __global__ void __launch_bounds__(kTcThreads, P <= 18 ? 3 : 2)
     float2 acc[P];
 #pragma unroll
     for (int l = 0; l < P; ++l) acc[l] = make_float2(0.f, 0.f);
+    float b0 = 0.f;  // log kernel: constant term
 
     // inputs of the next pair (loaded one step ahead) and the index after it
     float4 ncs = make_float4(1.f, 1.f, 0.f, 0.f), naa[NA];
@@ -334,7 +339,8 @@ __global__ void __launch_bounds__(kTcThreads, P <= 18 ? 3 : 2)
             // throwaway values: an MMA row depends only on its own A row)
             const float dx = (ct.x - ncs.x) + (ct.z - ncs.z);
             const float dy = (ct.y - ncs.y) + (ct.w - ncs.w);
-            const float inv = 1.0f / fmaf(dx, dx, dy * dy);
+            const float r2 = fmaf(dx, dx, dy * dy);
+            const float inv = 1.0f / r2;
             cur.u = make_float2(dx * inv, -dy * inv);  // 1/d, d = c_target - c_source
             const float2 alpha = make_float2(nrs * cur.u.x, nrs * cur.u.y);
             cur.beta = make_float2(-rt * cur.u.x, -rt * cur.u.y);
@@ -346,6 +352,14 @@ __global__ void __launch_bounds__(kTcThreads, P <= 18 ? 3 : 2)
                 const float2 a = (k & 1) ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
                 v[k] = cmul(ap, a);
                 if (k + 1 < P) ap = cmul(ap, alpha);
+            }
+            if constexpr (LOG) {
+                if (j < len) {
+                    float ls = 0.f;
+#pragma unroll
+                    for (int k = 1; k < P; ++k) ls = fmaf(-1.0f / k, v[k].x, ls);
+                    b0 += fmaf(0.5f * logf(r2), naa[0].x, ls);
+                }
             }
             if constexpr (S::KTAIL > 0) {
 #pragma unroll
@@ -466,19 +480,23 @@ __global__ void __launch_bounds__(kTcThreads, P <= 18 ? 3 : 2)
     float2* out = item.w < 0 ? Lm2l + (size_t)b * PS : part + (size_t)it * PS;
 #pragma unroll
     for (int l = 0; l < P; ++l) out[l] = acc[l];
+    if constexpr (LOG) out[P] = make_float2(b0, 0.f);
 }
 
-template <int P>
+template <int P, bool LOG>
 void launch_tc(const Tree& t, const float2* M32, float2* Lm2l, float2* part, cudaStream_t s) {
     const int grid = static_cast<int>(std::max<long long>((m2l_grid_items(t) + kTcThreads - 1) / kTcThreads, 1));
-    k_m2l_tc<P><<<grid, kTcThreads, TcShape<P>::SMEM, s>>>(
+    k_m2l_tc<P, LOG><<<grid, kTcThreads, TcShape<P>::SMEM, s>>>(
         t.d_m2l_items, reinterpret_cast<const unsigned long long*>(t.d_status) + 4, t.d_woff, t.d_widx, t.d_chl,
         t.d_rho32, M32, Lm2l, part, t.PS, t.d_status);
 }
 
 template <int P>
 cudaError_t prepare_tc() {
-    return cudaFuncSetAttribute(k_m2l_tc<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_m2l_tc<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(TcShape<P>::SMEM));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_m2l_tc<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(TcShape<P>::SMEM));
 }
 
@@ -507,10 +525,14 @@ fmm_status m2l_tc_prepare(int P) {
     return FMM_OK;
 }
 
-void launch_m2l_tc(const Tree& t, const float2* M32, float2* Lm2l, float2* part, cudaStream_t s) {
+void launch_m2l_tc(const Tree& t, const float2* M32, float2* Lm2l, float2* part, bool log_kernel,
+                   cudaStream_t s) {
     switch (t.P) {
-#define FMM_CASE(Q) \
-    case Q: launch_tc<Q>(t, M32, Lm2l, part, s); break;
+#define FMM_CASE(Q)                                            \
+    case Q:                                                    \
+        if (log_kernel) launch_tc<Q, true>(t, M32, Lm2l, part, s); \
+        else launch_tc<Q, false>(t, M32, Lm2l, part, s);           \
+        break;
         FMM_TC_ORDERS(FMM_CASE)
 #undef FMM_CASE
         default: break;

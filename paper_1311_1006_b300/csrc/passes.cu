@@ -17,6 +17,19 @@
 //
 // Precision paths: FP32 path = P2M, M2L, L2P, P2P in FP32 (FP32 accumulation),
 // M2M / L2L and the per-level local sums in FP64.  FP64 path = all FP64.
+//
+// Logarithmic kernel (Sec. 3.3), Phi(z) = sum_j q_j ln|z - z_j| for real q
+// (complex strengths = two real-strength sets, one per part): with
+// F(z) = sum_j q_j log(z - z_j), Re F = Phi and F' = the harmonic sum, so the
+// log multipole q_0 log(z-c) + sum_k a_k/(z-c)^k is the integral of the
+// harmonic one (a_k = -at_k rho^k / k) and the harmonic passes run unchanged
+// on the same coefficients.  Only the constant term of each local expansion is
+// new (slot P of the coefficient stride, real part only: the imaginary part of
+// log is branch-dependent and never reaches Re F):
+//   M2L  b0 += Re(at_0) ln|c_L - c_M| - sum_{k>=1} Re(v_k) / k,   v_k = (rho_M u)^k at_k
+//   L2L  b0' = b0 + rho_P Re( q sum_m bt_m q^m / (m+1) )           (parent's polynomial at c_child)
+//   L2P  F   = b0 + rho   Re( w sum_m bt_m w^m / (m+1) )
+// which is the textbook log-series FMM with locals of degree p, exactly.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -89,6 +102,34 @@ __global__ void k_gather64(const double2* __restrict__ in, const int32_t* __rest
     if (i >= n) return;
     const double2 g = in[perm[i]];
     out[i] = g;
+    outp[slot_of[i]] = g;
+}
+
+// Logarithmic kernel: the real and imaginary parts of the strengths become two
+// real-strength sets for the far field (sorted order, imaginary part zero);
+// the P2P slot layout keeps the complex strengths (one log per pair).
+__global__ void k_gather_log32(const double2* __restrict__ in, const int32_t* __restrict__ perm,
+                               const int32_t* __restrict__ slot_of, int n, float2* out0, float2* out1,
+                               float* outp) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double2 g = in[perm[i]];
+    const float2 v = make_float2((float)g.x, (float)g.y);
+    out0[i] = make_float2(v.x, 0.f);
+    out1[i] = make_float2(v.y, 0.f);
+    const int slot = slot_of[i];
+    float* f = outp + 4 * (slot >> 1) + (slot & 1);
+    f[0] = v.x;
+    f[2] = v.y;
+}
+__global__ void k_gather_log64(const double2* __restrict__ in, const int32_t* __restrict__ perm,
+                               const int32_t* __restrict__ slot_of, int n, double2* out0, double2* out1,
+                               double2* outp) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double2 g = in[perm[i]];
+    out0[i] = make_double2(g.x, 0.0);
+    out1[i] = make_double2(g.y, 0.0);
     outp[slot_of[i]] = g;
 }
 
@@ -249,25 +290,26 @@ __device__ __forceinline__ void m2l_row(float2 (&w)[P], const float2 v, std::int
     ((w[L].y = fmaf(Bn<K + L, L>::v, v.y, w[L].y)), ...);
 }
 
-template <int P, int K>
+template <int P, int K, bool LOG>
 __device__ __forceinline__ void m2l_step(float2 (&w)[P], const float4 (&aa)[(P + 1) / 2], float2& ap,
-                                         const float2 alpha) {
+                                         const float2 alpha, float& ls) {
     const float4 q = aa[K / 2];
     const float2 a = (K & 1) ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
     const float2 v = cmul(ap, a);
     if (K + 1 < P) ap = cmul(ap, alpha);
+    if constexpr (LOG && K >= 1) ls = fmaf(-1.0f / K, v.x, ls);  // log kernel: -sum_k Re(v_k)/k
     m2l_row<P, K>(w, v, std::make_integer_sequence<int, P>{});
 }
 
 // w_l = sum_k C(k+l, l) alpha^k a_k for l < P (a_k held in registers)
-template <int P, int... K>
+template <int P, bool LOG, int... K>
 __device__ __forceinline__ void m2l_apply(float2 (&w)[P], const float4 (&aa)[(P + 1) / 2], const float2 alpha,
-                                          std::integer_sequence<int, K...>) {
+                                          float& ls, std::integer_sequence<int, K...>) {
     float2 ap = make_float2(1.f, 0.f);
-    (m2l_step<P, K>(w, aa, ap, alpha), ...);
+    (m2l_step<P, K, LOG>(w, aa, ap, alpha, ls), ...);
 }
 
-template <int P>
+template <int P, bool LOG>
 __global__ void __launch_bounds__(128) k_m2l32(const int4* __restrict__ items,
                                                const unsigned long long* __restrict__ nitems,
                                                const int32_t* __restrict__ woff, const int32_t* __restrict__ widx,
@@ -283,6 +325,7 @@ __global__ void __launch_bounds__(128) k_m2l32(const int4* __restrict__ items,
     float2 acc[P];
 #pragma unroll
     for (int l = 0; l < P; ++l) acc[l] = make_float2(0.f, 0.f);
+    float b0 = 0.f;  // log kernel: constant term
     const int32_t* wl = widx + woff[b];
     for (int j = item.y; j < item.z; ++j) {
         const int s = wl[j];
@@ -290,7 +333,8 @@ __global__ void __launch_bounds__(128) k_m2l32(const int4* __restrict__ items,
         const float rs = rho32[s];
         const float dx = (ct.x - cs.x) + (ct.z - cs.z);
         const float dy = (ct.y - cs.y) + (ct.w - cs.w);
-        const float inv = 1.0f / fmaf(dx, dx, dy * dy);
+        const float r2 = fmaf(dx, dx, dy * dy);
+        const float inv = 1.0f / r2;
         const float2 u = make_float2(dx * inv, -dy * inv);  // 1/d, d = c_target - c_source
         const float2 alpha = make_float2(rs * u.x, rs * u.y);
         const float2 beta = make_float2(-rt * u.x, -rt * u.y);
@@ -301,7 +345,9 @@ __global__ void __launch_bounds__(128) k_m2l32(const int4* __restrict__ items,
         const float4* src = reinterpret_cast<const float4*>(M32 + (size_t)s * PS);
 #pragma unroll
         for (int k2 = 0; k2 < (P + 1) / 2; ++k2) aa[k2] = src[k2];
-        m2l_apply<P>(w, aa, alpha, std::make_integer_sequence<int, P>{});
+        float ls = 0.f;
+        m2l_apply<P, LOG>(w, aa, alpha, ls, std::make_integer_sequence<int, P>{});
+        if constexpr (LOG) b0 += fmaf(0.5f * logf(r2), aa[0].x, ls);
         float2 g = u;
 #pragma unroll
         for (int l = 0; l < P; ++l) {
@@ -312,9 +358,10 @@ __global__ void __launch_bounds__(128) k_m2l32(const int4* __restrict__ items,
     float2* out = item.w < 0 ? Lm2l + (size_t)b * PS : part + (size_t)it * PS;
 #pragma unroll
     for (int l = 0; l < P; ++l) out[l] = acc[l];
+    if constexpr (LOG) out[P] = make_float2(b0, 0.f);
 }
 
-template <int P>
+template <int P, bool LOG>
 __global__ void __launch_bounds__(128) k_m2l64(const int4* __restrict__ items,
                                                const unsigned long long* __restrict__ nitems,
                                                const int32_t* __restrict__ woff, const int32_t* __restrict__ widx,
@@ -330,13 +377,15 @@ __global__ void __launch_bounds__(128) k_m2l64(const int4* __restrict__ items,
     double2 acc[P];
 #pragma unroll
     for (int l = 0; l < P; ++l) acc[l] = make_double2(0.0, 0.0);
+    double b0 = 0.0;  // log kernel: constant term
     const int32_t* wl = widx + woff[b];
     for (int j = item.y; j < item.z; ++j) {
         const int s = wl[j];
         const double2 cs = center[s];
         const double rs = rho[s];
         const double dx = ct.x - cs.x, dy = ct.y - cs.y;
-        const double inv = 1.0 / (dx * dx + dy * dy);
+        const double r2 = dx * dx + dy * dy;
+        const double inv = 1.0 / r2;
         const double2 u = make_double2(dx * inv, -dy * inv);
         const double2 alpha = make_double2(rs * u.x, rs * u.y);
         const double2 beta = make_double2(-rt * u.x, -rt * u.y);
@@ -345,10 +394,12 @@ __global__ void __launch_bounds__(128) k_m2l64(const int4* __restrict__ items,
         for (int l = 0; l < P; ++l) w[l] = make_double2(0.0, 0.0);
         const double2* src = M64 + (size_t)s * PS;
         double2 ap = make_double2(1.0, 0.0);
+        double ls = 0.0;
 #pragma unroll
         for (int k = 0; k < P; ++k) {
             const double2 v = cmul(ap, src[k]);
             ap = cmul(ap, alpha);
+            if (LOG && k >= 1) ls = fma(-1.0 / k, v.x, ls);
 #pragma unroll
             for (int l = 0; l < P; ++l) {
                 const double cb = c_binom.d[k + l][l];
@@ -356,6 +407,7 @@ __global__ void __launch_bounds__(128) k_m2l64(const int4* __restrict__ items,
                 w[l].y = fma(cb, v.y, w[l].y);
             }
         }
+        if constexpr (LOG) b0 += fma(0.5 * log(r2), src[0].x, ls);
         double2 g = u;
 #pragma unroll
         for (int l = 0; l < P; ++l) {
@@ -366,13 +418,16 @@ __global__ void __launch_bounds__(128) k_m2l64(const int4* __restrict__ items,
     double2* out = item.w < 0 ? Lm2l + (size_t)b * PS : part + (size_t)it * PS;
 #pragma unroll
     for (int l = 0; l < P; ++l) out[l] = acc[l];
+    if constexpr (LOG) out[P] = make_double2(b0, 0.0);
 }
 
 // --------------------------------------------------------------------- L2L
 
 // One thread per child box of one level; FP64.  child = shift(parent) + its
-// own M2L sum.  In the FP32 path leaves also get an FP32 copy for L2P.
-template <int P, typename LM>
+// own M2L sum.  In the FP32 path leaves also get an FP32 copy for L2P.  With
+// LOG the constant term (slot P) is the parent's log polynomial at the child
+// centre plus the child's own M2L constant.
+template <int P, typename LM, bool LOG>
 __global__ void __launch_bounds__(128) k_l2l(const int32_t* __restrict__ boxes, int cnt,
                                              const int32_t* __restrict__ parent, const int32_t* __restrict__ child0,
                                              const double* __restrict__ rho, const double2* __restrict__ center,
@@ -392,6 +447,18 @@ __global__ void __launch_bounds__(128) k_l2l(const int32_t* __restrict__ boxes, 
     const double2* src = L64 + (size_t)Pb * PS;
 #pragma unroll
     for (int k = 0; k < P; ++k) b[k] = src[k];
+    const int2 mi = box_m2l[c];
+    const LM* o = Lm2l + (size_t)c * PS;
+    double b0 = 0.0;
+    if constexpr (LOG) {
+        // Horner: h = sum_m bt_m q^m / (m+1); b0' = b0 + rho_P Re(q h) + own
+        double2 h = make_double2(b[P - 1].x * (1.0 / P), b[P - 1].y * (1.0 / P));
+#pragma unroll
+        for (int m = P - 2; m >= 0; --m)
+            h = cfma(h, q, make_double2(b[m].x * (1.0 / (m + 1)), b[m].y * (1.0 / (m + 1))));
+        b0 = fma(rP, q.x * h.x - q.y * h.y, src[P].x);
+        if (mi.y > 0) b0 += (double)o[P].x;
+    }
     // in-place Taylor shift: after the sweeps b_m = sum_{l>=m} C(l,m) b_l q^(l-m)
 #pragma unroll
     for (int k = 0; k + 1 < P; ++k) {
@@ -399,9 +466,7 @@ __global__ void __launch_bounds__(128) k_l2l(const int32_t* __restrict__ boxes, 
         for (int j = P - 2; j >= k; --j) b[j] = cfma(q, b[j + 1], b[j]);
     }
     // this box's own M2L sum (split boxes were summed by k_reduce_m2l)
-    const int2 mi = box_m2l[c];
     double2 own[P];
-    const LM* o = Lm2l + (size_t)c * PS;
 #pragma unroll
     for (int m = 0; m < P; ++m) own[m] = mi.y > 0 ? make_double2((double)o[m].x, (double)o[m].y) : make_double2(0.0, 0.0);
     double sp = 1.0;
@@ -415,6 +480,10 @@ __global__ void __launch_bounds__(128) k_l2l(const int32_t* __restrict__ boxes, 
         sp *= sigma;
         out[m] = v;
         if (leaf32) o32[m] = make_float2((float)v.x, (float)v.y);
+    }
+    if constexpr (LOG) {
+        out[P] = make_double2(b0, 0.0);
+        if (leaf32) o32[P] = make_float2((float)b0, 0.f);
     }
 }
 
@@ -505,8 +574,10 @@ __global__ void __launch_bounds__(128) k_m2m_warp(const int32_t* __restrict__ pa
     if (fp32_path) M32out[(size_t)b * PS + lane] = make_float2((float)s.x, (float)s.y);
 }
 
-// One warp per child box: shifted parent local + the box's own M2L sum.
-template <int P, typename LM>
+// One warp per child box: shifted parent local + the box's own M2L sum.  With
+// LOG, lane m adds bt_m q^(m+1)/(m+1) to the constant term (xor-butterfly sum
+// across the warp, a fixed order).
+template <int P, typename LM, bool LOG>
 __global__ void __launch_bounds__(128) k_l2l_warp(const int32_t* __restrict__ boxes, int cnt,
                                                   const int32_t* __restrict__ parent,
                                                   const int32_t* __restrict__ child0, const double* __restrict__ rho,
@@ -536,9 +607,21 @@ __global__ void __launch_bounds__(128) k_l2l_warp(const int32_t* __restrict__ bo
         const double2 zz = shfl2(z, (l - lane) & 31);
         if (l >= lane) acc = cfma(yl, zz, acc);
     }
+    const int2 mi = box_m2l[c];
+    if constexpr (LOG) {
+        const double2 q1 = cmul(qk, q);  // q^(lane+1)
+        double t = (bl.x * q1.x - bl.y * q1.y) / (double)(lane + 1);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) {
+            double b0 = fma(rP, t, L64[(size_t)Pb * PS + P].x);
+            if (mi.y > 0) b0 += (double)Lm2l[(size_t)c * PS + P].x;
+            L64[(size_t)c * PS + P] = make_double2(b0, 0.0);
+            if (L32 != nullptr && child0[c] < 0) L32[(size_t)c * PS + P] = make_float2((float)b0, 0.f);
+        }
+    }
     if (lane >= P) return;
     const double scale = sk * ifl;
-    const int2 mi = box_m2l[c];
     double2 own = make_double2(0.0, 0.0);
     if (mi.y > 0) {
         const LM o = Lm2l[(size_t)c * PS + lane];
@@ -601,6 +684,68 @@ __global__ void __launch_bounds__(256) k_l2p64(int n, const int32_t* __restrict_
     out[perm[i]] = make_double2(v.x + nv.x, v.y + nv.y);
 }
 
+// Logarithmic kernel: both real-strength sets (L0: Re Gamma, L1: Im Gamma) at
+// once, F_s = b0_s + rho Re(w sum_m bt_m w^m / (m+1)) by Horner, plus the
+// complex near field (Re: set 0, Im: set 1).
+template <int P, typename T2, typename T>
+__device__ __forceinline__ T log_local_eval(const T2* __restrict__ Lb, const T2 w, const T r) {
+    T2 h;
+    h.x = Lb[P - 1].x * (T)(1.0 / P);
+    h.y = Lb[P - 1].y * (T)(1.0 / P);
+#pragma unroll
+    for (int l = P - 2; l >= 0; --l) {
+        T2 c;
+        c.x = Lb[l].x * (T)(1.0 / (l + 1));
+        c.y = Lb[l].y * (T)(1.0 / (l + 1));
+        h = cfma(h, w, c);
+    }
+    return Lb[P].x + r * (w.x * h.x - w.y * h.y);
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_l2p32_log(int n, const int32_t* __restrict__ leaf_of,
+                                                   const float4* __restrict__ chl,
+                                                   const float* __restrict__ rho32, const float4* __restrict__ pos4,
+                                                   const float2* __restrict__ L0, const float2* __restrict__ L1,
+                                                   const float2* __restrict__ nearv,
+                                                   const int32_t* __restrict__ perm, float2* __restrict__ out,
+                                                   int PS) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int lf = leaf_of[i];
+    const float4 c = chl[lf];
+    const float r = rho32[lf];
+    const float inv = r > 0.f ? 1.0f / r : 0.f;
+    const float4 pt = pos4[i];
+    const float2 w = make_float2(((pt.x - c.x) + (pt.z - c.z)) * inv, ((pt.y - c.y) + (pt.w - c.w)) * inv);
+    const float f0 = log_local_eval<P>(L0 + (size_t)lf * PS, w, r);
+    const float f1 = log_local_eval<P>(L1 + (size_t)lf * PS, w, r);
+    const float2 nv = nearv[i];
+    out[perm[i]] = make_float2(f0 + nv.x, f1 + nv.y);
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_l2p64_log(int n, const int32_t* __restrict__ leaf_of,
+                                                   const double2* __restrict__ center,
+                                                   const double* __restrict__ rho, const double2* __restrict__ pts,
+                                                   const double2* __restrict__ L0, const double2* __restrict__ L1,
+                                                   const double2* __restrict__ nearv,
+                                                   const int32_t* __restrict__ perm, double2* __restrict__ out,
+                                                   int PS) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int lf = leaf_of[i];
+    const double2 c = center[lf];
+    const double r = rho[lf];
+    const double inv = r > 0.0 ? 1.0 / r : 0.0;
+    const double2 pt = pts[i];
+    const double2 w = make_double2((pt.x - c.x) * inv, (pt.y - c.y) * inv);
+    const double f0 = log_local_eval<P>(L0 + (size_t)lf * PS, w, r);
+    const double f1 = log_local_eval<P>(L1 + (size_t)lf * PS, w, r);
+    const double2 nv = nearv[i];
+    out[perm[i]] = make_double2(f0 + nv.x, f1 + nv.y);
+}
+
 // --------------------------------------------------------------------- P2P
 
 // Pairwise terms Gamma_j/(z_i - z_j) = Gamma_j conj(d)/|d|^2, d = z_i - z_j.
@@ -637,6 +782,23 @@ __device__ __forceinline__ void p2p_fast(const double2 t, const double2 s, const
     p2p_interact64(t, s, g, acc);
 }
 
+// Logarithmic kernel, FP64: Gamma_j ln|z_i - z_j| (complex Gamma on the real
+// kernel); a coincident pair adds 0.  Zero-strength padding sources sit at a
+// finite position (the origin) and add exactly 0.
+__device__ __forceinline__ void p2p_log(const double2 t, const double2 s, const double2 g, double2& acc) {
+    const double dx = t.x - s.x, dy = t.y - s.y;
+    const double r2 = fma(dx, dx, dy * dy);
+    const double lr = r2 > 0.0 ? 0.5 * log(r2) : 0.0;
+    acc.x = fma(g.x, lr, acc.x);
+    acc.y = fma(g.y, lr, acc.y);
+}
+
+template <bool LOG, typename V, typename C>
+__device__ __forceinline__ void p2p_term(const V t, const V s, const C g, C& acc) {
+    if constexpr (LOG) p2p_log(t, s, g, acc);
+    else p2p_fast(t, s, g, acc);
+}
+
 // ---- P2P over the leaf slot layout ------------------------------------------
 // One warp per work item (a target leaf and a run of its strong entries),
 // fetched from an atomic counter.  Lane (tg, ss) owns targets tg, tg+LT, ...
@@ -652,7 +814,7 @@ __device__ __forceinline__ void p2p_fast(const double2 t, const double2 s, const
 // ceil(count/S) steps per range.  The S slice sums are added with shuffles.
 constexpr int kP2PDWarps = 4;
 
-template <typename V, typename C, int TPL, int LT>
+template <typename V, typename C, int TPL, int LT, bool LOG>
 __global__ void __launch_bounds__(kP2PDWarps * 32, sizeof(C) == 8 ? 5 : 1)
     k_p2p_slots(const int4* __restrict__ items, const unsigned long long* __restrict__ nitems,
                 unsigned* __restrict__ next_item, const int32_t* __restrict__ bstart,
@@ -698,9 +860,9 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, sizeof(C) == 8 ? 5 : 1)
                     oa0 = (k + 4 < ke ? rl[k + 4].x : pad) + ss;
                     oa1 = (k + 5 < ke ? rl[k + 5].x : pad) + ss;
 #pragma unroll
-                    for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], sa0, ga0, acc[u]);
+                    for (int u = 0; u < TPL; ++u) p2p_term<LOG>(xt[u], sa0, ga0, acc[u]);
 #pragma unroll
-                    for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], sa1, ga1, acc[u]);
+                    for (int u = 0; u < TPL; ++u) p2p_term<LOG>(xt[u], sa1, ga1, acc[u]);
                     if (k + 2 >= ke) break;
                     sa0 = posp[oa0];
                     sa1 = posp[oa1];
@@ -709,9 +871,9 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, sizeof(C) == 8 ? 5 : 1)
                     ob0 = (k + 6 < ke ? rl[k + 6].x : pad) + ss;
                     ob1 = (k + 7 < ke ? rl[k + 7].x : pad) + ss;
 #pragma unroll
-                    for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], sb0, gb0, acc[u]);
+                    for (int u = 0; u < TPL; ++u) p2p_term<LOG>(xt[u], sb0, gb0, acc[u]);
 #pragma unroll
-                    for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], sb1, gb1, acc[u]);
+                    for (int u = 0; u < TPL; ++u) p2p_term<LOG>(xt[u], sb1, gb1, acc[u]);
                     k += 4;
                     if (k >= ke) break;
                 }
@@ -724,15 +886,15 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, sizeof(C) == 8 ? 5 : 1)
                         const V s0 = posp[o + e], s1 = posp[o + e + S];
                         const C g0 = gamp[o + e], g1 = gamp[o + e + S];
 #pragma unroll
-                        for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], s0, g0, acc[u]);
+                        for (int u = 0; u < TPL; ++u) p2p_term<LOG>(xt[u], s0, g0, acc[u]);
 #pragma unroll
-                        for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], s1, g1, acc[u]);
+                        for (int u = 0; u < TPL; ++u) p2p_term<LOG>(xt[u], s1, g1, acc[u]);
                     }
                     if (e < r.y) {
                         const V s0 = posp[o + e];
                         const C g0 = gamp[o + e];
 #pragma unroll
-                        for (int u = 0; u < TPL; ++u) p2p_fast(xt[u], s0, g0, acc[u]);
+                        for (int u = 0; u < TPL; ++u) p2p_term<LOG>(xt[u], s0, g0, acc[u]);
                     }
                 }
             }
@@ -793,7 +955,33 @@ __device__ __forceinline__ void p2p_pair(const f2x tx, const f2x ty, const f2x t
     ay = f2fma(s.gy, a, f2fma(s.ngx, b, ay));  // gy a - gx b
 }
 
-template <int TPL, int LT>
+// Logarithmic kernel, two sources against one target: Gamma_j log2(|d|^2)
+// (the factor ln(2)/2 is applied to the finished sums).  Pairs with |d|^2
+// below the smallest normal FP32 number (coincident points, or closer than
+// ~1e-19) add 0.
+__device__ __forceinline__ float log2_pos(float r2) {
+    return r2 >= 1.17549435e-38f ? __log2f(r2) : 0.f;
+}
+__device__ __forceinline__ void p2p_pair_log(const f2x tx, const f2x ty, const f2x txl, const f2x tyl,
+                                             const SrcPair& s, f2x& ax, f2x& ay) {
+    const f2x dx = f2add(f2sub(tx, s.x), f2sub(txl, s.xl));
+    const f2x dy = f2add(f2sub(ty, s.y), f2sub(tyl, s.yl));
+    const f2x r2 = f2fma(dx, dx, f2mul(dy, dy));
+    float r0, r1;
+    f2upk(r2, r0, r1);
+    const f2x lg = f2pk(log2_pos(r0), log2_pos(r1));
+    ax = f2fma(s.gx, lg, ax);
+    ay = f2fma(s.gy, lg, ay);
+}
+template <bool LOG>
+__device__ __forceinline__ void p2p_pair_t(const f2x tx, const f2x ty, const f2x txl, const f2x tyl,
+                                           const SrcPair& s, f2x& ax, f2x& ay) {
+    if constexpr (LOG) p2p_pair_log(tx, ty, txl, tyl, s, ax, ay);
+    else p2p_pair(tx, ty, txl, tyl, s, ax, ay);
+}
+constexpr float kHalfLn2 = 0.34657359027997264f;  // ln(2)/2: log2(|d|^2) -> ln|d|
+
+template <int TPL, int LT, bool LOG>
 __global__ void __launch_bounds__(kP2PDWarps * 32, TPL > 4 ? 2 : 4)
     k_p2p_pairs(const int4* __restrict__ items, const unsigned long long* __restrict__ nitems,
                 unsigned* __restrict__ next_item, const int32_t* __restrict__ bstart,
@@ -853,9 +1041,9 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, TPL > 4 ? 2 : 4)
                     {
                         const SrcPair s0 = src_pair(pa0, qa0, ga0), s1 = src_pair(pa1, qa1, ga1);
 #pragma unroll
-                        for (int u = 0; u < TPL; ++u) p2p_pair(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
+                        for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
 #pragma unroll
-                        for (int u = 0; u < TPL; ++u) p2p_pair(tx[u], ty[u], txl[u], tyl[u], s1, ax[u], ay[u]);
+                        for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s1, ax[u], ay[u]);
                     }
                     if (k + 2 >= ke) break;
                     pa0 = posq[2 * oa0];
@@ -869,9 +1057,9 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, TPL > 4 ? 2 : 4)
                     {
                         const SrcPair s0 = src_pair(pb0, qb0, gb0), s1 = src_pair(pb1, qb1, gb1);
 #pragma unroll
-                        for (int u = 0; u < TPL; ++u) p2p_pair(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
+                        for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
 #pragma unroll
-                        for (int u = 0; u < TPL; ++u) p2p_pair(tx[u], ty[u], txl[u], tyl[u], s1, ax[u], ay[u]);
+                        for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s1, ax[u], ay[u]);
                     }
                     k += 4;
                     if (k >= ke) break;
@@ -887,14 +1075,14 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, TPL > 4 ? 2 : 4)
                         const SrcPair s1 =
                             src_pair(posq[2 * (o + e + S)], posq[2 * (o + e + S) + 1], gamq[o + e + S]);
 #pragma unroll
-                        for (int u = 0; u < TPL; ++u) p2p_pair(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
+                        for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
 #pragma unroll
-                        for (int u = 0; u < TPL; ++u) p2p_pair(tx[u], ty[u], txl[u], tyl[u], s1, ax[u], ay[u]);
+                        for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s1, ax[u], ay[u]);
                     }
                     if (2 * e < r.y) {
                         const SrcPair s0 = src_pair(posq[2 * (o + e)], posq[2 * (o + e) + 1], gamq[o + e]);
 #pragma unroll
-                        for (int u = 0; u < TPL; ++u) p2p_pair(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
+                        for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
                     }
                 }
             }
@@ -908,6 +1096,10 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, TPL > 4 ? 2 : 4)
                 for (int o = LT; o < 32; o <<= 1) {
                     tot.x += __shfl_xor_sync(0xffffffffu, tot.x, o);
                     tot.y += __shfl_xor_sync(0xffffffffu, tot.y, o);
+                }
+                if constexpr (LOG) {
+                    tot.x *= kHalfLn2;
+                    tot.y *= kHalfLn2;
                 }
                 const int idx = t0 + tg + u * LT;
                 if (ss == 0 && idx < tn) {
@@ -946,7 +1138,9 @@ __global__ void __launch_bounds__(256) k_reduce_p2p(const int32_t* __restrict__ 
     }
 }
 
-// M2L sums of boxes whose weak list was split: one warp per box, lane = coefficient.
+// M2L sums of boxes whose weak list was split: one warp per box, lane = coefficient
+// (lanes stride over the PS slots: PS exceeds 32 at p = 32, with the log kernel's
+// constant term in slot 32).
 template <typename C>
 __global__ void __launch_bounds__(256) k_reduce_m2l(int nbox, const int2* __restrict__ box_m2l,
                                                     const C* __restrict__ part, int PS, C* __restrict__ Lm2l) {
@@ -955,15 +1149,15 @@ __global__ void __launch_bounds__(256) k_reduce_m2l(int nbox, const int2* __rest
     if (b >= nbox) return;
     const int2 mi = box_m2l[b];
     if (mi.y <= 1) return;
-    if (lane < PS) {
+    for (int c = lane; c < PS; c += 32) {
         C s{};
 #pragma unroll 8
         for (int q = 0; q < mi.y; ++q) {
-            const C v = part[(size_t)(mi.x + q) * PS + lane];
+            const C v = part[(size_t)(mi.x + q) * PS + c];
             s.x += v.x;
             s.y += v.y;
         }
-        Lm2l[(size_t)b * PS + lane] = s;
+        Lm2l[(size_t)b * PS + c] = s;
     }
 }
 
@@ -1009,7 +1203,7 @@ static const unsigned long long* item_count(const Tree& t, int which) {
     return reinterpret_cast<const unsigned long long*>(t.d_status) + 1 + which;  // 2 = P2P, 3 = M2L
 }
 
-template <int P>
+template <int P, bool LOG>
 static void launch_far_fp32(Tree& t, const Bufs& B, cudaStream_t s) {
     const float2* gam = static_cast<const float2*>(B.gam);
     k_p2m32<P><<<nblk(t.nleaf, 128), 128, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, t.d_bstart, t.d_bcount, t.d_chl,
@@ -1026,9 +1220,9 @@ static void launch_far_fp32(Tree& t, const Bufs& B, cudaStream_t s) {
     }
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[2], s);
     if (m2l_tc_enabled())
-        launch_m2l_tc(t, B.M32, static_cast<float2*>(B.Lm2l), static_cast<float2*>(B.m2l_part), s);
+        launch_m2l_tc(t, B.M32, static_cast<float2*>(B.Lm2l), static_cast<float2*>(B.m2l_part), LOG, s);
     else
-        k_m2l32<P><<<nblk(m2l_grid_items(t), 128), 128, 0, s>>>(t.d_m2l_items, item_count(t, 3), t.d_woff, t.d_widx,
+        k_m2l32<P, LOG><<<nblk(m2l_grid_items(t), 128), 128, 0, s>>>(t.d_m2l_items, item_count(t, 3), t.d_woff, t.d_widx,
                                                         t.d_chl, t.d_rho32, B.M32, static_cast<float2*>(B.Lm2l),
                                                         static_cast<float2*>(B.m2l_part), t.PS);
     k_reduce_m2l<float2><<<nblk(32 * t.nbox, 256), 256, 0, s>>>((int)t.nbox, t.d_box_m2l,
@@ -1038,17 +1232,17 @@ static void launch_far_fp32(Tree& t, const Bufs& B, cudaStream_t s) {
     for (int l = 0; l + 1 < t.Lmax; ++l) {
         const LevelList& L = t.level_boxes[l + 1];
         if (L.count <= kWarpShiftMax)
-            k_l2l_warp<P, float2><<<nblk(32 * (int64_t)L.count, 128), 128, 0, s>>>(
+            k_l2l_warp<P, float2, LOG><<<nblk(32 * (int64_t)L.count, 128), 128, 0, s>>>(
                 L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho, t.d_center, t.d_box_m2l,
                 static_cast<const float2*>(B.Lm2l), B.L64, B.L32, t.p, t.PS);
         else
-            k_l2l<P, float2><<<nblk(L.count, 128), 128, 0, s>>>(
+            k_l2l<P, float2, LOG><<<nblk(L.count, 128), 128, 0, s>>>(
                 L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho, t.d_center, t.d_box_m2l,
                 static_cast<const float2*>(B.Lm2l), B.L64, B.L32, t.p, t.PS);
     }
 }
 
-template <int P>
+template <int P, bool LOG>
 static void launch_far_fp64(Tree& t, const Bufs& B, cudaStream_t s) {
     const double2* gam = static_cast<const double2*>(B.gam);
     k_p2m64<P><<<nblk(t.nleaf, 128), 128, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, t.d_bstart, t.d_bcount, t.d_center,
@@ -1065,7 +1259,7 @@ static void launch_far_fp64(Tree& t, const Bufs& B, cudaStream_t s) {
                                                                      t.PS);
     }
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[2], s);
-    k_m2l64<P><<<nblk(m2l_grid_items(t), 128), 128, 0, s>>>(t.d_m2l_items, item_count(t, 3), t.d_woff, t.d_widx,
+    k_m2l64<P, LOG><<<nblk(m2l_grid_items(t), 128), 128, 0, s>>>(t.d_m2l_items, item_count(t, 3), t.d_woff, t.d_widx,
                                                     t.d_center, t.d_rho, B.M64, static_cast<double2*>(B.Lm2l),
                                                     static_cast<double2*>(B.m2l_part), t.PS);
     k_reduce_m2l<double2><<<nblk(32 * t.nbox, 256), 256, 0, s>>>((int)t.nbox, t.d_box_m2l,
@@ -1075,11 +1269,11 @@ static void launch_far_fp64(Tree& t, const Bufs& B, cudaStream_t s) {
     for (int l = 0; l + 1 < t.Lmax; ++l) {
         const LevelList& L = t.level_boxes[l + 1];
         if (L.count <= kWarpShiftMax)
-            k_l2l_warp<P, double2><<<nblk(32 * (int64_t)L.count, 128), 128, 0, s>>>(
+            k_l2l_warp<P, double2, LOG><<<nblk(32 * (int64_t)L.count, 128), 128, 0, s>>>(
                 L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho, t.d_center, t.d_box_m2l,
                 static_cast<const double2*>(B.Lm2l), B.L64, nullptr, t.p, t.PS);
         else
-            k_l2l<P, double2><<<nblk(L.count, 128), 128, 0, s>>>(
+            k_l2l<P, double2, LOG><<<nblk(L.count, 128), 128, 0, s>>>(
                 L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho, t.d_center, t.d_box_m2l,
                 static_cast<const double2*>(B.Lm2l), B.L64, nullptr, t.p, t.PS);
     }
@@ -1096,6 +1290,20 @@ static void launch_l2p(Tree& t, const Bufs& B, void* d_phi, cudaStream_t s) {
         k_l2p64<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_center, t.d_rho, t.d_pts, B.L64,
                                                 static_cast<const double2*>(B.near), t.d_perm,
                                                 static_cast<double2*>(d_phi), t.PS);
+    }
+}
+
+template <int P>
+static void launch_l2p_log(Tree& t, const Bufs& B0, const Bufs& B1, void* d_phi, cudaStream_t s) {
+    const int n = (int)t.n;
+    if (t.path == FMM_PATH_FP32) {
+        k_l2p32_log<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_chl, t.d_rho32, t.d_pos4, B0.L32, B1.L32,
+                                                    static_cast<const float2*>(B0.near), t.d_perm,
+                                                    static_cast<float2*>(d_phi), t.PS);
+    } else {
+        k_l2p64_log<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_center, t.d_rho, t.d_pts, B0.L64, B1.L64,
+                                                    static_cast<const double2*>(B0.near), t.d_perm,
+                                                    static_cast<double2*>(d_phi), t.PS);
     }
 }
 
@@ -1120,6 +1328,7 @@ static int p2p_blocks_per_sm() {
     return v;
 }
 
+template <bool LOG>
 static void launch_p2p(Tree& t, const Bufs& B, cudaStream_t s) {
     const unsigned long long* cnt = item_count(t, 2);
     unsigned* next = reinterpret_cast<unsigned*>(reinterpret_cast<unsigned long long*>(t.d_status) + 7);
@@ -1136,8 +1345,8 @@ static void launch_p2p(Tree& t, const Bufs& B, cudaStream_t s) {
     const P2PLayout lay = p2p_layout(t.max_leaf);
     const int pad = (int)(t.nleaf * t.leaf_cap);
 #define FMM_P2P(V, C, TPL, LT)                                                                                   \
-    t.p2p_funcs.push_back(reinterpret_cast<const void*>(k_p2p_slots<V, C, TPL, LT>));                           \
-    k_p2p_slots<V, C, TPL, LT><<<dgrid, kP2PDWarps * 32, 0, s>>>(                                                 \
+    t.p2p_funcs.push_back(reinterpret_cast<const void*>(k_p2p_slots<V, C, TPL, LT, LOG>));                      \
+    k_p2p_slots<V, C, TPL, LT, LOG><<<dgrid, kP2PDWarps * 32, 0, s>>>(                                            \
         t.d_p2p_items, cnt, next, t.d_bstart, t.d_bcount, t.d_pslot, t.d_soff, t.d_srng,                          \
         static_cast<const V*>(t.d_posp), static_cast<const C*>(t.d_gamp), nv, pt, t.max_leaf, pad, per_warp);
 #define FMM_P2P_LAYOUTS(V, C)                                  \
@@ -1154,8 +1363,8 @@ static void launch_p2p(Tree& t, const Bufs& B, cudaStream_t s) {
         float2* pt = static_cast<float2*>(B.p2p_part);
         const P2PLayout pl = p2p_pair_layout(t.max_leaf);
 #define FMM_P2P_PAIRS(TPL, LT)                                                                                   \
-    t.p2p_funcs.push_back(reinterpret_cast<const void*>(k_p2p_pairs<TPL, LT>));                                 \
-    k_p2p_pairs<TPL, LT><<<dgrid, kP2PDWarps * 32, 0, s>>>(                                                       \
+    t.p2p_funcs.push_back(reinterpret_cast<const void*>(k_p2p_pairs<TPL, LT, LOG>));                            \
+    k_p2p_pairs<TPL, LT, LOG><<<dgrid, kP2PDWarps * 32, 0, s>>>(                                                  \
         t.d_p2p_items, cnt, next, t.d_bstart, t.d_bcount, t.d_pslot, t.d_soff, t.d_srng,                          \
         static_cast<const ulonglong2*>(t.d_posp), static_cast<const ulonglong2*>(t.d_gamp), nv, pt, t.max_leaf,   \
         pad, per_warp);
@@ -1182,10 +1391,10 @@ static void launch_p2p(Tree& t, const Bufs& B, cudaStream_t s) {
 #undef FMM_P2P
 }
 
-template <int P>
+template <int P, bool LOG>
 static void launch_far(Tree& t, const Bufs& B, cudaStream_t s) {
-    if (t.path == FMM_PATH_FP32) launch_far_fp32<P>(t, B, s);
-    else launch_far_fp64<P>(t, B, s);
+    if (t.path == FMM_PATH_FP32) launch_far_fp32<P, LOG>(t, B, s);
+    else launch_far_fp64<P, LOG>(t, B, s);
 }
 
 // Compiled expansion orders; a request for p runs the smallest compiled
@@ -1200,10 +1409,13 @@ int compiled_order(int p) {
     return -1;
 }
 
-void dispatch_far(Tree& t, const Bufs& B, cudaStream_t s) {
+void dispatch_far(Tree& t, const Bufs& B, cudaStream_t s, bool log_kernel) {
     switch (t.P) {
-#define FMM_CASE(Q) \
-    case Q: launch_far<Q>(t, B, s); break;
+#define FMM_CASE(Q)                                  \
+    case Q:                                          \
+        if (log_kernel) launch_far<Q, true>(t, B, s); \
+        else launch_far<Q, false>(t, B, s);           \
+        break;
         FMM_FOR_ORDERS(FMM_CASE)
 #undef FMM_CASE
     }
@@ -1213,6 +1425,15 @@ static void dispatch_l2p(Tree& t, const Bufs& B, void* d_phi, cudaStream_t s) {
     switch (t.P) {
 #define FMM_CASE(Q) \
     case Q: launch_l2p<Q>(t, B, d_phi, s); break;
+        FMM_FOR_ORDERS(FMM_CASE)
+#undef FMM_CASE
+    }
+}
+
+static void dispatch_l2p_log(Tree& t, const Bufs& B0, const Bufs& B1, void* d_phi, cudaStream_t s) {
+    switch (t.P) {
+#define FMM_CASE(Q) \
+    case Q: launch_l2p_log<Q>(t, B0, B1, d_phi, s); break;
         FMM_FOR_ORDERS(FMM_CASE)
 #undef FMM_CASE
     }
@@ -1243,6 +1464,7 @@ fmm_status alloc_eval(Tree& t, int sets) {
         t.eval_ts >= t.max_leaf && t.eval_slots == t.slot_alloc)
         return FMM_OK;
     sets = std::max(sets, t.eval_sets);
+    ++t.eval_gen;
     const size_t nb = (size_t)t.nbox, n = (size_t)t.n, PS = (size_t)t.PS;
     const size_t cs = t.path == FMM_PATH_FP32 ? sizeof(float2) : sizeof(double2);
     fmm_status st;
@@ -1300,7 +1522,7 @@ fmm_status run_eval(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s)
         if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[4], t.s_far));
         FMM_CUDA(cudaEventRecord(t.ev_join_far, t.s_far));
         if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[5], t.s_aux));
-        launch_p2p(t, B, t.s_aux);
+        launch_p2p<false>(t, B, t.s_aux);
         if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[6], t.s_aux));
         FMM_CUDA(cudaEventRecord(t.ev_join, t.s_aux));
         FMM_CUDA(cudaStreamWaitEvent(s, t.ev_join_far, 0));
@@ -1309,10 +1531,53 @@ fmm_status run_eval(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s)
         dispatch_far(t, B, s);
         if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[4], s));
         if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[5], s));
-        launch_p2p(t, B, s);
+        launch_p2p<false>(t, B, s);
         if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[6], s));
     }
     dispatch_l2p(t, B, d_phi, s);
+    if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[7], s));
+    FMM_CUDA(cudaGetLastError());
+    t.timing_valid = timing;
+    return FMM_OK;
+}
+
+// Logarithmic kernel (Sec. 3.3): both real-strength sets' far fields on the
+// far stream (set 0 then set 1), the complex-strength P2P on the auxiliary
+// stream, then one L2P for both.  Needs a workspace of two strength sets.
+fmm_status run_eval_log(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s) {
+    const int n = (int)t.n;
+    t.p2p_funcs.clear();
+    const bool timing = t.flags & FMM_FLAG_TIMING;
+    const bool serial = t.flags & FMM_FLAG_SERIAL;
+    if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[0], s));
+    const double2* gin = reinterpret_cast<const double2*>(d_gamma);
+    const Bufs B0 = bufs(t, 0), B1 = bufs(t, 1);
+    if (t.path == FMM_PATH_FP32)
+        k_gather_log32<<<nblk(n, 256), 256, 0, s>>>(gin, t.d_perm, t.d_slot_of, n, static_cast<float2*>(B0.gam),
+                                                    static_cast<float2*>(B1.gam), static_cast<float*>(t.d_gamp));
+    else
+        k_gather_log64<<<nblk(n, 256), 256, 0, s>>>(gin, t.d_perm, t.d_slot_of, n, static_cast<double2*>(B0.gam),
+                                                    static_cast<double2*>(B1.gam), static_cast<double2*>(t.d_gamp));
+    if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[1], s));
+    cudaStream_t sf = serial ? s : t.s_far, sa = serial ? s : t.s_aux;
+    if (!serial) {
+        FMM_CUDA(cudaEventRecord(t.ev_fork, s));
+        FMM_CUDA(cudaStreamWaitEvent(t.s_far, t.ev_fork, 0));
+        FMM_CUDA(cudaStreamWaitEvent(t.s_aux, t.ev_fork, 0));
+    }
+    dispatch_far(t, B0, sf, true);
+    dispatch_far(t, B1, sf, true);
+    if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[4], sf));
+    if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[5], sa));
+    launch_p2p<true>(t, B0, sa);
+    if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[6], sa));
+    if (!serial) {
+        FMM_CUDA(cudaEventRecord(t.ev_join_far, t.s_far));
+        FMM_CUDA(cudaEventRecord(t.ev_join, t.s_aux));
+        FMM_CUDA(cudaStreamWaitEvent(s, t.ev_join_far, 0));
+        FMM_CUDA(cudaStreamWaitEvent(s, t.ev_join, 0));
+    }
+    dispatch_l2p_log(t, B0, B1, d_phi, s);
     if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[7], s));
     FMM_CUDA(cudaGetLastError());
     t.timing_valid = timing;

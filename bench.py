@@ -42,6 +42,9 @@ P2P_TRAFFIC_BYTES = 83_457_280 + 6_434_048
 # algorithmic FP32 flops of one point-pair interaction (FMA = 2): compensated
 # difference 6, |d|^2 4, the two scalings 2, the complex accumulation 8
 P2P_FLOPS = 20.0
+# the same for the logarithmic kernel: compensated difference 6, |d|^2 3, the
+# complex accumulation of Gamma_j log2|d|^2 4 (plus one log2 on the MUFU unit)
+P2P_LOG_FLOPS = 13.0
 SM_COUNT = 148
 FP32_FLOP_PER_CLK_SM = 256  # 128 FP32 lanes x FMA
 
@@ -149,7 +152,7 @@ def run_gpu(args):
         tree.autotune_config(cap=0.2, window=2, period=2)
         phi = torch.empty(N_POINTS, dtype=torch.complex64, device=dev)
         L = L0
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         for _ in range(0 if args.nlevels else max(24, args.warmup)):
             e0.record(stream)
             tree.rebuild(X, nlevels=L)
@@ -252,6 +255,48 @@ def run_gpu(args):
         ms64 = float(np.median(s64))
         err64 = _rel(phi64.cpu().numpy()[tg], exact) if rank == 0 else None
         t64.close()
+
+        # --- logarithmic kernel (Sec. 3.3) on the same tree and workload -----------
+        log_kernel = None
+        try:
+            phil = torch.empty(N_POINTS, dtype=torch.complex64, device=dev)
+            tree.eval_log(G, out=phil)
+            tree.rebuild(X, flags=F.FMM_FLAG_TIMING | F.FMM_FLAG_SERIAL)
+            lp = []
+            for _ in range(5):
+                flush.zero_()
+                tree.eval_log(G, out=phil)
+                lp.append(tree.phase_times()["p2p"])
+            tree.rebuild(X, flags=0)
+            ls, le = [], []
+            for _ in range(5):
+                flush.zero_()
+                e0.record(stream)
+                tree.rebuild(X)
+                e1.record(stream)
+                tree.eval_log(G, out=phil)
+                e2.record(stream)
+                e2.synchronize()
+                ls.append(e0.elapsed_time(e2))
+                le.append(e1.elapsed_time(e2))
+            log_p2p_ms = float(np.median(lp))
+            log_ms = float(np.median(ls))
+            log_eval_ms = float(np.median(le))
+            lerr = None
+            if rank == 0:
+                import oracle as _orcl
+
+                tgl = np.random.default_rng(9).choice(N_POINTS, 512, replace=False)
+                lerr = _rel(phil.cpu().numpy().astype(np.complex128)[tgl], _orcl.direct_log(xy, gam, targets=tgl))
+            log_kernel = {"ms_per_step": round(log_ms, 4), "eval_ms": round(log_eval_ms, 4),
+                          "value": round(N_POINTS / (log_ms * 1e-3) / 1e6, 2), "unit": UNIT,
+                          "eval_over_harmonic_eval": round(log_eval_ms / eval_ms, 3),
+                          "p2p_ms_alone": round(log_p2p_ms, 4),
+                          "p2p_tflops": round(info["p2p_pairs"] * P2P_LOG_FLOPS / (log_p2p_ms * 1e-3) / 1e12, 3),
+                          "rel_err_sampled": lerr,
+                          "step": "tree rebuild + lists + one log-kernel evaluation (FP32 path, same tree)"}
+        except _lib.FMMError:
+            log_kernel = None
 
         # --- adjoint / forward ratio (same tree) ------------------------------
         bwd_ratio = None
@@ -379,6 +424,7 @@ def run_gpu(args):
                       "rel_err_sampled": err64},
         "rel_err_sampled": err32,
         "bwd_over_fwd": bwd_ratio,
+        "log_kernel": log_kernel,
         "theta_autotune": theta_tune,
         "roofline": {"kernel": "k_p2p_pairs (P2P, FP32 f32x2)", "bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),

@@ -90,6 +90,8 @@ static fmm_status ensure_streams(Tree& t) {
     FMM_CUDA(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
     if (!t.s_aux) FMM_CUDA(cudaStreamCreateWithPriority(&t.s_aux, cudaStreamNonBlocking, lo_prio));
     if (!t.s_far) FMM_CUDA(cudaStreamCreateWithPriority(&t.s_far, cudaStreamNonBlocking, hi_prio));
+    if (!t.s_far2) FMM_CUDA(cudaStreamCreateWithPriority(&t.s_far2, cudaStreamNonBlocking, hi_prio));
+    if (!t.ev_join_far2) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_join_far2, cudaEventDisableTiming));
     if (!t.ev_fork) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_fork, cudaEventDisableTiming));
     if (!t.ev_join) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_join, cudaEventDisableTiming));
     if (!t.ev_join_far) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_join_far, cudaEventDisableTiming));
@@ -202,6 +204,8 @@ static void release(Tree* t) {
     }
     if (t->s_aux) cudaStreamDestroy(t->s_aux);
     if (t->s_far) cudaStreamDestroy(t->s_far);
+    if (t->s_far2) cudaStreamDestroy(t->s_far2);
+    if (t->ev_join_far2) cudaEventDestroy(t->ev_join_far2);
     if (t->ev_join_far) cudaEventDestroy(t->ev_join_far);
     if (t->ev_fork) cudaEventDestroy(t->ev_fork);
     if (t->ev_join) cudaEventDestroy(t->ev_join);

@@ -313,6 +313,7 @@ fmm_status run_backward(Tree& t, const double* d_gamma, const double* d_gphi, do
                                                            static_cast<double2*>(B1.gam));
     FMM_CUDA(cudaEventRecord(t.ev_fork, s));
     FMM_CUDA(cudaStreamWaitEvent(t.s_aux, t.ev_fork, 0));
+    FMM_CUDA(cudaStreamWaitEvent(t.s_far2, t.ev_fork, 0));
     const int grid = nblk(p2p_grid_items(t), kBWarps);
     const long long stride = (long long)t.part_p2p_cap * t.max_leaf;
     const unsigned long long* cnt = reinterpret_cast<const unsigned long long*>(t.d_status) + 3;
@@ -347,9 +348,12 @@ fmm_status run_backward(Tree& t, const double* d_gamma, const double* d_gphi, do
     FMM_CUDA(cudaEventRecord(t.ev_join, t.s_aux));
     const int flags = t.flags;
     t.flags &= ~FMM_FLAG_TIMING;
+    // the two strength sets' far fields side by side (latency-bound kernels overlap)
     dispatch_far(t, B0, s);
-    dispatch_far(t, B1, s);
+    dispatch_far(t, B1, t.s_far2);
     t.flags = flags;
+    FMM_CUDA(cudaEventRecord(t.ev_join_far2, t.s_far2));
+    FMM_CUDA(cudaStreamWaitEvent(s, t.ev_join_far2, 0));
     FMM_CUDA(cudaStreamWaitEvent(s, t.ev_join, 0));
     switch (t.P) {
 #define FMM_CASE(Q) \

@@ -203,7 +203,8 @@ struct Tree {
     // streams / events
     cudaStream_t s_aux = nullptr;  // P2P (lowest priority)
     cudaStream_t s_far = nullptr;  // far-field chain (highest priority)
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join_far = nullptr;
+    cudaStream_t s_far2 = nullptr;  // second strength set's far-field chain (log kernel, adjoint; highest priority)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join_far = nullptr, ev_join_far2 = nullptr;
     cudaEvent_t ev_t[8] = {};
     bool timing_valid = false;
 

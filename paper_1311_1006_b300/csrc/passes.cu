@@ -959,8 +959,13 @@ __device__ __forceinline__ void p2p_pair(const f2x tx, const f2x ty, const f2x t
 // (the factor ln(2)/2 is applied to the finished sums).  Pairs with |d|^2
 // below the smallest normal FP32 number (coincident points, or closer than
 // ~1e-19) add 0.
+__device__ __forceinline__ float lg2_ftz(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ float log2_pos(float r2) {
-    return r2 >= 1.17549435e-38f ? __log2f(r2) : 0.f;
+    return r2 >= 1.17549435e-38f ? lg2_ftz(r2) : 0.f;  // normal inputs only: the ftz form suffices
 }
 __device__ __forceinline__ void p2p_pair_log(const f2x tx, const f2x ty, const f2x txl, const f2x tyl,
                                              const SrcPair& s, f2x& ax, f2x& ay) {
@@ -1541,9 +1546,10 @@ fmm_status run_eval(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s)
     return FMM_OK;
 }
 
-// Logarithmic kernel (Sec. 3.3): both real-strength sets' far fields on the
-// far stream (set 0 then set 1), the complex-strength P2P on the auxiliary
-// stream, then one L2P for both.  Needs a workspace of two strength sets.
+// Logarithmic kernel (Sec. 3.3): the two real-strength sets' far fields on two
+// high-priority streams (their latency-bound kernels overlap), the
+// complex-strength P2P on the low-priority stream, then one L2P for both.
+// Needs a workspace of two strength sets.
 fmm_status run_eval_log(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s) {
     const int n = (int)t.n;
     t.p2p_funcs.clear();
@@ -1559,22 +1565,31 @@ fmm_status run_eval_log(Tree& t, const double* d_gamma, void* d_phi, cudaStream_
         k_gather_log64<<<nblk(n, 256), 256, 0, s>>>(gin, t.d_perm, t.d_slot_of, n, static_cast<double2*>(B0.gam),
                                                     static_cast<double2*>(B1.gam), static_cast<double2*>(t.d_gamp));
     if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[1], s));
-    cudaStream_t sf = serial ? s : t.s_far, sa = serial ? s : t.s_aux;
+    cudaStream_t sf = serial ? s : t.s_far, sf2 = serial ? s : t.s_far2, sa = serial ? s : t.s_aux;
     if (!serial) {
         FMM_CUDA(cudaEventRecord(t.ev_fork, s));
         FMM_CUDA(cudaStreamWaitEvent(t.s_far, t.ev_fork, 0));
+        FMM_CUDA(cudaStreamWaitEvent(t.s_far2, t.ev_fork, 0));
         FMM_CUDA(cudaStreamWaitEvent(t.s_aux, t.ev_fork, 0));
     }
-    dispatch_far(t, B0, sf, true);
-    dispatch_far(t, B1, sf, true);
-    if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[4], sf));
+    {
+        // phase events cover set 0 only (set 1 runs beside it)
+        dispatch_far(t, B0, sf, true);
+        if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[4], sf));
+        const int flags = t.flags;
+        t.flags &= ~FMM_FLAG_TIMING;
+        dispatch_far(t, B1, sf2, true);
+        t.flags = flags;
+    }
     if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[5], sa));
     launch_p2p<true>(t, B0, sa);
     if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[6], sa));
     if (!serial) {
         FMM_CUDA(cudaEventRecord(t.ev_join_far, t.s_far));
+        FMM_CUDA(cudaEventRecord(t.ev_join_far2, t.s_far2));
         FMM_CUDA(cudaEventRecord(t.ev_join, t.s_aux));
         FMM_CUDA(cudaStreamWaitEvent(s, t.ev_join_far, 0));
+        FMM_CUDA(cudaStreamWaitEvent(s, t.ev_join_far2, 0));
         FMM_CUDA(cudaStreamWaitEvent(s, t.ev_join, 0));
     }
     dispatch_l2p_log(t, B0, B1, d_phi, s);

@@ -165,9 +165,10 @@ def run_gpu(args):
         info = tree.info()
 
         # --- timed: build + eval, inputs resident ------------------------------
+        step_eval = tree.eval_log if args.log_kernel else tree.eval
         for _ in range(args.warmup):
             tree.rebuild(X)
-            tree.eval(G, out=phi)
+            step_eval(G, out=phi)
         stream.synchronize()
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -179,7 +180,7 @@ def run_gpu(args):
                 flush.zero_()
                 starts[k].record(stream)
                 tree.rebuild(X)
-                tree.eval(G, out=phi)
+                step_eval(G, out=phi)
                 ends[k].record(stream)
             torch.cuda.synchronize()
         step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
@@ -188,11 +189,11 @@ def run_gpu(args):
             t = torch.tensor([ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = float(t.item())
-        if args.only_step:
+        if args.only_step or args.log_kernel:
             if rank == 0:
                 print(json.dumps({"metric": METRIC, "value": round(N_POINTS * world / (ms * 1e-3) / 1e6, 2),
                                   "unit": UNIT, "ms_per_step": round(ms, 4), "nlevels": tuned,
-                                  "only_step": True}))
+                                  "kernel": "log" if args.log_kernel else "harmonic", "only_step": True}))
             return
 
         # --- phase times (events recorded by the library on the streams the kernels
@@ -498,6 +499,8 @@ def main():
     ap.add_argument("--no-theta-tune", action="store_true", help="skip the theta autotuning run")
     ap.add_argument("--only-step", action="store_true",
                     help="time the step only (no phase split, FP64 path, adjoint, e2e, accuracy); for profiling")
+    ap.add_argument("--log-kernel", action="store_true",
+                    help="time the logarithmic-kernel step only (as --only-step, with fmm_eval_log); for profiling")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -255,6 +255,39 @@ def run_gpu(args):
             s64.append(e0.elapsed_time(e1))
         ms64 = float(np.median(s64))
         err64 = _rel(phi64.cpu().numpy()[tg], exact) if rank == 0 else None
+        # the FP64 path at its own smallest p that meets the same 1e-5 on the sampled points
+        fp64_pmin = None
+        if rank == 0:
+            for pp in range(8, P_TERMS + 1):
+                t64.rebuild(X, p=pp)
+                t64.eval(G, out=phi64)
+                e_pp = _rel(phi64.cpu().numpy()[tg], exact)
+                if e_pp <= 1e-5:
+                    # N_levels re-chosen for this p: the FP64 balance of P2P and M2L differs from FP32's
+                    best = None
+                    for Lp in (tuned - 1, tuned, tuned + 1):
+                        if Lp < 1 or 4 ** (Lp - 1) > N_POINTS:
+                            continue
+                        t64.rebuild(X, nlevels=Lp)
+                        t64.eval(G, out=phi64)
+                        e_l = _rel(phi64.cpu().numpy()[tg], exact)
+                        sp = []
+                        for _ in range(3):
+                            flush.zero_()
+                            e0.record(stream)
+                            t64.rebuild(X)
+                            t64.eval(G, out=phi64)
+                            e1.record(stream)
+                            e1.synchronize()
+                            sp.append(e0.elapsed_time(e1))
+                        mp = float(np.median(sp))
+                        if e_l <= 1e-5 and (best is None or mp < best[0]):
+                            best = (mp, Lp, e_l)
+                    if best is not None:
+                        mp, Lp, e_l = best
+                        fp64_pmin = {"p": pp, "nlevels": Lp, "ms_per_step": round(mp, 4),
+                                     "value": round(N_POINTS / (mp * 1e-3) / 1e6, 2), "rel_err_sampled": e_l}
+                    break
         t64.close()
 
         # --- logarithmic kernel (Sec. 3.3) on the same tree and workload -----------
@@ -421,8 +454,8 @@ def run_gpu(args):
                          "in_step": {k: round(v, 4) for k, v in phases.items()},
                          "alone": {k: round(v, 4) for k, v in phases_alone.items()}},
         "eval_only_mpoints_s": round(N_POINTS / (eval_ms * 1e-3) / 1e6, 2),
-        "fp64_path": {"ms_per_step": round(ms64, 4), "value": round(N_POINTS / (ms64 * 1e-3) / 1e6, 2),
-                      "rel_err_sampled": err64},
+        "fp64_path": {"p": P_TERMS, "ms_per_step": round(ms64, 4), "value": round(N_POINTS / (ms64 * 1e-3) / 1e6, 2),
+                      "rel_err_sampled": err64, "smallest_p_within_1e-5": fp64_pmin},
         "rel_err_sampled": err32,
         "bwd_over_fwd": bwd_ratio,
         "log_kernel": log_kernel,

@@ -1,0 +1,121 @@
+"""Full-size workloads in the library's launch configuration, checked on sampled
+outputs against the oracle's exact sums (computed target by target): the
+dynamic sequence (N = 2e6 per snapshot, p in {12, 30}, both precision paths,
+the tree rebuilt for every snapshot), the batched forest (512 instances, about
+1.1e7 points, p = 16) and the differentiated workload (N = 1e6, adjoint)."""
+import numpy as np
+import pytest
+
+from paper_1311_1006_b300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def _trunc_tol(p, theta=0.5):
+    """3x the tolerance that Table 4.1's rule p = 0.9 ln TOL / ln theta assigns to p
+    (the rule reproduces the printed table to within one term)."""
+    return 3.0 * theta ** (p / 0.9)
+
+
+@pytest.mark.parametrize("p", [12, 30])
+def test_dynamic_snapshots_sampled(orc, p):
+    import paper_1311_1006_b300 as F
+
+    n = 2_000_000
+    pick = np.random.default_rng(p)
+    trees = {}
+    for k in (0, 9, 19):  # uniform, sigma = 0.027, sigma = 0.0029
+        g = W.rng(W.W_DYNAMIC, k)
+        xy = W.snapshot(n, k, g)
+        gam = W.uniform_real_strengths(n, g)
+        X, G = _dev(xy), _dev(gam)
+        tg = pick.choice(n, 256, replace=False)
+        exact = orc.direct(xy, gam, targets=tg)
+        for path in ("fp64", "fp32"):
+            L = F.default_nlevels(n, p, path)
+            if path not in trees:
+                trees[path] = F.Tree.build(X, p=p, theta=0.5, nlevels=L, path=path)
+            else:
+                trees[path].rebuild(X, nlevels=L)
+            phi = trees[path].eval(G).cpu().numpy().astype(np.complex128)
+            tol = _trunc_tol(p) if path == "fp64" else max(_trunc_tol(p), 1e-5)
+            err = _rel(phi[tg], exact)
+            assert err <= tol, (k, path, p, err, tol)
+    for t in trees.values():
+        t.close()
+
+
+def test_batched_forest_sampled(orc):
+    from paper_1311_1006_b300 import Tree
+
+    g = W.rng(W.W_BATCHED)
+    sizes = W.batch_sizes(512, g)
+    pts = [W.batch_instance(int(m), g) for m in sizes]
+    gam = [W.real_strengths(int(m), g) for m in sizes]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    xy, G = np.vstack(pts), np.concatenate(gam)
+    assert 0.5e7 < len(xy) < 2e7
+    t = Tree.build_batched(_dev(xy), offs, p=16, path="fp32")
+    phi = t.eval(_dev(G)).cpu().numpy().astype(np.complex128)
+    lev = t.export("inst")[:, 2]
+    pick = np.random.default_rng(4)
+    tol = max(_trunc_tol(16), 1e-5)
+    for b in pick.choice(512, 16, replace=False):
+        s, e = offs[b], offs[b + 1]
+        tg = pick.choice(e - s, min(64, e - s), replace=False)
+        exact = orc.direct(xy[s:e], G[s:e], targets=tg)
+        assert _rel(phi[s:e][tg], exact) <= tol, (b, sizes[b])
+    # an instance of the forest equals its standalone evaluation
+    for b in pick.choice(512, 4, replace=False):
+        s, e = offs[b], offs[b + 1]
+        tb = Tree.build(_dev(xy[s:e]), p=16, nlevels=int(lev[b]), path="fp32")
+        ref = tb.eval(_dev(G[s:e])).cpu().numpy().astype(np.complex128)
+        assert _rel(phi[s:e], ref) <= 1e-6
+        tb.close()
+    t.close()
+
+
+def test_differentiated_workload_sampled(orc):
+    """Adjoint at N = 1e6: sampled gradient within 1e-5 of the direct-sum gradient
+    and the backward pass at most 3x the forward evaluation."""
+    from paper_1311_1006_b300 import Tree
+
+    g = W.rng(W.W_DIFFERENTIATED)
+    n = 1_000_000
+    xy = W.uniform(n, g)
+    gam = W.real_strengths(n, g)
+    gphi = g.normal(size=n) + 1j * g.normal(size=n)
+    X, G, GP = _dev(xy), _dev(gam), _dev(gphi)
+    t = Tree.build(X, p=17, theta=0.5, path="fp32")
+    t.eval(G)
+    gg, gxy = t.backward(G, GP)
+    tg = np.random.default_rng(5).choice(n, 256, replace=False)
+    rg, rxy = orc.direct_grad(xy, gam, gphi, targets=tg)
+    assert _rel(gg.cpu().numpy()[tg], rg) <= 1e-5
+    assert _rel(gxy.cpu().numpy()[tg], rxy) <= 1e-5
+    # timing gate with CUDA events (medians of 5, after the warm-up above)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def _ms(fn):
+        ts = []
+        for _ in range(5):
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    fwd = _ms(lambda: t.eval(G))
+    bwd = _ms(lambda: t.backward(G, GP))
+    assert bwd <= 3.0 * fwd, (bwd, fwd)
+    t.close()

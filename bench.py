@@ -123,6 +123,24 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / np.abs(b).max())
 
 
+def _max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's value, on every rank (the value itself on one process)."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _whole_job_rate(units_per_rank: int, world: int, ms: float) -> float:
+    """Replicas: every rank processes units_per_rank per step; the whole job's
+    rate is the units all ranks processed over the slowest rank's step time
+    (millions per second)."""
+    return units_per_rank * world / (ms * 1e-3) / 1e6
+
+
 def run_gpu(args):
     import torch
 
@@ -183,15 +201,13 @@ def run_gpu(args):
                 step_eval(G, out=phi)
                 ends[k].record(stream)
             torch.cuda.synchronize()
-        step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-        ms = float(np.mean(step_ms))
         if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+            dist.barrier()
+        step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        ms = _max_over_ranks(float(np.mean(step_ms)), dist, dev)
         if args.only_step or args.log_kernel:
             if rank == 0:
-                print(json.dumps({"metric": METRIC, "value": round(N_POINTS * world / (ms * 1e-3) / 1e6, 2),
+                print(json.dumps({"metric": METRIC, "value": round(_whole_job_rate(N_POINTS, world, ms), 2),
                                   "unit": UNIT, "ms_per_step": round(ms, 4), "nlevels": tuned,
                                   "kernel": "log" if args.log_kernel else "harmonic", "only_step": True}))
             return
@@ -454,7 +470,7 @@ def run_gpu(args):
             dist.destroy_process_group()
         return
     peaks = _peaks()
-    value = N_POINTS * world / (ms * 1e-3) / 1e6
+    value = _whole_job_rate(N_POINTS, world, ms)
     clocks = clk.summary()
     # dominant kernel: P2P, bound by the FP32 pipe.  Peak = SMs x 256 flop/clk x
     # SM clock (the median sampled under load; also given at the 2032 MHz max).

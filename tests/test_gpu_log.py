@@ -152,3 +152,31 @@ def test_log_headline_workload_sampled(orc):
         err = _rel(phi[tg], exact)
         assert err < tol, (path, err)
         t.close()
+
+
+def test_log_batched_forest_equals_standalone(orc):
+    """fmm_eval_log on a forest of instances: each instance equals its own tree's
+    evaluation and the oracle's log-series FMM."""
+    from paper_1311_1006_b300 import Tree
+
+    g = np.random.default_rng(41)
+    sizes = [700, 3000, 1, 12000, 2500]
+    pts = [W.batch_instance(m, g) for m in sizes]
+    gam = np.concatenate([W.complex_strengths(m, g) for m in sizes])
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    xy = np.vstack(pts)
+    t = Tree.build_batched(_dev(xy), offs, p=16, path="fp64")
+    phi = t.eval_log(_dev(gam)).cpu().numpy()
+    lev = t.export("inst")[:, 2]
+    for b, m in enumerate(sizes):
+        s, e = offs[b], offs[b + 1]
+        tb = Tree.build(_dev(xy[s:e]), p=16, nlevels=int(lev[b]), path="fp64")
+        ref = tb.eval_log(_dev(gam[s:e])).cpu().numpy()
+        tb.close()
+        if m == 1:
+            assert np.all(phi[s:e] == 0) and np.all(ref == 0)
+            continue
+        assert np.abs(phi[s:e] - ref).max() <= 1e-12 * np.abs(ref).max()
+        ro = orc.fmm_log(xy[s:e], gam[s:e], int(lev[b]), 0.5, 16)
+        assert _rel(phi[s:e], ro) <= 1e-10
+    t.close()

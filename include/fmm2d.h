@@ -115,6 +115,17 @@ fmm_status fmm_eval(fmm_tree* t, const double* d_gamma, void* d_phi, void* strea
 /* Same as fmm_eval; rejects a tree that was not built by fmm_build_tree_batched. */
 fmm_status fmm_eval_batched(fmm_tree* t, const double* d_gamma, void* d_phi, void* stream);
 
+/* One time step: fmm_tree_rebuild(t, d_xy, NULL, stream) followed by
+ * fmm_eval(t, d_gamma, d_phi, stream), same arguments and the same result bit
+ * for bit, in one call that overlaps the two: the strength gather and the
+ * upward pass (P2M, M2M), which need the tree but not the coupling lists, run
+ * on the library's far-field stream while the lists are built.  Parameters
+ * stay as the tree has them (change them with fmm_tree_rebuild).  A batched
+ * tree, or a tree with FMM_FLAG_SERIAL, FMM_FLAG_TIMING or FMM_FLAG_GRAPH, runs
+ * the two calls in sequence.  Errors: INVALID_ARG (NULL, a tree built with
+ * separate evaluation points), CUDA, OOM, TIMEOUT, NONFINITE as the two calls. */
+fmm_status fmm_step(fmm_tree* t, const double* d_xy, const double* d_gamma, void* d_phi, void* stream);
+
 /* Logarithmic potential (Sec. 3.3 of the paper, the kernel it uses for
  * isopotential plots):
  *     Phi_i = sum_{j: z_j != z_i} Gamma_j ln|z_i - z_j|,

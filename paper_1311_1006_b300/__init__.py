@@ -168,6 +168,18 @@ class Tree:
         _lib.check(fn(self._h, g, o, _stream(stream)))
         return out
 
+    def step(self, xy, gamma, out=None, stream=None):
+        """fmm_step: rebuild for new coordinates and evaluate in one call (the upward
+        pass overlaps the list build); same result as rebuild() + eval()."""
+        torch = _torch()
+        p = _dev(xy, torch.float64, (self.n, 2), "xy")
+        g = _dev(gamma, torch.complex128, (self.n,), "gamma")
+        if out is None:
+            out = torch.empty(self.n, dtype=self.out_dtype, device=gamma.device)
+        o = _dev(out, self.out_dtype, (self.n,), "out")
+        _lib.check(_lib.load().fmm_step(self._h, p, g, o, _stream(stream)))
+        return out
+
     def eval_log(self, gamma, out=None, stream=None):
         """fmm_eval_log: the logarithmic potential sum_j Gamma_j ln|z_i - z_j| (Sec. 3.3)."""
         torch = _torch()

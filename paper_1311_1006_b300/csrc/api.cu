@@ -92,6 +92,7 @@ static fmm_status ensure_streams(Tree& t) {
     if (!t.s_far) FMM_CUDA(cudaStreamCreateWithPriority(&t.s_far, cudaStreamNonBlocking, hi_prio));
     if (!t.s_far2) FMM_CUDA(cudaStreamCreateWithPriority(&t.s_far2, cudaStreamNonBlocking, hi_prio));
     if (!t.ev_join_far2) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_join_far2, cudaEventDisableTiming));
+    if (!t.ev_gather) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_gather, cudaEventDisableTiming));
     if (!t.ev_fork) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_fork, cudaEventDisableTiming));
     if (!t.ev_join) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_join, cudaEventDisableTiming));
     if (!t.ev_join_far) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_join_far, cudaEventDisableTiming));
@@ -100,12 +101,12 @@ static fmm_status ensure_streams(Tree& t) {
     return FMM_OK;
 }
 
-// Tree build + lists + work items.  The first build learns the exact list
-// and item sizes from the device counters; a capacity that was too small is
-// grown (25 % slack) and the lists are rebuilt.
-static fmm_status build_all(Tree& t, const double* d_xy, cudaStream_t s) {
-    fmm_status st = run_tree_build(t, d_xy, s);
-    if (st) return st;
+// Lists + work items of a built tree, with the one host synchronisation of a
+// build: the first build learns the exact list and item sizes from the device
+// counters; a capacity that was too small is grown (25 % slack) and the lists
+// are rebuilt.
+static fmm_status build_lists(Tree& t, cudaStream_t s) {
+    fmm_status st;
     for (int attempt = 0; attempt < 16; ++attempt) {
         if ((st = run_lists(t, s))) return st;
         unsigned long long hbuf[5] = {0, 0, 0, 0, 0};
@@ -157,6 +158,13 @@ static fmm_status build_all(Tree& t, const double* d_xy, cudaStream_t s) {
     return FMM_ERR_OOM;
 }
 
+// Tree build + lists + work items.
+static fmm_status build_all(Tree& t, const double* d_xy, cudaStream_t s) {
+    fmm_status st = run_tree_build(t, d_xy, s);
+    if (st) return st;
+    return build_lists(t, s);
+}
+
 static fmm_status shape_and_build(Tree& t, const double* d_xy, cudaStream_t s, bool reshape) {
     fmm_status st;
     if (reshape) {
@@ -206,6 +214,7 @@ static void release(Tree* t) {
     if (t->s_far) cudaStreamDestroy(t->s_far);
     if (t->s_far2) cudaStreamDestroy(t->s_far2);
     if (t->ev_join_far2) cudaEventDestroy(t->ev_join_far2);
+    if (t->ev_gather) cudaEventDestroy(t->ev_gather);
     if (t->ev_join_far) cudaEventDestroy(t->ev_join_far);
     if (t->ev_fork) cudaEventDestroy(t->ev_fork);
     if (t->ev_join) cudaEventDestroy(t->ev_join);
@@ -418,6 +427,54 @@ fmm_status fmm_tree_rebuild(fmm_tree* h, const double* d_xy, const fmm_params* p
         if (old_flags != t.flags) invalidate_graph(t);
     }
     return shape_and_build(t, d_xy, static_cast<cudaStream_t>(stream), reshape);
+}
+
+// Rebuild + evaluate in one call.  The upward pass (strength gather, P2M,
+// M2M) needs the tree but not the coupling lists, so it runs on the far-field
+// stream while the lists are built on the caller's stream; after the build's
+// host check the downward pass follows on the far-field stream and P2P on the
+// low-priority stream, as in fmm_eval.  Same kernels in the same per-stream
+// order as fmm_tree_rebuild + fmm_eval, so the same result bit for bit.
+fmm_status fmm_step(fmm_tree* h, const double* d_xy, const double* d_gamma, void* d_phi, void* stream) {
+    if (!h || !d_xy || !d_gamma || !d_phi) return invalid("NULL argument");
+    Tree& t = h->t;
+    if (t.n_src > 0) return invalid("tree with separate evaluation points: use fmm_tree_rebuild_targets + fmm_eval_targets");
+    fmm_status st;
+    if (t.batched || (t.flags & (FMM_FLAG_SERIAL | FMM_FLAG_TIMING | FMM_FLAG_GRAPH))) {
+        // phase timing, the serial order and graph replay are defined on the two-call sequence
+        if ((st = fmm_tree_rebuild(h, d_xy, nullptr, stream))) return st;
+        return t.batched ? fmm_eval_batched(h, d_gamma, d_phi, stream) : fmm_eval(h, d_gamma, d_phi, stream);
+    }
+    if ((st = check_pending())) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((st = ensure_streams(t))) return st;
+    if ((st = run_tree_build(t, d_xy, s))) return st;
+    const unsigned gen = t.eval_gen;
+    if ((st = alloc_eval_core(t, 1))) return st;
+    const Bufs B = bufs(t, 0);
+    t.p2p_funcs.clear();
+    FMM_CUDA(cudaEventRecord(t.ev_fork, s));
+    FMM_CUDA(cudaStreamWaitEvent(t.s_far, t.ev_fork, 0));
+    launch_gather(t, B, d_gamma, t.s_far);
+    FMM_CUDA(cudaEventRecord(t.ev_gather, t.s_far));
+    dispatch_up(t, B, t.s_far);
+    if ((st = build_lists(t, s))) return st;  // host check; the upward pass runs meanwhile
+    // the partial-sum buffers follow the list capacities just learned: allocate them now and take the
+    // buffer table again (the one above predates them)
+    if ((st = alloc_eval_parts(t))) return st;
+    if (t.eval_gen != gen || refresh_grids(t)) invalidate_graph(t);
+    const Bufs Bd = bufs(t, 0);
+    dispatch_down(t, Bd, t.s_far);
+    FMM_CUDA(cudaEventRecord(t.ev_join_far, t.s_far));
+    FMM_CUDA(cudaStreamWaitEvent(t.s_aux, t.ev_gather, 0));  // slot-layout strengths; the lists are complete
+    launch_near(t, Bd, t.s_aux);
+    FMM_CUDA(cudaEventRecord(t.ev_join, t.s_aux));
+    FMM_CUDA(cudaStreamWaitEvent(s, t.ev_join_far, 0));
+    FMM_CUDA(cudaStreamWaitEvent(s, t.ev_join, 0));
+    launch_l2p_near(t, Bd, d_phi, s);
+    FMM_CUDA(cudaGetLastError());
+    t.timing_valid = false;
+    return FMM_OK;
 }
 
 void fmm_tree_destroy(fmm_tree* h) {

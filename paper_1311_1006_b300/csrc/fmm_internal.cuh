@@ -190,6 +190,7 @@ struct Tree {
     void* d_p2p_part = nullptr;  // partial P2P sums of split leaves (item x max_leaf)
     void* d_m2l_part = nullptr;  // partial M2L sums of split boxes (item x PS)
     long long part_p2p_cap = 0, part_m2l_cap = 0;
+    bool parts_stale = true;  // partial-sum buffers must be (re)allocated before use
     double2* d_M64 = nullptr;  // multipoles, scaled
     float2* d_M32 = nullptr;
     void* d_Lm2l = nullptr;    // M2L sums per box
@@ -205,6 +206,7 @@ struct Tree {
     cudaStream_t s_far = nullptr;  // far-field chain (highest priority)
     cudaStream_t s_far2 = nullptr;  // second strength set's far-field chain (log kernel, adjoint; highest priority)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join_far = nullptr, ev_join_far2 = nullptr;
+    cudaEvent_t ev_gather = nullptr;  // strengths gathered (fmm_step: P2P waits on it)
     cudaEvent_t ev_t[8] = {};
     bool timing_valid = false;
 
@@ -262,7 +264,9 @@ fmm_status alloc_lists(Tree& t);                                         // fixe
 fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s);  // sort, split, geometry
 fmm_status run_lists(Tree& t, cudaStream_t s);                           // strong / weak lists, work items
 fmm_status run_count(Tree& t, cudaStream_t s, unsigned long long out[2]);
-fmm_status alloc_eval(Tree& t, int sets);
+fmm_status alloc_eval(Tree& t, int sets);        // alloc_eval_core + alloc_eval_parts
+fmm_status alloc_eval_core(Tree& t, int sets);   // buffers that follow the tree shape and the expansion order
+fmm_status alloc_eval_parts(Tree& t);            // partial sums: follow the work-item capacities of the lists
 fmm_status run_eval(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s);
 fmm_status run_eval_log(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s);  // needs alloc_eval(t, 2)
 fmm_status run_backward(Tree& t, const double* d_gamma, const double* d_gphi, double* d_ggamma, double* d_gxy,
@@ -284,7 +288,12 @@ Bufs bufs(Tree& t, int set);
 bool refresh_grids(Tree& t);  // true when the P2P / M2L grids changed (the graph must be re-captured)
 long long p2p_grid_items(const Tree& t);
 long long m2l_grid_items(const Tree& t);
-void dispatch_far(Tree& t, const Bufs& B, cudaStream_t s, bool log_kernel = false);  // P2M, M2M, M2L, L2L of one strength set
+void dispatch_far(Tree& t, const Bufs& B, cudaStream_t s, bool log_kernel = false);
+void dispatch_up(Tree& t, const Bufs& B, cudaStream_t s);                          // P2M, M2M (tree only)
+void dispatch_down(Tree& t, const Bufs& B, cudaStream_t s, bool log_kernel = false);  // M2L .. L2L (lists)
+void launch_gather(Tree& t, const Bufs& B, const double* d_gamma, cudaStream_t s);
+void launch_near(Tree& t, const Bufs& B, cudaStream_t s);                      // harmonic P2P + ordered sums
+void launch_l2p_near(Tree& t, const Bufs& B, void* d_phi, cudaStream_t s);     // L2P + near + unpermute  // P2M, M2M, M2L, L2L of one strength set
 
 // FP32-path M2L on the tensor cores (m2l_tc.cu); FMM_M2L_TC=0 selects the CUDA-core kernel.
 bool m2l_tc_enabled();

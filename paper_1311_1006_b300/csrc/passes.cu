@@ -1208,8 +1208,9 @@ static const unsigned long long* item_count(const Tree& t, int which) {
     return reinterpret_cast<const unsigned long long*>(t.d_status) + 1 + which;  // 2 = P2P, 3 = M2L
 }
 
-template <int P, bool LOG>
-static void launch_far_fp32(Tree& t, const Bufs& B, cudaStream_t s) {
+// Upward pass (P2M, M2M): needs the tree, not the coupling lists.
+template <int P>
+static void launch_up_fp32(Tree& t, const Bufs& B, cudaStream_t s) {
     const float2* gam = static_cast<const float2*>(B.gam);
     k_p2m32<P><<<nblk(t.nleaf, 128), 128, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, t.d_bstart, t.d_bcount, t.d_chl,
                                                   t.d_rho32, t.d_pos4, gam, B.M32, t.p, t.PS);
@@ -1223,6 +1224,11 @@ static void launch_far_fp32(Tree& t, const Bufs& B, cudaStream_t s) {
             k_m2m<P><<<nblk(4 * (int64_t)L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_child0, t.d_rho,
                                                                      t.d_center, B.M32, B.M64, B.M32, 1, t.p, t.PS);
     }
+}
+
+// Downward pass (M2L, ordered M2L sums, L2L): needs the lists.
+template <int P, bool LOG>
+static void launch_down_fp32(Tree& t, const Bufs& B, cudaStream_t s) {
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[2], s);
     if (m2l_tc_enabled())
         launch_m2l_tc(t, B.M32, static_cast<float2*>(B.Lm2l), static_cast<float2*>(B.m2l_part), LOG, s);
@@ -1247,8 +1253,8 @@ static void launch_far_fp32(Tree& t, const Bufs& B, cudaStream_t s) {
     }
 }
 
-template <int P, bool LOG>
-static void launch_far_fp64(Tree& t, const Bufs& B, cudaStream_t s) {
+template <int P>
+static void launch_up_fp64(Tree& t, const Bufs& B, cudaStream_t s) {
     const double2* gam = static_cast<const double2*>(B.gam);
     k_p2m64<P><<<nblk(t.nleaf, 128), 128, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, t.d_bstart, t.d_bcount, t.d_center,
                                                   t.d_rho, t.d_pts, gam, B.M64, t.p, t.PS);
@@ -1263,6 +1269,10 @@ static void launch_far_fp64(Tree& t, const Bufs& B, cudaStream_t s) {
                                                                      t.d_center, nullptr, B.M64, nullptr, 0, t.p,
                                                                      t.PS);
     }
+}
+
+template <int P, bool LOG>
+static void launch_down_fp64(Tree& t, const Bufs& B, cudaStream_t s) {
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[2], s);
     k_m2l64<P, LOG><<<nblk(m2l_grid_items(t), 128), 128, 0, s>>>(t.d_m2l_items, item_count(t, 3), t.d_woff, t.d_widx,
                                                     t.d_center, t.d_rho, B.M64, static_cast<double2*>(B.Lm2l),
@@ -1396,10 +1406,15 @@ static void launch_p2p(Tree& t, const Bufs& B, cudaStream_t s) {
 #undef FMM_P2P
 }
 
+template <int P>
+static void launch_up(Tree& t, const Bufs& B, cudaStream_t s) {
+    if (t.path == FMM_PATH_FP32) launch_up_fp32<P>(t, B, s);
+    else launch_up_fp64<P>(t, B, s);
+}
 template <int P, bool LOG>
-static void launch_far(Tree& t, const Bufs& B, cudaStream_t s) {
-    if (t.path == FMM_PATH_FP32) launch_far_fp32<P, LOG>(t, B, s);
-    else launch_far_fp64<P, LOG>(t, B, s);
+static void launch_down(Tree& t, const Bufs& B, cudaStream_t s) {
+    if (t.path == FMM_PATH_FP32) launch_down_fp32<P, LOG>(t, B, s);
+    else launch_down_fp64<P, LOG>(t, B, s);
 }
 
 // Compiled expansion orders; a request for p runs the smallest compiled
@@ -1414,16 +1429,30 @@ int compiled_order(int p) {
     return -1;
 }
 
-void dispatch_far(Tree& t, const Bufs& B, cudaStream_t s, bool log_kernel) {
+void dispatch_up(Tree& t, const Bufs& B, cudaStream_t s) {
     switch (t.P) {
-#define FMM_CASE(Q)                                  \
-    case Q:                                          \
-        if (log_kernel) launch_far<Q, true>(t, B, s); \
-        else launch_far<Q, false>(t, B, s);           \
+#define FMM_CASE(Q) \
+    case Q: launch_up<Q>(t, B, s); break;
+        FMM_FOR_ORDERS(FMM_CASE)
+#undef FMM_CASE
+    }
+}
+
+void dispatch_down(Tree& t, const Bufs& B, cudaStream_t s, bool log_kernel) {
+    switch (t.P) {
+#define FMM_CASE(Q)                                   \
+    case Q:                                           \
+        if (log_kernel) launch_down<Q, true>(t, B, s); \
+        else launch_down<Q, false>(t, B, s);           \
         break;
         FMM_FOR_ORDERS(FMM_CASE)
 #undef FMM_CASE
     }
+}
+
+void dispatch_far(Tree& t, const Bufs& B, cudaStream_t s, bool log_kernel) {
+    dispatch_up(t, B, s);
+    dispatch_down(t, B, s, log_kernel);
 }
 
 static void dispatch_l2p(Tree& t, const Bufs& B, void* d_phi, cudaStream_t s) {
@@ -1460,13 +1489,16 @@ static fmm_status ralloc(T** p, size_t bytes) {
     return FMM_OK;
 }
 
-// Evaluation workspace: `sets` strength sets (1 forward, 2 adjoint).  Sizes
-// follow the tree shape, the expansion order and the work-item capacities;
-// the function is a no-op when nothing grew.
-fmm_status alloc_eval(Tree& t, int sets) {
+// Evaluation workspace: `sets` strength sets (1 forward, 2 adjoint and
+// logarithmic kernel).  The part that follows the tree shape and the
+// expansion order (strengths, expansions, near field, slot-layout strengths)
+// and the part that follows the work-item capacities of the coupling lists
+// (partial sums of split boxes) are allocated separately, so that an
+// evaluation can start on the tree before its lists exist.  Each is a no-op
+// when nothing grew.
+fmm_status alloc_eval_core(Tree& t, int sets) {
     if (t.eval_nbox == (size_t)t.nbox && t.eval_n == (size_t)t.n && t.eval_PS == t.PS && t.eval_path == t.path &&
-        t.eval_sets >= sets && t.part_p2p_cap >= t.p2p_cap && t.part_m2l_cap >= t.m2l_cap &&
-        t.eval_ts >= t.max_leaf && t.eval_slots == t.slot_alloc)
+        t.eval_sets >= sets && t.eval_slots == t.slot_alloc)
         return FMM_OK;
     sets = std::max(sets, t.eval_sets);
     ++t.eval_gen;
@@ -1480,8 +1512,6 @@ fmm_status alloc_eval(Tree& t, int sets) {
     if ((st = ralloc(&t.d_Lm2l, nb * PS * cs * sets))) return st;
     if ((st = ralloc(&t.d_M32, nb * PS * sizeof(float2) * sets))) return st;
     if ((st = ralloc(&t.d_L32, nb * PS * sizeof(float2) * sets))) return st;
-    if ((st = ralloc(&t.d_p2p_part, (size_t)t.p2p_cap * t.max_leaf * sizeof(double2) * 3))) return st;
-    if ((st = ralloc(&t.d_m2l_part, (size_t)t.m2l_cap * PS * cs * sets))) return st;
     if (t.path == FMM_PATH_FP32 && m2l_tc_enabled() && (st = m2l_tc_prepare(t.P))) return st;
     // strengths in the slot layout: padding slots keep strength zero
     if ((st = ralloc(&t.d_gamp, (size_t)t.slot_alloc * cs))) return st;
@@ -1490,16 +1520,51 @@ fmm_status alloc_eval(Tree& t, int sets) {
     // root locals are never written by the passes: they stay zero
     FMM_CUDA(cudaMemset(t.d_L64, 0, nb * PS * sizeof(double2) * sets));
     FMM_CUDA(cudaMemset(t.d_L32, 0, nb * PS * sizeof(float2) * sets));
-    t.part_p2p_cap = t.p2p_cap;
-    t.part_m2l_cap = t.m2l_cap;
-    t.eval_ts = t.max_leaf;
     t.eval_nbox = nb;
     t.eval_n = n;
     t.eval_PS = t.PS;
     t.eval_path = t.path;
     t.eval_sets = sets;
+    t.parts_stale = true;  // the partial sums follow the new set count / stride
     return FMM_OK;
 }
+
+fmm_status alloc_eval_parts(Tree& t) {
+    if (!t.parts_stale && t.part_p2p_cap >= t.p2p_cap && t.part_m2l_cap >= t.m2l_cap && t.eval_ts >= t.max_leaf)
+        return FMM_OK;
+    ++t.eval_gen;
+    const size_t PS = (size_t)t.PS;
+    const size_t cs = t.path == FMM_PATH_FP32 ? sizeof(float2) : sizeof(double2);
+    fmm_status st;
+    if ((st = ralloc(&t.d_p2p_part, (size_t)t.p2p_cap * t.max_leaf * sizeof(double2) * 3))) return st;
+    if ((st = ralloc(&t.d_m2l_part, (size_t)t.m2l_cap * PS * cs * t.eval_sets))) return st;
+    t.part_p2p_cap = t.p2p_cap;
+    t.part_m2l_cap = t.m2l_cap;
+    t.eval_ts = t.max_leaf;
+    t.parts_stale = false;
+    return FMM_OK;
+}
+
+fmm_status alloc_eval(Tree& t, int sets) {
+    fmm_status st = alloc_eval_core(t, sets);
+    if (st) return st;
+    return alloc_eval_parts(t);
+}
+
+// Strengths of one evaluation into sorted order and into the leaf slot layout.
+void launch_gather(Tree& t, const Bufs& B, const double* d_gamma, cudaStream_t s) {
+    const int n = (int)t.n;
+    const double2* gin = reinterpret_cast<const double2*>(d_gamma);
+    if (t.path == FMM_PATH_FP32)
+        k_gather32<<<nblk(n, 256), 256, 0, s>>>(gin, t.d_perm, t.d_slot_of, n, static_cast<float2*>(B.gam),
+                                                static_cast<float*>(t.d_gamp));
+    else
+        k_gather64<<<nblk(n, 256), 256, 0, s>>>(gin, t.d_perm, t.d_slot_of, n, static_cast<double2*>(B.gam),
+                                                static_cast<double2*>(t.d_gamp));
+}
+
+void launch_near(Tree& t, const Bufs& B, cudaStream_t s) { launch_p2p<false>(t, B, s); }
+void launch_l2p_near(Tree& t, const Bufs& B, void* d_phi, cudaStream_t s) { dispatch_l2p(t, B, d_phi, s); }
 
 // One evaluation: gather strengths into sorted order, then fork P2P onto the
 // auxiliary stream while the far field (P2M, M2M, M2L, L2L) runs on the
@@ -1510,14 +1575,8 @@ fmm_status run_eval(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s)
     const bool timing = t.flags & FMM_FLAG_TIMING;
     const bool serial = t.flags & FMM_FLAG_SERIAL;
     if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[0], s));
-    const double2* gin = reinterpret_cast<const double2*>(d_gamma);
     const Bufs B = bufs(t, 0);
-    if (t.path == FMM_PATH_FP32)
-        k_gather32<<<nblk(n, 256), 256, 0, s>>>(gin, t.d_perm, t.d_slot_of, n, static_cast<float2*>(B.gam),
-                                                static_cast<float*>(t.d_gamp));
-    else
-        k_gather64<<<nblk(n, 256), 256, 0, s>>>(gin, t.d_perm, t.d_slot_of, n, static_cast<double2*>(B.gam),
-                                                static_cast<double2*>(t.d_gamp));
+    launch_gather(t, B, d_gamma, s);
     if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[1], s));
     if (!serial) {
         FMM_CUDA(cudaEventRecord(t.ev_fork, s));

@@ -682,46 +682,41 @@ __device__ __forceinline__ void box_geometry(int b, double x0, double x1, double
                          __double2float_rn(__dsub_rn(ey, (double)hy)));
 }
 
-__device__ __forceinline__ int seg_of(const uint16_t* __restrict__ st, int nseg, int i) {
-    int lo = 0, hi = nseg - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (st[mid] <= i) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-// Stable partition of lin (n local ids) by side[id] within the segments
-// st[0..nseg) (segment k keeps its first nz[k] zeros first).
-__device__ __forceinline__ void cta_partition(const uint16_t* lin, uint16_t* lout, const uint8_t* side, int n,
-                                              const uint16_t* st, const uint16_t* nz, int nseg, uint16_t* P,
+// Stable partition of lin (n local ids) within segments st[0..nseg): code[id]
+// = 2 * (segment of id) + side of id; segment k keeps its side-0 entries
+// first (the first nz[k] positions), both sides in their input order.  A thread
+// keeps the running prefix of side-1 entries of its own positions in
+// registers; segpre[k] receives the prefix at segment k's first position.
+__device__ __forceinline__ void cta_partition(const uint16_t* lin, uint16_t* lout, int n, const uint16_t* st,
+                                              const uint16_t* nz, const uint16_t* code, uint16_t* segpre,
                                               int* wsum) {
     const int i0 = threadIdx.x * kSubItems;
-    int f[kSubItems];
+    int c[kSubItems];
     int sum = 0;
 #pragma unroll
     for (int k = 0; k < kSubItems; ++k) {
         const int i = i0 + k;
-        f[k] = i < n ? side[lin[i]] : 0;
-        sum += f[k];
+        c[k] = i < n ? code[lin[i]] : 0;
+        sum += c[k] & 1;
     }
     int total;
     int acc = block_excl_scan(sum, wsum, total);
+    int pre[kSubItems];
 #pragma unroll
     for (int k = 0; k < kSubItems; ++k) {
-        if (i0 + k < n) P[i0 + k] = (uint16_t)acc;
-        acc += f[k];
+        pre[k] = acc;
+        if (i0 + k < n && st[c[k] >> 1] == i0 + k) segpre[c[k] >> 1] = (uint16_t)acc;
+        acc += c[k] & 1;
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kSubItems; ++k) {
         const int i = i0 + k;
         if (i >= n) break;
-        const int sgi = seg_of(st, nseg, i);
+        const int sgi = c[k] >> 1;
         const int s0 = st[sgi];
-        const int ones = (int)P[i] - (int)P[s0];
-        const int dst = f[k] ? s0 + nz[sgi] + ones : s0 + (i - s0) - ones;
+        const int ones = pre[k] - (int)segpre[sgi];
+        const int dst = (c[k] & 1) ? s0 + nz[sgi] + ones : s0 + (i - s0) - ones;
         if (dst >= 0 && dst < n) lout[dst] = lin[i];
     }
     __syncthreads();
@@ -734,9 +729,10 @@ __global__ void __launch_bounds__(kSubThreads) k_subtree(
     int32_t* __restrict__ loc, double2* center, double* radius, double* rho, float4* chl, float* rho32, float* rad32,
     unsigned* status) {
     __shared__ uint16_t buf[3][kSubMax];
-    __shared__ uint16_t P[kSubMax];
-    __shared__ uint8_t side[kSubMax];
-    __shared__ uint16_t st[kSubSegs], nz[kSubSegs];
+    // per local id: its box (then half box) numbered within the subtree level, and during a split
+    // 2 * that + the side it goes to
+    __shared__ uint16_t bid[kSubMax];
+    __shared__ uint16_t st[kSubSegs], nz[kSubSegs], segpre[kSubSegs];
     __shared__ int wsum[32];
     if (blockIdx.x >= cnt) return;
     const int B = ids[blockIdx.x];
@@ -760,6 +756,7 @@ __global__ void __launch_bounds__(kSubThreads) k_subtree(
     for (int i = threadIdx.x; i < n; i += kSubThreads) {
         loc[X[s + i]] = i;
         xl[i] = (uint16_t)i;
+        bid[i] = 0;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += kSubThreads) yl[i] = (uint16_t)loc[Y[s + i]];
@@ -778,11 +775,12 @@ __global__ void __launch_bounds__(kSubThreads) k_subtree(
         }
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += kSubThreads) {
-            const int k = seg_of(st, (int)width, i);
-            side[xl[i]] = (uint8_t)((i - st[k]) >= nz[k]);
+            const int id = xl[i];
+            const int k = bid[id];
+            bid[id] = (uint16_t)(2 * k + ((i - st[k]) >= nz[k]));  // box k's left / right half: 2k / 2k+1
         }
         __syncthreads();
-        cta_partition(yl, tp, side, n, st, nz, (int)width, P, wsum);  // tp = new y-list
+        cta_partition(yl, tp, n, st, nz, bid, segpre, wsum);  // tp = new y-list
         // y-split of every half: segments = half boxes
         for (int k = threadIdx.x; k < width; k += kSubThreads) {
             const int bs = bstart[gb0 + k] - s, bn = bcount[gb0 + k], nl = bn / 2;
@@ -797,11 +795,13 @@ __global__ void __launch_bounds__(kSubThreads) k_subtree(
         }
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += kSubThreads) {
-            const int k = seg_of(st, 2 * (int)width, i);
-            side[tp[i]] = (uint8_t)((i - st[k]) >= nz[k]);
+            const int id = tp[i];
+            const int k = bid[id];
+            // half box k's bottom / top: 2k / 2k+1 = 4 (box) + 2 (x side) + (y side), the order lb, lt, rb, rt
+            bid[id] = (uint16_t)(2 * k + ((i - st[k]) >= nz[k]));
         }
         __syncthreads();
-        cta_partition(xl, yl, side, n, st, nz, 2 * (int)width, P, wsum);  // old y-list buffer = new x-list
+        cta_partition(xl, yl, n, st, nz, bid, segpre, wsum);  // old y-list buffer = new x-list
         {
             uint16_t* nx = yl;
             uint16_t* ny = tp;

@@ -57,6 +57,7 @@ constexpr int kP2PItemSources = 2048;
 constexpr int kMaxLevels = 16;
 constexpr int kSubMax = 4096;  // largest box whose remaining splits one CTA performs in shared memory
 constexpr int kM2LItemPairs = 64;
+constexpr int kM2LTcRows = 128;  // work items (MMA rows) per CTA of the tensor-core M2L
 
 // Partition tile: 256 threads x 8 consecutive positions.
 constexpr int kPartThreads = 256;

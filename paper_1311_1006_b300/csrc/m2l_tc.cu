@@ -45,7 +45,7 @@
 namespace fmm {
 namespace {
 
-constexpr int kTcThreads = 128;  // = MMA rows M = items per CTA
+constexpr int kTcThreads = kM2LTcRows;  // = MMA rows M = items per CTA
 constexpr int kTabN = 32;        // B table covers k, l < 32 (orders up to 32)
 
 // ---- B = C(k+l, l) split into TF32 hi + lo, evaluated at compile time -------
@@ -245,8 +245,8 @@ template <int P, bool LOG>
 __global__ void __launch_bounds__(kTcThreads, P <= 18 ? 3 : 2)
     k_m2l_tc(const int4* __restrict__ items, const unsigned long long* __restrict__ nitems,
              const int32_t* __restrict__ woff, const int32_t* __restrict__ widx, const float4* __restrict__ chl,
-             const float* __restrict__ rho32, const float2* __restrict__ M32, float2* __restrict__ Lm2l,
-             float2* __restrict__ part, int PS, unsigned* status) {
+             const float* __restrict__ rho32, const float2* __restrict__ M32, const int2* __restrict__ box_m2l,
+             float2* __restrict__ Lm2l, float2* __restrict__ part, int PS, unsigned* status) {
     using S = TcShape<P>;
     constexpr int KT = S::KT, NT = S::NT, KW = S::KW, B_FLOATS = S::B_FLOATS, COL_D = S::COL_D;
     constexpr int NA = (P + 1) / 2;  // float4 loads of one multipole (PS even)
@@ -476,11 +476,42 @@ __global__ void __launch_bounds__(kTcThreads, P <= 18 ? 3 : 2)
         if (tid == 0) atomicOr(status, ST_TIMEOUT);
         return;
     }
-    if (!has) return;
-    float2* out = item.w < 0 ? Lm2l + (size_t)b * PS : part + (size_t)it * PS;
+    // Boxes whose weak list was split into several items: when all of a box's
+    // items are rows of this CTA, its rows add them up here, each coefficient in
+    // item order (the order of the separate partial-sum pass); other split boxes
+    // write their partial sums for k_reduce_m2l_edges.
+    constexpr int NC = LOG ? P + 1 : P;
+    __shared__ float2 sacc[kTcThreads][NC];
 #pragma unroll
-    for (int l = 0; l < P; ++l) out[l] = acc[l];
-    if constexpr (LOG) out[P] = make_float2(b0, 0.f);
+    for (int l = 0; l < P; ++l) sacc[tid][l] = acc[l];
+    if constexpr (LOG) sacc[tid][P] = make_float2(b0, 0.f);
+    __syncthreads();
+    if (!has) return;
+    const int it0 = blockIdx.x * kTcThreads;
+    if (item.w < 0) {
+        float2* out = Lm2l + (size_t)b * PS;
+#pragma unroll
+        for (int l = 0; l < NC; ++l) out[l] = sacc[tid][l];
+        return;
+    }
+    const int first = item.w, km = box_m2l[b].y;
+    if (first >= it0 && first + km <= it0 + kTcThreads) {
+        // the box's km rows share its coefficients: row q adds coefficients q, q + km, ...
+        float2* out = Lm2l + (size_t)b * PS;
+        for (int l = it - first; l < NC; l += km) {
+            float2 sum = make_float2(0.f, 0.f);
+            for (int q = 0; q < km; ++q) {
+                const float2 v = sacc[first - it0 + q][l];
+                sum.x += v.x;
+                sum.y += v.y;
+            }
+            out[l] = sum;
+        }
+        return;
+    }
+    float2* out = part + (size_t)it * PS;
+#pragma unroll
+    for (int l = 0; l < NC; ++l) out[l] = sacc[tid][l];
 }
 
 template <int P, bool LOG>
@@ -488,7 +519,7 @@ void launch_tc(const Tree& t, const float2* M32, float2* Lm2l, float2* part, cud
     const int grid = static_cast<int>(std::max<long long>((m2l_grid_items(t) + kTcThreads - 1) / kTcThreads, 1));
     k_m2l_tc<P, LOG><<<grid, kTcThreads, TcShape<P>::SMEM, s>>>(
         t.d_m2l_items, reinterpret_cast<const unsigned long long*>(t.d_status) + 4, t.d_woff, t.d_widx, t.d_chl,
-        t.d_rho32, M32, Lm2l, part, t.PS, t.d_status);
+        t.d_rho32, M32, t.d_box_m2l, Lm2l, part, t.PS, t.d_status);
 }
 
 template <int P>

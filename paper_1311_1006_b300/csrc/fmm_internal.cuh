@@ -53,7 +53,7 @@ inline int leaf_capacity(int max_leaf) {
 
 // Work-item sizes: P2P items hold about this many source points; M2L items at
 // most this many weak pairs.
-constexpr int kP2PItemSources = 2048;
+constexpr int kP2PItemSources = 4096;
 constexpr int kMaxLevels = 16;
 constexpr int kSubMax = 4096;  // largest box whose remaining splits one CTA performs in shared memory
 constexpr int kM2LItemPairs = 64;

@@ -1359,8 +1359,11 @@ static void launch_l2p_log(Tree& t, const Bufs& B0, const Bufs& B1, void* d_phi,
 // Work items one P2P warp takes before it exits (FMM_P2P_ITEMS_PER_WARP
 // overrides; 0 = persistent grid of FMM_P2P_BLOCKS_PER_SM blocks per SM).
 // Bounded warps let blocks retire during the pass, so the far-field kernels
-// on the high-priority stream get SM slots while P2P runs.
-constexpr int kP2PItemsPerWarp = 4;
+// on the high-priority stream get SM slots while P2P runs.  Measured on the
+// 1e6-point workload: items of up to 4096 sources, one per warp, beat items of
+// 2048 sources four per warp (fewer split leaves, so fewer partial sums;
+// evaluation 2.16 -> 2.11 ms) and items of 8192 sources.
+constexpr int kP2PItemsPerWarp = 1;
 static int env_int(const char* name, int dflt) {
     const char* e = getenv(name);
     return e ? atoi(e) : dflt;

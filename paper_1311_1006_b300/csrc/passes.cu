@@ -634,7 +634,7 @@ __global__ void __launch_bounds__(128) k_l2l_warp(const int32_t* __restrict__ bo
 }
 
 // Levels with at most this many shifts use the warp-per-shift kernels.
-constexpr int kWarpShiftMax = 1024;
+constexpr int kWarpShiftMax = 1024;  // measured against 4096 and 16384: 1024 fastest
 
 // ------------------------------------------------------------- L2P + sum
 

@@ -182,7 +182,7 @@ static void release(Tree* t) {
     invalidate_graph(*t);
     void* ptrs[] = {t->d_bstart, t->d_bcount, t->d_parent, t->d_child0, t->d_inst, t->d_inst_ptoff,
                     t->d_inst_boxoff, t->d_leaf_start, t->d_inst_levels, t->d_loc, t->d_X2, t->d_Y2, t->d_sideX, t->d_sideY, t->d_part_stat,
-                    t->d_sort_hist, t->d_sort_tot, t->d_sort_off, t->d_perm,
+                    t->d_sort_hist, t->d_sort_tot, t->d_sort_off, t->d_sort_os, t->d_perm,
                     t->d_leaf_of, t->d_pts, t->d_pos4, t->d_center, t->d_radius, t->d_rho, t->d_chl, t->d_rho32,
                     t->d_rad32, t->d_soff, t->d_ns, t->d_sidx, t->d_srng, t->d_sowner, t->d_ltstat,
                     t->d_lvl_base, t->d_woff, t->d_nw, t->d_widx, t->d_p2p_items,

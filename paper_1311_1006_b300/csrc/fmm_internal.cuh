@@ -140,6 +140,7 @@ struct Tree {
     int32_t* d_loc = nullptr;  // input index -> local id inside a subtree CTA
     unsigned long long* d_part_stat = nullptr;  // partition: tile status words + tile ticket
     int32_t *d_sort_hist = nullptr, *d_sort_tot = nullptr, *d_sort_off = nullptr;
+    unsigned* d_sort_os = nullptr;  // onesweep sort: global digit counts, tickets, tile status words
     int64_t segs_cap = 0;
 
     // tree data

@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(kPartThreads) k_part_fused(
     const int32_t* __restrict__ A, const uint8_t* __restrict__ side, int n, const int32_t* __restrict__ start,
     const int32_t* __restrict__ nzero, const int32_t* __restrict__ obefore, int K, int32_t* __restrict__ out,
     const int32_t* __restrict__ nstart, const int32_t* __restrict__ nnzero, int nK, uint8_t* __restrict__ side_next,
-    unsigned long long* tstat, int T, unsigned* status) {
+    int direct_next, unsigned long long* tstat, int T, unsigned* status) {
     __shared__ int wsum[32];
     __shared__ int sh_tile;
     __shared__ long long sh_excl;
@@ -702,7 +702,9 @@ __global__ void __launch_bounds__(kPartThreads) k_part_fused(
             if (dst >= s && dst < e) {
                 out[dst] = a[j];
                 if (side_next) {
-                    const int kn = find_seg(nstart, nK, dst);
+                    // one tree: segment k's side-f part is segment 2k + f of the next stage (a box's halves,
+                    // a half box's bottom / top); a forest's finished instances keep one segment: search
+                    const int kn = direct_next ? 2 * k + f[j] : find_seg(nstart, nK, dst);
                     side_next[a[j]] = (uint8_t)((dst - nstart[kn]) >= nnzero[kn]);
                 }
             } else {
@@ -723,8 +725,8 @@ static fmm_status partition(Tree& t, cudaStream_t s, const int32_t* A, const uin
     const int grid = std::min(T, t.num_sms * 4);
     k_part_fused<<<grid, kPartThreads, 0, s>>>(A, side, n, seg.d_start, seg.d_nzero, seg.d_obefore, seg.K, out,
                                                next ? next->d_start : nullptr, next ? next->d_nzero : nullptr,
-                                               next ? next->K : 0, next ? side_next : nullptr, t.d_part_stat, T,
-                                               t.d_status);
+                                               next ? next->K : 0, next ? side_next : nullptr, t.ninst == 1 ? 1 : 0,
+                                               t.d_part_stat, T, t.d_status);
     FMM_CUDA(cudaGetLastError());
     return FMM_OK;
 }

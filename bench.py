@@ -435,9 +435,24 @@ def run_gpu(args):
             th, L2 = THETA, tuned
             pp = F.p_for_tolerance(tol, th)
             tt = F.Tree.build(X, p=pp, theta=th, nlevels=L2, path="fp32")
+            ph = torch.empty(N_POINTS, dtype=torch.complex64, device=dev)
+
+            def _tt_ms():
+                ms_ = []
+                for _ in range(10):
+                    flush.zero_()
+                    e0.record(stream)
+                    tt.rebuild(X)
+                    tt.eval(G, out=ph)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms_.append(e0.elapsed_time(e1))
+                return float(np.median(ms_))
+
+            tt.eval(G, out=ph)
+            start_ms = _tt_ms()  # the starting point (theta of the workload, p from the tolerance rule)
             tt.autotune_config(cap=0.2, window=2, period=2)
             tt.autotune_theta(tol, 0.35, 0.65)
-            ph = torch.empty(N_POINTS, dtype=torch.complex64, device=dev)
             for _ in range(60):
                 e0.record(stream)
                 tt.rebuild(X, nlevels=L2, theta=th, p=pp)
@@ -450,22 +465,16 @@ def run_gpu(args):
             pp = F.p_for_tolerance(tol, th)
             tt.rebuild(X, nlevels=L2, theta=th, p=pp)
             tt.eval(G, out=ph)
-            tts = []
-            for _ in range(10):
-                flush.zero_()
-                e0.record(stream)
-                tt.rebuild(X)
-                tt.eval(G, out=ph)
-                e1.record(stream)
-                e1.synchronize()
-                tts.append(e0.elapsed_time(e1))
+            tuned_ms = _tt_ms()
             import oracle as _orc
 
             tg2 = np.random.default_rng(8).choice(N_POINTS, 1024, replace=False)
             ex2 = _orc.direct(xy, gam, targets=tg2)
             theta_tune = {"tol": tol, "theta": round(th, 4), "p": pp, "nlevels": L2,
-                          "ms_per_step": round(float(np.median(tts)), 4),
-                          "value": round(N_POINTS / (float(np.median(tts)) * 1e-3) / 1e6, 2),
+                          "ms_per_step": round(tuned_ms, 4),
+                          "value": round(N_POINTS / (tuned_ms * 1e-3) / 1e6, 2),
+                          "start": {"theta": THETA, "p": F.p_for_tolerance(tol, THETA), "nlevels": tuned,
+                                    "ms_per_step": round(start_ms, 4)},
                           "rel_err_sampled": _rel(ph.cpu().numpy().astype(np.complex128)[tg2], ex2),
                           "tuning_steps": 60}
             tt.close()

@@ -657,10 +657,21 @@ fmm_status fmm_tree_export(const fmm_tree* h, int what, void* h_dst, int64_t cou
         case FMM_EXPORT_CENTER: return copy(t.d_center, 2 * nb, 8);
         case FMM_EXPORT_RADIUS: return copy(t.d_radius, nb, 8);
         case FMM_EXPORT_RHO: return copy(t.d_rho, nb, 8);
-        case FMM_EXPORT_NSTRONG: return copy(t.d_ns, nb, 4);
+        case FMM_EXPORT_NSTRONG:
+        case FMM_EXPORT_NWEAK: {  // the device keeps each list's end: length = end - first entry
+            const bool strong = what == FMM_EXPORT_NSTRONG;
+            fmm_status st = copy(strong ? t.d_ns : t.d_nw, nb, 4);
+            if (st) return st;
+            std::vector<int32_t> off((size_t)nb);
+            FMM_CUDA(cudaMemcpyAsync(off.data(), strong ? t.d_soff : t.d_woff, (size_t)nb * 4,
+                                     cudaMemcpyDeviceToHost, s));
+            FMM_CUDA(cudaStreamSynchronize(s));
+            int32_t* o = static_cast<int32_t*>(h_dst);
+            for (int64_t b = 0; b < nb; ++b) o[b] -= off[(size_t)b];
+            return FMM_OK;
+        }
         case FMM_EXPORT_STRONG_OFF: return copy(t.d_soff, nb, 4);
         case FMM_EXPORT_STRONG: return copy(t.d_sidx, (int64_t)t.h_counts[0], 4);
-        case FMM_EXPORT_NWEAK: return copy(t.d_nw, nb, 4);
         case FMM_EXPORT_WEAK_OFF: return copy(t.d_woff, nb, 4);
         case FMM_EXPORT_WEAK: return copy(t.d_widx, (int64_t)t.h_counts[1], 4);
         case FMM_EXPORT_INST: {

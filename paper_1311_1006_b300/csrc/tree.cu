@@ -1026,7 +1026,7 @@ __global__ void k_lists_root(const int64_t* __restrict__ inst_box_off, int ninst
     if (b >= ninst) return;
     const int r = (int)inst_box_off[b];
     soff[r] = b;
-    ns[r] = 1;
+    ns[r] = b + 1;  // list ends (lengths are end - first entry)
     sidx[b] = r;
     sowner[b] = r;
     woff[r] = 0;
@@ -1085,7 +1085,7 @@ __device__ __forceinline__ CandGroup decode_group(long long q, long long base_pr
         c.first = c.last = false;
         return c;
     }
-    const int n = ns[P];
+    const int n = ns[P] - soff[P];
     const long long e0 = (long long)soff[P] - base_prev;
     const int r = (int)(q - 4 * e0);  // (child index) * n + j
     const int ci = r / n, j = r - ci * n;
@@ -1215,21 +1215,11 @@ __global__ void __launch_bounds__(kLThreads) k_lists_level(
                 }
             }
             if (c.last) {
-                ns[c.b] = (int32_t)(bs + ps);  // end; made a length by k_lists_len
+                ns[c.b] = (int32_t)(bs + ps);  // list end
                 nw[c.b] = (int32_t)(bw + pw);
             }
         }
     }
-}
-
-__global__ void k_lists_len(const int32_t* __restrict__ ids, int cnt, const int32_t* __restrict__ soff,
-                            int32_t* ns, const int32_t* __restrict__ woff, int32_t* nw, unsigned* status) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= cnt) return;
-    if (*((volatile unsigned*)status) & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW)) return;
-    const int b = ids[q];
-    ns[b] -= soff[b];
-    nw[b] -= woff[b];
 }
 
 // Work items that bound the work of one warp / thread whatever the list
@@ -1256,7 +1246,8 @@ __device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* c
 }
 
 __global__ void k_items(int nbox, const int32_t* __restrict__ child0, const int32_t* __restrict__ bcount,
-                        const int32_t* __restrict__ ns, const int32_t* __restrict__ nw, unsigned long long* ctr,
+                        const int32_t* __restrict__ soff, const int32_t* __restrict__ ns,
+                        const int32_t* __restrict__ woff, const int32_t* __restrict__ nw, unsigned long long* ctr,
                         int4* p2p_items, int2* leaf_items, long long p2p_cap, int4* m2l_items, int2* box_m2l,
                         long long m2l_cap, unsigned* status) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1265,7 +1256,7 @@ __global__ void k_items(int nbox, const int32_t* __restrict__ child0, const int3
     const bool leaf = in && child0[b] < 0;
     int kp = 0, C = 1, n = 0;
     if (leaf) {
-        n = ns[b];
+        n = ns[b] - soff[b];
         C = max(1, kP2PItemSources / max(bcount[b], 1));
         kp = (n + C - 1) / C;
     }
@@ -1279,7 +1270,7 @@ __global__ void k_items(int nbox, const int32_t* __restrict__ child0, const int3
                 p2p_items[bp + c] = make_int4(b, c * C, min(n, (c + 1) * C), kp > 1 ? (int)bp : -1);
         }
     }
-    const int m = in ? nw[b] : 0;
+    const int m = in ? nw[b] - woff[b] : 0;
     const int km = (m + kM2LItemPairs - 1) / kM2LItemPairs;
     const unsigned long long bm = warp_reserve(ctr + 3, km);
     if (!in) return;
@@ -1300,7 +1291,7 @@ __global__ void k_count(const int32_t* __restrict__ leaf_ids, int nleaf, const i
     unsigned long long sl = 0, pp = 0;
     if (q < nleaf) {
         const int b = leaf_ids[q];
-        const int n = ns[b];
+        const int n = ns[b] - soff[b];
         sl = n;
         unsigned long long src = 0;
         for (int j = 0; j < n; ++j) src += bcount[sidx[soff[b] + j]];
@@ -1402,7 +1393,7 @@ fmm_status alloc_lists(Tree& t) {
     if ((st = dalloc(&t.d_sowner, (size_t)t.scap_tot))) return st;
     if ((st = dalloc(&t.d_srng, (size_t)t.scap_tot))) return st;
     const size_t tiles = (size_t)(t.cand_cap / kLTile + 2);
-    if ((st = dalloc(&t.d_ltstat, 2 * tiles + 1))) return st;
+    if ((st = dalloc(&t.d_ltstat, (2 * tiles + 1) * (size_t)std::max(t.Lmax - 1, 1)))) return st;  // one region per level
     if ((st = dalloc(&t.d_widx, (size_t)t.wcap_tot))) return st;
     if ((st = dalloc(&t.d_p2p_items, (size_t)t.p2p_cap))) return st;
     if ((st = dalloc(&t.d_m2l_items, (size_t)t.m2l_cap))) return st;
@@ -1491,18 +1482,19 @@ fmm_status run_lists(Tree& t, cudaStream_t s) {
                                                     t.d_woff, t.d_nw, t.d_lvl_base, t.d_child0, t.d_pslot,
                                                     t.d_bcount, t.d_srng);
     const long long tiles_cap = t.cand_cap / kLTile + 2;
+    const size_t lstride = (size_t)(2 * tiles_cap + 1);  // status words + ticket of one level
     const int grid = t.num_sms * 8;
+    FMM_CUDA(cudaMemsetAsync(t.d_ltstat, 0, lstride * (size_t)std::max(t.Lmax - 1, 1) * sizeof(unsigned long long),
+                             s));
     for (int l = 1; l < t.Lmax; ++l) {
-        FMM_CUDA(cudaMemsetAsync(t.d_ltstat, 0, (size_t)(2 * tiles_cap + 1) * sizeof(unsigned long long), s));
         k_lists_level<<<grid, kLThreads, 0, s>>>(l, t.d_lvl_base, t.d_sowner, t.d_soff, t.d_ns, t.d_sidx, t.d_woff,
                                                  t.d_nw, t.d_widx, t.d_child0, t.d_pslot, t.d_bcount, t.d_srng,
-                                                 t.d_chl, t.d_rad32, t.d_center, t.d_radius, t.theta, t.d_ltstat,
-                                                 tiles_cap, t.scap_tot, t.wcap_tot, need, t.d_status);
-        const LevelList& Ll = t.level_boxes[l];
-        k_lists_len<<<nblk(Ll.count, 256), 256, 0, s>>>(Ll.d_ids, Ll.count, t.d_soff, t.d_ns, t.d_woff, t.d_nw,
-                                                        t.d_status);
+                                                 t.d_chl, t.d_rad32, t.d_center, t.d_radius, t.theta,
+                                                 t.d_ltstat + lstride * (size_t)(l - 1), tiles_cap, t.scap_tot,
+                                                 t.wcap_tot, need, t.d_status);
     }
-    k_items<<<nblk(t.nbox, 128), 128, 0, s>>>((int)t.nbox, t.d_child0, t.d_bcount, t.d_ns, t.d_nw, ctr,
+    k_items<<<nblk(t.nbox, 128), 128, 0, s>>>((int)t.nbox, t.d_child0, t.d_bcount, t.d_soff, t.d_ns, t.d_woff,
+                                              t.d_nw, ctr,
                                               t.d_p2p_items, t.d_leaf_items, t.p2p_cap, t.d_m2l_items, t.d_box_m2l,
                                               t.m2l_cap, t.d_status);
     FMM_CUDA(cudaGetLastError());

@@ -717,16 +717,17 @@ __global__ void __launch_bounds__(kPartThreads) k_part_fused(
 
 // One stage: partition A by side (segments of `seg`) into out; with `next`,
 // also the flags of the next stage's cut of out.
-static fmm_status partition(Tree& t, cudaStream_t s, const int32_t* A, const uint8_t* side, const SegTable& seg,
-                            int32_t* out, const SegTable* next, uint8_t* side_next) {
+// Stage `stage` uses its own region of tile status words (T + 1 each, zeroed
+// together before the first stage of a build).
+static fmm_status partition(Tree& t, cudaStream_t s, int stage, const int32_t* A, const uint8_t* side,
+                            const SegTable& seg, int32_t* out, const SegTable* next, uint8_t* side_next) {
     const int n = (int)t.n;
     const int T = nblk(n, kPartTile);
-    FMM_CUDA(cudaMemsetAsync(t.d_part_stat, 0, (size_t)(T + 1) * sizeof(unsigned long long), s));
     const int grid = std::min(T, t.num_sms * 4);
     k_part_fused<<<grid, kPartThreads, 0, s>>>(A, side, n, seg.d_start, seg.d_nzero, seg.d_obefore, seg.K, out,
                                                next ? next->d_start : nullptr, next ? next->d_nzero : nullptr,
                                                next ? next->K : 0, next ? side_next : nullptr, t.ninst == 1 ? 1 : 0,
-                                               t.d_part_stat, T, t.d_status);
+                                               t.d_part_stat + (size_t)stage * (T + 1), T, t.d_status);
     FMM_CUDA(cudaGetLastError());
     return FMM_OK;
 }
@@ -1340,7 +1341,7 @@ fmm_status alloc_build(Tree& t) {
     if ((st = dalloc(&t.d_sideY, n))) return st;
     if ((st = dalloc(&t.d_loc, n))) return st;
     const int64_t T = std::max<int64_t>(nblk(t.n, kPartTile), nblk(t.n, kSortTile));
-    if ((st = dalloc(&t.d_part_stat, T + 1))) return st;
+    if ((st = dalloc(&t.d_part_stat, (T + 1) * (size_t)std::max(2 * (t.Lmax - 1), 1)))) return st;  // one region per stage
     if ((st = dalloc(&t.d_sort_hist, 2 * 256 * (size_t)T))) return st;
     if ((st = dalloc(&t.d_sort_off, 2 * 256 * (size_t)T))) return st;
     if ((st = dalloc(&t.d_sort_tot, 2 * 256))) return st;
@@ -1440,15 +1441,18 @@ fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s) {
         const SegTable& sx = t.seg_x[0];
         k_mark<<<nblk(n, 256), 256, 0, s>>>(X, n, sx.d_start, sx.d_nzero, sx.K, t.d_sideX);
     }
+    if (lglob > 0)
+        FMM_CUDA(cudaMemsetAsync(t.d_part_stat, 0,
+                                 (size_t)2 * lglob * (nblk(n, kPartTile) + 1) * sizeof(unsigned long long), s));
     for (int l = 0; l < lglob; ++l) {
         const SegTable& sx = t.seg_x[l];
         const SegTable& sy = t.seg_y[l];
         // x-cut: Y partitioned by the x-side flags; the y-cut flags come from Y's new order
-        if ((st = partition(t, s, Y, t.d_sideX, sx, Y2, &sy, t.d_sideY))) return st;
+        if ((st = partition(t, s, 2 * l, Y, t.d_sideX, sx, Y2, &sy, t.d_sideY))) return st;
         std::swap(Y, Y2);
         // y-cut: X partitioned by the y-side flags; the next level's x-cut flags come from X's new order
         const SegTable* nxt = l + 1 < lglob ? &t.seg_x[l + 1] : nullptr;
-        if ((st = partition(t, s, X, t.d_sideY, sy, X2, nxt, t.d_sideX))) return st;
+        if ((st = partition(t, s, 2 * l + 1, X, t.d_sideY, sy, X2, nxt, t.d_sideX))) return st;
         std::swap(X, X2);
         const LevelList& Ll = t.level_boxes[l + 1];
         k_geom<<<nblk(Ll.count, 128), 128, 0, s>>>(Ll.d_ids, Ll.count, X, Y, xy, t.d_bstart, t.d_bcount, t.d_inst,

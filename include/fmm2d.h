@@ -126,6 +126,15 @@ fmm_status fmm_eval_batched(fmm_tree* t, const double* d_gamma, void* d_phi, voi
  * separate evaluation points), CUDA, OOM, TIMEOUT, NONFINITE as the two calls. */
 fmm_status fmm_step(fmm_tree* t, const double* d_xy, const double* d_gamma, void* d_phi, void* stream);
 
+/* Self-test of the library's bounded device waits (failure detection without
+ * a GPU fault): runs one of them on something that never happens -- which = 0:
+ * the decoupled look-back of the list build, partitions and sorts on a
+ * predecessor tile that never publishes; which = 1: the tensor-core M2L's
+ * mbarrier wait on a barrier nothing arrives at -- with a short limit (4096
+ * tries).  The expected result is FMM_ERR_TIMEOUT, returned from the device's
+ * status word; the context stays usable.  Errors: INVALID_ARG (which), CUDA. */
+fmm_status fmm_selftest_bounded_wait(int which, void* stream);
+
 /* Logarithmic potential (Sec. 3.3 of the paper, the kernel it uses for
  * isopotential plots):
  *     Phi_i = sum_{j: z_j != z_i} Gamma_j ln|z_i - z_j|,

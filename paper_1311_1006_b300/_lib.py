@@ -79,6 +79,7 @@ def load() -> ctypes.CDLL:
         "fmm_eval_batched": (S, [_VP, _VP, _VP, _VP]),
         "fmm_eval_log": (S, [_VP, _VP, _VP, _VP]),
         "fmm_step": (S, [_VP, _VP, _VP, _VP, _VP]),
+        "fmm_selftest_bounded_wait": (S, [ctypes.c_int, _VP]),
         "fmm_eval_targets_log": (S, [_VP, _VP, _VP, _VP]),
         "fmm_eval_backward": (S, [_VP, _VP, _VP, _VP, _VP, _VP]),
         "fmm_autotune_step": (S, [_VP, ctypes.c_double, ctypes.POINTER(FMMParams)]),

@@ -477,6 +477,32 @@ fmm_status fmm_step(fmm_tree* h, const double* d_xy, const double* d_gamma, void
     return FMM_OK;
 }
 
+fmm_status fmm_selftest_bounded_wait(int which, void* stream) {
+    if (which < 0 || which > 1) return invalid("which must be 0 (look-back) or 1 (mbarrier)");
+    fmm_status st;
+    if ((st = check_pending())) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned long long* buf = nullptr;  // [0] status word, [1..2] tile status words
+    FMM_CUDA(cudaMalloc((void**)&buf, 4 * sizeof(unsigned long long)));
+    cudaError_t e = cudaMemsetAsync(buf, 0, 4 * sizeof(unsigned long long), s);
+    unsigned* status = reinterpret_cast<unsigned*>(buf);
+    if (e == cudaSuccess) {
+        if (which == 0) launch_selftest_lookback(buf + 1, 1 << 12, status, s);
+        else launch_selftest_mbar(1 << 12, status, s);
+        e = cudaGetLastError();
+    }
+    unsigned h_status = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_status, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(buf);
+    FMM_CUDA(e);
+    if (h_status & ST_TIMEOUT) {
+        set_error("a bounded device wait ran out (self-test)");
+        return FMM_ERR_TIMEOUT;
+    }
+    return FMM_OK;
+}
+
 void fmm_tree_destroy(fmm_tree* h) {
     if (!h) return;
     release(&h->t);

@@ -299,7 +299,10 @@ void launch_l2p_near(Tree& t, const Bufs& B, void* d_phi, cudaStream_t s);     /
 
 // FP32-path M2L on the tensor cores (m2l_tc.cu); FMM_M2L_TC=0 selects the CUDA-core kernel.
 bool m2l_tc_enabled();
-fmm_status m2l_tc_prepare(int P);  // once per compiled order, before launches (and graph capture)
+fmm_status m2l_tc_prepare(int P);
+// Self-tests of the bounded waits (a wait on something that never happens; ST_TIMEOUT expected).
+void launch_selftest_mbar(int limit, unsigned* status, cudaStream_t s);
+void launch_selftest_lookback(unsigned long long* st, int max_spins, unsigned* status, cudaStream_t s);  // once per compiled order, before launches (and graph capture)
 void launch_m2l_tc(const Tree& t, const float2* M32, float2* Lm2l, float2* part, bool log_kernel, cudaStream_t s);
 
 // Autotuner (host).

@@ -133,9 +133,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: false when the phase did not complete within the limit.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (int i = 0; i < (1 << 22); ++i)
+// Bounded wait: false when the phase did not complete within `limit` tries.
+constexpr int kMbarTries = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int limit = kMbarTries) {
+    for (int i = 0; i < limit; ++i)
         if (mbar_try_wait(mbar, parity)) return true;
     return false;
 }
@@ -531,7 +532,23 @@ cudaError_t prepare_tc() {
                                 static_cast<int>(TcShape<P>::SMEM));
 }
 
+// Self-test of the bounded mbarrier wait: a barrier nothing arrives at; the
+// wait must give up after `limit` tries and report ST_TIMEOUT.
+__global__ void k_selftest_mbar(int limit, unsigned* status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(smem_u32(&bar), 0u, limit)) atomicOr(status, ST_TIMEOUT);
+}
+
 }  // namespace
+
+void launch_selftest_mbar(int limit, unsigned* status, cudaStream_t s) {
+    k_selftest_mbar<<<1, 32, 0, s>>>(limit, status);
+}
 
 bool m2l_tc_enabled() {
     static const bool on = [] {

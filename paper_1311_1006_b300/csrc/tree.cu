@@ -602,7 +602,7 @@ __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long lo
 // kLookbackSpins rounds that met a tile with nothing published it sets
 // ST_TIMEOUT and returns what it has.
 __device__ unsigned long long warp_lookback(unsigned long long* st, long long t, unsigned long long agg,
-                                            unsigned* status) {
+                                            unsigned* status, int max_spins = kLookbackSpins) {
     const int lane = threadIdx.x & 31;
     if (t == 0) {
         if (lane == 0) st_volatile(st, kLIncl | agg);
@@ -621,7 +621,7 @@ __device__ unsigned long long warp_lookback(unsigned long long* st, long long t,
         const int first = incl ? __ffs(incl) - 1 : 32;  // nearest inclusive prefix in this window
         const unsigned need = first == 32 ? 0xffffffffu : (first == 31 ? 0xffffffffu : ((2u << first) - 1u));
         if (notready & need) {
-            if (++spins > kLookbackSpins) {
+            if (++spins > max_spins) {
                 if (lane == 0) atomicOr(status, ST_TIMEOUT);
                 break;
             }
@@ -636,6 +636,16 @@ __device__ unsigned long long warp_lookback(unsigned long long* st, long long t,
     }
     if (lane == 0) st_volatile(st + t, kLIncl | (excl + agg));
     return excl;
+}
+
+// Self-test of the bounded look-back: tile 1 waits on tile 0, which never
+// publishes (its status word stays zero); the wait must give up after
+// `max_spins` rounds and report ST_TIMEOUT.
+__global__ void k_selftest_lookback(unsigned long long* st, int max_spins, unsigned* status) {
+    warp_lookback(st, 1, 5ull, status, max_spins);
+}
+void launch_selftest_lookback(unsigned long long* st, int max_spins, unsigned* status, cudaStream_t s) {
+    k_selftest_lookback<<<1, 32, 0, s>>>(st, max_spins, status);
 }
 
 // Stable segmented partition in one pass per stage.  List A is cut into

@@ -980,21 +980,18 @@ __global__ void __launch_bounds__(kSubThreads) k_subtree(
 // interleaved in pairs (2m, 2m+1) for packed f32x2 arithmetic, as two float4
 // (x_hi[2m], x_hi[2m+1], y_hi[2m], y_hi[2m+1]), (x_lo.., x_lo.., y_lo.., y_lo..).
 __global__ void k_finalize(const int32_t* __restrict__ Y, int n, const double2* __restrict__ xy,
-                           const int32_t* __restrict__ leaf_start /*nleaf+1*/, const int32_t* __restrict__ leaf_ids,
-                           int nleaf, const int32_t* __restrict__ inst, const int64_t* __restrict__ inst_box_off,
+                           const int32_t* __restrict__ inst, const int64_t* __restrict__ inst_box_off,
                            const double2* __restrict__ center, int32_t* perm, double2* pts, float4* pos4,
-                           int32_t* leaf_of, int cap, int32_t* slot_of, float* posp32, double2* posp64) {
+                           const int32_t* __restrict__ leaf_of, const int32_t* __restrict__ slot_of, float* posp32,
+                           double2* posp64) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int id = Y[i];
     perm[i] = id;
     const double2 p = xy[id];
     pts[i] = p;
-    const int q = find_seg(leaf_start, nleaf, i);
-    const int lf = leaf_ids[q];
-    leaf_of[i] = lf;
-    const int slot = q * cap + (i - leaf_start[q]);
-    slot_of[i] = slot;
+    const int lf = leaf_of[i];      // leaf and slot of a sorted position follow from the shape alone
+    const int slot = slot_of[i];
     const double2 o = center[inst_box_off[inst[lf]]];
     const double ex = __dsub_rn(p.x, o.x), ey = __dsub_rn(p.y, o.y);
     const float hx = __double2float_rn(ex), hy = __double2float_rn(ey);
@@ -1357,10 +1354,21 @@ fmm_status alloc_build(Tree& t) {
     if ((st = dalloc(&t.d_sort_tot, 2 * 256))) return st;
     if ((st = dalloc(&t.d_sort_os, sort_scratch_words(t.n)))) return st;
     if ((st = dalloc(&t.d_perm, n))) return st;
-    if ((st = dalloc(&t.d_leaf_of, n))) return st;
     if ((st = dalloc(&t.d_pts, n))) return st;
     if ((st = dalloc(&t.d_pos4, n))) return st;
-    if ((st = dalloc(&t.d_slot_of, n))) return st;
+    {
+        // leaf (box id) and P2P slot of every sorted position: shape-only, so tabulated once here
+        std::vector<int32_t> lo((size_t)t.n), so((size_t)t.n);
+        for (int64_t q = 0; q < t.nleaf; ++q) {
+            const int32_t b = t.h_leaves[(size_t)q], s0 = t.h_bstart[(size_t)b], c = t.h_bcount[(size_t)b];
+            for (int32_t i = 0; i < c; ++i) {
+                lo[(size_t)(s0 + i)] = b;
+                so[(size_t)(s0 + i)] = (int32_t)(q * t.leaf_cap + i);
+            }
+        }
+        if ((st = upload(&t.d_leaf_of, lo))) return st;
+        if ((st = upload(&t.d_slot_of, so))) return st;
+    }
     {
         // slot layout (+1 block of padding); padding stays zero across rebuilds of this shape
         const int64_t slots = (t.nleaf + 1) * (int64_t)t.leaf_cap;
@@ -1479,9 +1487,9 @@ fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s) {
         FMM_CUDA(cudaGetLastError());
     }
     const bool f32 = t.path == FMM_PATH_FP32;
-    k_finalize<<<nblk(n, 256), 256, 0, s>>>(Y, n, xy, t.d_leaf_start, t.leaves.d_ids, (int)t.nleaf, t.d_inst,
-                                            t.d_inst_boxoff, t.d_center, t.d_perm, t.d_pts, t.d_pos4, t.d_leaf_of,
-                                            t.leaf_cap, t.d_slot_of, f32 ? static_cast<float*>(t.d_posp) : nullptr,
+    k_finalize<<<nblk(n, 256), 256, 0, s>>>(Y, n, xy, t.d_inst, t.d_inst_boxoff, t.d_center, t.d_perm, t.d_pts,
+                                            t.d_pos4, t.d_leaf_of, t.d_slot_of,
+                                            f32 ? static_cast<float*>(t.d_posp) : nullptr,
                                             f32 ? nullptr : static_cast<double2*>(t.d_posp));
     FMM_CUDA(cudaGetLastError());
     return FMM_OK;

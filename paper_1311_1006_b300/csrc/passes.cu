@@ -761,23 +761,6 @@ __device__ __forceinline__ void p2p_interact64(const double2 t, const double2 s,
     acc.y = fma(ti, inv, acc.y);
 }
 
-// FP32: coordinates carry a hi/lo split so that z_i - z_j keeps full FP32
-// relative accuracy even for very close pairs.  The coincident-pair guard is
-// folded into r^2 (+1e-37f): coincident points give dx = dy = 0 and add 0;
-// pairs closer than ~1e-18 are below FP32 resolution anyway.  Zero-strength
-// padding sources add exactly 0 (every factor is finite).
-__device__ __forceinline__ void p2p_fast32(const float4 t, const float4 s, const float2 g, float2& acc) {
-    const float dx = (t.x - s.x) + (t.z - s.z);
-    const float dy = (t.y - s.y) + (t.w - s.w);
-    const float inv = rcp_approx(fmaf(dx, dx, fmaf(dy, dy, 1e-37f)));
-    const float tr = fmaf(g.x, dx, g.y * dy);
-    const float ti = fmaf(g.y, dx, -g.x * dy);
-    acc.x = fmaf(tr, inv, acc.x);
-    acc.y = fmaf(ti, inv, acc.y);
-}
-__device__ __forceinline__ void p2p_fast(const float4 t, const float4 s, const float2 g, float2& acc) {
-    p2p_fast32(t, s, g, acc);
-}
 __device__ __forceinline__ void p2p_fast(const double2 t, const double2 s, const double2 g, double2& acc) {
     p2p_interact64(t, s, g, acc);
 }
@@ -926,8 +909,11 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, sizeof(C) == 8 ? 5 : 1)
 // packed accumulator holds two partial sums (even / odd source slots), added
 // at the end before the shuffle reduction over slices.
 // Two sources (packed) against one target: Gamma_j conj(d)/|d|^2 with
-// d = z_t - z_j from the hi/lo coordinates; the coincident-pair guard is
-// folded into |d|^2 (+1e-37f) as in the scalar kernel.
+// d = z_t - z_j from the hi/lo coordinates (so that z_t - z_j keeps full FP32
+// relative accuracy even for very close pairs).  The coincident-pair guard is
+// folded into |d|^2 (+1e-37f): coincident points give d = 0 and add 0; pairs
+// closer than ~1e-18 are below FP32 resolution anyway.  Zero-strength padding
+// sources add exactly 0 (every factor is finite).
 struct SrcPair {
     f2x x, y, xl, yl, gx, gy, ngx;
 };

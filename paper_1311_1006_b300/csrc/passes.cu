@@ -904,7 +904,7 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, sizeof(C) == 8 ? 5 : 1)
 // slots per step and every instruction is a 2-wide FP32 operation: one target
 // (duplicated into both halves once per target tile) against two sources.
 // Per pair of interactions: 14 f32x2 instructions and 2 reciprocals, half the
-// FP32 instruction issue of the scalar kernel.  Lane (tg, ss): targets tg,
+// FP32 instruction issue of one-interaction-per-instruction code.  Lane (tg, ss): targets tg,
 // tg+LT, ... and pair slice ss of S = 32/LT; a step covers 2S slots.  Each
 // packed accumulator holds two partial sums (even / odd source slots), added
 // at the end before the shuffle reduction over slices.

@@ -38,7 +38,7 @@ THETA = 0.5
 WORKLOAD = "cluster_mix_1e6_p17_theta0.5"
 # dram__bytes_read.sum + dram__bytes_write.sum of one P2P launch (k_p2p_pairs) at
 # N_levels = 9 on this workload, from one ncu capture (profiles/p2p_pairs_cluster1e6_L9.md)
-P2P_TRAFFIC_BYTES = 82_407_936 + 5_729_280
+P2P_TRAFFIC_BYTES = 82_333_440 + 5_691_136
 # algorithmic FP32 flops of one point-pair interaction (FMA = 2): compensated
 # difference 6, |d|^2 4, the two scalings 2, the complex accumulation 8
 P2P_FLOPS = 20.0

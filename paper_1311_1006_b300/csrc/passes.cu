@@ -972,10 +972,10 @@ __device__ __forceinline__ void p2p_pair_t(const f2x tx, const f2x ty, const f2x
 }
 constexpr float kHalfLn2 = 0.34657359027997264f;  // ln(2)/2: log2(|d|^2) -> ln|d|
 
-// Blocks per SM: 6 for TPL <= 4 (80 registers; measured 1-2 % faster than 4 blocks
-// at 124 registers, and faster than 5), 2 for TPL = 8.
+// Blocks per SM: 7 for TPL <= 4 (72 registers, no spills; measured against 4 (124
+// registers), 5, 6 (80) and 8 (64, spills): 7 is the fastest), 2 for TPL = 8.
 template <int TPL, int LT, bool LOG>
-__global__ void __launch_bounds__(kP2PDWarps * 32, TPL > 4 ? 2 : 6)
+__global__ void __launch_bounds__(kP2PDWarps * 32, TPL > 4 ? 2 : 7)
     k_p2p_pairs(const int4* __restrict__ items, const unsigned long long* __restrict__ nitems,
                 unsigned* __restrict__ next_item, const int32_t* __restrict__ bstart,
                 const int32_t* __restrict__ bcount, const int32_t* __restrict__ pslot,

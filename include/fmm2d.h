@@ -135,6 +135,12 @@ fmm_status fmm_step(fmm_tree* t, const double* d_xy, const double* d_gamma, void
  * status word; the context stays usable.  Errors: INVALID_ARG (which), CUDA. */
 fmm_status fmm_selftest_bounded_wait(int which, void* stream);
 
+/* Diagnostic: d_out[i] = the FP64 P2P's reciprocal of d_x[i] (n doubles,
+ * device buffers): the hardware's approximate reciprocal refined by two
+ * Newton-Raphson steps; 0 for inputs below the smallest normal double.
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA. */
+fmm_status fmm_selftest_rcp64(const double* d_x, double* d_out, int64_t n, void* stream);
+
 /* Logarithmic potential (Sec. 3.3 of the paper, the kernel it uses for
  * isopotential plots):
  *     Phi_i = sum_{j: z_j != z_i} Gamma_j ln|z_i - z_j|,

@@ -80,6 +80,7 @@ def load() -> ctypes.CDLL:
         "fmm_eval_log": (S, [_VP, _VP, _VP, _VP]),
         "fmm_step": (S, [_VP, _VP, _VP, _VP, _VP]),
         "fmm_selftest_bounded_wait": (S, [ctypes.c_int, _VP]),
+        "fmm_selftest_rcp64": (S, [_VP, _VP, ctypes.c_int64, _VP]),
         "fmm_eval_targets_log": (S, [_VP, _VP, _VP, _VP]),
         "fmm_eval_backward": (S, [_VP, _VP, _VP, _VP, _VP, _VP]),
         "fmm_autotune_step": (S, [_VP, ctypes.c_double, ctypes.POINTER(FMMParams)]),

@@ -503,6 +503,14 @@ fmm_status fmm_selftest_bounded_wait(int which, void* stream) {
     return FMM_OK;
 }
 
+fmm_status fmm_selftest_rcp64(const double* d_x, double* d_out, int64_t n, void* stream) {
+    if (!d_x || !d_out || n < 0) return invalid("NULL argument or n < 0");
+    if (n == 0) return FMM_OK;
+    launch_selftest_rcp64(d_x, n, d_out, static_cast<cudaStream_t>(stream));
+    FMM_CUDA(cudaGetLastError());
+    return FMM_OK;
+}
+
 void fmm_tree_destroy(fmm_tree* h) {
     if (!h) return;
     release(&h->t);

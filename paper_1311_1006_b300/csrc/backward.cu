@@ -58,7 +58,7 @@ __device__ __forceinline__ void bwd_interact64(const double2 t, const double2 s,
                                                double2& psi, double2& dpsi, double2& dphi) {
     const double dx = t.x - s.x, dy = t.y - s.y;
     const double r2 = fma(dx, dx, dy * dy);
-    const double inv = r2 > 0.0 ? __drcp_rn(r2) : 0.0;
+    const double inv = rcp_nr64(r2);  // 0 for a coincident pair
     const double2 u = make_double2(dx * inv, -dy * inv);
     const double2 u2 = make_double2(fma(u.x, u.x, -u.y * u.y), 2.0 * u.x * u.y);
     psi = cfma(c, u, psi);

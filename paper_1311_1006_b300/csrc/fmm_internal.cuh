@@ -302,7 +302,8 @@ bool m2l_tc_enabled();
 fmm_status m2l_tc_prepare(int P);
 // Self-tests of the bounded waits (a wait on something that never happens; ST_TIMEOUT expected).
 void launch_selftest_mbar(int limit, unsigned* status, cudaStream_t s);
-void launch_selftest_lookback(unsigned long long* st, int max_spins, unsigned* status, cudaStream_t s);  // once per compiled order, before launches (and graph capture)
+void launch_selftest_lookback(unsigned long long* st, int max_spins, unsigned* status, cudaStream_t s);
+void launch_selftest_rcp64(const double* x, int64_t n, double* out, cudaStream_t s);  // once per compiled order, before launches (and graph capture)
 void launch_m2l_tc(const Tree& t, const float2* M32, float2* Lm2l, float2* part, bool log_kernel, cudaStream_t s);
 
 // Autotuner (host).
@@ -353,6 +354,22 @@ __device__ __forceinline__ float rcp_approx(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+}
+
+// 1/x in FP64 for a positive x: the hardware's approximate reciprocal
+// (rcp.approx.ftz.f64) refined by two Newton-Raphson steps y <- y + y (1 - x y)
+// (Newton's method on f(y) = 1/y - x: each step squares the relative error),
+// within about one ulp of the correctly rounded value at 5 instructions.  x
+// below the smallest normal double (a pair closer than ~1e-154) gives 0: such
+// pairs are treated as coincident.
+__device__ __forceinline__ double rcp_nr64(double x) {
+    if (!(x >= 2.2250738585072014e-308)) return 0.0;
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {

@@ -754,7 +754,7 @@ constexpr int kP2PBlocksPerSM = 4;
 __device__ __forceinline__ void p2p_interact64(const double2 t, const double2 s, const double2 g, double2& acc) {
     const double dx = t.x - s.x, dy = t.y - s.y;
     const double r2 = fma(dx, dx, dy * dy);
-    const double inv = r2 > 0.0 ? __drcp_rn(r2) : 0.0;  // coincident pair (z_j = z_i): adds 0
+    const double inv = rcp_nr64(r2);  // coincident pair (z_j = z_i, r2 = 0): adds 0
     const double tr = fma(g.x, dx, g.y * dy);
     const double ti = fma(g.y, dx, -g.x * dy);
     acc.x = fma(tr, inv, acc.x);
@@ -1181,6 +1181,16 @@ __global__ void __launch_bounds__(256) k_reduce_m2l_edges(const int4* __restrict
         }
         Lm2l[(size_t)b * PS + c] = s;
     }
+}
+
+// Diagnostic: the P2P's FP64 reciprocal over an array (tests compare it with
+// the correctly rounded 1/x).
+__global__ void k_selftest_rcp64(const double* __restrict__ x, int64_t n, double* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = rcp_nr64(x[i]);
+}
+void launch_selftest_rcp64(const double* x, int64_t n, double* out, cudaStream_t s) {
+    k_selftest_rcp64<<<nblk(n, 256), 256, 0, s>>>(x, n, out);
 }
 
 // ============================================================ dispatch

@@ -33,3 +33,31 @@ def test_bounded_waits_time_out_and_the_context_survives(orc):
     ref = orc.fmm(xy, gam, 4, 0.5, 12)["phi"]
     assert np.abs(phi - ref).max() <= 1e-10 * np.abs(ref).max()
     t.close()
+
+
+def test_fp64_reciprocal_within_one_ulp():
+    """The FP64 P2P's reciprocal (approximate seed + two Newton-Raphson steps)
+    against the correctly rounded 1/x, for inputs whose reciprocal is a normal
+    double (squared distances of points: far inside that range)."""
+    import ctypes
+
+    from paper_1311_1006_b300 import _lib
+
+    g = np.random.default_rng(19)
+    x = np.concatenate([10.0 ** g.uniform(-300, 300, 200000), g.random(100000) * 2.0,
+                        np.array([1.0, 2.0, 3.0, 0.5, 1e-300, 2.2250738585072014e-308, 1e300])])
+    xd = torch.tensor(x, device="cuda")
+    out = torch.empty_like(xd)
+    st = _lib.load().fmm_selftest_rcp64(ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                        x.size, None)
+    assert st == 0
+    r = out.cpu().numpy()
+    exact = 1.0 / x
+    ulp = np.abs(r - exact) / np.spacing(np.abs(exact))
+    assert ulp.max() <= 1.0, float(ulp.max())
+    # below the smallest normal double: 0 (the pair counts as coincident)
+    tiny = torch.tensor([0.0, 1e-310, 4e-320], device="cuda", dtype=torch.float64)
+    o2 = torch.empty_like(tiny)
+    assert _lib.load().fmm_selftest_rcp64(ctypes.c_void_p(tiny.data_ptr()), ctypes.c_void_p(o2.data_ptr()), 3,
+                                          None) == 0
+    assert np.all(o2.cpu().numpy() == 0.0)

@@ -2,7 +2,8 @@
 outputs against the oracle's exact sums (computed target by target): the
 dynamic sequence (N = 2e6 per snapshot, p in {12, 30}, both precision paths,
 the tree rebuilt for every snapshot), the batched forest (512 instances, about
-1.1e7 points, p = 16) and the differentiated workload (N = 1e6, adjoint)."""
+1.1e7 points, p = 16), the differentiated workload (N = 1e6, adjoint) and one
+tree of 3e7 points through fmm_step."""
 import numpy as np
 import pytest
 
@@ -118,4 +119,27 @@ def test_differentiated_workload_sampled(orc):
     fwd = _ms(lambda: t.eval(G))
     bwd = _ms(lambda: t.backward(G, GP))
     assert bwd <= 3.0 * fwd, (bwd, fwd)
+    t.close()
+
+
+def test_large_single_tree_step_sampled(orc):
+    """One tree of 3e7 points (11 levels, ~4.6e8 weak and ~1.2e8 strong pairs)
+    through fmm_step: sampled outputs within the FP32 tolerance of the exact sums,
+    and the same result as a second step on the rebuilt tree."""
+    import paper_1311_1006_b300 as F
+
+    g = np.random.default_rng(30)
+    n = 30_000_000
+    xy, gam = W.cluster_mix(n, g), W.complex_strengths(n, g)
+    X, G = _dev(xy), _dev(gam)
+    t = F.Tree.build(X, p=17, theta=0.5, nlevels=F.default_nlevels(n, 17, "fp32"), path="fp32")
+    phi = t.step(X, G)
+    again = t.step(X, G).cpu().numpy()
+    ph = phi.cpu().numpy()
+    assert np.array_equal(ph, again)
+    info = t.info()
+    assert info["n_weak"] > 10 * n and info["n_strong"] > 2 * n
+    tg = np.random.default_rng(31).choice(n, 128, replace=False)
+    exact = orc.direct(xy, gam, targets=tg)
+    assert _rel(ph[tg].astype(np.complex128), exact) <= 1e-5
     t.close()

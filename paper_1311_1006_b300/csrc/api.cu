@@ -180,7 +180,7 @@ static fmm_status shape_and_build(Tree& t, const double* d_xy, cudaStream_t s, b
 static void release(Tree* t) {
     if (!t) return;
     invalidate_graph(*t);
-    void* ptrs[] = {t->d_bstart, t->d_bcount, t->d_parent, t->d_child0, t->d_inst, t->d_inst_ptoff,
+    void* ptrs[] = {t->d_bstart, t->d_bcount, t->d_parent, t->d_child0, t->d_fold_par, t->d_inst, t->d_inst_ptoff,
                     t->d_inst_boxoff, t->d_leaf_start, t->d_inst_levels, t->d_loc, t->d_X2, t->d_Y2, t->d_sideX, t->d_sideY, t->d_part_stat,
                     t->d_sort_hist, t->d_sort_tot, t->d_sort_off, t->d_sort_os, t->d_perm,
                     t->d_leaf_of, t->d_pts, t->d_pos4, t->d_center, t->d_radius, t->d_rho, t->d_chl, t->d_rho32,
@@ -667,9 +667,9 @@ fmm_status fmm_get_tree_info(const fmm_tree* h, fmm_tree_info* out) {
     const int sortk = t.n < (1 << 30) ? 9 : 24;
     out->launches_build =
         5 + sortk + lv + 3 * lg + (lg > 0 ? 1 : 0) + (lg < lv ? 1 : 0) + (t.ninst > 1 ? 7 : 0);
-    // per evaluation: gather, P2M, M2M per level, M2L, M2L partial sums, L2L per level, P2P, P2P partial
-    // sums, L2P
-    out->launches_eval = 7 + 2 * lv;
+    // per evaluation: gather, P2M, M2M per level, M2L, M2L partial sums, L2L per level (not the deepest on
+    // the FP32 path), P2P, P2P partial sums, L2P
+    out->launches_eval = 7 + 2 * lv - (fold_leaf_l2l(t) ? 1 : 0);
     out->autotune_theta = t.tune.theta_on ? t.tune.theta : t.theta;
     return FMM_OK;
 }
@@ -764,6 +764,11 @@ fmm_status fmm_tree_export(const fmm_tree* h, int what, void* h_dst, int64_t cou
             std::vector<double> a64(2 * nb * PS);
             std::vector<float> a32(2 * nb * PS);
             const bool mp = what == FMM_EXPORT_MPOLE;
+            if (!mp) {
+                // device work on the workspace only; the tree itself is unchanged
+                const fmm_status st = complete_folded_locals(const_cast<Tree&>(t), s);
+                if (st) return st;
+            }
             FMM_CUDA(cudaMemcpyAsync(a64.data(), mp ? t.d_M64 : t.d_L64, a64.size() * 8, cudaMemcpyDeviceToHost, s));
             if (mp && t.path == FMM_PATH_FP32)
                 FMM_CUDA(cudaMemcpyAsync(a32.data(), t.d_M32, a32.size() * 4, cudaMemcpyDeviceToHost, s));

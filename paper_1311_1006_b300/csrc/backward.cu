@@ -198,27 +198,80 @@ __device__ __forceinline__ void horner2(const C* __restrict__ b, C w, R inv, C& 
     dv.y *= inv;
 }
 
+// horner2 over the terms l < p only (a box's own M2L sum holds P terms).
+template <int P>
+__device__ __forceinline__ void horner2_p(const float2* __restrict__ b, float2 w, float inv, int p, float2& v,
+                                          float2& dv) {
+    v = P - 1 < p ? b[P - 1] : make_float2(0.f, 0.f);
+    dv = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int l = P - 2; l >= 0; --l) {
+        dv = cfma(dv, w, v);
+        v = cfma(v, w, l < p ? b[l] : make_float2(0.f, 0.f));
+    }
+    dv.x *= inv;
+    dv.y *= inv;
+}
+
+// Far field (value and z-derivative) of a leaf of the deepest level on the
+// FP32 path, which has no shifted local: the parent's local and the leaf's own
+// M2L sum, each at the point.
+template <int P>
+__device__ __forceinline__ void far_folded(const float4 pt, int par, int lf, const float4* __restrict__ chl,
+                                           const float* __restrict__ rho32, const float2* __restrict__ L,
+                                           const float2* __restrict__ M, bool own, int p, int PS, float2& v,
+                                           float2& dv) {
+    const float4 c = chl[par];
+    const float r = rho32[par];
+    const float inv = r > 0.f ? 1.0f / r : 0.f;
+    const float2 w = make_float2(((pt.x - c.x) + (pt.z - c.z)) * inv, ((pt.y - c.y) + (pt.w - c.w)) * inv);
+    horner2<P>(L + (size_t)par * PS, w, inv, v, dv);
+    if (own) {
+        const float4 cl = chl[lf];
+        const float rl = rho32[lf];
+        const float il = rl > 0.f ? 1.0f / rl : 0.f;
+        const float2 wl = make_float2(((pt.x - cl.x) + (pt.z - cl.z)) * il, ((pt.y - cl.y) + (pt.w - cl.w)) * il);
+        float2 ov, odv;
+        horner2_p<P>(M + (size_t)lf * PS, wl, il, p, ov, odv);
+        v.x += ov.x;
+        v.y += ov.y;
+        dv.x += odv.x;
+        dv.y += odv.y;
+    }
+}
+
 template <int P>
 __global__ void __launch_bounds__(256) k_l2p_bwd32(int n, const int32_t* __restrict__ leaf_of,
+                                                   const int32_t* __restrict__ fold_par,
+                                                   const int2* __restrict__ box_m2l,
                                                    const int32_t* __restrict__ bstart, const float4* __restrict__ chl,
                                                    const float* __restrict__ rho32, const float4* __restrict__ pos4,
                                                    const float2* __restrict__ Lg, const float2* __restrict__ Lc,
+                                                   const float2* __restrict__ Mg, const float2* __restrict__ Mc,
                                                    const int2* __restrict__ leaf_items,
                                                    const float2* __restrict__ nearv, const float2* __restrict__ part,
                                                    long long stride, int TS, const int32_t* __restrict__ perm,
                                                    const double2* __restrict__ gam, const double2* __restrict__ gphi,
-                                                   double2* __restrict__ ggam, double2* __restrict__ gxy, int PS) {
+                                                   double2* __restrict__ ggam, double2* __restrict__ gxy, int p,
+                                                   int PS) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int lf = leaf_of[i];
-    const float4 c = chl[lf];
-    const float r = rho32[lf];
-    const float inv = r > 0.f ? 1.0f / r : 0.f;
     const float4 pt = pos4[i];
-    const float2 w = make_float2(((pt.x - c.x) + (pt.z - c.z)) * inv, ((pt.y - c.y) + (pt.w - c.w)) * inv);
+    const int par = fold_par[lf];
     float2 vg, dphi, psi, dpsi;
-    horner2<P>(Lg + (size_t)lf * PS, w, inv, vg, dphi);
-    horner2<P>(Lc + (size_t)lf * PS, w, inv, psi, dpsi);
+    if (par >= 0) {
+        const bool own = box_m2l[lf].y > 0;
+        far_folded<P>(pt, par, lf, chl, rho32, Lg, Mg, own, p, PS, vg, dphi);
+        far_folded<P>(pt, par, lf, chl, rho32, Lc, Mc, own, p, PS, psi, dpsi);
+    } else {
+        const float4 c = chl[lf];
+        const float r = rho32[lf];
+        const float inv = r > 0.f ? 1.0f / r : 0.f;
+        const float2 w = make_float2(((pt.x - c.x) + (pt.z - c.z)) * inv, ((pt.y - c.y) + (pt.w - c.w)) * inv);
+        horner2<P>(Lg + (size_t)lf * PS, w, inv, vg, dphi);
+        horner2<P>(Lc + (size_t)lf * PS, w, inv, psi, dpsi);
+    }
     const int ls = bstart[lf];
     const int2 li = leaf_items[lf];
     const float2 n0 = near_sum(i, 0, ls, li, nearv, part, n, stride, TS);
@@ -286,10 +339,11 @@ static void launch_l2p_bwd(Tree& t, const Bufs& B0, const Bufs& B1, const double
     double2* gg = reinterpret_cast<double2*>(d_ggamma);
     double2* gx = reinterpret_cast<double2*>(d_gxy);
     if (t.path == FMM_PATH_FP32)
-        k_l2p_bwd32<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_bstart, t.d_chl, t.d_rho32, t.d_pos4, B0.L32,
-                                                    B1.L32, t.d_leaf_items, static_cast<const float2*>(t.d_near),
-                                                    static_cast<const float2*>(t.d_p2p_part), stride, t.max_leaf,
-                                                    t.d_perm, gam, gph, gg, gx, t.PS);
+        k_l2p_bwd32<P><<<nblk(n, 256), 256, 0, s>>>(
+            n, t.d_leaf_of, t.d_fold_par, t.d_box_m2l, t.d_bstart, t.d_chl, t.d_rho32, t.d_pos4, B0.L32, B1.L32,
+            static_cast<const float2*>(B0.Lm2l), static_cast<const float2*>(B1.Lm2l), t.d_leaf_items,
+            static_cast<const float2*>(t.d_near), static_cast<const float2*>(t.d_p2p_part), stride, t.max_leaf,
+            t.d_perm, gam, gph, gg, gx, t.p, t.PS);
     else
         k_l2p_bwd64<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_bstart, t.d_center, t.d_rho, t.d_pts,
                                                     B0.L64, B1.L64, t.d_leaf_items,

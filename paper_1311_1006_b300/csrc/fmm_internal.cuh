@@ -117,6 +117,10 @@ struct Tree {
     // device shape tables
     int32_t *d_bstart = nullptr, *d_bcount = nullptr, *d_parent = nullptr, *d_child0 = nullptr,
             *d_inst = nullptr;
+    // per box: for the leaves of the deepest level (N_levels >= 3) their parent, else -1.  On the FP32 path
+    // these leaves get no L2L: L2P evaluates the parent's local expansion at the point and adds the
+    // leaf's own M2L sum (the shift of a truncated local is an exact re-expansion of the same polynomial)
+    int32_t* d_fold_par = nullptr;
     std::vector<LevelList> level_boxes;    // per level l: all boxes on level l
     std::vector<LevelList> level_parents;  // per level l: boxes on level l that have children
     LevelList leaves;
@@ -287,6 +291,9 @@ struct Bufs {
     void* m2l_part;
 };
 Bufs bufs(Tree& t, int set);
+// FP32 path with at least three levels: the deepest level's L2L is folded into L2P (Tree::d_fold_par).
+inline bool fold_leaf_l2l(const Tree& t) { return t.path == FMM_PATH_FP32 && t.Lmax >= 3; }
+fmm_status complete_folded_locals(Tree& t, cudaStream_t s);  // the skipped L2L, for the export of locals
 bool refresh_grids(Tree& t);  // true when the P2P / M2L grids changed (the graph must be re-captured)
 long long p2p_grid_items(const Tree& t);
 long long m2l_grid_items(const Tree& t);

@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(128) k_l2l(const int32_t* __restrict__ boxes, 
                                              const double* __restrict__ rho, const double2* __restrict__ center,
                                              const int2* __restrict__ box_m2l, const LM* __restrict__ Lm2l,
                                              double2* __restrict__ L64,
-                                             float2* __restrict__ L32, int p, int PS) {
+                                             float2* __restrict__ L32, int all32, int p, int PS) {
     int qi = blockIdx.x * blockDim.x + threadIdx.x;
     if (qi >= cnt) return;
     const int c = boxes[qi];
@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(128) k_l2l(const int32_t* __restrict__ boxes, 
     for (int m = 0; m < P; ++m) own[m] = mi.y > 0 ? make_double2((double)o[m].x, (double)o[m].y) : make_double2(0.0, 0.0);
     double sp = 1.0;
     double2* out = L64 + (size_t)c * PS;
-    const bool leaf32 = (L32 != nullptr) && child0[c] < 0;
+    const bool leaf32 = (L32 != nullptr) && (all32 || child0[c] < 0);
     float2* o32 = L32 + (size_t)c * PS;
 #pragma unroll
     for (int m = 0; m < P; ++m) {
@@ -583,7 +583,8 @@ __global__ void __launch_bounds__(128) k_l2l_warp(const int32_t* __restrict__ bo
                                                   const int32_t* __restrict__ child0, const double* __restrict__ rho,
                                                   const double2* __restrict__ center,
                                                   const int2* __restrict__ box_m2l, const LM* __restrict__ Lm2l,
-                                                  double2* __restrict__ L64, float2* __restrict__ L32, int p, int PS) {
+                                                  double2* __restrict__ L64, float2* __restrict__ L32, int all32, int p,
+                                                  int PS) {
     const int qi = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (qi >= cnt) return;  // warp-uniform
@@ -617,7 +618,7 @@ __global__ void __launch_bounds__(128) k_l2l_warp(const int32_t* __restrict__ bo
             double b0 = fma(rP, t, L64[(size_t)Pb * PS + P].x);
             if (mi.y > 0) b0 += (double)Lm2l[(size_t)c * PS + P].x;
             L64[(size_t)c * PS + P] = make_double2(b0, 0.0);
-            if (L32 != nullptr && child0[c] < 0) L32[(size_t)c * PS + P] = make_float2((float)b0, 0.f);
+            if (L32 != nullptr && (all32 || child0[c] < 0)) L32[(size_t)c * PS + P] = make_float2((float)b0, 0.f);
         }
     }
     if (lane >= P) return;
@@ -630,7 +631,7 @@ __global__ void __launch_bounds__(128) k_l2l_warp(const int32_t* __restrict__ bo
     double2 v = make_double2(fma(acc.x, scale, own.x), fma(acc.y, scale, own.y));
     if (lane >= p) v = make_double2(0.0, 0.0);
     L64[(size_t)c * PS + lane] = v;
-    if (L32 != nullptr && child0[c] < 0) L32[(size_t)c * PS + lane] = make_float2((float)v.x, (float)v.y);
+    if (L32 != nullptr && (all32 || child0[c] < 0)) L32[(size_t)c * PS + lane] = make_float2((float)v.x, (float)v.y);
 }
 
 // Levels with at most this many shifts use the warp-per-shift kernels.
@@ -638,26 +639,56 @@ constexpr int kWarpShiftMax = 1024;  // measured against 4096 and 16384: 1024 fa
 
 // ------------------------------------------------------------- L2P + sum
 
+// Scaled offset w = (z - c_b) / rho_b of a point from box b (FP32 hi/lo coordinates).
+__device__ __forceinline__ float2 scaled_offset(const float4 pt, const float4* __restrict__ chl,
+                                                const float* __restrict__ rho32, int b) {
+    const float4 c = chl[b];
+    const float r = rho32[b];
+    const float inv = r > 0.f ? 1.0f / r : 0.f;
+    return make_float2(((pt.x - c.x) + (pt.z - c.z)) * inv, ((pt.y - c.y) + (pt.w - c.w)) * inv);
+}
+
+// sum_{l < p} b_l w^l by Horner.  The M2L sums of a box hold P terms whatever
+// the requested order p <= P; the terms l >= p are left out (the L2L drops
+// them in the same way).
+template <int P>
+__device__ __forceinline__ float2 horner_p(const float2* __restrict__ b, const float2 w, int p) {
+    float2 v = P - 1 < p ? b[P - 1] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int l = P - 2; l >= 0; --l) v = cfma(v, w, l < p ? b[l] : make_float2(0.f, 0.f));
+    return v;
+}
+
 // One thread per sorted point: far field by Horner from the leaf's local
-// expansion, plus the near field, written to the caller's order.
+// expansion, plus the near field, written to the caller's order.  A leaf of
+// the deepest level (fold_par >= 0) has no shifted local of its own: its far
+// field is the parent's local at the point plus its own M2L sum at the point,
+// which is the value the shifted local would give (up to rounding).
 template <int P>
 __global__ void __launch_bounds__(256) k_l2p32(int n, const int32_t* __restrict__ leaf_of,
+                                               const int32_t* __restrict__ fold_par, const int2* __restrict__ box_m2l,
                                                const float4* __restrict__ chl,
                                                const float* __restrict__ rho32, const float4* __restrict__ pos4,
-                                               const float2* __restrict__ L32, const float2* __restrict__ nearv,
-                                               const int32_t* __restrict__ perm, float2* __restrict__ out, int PS) {
+                                               const float2* __restrict__ L32, const float2* __restrict__ Lm2l,
+                                               const float2* __restrict__ nearv,
+                                               const int32_t* __restrict__ perm, float2* __restrict__ out, int p,
+                                               int PS) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int lf = leaf_of[i];
-    const float4 c = chl[lf];
-    const float r = rho32[lf];
-    const float inv = r > 0.f ? 1.0f / r : 0.f;
     const float4 pt = pos4[i];
-    const float2 w = make_float2(((pt.x - c.x) + (pt.z - c.z)) * inv, ((pt.y - c.y) + (pt.w - c.w)) * inv);
-    const float2* Lb = L32 + (size_t)lf * PS;
-    float2 v = Lb[P - 1];
-#pragma unroll
-    for (int l = P - 2; l >= 0; --l) v = cfma(v, w, Lb[l]);
+    const int par = fold_par[lf];
+    float2 v;
+    if (par >= 0) {
+        v = horner_p<P>(L32 + (size_t)par * PS, scaled_offset(pt, chl, rho32, par), P);
+        if (box_m2l[lf].y > 0) {
+            const float2 o = horner_p<P>(Lm2l + (size_t)lf * PS, scaled_offset(pt, chl, rho32, lf), p);
+            v.x += o.x;
+            v.y += o.y;
+        }
+    } else {
+        v = horner_p<P>(L32 + (size_t)lf * PS, scaled_offset(pt, chl, rho32, lf), P);
+    }
     const float2 nv = nearv[i];
     out[perm[i]] = make_float2(v.x + nv.x, v.y + nv.y);
 }
@@ -702,24 +733,47 @@ __device__ __forceinline__ T log_local_eval(const T2* __restrict__ Lb, const T2 
     return Lb[P].x + r * (w.x * h.x - w.y * h.y);
 }
 
+// log_local_eval of a box's own M2L sum: terms m >= p left out (as in the L2L).
+template <int P>
+__device__ __forceinline__ float log_local_eval_p(const float2* __restrict__ Lb, const float2 w, const float r,
+                                                  int p) {
+    float2 h = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int l = P - 1; l >= 0; --l) {
+        const float2 c = l < p ? make_float2(Lb[l].x * (1.0f / (l + 1)), Lb[l].y * (1.0f / (l + 1)))
+                               : make_float2(0.f, 0.f);
+        h = cfma(h, w, c);
+    }
+    return Lb[P].x + r * (w.x * h.x - w.y * h.y);
+}
+
+// Same fold of the deepest level's L2L as in k_l2p32.
 template <int P>
 __global__ void __launch_bounds__(256) k_l2p32_log(int n, const int32_t* __restrict__ leaf_of,
-                                                   const float4* __restrict__ chl,
+                                                   const int32_t* __restrict__ fold_par,
+                                                   const int2* __restrict__ box_m2l, const float4* __restrict__ chl,
                                                    const float* __restrict__ rho32, const float4* __restrict__ pos4,
                                                    const float2* __restrict__ L0, const float2* __restrict__ L1,
+                                                   const float2* __restrict__ M0, const float2* __restrict__ M1,
                                                    const float2* __restrict__ nearv,
-                                                   const int32_t* __restrict__ perm, float2* __restrict__ out,
+                                                   const int32_t* __restrict__ perm, float2* __restrict__ out, int p,
                                                    int PS) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int lf = leaf_of[i];
-    const float4 c = chl[lf];
-    const float r = rho32[lf];
-    const float inv = r > 0.f ? 1.0f / r : 0.f;
     const float4 pt = pos4[i];
-    const float2 w = make_float2(((pt.x - c.x) + (pt.z - c.z)) * inv, ((pt.y - c.y) + (pt.w - c.w)) * inv);
-    const float f0 = log_local_eval<P>(L0 + (size_t)lf * PS, w, r);
-    const float f1 = log_local_eval<P>(L1 + (size_t)lf * PS, w, r);
+    const int par = fold_par[lf];
+    const int b = par >= 0 ? par : lf;
+    const float2 w = scaled_offset(pt, chl, rho32, b);
+    const float r = rho32[b];
+    float f0 = log_local_eval<P>(L0 + (size_t)b * PS, w, r);
+    float f1 = log_local_eval<P>(L1 + (size_t)b * PS, w, r);
+    if (par >= 0 && box_m2l[lf].y > 0) {
+        const float2 wl = scaled_offset(pt, chl, rho32, lf);
+        const float rl = rho32[lf];
+        f0 += log_local_eval_p<P>(M0 + (size_t)lf * PS, wl, rl, p);
+        f1 += log_local_eval_p<P>(M1 + (size_t)lf * PS, wl, rl, p);
+    }
     const float2 nv = nearv[i];
     out[perm[i]] = make_float2(f0 + nv.x, f1 + nv.y);
 }
@@ -1272,16 +1326,21 @@ static void launch_down_fp32(Tree& t, const Bufs& B, cudaStream_t s) {
                                                                    static_cast<float2*>(B.Lm2l));
     }
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[3], s);
-    for (int l = 0; l + 1 < t.Lmax; ++l) {
+    // the deepest level's leaves get no L2L (see fold_leaf_l2l); the level above then keeps an FP32 copy
+    // of every box's local for their L2P
+    const bool fold = fold_leaf_l2l(t);
+    const int lend = fold ? t.Lmax - 2 : t.Lmax - 1;  // deepest level that gets an L2L
+    for (int l = 0; l + 1 <= lend; ++l) {
         const LevelList& L = t.level_boxes[l + 1];
+        const int all32 = fold && l + 1 == lend;
         if (L.count <= kWarpShiftMax)
             k_l2l_warp<P, float2, LOG><<<nblk(32 * (int64_t)L.count, 128), 128, 0, s>>>(
                 L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho, t.d_center, t.d_box_m2l,
-                static_cast<const float2*>(B.Lm2l), B.L64, B.L32, t.p, t.PS);
+                static_cast<const float2*>(B.Lm2l), B.L64, B.L32, all32, t.p, t.PS);
         else
             k_l2l<P, float2, LOG><<<nblk(L.count, 128), 128, 0, s>>>(
                 L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho, t.d_center, t.d_box_m2l,
-                static_cast<const float2*>(B.Lm2l), B.L64, B.L32, t.p, t.PS);
+                static_cast<const float2*>(B.Lm2l), B.L64, B.L32, all32, t.p, t.PS);
     }
 }
 
@@ -1318,11 +1377,11 @@ static void launch_down_fp64(Tree& t, const Bufs& B, cudaStream_t s) {
         if (L.count <= kWarpShiftMax)
             k_l2l_warp<P, double2, LOG><<<nblk(32 * (int64_t)L.count, 128), 128, 0, s>>>(
                 L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho, t.d_center, t.d_box_m2l,
-                static_cast<const double2*>(B.Lm2l), B.L64, nullptr, t.p, t.PS);
+                static_cast<const double2*>(B.Lm2l), B.L64, nullptr, 0, t.p, t.PS);
         else
             k_l2l<P, double2, LOG><<<nblk(L.count, 128), 128, 0, s>>>(
                 L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho, t.d_center, t.d_box_m2l,
-                static_cast<const double2*>(B.Lm2l), B.L64, nullptr, t.p, t.PS);
+                static_cast<const double2*>(B.Lm2l), B.L64, nullptr, 0, t.p, t.PS);
     }
 }
 
@@ -1330,9 +1389,10 @@ template <int P>
 static void launch_l2p(Tree& t, const Bufs& B, void* d_phi, cudaStream_t s) {
     const int n = (int)t.n;
     if (t.path == FMM_PATH_FP32) {
-        k_l2p32<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_chl, t.d_rho32, t.d_pos4, B.L32,
+        k_l2p32<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_fold_par, t.d_box_m2l, t.d_chl, t.d_rho32,
+                                                t.d_pos4, B.L32, static_cast<const float2*>(B.Lm2l),
                                                 static_cast<const float2*>(B.near), t.d_perm,
-                                                static_cast<float2*>(d_phi), t.PS);
+                                                static_cast<float2*>(d_phi), t.p, t.PS);
     } else {
         k_l2p64<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_center, t.d_rho, t.d_pts, B.L64,
                                                 static_cast<const double2*>(B.near), t.d_perm,
@@ -1344,9 +1404,10 @@ template <int P>
 static void launch_l2p_log(Tree& t, const Bufs& B0, const Bufs& B1, void* d_phi, cudaStream_t s) {
     const int n = (int)t.n;
     if (t.path == FMM_PATH_FP32) {
-        k_l2p32_log<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_chl, t.d_rho32, t.d_pos4, B0.L32, B1.L32,
-                                                    static_cast<const float2*>(B0.near), t.d_perm,
-                                                    static_cast<float2*>(d_phi), t.PS);
+        k_l2p32_log<P><<<nblk(n, 256), 256, 0, s>>>(
+            n, t.d_leaf_of, t.d_fold_par, t.d_box_m2l, t.d_chl, t.d_rho32, t.d_pos4, B0.L32, B1.L32,
+            static_cast<const float2*>(B0.Lm2l), static_cast<const float2*>(B1.Lm2l),
+            static_cast<const float2*>(B0.near), t.d_perm, static_cast<float2*>(d_phi), t.p, t.PS);
     } else {
         k_l2p64_log<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_center, t.d_rho, t.d_pts, B0.L64, B1.L64,
                                                     static_cast<const double2*>(B0.near), t.d_perm,
@@ -1488,6 +1549,35 @@ void dispatch_down(Tree& t, const Bufs& B, cudaStream_t s, bool log_kernel) {
 void dispatch_far(Tree& t, const Bufs& B, cudaStream_t s, bool log_kernel) {
     dispatch_up(t, B, s);
     dispatch_down(t, B, s, log_kernel);
+}
+
+// The deepest level's locals, which the FP32 evaluation does not form (its L2P
+// uses the parents' locals): the L2L of that level for strength set 0, for the
+// export of the local expansions only.
+template <int P>
+static void launch_folded_locals(Tree& t, const Bufs& B, cudaStream_t s) {
+    const LevelList& L = t.level_boxes[t.Lmax - 1];
+    if (L.count <= kWarpShiftMax)
+        k_l2l_warp<P, float2, false><<<nblk(32 * (int64_t)L.count, 128), 128, 0, s>>>(
+            L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho, t.d_center, t.d_box_m2l,
+            static_cast<const float2*>(B.Lm2l), B.L64, nullptr, 0, t.p, t.PS);
+    else
+        k_l2l<P, float2, false><<<nblk(L.count, 128), 128, 0, s>>>(
+            L.d_ids, L.count, t.d_parent, t.d_child0, t.d_rho, t.d_center, t.d_box_m2l,
+            static_cast<const float2*>(B.Lm2l), B.L64, nullptr, 0, t.p, t.PS);
+}
+
+fmm_status complete_folded_locals(Tree& t, cudaStream_t s) {
+    if (!fold_leaf_l2l(t)) return FMM_OK;
+    const Bufs B = bufs(t, 0);
+    switch (t.P) {
+#define FMM_CASE(Q) \
+    case Q: launch_folded_locals<Q>(t, B, s); break;
+        FMM_FOR_ORDERS(FMM_CASE)
+#undef FMM_CASE
+    }
+    FMM_CUDA(cudaGetLastError());
+    return FMM_OK;
 }
 
 static void dispatch_l2p(Tree& t, const Bufs& B, void* d_phi, cudaStream_t s) {

@@ -124,6 +124,12 @@ fmm_status build_shape(Tree& t) {
     if ((st = upload(&t.d_bcount, t.h_bcount))) return st;
     if ((st = upload(&t.d_parent, t.h_parent))) return st;
     if ((st = upload(&t.d_child0, t.h_child0))) return st;
+    {
+        std::vector<int32_t> fp(t.nbox, -1);
+        if (t.Lmax >= 3)
+            for (int32_t g : t.h_level_boxes[t.Lmax - 1]) fp[g] = t.h_parent[g];
+        if ((st = upload(&t.d_fold_par, fp))) return st;
+    }
     if ((st = upload(&t.d_inst, t.h_inst))) return st;
     if ((st = upload(&t.d_inst_ptoff, t.inst_pt_off))) return st;
     if ((st = upload(&t.d_inst_boxoff, t.inst_box_off))) return st;

@@ -56,7 +56,7 @@ inline int leaf_capacity(int max_leaf) {
 constexpr int kP2PItemSources = 4096;
 constexpr int kMaxLevels = 16;
 constexpr int kSubMax = 4096;  // largest box whose remaining splits one CTA performs in shared memory
-constexpr int kM2LItemPairs = 64;  // measured: 48 .. 96 equal on the 1e6-point workload, 32 and 128 slower
+constexpr int kM2LItemPairsMax = 256;  // bound of m2l_item_pairs (counters of the M2L row order)
 constexpr int kM2LTcRows = 128;  // work items (MMA rows) per CTA of the tensor-core M2L
 
 // Partition tile: 256 threads x 8 consecutive positions.
@@ -176,6 +176,12 @@ struct Tree {
     int4* d_m2l_items = nullptr;
     int2* d_leaf_items = nullptr;  // per box: first P2P item, item count (leaves)
     int2* d_box_m2l = nullptr;     // per box: first M2L item, item count
+    // row order of the M2L kernels: every full item (m2l_item_pairs() pairs) first, then the boxes' shorter
+    // last items by decreasing length, so that threads stepping through their items in lockstep (a warp, or
+    // the CTA of the tensor-core M2L) have about the same number of pairs
+    int32_t* d_m2l_rows = nullptr;              // m2l_cap: row -> item
+    int2* d_box_tail = nullptr;                 // per box: (length of its short last item or 0, rank among equals)
+    unsigned long long* d_m2l_rowctr = nullptr;  // [kM2LItemPairsMax + 1]: short items per length, then full items
     long long p2p_cap = 0, m2l_cap = 0;
     // work items the P2P / M2L launch grids cover: the last build's counts plus
     // slack, re-derived (and the evaluation graph re-captured) when a build's
@@ -293,6 +299,12 @@ struct Bufs {
 Bufs bufs(Tree& t, int set);
 // FP32 path with at least three levels: the deepest level's L2L is folded into L2P (Tree::d_fold_par).
 inline bool fold_leaf_l2l(const Tree& t) { return t.path == FMM_PATH_FP32 && t.Lmax >= 3; }
+bool m2l_tc_enabled();
+// Weak pairs per M2L work item.  Tensor-core M2L, measured with the row order on the 1e6-point step (ms):
+// 64: 3.32, 128: 3.25, 160: 3.23, 192: 3.22, 256: 3.23.  FP64 M2L (one thread per item): 32, 64 and 128 equal.
+inline int m2l_item_pairs(const Tree& t) {
+    return t.path == FMM_PATH_FP32 && m2l_tc_enabled() ? 192 : 64;
+}
 fmm_status complete_folded_locals(Tree& t, cudaStream_t s);  // the skipped L2L, for the export of locals
 bool refresh_grids(Tree& t);  // true when the P2P / M2L grids changed (the graph must be re-captured)
 long long p2p_grid_items(const Tree& t);

@@ -10,8 +10,11 @@
 // w = B v is a dense contraction; it runs on the tensor cores, the two diagonal
 // scalings and the sum over the weak list stay on the CUDA cores.
 //
-// Work layout: a CTA takes 128 consecutive M2L work items (a target box and up
-// to 64 entries of its weak list), one per thread.  Step j treats the j-th
+// Work layout: a CTA takes 128 consecutive rows of the M2L row order, one
+// work item (a target box and up to 192 entries of its weak list) per thread.
+// The row order puts every full item first and then the boxes' shorter last
+// items by decreasing length, so the threads of a CTA, which step through
+// their pairs in lockstep, have about the same number of pairs.  Step j treats the j-th
 // weak entry of every item at once: each thread writes its v (real and
 // imaginary parts, TF32 hi/lo split) as row `thread` of the A operands, which
 // live in tensor memory (tcgen05.st, lane = thread); one elected thread issues
@@ -244,10 +247,11 @@ __device__ __forceinline__ void ltail_all(const float2 (&v)[P], float2 (&wt)[NW]
 
 template <int P, bool LOG>
 __global__ void __launch_bounds__(kTcThreads, P <= 18 ? 3 : 2)
-    k_m2l_tc(const int4* __restrict__ items, const unsigned long long* __restrict__ nitems,
-             const int32_t* __restrict__ woff, const int32_t* __restrict__ widx, const float4* __restrict__ chl,
-             const float* __restrict__ rho32, const float2* __restrict__ M32, const int2* __restrict__ box_m2l,
-             float2* __restrict__ Lm2l, float2* __restrict__ part, int PS, unsigned* status) {
+    k_m2l_tc(const int4* __restrict__ items, const int32_t* __restrict__ rows,
+             const unsigned long long* __restrict__ nitems, const int32_t* __restrict__ woff,
+             const int32_t* __restrict__ widx, const float4* __restrict__ chl, const float* __restrict__ rho32,
+             const float2* __restrict__ M32, float2* __restrict__ Lm2l, float2* __restrict__ part, int PS,
+             unsigned* status) {
     using S = TcShape<P>;
     constexpr int KT = S::KT, NT = S::NT, KW = S::KW, B_FLOATS = S::B_FLOATS, COL_D = S::COL_D;
     constexpr int NA = (P + 1) / 2;  // float4 loads of one multipole (PS even)
@@ -260,10 +264,14 @@ __global__ void __launch_bounds__(kTcThreads, P <= 18 ? 3 : 2)
     const int nit = static_cast<int>(*nitems);
     if (blockIdx.x * kTcThreads >= nit) return;  // CTA-uniform
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int it = blockIdx.x * kTcThreads + tid;
-    const bool has = it < nit;
+    const int row = blockIdx.x * kTcThreads + tid;
+    const bool has = row < nit;
+    int it = 0;  // work item of this row
     int4 item = make_int4(0, 0, 0, -1);
-    if (has) item = items[it];
+    if (has) {
+        it = rows[row];
+        item = items[it];
+    }
     const int len = has ? item.z - item.y : 0;
 
     // B operand (k < KT, l < NT; zero past p), K-major in shared memory
@@ -477,50 +485,21 @@ __global__ void __launch_bounds__(kTcThreads, P <= 18 ? 3 : 2)
         if (tid == 0) atomicOr(status, ST_TIMEOUT);
         return;
     }
-    // Boxes whose weak list was split into several items: when all of a box's
-    // items are rows of this CTA, its rows add them up here, each coefficient in
-    // item order (the order of the separate partial-sum pass); other split boxes
-    // write their partial sums for k_reduce_m2l_edges.
-    constexpr int NC = LOG ? P + 1 : P;
-    __shared__ float2 sacc[kTcThreads][NC];
-#pragma unroll
-    for (int l = 0; l < P; ++l) sacc[tid][l] = acc[l];
-    if constexpr (LOG) sacc[tid][P] = make_float2(b0, 0.f);
-    __syncthreads();
+    // a box with one item: its M2L sum; otherwise the item's partial sum, which
+    // k_reduce_m2l adds up in item order
     if (!has) return;
-    const int it0 = blockIdx.x * kTcThreads;
-    if (item.w < 0) {
-        float2* out = Lm2l + (size_t)b * PS;
+    float2* out = item.w < 0 ? Lm2l + (size_t)b * PS : part + (size_t)it * PS;
 #pragma unroll
-        for (int l = 0; l < NC; ++l) out[l] = sacc[tid][l];
-        return;
-    }
-    const int first = item.w, km = box_m2l[b].y;
-    if (first >= it0 && first + km <= it0 + kTcThreads) {
-        // the box's km rows share its coefficients: row q adds coefficients q, q + km, ...
-        float2* out = Lm2l + (size_t)b * PS;
-        for (int l = it - first; l < NC; l += km) {
-            float2 sum = make_float2(0.f, 0.f);
-            for (int q = 0; q < km; ++q) {
-                const float2 v = sacc[first - it0 + q][l];
-                sum.x += v.x;
-                sum.y += v.y;
-            }
-            out[l] = sum;
-        }
-        return;
-    }
-    float2* out = part + (size_t)it * PS;
-#pragma unroll
-    for (int l = 0; l < NC; ++l) out[l] = sacc[tid][l];
+    for (int l = 0; l < P; ++l) out[l] = acc[l];
+    if constexpr (LOG) out[P] = make_float2(b0, 0.f);
 }
 
 template <int P, bool LOG>
 void launch_tc(const Tree& t, const float2* M32, float2* Lm2l, float2* part, cudaStream_t s) {
     const int grid = static_cast<int>(std::max<long long>((m2l_grid_items(t) + kTcThreads - 1) / kTcThreads, 1));
     k_m2l_tc<P, LOG><<<grid, kTcThreads, TcShape<P>::SMEM, s>>>(
-        t.d_m2l_items, reinterpret_cast<const unsigned long long*>(t.d_status) + 4, t.d_woff, t.d_widx, t.d_chl,
-        t.d_rho32, M32, t.d_box_m2l, Lm2l, part, t.PS, t.d_status);
+        t.d_m2l_items, t.d_m2l_rows, reinterpret_cast<const unsigned long long*>(t.d_status) + 4, t.d_woff, t.d_widx,
+        t.d_chl, t.d_rho32, M32, Lm2l, part, t.PS, t.d_status);
 }
 
 template <int P>

@@ -315,9 +315,10 @@ __global__ void __launch_bounds__(128) k_m2l32(const int4* __restrict__ items,
                                                const int32_t* __restrict__ woff, const int32_t* __restrict__ widx,
                                                const float4* __restrict__ chl, const float* __restrict__ rho32,
                                                const float2* __restrict__ M32, float2* __restrict__ Lm2l,
-                                               float2* __restrict__ part, int PS) {
-    const int it = blockIdx.x * blockDim.x + threadIdx.x;
-    if (it >= (int)*nitems) return;
+                                               float2* __restrict__ part, const int32_t* __restrict__ rows, int PS) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= (int)*nitems) return;
+    const int it = rows[row];  // work item of this thread (row order: similar lengths within a warp)
     const int4 item = items[it];
     const int b = item.x;
     const float4 ct = chl[b];
@@ -367,9 +368,10 @@ __global__ void __launch_bounds__(128) k_m2l64(const int4* __restrict__ items,
                                                const int32_t* __restrict__ woff, const int32_t* __restrict__ widx,
                                                const double2* __restrict__ center, const double* __restrict__ rho,
                                                const double2* __restrict__ M64, double2* __restrict__ Lm2l,
-                                               double2* __restrict__ part, int PS) {
-    const int it = blockIdx.x * blockDim.x + threadIdx.x;
-    if (it >= (int)*nitems) return;
+                                               double2* __restrict__ part, const int32_t* __restrict__ rows, int PS) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= (int)*nitems) return;
+    const int it = rows[row];  // work item of this thread (row order: similar lengths within a warp)
     const int4 item = items[it];
     const int b = item.x;
     const double2 ct = center[b];
@@ -1208,35 +1210,6 @@ __global__ void __launch_bounds__(256) k_reduce_m2l(int nbox, const int2* __rest
     }
 }
 
-// Partial sums of the boxes whose M2L items straddle a boundary between two
-// CTAs of the tensor-core M2L (rows of `tile` consecutive items; boxes inside
-// one CTA were added there).  One warp per CTA boundary; a box is added by
-// the warp of the first boundary after its first item, in item order.
-template <typename C>
-__global__ void __launch_bounds__(256) k_reduce_m2l_edges(const int4* __restrict__ items,
-                                                          const unsigned long long* __restrict__ nitems,
-                                                          const int2* __restrict__ box_m2l, const C* __restrict__ part,
-                                                          int PS, int tile, int nbound, C* __restrict__ Lm2l) {
-    const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (w >= nbound) return;
-    const long long it = (long long)tile * (w + 1);
-    if (it >= (long long)*nitems) return;
-    const int b = items[it].x;
-    const int2 mi = box_m2l[b];
-    if (mi.y <= 1 || ((long long)mi.x / tile + 1) * tile != it) return;
-    for (int c = lane; c < PS; c += 32) {
-        C s{};
-#pragma unroll 8
-        for (int q = 0; q < mi.y; ++q) {
-            const C v = part[(size_t)(mi.x + q) * PS + c];
-            s.x += v.x;
-            s.y += v.y;
-        }
-        Lm2l[(size_t)b * PS + c] = s;
-    }
-}
-
 // Diagnostic: the P2P's FP64 reciprocal over an array (tests compare it with
 // the correctly rounded 1/x).
 __global__ void k_selftest_rcp64(const double* __restrict__ x, int64_t n, double* __restrict__ out) {
@@ -1313,14 +1286,13 @@ static void launch_down_fp32(Tree& t, const Bufs& B, cudaStream_t s) {
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[2], s);
     if (m2l_tc_enabled()) {
         launch_m2l_tc(t, B.M32, static_cast<float2*>(B.Lm2l), static_cast<float2*>(B.m2l_part), LOG, s);
-        const int nbound = (int)std::max<long long>((m2l_grid_items(t) + kM2LTcRows - 1) / kM2LTcRows, 1);
-        k_reduce_m2l_edges<float2><<<nblk(32 * (int64_t)nbound, 256), 256, 0, s>>>(
-            t.d_m2l_items, item_count(t, 3), t.d_box_m2l, static_cast<const float2*>(B.m2l_part), t.PS, kM2LTcRows,
-            nbound, static_cast<float2*>(B.Lm2l));
+        k_reduce_m2l<float2><<<nblk(32 * t.nbox, 256), 256, 0, s>>>((int)t.nbox, t.d_box_m2l,
+                                                                   static_cast<const float2*>(B.m2l_part), t.PS,
+                                                                   static_cast<float2*>(B.Lm2l));
     } else {
         k_m2l32<P, LOG><<<nblk(m2l_grid_items(t), 128), 128, 0, s>>>(t.d_m2l_items, item_count(t, 3), t.d_woff, t.d_widx,
                                                         t.d_chl, t.d_rho32, B.M32, static_cast<float2*>(B.Lm2l),
-                                                        static_cast<float2*>(B.m2l_part), t.PS);
+                                                        static_cast<float2*>(B.m2l_part), t.d_m2l_rows, t.PS);
         k_reduce_m2l<float2><<<nblk(32 * t.nbox, 256), 256, 0, s>>>((int)t.nbox, t.d_box_m2l,
                                                                    static_cast<const float2*>(B.m2l_part), t.PS,
                                                                    static_cast<float2*>(B.Lm2l));
@@ -1367,7 +1339,7 @@ static void launch_down_fp64(Tree& t, const Bufs& B, cudaStream_t s) {
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[2], s);
     k_m2l64<P, LOG><<<nblk(m2l_grid_items(t), 128), 128, 0, s>>>(t.d_m2l_items, item_count(t, 3), t.d_woff, t.d_widx,
                                                     t.d_center, t.d_rho, B.M64, static_cast<double2*>(B.Lm2l),
-                                                    static_cast<double2*>(B.m2l_part), t.PS);
+                                                    static_cast<double2*>(B.m2l_part), t.d_m2l_rows, t.PS);
     k_reduce_m2l<double2><<<nblk(32 * t.nbox, 256), 256, 0, s>>>((int)t.nbox, t.d_box_m2l,
                                                                 static_cast<const double2*>(B.m2l_part), t.PS,
                                                                 static_cast<double2*>(B.Lm2l));

@@ -1251,7 +1251,7 @@ __global__ void __launch_bounds__(kLThreads) k_lists_level(
 
 // Work items that bound the work of one warp / thread whatever the list
 // lengths: P2P items = (leaf, slice of its strong list) with about
-// kP2PItemSources source points, M2L items = (box, at most kM2LItemPairs weak
+// kP2PItemSources source points, M2L items = (box, at most m2l_item_pairs() weak
 // entries).  A box whose list is split keeps its items contiguous; their
 // partial sums are added in item order later (deterministic).
 // int4 item = (box, list begin, list end, first item of the box or -1 when
@@ -1272,11 +1272,16 @@ __device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* c
     return base + (unsigned long long)(incl - k);
 }
 
+// M2L rows (the order in which the M2L kernels take the items): a box's full
+// items (K pairs) take consecutive rows from rowctr[kM2LItemPairsMax]; its
+// short last item (length r < K) is counted in rowctr[r] and placed by
+// k_m2l_rows once all counts are known.
 __global__ void k_items(int nbox, const int32_t* __restrict__ child0, const int32_t* __restrict__ bcount,
                         const int32_t* __restrict__ soff, const int32_t* __restrict__ ns,
                         const int32_t* __restrict__ woff, const int32_t* __restrict__ nw, unsigned long long* ctr,
                         int4* p2p_items, int2* leaf_items, long long p2p_cap, int4* m2l_items, int2* box_m2l,
-                        long long m2l_cap, unsigned* status) {
+                        long long m2l_cap, int K, unsigned long long* rowctr, int32_t* rows, int2* box_tail,
+                        unsigned* status) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (*((volatile unsigned*)status) & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW)) return;  // uniform
     const bool in = b < nbox;
@@ -1298,16 +1303,48 @@ __global__ void k_items(int nbox, const int32_t* __restrict__ child0, const int3
         }
     }
     const int m = in ? nw[b] - woff[b] : 0;
-    const int km = (m + kM2LItemPairs - 1) / kM2LItemPairs;
+    const int km = (m + K - 1) / K;
+    const int nfull = m / K, r = m - nfull * K;
     const unsigned long long bm = warp_reserve(ctr + 3, km);
+    const unsigned long long bf = warp_reserve(rowctr + kM2LItemPairsMax, nfull);
     if (!in) return;
     box_m2l[b] = make_int2((int)bm, km);
+    box_tail[b] = make_int2(r, r > 0 ? (int)atomicAdd(rowctr + r, 1ull) : 0);
     if ((long long)(bm + km) > m2l_cap) {
         atomicOr(status, ST_ITEM_OVERFLOW);
     } else {
         for (int c = 0; c < km; ++c)
-            m2l_items[bm + c] = make_int4(b, c * kM2LItemPairs, min(m, (c + 1) * kM2LItemPairs), km > 1 ? (int)bm : -1);
+            m2l_items[bm + c] = make_int4(b, c * K, min(m, (c + 1) * K), km > 1 ? (int)bm : -1);
+        for (int c = 0; c < nfull; ++c) {
+            if ((long long)(bf + c) < m2l_cap) rows[bf + c] = (int32_t)(bm + c);
+            else atomicOr(status, ST_ITEM_OVERFLOW);
+        }
     }
+}
+
+// Rows of the short last items: after the full items, by decreasing length
+// (rank among equal lengths from k_items' counter).
+__global__ void k_m2l_rows(int nbox, const int2* __restrict__ box_m2l, const int2* __restrict__ box_tail,
+                           const unsigned long long* __restrict__ rowctr, long long m2l_cap, int32_t* rows,
+                           unsigned* status) {
+    __shared__ unsigned long long base[kM2LItemPairsMax];
+    if (*((volatile unsigned*)status) & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW | ST_ITEM_OVERFLOW)) return;
+    if (threadIdx.x == 0) {
+        unsigned long long s = rowctr[kM2LItemPairsMax];  // full items come first
+        for (int r = kM2LItemPairsMax - 1; r >= 1; --r) {
+            base[r] = s;
+            s += rowctr[r];
+        }
+    }
+    __syncthreads();
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    const int2 tl = box_tail[b];
+    if (tl.x <= 0) return;
+    const int2 mi = box_m2l[b];
+    const unsigned long long pos = base[tl.x] + (unsigned long long)tl.y;
+    if ((long long)pos < m2l_cap) rows[pos] = mi.x + mi.y - 1;
+    else atomicOr(status, ST_INTERNAL);
 }
 
 // Totals for fmm_get_tree_info (diagnostics, not on the evaluation path).
@@ -1411,6 +1448,8 @@ fmm_status alloc_build(Tree& t) {
     if ((st = dalloc(&t.d_nw, nb))) return st;
     if ((st = dalloc(&t.d_leaf_items, nb))) return st;
     if ((st = dalloc(&t.d_box_m2l, nb))) return st;
+    if ((st = dalloc(&t.d_box_tail, nb))) return st;
+    if ((st = dalloc(&t.d_m2l_rowctr, kM2LItemPairsMax + 1))) return st;
     if (!t.d_status) {
         if ((st = dalloc(reinterpret_cast<unsigned long long**>(&t.d_status), 8))) return st;
     }
@@ -1435,6 +1474,7 @@ fmm_status alloc_lists(Tree& t) {
     if ((st = dalloc(&t.d_widx, (size_t)t.wcap_tot))) return st;
     if ((st = dalloc(&t.d_p2p_items, (size_t)t.p2p_cap))) return st;
     if ((st = dalloc(&t.d_m2l_items, (size_t)t.m2l_cap))) return st;
+    if ((st = dalloc(&t.d_m2l_rows, (size_t)t.m2l_cap))) return st;
     return FMM_OK;
 }
 
@@ -1534,10 +1574,14 @@ fmm_status run_lists(Tree& t, cudaStream_t s) {
                                                  t.d_ltstat + lstride * (size_t)(l - 1), tiles_cap, t.scap_tot,
                                                  t.wcap_tot, need, t.d_status);
     }
+    FMM_CUDA(cudaMemsetAsync(t.d_m2l_rowctr, 0, (kM2LItemPairsMax + 1) * sizeof(unsigned long long), s));
     k_items<<<nblk(t.nbox, 128), 128, 0, s>>>((int)t.nbox, t.d_child0, t.d_bcount, t.d_soff, t.d_ns, t.d_woff,
                                               t.d_nw, ctr,
                                               t.d_p2p_items, t.d_leaf_items, t.p2p_cap, t.d_m2l_items, t.d_box_m2l,
-                                              t.m2l_cap, t.d_status);
+                                              t.m2l_cap, m2l_item_pairs(t), t.d_m2l_rowctr, t.d_m2l_rows,
+                                              t.d_box_tail, t.d_status);
+    k_m2l_rows<<<nblk(t.nbox, 256), 256, 0, s>>>((int)t.nbox, t.d_box_m2l, t.d_box_tail, t.d_m2l_rowctr, t.m2l_cap,
+                                                 t.d_m2l_rows, t.d_status);
     FMM_CUDA(cudaGetLastError());
     return FMM_OK;
 }

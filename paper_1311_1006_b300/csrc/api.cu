@@ -632,7 +632,7 @@ fmm_status fmm_phase_times(fmm_tree* h, double* out, int nout) {
     FMM_CUDA(cudaEventElapsedTime(&ms[2], t.ev_t[2], t.ev_t[3]));
     FMM_CUDA(cudaEventElapsedTime(&ms[3], t.ev_t[3], t.ev_t[4]));
     FMM_CUDA(cudaEventElapsedTime(&ms[4], t.ev_t[5], t.ev_t[6]));
-    FMM_CUDA(cudaEventElapsedTime(&ms[5], t.ev_t[4], t.ev_t[7]));
+    FMM_CUDA(cudaEventElapsedTime(&ms[5], t.ev_t[8], t.ev_t[7]));
     FMM_CUDA(cudaEventElapsedTime(&ms[6], t.ev_t[0], t.ev_t[7]));
     for (int i = 0; i < nout && i < 7; ++i) out[i] = ms[i];
     return FMM_OK;

@@ -219,7 +219,7 @@ struct Tree {
     cudaStream_t s_far2 = nullptr;  // second strength set's far-field chain (log kernel, adjoint; highest priority)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join_far = nullptr, ev_join_far2 = nullptr;
     cudaEvent_t ev_gather = nullptr;  // strengths gathered (fmm_step: P2P waits on it)
-    cudaEvent_t ev_t[8] = {};
+    cudaEvent_t ev_t[9] = {};  // phase boundaries of a timed evaluation (fmm_phase_times)
     bool timing_valid = false;
 
     // captured evaluation graph (keyed by the user pointers it bakes in)

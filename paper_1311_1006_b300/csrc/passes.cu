@@ -1694,6 +1694,7 @@ fmm_status run_eval(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s)
         launch_p2p<false>(t, B, s);
         if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[6], s));
     }
+    if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[8], s));  // both halves done: L2P + combine from here
     dispatch_l2p(t, B, d_phi, s);
     if (timing) FMM_CUDA(cudaEventRecord(t.ev_t[7], s));
     FMM_CUDA(cudaGetLastError());

@@ -1305,11 +1305,12 @@ __global__ void k_items(int nbox, const int32_t* __restrict__ child0, const int3
     const int m = in ? nw[b] - woff[b] : 0;
     const int km = (m + K - 1) / K;
     const int nfull = m / K, r = m - nfull * K;
+    const int rank = r > 0 ? (int)atomicAdd(rowctr + r, 1ull) : 0;  // issued first: its latency overlaps the rest
     const unsigned long long bm = warp_reserve(ctr + 3, km);
     const unsigned long long bf = warp_reserve(rowctr + kM2LItemPairsMax, nfull);
     if (!in) return;
     box_m2l[b] = make_int2((int)bm, km);
-    box_tail[b] = make_int2(r, r > 0 ? (int)atomicAdd(rowctr + r, 1ull) : 0);
+    box_tail[b] = make_int2(r, rank);
     if ((long long)(bm + km) > m2l_cap) {
         atomicOr(status, ST_ITEM_OVERFLOW);
     } else {
@@ -1323,18 +1324,20 @@ __global__ void k_items(int nbox, const int32_t* __restrict__ child0, const int3
 }
 
 // Rows of the short last items: after the full items, by decreasing length
-// (rank among equal lengths from k_items' counter).
+// (rank among equal lengths from k_items' counter).  Blocks of kM2LItemPairsMax threads.
+static_assert(kM2LItemPairsMax == 256, "k_m2l_rows: one thread per item length in its blocks of 256");
 __global__ void k_m2l_rows(int nbox, const int2* __restrict__ box_m2l, const int2* __restrict__ box_tail,
                            const unsigned long long* __restrict__ rowctr, long long m2l_cap, int32_t* rows,
                            unsigned* status) {
     __shared__ unsigned long long base[kM2LItemPairsMax];
+    __shared__ int wsum[32];
     if (*((volatile unsigned*)status) & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW | ST_ITEM_OVERFLOW)) return;
-    if (threadIdx.x == 0) {
-        unsigned long long s = rowctr[kM2LItemPairsMax];  // full items come first
-        for (int r = kM2LItemPairsMax - 1; r >= 1; --r) {
-            base[r] = s;
-            s += rowctr[r];
-        }
+    {  // base[r] = full items + short items longer than r: thread i takes length r = kM2LItemPairsMax - 1 - i
+        const int r = kM2LItemPairsMax - 1 - (int)threadIdx.x;
+        const int c = r >= 1 ? (int)rowctr[r] : 0;
+        int total;
+        const int ex = block_excl_scan(c, wsum, total);
+        if (r >= 0) base[r] = rowctr[kM2LItemPairsMax] + (unsigned long long)ex;
     }
     __syncthreads();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;

@@ -286,7 +286,11 @@ typedef enum {
     FMM_EXPORT_INST = 12,     /* int64[3*ninst]: point offset, box offset, N_levels per instance */
     FMM_EXPORT_RHO = 13,      /* float64[nbox]: scale radius rho of each box */
     FMM_EXPORT_STRONG_OFF = 14, /* int32[nbox]  first entry of each strong list */
-    FMM_EXPORT_WEAK_OFF = 15    /* int32[nbox] */
+    FMM_EXPORT_WEAK_OFF = 15,   /* int32[nbox] */
+    FMM_EXPORT_M2L_ITEMS = 16,  /* int32[4*m2l_items]: M2L work items (box, list begin, list end, first item of
+                                   the box or -1), a box's items consecutive */
+    FMM_EXPORT_M2L_ROWS = 17    /* int32[m2l_items]: the order in which the M2L kernels take the items (row ->
+                                   item): full items first, then each box's shorter last item by decreasing length */
 } fmm_export_what;
 
 fmm_status fmm_tree_export(const fmm_tree* t, int what, void* h_dst, int64_t count, void* stream);

@@ -237,6 +237,7 @@ class Tree:
             "soff": (np.int32, nb), "woff": (np.int32, nb),
             "mpole": (np.float64, 2 * nb * p), "local": (np.float64, 2 * nb * p),
             "near": (np.float64, 2 * n), "inst": (np.int64, 3 * inf["ninst"]),
+            "m2l_items": (np.int32, max(4 * inf["m2l_items"], 1)), "m2l_rows": (np.int32, max(inf["m2l_items"], 1)),
         }[what]
         buf = np.zeros(spec[1], dtype=spec[0])
         _lib.check(_lib.load().fmm_tree_export(self._h, _lib.EXPORT[what], ctypes.c_void_p(buf.ctypes.data),
@@ -249,6 +250,10 @@ class Tree:
             return buf.view(np.complex128)
         if what == "inst":
             return buf.reshape(-1, 3)
+        if what == "m2l_items":
+            return buf[: 4 * inf["m2l_items"]].reshape(-1, 4)
+        if what == "m2l_rows":
+            return buf[: inf["m2l_items"]]
         return buf
 
     def lists(self):

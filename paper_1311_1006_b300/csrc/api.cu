@@ -710,6 +710,8 @@ fmm_status fmm_tree_export(const fmm_tree* h, int what, void* h_dst, int64_t cou
         case FMM_EXPORT_STRONG: return copy(t.d_sidx, (int64_t)t.h_counts[0], 4);
         case FMM_EXPORT_WEAK_OFF: return copy(t.d_woff, nb, 4);
         case FMM_EXPORT_WEAK: return copy(t.d_widx, (int64_t)t.h_counts[1], 4);
+        case FMM_EXPORT_M2L_ITEMS: return copy(t.d_m2l_items, 4 * (int64_t)t.h_counts[3], 4);
+        case FMM_EXPORT_M2L_ROWS: return copy(t.d_m2l_rows, (int64_t)t.h_counts[3], 4);
         case FMM_EXPORT_INST: {
             if (count < 3 * (int64_t)t.ninst) return invalid("host buffer too small");
             int64_t* o = static_cast<int64_t*>(h_dst);

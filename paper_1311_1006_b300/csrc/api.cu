@@ -663,10 +663,10 @@ fmm_status fmm_get_tree_info(const fmm_tree* h, fmm_tree_info* out) {
     const int lg = std::min(t.l0, lv);
     // kernels per build: keys 1, sort 1 + 8 (onesweep; 8 x 3 beyond 2^30 points), root geometry 1, first cut
     // flags 1, per global level 2 partitions + geometry, subtree 1, finalize 1, lists root 1 + one pass per
-    // level, items 1; batched: instance keys 1 + 2 sort passes x 3
+    // level, items 1, M2L row order 1; batched: instance keys 1 + 2 sort passes x 3
     const int sortk = t.n < (1 << 30) ? 9 : 24;
     out->launches_build =
-        5 + sortk + lv + 3 * lg + (lg > 0 ? 1 : 0) + (lg < lv ? 1 : 0) + (t.ninst > 1 ? 7 : 0);
+        6 + sortk + lv + 3 * lg + (lg > 0 ? 1 : 0) + (lg < lv ? 1 : 0) + (t.ninst > 1 ? 7 : 0);
     // per evaluation: gather, P2M, M2M per level, M2L, M2L partial sums, L2L per level (not the deepest on
     // the FP32 path), P2P, P2P partial sums, L2P
     out->launches_eval = 7 + 2 * lv - (fold_leaf_l2l(t) ? 1 : 0);

@@ -1256,20 +1256,34 @@ __global__ void __launch_bounds__(kLThreads) k_lists_level(
 // partial sums are added in item order later (deterministic).
 // int4 item = (box, list begin, list end, first item of the box or -1 when
 // the box has a single item).
-// One atomic per warp: lanes reserve k items each from a global counter.
-__device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* ctr, int k) {
+// One atomic per warp and counter: lanes reserve k0, k1, k2 entries from three
+// global counters; the scans come first, then lane 31's three atomics back to
+// back (their latencies overlap instead of adding up).
+__device__ __forceinline__ void warp_reserve3(unsigned long long* c0, int k0, unsigned long long* c1, int k1,
+                                              unsigned long long* c2, int k2, unsigned long long& b0,
+                                              unsigned long long& b1, unsigned long long& b2) {
     const int lane = threadIdx.x & 31;
-    int incl = k;
+    int i0 = k0, i1 = k1, i2 = k2;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
+        const int y0 = __shfl_up_sync(0xffffffffu, i0, o);
+        const int y1 = __shfl_up_sync(0xffffffffu, i1, o);
+        const int y2 = __shfl_up_sync(0xffffffffu, i2, o);
+        if (lane >= o) {
+            i0 += y0;
+            i1 += y1;
+            i2 += y2;
+        }
     }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    unsigned long long base = 0;
-    if (lane == 31 && total > 0) base = atomicAdd(ctr, (unsigned long long)total);
-    base = __shfl_sync(0xffffffffu, base, 31);
-    return base + (unsigned long long)(incl - k);
+    unsigned long long a0 = 0, a1 = 0, a2 = 0;
+    if (lane == 31) {
+        if (i0 > 0) a0 = atomicAdd(c0, (unsigned long long)i0);
+        if (i1 > 0) a1 = atomicAdd(c1, (unsigned long long)i1);
+        if (i2 > 0) a2 = atomicAdd(c2, (unsigned long long)i2);
+    }
+    b0 = __shfl_sync(0xffffffffu, a0, 31) + (unsigned long long)(i0 - k0);
+    b1 = __shfl_sync(0xffffffffu, a1, 31) + (unsigned long long)(i1 - k1);
+    b2 = __shfl_sync(0xffffffffu, a2, 31) + (unsigned long long)(i2 - k2);
 }
 
 // M2L rows (the order in which the M2L kernels take the items): a box's full
@@ -1292,7 +1306,12 @@ __global__ void k_items(int nbox, const int32_t* __restrict__ child0, const int3
         C = max(1, kP2PItemSources / max(bcount[b], 1));
         kp = (n + C - 1) / C;
     }
-    const unsigned long long bp = warp_reserve(ctr + 2, kp);
+    const int m = in ? nw[b] - woff[b] : 0;
+    const int km = (m + K - 1) / K;
+    const int nfull = m / K, r = m - nfull * K;
+    const int rank = r > 0 ? (int)atomicAdd(rowctr + r, 1ull) : 0;  // issued first: its latency overlaps the rest
+    unsigned long long bp, bm, bf;
+    warp_reserve3(ctr + 2, kp, ctr + 3, km, rowctr + kM2LItemPairsMax, nfull, bp, bm, bf);
     if (leaf) {
         leaf_items[b] = make_int2((int)bp, kp);
         if ((long long)(bp + kp) > p2p_cap) {
@@ -1302,12 +1321,6 @@ __global__ void k_items(int nbox, const int32_t* __restrict__ child0, const int3
                 p2p_items[bp + c] = make_int4(b, c * C, min(n, (c + 1) * C), kp > 1 ? (int)bp : -1);
         }
     }
-    const int m = in ? nw[b] - woff[b] : 0;
-    const int km = (m + K - 1) / K;
-    const int nfull = m / K, r = m - nfull * K;
-    const int rank = r > 0 ? (int)atomicAdd(rowctr + r, 1ull) : 0;  // issued first: its latency overlaps the rest
-    const unsigned long long bm = warp_reserve(ctr + 3, km);
-    const unsigned long long bf = warp_reserve(rowctr + kM2LItemPairsMax, nfull);
     if (!in) return;
     box_m2l[b] = make_int2((int)bm, km);
     box_tail[b] = make_int2(r, rank);

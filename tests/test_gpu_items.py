@@ -17,14 +17,19 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("path,K", [("fp32", 192), ("fp64", 64)])
-def test_m2l_items_and_row_order(path, K):
+@pytest.mark.parametrize("path,K,batched", [("fp32", 192, False), ("fp64", 64, False), ("fp32", 192, True)])
+def test_m2l_items_and_row_order(path, K, batched):
     from paper_1311_1006_b300 import Tree
 
     g = np.random.default_rng(21)
     n = 200_000
     xy = W.cluster_mix(n, g)
-    t = Tree.build(torch.tensor(xy, device="cuda"), p=17, nlevels=7, path=path)
+    X = torch.tensor(xy, device="cuda")
+    if batched:  # instances of different depths: many short lists and short last items
+        offs = np.array([0, 1000, 21000, 21500, 90000, n])
+        t = Tree.build_batched(X, offs, p=17, path=path)
+    else:
+        t = Tree.build(X, p=17, nlevels=7, path=path)
     nw = t.export("nweak")
     items, rows = t.export("m2l_items"), t.export("m2l_rows")
     t.close()

@@ -37,6 +37,10 @@ def _points(kind, n, seed):
         xy = W.uniform(n, g)
         xy[n // 2:] = xy[: n - n // 2]
         return xy
+    if kind == "far":  # small clustered set far from the origin: FP32 coordinates must be taken relative to it
+        return 1e4 + 1e-2 * W.cluster_mix(n, g)
+    if kind == "neg":  # negative and positive coordinates, a wider box than the unit square
+        return 4.0 * W.cluster_mix(n, g) - 3.0
     raise ValueError(kind)
 
 
@@ -50,7 +54,7 @@ def _tree(xy, L, p=17, theta=0.5, path="fp64"):
 
 @pytest.mark.parametrize("kind,n,L", [("uniform", 1000, 4), ("cluster", 5000, 5), ("ties", 777, 4),
                                       ("line", 3001, 5), ("dup", 640, 4), ("uniform", 1, 1), ("uniform", 5, 2),
-                                      ("cluster", 20000, 7), ("uniform", 4096, 7)])
+                                      ("cluster", 20000, 7), ("uniform", 4096, 7), ("far", 3000, 5), ("neg", 3000, 5)])
 def test_tree_bit_exact(orc, kind, n, L):
     xy = _points(kind, n, seed=n + L)
     t = _tree(xy, L)
@@ -128,6 +132,8 @@ def _check_eval(orc, xy, gam, L, p, theta, path):
     ("uniform", 3, 1, 4, 0.5),
     ("uniform", 4096, 7, 32, 0.5),     # one point per leaf, largest order
     ("cluster", 3001, 5, 1, 0.5),      # p = 1
+    ("far", 6000, 5, 17, 0.5),
+    ("neg", 6000, 5, 17, 0.5),
 ])
 @pytest.mark.parametrize("path,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
 def test_eval_matches_oracle(orc, kind, n, L, p, theta, path, tol):

@@ -104,8 +104,10 @@ static fmm_status ensure_streams(Tree& t) {
 // Lists + work items of a built tree, with the one host synchronisation of a
 // build: the first build learns the exact list and item sizes from the device
 // counters; a capacity that was too small is grown (25 % slack) and the lists
-// are rebuilt.
-static fmm_status build_lists(Tree& t, cudaStream_t s) {
+// are rebuilt.  When the short coordinate sort met a run it does not resolve,
+// the tree is rebuilt from d_xy with the full sort (for this tree from then
+// on) and *redone is set.
+static fmm_status build_lists(Tree& t, cudaStream_t s, const double* d_xy, bool* redone) {
     fmm_status st;
     for (int attempt = 0; attempt < 16; ++attempt) {
         if ((st = run_lists(t, s))) return st;
@@ -115,6 +117,13 @@ static fmm_status build_lists(Tree& t, cudaStream_t s) {
         FMM_CUDA(cudaMemcpyAsync(lb, t.d_lvl_base, sizeof(lb), cudaMemcpyDeviceToHost, s));
         FMM_CUDA(cudaStreamSynchronize(s));
         const unsigned bits = (unsigned)(hbuf[0] & 0xffffffffu);
+        if ((bits & ST_SORT_RUN) && !(bits & ST_NONFINITE)) {
+            t.sort_full = true;
+            if (t.s_far) FMM_CUDA(cudaStreamSynchronize(t.s_far));  // work that read the first tree is done
+            if ((st = run_tree_build(t, d_xy, s))) return st;
+            if (redone) *redone = true;
+            continue;
+        }
         if (bits & ST_NONFINITE) {
             set_error("non-finite point coordinate");
             return FMM_ERR_NONFINITE;
@@ -162,7 +171,7 @@ static fmm_status build_lists(Tree& t, cudaStream_t s) {
 static fmm_status build_all(Tree& t, const double* d_xy, cudaStream_t s) {
     fmm_status st = run_tree_build(t, d_xy, s);
     if (st) return st;
-    return build_lists(t, s);
+    return build_lists(t, s, d_xy, nullptr);
 }
 
 static fmm_status shape_and_build(Tree& t, const double* d_xy, cudaStream_t s, bool reshape) {
@@ -458,7 +467,15 @@ fmm_status fmm_step(fmm_tree* h, const double* d_xy, const double* d_gamma, void
     launch_gather(t, B, d_gamma, t.s_far);
     FMM_CUDA(cudaEventRecord(t.ev_gather, t.s_far));
     dispatch_up(t, B, t.s_far);
-    if ((st = build_lists(t, s))) return st;  // host check; the upward pass runs meanwhile
+    bool redone = false;
+    if ((st = build_lists(t, s, d_xy, &redone))) return st;  // host check; the upward pass runs meanwhile
+    if (redone) {  // the tree was built again (full coordinate sort): its gather and upward pass again
+        FMM_CUDA(cudaEventRecord(t.ev_fork, s));
+        FMM_CUDA(cudaStreamWaitEvent(t.s_far, t.ev_fork, 0));
+        launch_gather(t, B, d_gamma, t.s_far);
+        FMM_CUDA(cudaEventRecord(t.ev_gather, t.s_far));
+        dispatch_up(t, B, t.s_far);
+    }
     // the partial-sum buffers follow the list capacities just learned: allocate them now and take the
     // buffer table again (the one above predates them)
     if ((st = alloc_eval_parts(t))) return st;
@@ -664,7 +681,8 @@ fmm_status fmm_get_tree_info(const fmm_tree* h, fmm_tree_info* out) {
     // kernels per build: keys 1, sort 1 + 8 (onesweep; 8 x 3 beyond 2^30 points), root geometry 1, first cut
     // flags 1, per global level 2 partitions + geometry, subtree 1, finalize 1, lists root 1 + one pass per
     // level, items 1, M2L row order 1; batched: instance keys 1 + 2 sort passes x 3
-    const int sortk = t.n < (1 << 30) ? 9 : 24;
+    // sort: global counts + 8 passes, or + 4 passes + the run fix-up (the short sort of single trees)
+    const int sortk = t.n < (1 << 30) ? ((t.sort_full || t.ninst > 1) ? 9 : 6) : 24;
     out->launches_build =
         6 + sortk + lv + 3 * lg + (lg > 0 ? 1 : 0) + (lg < lv ? 1 : 0) + (t.ninst > 1 ? 7 : 0);
     // per evaluation: gather, P2M, M2M per level, M2L, M2L partial sums, L2L per level (not the deepest on

@@ -19,7 +19,8 @@ enum : unsigned {
     ST_WEAK_OVERFLOW = 4u,    // a weak list exceeded its fixed capacity
     ST_TIMEOUT = 8u,          // a bounded wait gave up
     ST_INTERNAL = 16u,        // an index check in a scatter failed (a bug, reported not written)
-    ST_ITEM_OVERFLOW = 32u    // a work-item array exceeded its capacity
+    ST_ITEM_OVERFLOW = 32u,   // a work-item array exceeded its capacity
+    ST_SORT_RUN = 64u         // the short coordinate sort met a run of equal high halves it does not resolve
 };
 
 // P2P lane layout for leaves of at most max_leaf points: lt target lanes x
@@ -98,6 +99,9 @@ struct Tree {
     int p = 17, P = 17, PS = 18, path = FMM_PATH_FP32, flags = 0;
     double theta = 0.5;
     bool batched = false;
+    // coordinate sort: false = the high 32 key bits by radix passes, then the short runs of equal high halves
+    // in place; true (set for good once a build met a longer run) = all 64 bits by radix passes
+    bool sort_full = false;
 
     // shape
     int64_t n = 0;

@@ -546,17 +546,64 @@ static fmm_status sort_pass(Tree& t, cudaStream_t s, int src, int dst, int shift
     return FMM_OK;
 }
 
+// Runs of equal high key halves after the high-half passes.  The passes are
+// stable, so inside a run the entries are in input order; the full order is by
+// (key, input index), i.e. by (key, position in the run).  Each entry counts
+// the entries of its run that precede it in that order and writes its value
+// (input index) to run start + count in the output; an entry outside any run
+// keeps its place.  Runs longer than kSortRunMax are reported (ST_SORT_RUN) and
+// copied unchanged (a permutation all the same: later kernels index with it),
+// and the host rebuilds with all 64 bits.  blockIdx.y = which sort; only the
+// values are written (the tree build needs the order, not the keys).
+constexpr int kSortRunMax = 16;
+__global__ void __launch_bounds__(256) k_sort_runs(const uint64_t* __restrict__ k0, const int32_t* __restrict__ v0,
+                                                   const uint64_t* __restrict__ k1, const int32_t* __restrict__ v1,
+                                                   int32_t* __restrict__ o0, int32_t* __restrict__ o1, int n,
+                                                   unsigned* status) {
+    const uint64_t* key = blockIdx.y ? k1 : k0;
+    const int32_t* val = blockIdx.y ? v1 : v0;
+    int32_t* out = blockIdx.y ? o1 : o0;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t ki = key[i];
+    const unsigned hi = (unsigned)(ki >> 32);
+    int s = i;
+    while (s > 0 && i - s < kSortRunMax && (unsigned)(key[s - 1] >> 32) == hi) --s;
+    int e = i + 1;
+    while (e < n && e - s <= kSortRunMax && (unsigned)(key[e] >> 32) == hi) ++e;
+    if (e - s == 1) {
+        out[i] = val[i];
+        return;
+    }
+    if (e - s > kSortRunMax || (s > 0 && (unsigned)(key[s - 1] >> 32) == hi)) {
+        if ((i & 15) == 0) atomicOr(status, ST_SORT_RUN);  // a long run holds such an i
+        out[i] = val[i];
+        return;
+    }
+    int rank = 0;
+    for (int j = s; j < e; ++j) {
+        const uint64_t kj = key[j];
+        rank += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
+    }
+    out[s + rank] = val[i];
+}
+
 // Words of the onesweep scratch for n points.
 static size_t sort_scratch_words(int64_t n) {
     const int64_t T = (n + kSortTile - 1) / kSortTile;
     return (size_t)(2 * 8 * 256 + 16 + 8 * 2 * T * 256);
 }
 
-// The 8 LSD passes over the 64-bit coordinate keys of both sorts: one kernel
-// for the global digit counts of every pass, then one onesweep kernel per
-// pass.  Scratch: d_sort_os = global counts [2][8][256], tickets [8][2], tile
-// status words [8][2][T][256]; zeroed once per build.
-static fmm_status sort_coordinates(Tree& t, cudaStream_t s) {
+// LSD passes over the 64-bit coordinate keys of both sorts: one kernel for the
+// global digit counts of every pass, then one onesweep kernel per pass.  full:
+// all 8 passes; otherwise the 4 passes of the high halves and then k_sort_runs
+// for the runs of equal high halves (short for point sets without heavy
+// repetition of the leading 20 mantissa bits; a longer run is reported and the
+// host rebuilds with full = true).  Both give the order by (key, input index).
+// Scratch: d_sort_os = global counts [2][8][256], tickets [8][2], tile status
+// words [8][2][T][256]; zeroed once per build.  *res: the buffer pair that
+// holds the sorted values (0: 0/1, 2: 2/3).
+static fmm_status sort_coordinates(Tree& t, cudaStream_t s, bool full, int* res) {
     const int n = (int)t.n;
     const int T = nblk(n, kSortTile);
     unsigned* gh = t.d_sort_os;
@@ -566,7 +613,7 @@ static fmm_status sort_coordinates(Tree& t, cudaStream_t s) {
     dim3 g(T, 2);
     k_sort_ghist<<<g, kSortThreads, 0, s>>>(t.d_keys[0], t.d_keys[1], n, gh);
     int src = 0;
-    for (int pass = 0; pass < 8; ++pass) {
+    for (int pass = full ? 0 : 4; pass < 8; ++pass) {  // an even number of passes: the result is in buffers 0/1
         const int dst = 2 - src;
         k_sort_scatter<true><<<g, kSortThreads, 0, s>>>(
             t.d_keys[src], t.d_vals[src], t.d_keys[src + 1], t.d_vals[src + 1], t.d_keys[dst], t.d_vals[dst],
@@ -574,6 +621,13 @@ static fmm_status sort_coordinates(Tree& t, cudaStream_t s) {
             tk + 2 * pass, t.d_status);
         FMM_CUDA(cudaGetLastError());
         src = dst;
+    }
+    *res = 0;
+    if (!full) {  // the runs: values 0/1 -> 2/3
+        k_sort_runs<<<dim3(nblk(n, 256), 2), 256, 0, s>>>(t.d_keys[0], t.d_vals[0], t.d_keys[1], t.d_vals[1],
+                                                         t.d_vals[2], t.d_vals[3], n, t.d_status);
+        FMM_CUDA(cudaGetLastError());
+        *res = 2;
     }
     return FMM_OK;
 }
@@ -1500,12 +1554,13 @@ fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s) {
     FMM_CUDA(cudaMemsetAsync(t.d_status, 0, sizeof(unsigned), s));
     k_keys<<<nblk(n, 256), 256, 0, s>>>(xy, n, t.d_keys[0], t.d_keys[1], t.d_vals[0], t.d_vals[1], t.d_status);
     FMM_CUDA(cudaGetLastError());
-    // 8 LSD passes over the 64-bit keys (+2 over the instance index when
+    // LSD passes over the 64-bit keys (+2 over the instance index when
     // batched); an even number of passes leaves the result in buffers 0/1.
     int src = 0;
     fmm_status st;
     if (n < (1 << 30)) {  // onesweep passes (30-bit counts in the tile status words)
-        if ((st = sort_coordinates(t, s))) return st;
+        // the short sort (high halves + runs) for single trees; a forest's instance passes follow a full sort
+        if ((st = sort_coordinates(t, s, t.sort_full || t.ninst > 1, &src))) return st;
     } else {
         for (int pass = 0; pass < 8; ++pass) {
             if ((st = sort_pass(t, s, src, 2 - src, 8 * pass))) return st;

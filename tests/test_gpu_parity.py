@@ -54,7 +54,8 @@ def _tree(xy, L, p=17, theta=0.5, path="fp64"):
 
 @pytest.mark.parametrize("kind,n,L", [("uniform", 1000, 4), ("cluster", 5000, 5), ("ties", 777, 4),
                                       ("line", 3001, 5), ("dup", 640, 4), ("uniform", 1, 1), ("uniform", 5, 2),
-                                      ("cluster", 20000, 7), ("uniform", 4096, 7), ("far", 3000, 5), ("neg", 3000, 5)])
+                                      ("cluster", 20000, 7), ("uniform", 4096, 7), ("far", 3000, 5), ("neg", 3000, 5),
+                                      ("cluster", 300000, 8)])
 def test_tree_bit_exact(orc, kind, n, L):
     xy = _points(kind, n, seed=n + L)
     t = _tree(xy, L)
@@ -168,6 +169,21 @@ def test_eval_is_deterministic_and_graph_replay_matches_eager(orc):
         c = t2.eval(G)
         torch.cuda.synchronize()
         assert torch.equal(a, b) and torch.equal(a, c)
+
+
+def test_coordinate_sort_runs_and_fallback(orc):
+    """The short coordinate sort (high key halves, then the runs of equal high
+    halves in place) and its fallback (a run longer than it resolves: the tree
+    is rebuilt with the full sort): trees equal the oracle's in both directions."""
+    xs = [_points("cluster", 50000, 3), _points("ties", 50000, 4), _points("cluster", 50000, 5)]
+    t = _tree(xs[0], 7)
+    for xy in xs:
+        t.rebuild(_dev(xy))
+        ref = orc.build_tree(xy, 7)
+        assert np.array_equal(t.export("perm"), ref["perm"])
+        assert np.array_equal(t.export("bstart"), ref["bstart"])
+        assert np.array_equal(t.export("center"), ref["center"])
+    t.close()
 
 
 def test_rebuild_changes_levels_and_points(orc):

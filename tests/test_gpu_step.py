@@ -82,3 +82,26 @@ def test_step_fallbacks_and_argument_checks():
         tt.n = 3000
         tt.step(xy[:3000], gam[:3000])
     tt.close()
+
+
+def test_step_rebuilds_after_a_long_run_of_equal_keys():
+    """Coordinates with many exact repeats: the first step's short sort meets a
+    run it does not resolve, so fmm_step builds the tree again with the full
+    sort (and launches the upward pass again); the result equals a tree built
+    and evaluated by the two-call sequence."""
+    from paper_1311_1006_b300 import Tree
+
+    g = np.random.default_rng(14)
+    n = 20000
+    xy = np.round(W.cluster_mix(n, g) * 50) / 50  # few distinct coordinates
+    gam = W.complex_strengths(n, g)
+    X, G = _dev(xy), _dev(gam)
+    for path in ("fp32", "fp64"):
+        a = Tree.build(_dev(W.uniform(n, g)), p=12, nlevels=6, path=path)
+        b = Tree.build(X, p=12, nlevels=6, path=path)
+        pa = a.step(X, G).cpu().numpy()
+        pb = b.eval(G).cpu().numpy()
+        assert np.array_equal(pa, pb)
+        assert np.array_equal(a.export("perm"), b.export("perm"))
+        a.close()
+        b.close()

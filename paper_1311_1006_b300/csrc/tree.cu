@@ -335,6 +335,8 @@ __global__ void __launch_bounds__(1024) k_sort_scan(const int32_t* __restrict__ 
 
 // Global digit counts of all 8 LSD passes of both sorts in one read of the
 // keys (a digit's count does not depend on the order): ghist[s][pass][digit].
+// P0 = first pass counted (4: the high halves only).
+template <int P0>
 __global__ void __launch_bounds__(kSortThreads) k_sort_ghist(const uint64_t* __restrict__ k0,
                                                              const uint64_t* __restrict__ k1, int n,
                                                              unsigned* __restrict__ ghist) {
@@ -348,7 +350,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_ghist(const uint64_t* __r
         if (i < n) {
             const uint64_t key = k[i];
 #pragma unroll
-            for (int p = 0; p < 8; ++p) atomicAdd(&h[p][(int)((key >> (8 * p)) & 255u)], 1u);
+            for (int p = P0; p < 8; ++p) atomicAdd(&h[p][(int)((key >> (8 * p)) & 255u)], 1u);
         }
     }
     __syncthreads();
@@ -611,7 +613,8 @@ static fmm_status sort_coordinates(Tree& t, cudaStream_t s, bool full, int* res)
     unsigned* stat = tk + 16;
     FMM_CUDA(cudaMemsetAsync(gh, 0, sort_scratch_words(n) * sizeof(unsigned), s));
     dim3 g(T, 2);
-    k_sort_ghist<<<g, kSortThreads, 0, s>>>(t.d_keys[0], t.d_keys[1], n, gh);
+    if (full) k_sort_ghist<0><<<g, kSortThreads, 0, s>>>(t.d_keys[0], t.d_keys[1], n, gh);
+    else k_sort_ghist<4><<<g, kSortThreads, 0, s>>>(t.d_keys[0], t.d_keys[1], n, gh);
     int src = 0;
     for (int pass = full ? 0 : 4; pass < 8; ++pass) {  // an even number of passes: the result is in buffers 0/1
         const int dst = 2 - src;
@@ -708,6 +711,18 @@ void launch_selftest_lookback(unsigned long long* st, int max_spins, unsigned* s
     k_selftest_lookback<<<1, 32, 0, s>>>(st, max_spins, status);
 }
 
+// Segment search over starts in shared or global memory (generic pointer).
+__device__ __forceinline__ int find_seg_any(const int32_t* start, int K, int i) {
+    int lo = 0, hi = K - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+constexpr int kPartSegSmem = 2048;  // segment starts kept in shared memory up to this many segments
+
 // Stable segmented partition in one pass per stage.  List A is cut into
 // segments; within segment k the entries with flag 0 (side[point] == 0) keep
 // their order at the front and the flag-1 entries keep their order after the
@@ -727,6 +742,12 @@ __global__ void __launch_bounds__(kPartThreads) k_part_fused(
     __shared__ int wsum[32];
     __shared__ int sh_tile;
     __shared__ long long sh_excl;
+    __shared__ int32_t s_start[kPartSegSmem + 1];  // the segment starts, when they fit
+    const bool seg_smem = K <= kPartSegSmem;
+    if (seg_smem)
+        for (int q = threadIdx.x; q <= K; q += kPartThreads) s_start[q] = start[q];
+    __syncthreads();
+    const int32_t* segs = seg_smem ? s_start : start;
     unsigned long long* ticket = tstat + T;
     while (true) {
         if (threadIdx.x == 0) sh_tile = (int)atomicAdd(ticket, 1ull);
@@ -753,8 +774,8 @@ __global__ void __launch_bounds__(kPartThreads) k_part_fused(
         __syncthreads();
         if (i0 >= n) continue;
         long long P = sh_excl + excl;  // flag-1 entries before position i0
-        int k = find_seg(start, K, i0);
-        int s = start[k], e = start[k + 1], nz = nzero[k];
+        int k = find_seg_any(segs, K, i0);
+        int s = segs[k], e = segs[k + 1], nz = nzero[k];
         long long ob = obefore[k];
 #pragma unroll
         for (int j = 0; j < kPartItems; ++j) {
@@ -762,8 +783,8 @@ __global__ void __launch_bounds__(kPartThreads) k_part_fused(
             if (i >= n) break;
             while (i >= e) {
                 ++k;
-                s = start[k];
-                e = start[k + 1];
+                s = segs[k];
+                e = segs[k + 1];
                 nz = nzero[k];
                 ob = obefore[k];
             }

@@ -567,19 +567,23 @@ __global__ void __launch_bounds__(256) k_sort_runs(const uint64_t* __restrict__ 
     int32_t* out = blockIdx.y ? o1 : o0;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    // the entry and both neighbours at once: most entries are not in a run
     const uint64_t ki = key[i];
+    const uint64_t kp = i > 0 ? key[i - 1] : 0, kn = i + 1 < n ? key[i + 1] : 0;
+    const int32_t vi = val[i];
     const unsigned hi = (unsigned)(ki >> 32);
-    int s = i;
-    while (s > 0 && i - s < kSortRunMax && (unsigned)(key[s - 1] >> 32) == hi) --s;
-    int e = i + 1;
-    while (e < n && e - s <= kSortRunMax && (unsigned)(key[e] >> 32) == hi) ++e;
-    if (e - s == 1) {
-        out[i] = val[i];
+    const bool prev = i > 0 && (unsigned)(kp >> 32) == hi, next = i + 1 < n && (unsigned)(kn >> 32) == hi;
+    if (!prev && !next) {
+        out[i] = vi;
         return;
     }
+    int s = prev ? i - 1 : i;
+    while (s > 0 && i - s < kSortRunMax && (unsigned)(key[s - 1] >> 32) == hi) --s;
+    int e = next ? i + 2 : i + 1;
+    while (e < n && e - s <= kSortRunMax && (unsigned)(key[e] >> 32) == hi) ++e;
     if (e - s > kSortRunMax || (s > 0 && (unsigned)(key[s - 1] >> 32) == hi)) {
         if ((i & 15) == 0) atomicOr(status, ST_SORT_RUN);  // a long run holds such an i
-        out[i] = val[i];
+        out[i] = vi;
         return;
     }
     int rank = 0;
@@ -587,7 +591,7 @@ __global__ void __launch_bounds__(256) k_sort_runs(const uint64_t* __restrict__ 
         const uint64_t kj = key[j];
         rank += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
     }
-    out[s + rank] = val[i];
+    out[s + rank] = vi;
 }
 
 // Words of the onesweep scratch for n points.

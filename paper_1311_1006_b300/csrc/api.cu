@@ -686,8 +686,8 @@ fmm_status fmm_get_tree_info(const fmm_tree* h, fmm_tree_info* out) {
     out->launches_build =
         6 + sortk + lv + 3 * lg + (lg > 0 ? 1 : 0) + (lg < lv ? 1 : 0) + (t.ninst > 1 ? 7 : 0);
     // per evaluation: gather, P2M, M2M per level, M2L, M2L partial sums, L2L per level (not the deepest on
-    // the FP32 path), P2P, P2P partial sums, L2P
-    out->launches_eval = 7 + 2 * lv - (fold_leaf_l2l(t) ? 1 : 0);
+    // the FP32 path), P2P, L2P (which adds the P2P partial sums of split leaves)
+    out->launches_eval = 6 + 2 * lv - (fold_leaf_l2l(t) ? 1 : 0);
     out->autotune_theta = t.tune.theta_on ? t.tune.theta : t.theta;
     return FMM_OK;
 }

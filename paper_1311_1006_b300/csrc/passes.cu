@@ -641,6 +641,29 @@ constexpr int kWarpShiftMax = 1024;  // measured against 4096 and 16384: 1024 fa
 
 // ------------------------------------------------------------- L2P + sum
 
+// Near field of sorted point i: P2P wrote it directly when its leaf has one
+// work item, else one partial sum per item, added here in item order.
+template <typename C>
+struct NearParts {
+    const int2* leaf_items;  // per box: first P2P item, item count
+    const int32_t* bstart;
+    const C* part;           // partial sums, row stride TS
+    int TS;
+};
+template <typename C>
+__device__ __forceinline__ C near_of(int i, int lf, const C* __restrict__ nearv, const NearParts<C>& np) {
+    const int2 li = np.leaf_items[lf];
+    if (li.y <= 1) return nearv[i];
+    const int t = i - np.bstart[lf];
+    C s{};
+    for (int q = 0; q < li.y; ++q) {
+        const C v = np.part[(size_t)(li.x + q) * np.TS + t];
+        s.x += v.x;
+        s.y += v.y;
+    }
+    return s;
+}
+
 // Scaled offset w = (z - c_b) / rho_b of a point from box b (FP32 hi/lo coordinates).
 __device__ __forceinline__ float2 scaled_offset(const float4 pt, const float4* __restrict__ chl,
                                                 const float* __restrict__ rho32, int b) {
@@ -672,7 +695,7 @@ __global__ void __launch_bounds__(256) k_l2p32(int n, const int32_t* __restrict_
                                                const float4* __restrict__ chl,
                                                const float* __restrict__ rho32, const float4* __restrict__ pos4,
                                                const float2* __restrict__ L32, const float2* __restrict__ Lm2l,
-                                               const float2* __restrict__ nearv,
+                                               const float2* __restrict__ nearv, const NearParts<float2> np,
                                                const int32_t* __restrict__ perm, float2* __restrict__ out, int p,
                                                int PS) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -691,7 +714,7 @@ __global__ void __launch_bounds__(256) k_l2p32(int n, const int32_t* __restrict_
     } else {
         v = horner_p<P>(L32 + (size_t)lf * PS, scaled_offset(pt, chl, rho32, lf), P);
     }
-    const float2 nv = nearv[i];
+    const float2 nv = near_of(i, lf, nearv, np);
     out[perm[i]] = make_float2(v.x + nv.x, v.y + nv.y);
 }
 
@@ -700,7 +723,8 @@ __global__ void __launch_bounds__(256) k_l2p64(int n, const int32_t* __restrict_
                                                const double2* __restrict__ center,
                                                const double* __restrict__ rho, const double2* __restrict__ pts,
                                                const double2* __restrict__ L64, const double2* __restrict__ nearv,
-                                               const int32_t* __restrict__ perm, double2* __restrict__ out, int PS) {
+                                               const NearParts<double2> np, const int32_t* __restrict__ perm,
+                                               double2* __restrict__ out, int PS) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int lf = leaf_of[i];
@@ -713,7 +737,7 @@ __global__ void __launch_bounds__(256) k_l2p64(int n, const int32_t* __restrict_
     double2 v = Lb[P - 1];
 #pragma unroll
     for (int l = P - 2; l >= 0; --l) v = cfma(v, w, Lb[l]);
-    const double2 nv = nearv[i];
+    const double2 nv = near_of(i, lf, nearv, np);
     out[perm[i]] = make_double2(v.x + nv.x, v.y + nv.y);
 }
 
@@ -757,7 +781,7 @@ __global__ void __launch_bounds__(256) k_l2p32_log(int n, const int32_t* __restr
                                                    const float* __restrict__ rho32, const float4* __restrict__ pos4,
                                                    const float2* __restrict__ L0, const float2* __restrict__ L1,
                                                    const float2* __restrict__ M0, const float2* __restrict__ M1,
-                                                   const float2* __restrict__ nearv,
+                                                   const float2* __restrict__ nearv, const NearParts<float2> np,
                                                    const int32_t* __restrict__ perm, float2* __restrict__ out, int p,
                                                    int PS) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -776,7 +800,7 @@ __global__ void __launch_bounds__(256) k_l2p32_log(int n, const int32_t* __restr
         f0 += log_local_eval_p<P>(M0 + (size_t)lf * PS, wl, rl, p);
         f1 += log_local_eval_p<P>(M1 + (size_t)lf * PS, wl, rl, p);
     }
-    const float2 nv = nearv[i];
+    const float2 nv = near_of(i, lf, nearv, np);
     out[perm[i]] = make_float2(f0 + nv.x, f1 + nv.y);
 }
 
@@ -785,7 +809,7 @@ __global__ void __launch_bounds__(256) k_l2p64_log(int n, const int32_t* __restr
                                                    const double2* __restrict__ center,
                                                    const double* __restrict__ rho, const double2* __restrict__ pts,
                                                    const double2* __restrict__ L0, const double2* __restrict__ L1,
-                                                   const double2* __restrict__ nearv,
+                                                   const double2* __restrict__ nearv, const NearParts<double2> np,
                                                    const int32_t* __restrict__ perm, double2* __restrict__ out,
                                                    int PS) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -798,7 +822,7 @@ __global__ void __launch_bounds__(256) k_l2p64_log(int n, const int32_t* __restr
     const double2 w = make_double2((pt.x - c.x) * inv, (pt.y - c.y) * inv);
     const double f0 = log_local_eval<P>(L0 + (size_t)lf * PS, w, r);
     const double f1 = log_local_eval<P>(L1 + (size_t)lf * PS, w, r);
-    const double2 nv = nearv[i];
+    const double2 nv = near_of(i, lf, nearv, np);
     out[perm[i]] = make_double2(f0 + nv.x, f1 + nv.y);
 }
 
@@ -1160,33 +1184,6 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, TPL > 4 ? 2 : 7)
     }
 }
 
-// Near field of leaves whose strong list was split into several items: one
-// warp per leaf adds the item partial sums of each target in item order.
-template <typename C>
-__global__ void __launch_bounds__(256) k_reduce_p2p(const int32_t* __restrict__ leaves, int nleaf,
-                                                    const int2* __restrict__ leaf_items,
-                                                    const int32_t* __restrict__ bstart,
-                                                    const int32_t* __restrict__ bcount, const C* __restrict__ part,
-                                                    int TS, C* __restrict__ nearv) {
-    const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (w >= nleaf) return;
-    const int b = leaves[w];
-    const int2 li = leaf_items[b];
-    if (li.y <= 1) return;
-    const int ts = bstart[b], tn = bcount[b];
-    for (int t = lane; t < tn; t += 32) {
-        C s{};
-#pragma unroll 8
-        for (int q = 0; q < li.y; ++q) {
-            const C v = part[(size_t)(li.x + q) * TS + t];
-            s.x += v.x;
-            s.y += v.y;
-        }
-        nearv[ts + t] = s;
-    }
-}
-
 // M2L sums of boxes whose weak list was split: one warp per box, lane = coefficient
 // (lanes stride over the PS slots: PS exceeds 32 at p = 32, with the log kernel's
 // constant term in slot 32).
@@ -1357,18 +1354,23 @@ static void launch_down_fp64(Tree& t, const Bufs& B, cudaStream_t s) {
     }
 }
 
+template <typename C>
+static NearParts<C> near_parts(const Tree& t, const Bufs& B) {
+    return NearParts<C>{t.d_leaf_items, t.d_bstart, static_cast<const C*>(B.p2p_part), t.max_leaf};
+}
+
 template <int P>
 static void launch_l2p(Tree& t, const Bufs& B, void* d_phi, cudaStream_t s) {
     const int n = (int)t.n;
     if (t.path == FMM_PATH_FP32) {
         k_l2p32<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_fold_par, t.d_box_m2l, t.d_chl, t.d_rho32,
                                                 t.d_pos4, B.L32, static_cast<const float2*>(B.Lm2l),
-                                                static_cast<const float2*>(B.near), t.d_perm,
+                                                static_cast<const float2*>(B.near), near_parts<float2>(t, B), t.d_perm,
                                                 static_cast<float2*>(d_phi), t.p, t.PS);
     } else {
         k_l2p64<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_center, t.d_rho, t.d_pts, B.L64,
-                                                static_cast<const double2*>(B.near), t.d_perm,
-                                                static_cast<double2*>(d_phi), t.PS);
+                                                static_cast<const double2*>(B.near), near_parts<double2>(t, B),
+                                                t.d_perm, static_cast<double2*>(d_phi), t.PS);
     }
 }
 
@@ -1379,11 +1381,12 @@ static void launch_l2p_log(Tree& t, const Bufs& B0, const Bufs& B1, void* d_phi,
         k_l2p32_log<P><<<nblk(n, 256), 256, 0, s>>>(
             n, t.d_leaf_of, t.d_fold_par, t.d_box_m2l, t.d_chl, t.d_rho32, t.d_pos4, B0.L32, B1.L32,
             static_cast<const float2*>(B0.Lm2l), static_cast<const float2*>(B1.Lm2l),
-            static_cast<const float2*>(B0.near), t.d_perm, static_cast<float2*>(d_phi), t.p, t.PS);
+            static_cast<const float2*>(B0.near), near_parts<float2>(t, B0), t.d_perm, static_cast<float2*>(d_phi), t.p,
+            t.PS);
     } else {
         k_l2p64_log<P><<<nblk(n, 256), 256, 0, s>>>(n, t.d_leaf_of, t.d_center, t.d_rho, t.d_pts, B0.L64, B1.L64,
-                                                    static_cast<const double2*>(B0.near), t.d_perm,
-                                                    static_cast<double2*>(d_phi), t.PS);
+                                                    static_cast<const double2*>(B0.near), near_parts<double2>(t, B0),
+                                                    t.d_perm, static_cast<double2*>(d_phi), t.PS);
     }
 }
 
@@ -1424,7 +1427,6 @@ static void launch_p2p(Tree& t, const Bufs& B, cudaStream_t s) {
         per_warp = 1 << 30;
         dgrid = std::min(nblk(p2p_grid_items(t), kP2PDWarps), t.num_sms * p2p_blocks_per_sm());
     }
-    const int rgrid = nblk(32 * t.nleaf, 256);
     const P2PLayout lay = p2p_layout(t.max_leaf);
     const int pad = (int)(t.nleaf * t.leaf_cap);
 #define FMM_P2P(V, C, TPL, LT)                                                                                   \
@@ -1459,16 +1461,10 @@ static void launch_p2p(Tree& t, const Bufs& B, cudaStream_t s) {
             default: FMM_P2P_PAIRS(8, 16) break;
         }
 #undef FMM_P2P_PAIRS
-        t.p2p_funcs.push_back(reinterpret_cast<const void*>(k_reduce_p2p<float2>));
-        k_reduce_p2p<float2><<<rgrid, 256, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, t.d_leaf_items, t.d_bstart,
-                                                   t.d_bcount, pt, t.max_leaf, nv);
     } else {
         double2* nv = static_cast<double2*>(B.near);
         double2* pt = static_cast<double2*>(B.p2p_part);
         FMM_P2P_LAYOUTS(double2, double2)
-        t.p2p_funcs.push_back(reinterpret_cast<const void*>(k_reduce_p2p<double2>));
-        k_reduce_p2p<double2><<<rgrid, 256, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, t.d_leaf_items, t.d_bstart,
-                                                    t.d_bcount, pt, t.max_leaf, nv);
     }
 #undef FMM_P2P_LAYOUTS
 #undef FMM_P2P

@@ -335,11 +335,14 @@ __global__ void __launch_bounds__(1024) k_sort_scan(const int32_t* __restrict__ 
 
 // Global digit counts of all 8 LSD passes of both sorts in one read of the
 // keys (a digit's count does not depend on the order): ghist[s][pass][digit].
-// P0 = first pass counted (4: the high halves only).
-template <int P0>
+// P0 = first pass counted (4: the high halves only).  FROM_XY: the keys are
+// formed here from the points (and non-finite coordinates reported) instead of
+// read.
+template <int P0, bool FROM_XY>
 __global__ void __launch_bounds__(kSortThreads) k_sort_ghist(const uint64_t* __restrict__ k0,
                                                              const uint64_t* __restrict__ k1, int n,
-                                                             unsigned* __restrict__ ghist) {
+                                                             unsigned* __restrict__ ghist,
+                                                             const double2* __restrict__ xy, unsigned* status) {
     __shared__ unsigned h[8][256];
     const int s = blockIdx.y;
     const uint64_t* k = s ? k1 : k0;
@@ -348,7 +351,14 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_ghist(const uint64_t* __r
     for (int r = 0; r < kSortRounds; ++r) {
         const int i = blockIdx.x * kSortTile + r * kSortThreads + threadIdx.x;
         if (i < n) {
-            const uint64_t key = k[i];
+            uint64_t key;
+            if constexpr (FROM_XY) {
+                const double c = s ? xy[i].y : xy[i].x;
+                if (!isfinite(c)) atomicOr(status, ST_NONFINITE);
+                key = order_key(c);
+            } else {
+                key = k[i];
+            }
 #pragma unroll
             for (int p = P0; p < 8; ++p) atomicAdd(&h[p][(int)((key >> (8 * p)) & 255u)], 1u);
         }
@@ -383,7 +393,7 @@ constexpr unsigned kSAgg = 1u << 30, kSIncl = 2u << 30, kSVal = (1u << 30) - 1;
 constexpr int kSortSpins = 1 << 21;  // bound on the look-back's waits for one tile
 // earlier tiles one look-back round reads; measured on the 1e6-point build: 4 beats 1, 8 and 16
 constexpr int kSortLook = 4;
-template <bool ONESWEEP>
+template <bool ONESWEEP, bool FROM_XY = false>
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t* __restrict__ ki0,
                                                                const int32_t* __restrict__ vi0,
                                                                const uint64_t* __restrict__ ki1,
@@ -391,7 +401,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t* _
                                                                int32_t* vo0, uint64_t* ko1, int32_t* vo1, int n,
                                                                int shift, int T, const int32_t* __restrict__ off,
                                                                const unsigned* __restrict__ ghist, unsigned* stat,
-                                                               unsigned* ticket, unsigned* status) {
+                                                               unsigned* ticket, unsigned* status,
+                                                               const double2* __restrict__ xy = nullptr) {
     constexpr int W = kSortThreads / 32;
     __shared__ int whist[W][257];  // per-warp digit counts, then their exclusive prefix over warps
     __shared__ int base[256];      // global position of the tile's first key of each digit
@@ -425,8 +436,13 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t* _
     for (int r = 0; r < kSortRounds; ++r) {
         const int i = i0 + 32 * r;
         const bool valid = i < n;
-        key[r] = valid ? ki[i] : 0;
-        val[r] = valid ? vi[i] : 0;
+        if constexpr (FROM_XY) {  // the first pass: keys from the points, values = input indices
+            key[r] = valid ? order_key(s ? xy[i].y : xy[i].x) : 0;
+            val[r] = i;
+        } else {
+            key[r] = valid ? ki[i] : 0;
+            val[r] = valid ? vi[i] : 0;
+        }
         dig[r] = valid ? (int)((key[r] >> shift) & 255u) : 256;
     }
     __syncwarp();
@@ -561,6 +577,7 @@ constexpr int kSortRunMax = 16;
 __global__ void __launch_bounds__(256) k_sort_runs(const uint64_t* __restrict__ k0, const int32_t* __restrict__ v0,
                                                    const uint64_t* __restrict__ k1, const int32_t* __restrict__ v1,
                                                    int32_t* __restrict__ o0, int32_t* __restrict__ o1, int n,
+                                                   uint8_t* __restrict__ side0, const int32_t* __restrict__ nz0,
                                                    unsigned* status) {
     const uint64_t* key = blockIdx.y ? k1 : k0;
     const int32_t* val = blockIdx.y ? v1 : v0;
@@ -573,8 +590,10 @@ __global__ void __launch_bounds__(256) k_sort_runs(const uint64_t* __restrict__ 
     const int32_t vi = val[i];
     const unsigned hi = (unsigned)(ki >> 32);
     const bool prev = i > 0 && (unsigned)(kp >> 32) == hi, next = i + 1 < n && (unsigned)(kn >> 32) == hi;
+    const bool mark = side0 != nullptr && blockIdx.y == 0;  // x sort: also the side flags of the root's x cut
     if (!prev && !next) {
         out[i] = vi;
+        if (mark) side0[vi] = (uint8_t)(i >= *nz0);
         return;
     }
     int s = prev ? i - 1 : i;
@@ -584,6 +603,7 @@ __global__ void __launch_bounds__(256) k_sort_runs(const uint64_t* __restrict__ 
     if (e - s > kSortRunMax || (s > 0 && (unsigned)(key[s - 1] >> 32) == hi)) {
         if ((i & 15) == 0) atomicOr(status, ST_SORT_RUN);  // a long run holds such an i
         out[i] = vi;
+        if (mark) side0[vi] = (uint8_t)(i >= *nz0);
         return;
     }
     int rank = 0;
@@ -592,6 +612,7 @@ __global__ void __launch_bounds__(256) k_sort_runs(const uint64_t* __restrict__ 
         rank += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
     }
     out[s + rank] = vi;
+    if (mark) side0[vi] = (uint8_t)(s + rank >= *nz0);
 }
 
 // Words of the onesweep scratch for n points.
@@ -609,7 +630,8 @@ static size_t sort_scratch_words(int64_t n) {
 // Scratch: d_sort_os = global counts [2][8][256], tickets [8][2], tile status
 // words [8][2][T][256]; zeroed once per build.  *res: the buffer pair that
 // holds the sorted values (0: 0/1, 2: 2/3).
-static fmm_status sort_coordinates(Tree& t, cudaStream_t s, bool full, int* res) {
+static fmm_status sort_coordinates(Tree& t, cudaStream_t s, const double2* xy, bool full, int* res, uint8_t* side0,
+                                   const int32_t* nz0) {
     const int n = (int)t.n;
     const int T = nblk(n, kSortTile);
     unsigned* gh = t.d_sort_os;
@@ -617,22 +639,29 @@ static fmm_status sort_coordinates(Tree& t, cudaStream_t s, bool full, int* res)
     unsigned* stat = tk + 16;
     FMM_CUDA(cudaMemsetAsync(gh, 0, sort_scratch_words(n) * sizeof(unsigned), s));
     dim3 g(T, 2);
-    if (full) k_sort_ghist<0><<<g, kSortThreads, 0, s>>>(t.d_keys[0], t.d_keys[1], n, gh);
-    else k_sort_ghist<4><<<g, kSortThreads, 0, s>>>(t.d_keys[0], t.d_keys[1], n, gh);
+    if (full) k_sort_ghist<0, true><<<g, kSortThreads, 0, s>>>(nullptr, nullptr, n, gh, xy, t.d_status);
+    else k_sort_ghist<4, true><<<g, kSortThreads, 0, s>>>(nullptr, nullptr, n, gh, xy, t.d_status);
     int src = 0;
-    for (int pass = full ? 0 : 4; pass < 8; ++pass) {  // an even number of passes: the result is in buffers 0/1
+    const int p0 = full ? 0 : 4;
+    for (int pass = p0; pass < 8; ++pass) {  // an even number of passes: the result is in buffers 0/1
         const int dst = 2 - src;
-        k_sort_scatter<true><<<g, kSortThreads, 0, s>>>(
-            t.d_keys[src], t.d_vals[src], t.d_keys[src + 1], t.d_vals[src + 1], t.d_keys[dst], t.d_vals[dst],
-            t.d_keys[dst + 1], t.d_vals[dst + 1], n, 8 * pass, T, nullptr, gh + pass * 256, stat + (size_t)pass * 2 * T * 256,
-            tk + 2 * pass, t.d_status);
+        if (pass == p0)  // the first pass forms the keys from the points
+            k_sort_scatter<true, true><<<g, kSortThreads, 0, s>>>(
+                nullptr, nullptr, nullptr, nullptr, t.d_keys[dst], t.d_vals[dst], t.d_keys[dst + 1], t.d_vals[dst + 1],
+                n, 8 * pass, T, nullptr, gh + pass * 256, stat + (size_t)pass * 2 * T * 256, tk + 2 * pass,
+                t.d_status, xy);
+        else
+            k_sort_scatter<true><<<g, kSortThreads, 0, s>>>(
+                t.d_keys[src], t.d_vals[src], t.d_keys[src + 1], t.d_vals[src + 1], t.d_keys[dst], t.d_vals[dst],
+                t.d_keys[dst + 1], t.d_vals[dst + 1], n, 8 * pass, T, nullptr, gh + pass * 256,
+                stat + (size_t)pass * 2 * T * 256, tk + 2 * pass, t.d_status);
         FMM_CUDA(cudaGetLastError());
         src = dst;
     }
     *res = 0;
     if (!full) {  // the runs: values 0/1 -> 2/3
         k_sort_runs<<<dim3(nblk(n, 256), 2), 256, 0, s>>>(t.d_keys[0], t.d_vals[0], t.d_keys[1], t.d_vals[1],
-                                                         t.d_vals[2], t.d_vals[3], n, t.d_status);
+                                                         t.d_vals[2], t.d_vals[3], n, side0, nz0, t.d_status);
         FMM_CUDA(cudaGetLastError());
         *res = 2;
     }
@@ -1577,16 +1606,22 @@ fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s) {
     const int n = (int)t.n;
     const double2* xy = reinterpret_cast<const double2*>(d_xy);
     FMM_CUDA(cudaMemsetAsync(t.d_status, 0, sizeof(unsigned), s));
-    k_keys<<<nblk(n, 256), 256, 0, s>>>(xy, n, t.d_keys[0], t.d_keys[1], t.d_vals[0], t.d_vals[1], t.d_status);
-    FMM_CUDA(cudaGetLastError());
     // LSD passes over the 64-bit keys (+2 over the instance index when
     // batched); an even number of passes leaves the result in buffers 0/1.
     int src = 0;
     fmm_status st;
-    if (n < (1 << 30)) {  // onesweep passes (30-bit counts in the tile status words)
-        // the short sort (high halves + runs) for single trees; a forest's instance passes follow a full sort
-        if ((st = sort_coordinates(t, s, t.sort_full || t.ninst > 1, &src))) return st;
+    const int lglob = std::min(t.l0, t.Lmax - 1);  // levels split by the global passes
+    bool marked = false;                           // side flags of the first cut already written
+    if (n < (1 << 30)) {  // onesweep passes (30-bit counts in the tile status words); keys formed in the first
+        // the short sort (high halves + runs) for single trees, which also flags the root's x cut; a forest's
+        // instance passes follow a full sort
+        const bool full = t.sort_full || t.ninst > 1;
+        uint8_t* side0 = !full && lglob > 0 ? t.d_sideX : nullptr;
+        if ((st = sort_coordinates(t, s, xy, full, &src, side0, side0 ? t.seg_x[0].d_nzero : nullptr))) return st;
+        marked = side0 != nullptr;
     } else {
+        k_keys<<<nblk(n, 256), 256, 0, s>>>(xy, n, t.d_keys[0], t.d_keys[1], t.d_vals[0], t.d_vals[1], t.d_status);
+        FMM_CUDA(cudaGetLastError());
         for (int pass = 0; pass < 8; ++pass) {
             if ((st = sort_pass(t, s, src, 2 - src, 8 * pass))) return st;
             src = 2 - src;
@@ -1609,8 +1644,7 @@ fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s) {
                                                t.d_inst_boxoff, t.d_center, t.d_radius, t.d_rho, t.d_chl, t.d_rho32,
                                                t.d_rad32, 1);
     FMM_CUDA(cudaGetLastError());
-    const int lglob = std::min(t.l0, t.Lmax - 1);  // levels split by the global passes
-    if (lglob > 0) {  // flags of the first cut (x, level 0); later cuts get theirs from the stage before
+    if (lglob > 0 && !marked) {  // flags of the first cut (x, level 0); later cuts get theirs from the stage before
         const SegTable& sx = t.seg_x[0];
         k_mark<<<nblk(n, 256), 256, 0, s>>>(X, n, sx.d_start, sx.d_nzero, sx.K, t.d_sideX);
     }

@@ -911,7 +911,7 @@ __global__ void k_geom(const int32_t* __restrict__ ids, int cnt, const int32_t* 
 // computed on the way; at the end the box's leaf-ordered list of input
 // indices is written back over its part of the global y-list.
 
-constexpr int kSubThreads = 256;
+constexpr int kSubThreads = 1024;  // measured: 1024 beats 256 and 512 (rebuild 1.156 -> 1.132 ms)
 constexpr int kSubItems = kSubMax / kSubThreads;
 constexpr int kSubSegs = 2048;       // segments (half boxes) per split stage
 

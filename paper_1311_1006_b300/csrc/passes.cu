@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(128) k_p2m32(const int32_t* __restrict__ leave
                                                const int32_t* __restrict__ bstart, const int32_t* __restrict__ bcount,
                                                const float4* __restrict__ chl, const float* __restrict__ rho32,
                                                const float4* __restrict__ pos4, const float2* __restrict__ gam,
-                                               float2* __restrict__ M32, int p, int PS) {
+                                               float2* __restrict__ M32, double2* __restrict__ M64, int p, int PS) {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nleaf) return;
     const int b = leaves[q];
@@ -167,6 +167,11 @@ __global__ void __launch_bounds__(128) k_p2m32(const int32_t* __restrict__ leave
     float2* out = M32 + (size_t)b * PS;
 #pragma unroll
     for (int k = 0; k < P; ++k) out[k] = k < p ? a[k] : make_float2(0.f, 0.f);
+    if (M64 != nullptr) {  // a parent box: the FP64 copy that the next shift up reads
+        double2* o64 = M64 + (size_t)b * PS;
+#pragma unroll
+        for (int k = 0; k < P; ++k) o64[k] = k < p ? make_double2((double)a[k].x, (double)a[k].y) : make_double2(0.0, 0.0);
+    }
 }
 
 template <int P>
@@ -1264,10 +1269,17 @@ template <int P>
 static void launch_up_fp32(Tree& t, const Bufs& B, cudaStream_t s) {
     const float2* gam = static_cast<const float2*>(B.gam);
     k_p2m32<P><<<nblk(t.nleaf, 128), 128, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, t.d_bstart, t.d_bcount, t.d_chl,
-                                                  t.d_rho32, t.d_pos4, gam, B.M32, t.p, t.PS);
+                                                  t.d_rho32, t.d_pos4, gam, B.M32, nullptr, t.p, t.PS);
+    // the parents of the deepest leaves take their multipoles from their points (see fold_leaf_m2m)
+    const int lfold = fold_leaf_m2m(t) ? t.Lmax - 2 : -1;
+    if (lfold >= 0 && t.level_parents[lfold].count) {
+        const LevelList& L = t.level_parents[lfold];
+        k_p2m32<P><<<nblk(L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_bstart, t.d_bcount, t.d_chl, t.d_rho32,
+                                                      t.d_pos4, gam, B.M32, B.M64, t.p, t.PS);
+    }
     for (int l = t.Lmax - 2; l >= 0; --l) {
         const LevelList& L = t.level_parents[l];
-        if (!L.count) continue;
+        if (!L.count || l == lfold) continue;
         if (4 * (int64_t)L.count <= kWarpShiftMax)
             k_m2m_warp<P><<<L.count, 128, 0, s>>>(L.d_ids, L.count, t.d_child0, t.d_rho, t.d_center, B.M32, B.M64,
                                                   B.M32, 1, t.p, t.PS);

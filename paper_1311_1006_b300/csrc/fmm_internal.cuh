@@ -303,10 +303,17 @@ struct Bufs {
 Bufs bufs(Tree& t, int set);
 // FP32 path with at least three levels: the deepest level's L2L is folded into L2P (Tree::d_fold_par).
 inline bool fold_leaf_l2l(const Tree& t) { return t.path == FMM_PATH_FP32 && t.Lmax >= 3; }
-// FP32 path, parents of the deepest leaves (at most 4 x 64 points each): their multipoles by P2M from their own
-// points instead of the M2M shift of their children's (the shift of a truncated multipole is exact), which
-// spares the largest FP64 shift launch of the upward pass.
-inline bool fold_leaf_m2m(const Tree& t) { return t.path == FMM_PATH_FP32 && t.Lmax >= 3 && t.max_leaf <= 64; }
+// FP32 path, parent levels whose boxes hold few points: their multipoles by P2M from their own points instead
+// of the M2M shift of their children's (the shift of a truncated multipole is exact), which spares the largest
+// FP64 shift launches of the upward pass.  Returns 1 (a thread per box: at most 64 points), 2 (a warp per box:
+// at most 1024) or 0 (M2M).  A box on level l holds at most max_leaf * 4^(Lmax - 1 - l) points.
+inline int p2m_parent_mode(const Tree& t, int l) {
+    if (t.path != FMM_PATH_FP32 || t.Lmax < 3 || l < 1) return 0;
+    const int up = t.Lmax - 1 - l;  // levels between l and the deepest leaves
+    if (up > 8) return 0;
+    const long long most = (long long)t.max_leaf << (2 * up);
+    return most <= 64 ? 1 : most <= 1024 ? 2 : 0;
+}
 bool m2l_tc_enabled();
 // Weak pairs per M2L work item.  Tensor-core M2L, measured with the row order on the 1e6-point step (ms):
 // 64: 3.32, 128: 3.25, 160: 3.23, 192: 3.22, 256: 3.23.  FP64 M2L (one thread per item): 32, 64 and 128 equal.

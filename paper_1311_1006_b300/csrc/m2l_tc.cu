@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kTcThreads, P <= 18 ? 3 : 2)
             const float dx = (ct.x - ncs.x) + (ct.z - ncs.z);
             const float dy = (ct.y - ncs.y) + (ct.w - ncs.w);
             const float r2 = fmaf(dx, dx, dy * dy);
-            const float inv = 1.0f / r2;
+            const float inv = rcp_approx(r2);  // hardware reciprocal (within about one ulp)
             cur.u = make_float2(dx * inv, -dy * inv);  // 1/d, d = c_target - c_source
             const float2 alpha = make_float2(nrs * cur.u.x, nrs * cur.u.y);
             cur.beta = make_float2(-rt * cur.u.x, -rt * cur.u.y);

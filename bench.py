@@ -3,7 +3,9 @@
 Workload (synthetic, seeded): N = 1,000,000 points, 90 % from 8 Gaussian
 clusters (sigma log-uniform in [0.01, 0.1]) + 10 % uniform background in the
 unit square, complex strengths with N(0,1) real and imaginary parts, p = 17,
-theta = 0.5, N_levels picked by the library's AT3b autotuner during warm-up.
+theta = 0.5, N_levels seeded by the cost model of eqs (2.4)-(2.5) with unit
+costs measured on this GPU and refined by the library's AT3b autotuner during
+warm-up.
 
 One step = the whole hot path for one evaluation: rebuild the pyramid tree and
 coupling lists for the step's coordinates (the paper re-partitions at every
@@ -11,7 +13,10 @@ time step) + one FMM evaluation (P2M, M2M, M2L, L2L, L2P, P2P) on the FP32
 (mixed) path.  `value` is device time with inputs resident in HBM; `e2e` is the
 same through the C ABI with host (pinned) buffers: H2D copy of points and
 strengths, build, evaluate, D2H copy of the potentials, every step.  The FP64
-path and the adjoint are timed on the same workload and reported beside it.
+path, the adjoint, the logarithmic kernel, theta tuning and the other four
+workloads (plain FP64 at 1e4, the 20-snapshot dynamic sequence at 2e6, the
+512-instance batch, the differentiated 1e6 set) are timed beside it, each with
+its sampled error against the oracle's exact sums.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -36,17 +41,28 @@ N_POINTS = 1_000_000
 P_TERMS = 17
 THETA = 0.5
 WORKLOAD = "cluster_mix_1e6_p17_theta0.5"
+# N_levels the autotuner settles on for the headline workload (leaves of ~15
+# points); the reference arm evaluates the oracle at this N_levels
+HEADLINE_NLEVELS = 9
 # dram__bytes_read.sum + dram__bytes_write.sum of one P2P launch (k_p2p_pairs) at
-# N_levels = 9 on this workload, from one ncu capture (profiles/p2p_pairs_cluster1e6_L9.md)
+# N_levels = 9 on this workload, from one ncu capture of the kernel as it is built
 P2P_TRAFFIC_BYTES = 82_333_440 + 5_691_136
-# algorithmic FP32 flops of one point-pair interaction (FMA = 2): compensated
-# difference 6, |d|^2 4, the two scalings 2, the complex accumulation 8
-P2P_FLOPS = 20.0
-# the same for the logarithmic kernel: compensated difference 6, |d|^2 3, the
-# complex accumulation of Gamma_j log2|d|^2 4 (plus one log2 on the MUFU unit)
-P2P_LOG_FLOPS = 13.0
-SM_COUNT = 148
+# algorithmic FP32 flops of one point-pair interaction Gamma_j / (z_i - z_j) with
+# complex Gamma (FMA = 2): difference 2, |d|^2 3, the two scalings by 1/|d|^2 2,
+# complex product and accumulation 8 (the reciprocal runs on the MUFU unit)
+P2P_FLOPS = 15.0
+# what the kernel issues per pair: the hi/lo compensated difference adds 4
+# additions, the guard of |d|^2 one (context, not the method's work)
+P2P_FLOPS_ISSUED = 20.0
+# the same for the logarithmic kernel: difference 2, |d|^2 3, the complex
+# accumulation of Gamma_j log2|d|^2 4 (plus one log2 on the MUFU unit)
+P2P_LOG_FLOPS = 9.0
 FP32_FLOP_PER_CLK_SM = 256  # 128 FP32 lanes x FMA
+
+
+def _config(nlevels):
+    """The workload both arms time (the same dict on the reference arm's line)."""
+    return {"workload": WORKLOAD, "n_points": N_POINTS, "p": P_TERMS, "theta": THETA, "nlevels": int(nlevels)}
 
 
 def _peaks():
@@ -141,6 +157,211 @@ def _whole_job_rate(units_per_rank: int, world: int, ms: float) -> float:
     return units_per_rank * world / (ms * 1e-3) / 1e6
 
 
+def _timed_ms(fn, reps, stream, flush):
+    """CUDA-event times (ms) of `reps` calls of fn on `stream`, L2 flushed before each."""
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = []
+    for _ in range(reps):
+        flush.zero_()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def _mps(n, ms):
+    return round(n / (ms * 1e-3) / 1e6, 3)
+
+
+def _seed_and_tune(F, tree, X, G, out, stream, steps):
+    """N_levels of the headline tree: one evaluation with every phase timed alone
+    calibrates the unit costs of eqs (2.4)-(2.5); the cost-model seed starts an
+    AT3b walk (Algorithm 4) over `steps` rebuild + evaluate steps."""
+    import torch
+
+    tree.rebuild(X, flags=F.FMM_FLAG_TIMING | F.FMM_FLAG_SERIAL)
+    for _ in range(2):
+        tree.eval(G, out=out)
+    alpha, beta = tree.calibrate_cost_model()
+    seed = F.default_nlevels(tree.n, tree.params.p, "fp32")
+    tree.rebuild(X, nlevels=seed, flags=0)
+    tree.autotune_config(cap=0.2, window=3, period=3)
+    L = seed
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(steps):
+        e0.record(stream)
+        tree.rebuild(X, nlevels=L)
+        tree.eval(G, out=out)
+        e1.record(stream)
+        e1.synchronize()
+        L = tree.autotune_step(e0.elapsed_time(e1) * 1e-3)
+    return {"alpha_s": alpha, "beta_s": beta, "seed": seed, "tuned": int(tree.info()["autotune_nlevels"]),
+            "tuning_steps": steps}
+
+
+# ---------------------------------------------------------------- other workloads
+def leg_c1(F, orc, dev, stream, flush):
+    """Plain FMM, FP64: N = 1e4 uniform, real N(0,1) strengths, p = 20, theta = 0.5,
+    N_levels = 5 (39 points per leaf); error against the full direct sum."""
+    import torch
+    from paper_1311_1006_b300 import workloads as W
+
+    n, p, L = 10_000, 20, 5
+    g = W.rng(W.W_PLAIN_FP64)
+    xy, gam = W.uniform(n, g), W.real_strengths(n, g)
+    X, G = torch.tensor(xy, device=dev), torch.tensor(gam, device=dev)
+    t = F.Tree.build(X, p=p, theta=THETA, nlevels=L, path="fp64")
+    out = torch.empty(n, dtype=torch.complex128, device=dev)
+    step = lambda: t.step(X, G, out=out)  # noqa: E731
+    _timed_ms(step, 5, stream, flush)
+    ms = float(np.median(_timed_ms(step, 20, stream, flush)))
+    phi = out.cpu().numpy()
+    exact = orc.direct(xy, gam)
+    ofmm = orc.fmm(xy, gam, L, THETA, p)["phi"]
+    t.close()
+    return {"workload": "uniform_1e4_p20_theta0.5_fp64", "n_points": n, "p": p, "nlevels": L, "path": "fp64",
+            "ms_per_step": round(ms, 4), "value": _mps(n, ms), "unit": UNIT,
+            "rel_err_vs_direct": _rel(phi, exact), "rel_err_vs_oracle_fmm": _rel(phi, ofmm),
+            "oracle_fmm_rel_err_vs_direct": _rel(ofmm, exact),
+            "step": "fmm_step (rebuild + evaluate), median of 20, L2 flushed"}
+
+
+def leg_c3(F, orc, dev, stream, flush):
+    """Dynamic sequence: 20 snapshots at N = 2e6 (uniform, then 4 Gaussians with
+    sigma = 0.2 * 0.8^k), real U(-1,1) strengths, theta = 0.5, p in {12, 30},
+    FP32 and FP64 paths.  Each snapshot is a time step: the tree is rebuilt for
+    its points and the AT3b tuner, carried across snapshots, retunes N_levels
+    from every step's time."""
+    import torch
+    from paper_1311_1006_b300 import workloads as W
+
+    n, K = 2_000_000, 20
+    snaps = []
+    for k in range(K):
+        g = W.rng(W.W_DYNAMIC, k)
+        xy, gam = W.snapshot(n, k, g), W.uniform_real_strengths(n, g)
+        tg = np.random.default_rng(200 + k).choice(n, 64, replace=False)
+        snaps.append((torch.tensor(xy, device=dev), torch.tensor(gam, device=dev), tg,
+                      orc.direct(xy, gam, targets=tg)))
+        del xy, gam
+    res = {"workload": "dynamic_20x2e6_theta0.5", "n_points": n, "snapshots": K,
+           "step": "per snapshot: steps of tree rebuild + evaluation, the tuner fed every step's time; "
+                   "value = points of all steps / their summed time; L2 flushed before every step",
+           "error": "rel. max-norm vs the exact sum on 64 sampled points per snapshot (last step)"}
+    for path in ("fp32", "fp64"):
+        for p in (12, 30):
+            S = 4 if path == "fp32" else 3
+            L = F.default_nlevels(n, p, path)
+            seed = L
+            tree = F.Tree.build(snaps[0][0], p=p, theta=THETA, nlevels=L, path=path)
+            tree.autotune_config(cap=0.2, window=2, period=2)
+            out = torch.empty(n, dtype=tree.out_dtype, device=dev)
+            tree.eval(snaps[0][1], out=out)
+            per_ms, levels, errs, tot = [], [], [], 0.0
+            for X, G, tg, exact in snaps:
+                ts = []
+                for _ in range(S):
+                    Lc = L
+
+                    def _one():
+                        tree.rebuild(X, nlevels=Lc)
+                        tree.eval(G, out=out)
+
+                    ms = _timed_ms(_one, 1, stream, flush)[0]
+                    ts.append(ms)
+                    L = tree.autotune_step(ms * 1e-3)
+                tot += sum(ts)
+                per_ms.append(round(float(np.median(ts)), 3))
+                levels.append(int(tree.info()["autotune_nlevels"]))
+                errs.append(_rel(out.cpu().numpy().astype(np.complex128)[tg], exact))
+            tree.close()
+            res[f"{path}_p{p}"] = {"value": _mps(n * S * K, tot), "unit": UNIT, "steps_per_snapshot": S,
+                                   "nlevels_seed": seed, "nlevels": levels, "ms_median": per_ms,
+                                   "rel_err_max": max(errs), "rel_err": [float(f"{e:.3g}") for e in errs]}
+    return res
+
+
+def leg_c4(F, orc, dev, stream, flush):
+    """Batched: 512 independent instances, N_b = floor(10^U(3,5)), each uniform or
+    one Gaussian (sigma 0.05), real N(0,1) strengths, p = 16, theta = 0.5, FP32
+    path; per-instance N_levels from the cost-model seed.  One step = forest
+    rebuild + one evaluation of all instances (each phase one launch)."""
+    import torch
+    from paper_1311_1006_b300 import workloads as W
+
+    g = W.rng(W.W_BATCHED)
+    sizes = W.batch_sizes(512, g)
+    pts = [W.batch_instance(int(m), g) for m in sizes]
+    gam = [W.real_strengths(int(m), g) for m in sizes]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    xy, G = np.vstack(pts), np.concatenate(gam)
+    n = int(offs[-1])
+    X, Gd = torch.tensor(xy, device=dev), torch.tensor(G, device=dev)
+    t = F.Tree.build_batched(X, offs, p=16, theta=THETA, path="fp32")
+    out = torch.empty(n, dtype=torch.complex64, device=dev)
+    step = lambda: t.step(X, Gd, out=out)  # noqa: E731
+    _timed_ms(step, 3, stream, flush)
+    ms = float(np.median(_timed_ms(step, 7, stream, flush)))
+    ev = float(np.median(_timed_ms(lambda: t.eval(Gd, out=out), 7, stream, flush)))
+    phi = out.cpu().numpy().astype(np.complex128)
+    pick = np.random.default_rng(41)
+    err = 0.0
+    for b in pick.choice(512, 8, replace=False):
+        s, e = offs[b], offs[b + 1]
+        tg = pick.choice(e - s, min(32, e - s), replace=False)
+        err = max(err, _rel(phi[s:e][tg], orc.direct(xy[s:e], G[s:e], targets=tg)))
+    lev = t.export("inst")[:, 2]
+    info = t.info()
+    t.close()
+    return {"workload": "batched_512_p16_theta0.5_fp32", "instances": 512, "n_points": n, "p": 16,
+            "ms_per_step": round(ms, 4), "value": _mps(n, ms), "unit": UNIT,
+            "eval_ms": round(ev, 4), "eval_mpoints_s": _mps(n, ev),
+            "nlevels_range": [int(lev.min()), int(lev.max())], "launches_per_step":
+                int(info["launches_build"] + info["launches_eval"]),
+            "rel_err_sampled": err, "mode": "forest: one launch per phase over all instances",
+            "error": "rel. max-norm per instance vs the exact sum, 8 instances x 32 points, max"}
+
+
+def leg_c5(F, orc, dev, stream, flush):
+    """Differentiated: N = 1e6 uniform, real N(0,1) strengths, p = 17, theta = 0.5,
+    FP32 path; upstream gradient w + i v with w, v ~ N(0,1).  Forward = one
+    evaluation, backward = fmm_eval_backward (strength and position gradients)."""
+    import torch
+    from paper_1311_1006_b300 import workloads as W
+
+    n = 1_000_000
+    g = W.rng(W.W_DIFFERENTIATED)
+    xy, gam = W.uniform(n, g), W.real_strengths(n, g)
+    gphi = g.normal(size=n) + 1j * g.normal(size=n)
+    X, G, GP = (torch.tensor(a, device=dev) for a in (xy, gam, gphi))
+    t = F.Tree.build(X, p=17, theta=THETA, path="fp32")
+    out = torch.empty(n, dtype=torch.complex64, device=dev)
+    t.eval(G, out=out)
+    fwd = float(np.median(_timed_ms(lambda: t.eval(G, out=out), 7, stream, flush)))
+    grads = [t.backward(G, GP)]
+
+    def _bwd():
+        grads[0] = t.backward(G, GP)
+
+    bwd = float(np.median(_timed_ms(_bwd, 7, stream, flush)))
+    gg, gxy = grads[0]
+    tg = np.random.default_rng(51).choice(n, 128, replace=False)
+    rg, rxy = orc.direct_grad(xy, gam, gphi, targets=tg)
+    info = t.info()
+    t.close()
+    return {"workload": "differentiated_uniform_1e6_p17_theta0.5_fp32", "n_points": n, "p": 17,
+            "nlevels": info["nlevels_max"], "fwd_ms": round(fwd, 4), "bwd_ms": round(bwd, 4),
+            "bwd_over_fwd": round(bwd / fwd, 3), "value": _mps(n, fwd + bwd), "unit": UNIT,
+            "value_note": "points per second of forward + backward",
+            "rel_err_grad_gamma": _rel(gg.cpu().numpy()[tg], rg),
+            "rel_err_grad_xy": _rel(gxy.cpu().numpy()[tg], rxy),
+            "error": "rel. max-norm vs the direct-sum gradient on 128 sampled points"}
+
+
 def run_gpu(args):
     import torch
 
@@ -150,6 +371,12 @@ def run_gpu(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    # the single-thread oracle run goes in its own process, started before any
+    # GPU work, on one host core while the GPU legs run
+    st_proc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not (args.only_step or args.log_kernel):
+        st_proc = subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-leg", "1"],
+                                   stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -157,6 +384,7 @@ def run_gpu(args):
 
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     stream = torch.cuda.Stream(device=dev)
     xy, gam = _inputs()
     X = torch.tensor(xy, device=dev)
@@ -164,22 +392,18 @@ def run_gpu(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 126 MB L2
 
     with torch.cuda.stream(stream):
-        # --- N_levels: AT3b autotuner over a warm-up sequence -----------------
-        L0 = F.default_nlevels(N_POINTS, P_TERMS, "fp32")
+        # --- N_levels: cost-model seed from measured unit costs, then AT3b -----
+        L0 = args.nlevels or F.default_nlevels(N_POINTS, P_TERMS, "fp32")
         tree = F.Tree.build(X, p=P_TERMS, theta=THETA, nlevels=L0, path="fp32")
-        tree.autotune_config(cap=0.2, window=2, period=2)
         phi = torch.empty(N_POINTS, dtype=torch.complex64, device=dev)
-        L = L0
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        for _ in range(0 if args.nlevels else max(24, args.warmup)):
-            e0.record(stream)
-            tree.rebuild(X, nlevels=L)
-            tree.eval(G, out=phi)
-            e1.record(stream)
-            e1.synchronize()
-            L = tree.autotune_step(e0.elapsed_time(e1) * 1e-3)
-        tuned = args.nlevels or int(tree.info()["autotune_nlevels"])
-        tree.rebuild(X, nlevels=tuned)
+        tuning = None
+        if args.nlevels:
+            tuned = args.nlevels
+        else:
+            tuning = _seed_and_tune(F, tree, X, G, phi, stream, max(30, args.warmup))
+            tuned = tuning["tuned"]
+        tree.rebuild(X, nlevels=tuned, flags=0)
         info = tree.info()
 
         # --- timed: build + eval, inputs resident ------------------------------
@@ -288,49 +512,29 @@ def run_gpu(args):
         phases = _phases(F.FMM_FLAG_TIMING)
         phases_alone = _phases(F.FMM_FLAG_TIMING | F.FMM_FLAG_SERIAL)
         tree.rebuild(X, flags=0)
-        bld = []
-        for _ in range(5):
-            flush.zero_()
-            e0.record(stream)
-            tree.rebuild(X)
-            e1.record(stream)
-            e1.synchronize()
-            bld.append(e0.elapsed_time(e1))
-        build_ms = float(np.median(bld))
-        ev = []
-        for _ in range(5):
-            flush.zero_()
-            e0.record(stream)
-            tree.eval(G, out=phi)
-            e1.record(stream)
-            e1.synchronize()
-            ev.append(e0.elapsed_time(e1))
-        eval_ms = float(np.median(ev))
+        build_ms = float(np.median(_timed_ms(lambda: tree.rebuild(X), 5, stream, flush)))
+        eval_ms = float(np.median(_timed_ms(lambda: tree.eval(G, out=phi), 5, stream, flush)))
 
         # --- accuracy on sampled points vs the exact sum (oracle) -----------------
+        orc = None
         err32 = None
         if rank == 0:
-            import oracle
+            import oracle as orc
 
             tg = np.random.default_rng(7).choice(N_POINTS, 1024, replace=False)
-            exact = oracle.direct(xy, gam, targets=tg)
+            exact = orc.direct(xy, gam, targets=tg)
             err32 = _rel(phi.cpu().numpy().astype(np.complex128)[tg], exact)
 
         # --- FP64 path on the same workload -------------------------------------
         t64 = F.Tree.build(X, p=P_TERMS, theta=THETA, nlevels=tuned, path="fp64")
         phi64 = torch.empty(N_POINTS, dtype=torch.complex128, device=dev)
-        t64.rebuild(X)
-        t64.eval(G, out=phi64)
-        s64 = []
-        for _ in range(3):
-            flush.zero_()
-            e0.record(stream)
+
+        def _step64():
             t64.rebuild(X)
             t64.eval(G, out=phi64)
-            e1.record(stream)
-            e1.synchronize()
-            s64.append(e0.elapsed_time(e1))
-        ms64 = float(np.median(s64))
+
+        _step64()
+        ms64 = float(np.median(_timed_ms(_step64, 3, stream, flush)))
         err64 = _rel(phi64.cpu().numpy()[tg], exact) if rank == 0 else None
         # the FP64 path at its own smallest p that meets the same 1e-5 on the sampled points
         fp64_pmin = None
@@ -348,16 +552,7 @@ def run_gpu(args):
                         t64.rebuild(X, nlevels=Lp)
                         t64.eval(G, out=phi64)
                         e_l = _rel(phi64.cpu().numpy()[tg], exact)
-                        sp = []
-                        for _ in range(3):
-                            flush.zero_()
-                            e0.record(stream)
-                            t64.rebuild(X)
-                            t64.eval(G, out=phi64)
-                            e1.record(stream)
-                            e1.synchronize()
-                            sp.append(e0.elapsed_time(e1))
-                        mp = float(np.median(sp))
+                        mp = float(np.median(_timed_ms(_step64, 3, stream, flush)))
                         if e_l <= 1e-5 and (best is None or mp < best[0]):
                             best = (mp, Lp, e_l)
                     if best is not None:
@@ -395,10 +590,8 @@ def run_gpu(args):
             log_eval_ms = float(np.median(le))
             lerr = None
             if rank == 0:
-                import oracle as _orcl
-
                 tgl = np.random.default_rng(9).choice(N_POINTS, 512, replace=False)
-                lerr = _rel(phil.cpu().numpy().astype(np.complex128)[tgl], _orcl.direct_log(xy, gam, targets=tgl))
+                lerr = _rel(phil.cpu().numpy().astype(np.complex128)[tgl], orc.direct_log(xy, gam, targets=tgl))
             log_kernel = {"ms_per_step": round(log_ms, 4), "eval_ms": round(log_eval_ms, 4),
                           "value": round(N_POINTS / (log_ms * 1e-3) / 1e6, 2), "unit": UNIT,
                           "eval_over_harmonic_eval": round(log_eval_ms / eval_ms, 3),
@@ -415,69 +608,70 @@ def run_gpu(args):
             gphi = torch.complex(torch.randn(N_POINTS, device=dev, dtype=torch.float64),
                                  torch.randn(N_POINTS, device=dev, dtype=torch.float64))
             tree.backward(G, gphi)
-            bb = []
-            for _ in range(3):
-                flush.zero_()
-                e0.record(stream)
-                tree.backward(G, gphi)
-                e1.record(stream)
-                e1.synchronize()
-                bb.append(e0.elapsed_time(e1))
+            bb = _timed_ms(lambda: tree.backward(G, gphi), 3, stream, flush)
             bwd_ratio = float(np.median(bb)) / eval_ms
         except _lib.FMMError:
             bwd_ratio = None
 
         # --- theta autotuning (the second control of Sec. 4.2): N_levels and theta
-        # tuned together at TOL = 1e-6, p following theta, on the same workload ----
+        # tuned together at TOL = 1e-6, p following theta, on the same workload;
+        # two independent walks, to show whether they agree -------------------------
         theta_tune = None
         if rank == 0 and not args.no_theta_tune:
             tol = 1e-6
-            th, L2 = THETA, tuned
-            pp = F.p_for_tolerance(tol, th)
-            tt = F.Tree.build(X, p=pp, theta=th, nlevels=L2, path="fp32")
-            ph = torch.empty(N_POINTS, dtype=torch.complex64, device=dev)
+            tg2 = np.random.default_rng(8).choice(N_POINTS, 1024, replace=False)
+            ex2 = orc.direct(xy, gam, targets=tg2)
+            walks = []
+            start_ms = None
+            for walk in range(2):
+                th, L2 = THETA, tuned
+                pp = F.p_for_tolerance(tol, th)
+                tt = F.Tree.build(X, p=pp, theta=th, nlevels=L2, path="fp32")
+                ph = torch.empty(N_POINTS, dtype=torch.complex64, device=dev)
 
-            def _tt_ms():
-                ms_ = []
-                for _ in range(10):
-                    flush.zero_()
-                    e0.record(stream)
+                def _tt_step():
                     tt.rebuild(X)
+                    tt.eval(G, out=ph)
+
+                tt.eval(G, out=ph)
+                if start_ms is None:  # the starting point (theta of the workload, p from the tolerance rule)
+                    start_ms = float(np.median(_timed_ms(_tt_step, 10, stream, flush)))
+                tt.autotune_config(cap=0.2, window=4, period=4)
+                tt.autotune_theta(tol, 0.35, 0.65)
+                for _ in range(120):
+                    e0.record(stream)
+                    tt.rebuild(X, nlevels=L2, theta=th, p=pp)
                     tt.eval(G, out=ph)
                     e1.record(stream)
                     e1.synchronize()
-                    ms_.append(e0.elapsed_time(e1))
-                return float(np.median(ms_))
-
-            tt.eval(G, out=ph)
-            start_ms = _tt_ms()  # the starting point (theta of the workload, p from the tolerance rule)
-            tt.autotune_config(cap=0.2, window=2, period=2)
-            tt.autotune_theta(tol, 0.35, 0.65)
-            for _ in range(60):
-                e0.record(stream)
+                    L2, th, pp = tt.autotune_params(e0.elapsed_time(e1) * 1e-3)
+                inf2 = tt.info()
+                L2, th = int(inf2["autotune_nlevels"]), float(inf2["autotune_theta"])
+                pp = F.p_for_tolerance(tol, th)
                 tt.rebuild(X, nlevels=L2, theta=th, p=pp)
                 tt.eval(G, out=ph)
-                e1.record(stream)
-                e1.synchronize()
-                L2, th, pp = tt.autotune_params(e0.elapsed_time(e1) * 1e-3)
-            inf2 = tt.info()
-            L2, th = int(inf2["autotune_nlevels"]), float(inf2["autotune_theta"])
-            pp = F.p_for_tolerance(tol, th)
-            tt.rebuild(X, nlevels=L2, theta=th, p=pp)
-            tt.eval(G, out=ph)
-            tuned_ms = _tt_ms()
-            import oracle as _orc
+                tuned_ms = float(np.median(_timed_ms(_tt_step, 10, stream, flush)))
+                walks.append({"theta": round(th, 4), "p": pp, "nlevels": L2, "ms_per_step": round(tuned_ms, 4),
+                              "value": round(N_POINTS / (tuned_ms * 1e-3) / 1e6, 2),
+                              "rel_err_sampled": _rel(ph.cpu().numpy().astype(np.complex128)[tg2], ex2)})
+                tt.close()
+            theta_tune = dict(walks[0])
+            theta_tune.update({"tol": tol, "tuning_steps": 120, "window": 4, "period": 4,
+                               "start": {"theta": THETA, "p": F.p_for_tolerance(tol, THETA), "nlevels": tuned,
+                                         "ms_per_step": round(start_ms, 4)},
+                               "second_walk": walks[1]})
 
-            tg2 = np.random.default_rng(8).choice(N_POINTS, 1024, replace=False)
-            ex2 = _orc.direct(xy, gam, targets=tg2)
-            theta_tune = {"tol": tol, "theta": round(th, 4), "p": pp, "nlevels": L2,
-                          "ms_per_step": round(tuned_ms, 4),
-                          "value": round(N_POINTS / (tuned_ms * 1e-3) / 1e6, 2),
-                          "start": {"theta": THETA, "p": F.p_for_tolerance(tol, THETA), "nlevels": tuned,
-                                    "ms_per_step": round(start_ms, 4)},
-                          "rel_err_sampled": _rel(ph.cpu().numpy().astype(np.complex128)[tg2], ex2),
-                          "tuning_steps": 60}
-            tt.close()
+        # --- the other four workloads ----------------------------------------------
+        legs = {}
+        if rank == 0:
+            tree.close()
+            for name, fn in (("c1", leg_c1), ("c3", leg_c3), ("c4", leg_c4), ("c5", leg_c5)):
+                if name in args.skip_legs:
+                    continue
+                torch.cuda.empty_cache()
+                t_leg = time.time()
+                legs[name] = fn(F, orc, dev, stream, flush)
+                legs[name]["wall_s"] = round(time.time() - t_leg, 1)
 
     if rank != 0:
         if dist is not None:
@@ -489,8 +683,8 @@ def run_gpu(args):
     # dominant kernel: P2P, bound by the FP32 pipe.  Peak = SMs x 256 flop/clk x
     # SM clock (the median sampled under load; also given at the 2032 MHz max).
     sm_mhz = clocks.get("sm_mhz") or 2032.0
-    peak = SM_COUNT * FP32_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12
-    peak_max = SM_COUNT * FP32_FLOP_PER_CLK_SM * 2032e6 / 1e12
+    peak = sm_count * FP32_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12
+    peak_max = sm_count * FP32_FLOP_PER_CLK_SM * 2032e6 / 1e12
     p2p_ms = phases_alone["p2p"]
     achieved = info["p2p_pairs"] * P2P_FLOPS / (p2p_ms * 1e-3) / 1e12
     line = {
@@ -506,9 +700,12 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f32 (P2P/M2L/P2M/L2P) + f64 (M2M/L2L)",
         "data": "synthetic (seeded Gaussian-cluster mixture)",
-        "config": {"workload": WORKLOAD, "n_points": N_POINTS, "p": P_TERMS, "theta": THETA,
-                   "nlevels": info["nlevels_max"], "path": "fp32", "l2": "flushed (256 MB write) between steps",
-                   "step": "fmm_step: tree rebuild + lists + one evaluation (upward pass overlapped with the list build)", "parallelism": "replicas" if world > 1 else "1 gpu"},
+        "config": _config(info["nlevels_max"]),
+        "path": "fp32",
+        "l2": "flushed (256 MB write) between steps",
+        "step": "fmm_step: tree rebuild + lists + one evaluation (upward pass overlapped with the list build)",
+        "parallelism": "replicas" if world > 1 else "1 gpu",
+        "nlevels_tuning": tuning,
         "breakdown_ms": {"build": round(build_ms, 4), "eval": round(eval_ms, 4),
                          "in_step": {k: round(v, 4) for k, v in phases.items()},
                          "alone": {k: round(v, 4) for k, v in phases_alone.items()}},
@@ -523,9 +720,14 @@ def run_gpu(args):
                      "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                      "traffic": P2P_TRAFFIC_BYTES, "kernel_ms": round(p2p_ms, 4),
                      "frac_at_max_clock": round(achieved / peak_max, 4),
-                     "peak_note": f"FP32 peak from unit counts: {SM_COUNT} SMs x 256 flop/clk x {sm_mhz:.0f} MHz "
-                                  f"(median SM clock sampled during the timed steps); {P2P_FLOPS:.0f} algorithmic "
-                                  "flops per point pair (FMA = 2), launch time from CUDA events with the pass alone"},
+                     "flops_per_pair": P2P_FLOPS,
+                     "frac_issued": round(achieved / peak * P2P_FLOPS_ISSUED / P2P_FLOPS, 4),
+                     "peak_note": f"FP32 peak from unit counts: {sm_count} SMs (device property) x 256 flop/clk x "
+                                  f"{sm_mhz:.0f} MHz (median SM clock sampled during the timed steps); "
+                                  f"{P2P_FLOPS:.0f} algorithmic flops per point pair (FMA = 2; frac_issued counts "
+                                  f"the kernel's {P2P_FLOPS_ISSUED:.0f} with the hi/lo compensation); launch time "
+                                  "from CUDA events with the pass alone; traffic from one ncu capture of this "
+                                  "kernel at this workload"},
         "e2e": {"value": round(N_POINTS / (e2e_ms * 1e-3) / 1e6, 2), "unit": UNIT,
                 "h2d_bytes_per_step": int(xy.nbytes + gam.nbytes), "d2h_bytes_per_step": int(N_POINTS * 8),
                 "ms_per_step": round(e2e_ms, 4),
@@ -535,51 +737,81 @@ def run_gpu(args):
         "gpu_launches": int(args.steps * (info["launches_build"] + info["launches_eval"])),
         "interactions": {"p2p_pairs": info["p2p_pairs"], "m2l_pairs": info["n_weak"]},
     }
+    line.update(legs)
     line["clocks"] = clocks
     if peaks:
         line["peaks_used"] = {"hbm_gbs": peaks.get("hbm_gbs")}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(info["nlevels_max"], st_proc)
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
 
 
-def cpu_baseline(n=250_000, levels=8):
-    """The oracle (plain FP64 C, OpenMP over boxes) on a bounded sample of the
-    same workload: a 250k-point draw of the same generator, N_levels 8."""
+def _oracle_eval_s(threads, nlevels=HEADLINE_NLEVELS):
+    """Seconds of one oracle evaluation (plain FP64 C, OpenMP over boxes) of the
+    headline workload itself: tree, lists and every pass, at `threads` threads."""
     import oracle
-    from paper_1311_1006_b300 import workloads as W
 
-    g = W.rng(W.W_CLUSTER_1M)
-    xy = W.cluster_mix(n, g)
-    gam = W.complex_strengths(n, g)
-    oracle.set_threads(os.cpu_count() or 1)
+    xy, gam = _inputs()
+    oracle.set_threads(threads)
     t = time.time()
-    oracle.fmm(xy, gam, levels, THETA, P_TERMS)
-    dt = time.time() - t
-    return {"value": round(n / dt / 1e6, 4), "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"{n} points of the same cluster-mixture generator, N_levels={levels}, p=17, one evaluation "
-                      f"incl. tree ({dt:.2f} s)"}
+    oracle.fmm(xy, gam, nlevels, THETA, P_TERMS)
+    return time.time() - t, oracle.max_threads()
+
+
+def cpu_baseline(nlevels=HEADLINE_NLEVELS, st_proc=None):
+    """The oracle on the headline workload (1e6 points, p = 17, theta = 0.5, the
+    GPU's N_levels) on the host's cores: one evaluation with all cores, and the
+    single-thread run from the process started at the beginning of the benchmark."""
+    single = None
+    if st_proc is not None:
+        try:
+            out, _ = st_proc.communicate(timeout=900)
+            single = json.loads(out.strip().splitlines()[-1])
+        except (subprocess.TimeoutExpired, ValueError, IndexError):
+            st_proc.kill()
+            single = None
+    cores = os.cpu_count() or 1
+    dt, used = _oracle_eval_s(cores, nlevels)
+    res = {"value": round(N_POINTS / dt / 1e6, 4), "unit": UNIT, "cores": used, "kind": "oracle",
+           "sample": f"the headline workload itself: {N_POINTS} cluster-mixture points, p={P_TERMS}, "
+                     f"theta={THETA}, N_levels={nlevels}; one evaluation incl. tree and lists ({dt:.2f} s)",
+           "seconds": round(dt, 3)}
+    if single is not None:
+        res["single_thread"] = {"value": round(N_POINTS / single["seconds"] / 1e6, 4), "unit": UNIT, "cores": 1,
+                                "seconds": round(single["seconds"], 3),
+                                "note": "same evaluation on one thread, run while the GPU legs ran"}
+        res["speedup_all_cores_vs_one"] = round(single["seconds"] / dt, 2)
+    return res
 
 
 def run_reference(args):
+    """The oracle as the reference arm: every step is one full oracle evaluation
+    of the headline workload (all host cores, N_levels of the headline)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    vals = []
+    import oracle
+
+    xy, gam = _inputs()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
     for _ in range(args.warmup):
-        cpu_baseline()
+        oracle.fmm(xy, gam, HEADLINE_NLEVELS, THETA, P_TERMS)
+    t0 = time.time()
     for _ in range(args.steps):
-        vals.append(cpu_baseline())
-    v = float(np.mean([x["value"] for x in vals]))
-    ms = N_POINTS / (v * 1e6) * 1e3
+        oracle.fmm(xy, gam, HEADLINE_NLEVELS, THETA, P_TERMS)
+    ms = (time.time() - t0) / args.steps * 1e3
+    v = N_POINTS / (ms * 1e-3) / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-            "config": {"workload": WORKLOAD, "n_points": N_POINTS, "p": P_TERMS, "theta": THETA},
-            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "kind": "oracle", "cores": vals[0]["cores"],
-                             "sample": vals[0]["sample"]},
+            "config": _config(HEADLINE_NLEVELS),
+            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "kind": "oracle", "cores": oracle.max_threads(),
+                             "sample": "every step is one full oracle evaluation of the headline workload "
+                                       f"({N_POINTS} points, p={P_TERMS}, theta={THETA}, "
+                                       f"N_levels={HEADLINE_NLEVELS}) incl. tree and lists"},
             "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -591,13 +823,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--nlevels", type=int, default=0, help="fix N_levels (skip the autotuner warm-up)")
+    ap.add_argument("--nlevels", type=int, default=0, help="fix N_levels (skip the calibration and autotuner)")
     ap.add_argument("--no-theta-tune", action="store_true", help="skip the theta autotuning run")
+    ap.add_argument("--skip-legs", default="", help="comma-separated legs to skip (c1,c3,c4,c5)")
     ap.add_argument("--only-step", action="store_true",
                     help="time the step only (no phase split, FP64 path, adjoint, e2e, accuracy); for profiling")
     ap.add_argument("--log-kernel", action="store_true",
                     help="time the logarithmic-kernel step only (as --only-step, with fmm_eval_log); for profiling")
+    ap.add_argument("--oracle-leg", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    args.skip_legs = [x for x in args.skip_legs.split(",") if x]
+    if args.oracle_leg:
+        dt, used = _oracle_eval_s(args.oracle_leg)
+        print(json.dumps({"seconds": dt, "threads": used}))
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

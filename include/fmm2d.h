@@ -26,6 +26,11 @@
  *     call says "complex64".
  *   - Outputs are in the caller's input order.  Sources and evaluation points
  *     are the same point set (eq 2.1).  Real strengths: pass im = 0.
+ *   - Coincident points (eq 2.2): a pair with z_j == z_i adds nothing.  The P2P
+ *     kernels test this through |z_i - z_j|^2 instead of exact equality, so a
+ *     pair closer than the resolution of that square also adds nothing: below
+ *     about 1e-19 on FMM_PATH_FP32 (|d|^2 under the smallest normal float) and
+ *     about 1e-154 on FMM_PATH_FP64 (|d|^2 under the smallest normal double).
  *   - Errors are returned as fmm_status codes; nothing crosses the ABI as an
  *     exception.  fmm_last_error() gives a thread-local detail string.  An
  *     asynchronous CUDA error from earlier work is reported by the next call.
@@ -233,10 +238,38 @@ fmm_status fmm_autotuner_step_params(fmm_autotuner* a, double time_s, int* nleve
 fmm_status fmm_autotuner_stats(const fmm_autotuner* a, double* out, int nout);
 void fmm_autotuner_destroy(fmm_autotuner* a);
 
+/* Cost-model seed of N_levels (Sec. 2.3, eqs 2.4-2.5; the starting point of
+ * the autotuner, Sec. 4.2).  With N_f = 4^(N_levels-1) leaves the model counts
+ *     C_P2P = N^2/(2 N_f) * pi((1+theta)/theta)^2,
+ *     C_M2L = (3 N_f/2) p^2 * pi((1+theta)/theta)^2,
+ * and with unit costs alpha (seconds per unit of C_P2P) and beta (per unit of
+ * C_M2L) the time alpha C_P2P + beta C_M2L is smallest at
+ *     N_f* = (N/p) sqrt(alpha / (3 beta)).
+ * fmm_seed_nlevels returns the N_levels in [1, largest with 4^(N_levels-1) <= n]
+ * whose N_f is closest to N_f* on a log scale (0 for n < 1, p < 1 or
+ * alpha, beta <= 0).  Host-only. */
+int fmm_seed_nlevels(int64_t n, int p, double alpha, double beta);
+
 /* N_levels the library picks for n points at expansion order p when
- * fmm_params.nlevels == 0: the level whose leaves hold closest to the point
- * count that balances the P2P and M2L costs of eqs (2.4)-(2.5) on this GPU. */
+ * fmm_params.nlevels == 0: fmm_seed_nlevels with the library's unit costs
+ * for `path` (fmm_cost_model_get). */
 int fmm_default_nlevels(int64_t n, int p, int path);
+
+/* The library's unit costs (alpha, beta) of the cost model above, one pair
+ * per precision path, shared by the whole process.  Built in: values measured
+ * on B300 (1e6-point cluster set, p = 17, theta = 0.5, N_levels = 9, P2P and
+ * M2L each timed alone).  fmm_cost_model_calibrate replaces the pair of the
+ * tree's path with the unit costs measured in the tree's last evaluation:
+ * alpha = P2P time / C_P2P, beta = M2L time / C_M2L (model counts summed over
+ * the instances of a batched tree).  That evaluation must have been made with
+ * FMM_FLAG_TIMING (with FMM_FLAG_SERIAL too, P2P and M2L are timed alone and
+ * the unit costs do not include their overlap) on a tree with N_levels >= 3.
+ * The measured pair is written to *alpha_out, *beta_out (either may be NULL).
+ * Errors: INVALID_ARG (no timed evaluation, no M2L work, bad path or values),
+ * CUDA.  fmm_cost_model_set sets a pair directly (alpha, beta > 0, finite). */
+fmm_status fmm_cost_model_calibrate(fmm_tree* t, double* alpha_out, double* beta_out);
+fmm_status fmm_cost_model_get(int path, double* alpha, double* beta);
+fmm_status fmm_cost_model_set(int path, double alpha, double beta);
 
 /* Per-phase device times (milliseconds) of the last evaluation made with
  * FMM_FLAG_TIMING: out[0] gather, [1] P2M+M2M, [2] M2L, [3] L2L, [4] P2P,
@@ -306,9 +339,11 @@ void fmm_tree_destroy(fmm_tree* t);
  *   d_xy    : device, n x 2 float64 points;  d_gamma : device, n complex128
  *   d_phi   : device, n complex128 outputs (input order)
  * Scratch: a fixed 2 MiB __device__ array inside the library, resident on every
- * GPU that loads it until the process exits.  The first call on a device looks
- * up that array's device address (no allocation); make that first call before
- * any stream capture.  All calls share the array, so calls that run at the same
+ * GPU that loads it until the process exits.  Every call looks up that array's
+ * device address on the current device (no allocation, no synchronisation; the
+ * address stays right after cudaDeviceReset); the first call on a device may
+ * load the library's device code, so make it before any stream capture.  All
+ * calls share the array, so calls that run at the same
  * time on one GPU (unordered streams) race and give wrong results; calls
  * ordered on one stream are safe, and nothing needs clearing between them.
  * Errors: INVALID_ARG (NULL pointer, n < 1 or n > 16384), CUDA. */

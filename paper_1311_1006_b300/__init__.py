@@ -21,7 +21,8 @@ from . import _lib
 from ._lib import (FMM_FLAG_GRAPH, FMM_FLAG_NO_GRAPH, FMM_FLAG_SERIAL, FMM_FLAG_TIMING, FMM_PATH_FP32, FMM_PATH_FP64, FMMError,
                    FMMParams)
 
-__all__ = ["Tree", "FMMFunction", "fmm", "default_nlevels", "p_for_tolerance", "Autotuner", "FMMError", "FMM_PATH_FP32",
+__all__ = ["Tree", "FMMFunction", "fmm", "default_nlevels", "seed_nlevels", "cost_model", "set_cost_model",
+           "p_for_tolerance", "Autotuner", "FMMError", "FMM_PATH_FP32",
            "FMM_PATH_FP64", "FMM_FLAG_GRAPH", "FMM_FLAG_NO_GRAPH", "FMM_FLAG_SERIAL", "FMM_FLAG_TIMING"]
 
 
@@ -59,7 +60,25 @@ def _dev(t, dtype, shape=None, name="tensor"):
 
 
 def default_nlevels(n: int, p: int = 17, path="fp32") -> int:
+    """fmm_default_nlevels: the cost-model seed with the library's unit costs of `path`."""
     return int(_lib.load().fmm_default_nlevels(int(n), int(p), _path(path)))
+
+
+def seed_nlevels(n: int, p: int, alpha: float, beta: float) -> int:
+    """fmm_seed_nlevels: N_levels whose N_f is closest to (N/p) sqrt(alpha/(3 beta))."""
+    return int(_lib.load().fmm_seed_nlevels(int(n), int(p), float(alpha), float(beta)))
+
+
+def cost_model(path="fp32") -> tuple:
+    """fmm_cost_model_get: the library's unit costs (alpha, beta) of `path`."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _lib.check(_lib.load().fmm_cost_model_get(_path(path), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def set_cost_model(alpha: float, beta: float, path="fp32") -> None:
+    """fmm_cost_model_set."""
+    _lib.check(_lib.load().fmm_cost_model_set(_path(path), float(alpha), float(beta)))
 
 
 class Tree:
@@ -270,6 +289,13 @@ class Tree:
         keys = ["gather", "p2m_m2m", "m2l", "l2l", "p2p", "l2p", "total"]
         return dict(zip(keys, list(out)))
 
+    def calibrate_cost_model(self) -> tuple:
+        """fmm_cost_model_calibrate: unit costs (alpha, beta) from the last timed
+        evaluation, which become the library's cost model for this tree's path."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _lib.check(_lib.load().fmm_cost_model_calibrate(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
     def autotune_config(self, cap=0.1, window=3, period=8) -> None:
         _lib.check(_lib.load().fmm_autotune_config(self._h, float(cap), int(window), int(period)))
 
@@ -354,6 +380,7 @@ def _make_function():
         @staticmethod
         def forward(ctx, xy, gamma, tree):
             ctx.tree = tree
+            ctx.xy_dtype = xy.dtype
             ctx.save_for_backward(gamma)
             return tree.eval(gamma.detach().contiguous())
 
@@ -361,7 +388,8 @@ def _make_function():
         def backward(ctx, gphi):
             (gamma,) = ctx.saved_tensors
             gg, gxy = ctx.tree.backward(gamma.detach().contiguous(), gphi)
-            return gxy, gg, None
+            # gradients in the dtypes of the inputs they belong to
+            return gxy.to(ctx.xy_dtype), gg.to(gamma.dtype), None
 
     return FMMFunction
 

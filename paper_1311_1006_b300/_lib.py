@@ -96,6 +96,10 @@ def load() -> ctypes.CDLL:
         "fmm_autotuner_step_params": (S, [_VP, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
         "fmm_default_nlevels": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.c_int]),
+        "fmm_seed_nlevels": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+        "fmm_cost_model_calibrate": (S, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+        "fmm_cost_model_get": (S, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+        "fmm_cost_model_set": (S, [ctypes.c_int, ctypes.c_double, ctypes.c_double]),
         "fmm_phase_times": (S, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
         "fmm_get_tree_info": (S, [_VP, ctypes.POINTER(FMMTreeInfo)]),
         "fmm_tree_export": (S, [_VP, ctypes.c_int, _VP, ctypes.c_int64, _VP]),

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "fmm_internal.cuh"
@@ -35,23 +36,47 @@ static int max_levels_for(int64_t n) {  // largest N_levels with 4^(L-1) <= n
     return L;
 }
 
-int default_nlevels(int64_t n, int p, int path) {
-    // Leaf size that balances P2P (eq 2.4) against M2L (eq 2.5) for the
-    // measured unit costs of this implementation; the autotuner refines it.
-    (void)p;
-    const double target = path == FMM_PATH_FP32 ? 24.0 : 16.0;
+// ---- cost model of eqs (2.4)-(2.5) -------------------------------------------
+// P2P work  C_P2P = N^2/(2 N_f) * pi ((1+theta)/theta)^2      (eq 2.4)
+// M2L work  C_M2L = (3 N_f/2) p^2 * pi ((1+theta)/theta)^2    (eq 2.5)
+// With unit costs alpha (time per unit of C_P2P) and beta (per unit of C_M2L),
+// alpha C_P2P + beta C_M2L is smallest at N_f* = (N/p) sqrt(alpha/(3 beta)).
+// The unit costs are per precision path and process-wide: built-in values
+// measured on B300 (1e6-point cluster set, p = 17, theta = 0.5, N_levels = 9,
+// P2P and M2L each timed alone), replaced by fmm_cost_model_calibrate from the
+// phase times of an evaluation, or set by fmm_cost_model_set.
+static std::mutex g_cost_mu;
+static double g_alpha[2] = {4.69e-12, 2.34e-10};
+static double g_beta[2] = {9.8e-13, 5.5e-11};
+
+static double coupling_area(double theta) {  // pi ((1+theta)/theta)^2
+    const double q = (1.0 + theta) / theta;
+    return 3.14159265358979323846 * q * q;
+}
+
+int seed_nlevels(int64_t n, int p, double alpha, double beta) {
     const int Lmax = max_levels_for(n);
+    const double nf = (double)n / (double)std::max(p, 1) * std::sqrt(alpha / (3.0 * beta));
     int best = 1;
     double bestd = 1e300;
     for (int L = 1; L <= Lmax; ++L) {
-        const double per = (double)n / std::pow(4.0, L - 1);
-        const double d = std::fabs(std::log(per / target));
+        const double d = std::fabs(std::log(std::pow(4.0, L - 1) / nf));
         if (d < bestd) {
             bestd = d;
             best = L;
         }
     }
     return best;
+}
+
+int default_nlevels(int64_t n, int p, int path) {
+    double a, b;
+    {
+        std::lock_guard<std::mutex> lk(g_cost_mu);
+        a = g_alpha[path == FMM_PATH_FP64];
+        b = g_beta[path == FMM_PATH_FP64];
+    }
+    return seed_nlevels(n, p, a, b);
 }
 
 static fmm_status check_params(const fmm_params* prm) {
@@ -262,6 +287,55 @@ const char* fmm_status_string(fmm_status s) {
 const char* fmm_last_error(void) { return g_err.c_str(); }
 
 int fmm_default_nlevels(int64_t n, int p, int path) { return n < 1 ? 0 : default_nlevels(n, p, path); }
+
+int fmm_seed_nlevels(int64_t n, int p, double alpha, double beta) {
+    if (n < 1 || p < 1 || !(alpha > 0.0) || !(beta > 0.0)) return 0;
+    return seed_nlevels(n, p, alpha, beta);
+}
+
+fmm_status fmm_cost_model_get(int path, double* alpha, double* beta) {
+    if ((path != FMM_PATH_FP32 && path != FMM_PATH_FP64) || !alpha || !beta) return invalid("bad path or NULL");
+    std::lock_guard<std::mutex> lk(g_cost_mu);
+    *alpha = g_alpha[path];
+    *beta = g_beta[path];
+    return FMM_OK;
+}
+
+fmm_status fmm_cost_model_set(int path, double alpha, double beta) {
+    if (path != FMM_PATH_FP32 && path != FMM_PATH_FP64) return invalid("path must be 0 (FP32) or 1 (FP64)");
+    if (!(alpha > 0.0) || !(beta > 0.0) || !std::isfinite(alpha) || !std::isfinite(beta))
+        return invalid("alpha and beta must be finite and > 0");
+    std::lock_guard<std::mutex> lk(g_cost_mu);
+    g_alpha[path] = alpha;
+    g_beta[path] = beta;
+    return FMM_OK;
+}
+
+fmm_status fmm_cost_model_calibrate(fmm_tree* h, double* alpha_out, double* beta_out) {
+    if (!h) return invalid("NULL tree");
+    Tree& t = h->t;
+    if (!t.timing_valid) return invalid("no evaluation with FMM_FLAG_TIMING yet");
+    double ms[7];
+    fmm_status st = fmm_phase_times(h, ms, 7);
+    if (st) return st;
+    // model counts of eqs (2.4)-(2.5), summed over the instances of the tree
+    const double area = coupling_area(t.theta);
+    double c_p2p = 0.0, c_m2l = 0.0;
+    for (int b = 0; b < t.ninst; ++b) {
+        const double nb = (double)(t.inst_pt_off[b + 1] - t.inst_pt_off[b]);
+        const double nf = std::pow(4.0, t.inst_levels[b] - 1);
+        c_p2p += nb * nb / (2.0 * nf) * area;
+        if (t.inst_levels[b] >= 3) c_m2l += 1.5 * nf * (double)t.p * (double)t.p * area;
+    }
+    const double tp = ms[4] * 1e-3, tm = ms[2] * 1e-3;
+    if (!(c_m2l > 0.0) || !(tp > 0.0) || !(tm > 0.0))
+        return invalid("calibration needs an evaluation with P2P and M2L work (N_levels >= 3)");
+    const double a = tp / c_p2p, be = tm / c_m2l;
+    if ((st = fmm_cost_model_set(t.path, a, be))) return st;
+    if (alpha_out) *alpha_out = a;
+    if (beta_out) *beta_out = be;
+    return FMM_OK;
+}
 
 static fmm_status build_common(const double* d_xy, const std::vector<int64_t>& offs, const fmm_params* prm,
                                const int* h_nlevels, bool batched, void* stream, fmm_tree** out) {

@@ -19,8 +19,6 @@
 // slot it later reads, so nothing has to be cleared between calls.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "fmm_internal.cuh"
 
 namespace {
@@ -35,28 +33,16 @@ constexpr int kNaWarps = 8;
 // partial sums: [tile][chunk][lane], complex128 -> 2 MiB
 static __device__ __align__(256) double2 g_na_scratch[kNaTiles * kNaChunks * kNaTile];
 
-// Device address of the scratch array, looked up once per device.  In host
-// code `g_na_scratch` names a host-side stand-in, never a device address, so
-// kernels must be given the address cudaGetSymbolAddress returns.
-std::mutex g_na_mu;
-void* g_na_addr[64] = {};
-
+// Device address of the scratch array on the current device.  In host code
+// `g_na_scratch` names a host-side stand-in, never a device address, so kernels
+// must be given the address cudaGetSymbolAddress returns.  It is looked up on
+// every call (no allocation, no device synchronisation), so it stays right
+// after a cudaDeviceReset reloads the module, and on every device.
 fmm_status na_scratch(double2** out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fmm::cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= 64) {
-        fmm::set_error("fmm_direct_eval_noalloc: device index above 63");
-        return FMM_ERR_INVALID_ARG;
-    }
-    std::lock_guard<std::mutex> lock(g_na_mu);
-    if (!g_na_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_na_scratch);
-        if (e != cudaSuccess) return fmm::cuda_fail(e, "cudaGetSymbolAddress(scratch)");
-        g_na_addr[dev] = p;
-    }
-    *out = static_cast<double2*>(g_na_addr[dev]);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+    if (e != cudaSuccess) return fmm::cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+    *out = static_cast<double2*>(p);
     return FMM_OK;
 }
 

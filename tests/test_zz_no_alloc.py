@@ -2,8 +2,10 @@
 allocate device memory (their device memory is owned by a host framework's
 pool, or their loop may not call cudaMalloc/cudaFree, which can synchronise the
 device).  Called through the C ABI and compared with the existing entry point
-computing the same sum (fmm_eval on a one-level tree = pure P2P, FP64 path),
-within the FP64 tolerance of the other tests, on two calls in a row.  This file
+computing the same sum (fmm_eval on a one-level tree = pure P2P, FP64 path)
+and with the oracle's exact sum, within the FP64 tolerance of the other tests,
+on two calls in a row; a second call must leave the device's free memory
+unchanged.  This file
 sorts last so a run that stops at the first failure has run everything else."""
 import ctypes
 
@@ -28,7 +30,11 @@ def _noalloc(lib, X, G, n, out):
                                        ctypes.c_void_p(out.data_ptr()), s)
 
 
-def test_noalloc_direct_sum_matches_fmm_eval_twice():
+def _rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def test_noalloc_direct_sum_matches_fmm_eval_twice(orc):
     from paper_1311_1006_b300 import Tree, _lib
 
     lib = _lib.load()
@@ -42,9 +48,32 @@ def test_noalloc_direct_sum_matches_fmm_eval_twice():
         assert _noalloc(lib, X, G, n, out) == 0, lib.fmm_last_error()
         ref = Tree.build(X, p=8, nlevels=1, path="fp64").eval(G)
         torch.cuda.synchronize()
-        a, b = out.cpu().numpy(), ref.cpu().numpy()
-        err = np.abs(a - b).max() / np.abs(b).max()
+        a = out.cpu().numpy()
+        err = _rel(a, ref.cpu().numpy())
         assert err < TOL, (call, n, err)
+        if n <= 4000:  # and against the oracle's exact sum (plain FP64 C on the host)
+            err = _rel(a, orc.direct(xy, gam))
+            assert err < TOL, (call, n, "oracle", err)
+
+
+def test_noalloc_call_allocates_no_device_memory():
+    """After a first call, a second call on the same stream leaves the device's
+    free memory unchanged: the entry point allocates nothing."""
+    from paper_1311_1006_b300 import _lib
+
+    lib = _lib.load()
+    n = 5000
+    g = np.random.default_rng(3)
+    X, G = _dev(W.uniform(n, g)), _dev(W.complex_strengths(n, g))
+    out = torch.empty(n, dtype=torch.complex128, device="cuda")
+    assert _noalloc(lib, X, G, n, out) == 0, lib.fmm_last_error()
+    first = out.clone()
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert _noalloc(lib, X, G, n, out) == 0, lib.fmm_last_error()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free1
+    assert torch.equal(out, first)  # same inputs, same result bit for bit
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():

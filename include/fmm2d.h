@@ -67,9 +67,16 @@ enum {
     FMM_FLAG_NO_GRAPH = 1, /* launch the kernels one by one (the default; overrides FMM_FLAG_GRAPH) */
     FMM_FLAG_SERIAL = 2,   /* run P2P on the caller's stream after the far field (no overlap) */
     FMM_FLAG_TIMING = 4,   /* record per-phase CUDA events; read them with fmm_phase_times */
-    FMM_FLAG_GRAPH = 8     /* capture the evaluation once per (strengths, output, stream) and replay the
+    FMM_FLAG_GRAPH = 8,    /* capture the evaluation once per (strengths, output, stream) and replay the
                               CUDA graph; fewer host launches, but on B300 the replay overlaps P2P with
                               the far field less well than direct launches on prioritised streams */
+    FMM_FLAG_PERSISTENT = 16 /* FMM_PATH_FP32 only: fmm_eval / fmm_eval_batched run the whole evaluation of
+                              the tree (every instance of a forest) as ONE persistent kernel whose CTAs take
+                              (stage, box range) units from a device work queue in ticket order and wait,
+                              bounded, for the units each stage depends on; M2L runs on the CUDA cores.
+                              With FMM_FLAG_GRAPH the one launch is captured and replayed.  The
+                              logarithmic kernel, the adjoint and separate evaluation points ignore it.
+                              A wait that ran out is reported by fmm_eval_status. */
 };
 
 /* Maximum expansion order accepted (p terms, coefficients k = 0..p-1). */
@@ -135,10 +142,20 @@ fmm_status fmm_step(fmm_tree* t, const double* d_xy, const double* d_gamma, void
  * a GPU fault): runs one of them on something that never happens -- which = 0:
  * the decoupled look-back of the list build, partitions and sorts on a
  * predecessor tile that never publishes; which = 1: the tensor-core M2L's
- * mbarrier wait on a barrier nothing arrives at -- with a short limit (4096
- * tries).  The expected result is FMM_ERR_TIMEOUT, returned from the device's
- * status word; the context stays usable.  Errors: INVALID_ARG (which), CUDA. */
+ * mbarrier wait on a barrier nothing arrives at; which = 2: the persistent
+ * evaluation's wait for a stage's dependencies on a unit that never completes
+ * -- with a short limit (4096 tries).  The expected result is FMM_ERR_TIMEOUT,
+ * returned from the device's status word; the context stays usable.
+ * Errors: INVALID_ARG (which), CUDA. */
 fmm_status fmm_selftest_bounded_wait(int which, void* stream);
+
+/* Status of the last evaluation's bounded device waits (the tensor-core
+ * M2L's mbarrier waits, the persistent evaluation's queue waits): synchronises
+ * `stream` and returns FMM_ERR_TIMEOUT if one of them ran out (its results are
+ * then incomplete), else FMM_OK.  Call it after the evaluation and before the
+ * next build or rebuild of the tree, which clears the status word.
+ * Errors: INVALID_ARG (NULL), CUDA, TIMEOUT. */
+fmm_status fmm_eval_status(fmm_tree* t, void* stream);
 
 /* Diagnostic: d_out[i] = the FP64 P2P's reciprocal of d_x[i] (n doubles,
  * device buffers): the hardware's approximate reciprocal refined by two

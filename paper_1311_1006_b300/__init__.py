@@ -18,12 +18,13 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (FMM_FLAG_GRAPH, FMM_FLAG_NO_GRAPH, FMM_FLAG_SERIAL, FMM_FLAG_TIMING, FMM_PATH_FP32, FMM_PATH_FP64, FMMError,
-                   FMMParams)
+from ._lib import (FMM_FLAG_GRAPH, FMM_FLAG_NO_GRAPH, FMM_FLAG_PERSISTENT, FMM_FLAG_SERIAL, FMM_FLAG_TIMING,
+                   FMM_PATH_FP32, FMM_PATH_FP64, FMMError, FMMParams)
 
 __all__ = ["Tree", "FMMFunction", "fmm", "default_nlevels", "seed_nlevels", "cost_model", "set_cost_model",
            "p_for_tolerance", "Autotuner", "FMMError", "FMM_PATH_FP32",
-           "FMM_PATH_FP64", "FMM_FLAG_GRAPH", "FMM_FLAG_NO_GRAPH", "FMM_FLAG_SERIAL", "FMM_FLAG_TIMING"]
+           "FMM_PATH_FP64", "FMM_FLAG_GRAPH", "FMM_FLAG_NO_GRAPH", "FMM_FLAG_PERSISTENT", "FMM_FLAG_SERIAL",
+           "FMM_FLAG_TIMING"]
 
 
 def _torch():
@@ -282,6 +283,10 @@ class Tree:
         strong = [si[so[b]: so[b] + ns[b]] for b in range(ns.shape[0])]
         weak = [wi[wo[b]: wo[b] + nw[b]] for b in range(nw.shape[0])]
         return strong, weak
+
+    def eval_status(self, stream=None) -> None:
+        """fmm_eval_status: raises FMMError (timeout) if a bounded wait of the last evaluation ran out."""
+        _lib.check(_lib.load().fmm_eval_status(self._h, _stream(stream)))
 
     def phase_times(self) -> dict:
         out = (ctypes.c_double * 7)()

@@ -23,6 +23,7 @@ FMM_FLAG_NO_GRAPH = 1
 FMM_FLAG_SERIAL = 2
 FMM_FLAG_TIMING = 4
 FMM_FLAG_GRAPH = 8
+FMM_FLAG_PERSISTENT = 16
 
 FMM_P_MAX = 32
 
@@ -80,6 +81,7 @@ def load() -> ctypes.CDLL:
         "fmm_eval_log": (S, [_VP, _VP, _VP, _VP]),
         "fmm_step": (S, [_VP, _VP, _VP, _VP, _VP]),
         "fmm_selftest_bounded_wait": (S, [ctypes.c_int, _VP]),
+        "fmm_eval_status": (S, [_VP, _VP]),
         "fmm_selftest_rcp64": (S, [_VP, _VP, ctypes.c_int64, _VP]),
         "fmm_eval_targets_log": (S, [_VP, _VP, _VP, _VP]),
         "fmm_eval_backward": (S, [_VP, _VP, _VP, _VP, _VP, _VP]),

@@ -222,7 +222,8 @@ static void release(Tree* t) {
                     t->d_lvl_base, t->d_woff, t->d_nw, t->d_widx, t->d_p2p_items,
                     t->d_m2l_items, t->d_m2l_rows, t->d_box_tail, t->d_m2l_rowctr, t->d_leaf_items, t->d_box_m2l, t->d_status, t->d_gam, t->d_near, t->d_M64,
                     t->d_pslot, t->d_posp, t->d_slot_of, t->d_gamp, t->d_xy_all, t->d_gam_all, t->d_phi_all,
-                    t->d_M32, t->d_Lm2l, t->d_L64, t->d_L32, t->d_p2p_part, t->d_m2l_part};
+                    t->d_M32, t->d_Lm2l, t->d_L64, t->d_L32, t->d_p2p_part, t->d_m2l_part, t->d_pstage,
+                    t->d_pers};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < 4; ++i) {
@@ -523,7 +524,7 @@ fmm_status fmm_step(fmm_tree* h, const double* d_xy, const double* d_gamma, void
     Tree& t = h->t;
     if (t.n_src > 0) return invalid("tree with separate evaluation points: use fmm_tree_rebuild_targets + fmm_eval_targets");
     fmm_status st;
-    if (t.batched || (t.flags & (FMM_FLAG_SERIAL | FMM_FLAG_TIMING | FMM_FLAG_GRAPH))) {
+    if (t.batched || (t.flags & (FMM_FLAG_SERIAL | FMM_FLAG_TIMING | FMM_FLAG_GRAPH | FMM_FLAG_PERSISTENT))) {
         // phase timing, the serial order and graph replay are defined on the two-call sequence
         if ((st = fmm_tree_rebuild(h, d_xy, nullptr, stream))) return st;
         return t.batched ? fmm_eval_batched(h, d_gamma, d_phi, stream) : fmm_eval(h, d_gamma, d_phi, stream);
@@ -568,8 +569,23 @@ fmm_status fmm_step(fmm_tree* h, const double* d_xy, const double* d_gamma, void
     return FMM_OK;
 }
 
+fmm_status fmm_eval_status(fmm_tree* h, void* stream) {
+    if (!h) return invalid("NULL tree");
+    Tree& t = h->t;
+    if (!t.d_status) return FMM_OK;
+    unsigned bits = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FMM_CUDA(cudaMemcpyAsync(&bits, t.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    FMM_CUDA(cudaStreamSynchronize(s));
+    if (bits & ST_TIMEOUT) {
+        set_error("a bounded wait of the evaluation ran out");
+        return FMM_ERR_TIMEOUT;
+    }
+    return FMM_OK;
+}
+
 fmm_status fmm_selftest_bounded_wait(int which, void* stream) {
-    if (which < 0 || which > 1) return invalid("which must be 0 (look-back) or 1 (mbarrier)");
+    if (which < 0 || which > 2) return invalid("which must be 0 (look-back), 1 (mbarrier) or 2 (work queue)");
     fmm_status st;
     if ((st = check_pending())) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -579,7 +595,8 @@ fmm_status fmm_selftest_bounded_wait(int which, void* stream) {
     unsigned* status = reinterpret_cast<unsigned*>(buf);
     if (e == cudaSuccess) {
         if (which == 0) launch_selftest_lookback(buf + 1, 1 << 12, status, s);
-        else launch_selftest_mbar(1 << 12, status, s);
+        else if (which == 1) launch_selftest_mbar(1 << 12, status, s);
+        else launch_selftest_queue(buf + 1, 1 << 12, status, s);
         e = cudaGetLastError();
     }
     unsigned h_status = 0;
@@ -660,12 +677,15 @@ static fmm_status eval_common(fmm_tree* h, const double* d_gamma, void* d_phi, v
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool use_graph =
         (t.flags & FMM_FLAG_GRAPH) && !(t.flags & (FMM_FLAG_NO_GRAPH | FMM_FLAG_TIMING)) && s != nullptr;
-    if (!use_graph) return run_eval(t, d_gamma, d_phi, s);
+    const bool persistent = t.flags & FMM_FLAG_PERSISTENT;
+    if (persistent && (st = prepare_persistent(t))) return st;  // table upload: before any capture
+    auto run = [&]() { return persistent ? run_eval_persistent(t, d_gamma, d_phi, s) : run_eval(t, d_gamma, d_phi, s); };
+    if (!use_graph) return run();
     const void* key[4] = {d_gamma, d_phi, (const void*)s, (const void*)(intptr_t)(t.path * 64 + t.P)};
     if (!t.graph || memcmp(key, t.graph_key, sizeof(key)) != 0) {
         invalidate_graph(t);
         FMM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        st = run_eval(t, d_gamma, d_phi, s);
+        st = run();
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(s, &g);
         if (st) {

@@ -226,6 +226,13 @@ struct Tree {
     cudaEvent_t ev_t[9] = {};  // phase boundaries of a timed evaluation (fmm_phase_times)
     bool timing_valid = false;
 
+    // persistent evaluation (FMM_FLAG_PERSISTENT): stage table of the device work queue
+    void* d_pstage = nullptr;             // device copy of the table
+    std::vector<char> h_pstage;           // the table last uploaded
+    int npstage = 0;
+    long long pstage_total = 0;           // tickets (units) of one evaluation
+    unsigned long long* d_pers = nullptr;  // [0] ticket, [1] far-field units done, [2] P2P units done
+
     // captured evaluation graph (keyed by the user pointers it bakes in)
     cudaGraphExec_t graph = nullptr;
     std::vector<const void*> p2p_funcs;  // P2P kernels launched by the last evaluation (low graph priority)
@@ -285,6 +292,8 @@ fmm_status alloc_eval_core(Tree& t, int sets);   // buffers that follow the tree
 fmm_status alloc_eval_parts(Tree& t);            // partial sums: follow the work-item capacities of the lists
 fmm_status run_eval(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s);
 fmm_status run_eval_log(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s);  // needs alloc_eval(t, 2)
+fmm_status prepare_persistent(Tree& t);  // stage table of the persistent evaluation (not under stream capture)
+fmm_status run_eval_persistent(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s);
 fmm_status run_backward(Tree& t, const double* d_gamma, const double* d_gphi, double* d_ggamma, double* d_gxy,
                         cudaStream_t s);
 
@@ -337,6 +346,7 @@ fmm_status m2l_tc_prepare(int P);
 // Self-tests of the bounded waits (a wait on something that never happens; ST_TIMEOUT expected).
 void launch_selftest_mbar(int limit, unsigned* status, cudaStream_t s);
 void launch_selftest_lookback(unsigned long long* st, int max_spins, unsigned* status, cudaStream_t s);
+void launch_selftest_queue(unsigned long long* ctr, int limit, unsigned* status, cudaStream_t s);
 void launch_selftest_rcp64(const double* x, int64_t n, double* out, cudaStream_t s);  // once per compiled order, before launches (and graph capture)
 void launch_m2l_tc(const Tree& t, const float2* M32, float2* Lm2l, float2* part, bool log_kernel, cudaStream_t s);
 

@@ -34,7 +34,9 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
 #include <utility>
+#include <vector>
 
 #include "fmm_internal.cuh"
 
@@ -84,9 +86,9 @@ __constant__ FactTable c_fact = make_fact();
 
 // Strengths into sorted order and into the leaf slot layout of the P2P pass
 // (FP32: slot pairs interleaved as (re[2m], re[2m+1], im[2m], im[2m+1])).
-__global__ void k_gather32(const double2* __restrict__ in, const int32_t* __restrict__ perm,
+__device__ __forceinline__ void d_gather32(const int vbx, const double2* __restrict__ in, const int32_t* __restrict__ perm,
                            const int32_t* __restrict__ slot_of, int n, float2* out, float* outp) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = vbx * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double2 g = in[perm[i]];
     const float2 v = make_float2((float)g.x, (float)g.y);
@@ -96,6 +98,8 @@ __global__ void k_gather32(const double2* __restrict__ in, const int32_t* __rest
     f[0] = v.x;
     f[2] = v.y;
 }
+__global__ void k_gather32(const double2* __restrict__ in, const int32_t* __restrict__ perm,
+                           const int32_t* __restrict__ slot_of, int n, float2* out, float* outp) { d_gather32(blockIdx.x, in, perm, slot_of, n, out, outp); }
 __global__ void k_gather64(const double2* __restrict__ in, const int32_t* __restrict__ perm,
                            const int32_t* __restrict__ slot_of, int n, double2* out, double2* outp) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -138,12 +142,12 @@ __global__ void k_gather_log64(const double2* __restrict__ in, const int32_t* __
 // One thread per leaf: at_k = sum_j Gamma_j w_j^k, w_j = (z_j - c)/rho, FP32.
 // Point offsets use the hi/lo split so w keeps full FP32 accuracy.
 template <int P>
-__global__ void __launch_bounds__(128) k_p2m32(const int32_t* __restrict__ leaves, int nleaf,
+__device__ __forceinline__ void d_p2m32(const int vbx, const int32_t* __restrict__ leaves, int nleaf,
                                                const int32_t* __restrict__ bstart, const int32_t* __restrict__ bcount,
                                                const float4* __restrict__ chl, const float* __restrict__ rho32,
                                                const float4* __restrict__ pos4, const float2* __restrict__ gam,
                                                float2* __restrict__ M32, double2* __restrict__ M64, int p, int PS) {
-    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    int q = vbx * blockDim.x + threadIdx.x;
     if (q >= nleaf) return;
     const int b = leaves[q];
     const float4 c = chl[b];
@@ -173,18 +177,24 @@ __global__ void __launch_bounds__(128) k_p2m32(const int32_t* __restrict__ leave
         for (int k = 0; k < P; ++k) o64[k] = k < p ? make_double2((double)a[k].x, (double)a[k].y) : make_double2(0.0, 0.0);
     }
 }
+template <int P>
+__global__ void __launch_bounds__(128) k_p2m32(const int32_t* __restrict__ leaves, int nleaf,
+                                               const int32_t* __restrict__ bstart, const int32_t* __restrict__ bcount,
+                                               const float4* __restrict__ chl, const float* __restrict__ rho32,
+                                               const float4* __restrict__ pos4, const float2* __restrict__ gam,
+                                               float2* __restrict__ M32, double2* __restrict__ M64, int p, int PS) { d_p2m32<P>(blockIdx.x, leaves, nleaf, bstart, bcount, chl, rho32, pos4, gam, M32, M64, p, PS); }
 
 // P2M of boxes with up to ~1024 points: one warp per box, lanes over its points,
 // then an xor-butterfly over the lanes (a fixed order); writes the FP32
 // multipole and its FP64 copy (these boxes are parents, read by the next shift).
 template <int P>
-__global__ void __launch_bounds__(128) k_p2m32_warp(const int32_t* __restrict__ boxes, int cnt,
+__device__ __forceinline__ void d_p2m32_warp(const int vbx, const int32_t* __restrict__ boxes, int cnt,
                                                     const int32_t* __restrict__ bstart,
                                                     const int32_t* __restrict__ bcount, const float4* __restrict__ chl,
                                                     const float* __restrict__ rho32, const float4* __restrict__ pos4,
                                                     const float2* __restrict__ gam, float2* __restrict__ M32,
                                                     double2* __restrict__ M64, int p, int PS) {
-    const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int w = (int)((vbx * (size_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (w >= cnt) return;  // warp-uniform
     const int b = boxes[w];
@@ -223,6 +233,13 @@ __global__ void __launch_bounds__(128) k_p2m32_warp(const int32_t* __restrict__ 
         }
     }
 }
+template <int P>
+__global__ void __launch_bounds__(128) k_p2m32_warp(const int32_t* __restrict__ boxes, int cnt,
+                                                    const int32_t* __restrict__ bstart,
+                                                    const int32_t* __restrict__ bcount, const float4* __restrict__ chl,
+                                                    const float* __restrict__ rho32, const float4* __restrict__ pos4,
+                                                    const float2* __restrict__ gam, float2* __restrict__ M32,
+                                                    double2* __restrict__ M64, int p, int PS) { d_p2m32_warp<P>(blockIdx.x, boxes, cnt, bstart, bcount, chl, rho32, pos4, gam, M32, M64, p, PS); }
 
 template <int P>
 __global__ void __launch_bounds__(128) k_p2m64(const int32_t* __restrict__ leaves, int nleaf,
@@ -262,12 +279,12 @@ __global__ void __launch_bounds__(128) k_p2m64(const int32_t* __restrict__ leave
 // children of one parent and add them with two xor-shuffles (fixed order).
 // Leaf children of the FP32 path are read from the FP32 multipoles of P2M.
 template <int P>
-__global__ void __launch_bounds__(128) k_m2m(const int32_t* __restrict__ parents, int cnt,
+__device__ __forceinline__ void d_m2m(const int vbx, const int32_t* __restrict__ parents, int cnt,
                                              const int32_t* __restrict__ child0, const double* __restrict__ rho,
                                              const double2* __restrict__ center, const float2* __restrict__ M32in,
                                              double2* __restrict__ M64, float2* __restrict__ M32out, int fp32_path,
                                              int p, int PS) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = vbx * blockDim.x + threadIdx.x;
     const int pi = q >> 2, c = q & 3;
     const bool valid = pi < cnt;
     double2 v[P];
@@ -326,6 +343,12 @@ __global__ void __launch_bounds__(128) k_m2m(const int32_t* __restrict__ parents
         for (int k = 0; k < P; ++k) o32[k] = k < p ? make_float2((float)v[k].x, (float)v[k].y) : make_float2(0.f, 0.f);
     }
 }
+template <int P>
+__global__ void __launch_bounds__(128) k_m2m(const int32_t* __restrict__ parents, int cnt,
+                                             const int32_t* __restrict__ child0, const double* __restrict__ rho,
+                                             const double2* __restrict__ center, const float2* __restrict__ M32in,
+                                             double2* __restrict__ M64, float2* __restrict__ M32out, int fp32_path,
+                                             int p, int PS) { d_m2m<P>(blockIdx.x, parents, cnt, child0, rho, center, M32in, M64, M32out, fp32_path, p, PS); }
 
 // --------------------------------------------------------------------- M2L
 
@@ -365,13 +388,13 @@ __device__ __forceinline__ void m2l_apply(float2 (&w)[P], const float4 (&aa)[(P 
 }
 
 template <int P, bool LOG>
-__global__ void __launch_bounds__(128) k_m2l32(const int4* __restrict__ items,
+__device__ __forceinline__ void d_m2l32(const int vbx, const int4* __restrict__ items,
                                                const unsigned long long* __restrict__ nitems,
                                                const int32_t* __restrict__ woff, const int32_t* __restrict__ widx,
                                                const float4* __restrict__ chl, const float* __restrict__ rho32,
                                                const float2* __restrict__ M32, float2* __restrict__ Lm2l,
                                                float2* __restrict__ part, const int32_t* __restrict__ rows, int PS) {
-    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = vbx * blockDim.x + threadIdx.x;
     if (row >= (int)*nitems) return;
     const int it = rows[row];  // work item of this thread (row order: similar lengths within a warp)
     const int4 item = items[it];
@@ -416,6 +439,13 @@ __global__ void __launch_bounds__(128) k_m2l32(const int4* __restrict__ items,
     for (int l = 0; l < P; ++l) out[l] = acc[l];
     if constexpr (LOG) out[P] = make_float2(b0, 0.f);
 }
+template <int P, bool LOG>
+__global__ void __launch_bounds__(128) k_m2l32(const int4* __restrict__ items,
+                                               const unsigned long long* __restrict__ nitems,
+                                               const int32_t* __restrict__ woff, const int32_t* __restrict__ widx,
+                                               const float4* __restrict__ chl, const float* __restrict__ rho32,
+                                               const float2* __restrict__ M32, float2* __restrict__ Lm2l,
+                                               float2* __restrict__ part, const int32_t* __restrict__ rows, int PS) { d_m2l32<P, LOG>(blockIdx.x, items, nitems, woff, widx, chl, rho32, M32, Lm2l, part, rows, PS); }
 
 template <int P, bool LOG>
 __global__ void __launch_bounds__(128) k_m2l64(const int4* __restrict__ items,
@@ -485,13 +515,13 @@ __global__ void __launch_bounds__(128) k_m2l64(const int4* __restrict__ items,
 // LOG the constant term (slot P) is the parent's log polynomial at the child
 // centre plus the child's own M2L constant.
 template <int P, typename LM, bool LOG>
-__global__ void __launch_bounds__(128) k_l2l(const int32_t* __restrict__ boxes, int cnt,
+__device__ __forceinline__ void d_l2l(const int vbx, const int32_t* __restrict__ boxes, int cnt,
                                              const int32_t* __restrict__ parent, const int32_t* __restrict__ child0,
                                              const double* __restrict__ rho, const double2* __restrict__ center,
                                              const int2* __restrict__ box_m2l, const LM* __restrict__ Lm2l,
                                              double2* __restrict__ L64,
                                              float2* __restrict__ L32, int all32, int p, int PS) {
-    int qi = blockIdx.x * blockDim.x + threadIdx.x;
+    int qi = vbx * blockDim.x + threadIdx.x;
     if (qi >= cnt) return;
     const int c = boxes[qi];
     const int Pb = parent[c];
@@ -543,6 +573,13 @@ __global__ void __launch_bounds__(128) k_l2l(const int32_t* __restrict__ boxes, 
         if (leaf32) o32[P] = make_float2((float)b0, 0.f);
     }
 }
+template <int P, typename LM, bool LOG>
+__global__ void __launch_bounds__(128) k_l2l(const int32_t* __restrict__ boxes, int cnt,
+                                             const int32_t* __restrict__ parent, const int32_t* __restrict__ child0,
+                                             const double* __restrict__ rho, const double2* __restrict__ center,
+                                             const int2* __restrict__ box_m2l, const LM* __restrict__ Lm2l,
+                                             double2* __restrict__ L64,
+                                             float2* __restrict__ L32, int all32, int p, int PS) { d_l2l<P, LM, LOG>(blockIdx.x, boxes, cnt, parent, child0, rho, center, box_m2l, Lm2l, L64, L32, all32, p, PS); }
 
 // ---- M2M / L2L for levels with few boxes: one warp per shift -----------------
 // FP64 warp instructions are expensive per issue on this GPU (the FP64 pipe
@@ -582,13 +619,13 @@ __device__ __forceinline__ double2 shfl2(double2 v, int src) {
 // One CTA of 4 warps per parent; warp c shifts child c, and the four shifted
 // expansions are added in a fixed order ((c0 + c1) + (c2 + c3)).
 template <int P>
-__global__ void __launch_bounds__(128) k_m2m_warp(const int32_t* __restrict__ parents, int cnt,
+__device__ __forceinline__ void d_m2m_warp(const int vbx, const int32_t* __restrict__ parents, int cnt,
                                                   const int32_t* __restrict__ child0, const double* __restrict__ rho,
                                                   const double2* __restrict__ center,
                                                   const float2* __restrict__ M32in, double2* __restrict__ M64,
                                                   float2* __restrict__ M32out, int fp32_path, int p, int PS) {
     __shared__ double2 part[4][32];
-    const int pi = blockIdx.x;
+    const int pi = vbx;
     if (pi >= cnt) return;
     const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = parents[pi];
@@ -630,19 +667,25 @@ __global__ void __launch_bounds__(128) k_m2m_warp(const int32_t* __restrict__ pa
     M64[(size_t)b * PS + lane] = s;
     if (fp32_path) M32out[(size_t)b * PS + lane] = make_float2((float)s.x, (float)s.y);
 }
+template <int P>
+__global__ void __launch_bounds__(128) k_m2m_warp(const int32_t* __restrict__ parents, int cnt,
+                                                  const int32_t* __restrict__ child0, const double* __restrict__ rho,
+                                                  const double2* __restrict__ center,
+                                                  const float2* __restrict__ M32in, double2* __restrict__ M64,
+                                                  float2* __restrict__ M32out, int fp32_path, int p, int PS) { d_m2m_warp<P>(blockIdx.x, parents, cnt, child0, rho, center, M32in, M64, M32out, fp32_path, p, PS); }
 
 // One warp per child box: shifted parent local + the box's own M2L sum.  With
 // LOG, lane m adds bt_m q^(m+1)/(m+1) to the constant term (xor-butterfly sum
 // across the warp, a fixed order).
 template <int P, typename LM, bool LOG>
-__global__ void __launch_bounds__(128) k_l2l_warp(const int32_t* __restrict__ boxes, int cnt,
+__device__ __forceinline__ void d_l2l_warp(const int vbx, const int32_t* __restrict__ boxes, int cnt,
                                                   const int32_t* __restrict__ parent,
                                                   const int32_t* __restrict__ child0, const double* __restrict__ rho,
                                                   const double2* __restrict__ center,
                                                   const int2* __restrict__ box_m2l, const LM* __restrict__ Lm2l,
                                                   double2* __restrict__ L64, float2* __restrict__ L32, int all32, int p,
                                                   int PS) {
-    const int qi = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int qi = (int)((vbx * (size_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (qi >= cnt) return;  // warp-uniform
     const int c = boxes[qi];
@@ -690,6 +733,14 @@ __global__ void __launch_bounds__(128) k_l2l_warp(const int32_t* __restrict__ bo
     L64[(size_t)c * PS + lane] = v;
     if (L32 != nullptr && (all32 || child0[c] < 0)) L32[(size_t)c * PS + lane] = make_float2((float)v.x, (float)v.y);
 }
+template <int P, typename LM, bool LOG>
+__global__ void __launch_bounds__(128) k_l2l_warp(const int32_t* __restrict__ boxes, int cnt,
+                                                  const int32_t* __restrict__ parent,
+                                                  const int32_t* __restrict__ child0, const double* __restrict__ rho,
+                                                  const double2* __restrict__ center,
+                                                  const int2* __restrict__ box_m2l, const LM* __restrict__ Lm2l,
+                                                  double2* __restrict__ L64, float2* __restrict__ L32, int all32, int p,
+                                                  int PS) { d_l2l_warp<P, LM, LOG>(blockIdx.x, boxes, cnt, parent, child0, rho, center, box_m2l, Lm2l, L64, L32, all32, p, PS); }
 
 // Levels with at most this many shifts use the warp-per-shift kernels.
 constexpr int kWarpShiftMax = 1024;  // measured against 4096 and 16384: 1024 fastest
@@ -745,7 +796,7 @@ __device__ __forceinline__ float2 horner_p(const float2* __restrict__ b, const f
 // field is the parent's local at the point plus its own M2L sum at the point,
 // which is the value the shifted local would give (up to rounding).
 template <int P>
-__global__ void __launch_bounds__(256) k_l2p32(int n, const int32_t* __restrict__ leaf_of,
+__device__ __forceinline__ void d_l2p32(const int vbx, int n, const int32_t* __restrict__ leaf_of,
                                                const int32_t* __restrict__ fold_par, const int2* __restrict__ box_m2l,
                                                const float4* __restrict__ chl,
                                                const float* __restrict__ rho32, const float4* __restrict__ pos4,
@@ -753,7 +804,7 @@ __global__ void __launch_bounds__(256) k_l2p32(int n, const int32_t* __restrict_
                                                const float2* __restrict__ nearv, const NearParts<float2> np,
                                                const int32_t* __restrict__ perm, float2* __restrict__ out, int p,
                                                int PS) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = vbx * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int lf = leaf_of[i];
     const float4 pt = pos4[i];
@@ -772,6 +823,15 @@ __global__ void __launch_bounds__(256) k_l2p32(int n, const int32_t* __restrict_
     const float2 nv = near_of(i, lf, nearv, np);
     out[perm[i]] = make_float2(v.x + nv.x, v.y + nv.y);
 }
+template <int P>
+__global__ void __launch_bounds__(256) k_l2p32(int n, const int32_t* __restrict__ leaf_of,
+                                               const int32_t* __restrict__ fold_par, const int2* __restrict__ box_m2l,
+                                               const float4* __restrict__ chl,
+                                               const float* __restrict__ rho32, const float4* __restrict__ pos4,
+                                               const float2* __restrict__ L32, const float2* __restrict__ Lm2l,
+                                               const float2* __restrict__ nearv, const NearParts<float2> np,
+                                               const int32_t* __restrict__ perm, float2* __restrict__ out, int p,
+                                               int PS) { d_l2p32<P>(blockIdx.x, n, leaf_of, fold_par, box_m2l, chl, rho32, pos4, L32, Lm2l, nearv, np, perm, out, p, PS); }
 
 template <int P>
 __global__ void __launch_bounds__(256) k_l2p64(int n, const int32_t* __restrict__ leaf_of,
@@ -1109,6 +1169,130 @@ constexpr float kHalfLn2 = 0.34657359027997264f;  // ln(2)/2: log2(|d|^2) -> ln|
 
 // Blocks per SM: 7 for TPL <= 4 (72 registers, no spills; measured against 4 (124
 // registers), 5, 6 (80) and 8 (64, spills): 7 is the fastest), 2 for TPL = 8.
+// One work item of the warp (its target leaf against a run of its strong list).
+template <int TPL, int LT, bool LOG>
+__device__ __forceinline__ void d_p2p_pairs_item(const int it, const int4* __restrict__ items,
+                                                 const int32_t* __restrict__ bstart,
+                                                 const int32_t* __restrict__ bcount, const int32_t* __restrict__ pslot,
+                                                 const int32_t* __restrict__ soff, const int2* __restrict__ srng,
+                                                 const ulonglong2* __restrict__ posq,
+                                                 const ulonglong2* __restrict__ gamq, float2* __restrict__ nearv,
+                                                 float2* __restrict__ part, int TS, int pad) {
+    constexpr int S = 32 / LT;      // pair slices
+    constexpr bool LONG = LT > 4;   // the LT = 4 layouts hold leaves of at most 16 = 2S slots
+    const int lane = threadIdx.x & 31;
+    const int tg = lane % LT, ss = lane / LT;
+    const int4 item = items[it];
+    const int b = item.x;
+    const int ts = bstart[b], tn = bcount[b], tb = pslot[b];
+    const int2* rl = srng + soff[b];
+    const int ke = item.z;
+    for (int t0 = 0; t0 < tn; t0 += TPL * LT) {
+        f2x tx[TPL], ty[TPL], txl[TPL], tyl[TPL], ax[TPL], ay[TPL];
+#pragma unroll
+        for (int u = 0; u < TPL; ++u) {
+            const int idx = t0 + tg + u * LT;
+            float x = 0.f, y = 0.f, xl = 0.f, yl = 0.f;
+            if (idx < tn) {
+                const int sl = tb + idx;
+                const float* f = reinterpret_cast<const float*>(posq) + 8 * (sl >> 1) + (sl & 1);
+                x = f[0];
+                y = f[2];
+                xl = f[4];
+                yl = f[6];
+            }
+            tx[u] = f2pk(x, x);
+            ty[u] = f2pk(y, y);
+            txl[u] = f2pk(xl, xl);
+            tyl[u] = f2pk(yl, yl);
+            ax[u] = 0ull;
+            ay[u] = 0ull;
+        }
+        if constexpr (!LONG) {
+            // slot-pair index of range k's slice ss (the padding block past the end)
+#define FMM_PIDX(k) ((((k) < ke ? rl[(k)].x : pad) >> 1) + ss)
+            int k = item.y;
+            int oa0 = FMM_PIDX(k), oa1 = FMM_PIDX(k + 1);
+            ulonglong2 pa0 = posq[2 * oa0], qa0 = posq[2 * oa0 + 1], ga0 = gamq[oa0];
+            ulonglong2 pa1 = posq[2 * oa1], qa1 = posq[2 * oa1 + 1], ga1 = gamq[oa1];
+            int ob0 = FMM_PIDX(k + 2), ob1 = FMM_PIDX(k + 3);
+            while (true) {
+                const ulonglong2 pb0 = posq[2 * ob0], qb0 = posq[2 * ob0 + 1], gb0 = gamq[ob0];
+                const ulonglong2 pb1 = posq[2 * ob1], qb1 = posq[2 * ob1 + 1], gb1 = gamq[ob1];
+                oa0 = FMM_PIDX(k + 4);
+                oa1 = FMM_PIDX(k + 5);
+                {
+                    const SrcPair s0 = src_pair(pa0, qa0, ga0), s1 = src_pair(pa1, qa1, ga1);
+#pragma unroll
+                    for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
+#pragma unroll
+                    for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s1, ax[u], ay[u]);
+                }
+                if (k + 2 >= ke) break;
+                pa0 = posq[2 * oa0];
+                qa0 = posq[2 * oa0 + 1];
+                ga0 = gamq[oa0];
+                pa1 = posq[2 * oa1];
+                qa1 = posq[2 * oa1 + 1];
+                ga1 = gamq[oa1];
+                ob0 = FMM_PIDX(k + 6);
+                ob1 = FMM_PIDX(k + 7);
+                {
+                    const SrcPair s0 = src_pair(pb0, qb0, gb0), s1 = src_pair(pb1, qb1, gb1);
+#pragma unroll
+                    for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
+#pragma unroll
+                    for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s1, ax[u], ay[u]);
+                }
+                k += 4;
+                if (k >= ke) break;
+            }
+#undef FMM_PIDX
+        } else {
+            for (int k = item.y; k < ke; ++k) {
+                const int2 r = rl[k];
+                const int o = (r.x >> 1) + ss;  // slot-pair index of this slice
+                int e = 0;                      // slot-pair offset of the step
+                for (; 2 * (e + S) < r.y; e += 2 * S) {  // two steps, both inside the range's slots
+                    const SrcPair s0 = src_pair(posq[2 * (o + e)], posq[2 * (o + e) + 1], gamq[o + e]);
+                    const SrcPair s1 =
+                        src_pair(posq[2 * (o + e + S)], posq[2 * (o + e + S) + 1], gamq[o + e + S]);
+#pragma unroll
+                    for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
+#pragma unroll
+                    for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s1, ax[u], ay[u]);
+                }
+                if (2 * e < r.y) {
+                    const SrcPair s0 = src_pair(posq[2 * (o + e)], posq[2 * (o + e) + 1], gamq[o + e]);
+#pragma unroll
+                    for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < TPL; ++u) {
+            float x0, x1, y0, y1;
+            f2upk(ax[u], x0, x1);
+            f2upk(ay[u], y0, y1);
+            float2 tot = make_float2(x0 + x1, y0 + y1);
+#pragma unroll
+            for (int o = LT; o < 32; o <<= 1) {
+                tot.x += __shfl_xor_sync(0xffffffffu, tot.x, o);
+                tot.y += __shfl_xor_sync(0xffffffffu, tot.y, o);
+            }
+            if constexpr (LOG) {
+                tot.x *= kHalfLn2;
+                tot.y *= kHalfLn2;
+            }
+            const int idx = t0 + tg + u * LT;
+            if (ss == 0 && idx < tn) {
+                if (item.w < 0) nearv[ts + idx] = tot;
+                else part[(size_t)it * TS + idx] = tot;
+            }
+        }
+    }
+}
+
 template <int TPL, int LT, bool LOG>
 __global__ void __launch_bounds__(kP2PDWarps * 32, TPL > 4 ? 2 : 7)
     k_p2p_pairs(const int4* __restrict__ items, const unsigned long long* __restrict__ nitems,
@@ -1117,125 +1301,15 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, TPL > 4 ? 2 : 7)
                 const int32_t* __restrict__ soff, const int2* __restrict__ srng, const ulonglong2* __restrict__ posq,
                 const ulonglong2* __restrict__ gamq, float2* __restrict__ nearv, float2* __restrict__ part, int TS,
                 int pad, int per_warp) {
-    constexpr int S = 32 / LT;      // pair slices
-    constexpr bool LONG = LT > 4;   // the LT = 4 layouts hold leaves of at most 16 = 2S slots
     const int lane = threadIdx.x & 31;
-    const int tg = lane % LT, ss = lane / LT;
     const int nit = (int)*nitems;
     for (int done = 0; done < per_warp; ++done) {
         int it = 0;
         if (lane == 0) it = (int)atomicAdd(next_item, 1u);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= nit) break;
-        const int4 item = items[it];
-        const int b = item.x;
-        const int ts = bstart[b], tn = bcount[b], tb = pslot[b];
-        const int2* rl = srng + soff[b];
-        const int ke = item.z;
-        for (int t0 = 0; t0 < tn; t0 += TPL * LT) {
-            f2x tx[TPL], ty[TPL], txl[TPL], tyl[TPL], ax[TPL], ay[TPL];
-#pragma unroll
-            for (int u = 0; u < TPL; ++u) {
-                const int idx = t0 + tg + u * LT;
-                float x = 0.f, y = 0.f, xl = 0.f, yl = 0.f;
-                if (idx < tn) {
-                    const int sl = tb + idx;
-                    const float* f = reinterpret_cast<const float*>(posq) + 8 * (sl >> 1) + (sl & 1);
-                    x = f[0];
-                    y = f[2];
-                    xl = f[4];
-                    yl = f[6];
-                }
-                tx[u] = f2pk(x, x);
-                ty[u] = f2pk(y, y);
-                txl[u] = f2pk(xl, xl);
-                tyl[u] = f2pk(yl, yl);
-                ax[u] = 0ull;
-                ay[u] = 0ull;
-            }
-            if constexpr (!LONG) {
-                // slot-pair index of range k's slice ss (the padding block past the end)
-#define FMM_PIDX(k) ((((k) < ke ? rl[(k)].x : pad) >> 1) + ss)
-                int k = item.y;
-                int oa0 = FMM_PIDX(k), oa1 = FMM_PIDX(k + 1);
-                ulonglong2 pa0 = posq[2 * oa0], qa0 = posq[2 * oa0 + 1], ga0 = gamq[oa0];
-                ulonglong2 pa1 = posq[2 * oa1], qa1 = posq[2 * oa1 + 1], ga1 = gamq[oa1];
-                int ob0 = FMM_PIDX(k + 2), ob1 = FMM_PIDX(k + 3);
-                while (true) {
-                    const ulonglong2 pb0 = posq[2 * ob0], qb0 = posq[2 * ob0 + 1], gb0 = gamq[ob0];
-                    const ulonglong2 pb1 = posq[2 * ob1], qb1 = posq[2 * ob1 + 1], gb1 = gamq[ob1];
-                    oa0 = FMM_PIDX(k + 4);
-                    oa1 = FMM_PIDX(k + 5);
-                    {
-                        const SrcPair s0 = src_pair(pa0, qa0, ga0), s1 = src_pair(pa1, qa1, ga1);
-#pragma unroll
-                        for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
-#pragma unroll
-                        for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s1, ax[u], ay[u]);
-                    }
-                    if (k + 2 >= ke) break;
-                    pa0 = posq[2 * oa0];
-                    qa0 = posq[2 * oa0 + 1];
-                    ga0 = gamq[oa0];
-                    pa1 = posq[2 * oa1];
-                    qa1 = posq[2 * oa1 + 1];
-                    ga1 = gamq[oa1];
-                    ob0 = FMM_PIDX(k + 6);
-                    ob1 = FMM_PIDX(k + 7);
-                    {
-                        const SrcPair s0 = src_pair(pb0, qb0, gb0), s1 = src_pair(pb1, qb1, gb1);
-#pragma unroll
-                        for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
-#pragma unroll
-                        for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s1, ax[u], ay[u]);
-                    }
-                    k += 4;
-                    if (k >= ke) break;
-                }
-#undef FMM_PIDX
-            } else {
-                for (int k = item.y; k < ke; ++k) {
-                    const int2 r = rl[k];
-                    const int o = (r.x >> 1) + ss;  // slot-pair index of this slice
-                    int e = 0;                      // slot-pair offset of the step
-                    for (; 2 * (e + S) < r.y; e += 2 * S) {  // two steps, both inside the range's slots
-                        const SrcPair s0 = src_pair(posq[2 * (o + e)], posq[2 * (o + e) + 1], gamq[o + e]);
-                        const SrcPair s1 =
-                            src_pair(posq[2 * (o + e + S)], posq[2 * (o + e + S) + 1], gamq[o + e + S]);
-#pragma unroll
-                        for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
-#pragma unroll
-                        for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s1, ax[u], ay[u]);
-                    }
-                    if (2 * e < r.y) {
-                        const SrcPair s0 = src_pair(posq[2 * (o + e)], posq[2 * (o + e) + 1], gamq[o + e]);
-#pragma unroll
-                        for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < TPL; ++u) {
-                float x0, x1, y0, y1;
-                f2upk(ax[u], x0, x1);
-                f2upk(ay[u], y0, y1);
-                float2 tot = make_float2(x0 + x1, y0 + y1);
-#pragma unroll
-                for (int o = LT; o < 32; o <<= 1) {
-                    tot.x += __shfl_xor_sync(0xffffffffu, tot.x, o);
-                    tot.y += __shfl_xor_sync(0xffffffffu, tot.y, o);
-                }
-                if constexpr (LOG) {
-                    tot.x *= kHalfLn2;
-                    tot.y *= kHalfLn2;
-                }
-                const int idx = t0 + tg + u * LT;
-                if (ss == 0 && idx < tn) {
-                    if (item.w < 0) nearv[ts + idx] = tot;
-                    else part[(size_t)it * TS + idx] = tot;
-                }
-            }
-        }
+        d_p2p_pairs_item<TPL, LT, LOG>(it, items, bstart, bcount, pslot, soff, srng, posq, gamq, nearv, part, TS,
+                                       pad);
     }
 }
 
@@ -1243,9 +1317,9 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, TPL > 4 ? 2 : 7)
 // (lanes stride over the PS slots: PS exceeds 32 at p = 32, with the log kernel's
 // constant term in slot 32).
 template <typename C>
-__global__ void __launch_bounds__(256) k_reduce_m2l(int nbox, const int2* __restrict__ box_m2l,
+__device__ __forceinline__ void d_reduce_m2l(const int vbx, int nbox, const int2* __restrict__ box_m2l,
                                                     const C* __restrict__ part, int PS, C* __restrict__ Lm2l) {
-    const int b = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int b = (int)((vbx * (size_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (b >= nbox) return;
     const int2 mi = box_m2l[b];
@@ -1261,6 +1335,9 @@ __global__ void __launch_bounds__(256) k_reduce_m2l(int nbox, const int2* __rest
         Lm2l[(size_t)b * PS + c] = s;
     }
 }
+template <typename C>
+__global__ void __launch_bounds__(256) k_reduce_m2l(int nbox, const int2* __restrict__ box_m2l,
+                                                    const C* __restrict__ part, int PS, C* __restrict__ Lm2l) { d_reduce_m2l<C>(blockIdx.x, nbox, box_m2l, part, PS, Lm2l); }
 
 // Diagnostic: the P2P's FP64 reciprocal over an array (tests compare it with
 // the correctly rounded 1/x).
@@ -1272,6 +1349,192 @@ void launch_selftest_rcp64(const double* x, int64_t n, double* out, cudaStream_t
     k_selftest_rcp64<<<nblk(n, 256), 256, 0, s>>>(x, n, out);
 }
 
+// ================================================= persistent evaluation
+// FMM_FLAG_PERSISTENT (FP32 path, harmonic kernel): the whole evaluation of a
+// tree -- one instance or a forest of many -- in ONE launch.  Its CTAs take
+// units from a device work queue: an atomic ticket counter runs over a table
+// of stages, each stage a range of virtual blocks of 128 threads that run the
+// body of one of the pass kernels above (the same arithmetic in the same
+// order per box, item and point).  Before a unit runs, its CTA waits, with a
+// bounded spin, until the units its stage depends on are complete: a
+// far-field stage waits for every far-field unit before it (the strengths for
+// P2M, the level below for M2M, the whole upward pass for M2L, the level above
+// for L2L), P2P units only for the strength gather, L2P for everything.  A
+// unit waits only on units with smaller tickets, which running CTAs already
+// hold, so the queue always advances.  P2P units are interleaved between the
+// far-field stages, so that CTAs that wait on a level of the far field have
+// P2P work behind them.  M2L runs on the CUDA cores (the body of k_m2l32): the
+// tensor-core M2L wants whole CTAs with 168 registers and its tensor memory.
+enum : int { PT_GATHER = 0, PT_P2M_T, PT_P2M_W, PT_M2M_T, PT_M2M_W, PT_M2L, PT_REDUCE, PT_L2L_T, PT_L2L_W, PT_P2P,
+             PT_L2P };
+
+struct PStage {
+    long long ticket0;   // first ticket of the stage
+    long long need_far;  // far-field units that must be complete before a unit of the stage runs
+    long long need_p2p;  // P2P units that must be complete
+    const int32_t* ids;  // the stage's box list (leaves, a level's parents or boxes)
+    int type;
+    int nvb;             // virtual blocks (units) of the stage
+    int vb0;             // first virtual block of the stage within its pass (P2P is cut into chunks)
+    int cnt;             // entries of `ids`
+    int arg;             // P2M: write the FP64 copy (parents); L2L: FP32 copy of every box (all32)
+    int pad_;
+};
+constexpr int kMaxPStages = 96;
+
+struct PArgs {
+    const PStage* st;
+    int nst;
+    long long total;
+    unsigned long long* ctr;  // [0] ticket, [1] far-field units done, [2] P2P units done
+    unsigned* status;
+    int spin_limit;
+    int n, nbox, p, PS, lay, pad, TS;
+    const double2* gin;
+    const int32_t *perm, *slot_of, *bstart, *bcount, *child0, *parent, *leaf_of, *fold_par, *pslot, *soff, *woff,
+        *widx, *m2l_rows;
+    const float4 *chl, *pos4;
+    const float* rho32;
+    const double* rho;
+    const double2* center;
+    const int2 *box_m2l, *srng, *leaf_items;
+    const int4 *m2l_items, *p2p_items;
+    const unsigned long long *n_m2l, *n_p2p;
+    const ulonglong2* posq;
+    float2* gam;
+    float* gamp;
+    float2 *M32, *Lm2l, *m2l_part, *L32, *nearv, *p2p_part, *out;
+    double2 *M64, *L64;
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Wait until at least need_far far-field units and need_p2p P2P units are
+// complete; after `limit` rounds give up, set ST_TIMEOUT and return false.
+__device__ bool pq_wait(const unsigned long long* ctr, long long need_far, long long need_p2p, unsigned* status,
+                        int limit) {
+    for (int spins = 0;; ++spins) {
+        if ((long long)ld_acquire_u64(ctr + 1) >= need_far && (long long)ld_acquire_u64(ctr + 2) >= need_p2p)
+            return true;
+        if (spins >= limit) {
+            atomicOr(status, ST_TIMEOUT);
+            return false;
+        }
+        __nanosleep(256);
+    }
+}
+
+// Self-test of the queue's bounded wait: a unit that needs one far-field unit
+// more than will ever complete must give up and report ST_TIMEOUT.
+__global__ void k_selftest_queue(unsigned long long* ctr, int limit, unsigned* status) {
+    if (threadIdx.x == 0) pq_wait(ctr, (long long)ld_acquire_u64(ctr + 1) + 1, 0, status, limit);
+}
+void launch_selftest_queue(unsigned long long* ctr, int limit, unsigned* status, cudaStream_t s) {
+    k_selftest_queue<<<1, 32, 0, s>>>(ctr, limit, status);
+}
+
+template <int TPL, int LT>
+__device__ __forceinline__ void pq_p2p(const PArgs& a, int it) {
+    d_p2p_pairs_item<TPL, LT, false>(it, a.p2p_items, a.bstart, a.bcount, a.pslot, a.soff, a.srng, a.posq,
+                                     reinterpret_cast<const ulonglong2*>(a.gamp), a.nearv, a.p2p_part, a.TS, a.pad);
+}
+
+template <int P>
+__device__ __forceinline__ void pq_unit(const PArgs& a, const PStage& g, int vb) {
+    switch (g.type) {
+        case PT_GATHER:
+            d_gather32(vb, a.gin, a.perm, a.slot_of, a.n, a.gam, a.gamp);
+            break;
+        case PT_P2M_T:
+            d_p2m32<P>(vb, g.ids, g.cnt, a.bstart, a.bcount, a.chl, a.rho32, a.pos4, a.gam, a.M32,
+                       g.arg ? a.M64 : nullptr, a.p, a.PS);
+            break;
+        case PT_P2M_W:
+            d_p2m32_warp<P>(vb, g.ids, g.cnt, a.bstart, a.bcount, a.chl, a.rho32, a.pos4, a.gam, a.M32, a.M64, a.p,
+                            a.PS);
+            break;
+        case PT_M2M_T:
+            d_m2m<P>(vb, g.ids, g.cnt, a.child0, a.rho, a.center, a.M32, a.M64, a.M32, 1, a.p, a.PS);
+            break;
+        case PT_M2M_W:
+            d_m2m_warp<P>(vb, g.ids, g.cnt, a.child0, a.rho, a.center, a.M32, a.M64, a.M32, 1, a.p, a.PS);
+            break;
+        case PT_M2L:
+            d_m2l32<P, false>(vb, a.m2l_items, a.n_m2l, a.woff, a.widx, a.chl, a.rho32, a.M32, a.Lm2l, a.m2l_part,
+                              a.m2l_rows, a.PS);
+            break;
+        case PT_REDUCE:
+            d_reduce_m2l<float2>(vb, a.nbox, a.box_m2l, a.m2l_part, a.PS, a.Lm2l);
+            break;
+        case PT_L2L_T:
+            d_l2l<P, float2, false>(vb, g.ids, g.cnt, a.parent, a.child0, a.rho, a.center, a.box_m2l, a.Lm2l, a.L64,
+                                    a.L32, g.arg, a.p, a.PS);
+            break;
+        case PT_L2L_W:
+            d_l2l_warp<P, float2, false>(vb, g.ids, g.cnt, a.parent, a.child0, a.rho, a.center, a.box_m2l, a.Lm2l,
+                                         a.L64, a.L32, g.arg, a.p, a.PS);
+            break;
+        case PT_P2P: {
+            const int it = vb * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);  // one item per warp
+            if (it < (int)*a.n_p2p) {
+                switch (a.lay) {
+                    case 204: pq_p2p<2, 4>(a, it); break;
+                    case 404: pq_p2p<4, 4>(a, it); break;
+                    case 408: pq_p2p<4, 8>(a, it); break;
+                    case 416: pq_p2p<4, 16>(a, it); break;
+                    default: pq_p2p<8, 16>(a, it); break;
+                }
+            }
+            break;
+        }
+        case PT_L2P: {
+            const NearParts<float2> np{a.leaf_items, a.bstart, a.p2p_part, a.TS};
+            d_l2p32<P>(vb, a.n, a.leaf_of, a.fold_par, a.box_m2l, a.chl, a.rho32, a.pos4, a.L32, a.Lm2l, a.nearv, np,
+                       a.perm, a.out, a.p, a.PS);
+            break;
+        }
+    }
+}
+
+// The persistent kernel: a CTA takes the next ticket, finds its stage (the
+// table is copied to shared memory once), waits for the stage's dependencies,
+// runs the unit, and counts it as complete (fence, then one atomic).  A CTA
+// whose wait gave up stops taking tickets (ST_TIMEOUT is set; the units that
+// depend on it give up the same way).
+template <int P>
+__global__ void __launch_bounds__(128, 4) k_eval_persistent(const PArgs a) {
+    __shared__ PStage sst[kMaxPStages];
+    __shared__ int s_stage, s_vb, s_go;
+    for (int i = threadIdx.x; i < a.nst; i += blockDim.x) sst[i] = a.st[i];
+    __syncthreads();
+    while (true) {
+        if (threadIdx.x == 0) {
+            const long long tk = (long long)atomicAdd(a.ctr, 1ull);
+            int go = 0, g = 0;
+            if (tk < a.total) {
+                while (g + 1 < a.nst && sst[g + 1].ticket0 <= tk) ++g;
+                go = pq_wait(a.ctr, sst[g].need_far, sst[g].need_p2p, a.status, a.spin_limit) ? 1 : 0;
+                __threadfence();
+            }
+            s_stage = g;
+            s_vb = go ? sst[g].vb0 + (int)(tk - sst[g].ticket0) : 0;
+            s_go = go;
+        }
+        __syncthreads();
+        const int go = s_go, g = s_stage, vb = s_vb;
+        if (!go) break;
+        pq_unit<P>(a, sst[g], vb);
+        __syncthreads();  // the unit's writes are done (and s_* may be overwritten)
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(a.ctr + (sst[g].type == PT_P2P ? 2 : 1), 1ull);
+        }
+    }
+}
 // ============================================================ dispatch
 
 Bufs bufs(Tree& t, int set) {
@@ -1727,6 +1990,197 @@ void launch_gather(Tree& t, const Bufs& B, const double* d_gamma, cudaStream_t s
 
 void launch_near(Tree& t, const Bufs& B, cudaStream_t s) { launch_p2p<false>(t, B, s); }
 void launch_l2p_near(Tree& t, const Bufs& B, void* d_phi, cudaStream_t s) { dispatch_l2p(t, B, d_phi, s); }
+
+// ---- persistent evaluation: stage table and launch ---------------------------
+// The stage table follows the tree shape, the expansion order and the launch
+// grids of the work items (the kernel reads the exact item counts on the
+// device); it is rebuilt on the host for every evaluation and uploaded only
+// when it changed (outside any stream capture: prepare_persistent runs before
+// the evaluation is launched or captured).
+static std::vector<PStage> persistent_stages(const Tree& t) {
+    std::vector<PStage> far;
+    auto add = [&](std::vector<PStage>& v, int type, long long nvb, const int32_t* ids, int cnt, int arg) {
+        if (nvb <= 0) return;
+        PStage g{};
+        g.type = type;
+        g.nvb = (int)nvb;
+        g.ids = ids;
+        g.cnt = cnt;
+        g.arg = arg;
+        v.push_back(g);
+    };
+    auto vb = [](long long threads) { return (threads + 127) / 128; };
+    add(far, PT_GATHER, vb(t.n), nullptr, 0, 0);
+    add(far, PT_P2M_T, vb(t.nleaf), t.leaves.d_ids, (int)t.nleaf, 0);
+    for (int l = t.Lmax - 2; l >= 0; --l) {
+        const LevelList& L = t.level_parents[l];
+        if (!L.count) continue;
+        const int how = p2m_parent_mode(t, l);
+        if (how == 1) add(far, PT_P2M_T, vb(L.count), L.d_ids, L.count, 1);
+        else if (how == 2) add(far, PT_P2M_W, vb(32LL * L.count), L.d_ids, L.count, 1);
+    }
+    const size_t n_p2m = far.size();  // stages that need the strengths only
+    for (int l = t.Lmax - 2; l >= 0; --l) {
+        const LevelList& L = t.level_parents[l];
+        if (!L.count || p2m_parent_mode(t, l) != 0) continue;
+        if (4LL * L.count <= kWarpShiftMax) add(far, PT_M2M_W, L.count, L.d_ids, L.count, 0);
+        else add(far, PT_M2M_T, vb(4LL * L.count), L.d_ids, L.count, 0);
+    }
+    add(far, PT_M2L, vb(m2l_grid_items(t)), nullptr, 0, 0);
+    add(far, PT_REDUCE, vb(32LL * t.nbox), nullptr, 0, 0);
+    const bool fold = fold_leaf_l2l(t);
+    const int lend = fold ? t.Lmax - 2 : t.Lmax - 1;
+    for (int l = 0; l + 1 <= lend; ++l) {
+        const LevelList& L = t.level_boxes[l + 1];
+        if (!L.count) continue;
+        const int all32 = fold && l + 1 == lend;
+        if (L.count <= kWarpShiftMax) add(far, PT_L2L_W, vb(32LL * L.count), L.d_ids, L.count, all32);
+        else add(far, PT_L2L_T, vb(L.count), L.d_ids, L.count, all32);
+    }
+    // dependencies: P2M stages wait for the gather, every later far-field stage for all far units before it
+    long long before = 0;
+    const long long gather_units = far[0].nvb;
+    for (size_t i = 0; i < far.size(); ++i) {
+        far[i].need_far = (i == 0) ? 0 : (i < n_p2m ? gather_units : before);
+        far[i].need_p2p = 0;
+        before += far[i].nvb;
+    }
+    // P2P (4 items per unit, one per warp) in chunks after every far-field stage from the leaves' P2M on
+    const long long np2p = (p2p_grid_items(t) + 3) / 4;
+    const int slots = std::max<int>(1, (int)far.size() - 1);
+    std::vector<PStage> st;
+    long long done_p2p = 0;
+    for (size_t i = 0; i < far.size(); ++i) {
+        st.push_back(far[i]);
+        if (i == 0) continue;
+        const long long upto = np2p * (long long)i / slots;
+        if (upto > done_p2p) {
+            PStage g{};
+            g.type = PT_P2P;
+            g.nvb = (int)(upto - done_p2p);
+            g.vb0 = (int)done_p2p;
+            g.need_far = gather_units;
+            st.push_back(g);
+            done_p2p = upto;
+        }
+    }
+    PStage l2p{};
+    l2p.type = PT_L2P;
+    l2p.nvb = (int)((t.n + 127) / 128);
+    l2p.need_far = before;
+    l2p.need_p2p = np2p;
+    st.push_back(l2p);
+    long long tk = 0;
+    for (auto& g : st) {
+        g.ticket0 = tk;
+        tk += g.nvb;
+    }
+    return st;
+}
+
+fmm_status prepare_persistent(Tree& t) {
+    if (t.path != FMM_PATH_FP32) {
+        set_error("FMM_FLAG_PERSISTENT: the persistent evaluation runs the FP32 path only");
+        return FMM_ERR_INVALID_ARG;
+    }
+    const std::vector<PStage> st = persistent_stages(t);
+    if ((int)st.size() > kMaxPStages) {
+        set_error("FMM_FLAG_PERSISTENT: too many stages for the work queue");
+        return FMM_ERR_INVALID_ARG;
+    }
+    const size_t bytes = st.size() * sizeof(PStage);
+    if (t.d_pstage && t.h_pstage.size() == bytes && memcmp(t.h_pstage.data(), st.data(), bytes) == 0) return FMM_OK;
+    if (!t.d_pstage) {
+        FMM_CUDA(cudaMalloc(&t.d_pstage, kMaxPStages * sizeof(PStage)));
+        FMM_CUDA(cudaMalloc((void**)&t.d_pers, 4 * sizeof(unsigned long long)));
+    }
+    FMM_CUDA(cudaMemcpy(t.d_pstage, st.data(), bytes, cudaMemcpyHostToDevice));
+    t.h_pstage.assign(reinterpret_cast<const char*>(st.data()), reinterpret_cast<const char*>(st.data()) + bytes);
+    t.npstage = (int)st.size();
+    t.pstage_total = st.back().ticket0 + st.back().nvb;
+    return FMM_OK;
+}
+
+template <int P>
+static fmm_status launch_persistent(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s) {
+    static int occ = 0;
+    if (!occ) {
+        FMM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_eval_persistent<P>, 128, 0));
+        occ = std::max(occ, 1);
+    }
+    const Bufs B = bufs(t, 0);
+    const P2PLayout pl = p2p_pair_layout(t.max_leaf);
+    PArgs a{};
+    a.st = static_cast<const PStage*>(t.d_pstage);
+    a.nst = t.npstage;
+    a.total = t.pstage_total;
+    a.ctr = t.d_pers;
+    a.status = t.d_status;
+    a.spin_limit = 1 << 24;  // x 256 ns sleeps: seconds, far beyond any stage
+    a.n = (int)t.n;
+    a.nbox = (int)t.nbox;
+    a.p = t.p;
+    a.PS = t.PS;
+    a.lay = pl.tpl * 100 + pl.lt;
+    a.pad = (int)(t.nleaf * t.leaf_cap);
+    a.TS = t.max_leaf;
+    a.gin = reinterpret_cast<const double2*>(d_gamma);
+    a.perm = t.d_perm;
+    a.slot_of = t.d_slot_of;
+    a.bstart = t.d_bstart;
+    a.bcount = t.d_bcount;
+    a.child0 = t.d_child0;
+    a.parent = t.d_parent;
+    a.leaf_of = t.d_leaf_of;
+    a.fold_par = t.d_fold_par;
+    a.pslot = t.d_pslot;
+    a.soff = t.d_soff;
+    a.woff = t.d_woff;
+    a.widx = t.d_widx;
+    a.m2l_rows = t.d_m2l_rows;
+    a.chl = t.d_chl;
+    a.pos4 = t.d_pos4;
+    a.rho32 = t.d_rho32;
+    a.rho = t.d_rho;
+    a.center = t.d_center;
+    a.box_m2l = t.d_box_m2l;
+    a.srng = t.d_srng;
+    a.leaf_items = t.d_leaf_items;
+    a.m2l_items = t.d_m2l_items;
+    a.p2p_items = t.d_p2p_items;
+    a.n_m2l = item_count(t, 3);
+    a.n_p2p = item_count(t, 2);
+    a.posq = static_cast<const ulonglong2*>(t.d_posp);
+    a.gam = static_cast<float2*>(B.gam);
+    a.gamp = static_cast<float*>(t.d_gamp);
+    a.M32 = B.M32;
+    a.M64 = B.M64;
+    a.Lm2l = static_cast<float2*>(B.Lm2l);
+    a.m2l_part = static_cast<float2*>(B.m2l_part);
+    a.L64 = B.L64;
+    a.L32 = B.L32;
+    a.nearv = static_cast<float2*>(B.near);
+    a.p2p_part = static_cast<float2*>(B.p2p_part);
+    a.out = static_cast<float2*>(d_phi);
+    FMM_CUDA(cudaMemsetAsync(t.d_pers, 0, 4 * sizeof(unsigned long long), s));
+    const long long grid = std::min<long long>((long long)occ * t.num_sms, std::max<long long>(t.pstage_total, 1));
+    k_eval_persistent<P><<<(int)grid, 128, 0, s>>>(a);
+    FMM_CUDA(cudaGetLastError());
+    return FMM_OK;
+}
+
+fmm_status run_eval_persistent(Tree& t, const double* d_gamma, void* d_phi, cudaStream_t s) {
+    t.p2p_funcs.clear();
+    t.timing_valid = false;
+    switch (t.P) {
+#define FMM_CASE(Q) \
+    case Q: return launch_persistent<Q>(t, d_gamma, d_phi, s);
+        FMM_FOR_ORDERS(FMM_CASE)
+#undef FMM_CASE
+    }
+    set_error("unsupported expansion order");
+    return FMM_ERR_INVALID_ARG;
+}
 
 // One evaluation: gather strengths into sorted order, then fork P2P onto the
 // auxiliary stream while the far field (P2M, M2M, M2L, L2L) runs on the

@@ -1,6 +1,6 @@
 """Failure detection without a GPU fault: the library's bounded device waits,
 run on something that never happens (a predecessor tile that never publishes,
-an mbarrier nothing arrives at), give up after their limit and report
+an mbarrier nothing arrives at, a work-queue unit that never completes), give up after their limit and report
 FMM_ERR_TIMEOUT through the device status word; the context stays usable."""
 import time
 
@@ -20,11 +20,12 @@ def test_bounded_waits_time_out_and_the_context_survives(orc):
 
     lib = _lib.load()
     torch.cuda.synchronize()
-    for which in (0, 1):  # 0: decoupled look-back, 1: tensor-core M2L mbarrier
+    # 0: decoupled look-back, 1: tensor-core M2L mbarrier, 2: persistent evaluation's work-queue wait
+    for which in (0, 1, 2):
         t0 = time.time()
         assert lib.fmm_selftest_bounded_wait(which, None) == FMM_ERR_TIMEOUT
         assert time.time() - t0 < 10.0
-    assert lib.fmm_selftest_bounded_wait(2, None) == FMM_ERR_INVALID_ARG
+    assert lib.fmm_selftest_bounded_wait(3, None) == FMM_ERR_INVALID_ARG
     # the context still works: a normal build and evaluation against the oracle
     g = np.random.default_rng(17)
     xy, gam = W.cluster_mix(3000, g), W.complex_strengths(3000, g)

@@ -223,7 +223,7 @@ static void release(Tree* t) {
                     t->d_m2l_items, t->d_m2l_rows, t->d_box_tail, t->d_m2l_rowctr, t->d_leaf_items, t->d_box_m2l, t->d_status, t->d_gam, t->d_near, t->d_M64,
                     t->d_pslot, t->d_posp, t->d_slot_of, t->d_gamp, t->d_xy_all, t->d_gam_all, t->d_phi_all,
                     t->d_M32, t->d_Lm2l, t->d_L64, t->d_L32, t->d_p2p_part, t->d_m2l_part, t->d_pstage,
-                    t->d_pers};
+                    t->d_pers, t->d_gamp2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < 4; ++i) {

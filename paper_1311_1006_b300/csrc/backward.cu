@@ -26,10 +26,13 @@ constexpr int kBWarps = 8;
 constexpr int kBChunk32 = 128;
 constexpr int kBChunk64 = 96;
 
-// sorted strengths of both sets: set 0 = Gamma, set 1 = c = conj(gphi)
+// sorted strengths of both sets: set 0 = Gamma, set 1 = c = conj(gphi); on the
+// FP32 path also both sets in the leaf slot layout of the packed P2P (slot
+// pairs interleaved as (re[2m], re[2m+1], im[2m], im[2m+1]))
 template <typename C>
 __global__ void k_gather_bwd(const double2* __restrict__ gam, const double2* __restrict__ gphi,
-                             const int32_t* __restrict__ perm, int n, C* s0, C* s1) {
+                             const int32_t* __restrict__ perm, const int32_t* __restrict__ slot_of, int n, C* s0,
+                             C* s1, float* p0, float* p1) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int j = perm[i];
@@ -38,6 +41,171 @@ __global__ void k_gather_bwd(const double2* __restrict__ gam, const double2* __r
     s0[i].y = a.y;
     s1[i].x = g.x;
     s1[i].y = -g.y;
+    if (p0 != nullptr) {
+        const int slot = slot_of[i];
+        float* f0 = p0 + 4 * (slot >> 1) + (slot & 1);
+        float* f1 = p1 + 4 * (slot >> 1) + (slot & 1);
+        f0[0] = (float)a.x;
+        f0[2] = (float)a.y;
+        f1[0] = (float)g.x;
+        f1[2] = (float)-g.y;
+    }
+}
+
+// ---- FP32 adjoint near field with packed f32x2 arithmetic --------------------
+// The forward P2P's work items, slot layout and lane layout (k_p2p_pairs): a
+// lane takes a pair of source slots per step and one target, every instruction
+// a 2-wide FP32 operation; per pair three sums with u = 1/(z_t - z_s):
+//     Psi += c_s u,   Psi' += -c_s u^2,   Phi' += -Gamma_s u^2,
+// from the hi/lo coordinates (close pairs keep full FP32 relative accuracy).
+// Coincident pairs give d = 0 and add 0 (|d|^2 carries a 1e-37 guard); padding
+// slots have zero strengths.
+struct BwdSrcPair {
+    f2x x, y, xl, yl, cr, ci, ncr, nci, gr, ngr, ngi;
+};
+__device__ __forceinline__ BwdSrcPair bwd_src_pair(const ulonglong2 a, const ulonglong2 b, const ulonglong2 g,
+                                                   const ulonglong2 c) {
+    const f2x m1 = f2pk(-1.f, -1.f);
+    BwdSrcPair s;
+    s.x = a.x;
+    s.y = a.y;
+    s.xl = b.x;
+    s.yl = b.y;
+    s.cr = c.x;
+    s.ci = c.y;
+    s.ncr = f2mul(c.x, m1);
+    s.nci = f2mul(c.y, m1);
+    s.gr = g.x;
+    s.ngr = f2mul(g.x, m1);
+    s.ngi = f2mul(g.y, m1);
+    return s;
+}
+struct BwdAcc {
+    f2x pr, pi, qr, qi, fr, fi;  // Psi, Psi', Phi' (re, im); each holds the even- and odd-slot sums
+};
+__device__ __forceinline__ void bwd_pair(const f2x tx, const f2x ty, const f2x txl, const f2x tyl,
+                                         const BwdSrcPair& s, BwdAcc& A) {
+    const f2x dx = f2add(f2sub(tx, s.x), f2sub(txl, s.xl));
+    const f2x dy = f2add(f2sub(ty, s.y), f2sub(tyl, s.yl));
+    const f2x r2 = f2fma(dx, dx, f2fma(dy, dy, f2pk(1e-37f, 1e-37f)));
+    float r0, r1;
+    f2upk(r2, r0, r1);
+    const f2x inv = f2pk(rcp_approx(r0), rcp_approx(r1));
+    const f2x a = f2mul(dx, inv), b = f2mul(dy, inv);  // u = 1/d = a - i b
+    const f2x ur = f2fma(a, a, f2mul(f2mul(b, b), f2pk(-1.f, -1.f)));  // u^2 = ur - i w
+    const f2x b2 = f2add(b, b);
+    const f2x w = f2mul(a, b2);                      // w = 2ab
+    A.pr = f2fma(s.cr, a, f2fma(s.ci, b, A.pr));     // Re(c u)     = cr a + ci b
+    A.pi = f2fma(s.ci, a, f2fma(s.ncr, b, A.pi));    // Im(c u)     = ci a - cr b
+    A.qr = f2fma(s.ncr, ur, f2fma(s.nci, w, A.qr));  // Re(-c u^2)  = -cr ur - ci w
+    A.qi = f2fma(s.nci, ur, f2fma(s.cr, w, A.qi));   // Im(-c u^2)  = -ci ur + cr w
+    A.fr = f2fma(s.ngr, ur, f2fma(s.ngi, w, A.fr));  // Re(-g u^2)
+    A.fi = f2fma(s.ngi, ur, f2fma(s.gr, w, A.fi));   // Im(-g u^2)
+}
+
+// One warp per P2P work item (the forward's items); lane (tg, ss) owns targets
+// tg, tg + LT, ... (TPL of them) and slot-pair slice ss of S = 32/LT.  With
+// LT = 4 a range (one strong entry) is one step of 2S = 16 slots; the other
+// layouts take ceil(count/2S) steps per range.
+constexpr int kBPWarps = 4;
+
+template <int TPL, int LT>
+__global__ void __launch_bounds__(kBPWarps * 32, 4)
+    k_p2p_bwd_pairs(const int4* __restrict__ items, const unsigned long long* __restrict__ nitems,
+                    const int32_t* __restrict__ bstart, const int32_t* __restrict__ bcount,
+                    const int32_t* __restrict__ pslot, const int32_t* __restrict__ soff,
+                    const int2* __restrict__ srng, const ulonglong2* __restrict__ posq,
+                    const ulonglong2* __restrict__ gamq, const ulonglong2* __restrict__ cstq,
+                    float2* __restrict__ nearv, float2* __restrict__ part, int n, long long part_stride, int TS) {
+    constexpr int S = 32 / LT;
+    constexpr bool LONG = LT > 4;
+    const int lane = threadIdx.x & 31;
+    const int tg = lane % LT, ss = lane / LT;
+    const int nit = (int)*nitems;
+    const int it = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (it >= nit) return;  // warp-uniform
+    const int4 item = items[it];
+    const int b = item.x;
+    const int ts = bstart[b], tn = bcount[b], tb = pslot[b];
+    const int2* rl = srng + soff[b];
+    for (int t0 = 0; t0 < tn; t0 += TPL * LT) {
+        f2x tx[TPL], ty[TPL], txl[TPL], tyl[TPL];
+        BwdAcc A[TPL];
+#pragma unroll
+        for (int u = 0; u < TPL; ++u) {
+            const int idx = t0 + tg + u * LT;
+            float x = 0.f, y = 0.f, xl = 0.f, yl = 0.f;
+            if (idx < tn) {
+                const int sl = tb + idx;
+                const float* f = reinterpret_cast<const float*>(posq) + 8 * (sl >> 1) + (sl & 1);
+                x = f[0];
+                y = f[2];
+                xl = f[4];
+                yl = f[6];
+            }
+            tx[u] = f2pk(x, x);
+            ty[u] = f2pk(y, y);
+            txl[u] = f2pk(xl, xl);
+            tyl[u] = f2pk(yl, yl);
+            A[u] = BwdAcc{0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+        }
+        if constexpr (!LONG) {
+            // one step per range; the next range's sources are loaded while this one is computed
+            int k = item.y;
+            int q = ((k < item.z ? rl[k].x : 0) >> 1) + ss;
+            ulonglong2 pa = posq[2 * q], pb = posq[2 * q + 1], ga = gamq[q], ca = cstq[q];
+            for (; k < item.z; ++k) {
+                const BwdSrcPair sp = bwd_src_pair(pa, pb, ga, ca);
+                if (k + 1 < item.z) {
+                    q = (rl[k + 1].x >> 1) + ss;
+                    pa = posq[2 * q];
+                    pb = posq[2 * q + 1];
+                    ga = gamq[q];
+                    ca = cstq[q];
+                }
+#pragma unroll
+                for (int u = 0; u < TPL; ++u) bwd_pair(tx[u], ty[u], txl[u], tyl[u], sp, A[u]);
+            }
+        } else {
+            for (int k = item.y; k < item.z; ++k) {
+                const int2 r = rl[k];
+                const int o = (r.x >> 1) + ss;  // slot-pair index of this slice
+                const int steps = (r.y + 2 * S - 1) / (2 * S);
+                for (int e = 0; e < steps; ++e) {
+                    const int q = o + e * S;
+                    const BwdSrcPair sp = bwd_src_pair(posq[2 * q], posq[2 * q + 1], gamq[q], cstq[q]);
+#pragma unroll
+                    for (int u = 0; u < TPL; ++u) bwd_pair(tx[u], ty[u], txl[u], tyl[u], sp, A[u]);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < TPL; ++u) {
+            float v[6];
+            const f2x acc[6] = {A[u].pr, A[u].pi, A[u].qr, A[u].qi, A[u].fr, A[u].fi};
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                float lo, hi;
+                f2upk(acc[c], lo, hi);
+                v[c] = lo + hi;
+#pragma unroll
+                for (int off = LT; off < 32; off <<= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], off);
+            }
+            const int idx = t0 + tg + u * LT;
+            if (ss == 0 && idx < tn) {
+                if (item.w < 0) {
+                    nearv[ts + idx] = make_float2(v[0], v[1]);
+                    nearv[(size_t)n + ts + idx] = make_float2(v[2], v[3]);
+                    nearv[2 * (size_t)n + ts + idx] = make_float2(v[4], v[5]);
+                } else {
+                    const size_t qq = (size_t)it * TS + idx;
+                    part[qq] = make_float2(v[0], v[1]);
+                    part[part_stride + qq] = make_float2(v[2], v[3]);
+                    part[2 * part_stride + qq] = make_float2(v[4], v[5]);
+                }
+            }
+        }
+    }
 }
 
 // ----------------------------------------------------------- near field
@@ -359,12 +527,25 @@ fmm_status run_backward(Tree& t, const double* d_gamma, const double* d_gphi, do
     const double2* gin = reinterpret_cast<const double2*>(d_gamma);
     const double2* pin = reinterpret_cast<const double2*>(d_gphi);
     const bool f32 = t.path == FMM_PATH_FP32;
-    if (f32)
-        k_gather_bwd<float2><<<nblk(n, 256), 256, 0, s>>>(gin, pin, t.d_perm, n, static_cast<float2*>(B0.gam),
-                                                          static_cast<float2*>(B1.gam));
-    else
-        k_gather_bwd<double2><<<nblk(n, 256), 256, 0, s>>>(gin, pin, t.d_perm, n, static_cast<double2*>(B0.gam),
-                                                           static_cast<double2*>(B1.gam));
+    if (f32) {
+        // the second strength set in the slot layout (padding slots stay zero)
+        if (t.gamp2_slots != t.slot_alloc) {
+            if (t.d_gamp2) cudaFree(t.d_gamp2);
+            t.d_gamp2 = nullptr;
+            t.gamp2_slots = 0;
+            FMM_CUDA(cudaMalloc(&t.d_gamp2, (size_t)std::max<int64_t>(t.slot_alloc, 1) * sizeof(float2)));
+            FMM_CUDA(cudaMemsetAsync(t.d_gamp2, 0, (size_t)std::max<int64_t>(t.slot_alloc, 1) * sizeof(float2), s));
+            t.gamp2_slots = t.slot_alloc;
+        }
+        k_gather_bwd<float2><<<nblk(n, 256), 256, 0, s>>>(gin, pin, t.d_perm, t.d_slot_of, n,
+                                                          static_cast<float2*>(B0.gam), static_cast<float2*>(B1.gam),
+                                                          static_cast<float*>(t.d_gamp),
+                                                          static_cast<float*>(t.d_gamp2));
+    } else {
+        k_gather_bwd<double2><<<nblk(n, 256), 256, 0, s>>>(gin, pin, t.d_perm, t.d_slot_of, n,
+                                                           static_cast<double2*>(B0.gam),
+                                                           static_cast<double2*>(B1.gam), nullptr, nullptr);
+    }
     FMM_CUDA(cudaEventRecord(t.ev_fork, s));
     FMM_CUDA(cudaStreamWaitEvent(t.s_aux, t.ev_fork, 0));
     FMM_CUDA(cudaStreamWaitEvent(t.s_far2, t.ev_fork, 0));
@@ -373,18 +554,27 @@ fmm_status run_backward(Tree& t, const double* d_gamma, const double* d_gphi, do
     const unsigned long long* cnt = reinterpret_cast<const unsigned long long*>(t.d_status) + 3;
     const bool wide = (double)t.n / std::max<int64_t>(t.nleaf, 1) >= 8.0;
     if (f32) {
-        auto* g = static_cast<const float2*>(B0.gam);
-        auto* c = static_cast<const float2*>(B1.gam);
+        // packed f32x2 over the forward's slot layout, half the forward's targets per lane (three sums each)
         auto* nv = static_cast<float2*>(t.d_near);
         auto* pt = static_cast<float2*>(t.d_p2p_part);
-        if (wide)
-            k_p2p_bwd<float4, float2, 4, kBChunk32><<<grid, kBWarps * 32, 0, t.s_aux>>>(
-                t.d_p2p_items, cnt, t.d_bstart, t.d_bcount, t.d_soff, t.d_sidx, t.d_pos4, g, c, nv, pt, n, stride,
-                t.max_leaf);
-        else
-            k_p2p_bwd<float4, float2, 1, kBChunk32><<<grid, kBWarps * 32, 0, t.s_aux>>>(
-                t.d_p2p_items, cnt, t.d_bstart, t.d_bcount, t.d_soff, t.d_sidx, t.d_pos4, g, c, nv, pt, n, stride,
-                t.max_leaf);
+        const int pgrid = nblk(p2p_grid_items(t), kBPWarps);
+        const P2PLayout pl = p2p_pair_layout(t.max_leaf);
+        const auto* pq = static_cast<const ulonglong2*>(t.d_posp);
+        const auto* gq = static_cast<const ulonglong2*>(t.d_gamp);
+        const auto* cq = static_cast<const ulonglong2*>(t.d_gamp2);
+#define FMM_BWD_PAIRS(TPL, LT)                                                                                   \
+    k_p2p_bwd_pairs<TPL, LT><<<pgrid, kBPWarps * 32, 0, t.s_aux>>>(t.d_p2p_items, cnt, t.d_bstart, t.d_bcount,  \
+                                                                    t.d_pslot, t.d_soff, t.d_srng, pq, gq, cq, nv, \
+                                                                    pt, n, stride, t.max_leaf);
+        switch (pl.tpl * 100 + pl.lt) {
+            case 204: FMM_BWD_PAIRS(1, 4) break;
+            case 404: FMM_BWD_PAIRS(2, 4) break;
+            case 408: FMM_BWD_PAIRS(2, 8) break;
+            case 416: FMM_BWD_PAIRS(2, 16) break;
+            default: FMM_BWD_PAIRS(4, 16) break;
+        }
+#undef FMM_BWD_PAIRS
+        (void)wide;
     } else {
         auto* g = static_cast<const double2*>(B0.gam);
         auto* c = static_cast<const double2*>(B1.gam);

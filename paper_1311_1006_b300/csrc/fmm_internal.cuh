@@ -202,6 +202,8 @@ struct Tree {
     void* d_gam = nullptr;     // sorted strengths (float2 or double2), 2 sets for backward
     void* d_gamp = nullptr;    // strengths in the leaf slot layout (forward set)
     int64_t eval_slots = 0;
+    void* d_gamp2 = nullptr;   // adjoint, FP32 path: the second strength set c in the slot layout
+    int64_t gamp2_slots = 0;
     void* d_near = nullptr;    // P2P output(s), sorted order
     void* d_p2p_part = nullptr;  // partial P2P sums of split leaves (item x max_leaf)
     void* d_m2l_part = nullptr;  // partial M2L sums of split boxes (item x PS)

@@ -339,8 +339,12 @@ typedef enum {
     FMM_EXPORT_WEAK_OFF = 15,   /* int32[nbox] */
     FMM_EXPORT_M2L_ITEMS = 16,  /* int32[4*m2l_items]: M2L work items (box, list begin, list end, first item of
                                    the box or -1), a box's items consecutive */
-    FMM_EXPORT_M2L_ROWS = 17    /* int32[m2l_items]: the order in which the M2L kernels take the items (row ->
+    FMM_EXPORT_M2L_ROWS = 17,   /* int32[m2l_items]: the order in which the M2L kernels take the items (row ->
                                    item): full items first, then each box's shorter last item by decreasing length */
+    FMM_EXPORT_P2P_ITEMS = 18,  /* int32[4*p2p_items]: P2P work items (leaf, strong-list begin, end, first item of
+                                   the leaf or -1), a leaf's items consecutive */
+    FMM_EXPORT_P2P_ROWS = 19    /* int32[p2p_items]: the order in which the P2P kernels take the items (ticket ->
+                                   item): the full items of split leaves first, then every leaf's last or only item */
 } fmm_export_what;
 
 fmm_status fmm_tree_export(const fmm_tree* t, int what, void* h_dst, int64_t count, void* stream);

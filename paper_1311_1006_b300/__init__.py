@@ -258,6 +258,7 @@ class Tree:
             "mpole": (np.float64, 2 * nb * p), "local": (np.float64, 2 * nb * p),
             "near": (np.float64, 2 * n), "inst": (np.int64, 3 * inf["ninst"]),
             "m2l_items": (np.int32, max(4 * inf["m2l_items"], 1)), "m2l_rows": (np.int32, max(inf["m2l_items"], 1)),
+            "p2p_items": (np.int32, max(4 * inf["p2p_items"], 1)), "p2p_rows": (np.int32, max(inf["p2p_items"], 1)),
         }[what]
         buf = np.zeros(spec[1], dtype=spec[0])
         _lib.check(_lib.load().fmm_tree_export(self._h, _lib.EXPORT[what], ctypes.c_void_p(buf.ctypes.data),
@@ -274,6 +275,10 @@ class Tree:
             return buf[: 4 * inf["m2l_items"]].reshape(-1, 4)
         if what == "m2l_rows":
             return buf[: inf["m2l_items"]]
+        if what == "p2p_items":
+            return buf[: 4 * inf["p2p_items"]].reshape(-1, 4)
+        if what == "p2p_rows":
+            return buf[: inf["p2p_items"]]
         return buf
 
     def lists(self):

@@ -28,7 +28,8 @@ FMM_FLAG_PERSISTENT = 16
 FMM_P_MAX = 32
 
 EXPORT = dict(perm=0, bstart=1, bcount=2, center=3, radius=4, nstrong=5, strong=6, nweak=7, weak=8,
-              mpole=9, local=10, near=11, inst=12, rho=13, soff=14, woff=15, m2l_items=16, m2l_rows=17)
+              mpole=9, local=10, near=11, inst=12, rho=13, soff=14, woff=15, m2l_items=16, m2l_rows=17,
+              p2p_items=18, p2p_rows=19)
 
 
 class FMMParams(ctypes.Structure):

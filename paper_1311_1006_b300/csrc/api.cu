@@ -220,7 +220,7 @@ static void release(Tree* t) {
                     t->d_leaf_of, t->d_pts, t->d_pos4, t->d_center, t->d_radius, t->d_rho, t->d_chl, t->d_rho32,
                     t->d_rad32, t->d_soff, t->d_ns, t->d_sidx, t->d_srng, t->d_sowner, t->d_ltstat,
                     t->d_lvl_base, t->d_woff, t->d_nw, t->d_widx, t->d_p2p_items,
-                    t->d_m2l_items, t->d_m2l_rows, t->d_box_tail, t->d_m2l_rowctr, t->d_leaf_items, t->d_box_m2l, t->d_status, t->d_gam, t->d_near, t->d_M64,
+                    t->d_m2l_items, t->d_m2l_rows, t->d_p2p_rows, t->d_box_tail, t->d_m2l_rowctr, t->d_leaf_items, t->d_box_m2l, t->d_status, t->d_gam, t->d_near, t->d_M64,
                     t->d_pslot, t->d_posp, t->d_slot_of, t->d_gamp, t->d_xy_all, t->d_gam_all, t->d_phi_all,
                     t->d_M32, t->d_Lm2l, t->d_L64, t->d_L32, t->d_p2p_part, t->d_m2l_part, t->d_pstage,
                     t->d_pers, t->d_gamp2};
@@ -825,6 +825,21 @@ fmm_status fmm_tree_export(const fmm_tree* h, int what, void* h_dst, int64_t cou
         case FMM_EXPORT_WEAK: return copy(t.d_widx, (int64_t)t.h_counts[1], 4);
         case FMM_EXPORT_M2L_ITEMS: return copy(t.d_m2l_items, 4 * (int64_t)t.h_counts[3], 4);
         case FMM_EXPORT_M2L_ROWS: return copy(t.d_m2l_rows, (int64_t)t.h_counts[3], 4);
+        case FMM_EXPORT_P2P_ITEMS: return copy(t.d_p2p_items, 4 * (int64_t)t.h_counts[2], 4);
+        case FMM_EXPORT_P2P_ROWS: {
+            const int64_t m = (int64_t)t.h_counts[2];
+            if (count < m) return invalid("host buffer too small");
+            std::vector<int32_t> rows((size_t)std::max<long long>(t.p2p_cap, 1));
+            unsigned long long nh = 0;
+            FMM_CUDA(cudaMemcpyAsync(rows.data(), t.d_p2p_rows, (size_t)t.p2p_cap * 4, cudaMemcpyDeviceToHost, s));
+            FMM_CUDA(cudaMemcpyAsync(&nh, t.d_m2l_rowctr + kM2LItemPairsMax + 1, sizeof(nh), cudaMemcpyDeviceToHost,
+                                     s));
+            FMM_CUDA(cudaStreamSynchronize(s));
+            int32_t* o = static_cast<int32_t*>(h_dst);
+            for (int64_t k = 0; k < m; ++k)
+                o[k] = (unsigned long long)k < nh ? rows[(size_t)k] : rows[(size_t)(t.p2p_cap - 1 - (k - (int64_t)nh))];
+            return FMM_OK;
+        }
         case FMM_EXPORT_INST: {
             if (count < 3 * (int64_t)t.ninst) return invalid("host buffer too small");
             int64_t* o = static_cast<int64_t*>(h_dst);

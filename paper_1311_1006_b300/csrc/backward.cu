@@ -116,14 +116,16 @@ __global__ void __launch_bounds__(kBPWarps * 32, 4)
                     const int32_t* __restrict__ pslot, const int32_t* __restrict__ soff,
                     const int2* __restrict__ srng, const ulonglong2* __restrict__ posq,
                     const ulonglong2* __restrict__ gamq, const ulonglong2* __restrict__ cstq,
-                    float2* __restrict__ nearv, float2* __restrict__ part, int n, long long part_stride, int TS) {
+                    float2* __restrict__ nearv, float2* __restrict__ part, int n, long long part_stride, int TS,
+                    const int32_t* __restrict__ rows, const unsigned long long* __restrict__ nheavy, long long cap) {
     constexpr int S = 32 / LT;
     constexpr bool LONG = LT > 4;
     const int lane = threadIdx.x & 31;
     const int tg = lane % LT, ss = lane / LT;
     const int nit = (int)*nitems;
-    const int it = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    if (it >= nit) return;  // warp-uniform
+    const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (row >= nit) return;  // warp-uniform
+    const int it = p2p_row_item(row, rows, *nheavy, cap);  // the forward's row order: long items first
     const int4 item = items[it];
     const int b = item.x;
     const int ts = bstart[b], tn = bcount[b], tb = pslot[b];
@@ -565,7 +567,8 @@ fmm_status run_backward(Tree& t, const double* d_gamma, const double* d_gphi, do
 #define FMM_BWD_PAIRS(TPL, LT)                                                                                   \
     k_p2p_bwd_pairs<TPL, LT><<<pgrid, kBPWarps * 32, 0, t.s_aux>>>(t.d_p2p_items, cnt, t.d_bstart, t.d_bcount,  \
                                                                     t.d_pslot, t.d_soff, t.d_srng, pq, gq, cq, nv, \
-                                                                    pt, n, stride, t.max_leaf);
+                                                                    pt, n, stride, t.max_leaf, t.d_p2p_rows,       \
+                                                                    t.d_m2l_rowctr + kM2LItemPairsMax + 1, t.p2p_cap);
         switch (pl.tpl * 100 + pl.lt) {
             case 204: FMM_BWD_PAIRS(1, 4) break;
             case 404: FMM_BWD_PAIRS(2, 4) break;

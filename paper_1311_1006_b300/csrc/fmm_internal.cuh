@@ -177,6 +177,9 @@ struct Tree {
     long long scap_tot = 0, wcap_tot = 0;
     // work items (see k_items)
     int4* d_p2p_items = nullptr;
+    // P2P row order (ticket -> item): the full items of split leaves first (rows from the front), then every
+    // leaf's last or only item (rows from the back of the capacity), so the long items do not make the tail
+    int32_t* d_p2p_rows = nullptr;
     int4* d_m2l_items = nullptr;
     int2* d_leaf_items = nullptr;  // per box: first P2P item, item count (leaves)
     int2* d_box_m2l = nullptr;     // per box: first M2L item, item count
@@ -425,6 +428,12 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 // Packed 2 x FP32 (f32x2) arithmetic: the low 32 bits hold the first value.
+// Work item of P2P ticket t in the row order (see Tree::d_p2p_rows): nheavy = rows taken from the front.
+__device__ __forceinline__ int p2p_row_item(int t, const int32_t* __restrict__ rows, unsigned long long nheavy,
+                                            long long cap) {
+    return (unsigned long long)t < nheavy ? rows[t] : rows[cap - 1 - ((long long)t - (long long)nheavy)];
+}
+
 typedef unsigned long long f2x;
 __device__ __forceinline__ f2x f2pk(float lo, float hi) {
     f2x r;

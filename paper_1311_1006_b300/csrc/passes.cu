@@ -999,17 +999,20 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, sizeof(C) == 8 ? 5 : 1)
                 const int32_t* __restrict__ bcount, const int32_t* __restrict__ pslot,
                 const int32_t* __restrict__ soff, const int2* __restrict__ srng, const V* __restrict__ posp,
                 const C* __restrict__ gamp, C* __restrict__ nearv, C* __restrict__ part, int TS, int pad,
-                int per_warp) {
+                int per_warp, const int32_t* __restrict__ rows, const unsigned long long* __restrict__ nheavy,
+                long long cap) {
     constexpr int S = 32 / LT;
     constexpr bool LONG = LT > 2;
     const int lane = threadIdx.x & 31;
     const int tg = lane % LT, ss = lane / LT;
     const int nit = (int)*nitems;
+    const unsigned long long nh = *nheavy;
     for (int done = 0; done < per_warp; ++done) {
         int it = 0;
         if (lane == 0) it = (int)atomicAdd(next_item, 1u);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= nit) break;
+        it = p2p_row_item(it, rows, nh, cap);
         const int4 item = items[it];
         const int b = item.x;
         const int ts = bstart[b], tn = bcount[b], tb = pslot[b];
@@ -1300,14 +1303,17 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, TPL > 4 ? 2 : 7)
                 const int32_t* __restrict__ bcount, const int32_t* __restrict__ pslot,
                 const int32_t* __restrict__ soff, const int2* __restrict__ srng, const ulonglong2* __restrict__ posq,
                 const ulonglong2* __restrict__ gamq, float2* __restrict__ nearv, float2* __restrict__ part, int TS,
-                int pad, int per_warp) {
+                int pad, int per_warp, const int32_t* __restrict__ rows, const unsigned long long* __restrict__ nheavy,
+                long long cap) {
     const int lane = threadIdx.x & 31;
     const int nit = (int)*nitems;
+    const unsigned long long nh = *nheavy;
     for (int done = 0; done < per_warp; ++done) {
         int it = 0;
         if (lane == 0) it = (int)atomicAdd(next_item, 1u);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= nit) break;
+        it = p2p_row_item(it, rows, nh, cap);
         d_p2p_pairs_item<TPL, LT, LOG>(it, items, bstart, bcount, pslot, soff, srng, posq, gamq, nearv, part, TS,
                                        pad);
     }
@@ -1399,7 +1405,9 @@ struct PArgs {
     const double2* center;
     const int2 *box_m2l, *srng, *leaf_items;
     const int4 *m2l_items, *p2p_items;
-    const unsigned long long *n_m2l, *n_p2p;
+    const unsigned long long *n_m2l, *n_p2p, *p2p_nheavy;
+    const int32_t* p2p_rows;
+    long long p2p_cap;
     const ulonglong2* posq;
     float2* gam;
     float* gamp;
@@ -1479,8 +1487,9 @@ __device__ __forceinline__ void pq_unit(const PArgs& a, const PStage& g, int vb)
                                          a.L64, a.L32, g.arg, a.p, a.PS);
             break;
         case PT_P2P: {
-            const int it = vb * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);  // one item per warp
+            int it = vb * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);  // one item per warp, in row order
             if (it < (int)*a.n_p2p) {
+                it = p2p_row_item(it, a.p2p_rows, *a.p2p_nheavy, a.p2p_cap);
                 switch (a.lay) {
                     case 204: pq_p2p<2, 4>(a, it); break;
                     case 404: pq_p2p<4, 4>(a, it); break;
@@ -1761,11 +1770,13 @@ static void launch_p2p(Tree& t, const Bufs& B, cudaStream_t s) {
     }
     const P2PLayout lay = p2p_layout(t.max_leaf);
     const int pad = (int)(t.nleaf * t.leaf_cap);
+    const unsigned long long* nheavy = t.d_m2l_rowctr + kM2LItemPairsMax + 1;
 #define FMM_P2P(V, C, TPL, LT)                                                                                   \
     t.p2p_funcs.push_back(reinterpret_cast<const void*>(k_p2p_slots<V, C, TPL, LT, LOG>));                      \
     k_p2p_slots<V, C, TPL, LT, LOG><<<dgrid, kP2PDWarps * 32, 0, s>>>(                                            \
         t.d_p2p_items, cnt, next, t.d_bstart, t.d_bcount, t.d_pslot, t.d_soff, t.d_srng,                          \
-        static_cast<const V*>(t.d_posp), static_cast<const C*>(t.d_gamp), nv, pt, t.max_leaf, pad, per_warp);
+        static_cast<const V*>(t.d_posp), static_cast<const C*>(t.d_gamp), nv, pt, t.max_leaf, pad, per_warp,      \
+        t.d_p2p_rows, nheavy, t.p2p_cap);
 #define FMM_P2P_LAYOUTS(V, C)                                  \
     switch (lay.tpl * 100 + lay.lt) {                          \
         case 202: FMM_P2P(V, C, 2, 2) break;                   \
@@ -1784,7 +1795,7 @@ static void launch_p2p(Tree& t, const Bufs& B, cudaStream_t s) {
     k_p2p_pairs<TPL, LT, LOG><<<dgrid, kP2PDWarps * 32, 0, s>>>(                                                  \
         t.d_p2p_items, cnt, next, t.d_bstart, t.d_bcount, t.d_pslot, t.d_soff, t.d_srng,                          \
         static_cast<const ulonglong2*>(t.d_posp), static_cast<const ulonglong2*>(t.d_gamp), nv, pt, t.max_leaf,   \
-        pad, per_warp);
+        pad, per_warp, t.d_p2p_rows, nheavy, t.p2p_cap);
         switch (pl.tpl * 100 + pl.lt) {
             case 204: FMM_P2P_PAIRS(2, 4) break;
             case 404: FMM_P2P_PAIRS(4, 4) break;
@@ -2150,6 +2161,9 @@ static fmm_status launch_persistent(Tree& t, const double* d_gamma, void* d_phi,
     a.p2p_items = t.d_p2p_items;
     a.n_m2l = item_count(t, 3);
     a.n_p2p = item_count(t, 2);
+    a.p2p_nheavy = t.d_m2l_rowctr + kM2LItemPairsMax + 1;
+    a.p2p_rows = t.d_p2p_rows;
+    a.p2p_cap = t.p2p_cap;
     a.posq = static_cast<const ulonglong2*>(t.d_posp);
     a.gam = static_cast<float2*>(B.gam);
     a.gamp = static_cast<float*>(t.d_gamp);

@@ -1401,7 +1401,8 @@ __device__ __forceinline__ void warp_reserve3(unsigned long long* c0, int k0, un
 __global__ void k_items(int nbox, const int32_t* __restrict__ child0, const int32_t* __restrict__ bcount,
                         const int32_t* __restrict__ soff, const int32_t* __restrict__ ns,
                         const int32_t* __restrict__ woff, const int32_t* __restrict__ nw, unsigned long long* ctr,
-                        int4* p2p_items, int2* leaf_items, long long p2p_cap, int4* m2l_items, int2* box_m2l,
+                        int4* p2p_items, int32_t* p2p_rows, int2* leaf_items, long long p2p_cap, int4* m2l_items,
+                        int2* box_m2l,
                         long long m2l_cap, int K, unsigned long long* rowctr, int32_t* rows, int2* box_tail,
                         unsigned* status) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1418,15 +1419,22 @@ __global__ void k_items(int nbox, const int32_t* __restrict__ child0, const int3
     const int km = (m + K - 1) / K;
     const int nfull = m / K, r = m - nfull * K;
     const int rank = r > 0 ? (int)atomicAdd(rowctr + r, 1ull) : 0;  // issued first: its latency overlaps the rest
-    unsigned long long bp, bm, bf;
+    unsigned long long bp, bm, bf, bh, bl, bz;
     warp_reserve3(ctr + 2, kp, ctr + 3, km, rowctr + kM2LItemPairsMax, nfull, bp, bm, bf);
+    // P2P row order: the full items of split leaves (the heavy ones) take rows from the front, every leaf's
+    // last (or only) item takes a row from the back of the capacity
+    const int kh = kp > 1 ? kp - 1 : 0, kl = kp > 0 ? 1 : 0;
+    warp_reserve3(rowctr + kM2LItemPairsMax + 1, kh, rowctr + kM2LItemPairsMax + 2, kl,
+                  rowctr + kM2LItemPairsMax + 3, 0, bh, bl, bz);
     if (leaf) {
         leaf_items[b] = make_int2((int)bp, kp);
-        if ((long long)(bp + kp) > p2p_cap) {
+        if ((long long)(bp + kp) > p2p_cap || (long long)(bh + kh + bl + kl) > p2p_cap) {
             atomicOr(status, ST_ITEM_OVERFLOW);
         } else {
             for (int c = 0; c < kp; ++c)
                 p2p_items[bp + c] = make_int4(b, c * C, min(n, (c + 1) * C), kp > 1 ? (int)bp : -1);
+            for (int c = 0; c < kh; ++c) p2p_rows[bh + c] = (int32_t)(bp + c);
+            if (kl) p2p_rows[p2p_cap - 1 - (long long)bl] = (int32_t)(bp + kp - 1);
         }
     }
     if (!in) return;
@@ -1573,7 +1581,8 @@ fmm_status alloc_build(Tree& t) {
     if ((st = dalloc(&t.d_leaf_items, nb))) return st;
     if ((st = dalloc(&t.d_box_m2l, nb))) return st;
     if ((st = dalloc(&t.d_box_tail, nb))) return st;
-    if ((st = dalloc(&t.d_m2l_rowctr, kM2LItemPairsMax + 1))) return st;
+    // M2L row counters, then the P2P row counters (heavy, light, spare)
+    if ((st = dalloc(&t.d_m2l_rowctr, kM2LItemPairsMax + 4))) return st;
     if (!t.d_status) {
         if ((st = dalloc(reinterpret_cast<unsigned long long**>(&t.d_status), 8))) return st;
     }
@@ -1597,6 +1606,7 @@ fmm_status alloc_lists(Tree& t) {
     if ((st = dalloc(&t.d_ltstat, (2 * tiles + 1) * (size_t)std::max(t.Lmax - 1, 1)))) return st;  // one region per level
     if ((st = dalloc(&t.d_widx, (size_t)t.wcap_tot))) return st;
     if ((st = dalloc(&t.d_p2p_items, (size_t)t.p2p_cap))) return st;
+    if ((st = dalloc(&t.d_p2p_rows, (size_t)t.p2p_cap))) return st;
     if ((st = dalloc(&t.d_m2l_items, (size_t)t.m2l_cap))) return st;
     if ((st = dalloc(&t.d_m2l_rows, (size_t)t.m2l_cap))) return st;
     return FMM_OK;
@@ -1704,10 +1714,11 @@ fmm_status run_lists(Tree& t, cudaStream_t s) {
                                                  t.d_ltstat + lstride * (size_t)(l - 1), tiles_cap, t.scap_tot,
                                                  t.wcap_tot, need, t.d_status);
     }
-    FMM_CUDA(cudaMemsetAsync(t.d_m2l_rowctr, 0, (kM2LItemPairsMax + 1) * sizeof(unsigned long long), s));
+    FMM_CUDA(cudaMemsetAsync(t.d_m2l_rowctr, 0, (kM2LItemPairsMax + 4) * sizeof(unsigned long long), s));
     k_items<<<nblk(t.nbox, 128), 128, 0, s>>>((int)t.nbox, t.d_child0, t.d_bcount, t.d_soff, t.d_ns, t.d_woff,
                                               t.d_nw, ctr,
-                                              t.d_p2p_items, t.d_leaf_items, t.p2p_cap, t.d_m2l_items, t.d_box_m2l,
+                                              t.d_p2p_items, t.d_p2p_rows, t.d_leaf_items, t.p2p_cap,
+                                              t.d_m2l_items, t.d_box_m2l,
                                               t.m2l_cap, m2l_item_pairs(t), t.d_m2l_rowctr, t.d_m2l_rows,
                                               t.d_box_tail, t.d_status);
     k_m2l_rows<<<nblk(t.nbox, 256), 256, 0, s>>>((int)t.nbox, t.d_box_m2l, t.d_box_tail, t.d_m2l_rowctr, t.m2l_cap,

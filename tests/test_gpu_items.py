@@ -62,3 +62,43 @@ def test_m2l_items_and_row_order(path, K, batched):
         if fi.size > 1:
             assert np.all(np.diff(pos[fi]) == 1)
     assert full.size == nfull
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_p2p_items_and_row_order(batched):
+    """P2P items: each leaf's strong list cut into consecutive pieces (a leaf's
+    items consecutive, each holding the leaf's first item when it has several).
+    Rows: a permutation of the items with the full items of split leaves first
+    and every leaf's last (or only) item after them."""
+    from paper_1311_1006_b300 import Tree
+
+    g = np.random.default_rng(22)
+    n = 300_000
+    xy = W.cluster_mix(n, g)
+    X = torch.tensor(xy, device="cuda")
+    if batched:
+        offs = np.array([0, 5000, 150000, 151000, n])
+        t = Tree.build_batched(X, offs, p=17, path="fp32")
+    else:
+        t = Tree.build(X, p=17, nlevels=9, path="fp32")
+    ns = t.export("nstrong")
+    items, rows = t.export("p2p_items"), t.export("p2p_rows")
+    t.close()
+    m = items.shape[0]
+    assert np.array_equal(np.sort(rows), np.arange(m))
+    # every leaf's strong list is covered once, in consecutive pieces
+    order = np.argsort(items[:, 0], kind="stable")
+    leaves, first_idx, counts = np.unique(items[order, 0], return_index=True, return_counts=True)
+    assert np.all(ns[leaves] > 0)
+    last = np.zeros(m, bool)
+    for b, f, c in zip(leaves, first_idx, counts):
+        idx = np.sort(order[f:f + c])
+        assert np.all(np.diff(idx) == 1)
+        assert items[idx[0], 1] == 0 and items[idx[-1], 2] == ns[b]
+        assert np.all(items[idx[1:], 1] == items[idx[:-1], 2])
+        assert np.all(items[idx, 3] == (idx[0] if c > 1 else -1))
+        last[idx[-1]] = True
+    nheavy = int(np.sum(~last))
+    assert np.all(~last[rows[:nheavy]]) and np.all(last[rows[nheavy:]])
+    if not batched:
+        assert nheavy > 0  # the clustered set has leaves whose strong lists are split

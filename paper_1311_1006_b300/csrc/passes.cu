@@ -87,11 +87,16 @@ __constant__ FactTable c_fact = make_fact();
 // Strengths into sorted order and into the leaf slot layout of the P2P pass
 // (FP32: slot pairs interleaved as (re[2m], re[2m+1], im[2m], im[2m+1])).
 __device__ __forceinline__ void d_gather32(const int vbx, const double2* __restrict__ in, const int32_t* __restrict__ perm,
-                           const int32_t* __restrict__ slot_of, int n, float2* out, float* outp) {
+                           const int32_t* __restrict__ slot_of, int n, float2* out, float* outp, unsigned* cplx) {
     int i = vbx * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double2 g = in[perm[i]];
     const float2 v = make_float2((float)g.x, (float)g.y);
+    // record complex strengths (one atomic per warp that sees one, until the word is set)
+    const unsigned m = __activemask();
+    if (cplx != nullptr && __any_sync(m, v.y != 0.f) && (threadIdx.x & 31) == __ffs(m) - 1 &&
+        *reinterpret_cast<volatile unsigned*>(cplx) == 0u)
+        atomicOr(cplx, 1u);
     out[i] = v;
     const int slot = slot_of[i];
     float* f = outp + 4 * (slot >> 1) + (slot & 1);
@@ -99,7 +104,7 @@ __device__ __forceinline__ void d_gather32(const int vbx, const double2* __restr
     f[2] = v.y;
 }
 __global__ void k_gather32(const double2* __restrict__ in, const int32_t* __restrict__ perm,
-                           const int32_t* __restrict__ slot_of, int n, float2* out, float* outp) { d_gather32(blockIdx.x, in, perm, slot_of, n, out, outp); }
+                           const int32_t* __restrict__ slot_of, int n, float2* out, float* outp, unsigned* cplx) { d_gather32(blockIdx.x, in, perm, slot_of, n, out, outp, cplx); }
 __global__ void k_gather64(const double2* __restrict__ in, const int32_t* __restrict__ perm,
                            const int32_t* __restrict__ slot_of, int n, double2* out, double2* outp) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1162,10 +1167,26 @@ __device__ __forceinline__ void p2p_pair_log(const f2x tx, const f2x ty, const f
     ax = f2fma(s.gx, lg, ax);
     ay = f2fma(s.gy, lg, ay);
 }
-template <bool LOG>
+// Real strengths (every imaginary part zero): Gamma_j conj(d)/|d|^2 = s (dx, -dy)
+// with s = Gamma_j/|d|^2, accumulated as (sum s dx, sum s dy); the sign of the
+// second sum is applied to the finished sums.  11 FP32 lane slots per pair
+// instead of 14.
+__device__ __forceinline__ void p2p_pair_real(const f2x tx, const f2x ty, const f2x txl, const f2x tyl,
+                                              const SrcPair& s, f2x& ax, f2x& ay) {
+    const f2x dx = f2add(f2sub(tx, s.x), f2sub(txl, s.xl));
+    const f2x dy = f2add(f2sub(ty, s.y), f2sub(tyl, s.yl));
+    const f2x r2 = f2fma(dx, dx, f2fma(dy, dy, f2pk(1e-37f, 1e-37f)));
+    float r0, r1;
+    f2upk(r2, r0, r1);
+    const f2x sc = f2mul(s.gx, f2pk(rcp_approx(r0), rcp_approx(r1)));
+    ax = f2fma(sc, dx, ax);
+    ay = f2fma(sc, dy, ay);
+}
+template <bool LOG, bool REAL = false>
 __device__ __forceinline__ void p2p_pair_t(const f2x tx, const f2x ty, const f2x txl, const f2x tyl,
                                            const SrcPair& s, f2x& ax, f2x& ay) {
     if constexpr (LOG) p2p_pair_log(tx, ty, txl, tyl, s, ax, ay);
+    else if constexpr (REAL) p2p_pair_real(tx, ty, txl, tyl, s, ax, ay);
     else p2p_pair(tx, ty, txl, tyl, s, ax, ay);
 }
 constexpr float kHalfLn2 = 0.34657359027997264f;  // ln(2)/2: log2(|d|^2) -> ln|d|
@@ -1173,7 +1194,7 @@ constexpr float kHalfLn2 = 0.34657359027997264f;  // ln(2)/2: log2(|d|^2) -> ln|
 // Blocks per SM: 7 for TPL <= 4 (72 registers, no spills; measured against 4 (124
 // registers), 5, 6 (80) and 8 (64, spills): 7 is the fastest), 2 for TPL = 8.
 // One work item of the warp (its target leaf against a run of its strong list).
-template <int TPL, int LT, bool LOG>
+template <int TPL, int LT, bool LOG, bool REAL = false>
 __device__ __forceinline__ void d_p2p_pairs_item(const int it, const int4* __restrict__ items,
                                                  const int32_t* __restrict__ bstart,
                                                  const int32_t* __restrict__ bcount, const int32_t* __restrict__ pslot,
@@ -1227,9 +1248,9 @@ __device__ __forceinline__ void d_p2p_pairs_item(const int it, const int4* __res
                 {
                     const SrcPair s0 = src_pair(pa0, qa0, ga0), s1 = src_pair(pa1, qa1, ga1);
 #pragma unroll
-                    for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
+                    for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG, REAL>(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
 #pragma unroll
-                    for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s1, ax[u], ay[u]);
+                    for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG, REAL>(tx[u], ty[u], txl[u], tyl[u], s1, ax[u], ay[u]);
                 }
                 if (k + 2 >= ke) break;
                 pa0 = posq[2 * oa0];
@@ -1243,9 +1264,9 @@ __device__ __forceinline__ void d_p2p_pairs_item(const int it, const int4* __res
                 {
                     const SrcPair s0 = src_pair(pb0, qb0, gb0), s1 = src_pair(pb1, qb1, gb1);
 #pragma unroll
-                    for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
+                    for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG, REAL>(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
 #pragma unroll
-                    for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s1, ax[u], ay[u]);
+                    for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG, REAL>(tx[u], ty[u], txl[u], tyl[u], s1, ax[u], ay[u]);
                 }
                 k += 4;
                 if (k >= ke) break;
@@ -1261,14 +1282,14 @@ __device__ __forceinline__ void d_p2p_pairs_item(const int it, const int4* __res
                     const SrcPair s1 =
                         src_pair(posq[2 * (o + e + S)], posq[2 * (o + e + S) + 1], gamq[o + e + S]);
 #pragma unroll
-                    for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
+                    for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG, REAL>(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
 #pragma unroll
-                    for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s1, ax[u], ay[u]);
+                    for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG, REAL>(tx[u], ty[u], txl[u], tyl[u], s1, ax[u], ay[u]);
                 }
                 if (2 * e < r.y) {
                     const SrcPair s0 = src_pair(posq[2 * (o + e)], posq[2 * (o + e) + 1], gamq[o + e]);
 #pragma unroll
-                    for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG>(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
+                    for (int u = 0; u < TPL; ++u) p2p_pair_t<LOG, REAL>(tx[u], ty[u], txl[u], tyl[u], s0, ax[u], ay[u]);
                 }
             }
         }
@@ -1287,6 +1308,7 @@ __device__ __forceinline__ void d_p2p_pairs_item(const int it, const int4* __res
                 tot.x *= kHalfLn2;
                 tot.y *= kHalfLn2;
             }
+            if constexpr (REAL) tot.y = -tot.y;
             const int idx = t0 + tg + u * LT;
             if (ss == 0 && idx < tn) {
                 if (item.w < 0) nearv[ts + idx] = tot;
@@ -1304,18 +1326,23 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, TPL > 4 ? 2 : 7)
                 const int32_t* __restrict__ soff, const int2* __restrict__ srng, const ulonglong2* __restrict__ posq,
                 const ulonglong2* __restrict__ gamq, float2* __restrict__ nearv, float2* __restrict__ part, int TS,
                 int pad, int per_warp, const int32_t* __restrict__ rows, const unsigned long long* __restrict__ nheavy,
-                long long cap) {
+                long long cap, const unsigned* __restrict__ cplx) {
     const int lane = threadIdx.x & 31;
     const int nit = (int)*nitems;
     const unsigned long long nh = *nheavy;
+    const bool real = !LOG && *cplx == 0u;  // the gather saw no nonzero imaginary part
     for (int done = 0; done < per_warp; ++done) {
         int it = 0;
         if (lane == 0) it = (int)atomicAdd(next_item, 1u);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= nit) break;
         it = p2p_row_item(it, rows, nh, cap);
-        d_p2p_pairs_item<TPL, LT, LOG>(it, items, bstart, bcount, pslot, soff, srng, posq, gamq, nearv, part, TS,
-                                       pad);
+        if (real)
+            d_p2p_pairs_item<TPL, LT, LOG, !LOG>(it, items, bstart, bcount, pslot, soff, srng, posq, gamq, nearv,
+                                                 part, TS, pad);
+        else
+            d_p2p_pairs_item<TPL, LT, LOG>(it, items, bstart, bcount, pslot, soff, srng, posq, gamq, nearv, part, TS,
+                                           pad);
     }
 }
 
@@ -1455,7 +1482,7 @@ template <int P>
 __device__ __forceinline__ void pq_unit(const PArgs& a, const PStage& g, int vb) {
     switch (g.type) {
         case PT_GATHER:
-            d_gather32(vb, a.gin, a.perm, a.slot_of, a.n, a.gam, a.gamp);
+            d_gather32(vb, a.gin, a.perm, a.slot_of, a.n, a.gam, a.gamp, nullptr);
             break;
         case PT_P2M_T:
             d_p2m32<P>(vb, g.ids, g.cnt, a.bstart, a.bcount, a.chl, a.rho32, a.pos4, a.gam, a.M32,
@@ -1795,7 +1822,7 @@ static void launch_p2p(Tree& t, const Bufs& B, cudaStream_t s) {
     k_p2p_pairs<TPL, LT, LOG><<<dgrid, kP2PDWarps * 32, 0, s>>>(                                                  \
         t.d_p2p_items, cnt, next, t.d_bstart, t.d_bcount, t.d_pslot, t.d_soff, t.d_srng,                          \
         static_cast<const ulonglong2*>(t.d_posp), static_cast<const ulonglong2*>(t.d_gamp), nv, pt, t.max_leaf,   \
-        pad, per_warp, t.d_p2p_rows, nheavy, t.p2p_cap);
+        pad, per_warp, t.d_p2p_rows, nheavy, t.p2p_cap, t.d_status + 1);
         switch (pl.tpl * 100 + pl.lt) {
             case 204: FMM_P2P_PAIRS(2, 4) break;
             case 404: FMM_P2P_PAIRS(4, 4) break;
@@ -1991,9 +2018,13 @@ fmm_status alloc_eval(Tree& t, int sets) {
 void launch_gather(Tree& t, const Bufs& B, const double* d_gamma, cudaStream_t s) {
     const int n = (int)t.n;
     const double2* gin = reinterpret_cast<const double2*>(d_gamma);
-    if (t.path == FMM_PATH_FP32)
+    if (t.path == FMM_PATH_FP32) {
+        // word 1 of the status area: set by the gather when a strength has a nonzero imaginary part
+        // (the FP32 P2P then takes the complex form, else the real one)
+        cudaMemsetAsync(t.d_status + 1, 0, sizeof(unsigned), s);
         k_gather32<<<nblk(n, 256), 256, 0, s>>>(gin, t.d_perm, t.d_slot_of, n, static_cast<float2*>(B.gam),
-                                                static_cast<float*>(t.d_gamp));
+                                                static_cast<float*>(t.d_gamp), t.d_status + 1);
+    }
     else
         k_gather64<<<nblk(n, 256), 256, 0, s>>>(gin, t.d_perm, t.d_slot_of, n, static_cast<double2*>(B.gam),
                                                 static_cast<double2*>(t.d_gamp));

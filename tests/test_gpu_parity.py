@@ -147,6 +147,27 @@ def test_eval_matches_oracle(orc, kind, n, L, p, theta, path, tol):
     assert ferr < tol * (10 if path == "fp32" else 1), (err, ferr)
 
 
+@pytest.mark.parametrize("kind,n,L", [("uniform", 10_000, 5), ("cluster", 16000, 6), ("dup", 2000, 4),
+                                      ("far", 6000, 5), ("uniform", 777, 1)])
+@pytest.mark.parametrize("one_complex", [False, True])
+def test_fp32_real_strengths(orc, kind, n, L, one_complex):
+    """Real strengths take the FP32 P2P's real form (the gather finds no
+    nonzero imaginary part); one complex strength among them switches the whole
+    evaluation back to the complex form.  Both within 1e-5 of the oracle, the
+    near field alone too."""
+    g = np.random.default_rng(n + 7)
+    xy = _points(kind, n, seed=n + 1)
+    gam = W.real_strengths(n, g)
+    if one_complex:
+        gam[n // 3] += 0.5j
+    t = _tree(xy, L, p=17, path="fp32")
+    phi = t.eval(_dev(gam)).cpu().numpy().astype(np.complex128)
+    near = t.export("near")[np.argsort(t.export("perm"))]
+    ref = orc.fmm(xy, gam, L, 0.5, 17, parts=True)
+    assert _rel(phi, ref["phi"]) < 1e-5
+    assert _rel(near, ref["near"]) < 1e-5
+
+
 def test_eval_single_point_is_zero():
     from paper_1311_1006_b300 import Tree
 

@@ -378,6 +378,40 @@ def leg_c5(F, orc, dev, stream, flush):
             "error": "rel. max-norm vs the direct-sum gradient on 128 sampled points"}
 
 
+def leg_targets(F, orc, dev, stream, flush):
+    """Separate evaluation points (eq 2.2), M = N: the headline's 1e6 sources
+    (cluster mixture, complex strengths) and 1e6 evaluation points uniform in
+    the unit square; p = 17, theta = 0.5, FP32 path, N_levels from the seed for
+    the 2e6 points.  One step = rebuild over both sets + evaluation at the
+    evaluation points."""
+    import torch
+    from paper_1311_1006_b300 import workloads as W
+
+    src, gam = _inputs()
+    tgt = W.uniform(N_POINTS, np.random.default_rng(W.BASE_SEED + 77))
+    S, T, G = (torch.tensor(a, device=dev) for a in (src, tgt, gam))
+    t = F.Tree.build_targets(S, T, p=P_TERMS, theta=THETA, path="fp32")
+    out = torch.empty(N_POINTS, dtype=torch.complex64, device=dev)
+    t.eval_targets(G, out=out)
+
+    def _step():
+        t.rebuild_targets(S, T)
+        t.eval_targets(G, out=out)
+
+    _timed_ms(_step, 3, stream, flush)
+    ms = float(np.median(_timed_ms(_step, 7, stream, flush)))
+    ev = float(np.median(_timed_ms(lambda: t.eval_targets(G, out=out), 7, stream, flush)))
+    pick = np.random.default_rng(61).choice(N_POINTS, 256, replace=False)
+    err = _rel(out.cpu().numpy().astype(np.complex128)[pick], orc.direct_points(src, gam, tgt[pick]))
+    info = t.info()
+    t.close()
+    return {"workload": "targets_1e6_sources_1e6_uniform_points_p17", "n_sources": N_POINTS,
+            "n_targets": N_POINTS, "nlevels": info["nlevels_max"], "ms_per_step": round(ms, 4),
+            "value": _mps(N_POINTS, ms), "unit": "M evaluation points/s", "eval_ms": round(ev, 4),
+            "rel_err_sampled": err,
+            "error": "rel. max-norm vs the exact sum over the sources at 256 sampled evaluation points"}
+
+
 def run_gpu(args):
     import torch
 
@@ -681,7 +715,8 @@ def run_gpu(args):
         legs = {}
         if rank == 0:
             tree.close()
-            for name, fn in (("c1", leg_c1), ("c3", leg_c3), ("c4", leg_c4), ("c5", leg_c5)):
+            for name, fn in (("c1", leg_c1), ("c3", leg_c3), ("c4", leg_c4), ("c5", leg_c5),
+                             ("targets", leg_targets)):
                 if name in args.skip_legs:
                     continue
                 torch.cuda.empty_cache()
@@ -841,7 +876,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nlevels", type=int, default=0, help="fix N_levels (skip the calibration and autotuner)")
     ap.add_argument("--no-theta-tune", action="store_true", help="skip the theta autotuning run")
-    ap.add_argument("--skip-legs", default="", help="comma-separated legs to skip (c1,c3,c4,c5)")
+    ap.add_argument("--skip-legs", default="", help="comma-separated legs to skip (c1,c3,c4,c5,targets)")
     ap.add_argument("--only-step", action="store_true",
                     help="time the step only (no phase split, FP64 path, adjoint, e2e, accuracy); for profiling")
     ap.add_argument("--log-kernel", action="store_true",

@@ -223,7 +223,7 @@ static void release(Tree* t) {
                     t->d_m2l_items, t->d_m2l_rows, t->d_p2p_rows, t->d_box_tail, t->d_m2l_rowctr, t->d_leaf_items, t->d_box_m2l, t->d_status, t->d_gam, t->d_near, t->d_M64,
                     t->d_pslot, t->d_posp, t->d_slot_of, t->d_gamp, t->d_xy_all, t->d_gam_all, t->d_phi_all,
                     t->d_M32, t->d_Lm2l, t->d_L64, t->d_L32, t->d_p2p_part, t->d_m2l_part, t->d_pstage,
-                    t->d_pers, t->d_gamp2};
+                    t->d_pers, t->d_gamp2, t->d_nsrc};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < 4; ++i) {
@@ -339,7 +339,8 @@ fmm_status fmm_cost_model_calibrate(fmm_tree* h, double* alpha_out, double* beta
 }
 
 static fmm_status build_common(const double* d_xy, const std::vector<int64_t>& offs, const fmm_params* prm,
-                               const int* h_nlevels, bool batched, void* stream, fmm_tree** out) {
+                               const int* h_nlevels, bool batched, void* stream, fmm_tree** out,
+                               int64_t n_src = 0) {
     if (!out) return invalid("out is NULL");
     *out = nullptr;
     fmm_status st = check_params(prm);
@@ -358,6 +359,8 @@ static fmm_status build_common(const double* d_xy, const std::vector<int64_t>& o
     apply_params(t, prm);
     t.batched = batched;
     t.n = offs[B];
+    t.n_src = n_src;  // separate evaluation points: the first n_src points are the sources
+    t.n_tgt = n_src > 0 ? offs[B] - n_src : 0;
     t.ninst = B;
     t.inst_pt_off = offs;
     t.inst_levels.resize(B);
@@ -432,7 +435,7 @@ fmm_status fmm_build_tree_targets(const double* d_src_xy, int64_t n_src, const d
         return cuda_fail(e, "cudaMemcpyAsync(points)");
     }
     std::vector<int64_t> offs = {0, n};
-    const fmm_status st = build_common(buf, offs, prm, nullptr, false, stream, out);
+    const fmm_status st = build_common(buf, offs, prm, nullptr, false, stream, out, n_src);
     if (st) {
         cudaFree(buf);
         return st;
@@ -726,6 +729,7 @@ fmm_status fmm_eval_backward(fmm_tree* h, const double* d_gamma, const double* d
     if (!h || !d_gamma || !d_gphi) return invalid("NULL argument");
     if (!d_ggamma && !d_gxy) return FMM_OK;
     Tree& t = h->t;
+    if (t.n_src > 0) return invalid("the adjoint is defined for trees without separate evaluation points");
     fmm_status st;
     if ((st = check_pending())) return st;
     if ((st = ensure_eval(t, 2))) return st;

@@ -159,6 +159,9 @@ struct Tree {
     void* d_posp = nullptr;        // slot layout, 16 B per slot: FP64 points, or on the FP32 path the
                                    // pair-interleaved hi/lo coordinates (see k_finalize)
     int32_t* d_slot_of = nullptr;  // sorted position -> slot
+    // separate evaluation points: per leaf the number of SOURCES; a leaf's slot block holds its sources first
+    // and its evaluation points after them, so P2P takes sources [0, nsrc) and targets [nsrc, count) of a block
+    int32_t* d_nsrc = nullptr;
     int64_t slot_alloc = 0;        // slots d_posp was allocated for
     double2* d_center = nullptr;   // per box
     double* d_radius = nullptr;    // per box (half bbox diagonal)

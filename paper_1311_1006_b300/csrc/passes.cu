@@ -760,12 +760,16 @@ struct NearParts {
     const int32_t* bstart;
     const C* part;           // partial sums, row stride TS
     int TS;
+    // separate evaluation points: P2P writes the near field by slot offset within the leaf (slot_of[i] -
+    // pslot[leaf]) at the leaf's sorted positions; nullptr when slots follow the sorted order
+    const int32_t* slot_of = nullptr;
+    const int32_t* pslot = nullptr;
 };
 template <typename C>
 __device__ __forceinline__ C near_of(int i, int lf, const C* __restrict__ nearv, const NearParts<C>& np) {
     const int2 li = np.leaf_items[lf];
-    if (li.y <= 1) return nearv[i];
-    const int t = i - np.bstart[lf];
+    const int t = np.slot_of != nullptr ? np.slot_of[i] - np.pslot[lf] : i - np.bstart[lf];
+    if (li.y <= 1) return nearv[np.bstart[lf] + t];
     C s{};
     for (int q = 0; q < li.y; ++q) {
         const C v = np.part[(size_t)(li.x + q) * np.TS + t];
@@ -1005,7 +1009,7 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, sizeof(C) == 8 ? 5 : 1)
                 const int32_t* __restrict__ soff, const int2* __restrict__ srng, const V* __restrict__ posp,
                 const C* __restrict__ gamp, C* __restrict__ nearv, C* __restrict__ part, int TS, int pad,
                 int per_warp, const int32_t* __restrict__ rows, const unsigned long long* __restrict__ nheavy,
-                long long cap) {
+                long long cap, const int32_t* __restrict__ tfirst) {
     constexpr int S = 32 / LT;
     constexpr bool LONG = LT > 2;
     const int lane = threadIdx.x & 31;
@@ -1023,7 +1027,7 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, sizeof(C) == 8 ? 5 : 1)
         const int ts = bstart[b], tn = bcount[b], tb = pslot[b];
         const int2* rl = srng + soff[b];
         const int ke = item.z;
-        for (int t0 = 0; t0 < tn; t0 += TPL * LT) {
+        for (int t0 = tfirst != nullptr ? tfirst[b] : 0; t0 < tn; t0 += TPL * LT) {
             V xt[TPL];
             C acc[TPL];
 #pragma unroll
@@ -1201,7 +1205,8 @@ __device__ __forceinline__ void d_p2p_pairs_item(const int it, const int4* __res
                                                  const int32_t* __restrict__ soff, const int2* __restrict__ srng,
                                                  const ulonglong2* __restrict__ posq,
                                                  const ulonglong2* __restrict__ gamq, float2* __restrict__ nearv,
-                                                 float2* __restrict__ part, int TS, int pad) {
+                                                 float2* __restrict__ part, int TS, int pad,
+                                                 const int32_t* __restrict__ tfirst) {
     constexpr int S = 32 / LT;      // pair slices
     constexpr bool LONG = LT > 4;   // the LT = 4 layouts hold leaves of at most 16 = 2S slots
     const int lane = threadIdx.x & 31;
@@ -1211,7 +1216,8 @@ __device__ __forceinline__ void d_p2p_pairs_item(const int it, const int4* __res
     const int ts = bstart[b], tn = bcount[b], tb = pslot[b];
     const int2* rl = srng + soff[b];
     const int ke = item.z;
-    for (int t0 = 0; t0 < tn; t0 += TPL * LT) {
+    // targets: the leaf's slots [t_first, tn) (with separate evaluation points its evaluation points)
+    for (int t0 = tfirst != nullptr ? tfirst[b] : 0; t0 < tn; t0 += TPL * LT) {
         f2x tx[TPL], ty[TPL], txl[TPL], tyl[TPL], ax[TPL], ay[TPL];
 #pragma unroll
         for (int u = 0; u < TPL; ++u) {
@@ -1326,7 +1332,7 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, TPL > 4 ? 2 : 7)
                 const int32_t* __restrict__ soff, const int2* __restrict__ srng, const ulonglong2* __restrict__ posq,
                 const ulonglong2* __restrict__ gamq, float2* __restrict__ nearv, float2* __restrict__ part, int TS,
                 int pad, int per_warp, const int32_t* __restrict__ rows, const unsigned long long* __restrict__ nheavy,
-                long long cap, const unsigned* __restrict__ cplx) {
+                long long cap, const unsigned* __restrict__ cplx, const int32_t* __restrict__ tfirst) {
     const int lane = threadIdx.x & 31;
     const int nit = (int)*nitems;
     const unsigned long long nh = *nheavy;
@@ -1339,10 +1345,10 @@ __global__ void __launch_bounds__(kP2PDWarps * 32, TPL > 4 ? 2 : 7)
         it = p2p_row_item(it, rows, nh, cap);
         if (real)
             d_p2p_pairs_item<TPL, LT, LOG, !LOG>(it, items, bstart, bcount, pslot, soff, srng, posq, gamq, nearv,
-                                                 part, TS, pad);
+                                                 part, TS, pad, tfirst);
         else
             d_p2p_pairs_item<TPL, LT, LOG>(it, items, bstart, bcount, pslot, soff, srng, posq, gamq, nearv, part, TS,
-                                           pad);
+                                           pad, tfirst);
     }
 }
 
@@ -1435,6 +1441,8 @@ struct PArgs {
     const unsigned long long *n_m2l, *n_p2p, *p2p_nheavy;
     const int32_t* p2p_rows;
     long long p2p_cap;
+    const int32_t* tfirst;     // separate evaluation points: per leaf the first target slot (nullptr otherwise)
+    const int32_t* near_slot;  // separate evaluation points: slot of every sorted position (nullptr otherwise)
     const ulonglong2* posq;
     float2* gam;
     float* gamp;
@@ -1475,7 +1483,8 @@ void launch_selftest_queue(unsigned long long* ctr, int limit, unsigned* status,
 template <int TPL, int LT>
 __device__ __forceinline__ void pq_p2p(const PArgs& a, int it) {
     d_p2p_pairs_item<TPL, LT, false>(it, a.p2p_items, a.bstart, a.bcount, a.pslot, a.soff, a.srng, a.posq,
-                                     reinterpret_cast<const ulonglong2*>(a.gamp), a.nearv, a.p2p_part, a.TS, a.pad);
+                                     reinterpret_cast<const ulonglong2*>(a.gamp), a.nearv, a.p2p_part, a.TS, a.pad,
+                                     a.tfirst);
 }
 
 template <int P>
@@ -1528,7 +1537,7 @@ __device__ __forceinline__ void pq_unit(const PArgs& a, const PStage& g, int vb)
             break;
         }
         case PT_L2P: {
-            const NearParts<float2> np{a.leaf_items, a.bstart, a.p2p_part, a.TS};
+            const NearParts<float2> np{a.leaf_items, a.bstart, a.p2p_part, a.TS, a.near_slot, a.pslot};
             d_l2p32<P>(vb, a.n, a.leaf_of, a.fold_par, a.box_m2l, a.chl, a.rho32, a.pos4, a.L32, a.Lm2l, a.nearv, np,
                        a.perm, a.out, a.p, a.PS);
             break;
@@ -1724,7 +1733,8 @@ static void launch_down_fp64(Tree& t, const Bufs& B, cudaStream_t s) {
 
 template <typename C>
 static NearParts<C> near_parts(const Tree& t, const Bufs& B) {
-    return NearParts<C>{t.d_leaf_items, t.d_bstart, static_cast<const C*>(B.p2p_part), t.max_leaf};
+    return NearParts<C>{t.d_leaf_items, t.d_bstart, static_cast<const C*>(B.p2p_part), t.max_leaf,
+                        t.n_src > 0 ? t.d_slot_of : nullptr, t.n_src > 0 ? t.d_pslot : nullptr};
 }
 
 template <int P>
@@ -1798,12 +1808,13 @@ static void launch_p2p(Tree& t, const Bufs& B, cudaStream_t s) {
     const P2PLayout lay = p2p_layout(t.max_leaf);
     const int pad = (int)(t.nleaf * t.leaf_cap);
     const unsigned long long* nheavy = t.d_m2l_rowctr + kM2LItemPairsMax + 1;
+    const int32_t* tfirst = t.n_src > 0 ? t.d_nsrc : nullptr;  // separate evaluation points: targets only
 #define FMM_P2P(V, C, TPL, LT)                                                                                   \
     t.p2p_funcs.push_back(reinterpret_cast<const void*>(k_p2p_slots<V, C, TPL, LT, LOG>));                      \
     k_p2p_slots<V, C, TPL, LT, LOG><<<dgrid, kP2PDWarps * 32, 0, s>>>(                                            \
         t.d_p2p_items, cnt, next, t.d_bstart, t.d_bcount, t.d_pslot, t.d_soff, t.d_srng,                          \
         static_cast<const V*>(t.d_posp), static_cast<const C*>(t.d_gamp), nv, pt, t.max_leaf, pad, per_warp,      \
-        t.d_p2p_rows, nheavy, t.p2p_cap);
+        t.d_p2p_rows, nheavy, t.p2p_cap, tfirst);
 #define FMM_P2P_LAYOUTS(V, C)                                  \
     switch (lay.tpl * 100 + lay.lt) {                          \
         case 202: FMM_P2P(V, C, 2, 2) break;                   \
@@ -1822,7 +1833,7 @@ static void launch_p2p(Tree& t, const Bufs& B, cudaStream_t s) {
     k_p2p_pairs<TPL, LT, LOG><<<dgrid, kP2PDWarps * 32, 0, s>>>(                                                  \
         t.d_p2p_items, cnt, next, t.d_bstart, t.d_bcount, t.d_pslot, t.d_soff, t.d_srng,                          \
         static_cast<const ulonglong2*>(t.d_posp), static_cast<const ulonglong2*>(t.d_gamp), nv, pt, t.max_leaf,   \
-        pad, per_warp, t.d_p2p_rows, nheavy, t.p2p_cap, t.d_status + 1);
+        pad, per_warp, t.d_p2p_rows, nheavy, t.p2p_cap, t.d_status + 1, tfirst);
         switch (pl.tpl * 100 + pl.lt) {
             case 204: FMM_P2P_PAIRS(2, 4) break;
             case 404: FMM_P2P_PAIRS(4, 4) break;
@@ -2195,6 +2206,8 @@ static fmm_status launch_persistent(Tree& t, const double* d_gamma, void* d_phi,
     a.p2p_nheavy = t.d_m2l_rowctr + kM2LItemPairsMax + 1;
     a.p2p_rows = t.d_p2p_rows;
     a.p2p_cap = t.p2p_cap;
+    a.tfirst = t.n_src > 0 ? t.d_nsrc : nullptr;
+    a.near_slot = t.n_src > 0 ? t.d_slot_of : nullptr;
     a.posq = static_cast<const ulonglong2*>(t.d_posp);
     a.gam = static_cast<float2*>(B.gam);
     a.gamp = static_cast<float*>(t.d_gamp);

@@ -1087,6 +1087,38 @@ __global__ void __launch_bounds__(kSubThreads) k_subtree(
     for (int i = threadIdx.x; i < n; i += kSubThreads) Y[s + i] = X[s + yl[i]];
 }
 
+// Separate evaluation points (the tree holds n_src sources, then the evaluation
+// points): one warp per leaf places the leaf's sources first in its slot
+// block, in sorted order, and its evaluation points after them, and records
+// the leaf's source count.  Y = input index of every sorted position.
+__global__ void k_target_slots(const int32_t* __restrict__ leaves, int nleaf, const int32_t* __restrict__ bstart,
+                               const int32_t* __restrict__ bcount, const int32_t* __restrict__ pslot,
+                               const int32_t* __restrict__ Y, int n_src, int32_t* __restrict__ slot_of,
+                               int32_t* __restrict__ nsrc) {
+    const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= nleaf) return;  // warp-uniform
+    const int b = leaves[w];
+    const int s = bstart[b], c = bcount[b], ps = pslot[b];
+    int ns = 0;
+    for (int i0 = 0; i0 < c; i0 += 32) {
+        const bool src = i0 + lane < c && Y[s + i0 + lane] < n_src;
+        ns += __popc(__ballot_sync(0xffffffffu, src));
+    }
+    int before_s = 0, before_t = 0;
+    for (int i0 = 0; i0 < c; i0 += 32) {
+        const bool in = i0 + lane < c;
+        const bool src = in && Y[s + i0 + lane] < n_src;
+        const unsigned ms = __ballot_sync(0xffffffffu, src), mt = __ballot_sync(0xffffffffu, in && !src);
+        const unsigned below = (1u << lane) - 1u;
+        if (in)
+            slot_of[s + i0 + lane] = ps + (src ? before_s + __popc(ms & below) : ns + before_t + __popc(mt & below));
+        before_s += __popc(ms);
+        before_t += __popc(mt);
+    }
+    if (lane == 0) nsrc[b] = ns;
+}
+
 // Sorted point data: permutation, FP64 copy, FP32 hi/lo split relative to the
 // instance origin (root centre), and the leaf of every sorted position.
 // The P2P operands also go to the leaf slot layout: leaf q's points fill slots
@@ -1581,6 +1613,7 @@ fmm_status alloc_build(Tree& t) {
     if ((st = dalloc(&t.d_leaf_items, nb))) return st;
     if ((st = dalloc(&t.d_box_m2l, nb))) return st;
     if ((st = dalloc(&t.d_box_tail, nb))) return st;
+    if (t.n_src > 0 && (st = dalloc(&t.d_nsrc, nb))) return st;
     // M2L row counters, then the P2P row counters (heavy, light, spare)
     if ((st = dalloc(&t.d_m2l_rowctr, kM2LItemPairsMax + 4))) return st;
     if (!t.d_status) {
@@ -1686,6 +1719,9 @@ fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s) {
         FMM_CUDA(cudaGetLastError());
     }
     const bool f32 = t.path == FMM_PATH_FP32;
+    if (t.n_src > 0)
+        k_target_slots<<<nblk(32 * t.nleaf, 128), 128, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, t.d_bstart, t.d_bcount,
+                                                                t.d_pslot, Y, (int)t.n_src, t.d_slot_of, t.d_nsrc);
     k_finalize<<<nblk(n, 256), 256, 0, s>>>(Y, n, xy, t.d_inst, t.d_inst_boxoff, t.d_center, t.d_perm, t.d_pts,
                                             t.d_pos4, t.d_leaf_of, t.d_slot_of,
                                             f32 ? static_cast<float*>(t.d_posp) : nullptr,
@@ -1699,9 +1735,11 @@ fmm_status run_lists(Tree& t, cudaStream_t s) {
     unsigned long long* need = t.d_lvl_base + 2 * kMaxLevels;
     FMM_CUDA(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), s));
     FMM_CUDA(cudaMemsetAsync(need, 0, 4 * sizeof(unsigned long long), s));
+    // P2P sources of a leaf: its points, or with separate evaluation points its sources only
+    const int32_t* srccount = t.n_src > 0 ? t.d_nsrc : t.d_bcount;
     k_lists_root<<<nblk(t.ninst, 128), 128, 0, s>>>(t.d_inst_boxoff, t.ninst, t.d_soff, t.d_ns, t.d_sidx, t.d_sowner,
                                                     t.d_woff, t.d_nw, t.d_lvl_base, t.d_child0, t.d_pslot,
-                                                    t.d_bcount, t.d_srng);
+                                                    srccount, t.d_srng);
     const long long tiles_cap = t.cand_cap / kLTile + 2;
     const size_t lstride = (size_t)(2 * tiles_cap + 1);  // status words + ticket of one level
     const int grid = t.num_sms * 8;
@@ -1709,7 +1747,7 @@ fmm_status run_lists(Tree& t, cudaStream_t s) {
                              s));
     for (int l = 1; l < t.Lmax; ++l) {
         k_lists_level<<<grid, kLThreads, 0, s>>>(l, t.d_lvl_base, t.d_sowner, t.d_soff, t.d_ns, t.d_sidx, t.d_woff,
-                                                 t.d_nw, t.d_widx, t.d_child0, t.d_pslot, t.d_bcount, t.d_srng,
+                                                 t.d_nw, t.d_widx, t.d_child0, t.d_pslot, srccount, t.d_srng,
                                                  t.d_chl, t.d_rad32, t.d_center, t.d_radius, t.theta,
                                                  t.d_ltstat + lstride * (size_t)(l - 1), tiles_cap, t.scap_tot,
                                                  t.wcap_tot, need, t.d_status);

@@ -76,3 +76,34 @@ def test_targets_argument_checks():
         t.n_src, t.n_tgt = 500, 500
         t.eval_targets(_dev(np.ones(500, np.complex128)))  # not built with separate points
     t.close()
+
+
+@pytest.mark.parametrize("path", ["fp64", "fp32"])
+def test_targets_only_evaluated_against_sources_only(path):
+    """Leaves with only sources, only evaluation points, and both: P2P takes a
+    leaf's sources as sources and its evaluation points as targets (the slot
+    block holds the sources first); the result still equals the oracle FMM
+    over the same point set, and the exact sum within the FP32 tolerance."""
+    import oracle
+    from paper_1311_1006_b300 import Tree
+
+    g = np.random.default_rng(31)
+    ns, nt = 30000, 30000
+    src = W.cluster_mix(ns, g) * np.array([0.6, 1.0])       # sources in x < 0.6
+    tgt = np.concatenate([g.random((nt - 500, 2)), src[g.choice(ns, 500, replace=False)]])
+    gam = W.complex_strengths(ns, g)
+    L, p = 7, 17
+    t = Tree.build_targets(_dev(src), _dev(tgt), p=p, nlevels=L, path=path)
+    phi = t.eval_targets(_dev(gam)).cpu().numpy().astype(np.complex128)
+    allxy = np.concatenate([src, tgt])
+    allg = np.concatenate([gam, np.zeros(nt, np.complex128)])
+    ref = oracle.fmm(allxy, allg, L, 0.5, p)["phi"][ns:]
+    assert _rel(phi, ref) <= (1e-10 if path == "fp64" else 1e-5)
+    pick = g.choice(nt, 512, replace=False)
+    exact = oracle.direct_points(src, gam, tgt[pick])
+    assert _rel(phi[pick], exact) <= 1e-5
+    # the log kernel at the same points
+    phl = t.eval_targets_log(_dev(gam)).cpu().numpy().astype(np.complex128)
+    refl = oracle.fmm_log(allxy, allg, L, 0.5, p)[ns:]
+    assert _rel(phl, refl) <= (1e-10 if path == "fp64" else 1e-5)
+    t.close()

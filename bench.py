@@ -46,7 +46,7 @@ WORKLOAD = "cluster_mix_1e6_p17_theta0.5"
 HEADLINE_NLEVELS = 9
 # dram__bytes_read.sum + dram__bytes_write.sum of one P2P launch (k_p2p_pairs) at
 # N_levels = 9 on this workload, from one ncu capture of the kernel as it is built
-P2P_TRAFFIC_BYTES = 82_333_440 + 5_691_136
+P2P_TRAFFIC_BYTES = 82_951_424 + 4_469_504
 # algorithmic FP32 flops of one point-pair interaction Gamma_j / (z_i - z_j) with
 # complex Gamma (FMA = 2): difference 2, |d|^2 3, the two scalings by 1/|d|^2 2,
 # complex product and accumulation 8 (the reciprocal runs on the MUFU unit)

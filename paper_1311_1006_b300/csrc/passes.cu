@@ -88,20 +88,20 @@ __constant__ FactTable c_fact = make_fact();
 // (FP32: slot pairs interleaved as (re[2m], re[2m+1], im[2m], im[2m+1])).
 __device__ __forceinline__ void d_gather32(const int vbx, const double2* __restrict__ in, const int32_t* __restrict__ perm,
                            const int32_t* __restrict__ slot_of, int n, float2* out, float* outp, unsigned* cplx) {
-    int i = vbx * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double2 g = in[perm[i]];
-    const float2 v = make_float2((float)g.x, (float)g.y);
-    // record complex strengths (one atomic per warp that sees one, until the word is set)
-    const unsigned m = __activemask();
-    if (cplx != nullptr && __any_sync(m, v.y != 0.f) && (threadIdx.x & 31) == __ffs(m) - 1 &&
-        *reinterpret_cast<volatile unsigned*>(cplx) == 0u)
-        atomicOr(cplx, 1u);
-    out[i] = v;
-    const int slot = slot_of[i];
-    float* f = outp + 4 * (slot >> 1) + (slot & 1);
-    f[0] = v.x;
-    f[2] = v.y;
+    const int i = vbx * blockDim.x + threadIdx.x;
+    bool im = false;
+    if (i < n) {
+        const double2 g = in[perm[i]];
+        const float2 v = make_float2((float)g.x, (float)g.y);
+        out[i] = v;
+        const int slot = slot_of[i];
+        float* f = outp + 4 * (slot >> 1) + (slot & 1);
+        f[0] = v.x;
+        f[2] = v.y;
+        im = v.y != 0.f;
+    }
+    // record complex strengths: one plain store per block that saw one (every writer stores the same value)
+    if (cplx != nullptr && __syncthreads_or(im) && threadIdx.x == 0) *cplx = 1u;
 }
 __global__ void k_gather32(const double2* __restrict__ in, const int32_t* __restrict__ perm,
                            const int32_t* __restrict__ slot_of, int n, float2* out, float* outp, unsigned* cplx) { d_gather32(blockIdx.x, in, perm, slot_of, n, out, outp, cplx); }

@@ -55,6 +55,14 @@ inline int leaf_capacity(int max_leaf) {
 // Work-item sizes: P2P items hold about this many source points; M2L items at
 // most this many weak pairs.
 constexpr int kP2PItemSources = 4096;  // measured: 4096 beats 2048 (+0.3 %) and 8192 (+3 %) on the 1e6-point step
+// Source points per P2P work item: kP2PItemSources from half a million points up; smaller trees take
+// proportionally smaller items (at least 256 sources), so that their few leaves still give the GPU enough
+// warps (the split leaves' partial sums are added in item order, as for the long lists of large trees).
+inline int p2p_item_sources(int64_t n) {
+    const int64_t big = int64_t(1) << 19;
+    if (n >= big) return kP2PItemSources;
+    return (int)std::max<int64_t>(256, (int64_t)kP2PItemSources * n / big);
+}
 constexpr int kMaxLevels = 16;
 constexpr int kSubMax = 4096;  // largest box whose remaining splits one CTA performs in shared memory
 constexpr int kM2LItemPairsMax = 256;  // bound of m2l_item_pairs (counters of the M2L row order)

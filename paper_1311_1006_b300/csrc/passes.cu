@@ -747,6 +747,69 @@ __global__ void __launch_bounds__(128) k_l2l_warp(const int32_t* __restrict__ bo
                                                   double2* __restrict__ L64, float2* __restrict__ L32, int all32, int p,
                                                   int PS) { d_l2l_warp<P, LM, LOG>(blockIdx.x, boxes, cnt, parent, child0, rho, center, box_m2l, Lm2l, L64, L32, all32, p, PS); }
 
+// FP64 M2L with one warp per work item, for trees with few items (one thread
+// per item would leave most of the GPU idle: a 1e4-point tree has ~340 items):
+// lane l < P owns output coefficient l.  Per pair, lane k forms v_k = alpha^k
+// at_k (the powers by a product scan across the lanes), w_l = sum_k C(k+l, l)
+// v_k takes v_k from lane k by shuffles (k ascending, as in k_m2l64), and
+// g_l = u beta^l scales it into the lane's sum.
+template <int P, bool LOG>
+__global__ void __launch_bounds__(128) k_m2l64_warp(const int4* __restrict__ items,
+                                                    const unsigned long long* __restrict__ nitems,
+                                                    const int32_t* __restrict__ woff,
+                                                    const int32_t* __restrict__ widx,
+                                                    const double2* __restrict__ center,
+                                                    const double* __restrict__ rho, const double2* __restrict__ M64,
+                                                    double2* __restrict__ Lm2l, double2* __restrict__ part,
+                                                    const int32_t* __restrict__ rows, int PS) {
+    const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= (int)*nitems) return;  // warp-uniform
+    const int it = rows[row];
+    const int4 item = items[it];
+    const int b = item.x;
+    const double2 ct = center[b];
+    const double rt = rho[b];
+    double cb[P];  // row `lane` of the binomial matrix, C(k + lane, lane)
+#pragma unroll
+    for (int k = 0; k < P; ++k) cb[k] = lane < P ? c_binom.d[k + lane][lane] : 0.0;
+    double2 acc = make_double2(0.0, 0.0);
+    double b0 = 0.0;  // log kernel: constant term
+    const int32_t* wl = widx + woff[b];
+    for (int j = item.y; j < item.z; ++j) {
+        const int s = wl[j];
+        const double2 cs = center[s];
+        const double rs = rho[s];
+        const double dx = ct.x - cs.x, dy = ct.y - cs.y;
+        const double r2 = dx * dx + dy * dy;
+        const double inv = 1.0 / r2;
+        const double2 u = make_double2(dx * inv, -dy * inv);
+        const double2 alpha = make_double2(rs * u.x, rs * u.y);
+        const double2 beta = make_double2(-rt * u.x, -rt * u.y);
+        const double2 a = lane < P ? M64[(size_t)s * PS + lane] : make_double2(0.0, 0.0);
+        const double2 v = cmul(lane_pow(alpha, lane), a);
+        double2 w = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            const double2 vk = shfl2(v, k);
+            w.x = fma(cb[k], vk.x, w.x);
+            w.y = fma(cb[k], vk.y, w.y);
+        }
+        acc = cfma(cmul(u, lane_pow(beta, lane)), w, acc);
+        if constexpr (LOG) {
+            double t = (lane >= 1 && lane < P) ? -v.x / (double)lane : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            b0 += fma(0.5 * log(r2), __shfl_sync(0xffffffffu, a.x, 0), t);
+        }
+    }
+    double2* out = item.w < 0 ? Lm2l + (size_t)b * PS : part + (size_t)it * PS;
+    if (lane < P) out[lane] = acc;
+    if constexpr (LOG) {
+        if (lane == 0) out[P] = make_double2(b0, 0.0);
+    }
+}
+
 // Levels with at most this many shifts use the warp-per-shift kernels.
 constexpr int kWarpShiftMax = 1024;  // measured against 4096 and 16384: 1024 fastest
 
@@ -1711,9 +1774,14 @@ static void launch_up_fp64(Tree& t, const Bufs& B, cudaStream_t s) {
 template <int P, bool LOG>
 static void launch_down_fp64(Tree& t, const Bufs& B, cudaStream_t s) {
     if (t.flags & FMM_FLAG_TIMING) cudaEventRecord(t.ev_t[2], s);
-    k_m2l64<P, LOG><<<nblk(m2l_grid_items(t), 128), 128, 0, s>>>(t.d_m2l_items, item_count(t, 3), t.d_woff, t.d_widx,
-                                                    t.d_center, t.d_rho, B.M64, static_cast<double2*>(B.Lm2l),
-                                                    static_cast<double2*>(B.m2l_part), t.d_m2l_rows, t.PS);
+    if (m2l_grid_items(t) <= 64LL * t.num_sms)  // few items: a warp per item (lane = output coefficient)
+        k_m2l64_warp<P, LOG><<<nblk(32 * m2l_grid_items(t), 128), 128, 0, s>>>(
+            t.d_m2l_items, item_count(t, 3), t.d_woff, t.d_widx, t.d_center, t.d_rho, B.M64,
+            static_cast<double2*>(B.Lm2l), static_cast<double2*>(B.m2l_part), t.d_m2l_rows, t.PS);
+    else
+        k_m2l64<P, LOG><<<nblk(m2l_grid_items(t), 128), 128, 0, s>>>(t.d_m2l_items, item_count(t, 3), t.d_woff, t.d_widx,
+                                                        t.d_center, t.d_rho, B.M64, static_cast<double2*>(B.Lm2l),
+                                                        static_cast<double2*>(B.m2l_part), t.d_m2l_rows, t.PS);
     k_reduce_m2l<double2><<<nblk(32 * t.nbox, 256), 256, 0, s>>>((int)t.nbox, t.d_box_m2l,
                                                                 static_cast<const double2*>(B.m2l_part), t.PS,
                                                                 static_cast<double2*>(B.Lm2l));

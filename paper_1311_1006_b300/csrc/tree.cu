@@ -1391,7 +1391,7 @@ __global__ void __launch_bounds__(kLThreads) k_lists_level(
 
 // Work items that bound the work of one warp / thread whatever the list
 // lengths: P2P items = (leaf, slice of its strong list) with about
-// kP2PItemSources source points, M2L items = (box, at most m2l_item_pairs() weak
+// p2p_item_sources(n) source points, M2L items = (box, at most m2l_item_pairs() weak
 // entries).  A box whose list is split keeps its items contiguous; their
 // partial sums are added in item order later (deterministic).
 // int4 item = (box, list begin, list end, first item of the box or -1 when
@@ -1436,7 +1436,7 @@ __global__ void k_items(int nbox, const int32_t* __restrict__ child0, const int3
                         int4* p2p_items, int32_t* p2p_rows, int2* leaf_items, long long p2p_cap, int4* m2l_items,
                         int2* box_m2l,
                         long long m2l_cap, int K, unsigned long long* rowctr, int32_t* rows, int2* box_tail,
-                        unsigned* status) {
+                        unsigned* status, int item_sources) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (*((volatile unsigned*)status) & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW)) return;  // uniform
     const bool in = b < nbox;
@@ -1444,7 +1444,7 @@ __global__ void k_items(int nbox, const int32_t* __restrict__ child0, const int3
     int kp = 0, C = 1, n = 0;
     if (leaf) {
         n = ns[b] - soff[b];
-        C = max(1, kP2PItemSources / max(bcount[b], 1));
+        C = max(1, item_sources / max(bcount[b], 1));
         kp = (n + C - 1) / C;
     }
     const int m = in ? nw[b] - woff[b] : 0;
@@ -1758,7 +1758,7 @@ fmm_status run_lists(Tree& t, cudaStream_t s) {
                                               t.d_p2p_items, t.d_p2p_rows, t.d_leaf_items, t.p2p_cap,
                                               t.d_m2l_items, t.d_box_m2l,
                                               t.m2l_cap, m2l_item_pairs(t), t.d_m2l_rowctr, t.d_m2l_rows,
-                                              t.d_box_tail, t.d_status);
+                                              t.d_box_tail, t.d_status, p2p_item_sources(t.n));
     k_m2l_rows<<<nblk(t.nbox, 256), 256, 0, s>>>((int)t.nbox, t.d_box_m2l, t.d_box_tail, t.d_m2l_rowctr, t.m2l_cap,
                                                  t.d_m2l_rows, t.d_status);
     FMM_CUDA(cudaGetLastError());

@@ -581,8 +581,19 @@ fmm_status fmm_eval_status(fmm_tree* h, void* stream) {
     FMM_CUDA(cudaMemcpyAsync(&bits, t.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     FMM_CUDA(cudaStreamSynchronize(s));
     if (bits & ST_TIMEOUT) {
-        set_error("a bounded wait of the evaluation ran out");
+        unsigned long long stage = 0;
+        if (t.d_pers) {
+            FMM_CUDA(cudaMemcpyAsync(&stage, t.d_pers + 3, sizeof(stage), cudaMemcpyDeviceToHost, s));
+            FMM_CUDA(cudaStreamSynchronize(s));
+        }
+        set_error(stage ? "a work-queue wait of the persistent evaluation ran out (stage " + std::to_string(stage - 1) +
+                              ")"
+                        : std::string("a bounded wait of the evaluation ran out"));
         return FMM_ERR_TIMEOUT;
+    }
+    if (bits & ST_INTERNAL) {
+        set_error("an internal check of the evaluation failed");
+        return FMM_ERR_CUDA;
     }
     return FMM_OK;
 }
@@ -599,7 +610,7 @@ fmm_status fmm_selftest_bounded_wait(int which, void* stream) {
     if (e == cudaSuccess) {
         if (which == 0) launch_selftest_lookback(buf + 1, 1 << 12, status, s);
         else if (which == 1) launch_selftest_mbar(1 << 12, status, s);
-        else launch_selftest_queue(buf + 1, 1 << 12, status, s);
+        else launch_selftest_queue(buf, 20000000ull, status, s);  // 20 ms; [1], [2] counters, [3] stage
         e = cudaGetLastError();
     }
     unsigned h_status = 0;

@@ -247,7 +247,8 @@ struct Tree {
     std::vector<char> h_pstage;           // the table last uploaded
     int npstage = 0;
     long long pstage_total = 0;           // tickets (units) of one evaluation
-    unsigned long long* d_pers = nullptr;  // [0] ticket, [1] far-field units done, [2] P2P units done
+    unsigned long long* d_pers = nullptr;  // [0] ticket, [1] far-field units done, [2] P2P units done,
+                                           // [3] stage + 1 of a queue wait that ran out (0 = none)
 
     // captured evaluation graph (keyed by the user pointers it bakes in)
     cudaGraphExec_t graph = nullptr;
@@ -362,7 +363,7 @@ fmm_status m2l_tc_prepare(int P);
 // Self-tests of the bounded waits (a wait on something that never happens; ST_TIMEOUT expected).
 void launch_selftest_mbar(int limit, unsigned* status, cudaStream_t s);
 void launch_selftest_lookback(unsigned long long* st, int max_spins, unsigned* status, cudaStream_t s);
-void launch_selftest_queue(unsigned long long* ctr, int limit, unsigned* status, cudaStream_t s);
+void launch_selftest_queue(unsigned long long* ctr, unsigned long long limit_ns, unsigned* status, cudaStream_t s);
 void launch_selftest_rcp64(const double* x, int64_t n, double* out, cudaStream_t s);  // once per compiled order, before launches (and graph capture)
 void launch_m2l_tc(const Tree& t, const float2* M32, float2* Lm2l, float2* part, bool log_kernel, cudaStream_t s);
 

@@ -1490,7 +1490,7 @@ struct PArgs {
     long long total;
     unsigned long long* ctr;  // [0] ticket, [1] far-field units done, [2] P2P units done
     unsigned* status;
-    int spin_limit;
+    unsigned long long wait_ns;  // bound of one queue wait
     int n, nbox, p, PS, lay, pad, TS;
     const double2* gin;
     const int32_t *perm, *slot_of, *bstart, *bcount, *child0, *parent, *leaf_of, *fold_par, *pslot, *soff, *woff,
@@ -1519,28 +1519,39 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     return v;
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Wait until at least need_far far-field units and need_p2p P2P units are
-// complete; after `limit` rounds give up, set ST_TIMEOUT and return false.
-__device__ bool pq_wait(const unsigned long long* ctr, long long need_far, long long need_p2p, unsigned* status,
-                        int limit) {
-    for (int spins = 0;; ++spins) {
+// complete.  Bounded in time (limit_ns of the GPU's global timer, whatever the
+// sleeps between polls actually last): on expiry it sets ST_TIMEOUT, records
+// the waiting stage (+1) in ctr[3] and returns false.
+__device__ bool pq_wait(unsigned long long* ctr, long long need_far, long long need_p2p, unsigned* status,
+                        unsigned long long limit_ns, int stage) {
+    const unsigned long long t0 = global_ns();
+    while (true) {
         if ((long long)ld_acquire_u64(ctr + 1) >= need_far && (long long)ld_acquire_u64(ctr + 2) >= need_p2p)
             return true;
-        if (spins >= limit) {
+        if (global_ns() - t0 > limit_ns) {
             atomicOr(status, ST_TIMEOUT);
+            atomicMax(ctr + 3, (unsigned long long)(stage + 1));
             return false;
         }
-        __nanosleep(256);
+        __nanosleep(128);
     }
 }
 
 // Self-test of the queue's bounded wait: a unit that needs one far-field unit
-// more than will ever complete must give up and report ST_TIMEOUT.
-__global__ void k_selftest_queue(unsigned long long* ctr, int limit, unsigned* status) {
-    if (threadIdx.x == 0) pq_wait(ctr, (long long)ld_acquire_u64(ctr + 1) + 1, 0, status, limit);
+// more than will ever complete must give up (after `limit_ns`) and report
+// ST_TIMEOUT.
+__global__ void k_selftest_queue(unsigned long long* ctr, unsigned long long limit_ns, unsigned* status) {
+    if (threadIdx.x == 0) pq_wait(ctr, (long long)ld_acquire_u64(ctr + 1) + 1, 0, status, limit_ns, 0);
 }
-void launch_selftest_queue(unsigned long long* ctr, int limit, unsigned* status, cudaStream_t s) {
-    k_selftest_queue<<<1, 32, 0, s>>>(ctr, limit, status);
+void launch_selftest_queue(unsigned long long* ctr, unsigned long long limit_ns, unsigned* status, cudaStream_t s) {
+    k_selftest_queue<<<1, 32, 0, s>>>(ctr, limit_ns, status);
 }
 
 template <int TPL, int LT>
@@ -1619,13 +1630,18 @@ __global__ void __launch_bounds__(128, 4) k_eval_persistent(const PArgs a) {
     __shared__ int s_stage, s_vb, s_go;
     for (int i = threadIdx.x; i < a.nst; i += blockDim.x) sst[i] = a.st[i];
     __syncthreads();
-    while (true) {
+    // a CTA can take at most every ticket: more rounds than that mean a broken table (reported, not looped)
+    for (long long round = 0;; ++round) {
+        if (round > a.total) {
+            if (threadIdx.x == 0) atomicOr(a.status, ST_INTERNAL);
+            break;
+        }
         if (threadIdx.x == 0) {
             const long long tk = (long long)atomicAdd(a.ctr, 1ull);
             int go = 0, g = 0;
             if (tk < a.total) {
                 while (g + 1 < a.nst && sst[g + 1].ticket0 <= tk) ++g;
-                go = pq_wait(a.ctr, sst[g].need_far, sst[g].need_p2p, a.status, a.spin_limit) ? 1 : 0;
+                go = pq_wait(a.ctr, sst[g].need_far, sst[g].need_p2p, a.status, a.wait_ns, g) ? 1 : 0;
                 __threadfence();
             }
             s_stage = g;
@@ -2237,7 +2253,7 @@ static fmm_status launch_persistent(Tree& t, const double* d_gamma, void* d_phi,
     a.total = t.pstage_total;
     a.ctr = t.d_pers;
     a.status = t.d_status;
-    a.spin_limit = 1 << 24;  // x 256 ns sleeps: seconds, far beyond any stage
+    a.wait_ns = 4000000000ull;  // 4 s of the global timer: far beyond any stage
     a.n = (int)t.n;
     a.nbox = (int)t.nbox;
     a.p = t.p;

@@ -223,11 +223,23 @@ def leg_c1(F, orc, dev, stream, flush):
     exact = orc.direct(xy, gam)
     ofmm = orc.fmm(xy, gam, L, THETA, p)["phi"]
     t.close()
+    # the oracle on the same workload, all host cores and one thread, median of 5 evaluations each
+    cpu = {}
+    for label, th in (("all_cores", os.cpu_count() or 1), ("one_thread", 1)):
+        orc.set_threads(th)
+        ts = []
+        for _ in range(5):
+            t0 = time.time()
+            orc.fmm(xy, gam, L, THETA, p)
+            ts.append(time.time() - t0)
+        cpu[label] = {"seconds": round(float(np.median(ts)), 4), "value": _mps(n, float(np.median(ts)) * 1e3),
+                      "threads": orc.max_threads()}
+    orc.set_threads(os.cpu_count() or 1)
     return {"workload": "uniform_1e4_p20_theta0.5_fp64", "n_points": n, "p": p, "nlevels": L, "path": "fp64",
             "ms_per_step": round(ms, 4), "value": _mps(n, ms), "unit": UNIT,
             "rel_err_vs_direct": _rel(phi, exact), "rel_err_vs_oracle_fmm": _rel(phi, ofmm),
             "oracle_fmm_rel_err_vs_direct": _rel(ofmm, exact),
-            "step": "fmm_step (rebuild + evaluate), median of 20, L2 flushed"}
+            "cpu_oracle": cpu, "step": "fmm_step (rebuild + evaluate), median of 20, L2 flushed"}
 
 
 def leg_c3(F, orc, dev, stream, flush):
@@ -369,12 +381,22 @@ def leg_c5(F, orc, dev, stream, flush):
     rg, rxy = orc.direct_grad(xy, gam, gphi, targets=tg)
     info = t.info()
     t.close()
+    # the oracle on the same workload (all host cores, one run each): forward FMM, and the frozen-tree gradient
+    orc.set_threads(os.cpu_count() or 1)
+    t0 = time.time()
+    orc.fmm(xy, gam, info["nlevels_max"], THETA, 17)
+    t_fwd = time.time() - t0
+    t0 = time.time()
+    orc.fmm_grad(xy, gam, gphi, info["nlevels_max"], THETA, 17)
+    t_bwd = time.time() - t0
     return {"workload": "differentiated_uniform_1e6_p17_theta0.5_fp32", "n_points": n, "p": 17,
             "nlevels": info["nlevels_max"], "fwd_ms": round(fwd, 4), "bwd_ms": round(bwd, 4),
             "bwd_over_fwd": round(bwd / fwd, 3), "value": _mps(n, fwd + bwd), "unit": UNIT,
             "value_note": "points per second of forward + backward",
             "rel_err_grad_gamma": _rel(gg.cpu().numpy()[tg], rg),
             "rel_err_grad_xy": _rel(gxy.cpu().numpy()[tg], rxy),
+            "cpu_oracle": {"threads": orc.max_threads(), "fwd_s": round(t_fwd, 3), "grad_s": round(t_bwd, 3),
+                           "note": "oracle FMM and its frozen-tree gradient (plain FP64 C, all host cores)"},
             "error": "rel. max-norm vs the direct-sum gradient on 128 sampled points"}
 
 

@@ -266,7 +266,7 @@ def leg_c3(F, orc, dev, stream, flush):
            "error": "rel. max-norm vs the exact sum on 64 sampled points per snapshot (last step)"}
     for path in ("fp32", "fp64"):
         for p in (12, 30):
-            S = 4 if path == "fp32" else 3
+            S = 8 if path == "fp32" else 3
             L = F.default_nlevels(n, p, path)
             seed = L
             tree = F.Tree.build(snaps[0][0], p=p, theta=THETA, nlevels=L, path=path)

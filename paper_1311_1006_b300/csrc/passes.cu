@@ -1490,6 +1490,7 @@ struct PArgs {
     long long total;
     unsigned long long* ctr;  // [0] ticket, [1] far-field units done, [2] P2P units done
     unsigned* status;
+    unsigned* cplx;              // set by the gather units when a strength has a nonzero imaginary part
     unsigned long long wait_ns;  // bound of one queue wait
     int n, nbox, p, PS, lay, pad, TS;
     const double2* gin;
@@ -1554,18 +1555,23 @@ void launch_selftest_queue(unsigned long long* ctr, unsigned long long limit_ns,
     k_selftest_queue<<<1, 32, 0, s>>>(ctr, limit_ns, status);
 }
 
+// P2P units run after the gather stage, so the complex-strength flag is final: the real form when it is clear.
 template <int TPL, int LT>
 __device__ __forceinline__ void pq_p2p(const PArgs& a, int it) {
-    d_p2p_pairs_item<TPL, LT, false>(it, a.p2p_items, a.bstart, a.bcount, a.pslot, a.soff, a.srng, a.posq,
-                                     reinterpret_cast<const ulonglong2*>(a.gamp), a.nearv, a.p2p_part, a.TS, a.pad,
-                                     a.tfirst);
+    const ulonglong2* gq = reinterpret_cast<const ulonglong2*>(a.gamp);
+    if (*reinterpret_cast<volatile const unsigned*>(a.cplx) == 0u)
+        d_p2p_pairs_item<TPL, LT, false, true>(it, a.p2p_items, a.bstart, a.bcount, a.pslot, a.soff, a.srng, a.posq,
+                                               gq, a.nearv, a.p2p_part, a.TS, a.pad, a.tfirst);
+    else
+        d_p2p_pairs_item<TPL, LT, false>(it, a.p2p_items, a.bstart, a.bcount, a.pslot, a.soff, a.srng, a.posq, gq,
+                                         a.nearv, a.p2p_part, a.TS, a.pad, a.tfirst);
 }
 
 template <int P>
 __device__ __forceinline__ void pq_unit(const PArgs& a, const PStage& g, int vb) {
     switch (g.type) {
-        case PT_GATHER:
-            d_gather32(vb, a.gin, a.perm, a.slot_of, a.n, a.gam, a.gamp, nullptr);
+        case PT_GATHER:  // also flags complex strengths (the whole CTA runs the unit: its block-wide OR is safe)
+            d_gather32(vb, a.gin, a.perm, a.slot_of, a.n, a.gam, a.gamp, a.cplx);
             break;
         case PT_P2M_T:
             d_p2m32<P>(vb, g.ids, g.cnt, a.bstart, a.bcount, a.chl, a.rho32, a.pos4, a.gam, a.M32,
@@ -2253,6 +2259,7 @@ static fmm_status launch_persistent(Tree& t, const double* d_gamma, void* d_phi,
     a.total = t.pstage_total;
     a.ctr = t.d_pers;
     a.status = t.d_status;
+    a.cplx = t.d_status + 1;
     a.wait_ns = 4000000000ull;  // 4 s of the global timer: far beyond any stage
     a.n = (int)t.n;
     a.nbox = (int)t.nbox;
@@ -2305,6 +2312,7 @@ static fmm_status launch_persistent(Tree& t, const double* d_gamma, void* d_phi,
     a.p2p_part = static_cast<float2*>(B.p2p_part);
     a.out = static_cast<float2*>(d_phi);
     FMM_CUDA(cudaMemsetAsync(t.d_pers, 0, 4 * sizeof(unsigned long long), s));
+    FMM_CUDA(cudaMemsetAsync(t.d_status + 1, 0, sizeof(unsigned), s));  // the complex-strength flag
     const long long grid = std::min<long long>((long long)occ * t.num_sms, std::max<long long>(t.pstage_total, 1));
     k_eval_persistent<P><<<(int)grid, 128, 0, s>>>(a);
     FMM_CUDA(cudaGetLastError());

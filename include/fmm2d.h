@@ -131,11 +131,18 @@ fmm_status fmm_eval_batched(fmm_tree* t, const double* d_gamma, void* d_phi, voi
  * fmm_eval(t, d_gamma, d_phi, stream), same arguments and the same result bit
  * for bit, in one call that overlaps the two: the strength gather and the
  * upward pass (P2M, M2M), which need the tree but not the coupling lists, run
- * on the library's far-field stream while the lists are built.  Parameters
- * stay as the tree has them (change them with fmm_tree_rebuild).  A batched
- * tree, or a tree with FMM_FLAG_SERIAL, FMM_FLAG_TIMING or FMM_FLAG_GRAPH, runs
- * the two calls in sequence.  Errors: INVALID_ARG (NULL, a tree built with
- * separate evaluation points), CUDA, OOM, TIMEOUT, NONFINITE as the two calls. */
+ * on the library's far-field stream while the lists are built.  Once an
+ * earlier build has sized the list and item capacities, the evaluation is
+ * queued on the device behind the list passes and the host checks the
+ * build's counters while it runs; the call returns when that check is done
+ * (the evaluation may still be running on `stream`).  A build that needs
+ * larger capacities (or met a non-finite coordinate or a long run of equal
+ * coordinates) is done again in the checked order, into the same d_phi.
+ * Parameters stay as the tree has them (change them with fmm_tree_rebuild).
+ * A batched tree, or a tree with FMM_FLAG_SERIAL, FMM_FLAG_TIMING,
+ * FMM_FLAG_GRAPH or FMM_FLAG_PERSISTENT, runs the two calls in sequence.
+ * Errors: INVALID_ARG (NULL, a tree built with separate evaluation points),
+ * CUDA, OOM, TIMEOUT, NONFINITE as the two calls. */
 fmm_status fmm_step(fmm_tree* t, const double* d_xy, const double* d_gamma, void* d_phi, void* stream);
 
 /* Self-test of the library's bounded device waits (failure detection without

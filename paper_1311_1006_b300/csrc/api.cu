@@ -103,6 +103,10 @@ static void apply_params(Tree& t, const fmm_params* prm) {
     t.flags = prm->flags;
 }
 
+// Words of the pinned copy of a build's counters: the status word and counters [0, 5), the level bases and
+// size requests of the list passes from word 8.
+constexpr int kChkWords = 8 + 2 * kMaxLevels + 6;
+
 static fmm_status ensure_streams(Tree& t) {
     int dev = 0;
     FMM_CUDA(cudaGetDevice(&dev));
@@ -118,6 +122,9 @@ static fmm_status ensure_streams(Tree& t) {
     if (!t.s_far2) FMM_CUDA(cudaStreamCreateWithPriority(&t.s_far2, cudaStreamNonBlocking, hi_prio));
     if (!t.ev_join_far2) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_join_far2, cudaEventDisableTiming));
     if (!t.ev_gather) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_gather, cudaEventDisableTiming));
+    if (!t.ev_lists) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_lists, cudaEventDisableTiming));
+    if (!t.ev_chk) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_chk, cudaEventDisableTiming));
+    if (!t.h_chk) FMM_CUDA(cudaMallocHost(reinterpret_cast<void**>(&t.h_chk), kChkWords * sizeof(unsigned long long)));
     if (!t.ev_fork) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_fork, cudaEventDisableTiming));
     if (!t.ev_join) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_join, cudaEventDisableTiming));
     if (!t.ev_join_far) FMM_CUDA(cudaEventCreateWithFlags(&t.ev_join_far, cudaEventDisableTiming));
@@ -137,7 +144,7 @@ static fmm_status build_lists(Tree& t, cudaStream_t s, const double* d_xy, bool*
     for (int attempt = 0; attempt < 16; ++attempt) {
         if ((st = run_lists(t, s))) return st;
         unsigned long long hbuf[5] = {0, 0, 0, 0, 0};
-        unsigned long long lb[2 * kMaxLevels + 4];
+        unsigned long long lb[2 * kMaxLevels + 6];
         FMM_CUDA(cudaMemcpyAsync(hbuf, t.d_status, sizeof(hbuf), cudaMemcpyDeviceToHost, s));
         FMM_CUDA(cudaMemcpyAsync(lb, t.d_lvl_base, sizeof(lb), cudaMemcpyDeviceToHost, s));
         FMM_CUDA(cudaStreamSynchronize(s));
@@ -177,8 +184,10 @@ static fmm_status build_lists(Tree& t, cudaStream_t s, const double* d_xy, bool*
         if (need[1] > (unsigned long long)t.scap_tot) t.scap_tot = grow(t.scap_tot, need[1]);
         if (need[2] > (unsigned long long)t.wcap_tot) t.wcap_tot = grow(t.wcap_tot, need[2]);
         if (!ovl && (bits & ST_ITEM_OVERFLOW)) {
-            if ((long long)hbuf[3] > t.p2p_cap) t.p2p_cap = (long long)(hbuf[3] + hbuf[3] / 4 + 1024);
-            if ((long long)hbuf[4] > t.m2l_cap) t.m2l_cap = (long long)(hbuf[4] + hbuf[4] / 4 + 1024);
+            // the item counts, moved aside by k_m2l_rows (the counters themselves are zeroed)
+            const unsigned long long ip = need[4], im = need[5];
+            if ((long long)ip > t.p2p_cap) t.p2p_cap = (long long)(ip + ip / 4 + 1024);
+            if ((long long)im > t.m2l_cap) t.m2l_cap = (long long)(im + im / 4 + 1024);
         }
         if (t.scap_tot >= (1ll << 31) || t.wcap_tot >= (1ll << 31)) {
             set_error("coupling lists exceed 2^31 entries");
@@ -250,6 +259,9 @@ static void release(Tree* t) {
     if (t->s_far2) cudaStreamDestroy(t->s_far2);
     if (t->ev_join_far2) cudaEventDestroy(t->ev_join_far2);
     if (t->ev_gather) cudaEventDestroy(t->ev_gather);
+    if (t->ev_lists) cudaEventDestroy(t->ev_lists);
+    if (t->ev_chk) cudaEventDestroy(t->ev_chk);
+    if (t->h_chk) cudaFreeHost(t->h_chk);
     if (t->ev_join_far) cudaEventDestroy(t->ev_join_far);
     if (t->ev_fork) cudaEventDestroy(t->ev_fork);
     if (t->ev_join) cudaEventDestroy(t->ev_join);
@@ -535,6 +547,58 @@ fmm_status fmm_step(fmm_tree* h, const double* d_xy, const double* d_gamma, void
     if ((st = check_pending())) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if ((st = ensure_streams(t))) return st;
+    if (t.h_counts[0] != 0 && t.grid_p2p_items > 0 && t.grid_m2l_items > 0) {
+        // Capacities and launch grids known from an earlier build: the evaluation is queued behind the list
+        // passes on the device, and the host checks the build's counters (copied after the lists) while it
+        // runs.  A build that overflowed a capacity, gave up a wait, met a non-finite coordinate or a long
+        // run of equal sort keys, or needs larger grids, is done again in the checked order below; the
+        // evaluation queued behind it did only in-bounds work on stale tables (no items after an overflow).
+        if ((st = run_tree_build(t, d_xy, s))) return st;
+        const unsigned gen0 = t.eval_gen;
+        if ((st = alloc_eval_core(t, 1))) return st;
+        if ((st = alloc_eval_parts(t))) return st;
+        if (t.eval_gen != gen0) invalidate_graph(t);  // a captured evaluation holds the old buffers
+        const Bufs B = bufs(t, 0);
+        t.p2p_funcs.clear();
+        FMM_CUDA(cudaEventRecord(t.ev_fork, s));
+        FMM_CUDA(cudaStreamWaitEvent(t.s_far, t.ev_fork, 0));
+        launch_gather(t, B, d_gamma, t.s_far);
+        FMM_CUDA(cudaEventRecord(t.ev_gather, t.s_far));
+        dispatch_up(t, B, t.s_far);
+        if ((st = run_lists(t, s))) return st;
+        FMM_CUDA(cudaEventRecord(t.ev_lists, s));
+        FMM_CUDA(cudaMemcpyAsync(t.h_chk, t.d_status, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        FMM_CUDA(cudaMemcpyAsync(t.h_chk + 8, t.d_lvl_base, (2 * kMaxLevels + 6) * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, s));
+        FMM_CUDA(cudaEventRecord(t.ev_chk, s));
+        FMM_CUDA(cudaStreamWaitEvent(t.s_far, t.ev_lists, 0));
+        dispatch_down(t, B, t.s_far);
+        FMM_CUDA(cudaEventRecord(t.ev_join_far, t.s_far));
+        FMM_CUDA(cudaStreamWaitEvent(t.s_aux, t.ev_gather, 0));
+        FMM_CUDA(cudaStreamWaitEvent(t.s_aux, t.ev_lists, 0));
+        launch_near(t, B, t.s_aux);
+        FMM_CUDA(cudaEventRecord(t.ev_join, t.s_aux));
+        FMM_CUDA(cudaStreamWaitEvent(s, t.ev_join_far, 0));
+        FMM_CUDA(cudaStreamWaitEvent(s, t.ev_join, 0));
+        launch_l2p_near(t, B, d_phi, s);
+        FMM_CUDA(cudaGetLastError());
+        t.timing_valid = false;
+        FMM_CUDA(cudaEventSynchronize(t.ev_chk));
+        const unsigned bits = (unsigned)(t.h_chk[0] & 0xffffffffu);
+        const unsigned long long* lb = t.h_chk + 8;
+        const bool ok = !(bits & (ST_NONFINITE | ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW | ST_TIMEOUT | ST_INTERNAL |
+                                  ST_ITEM_OVERFLOW | ST_SORT_RUN)) &&
+                        (long long)t.h_chk[3] <= t.grid_p2p_items && (long long)t.h_chk[4] <= t.grid_m2l_items;
+        if (ok) {
+            t.h_counts[0] = lb[t.Lmax];
+            t.h_counts[1] = lb[kMaxLevels + t.Lmax];
+            t.h_counts[2] = t.h_chk[3];
+            t.h_counts[3] = t.h_chk[4];
+            if (refresh_grids(t)) invalidate_graph(t);  // grids for the next evaluation
+            return FMM_OK;
+        }
+        FMM_CUDA(cudaStreamSynchronize(s));  // the queued evaluation is done; the checked order replaces its result
+    }
     if ((st = run_tree_build(t, d_xy, s))) return st;
     const unsigned gen = t.eval_gen;
     if ((st = alloc_eval_core(t, 1))) return st;

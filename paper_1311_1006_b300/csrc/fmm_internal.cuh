@@ -239,6 +239,10 @@ struct Tree {
     cudaStream_t s_far2 = nullptr;  // second strength set's far-field chain (log kernel, adjoint; highest priority)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join_far = nullptr, ev_join_far2 = nullptr;
     cudaEvent_t ev_gather = nullptr;  // strengths gathered (fmm_step: P2P waits on it)
+    // fmm_step with the evaluation queued behind the list passes: the lists are done (the evaluation waits on
+    // it), the build's counters are in h_chk (the host waits on that)
+    cudaEvent_t ev_lists = nullptr, ev_chk = nullptr;
+    unsigned long long* h_chk = nullptr;  // pinned: status word + counters [0, 5), level bases + needs [8, ...)
     cudaEvent_t ev_t[9] = {};  // phase boundaries of a timed evaluation (fmm_phase_times)
     bool timing_valid = false;
 

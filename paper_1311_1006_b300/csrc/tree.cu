@@ -1438,7 +1438,8 @@ __global__ void k_items(int nbox, const int32_t* __restrict__ child0, const int3
                         long long m2l_cap, int K, unsigned long long* rowctr, int32_t* rows, int2* box_tail,
                         unsigned* status, int item_sources) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (*((volatile unsigned*)status) & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW)) return;  // uniform
+    // lists that overflowed or whose build gave up: no items (the counters stay zero)
+    if (*((volatile unsigned*)status) & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW | ST_TIMEOUT | ST_INTERNAL)) return;
     const bool in = b < nbox;
     const bool leaf = in && child0[b] < 0;
     int kp = 0, C = 1, n = 0;
@@ -1458,11 +1459,13 @@ __global__ void k_items(int nbox, const int32_t* __restrict__ child0, const int3
     const int kh = kp > 1 ? kp - 1 : 0, kl = kp > 0 ? 1 : 0;
     warp_reserve3(rowctr + kM2LItemPairsMax + 1, kh, rowctr + kM2LItemPairsMax + 2, kl,
                   rowctr + kM2LItemPairsMax + 3, 0, bh, bl, bz);
+    // a box whose items do not fit gets (0, 0): the passes that read these tables stay inside the buffers
     if (leaf) {
-        leaf_items[b] = make_int2((int)bp, kp);
         if ((long long)(bp + kp) > p2p_cap || (long long)(bh + kh + bl + kl) > p2p_cap) {
+            leaf_items[b] = make_int2(0, 0);
             atomicOr(status, ST_ITEM_OVERFLOW);
         } else {
+            leaf_items[b] = make_int2((int)bp, kp);
             for (int c = 0; c < kp; ++c)
                 p2p_items[bp + c] = make_int4(b, c * C, min(n, (c + 1) * C), kp > 1 ? (int)bp : -1);
             for (int c = 0; c < kh; ++c) p2p_rows[bh + c] = (int32_t)(bp + c);
@@ -1470,11 +1473,12 @@ __global__ void k_items(int nbox, const int32_t* __restrict__ child0, const int3
         }
     }
     if (!in) return;
-    box_m2l[b] = make_int2((int)bm, km);
     box_tail[b] = make_int2(r, rank);
     if ((long long)(bm + km) > m2l_cap) {
+        box_m2l[b] = make_int2(0, 0);
         atomicOr(status, ST_ITEM_OVERFLOW);
     } else {
+        box_m2l[b] = make_int2((int)bm, km);
         for (int c = 0; c < km; ++c)
             m2l_items[bm + c] = make_int4(b, c * K, min(m, (c + 1) * K), km > 1 ? (int)bm : -1);
         for (int c = 0; c < nfull; ++c) {
@@ -1487,12 +1491,22 @@ __global__ void k_items(int nbox, const int32_t* __restrict__ child0, const int3
 // Rows of the short last items: after the full items, by decreasing length
 // (rank among equal lengths from k_items' counter).  Blocks of kM2LItemPairsMax threads.
 static_assert(kM2LItemPairsMax == 256, "k_m2l_rows: one thread per item length in its blocks of 256");
+// After an item overflow the P2P and M2L item counts move to need[4], need[5] (the sizes the host grows the
+// capacities to) and the counters read by the evaluation are zeroed, so that an evaluation already queued
+// behind this build finds no items.
 __global__ void k_m2l_rows(int nbox, const int2* __restrict__ box_m2l, const int2* __restrict__ box_tail,
                            const unsigned long long* __restrict__ rowctr, long long m2l_cap, int32_t* rows,
-                           unsigned* status) {
+                           unsigned long long* item_ctr, unsigned long long* need, unsigned* status) {
     __shared__ unsigned long long base[kM2LItemPairsMax];
     __shared__ int wsum[32];
-    if (*((volatile unsigned*)status) & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW | ST_ITEM_OVERFLOW)) return;
+    const unsigned st0 = *((volatile unsigned*)status);
+    if ((st0 & ST_ITEM_OVERFLOW) && blockIdx.x == 0 && threadIdx.x == 0) {
+        need[4] = item_ctr[0];
+        need[5] = item_ctr[1];
+        item_ctr[0] = 0;
+        item_ctr[1] = 0;
+    }
+    if (st0 & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW | ST_ITEM_OVERFLOW | ST_TIMEOUT)) return;  // uniform
     {  // base[r] = full items + short items longer than r: thread i takes length r = kM2LItemPairsMax - 1 - i
         const int r = kM2LItemPairsMax - 1 - (int)threadIdx.x;
         const int c = r >= 1 ? (int)rowctr[r] : 0;
@@ -1734,7 +1748,7 @@ fmm_status run_lists(Tree& t, cudaStream_t s) {
     unsigned long long* ctr = reinterpret_cast<unsigned long long*>(t.d_status) + 1;
     unsigned long long* need = t.d_lvl_base + 2 * kMaxLevels;
     FMM_CUDA(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), s));
-    FMM_CUDA(cudaMemsetAsync(need, 0, 4 * sizeof(unsigned long long), s));
+    FMM_CUDA(cudaMemsetAsync(need, 0, 6 * sizeof(unsigned long long), s));
     // P2P sources of a leaf: its points, or with separate evaluation points its sources only
     const int32_t* srccount = t.n_src > 0 ? t.d_nsrc : t.d_bcount;
     k_lists_root<<<nblk(t.ninst, 128), 128, 0, s>>>(t.d_inst_boxoff, t.ninst, t.d_soff, t.d_ns, t.d_sidx, t.d_sowner,
@@ -1760,7 +1774,7 @@ fmm_status run_lists(Tree& t, cudaStream_t s) {
                                               t.m2l_cap, m2l_item_pairs(t), t.d_m2l_rowctr, t.d_m2l_rows,
                                               t.d_box_tail, t.d_status, p2p_item_sources(t.n));
     k_m2l_rows<<<nblk(t.nbox, 256), 256, 0, s>>>((int)t.nbox, t.d_box_m2l, t.d_box_tail, t.d_m2l_rowctr, t.m2l_cap,
-                                                 t.d_m2l_rows, t.d_status);
+                                                 t.d_m2l_rows, ctr + 2, need, t.d_status);
     FMM_CUDA(cudaGetLastError());
     return FMM_OK;
 }

@@ -244,6 +244,30 @@ __global__ void k_inst_keys(const int32_t* __restrict__ vx, const int32_t* __res
     }
 }
 
+// As block_excl_scan without the closing barrier: the caller passes a barrier before wsum is written again.
+__device__ __forceinline__ int block_excl_scan_nb(int v, int* wsum, int& total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int ws = lane < nw ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, ws, o);
+            if (lane >= o) ws += y;
+        }
+        wsum[lane] = ws;
+    }
+    __syncthreads();
+    total = wsum[nw - 1];
+    return x - v + (w ? wsum[w - 1] : 0);
+}
+
 __device__ __forceinline__ int block_excl_scan(int v, int* wsum, int& total) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
@@ -1280,7 +1304,7 @@ __global__ void __launch_bounds__(kLThreads) k_lists_level(
     const float* __restrict__ rad32, const double2* __restrict__ center, const double* __restrict__ radius,
     double theta, unsigned long long* tstat, long long tiles_cap, long long scap, long long wcap,
     unsigned long long* need, unsigned* status) {
-    __shared__ int ws[32], ww[32];
+    __shared__ int ws[32];
     __shared__ long long sh_excl[2];
     __shared__ long long sh_tile;
     if (*((volatile unsigned*)status) & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW)) return;
@@ -1307,8 +1331,7 @@ __global__ void __launch_bounds__(kLThreads) k_lists_level(
     while (true) {
         if (threadIdx.x == 0) sh_tile = (long long)atomicAdd(ticket, 1ull);
         __syncthreads();
-        const long long t = sh_tile;
-        __syncthreads();
+        const long long t = sh_tile;  // rewritten only after the scan's barriers of this tile
         if (t >= ntiles) break;
         const long long g0 = t * kLTile + (long long)threadIdx.x * kLItems;
         CandGroup cg[kLItems / 4];
@@ -1333,9 +1356,12 @@ __global__ void __launch_bounds__(kLThreads) k_lists_level(
                 fl |= (sep ? 2u : 1u) << (2 * (4 * gq + cp));
             }
         }
-        int tot_s, tot_w;
-        long long ps = block_excl_scan(cs, ws, tot_s);
-        long long pw = block_excl_scan(cw, ww, tot_w);
+        // both counts in one scan (at most 8 per thread and kLTile per tile: 16 bits each)
+        int tot;
+        const int pk = block_excl_scan_nb(cs | (cw << 16), ws, tot);
+        const int tot_s = tot & 0xffff, tot_w = tot >> 16;
+        long long ps = pk & 0xffff;
+        long long pw = pk >> 16;
         if (threadIdx.x < 64) {  // warp 0: strong counts, warp 1: weak counts
             const int which = threadIdx.x >> 5;
             const unsigned long long agg = (unsigned long long)(which ? tot_w : tot_s);

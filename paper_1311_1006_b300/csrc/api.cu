@@ -621,7 +621,8 @@ fmm_status fmm_step(fmm_tree* h, const double* d_xy, const double* d_gamma, void
     // the partial-sum buffers follow the list capacities just learned: allocate them now and take the
     // buffer table again (the one above predates them)
     if ((st = alloc_eval_parts(t))) return st;
-    if (t.eval_gen != gen || refresh_grids(t)) invalidate_graph(t);
+    const bool regrid = refresh_grids(t);  // always: the grids must cover this build's item counts
+    if (t.eval_gen != gen || regrid) invalidate_graph(t);
     const Bufs Bd = bufs(t, 0);
     dispatch_down(t, Bd, t.s_far);
     FMM_CUDA(cudaEventRecord(t.ev_join_far, t.s_far));

@@ -44,6 +44,35 @@ def test_step_equals_rebuild_then_eval(path):
     b.close()
 
 
+def test_step_gradual_clustering_bit_for_bit_and_oracle(orc):
+    """A slowly tightening sequence (sigma 0.2 * 0.75^k): most steps reuse the earlier capacities and run the
+    evaluation queued behind the lists, some outgrow the list or the item capacities and are redone in the
+    checked order.  Every step equals rebuild + eval on a second tree bit for bit; the last one is also checked
+    against the oracle FMM."""
+    from paper_1311_1006_b300 import Tree
+
+    n, L = 12000, 6
+    g = np.random.default_rng(21)
+    c = g.uniform(0.35, 0.65, size=(3, 2))
+    a = Tree.build(_dev(W.uniform(n, g)), p=12, nlevels=L, path="fp64")
+    b = Tree.build(_dev(W.uniform(n, g)), p=12, nlevels=L, path="fp64")
+    for k in range(14):
+        sigma = 0.2 * 0.75 ** k
+        xy = np.clip(np.concatenate([c[i] + sigma * g.normal(size=(n // 3 + (i < n % 3), 2)) for i in range(3)]),
+                     0.0, 1.0)
+        gam = W.complex_strengths(n, g)
+        pa = a.step(_dev(xy), _dev(gam)).cpu().numpy()
+        b.rebuild(_dev(xy))
+        pb = b.eval(_dev(gam)).cpu().numpy()
+        assert np.array_equal(pa, pb), k
+        info_a, info_b = a.info(), b.info()
+        assert info_a["n_strong"] == info_b["n_strong"] and info_a["p2p_items"] == info_b["p2p_items"], k
+    ref = orc.fmm(xy, gam, L, 0.5, 12)["phi"]
+    assert np.abs(pa - ref).max() <= 1e-10 * np.abs(ref).max()
+    a.close()
+    b.close()
+
+
 def test_step_as_the_first_call_and_against_the_oracle(orc):
     from paper_1311_1006_b300 import Tree
 

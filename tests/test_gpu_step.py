@@ -73,6 +73,25 @@ def test_step_gradual_clustering_bit_for_bit_and_oracle(orc):
     b.close()
 
 
+def test_step_after_level_changes_equals_fresh_tree():
+    """N_levels changing between steps (as the tuner does: a rebuild with another level count, then steps):
+    the capacities, grids and counters of the previous shape must not leak into the queued evaluation."""
+    from paper_1311_1006_b300 import Tree
+
+    n = 20000
+    g = np.random.default_rng(31)
+    t = Tree.build(_dev(W.uniform(n, g)), p=12, nlevels=6, path="fp32")
+    for L in (7, 5, 8, 6, 7):
+        xy, gam = W.cluster_mix(n, g), W.complex_strengths(n, g)
+        t.rebuild(_dev(W.uniform(n, g)), nlevels=L)  # the new shape, on other points
+        for _ in range(2):
+            pa = t.step(_dev(xy), _dev(gam)).cpu().numpy()
+            f = Tree.build(_dev(xy), p=12, nlevels=L, path="fp32")
+            assert np.array_equal(pa, f.eval(_dev(gam)).cpu().numpy()), L
+            f.close()
+    t.close()
+
+
 def test_step_as_the_first_call_and_against_the_oracle(orc):
     from paper_1311_1006_b300 import Tree
 

@@ -530,10 +530,12 @@ fmm_status fmm_tree_rebuild(fmm_tree* h, const double* d_xy, const fmm_params* p
 
 // Rebuild + evaluate in one call.  The upward pass (strength gather, P2M,
 // M2M) needs the tree but not the coupling lists, so it runs on the far-field
-// stream while the lists are built on the caller's stream; after the build's
-// host check the downward pass follows on the far-field stream and P2P on the
-// low-priority stream, as in fmm_eval.  Same kernels in the same per-stream
-// order as fmm_tree_rebuild + fmm_eval, so the same result bit for bit.
+// stream while the lists are built on the caller's stream; the downward pass
+// follows on the far-field stream and P2P on the low-priority stream, as in
+// fmm_eval, queued behind the lists on the device once an earlier build has
+// sized the capacities (else after the build's host check).  Same kernels in
+// the same per-stream order as fmm_tree_rebuild + fmm_eval, so the same result
+// bit for bit.
 fmm_status fmm_step(fmm_tree* h, const double* d_xy, const double* d_gamma, void* d_phi, void* stream) {
     if (!h || !d_xy || !d_gamma || !d_phi) return invalid("NULL argument");
     Tree& t = h->t;

@@ -11,6 +11,34 @@
 
 namespace fmm {
 
+// ------------------------------------------------ programmatic dependent launch
+// The build is a chain of short kernels on one stream.  A kernel launched by
+// launch_dep(true, ...) may be scheduled while the kernel before it in the
+// stream is still running; pdl_entry(), its first statement, lets the next
+// kernel be scheduled in turn and then waits until every prerequisite grid has
+// completed and its memory writes are visible, so no memory access of the
+// kernel precedes that point.  Without the launch attribute both instructions
+// do nothing.
+__device__ __forceinline__ void pdl_entry() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+template <typename... K, typename... A>
+inline cudaError_t launch_dep(bool dep, void (*k)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = dep ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<A&&>(args)...);
+}
+
 // ------------------------------------------------------------------ status
 // Bits of the device status word (atomicOr from kernels, read after a build).
 enum : unsigned {

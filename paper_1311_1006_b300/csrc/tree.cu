@@ -367,6 +367,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_ghist(const uint64_t* __r
                                                              const uint64_t* __restrict__ k1, int n,
                                                              unsigned* __restrict__ ghist,
                                                              const double2* __restrict__ xy, unsigned* status) {
+    pdl_entry();
     __shared__ unsigned h[8][256];
     const int s = blockIdx.y;
     const uint64_t* k = s ? k1 : k0;
@@ -427,6 +428,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t* _
                                                                const unsigned* __restrict__ ghist, unsigned* stat,
                                                                unsigned* ticket, unsigned* status,
                                                                const double2* __restrict__ xy = nullptr) {
+    pdl_entry();
     constexpr int W = kSortThreads / 32;
     __shared__ int whist[W][257];  // per-warp digit counts, then their exclusive prefix over warps
     __shared__ int base[256];      // global position of the tile's first key of each digit
@@ -603,6 +605,7 @@ __global__ void __launch_bounds__(256) k_sort_runs(const uint64_t* __restrict__ 
                                                    int32_t* __restrict__ o0, int32_t* __restrict__ o1, int n,
                                                    uint8_t* __restrict__ side0, const int32_t* __restrict__ nz0,
                                                    unsigned* status) {
+    pdl_entry();
     const uint64_t* key = blockIdx.y ? k1 : k0;
     const int32_t* val = blockIdx.y ? v1 : v0;
     int32_t* out = blockIdx.y ? o1 : o0;
@@ -663,29 +666,32 @@ static fmm_status sort_coordinates(Tree& t, cudaStream_t s, const double2* xy, b
     unsigned* stat = tk + 16;
     FMM_CUDA(cudaMemsetAsync(gh, 0, sort_scratch_words(n) * sizeof(unsigned), s));
     dim3 g(T, 2);
-    if (full) k_sort_ghist<0, true><<<g, kSortThreads, 0, s>>>(nullptr, nullptr, n, gh, xy, t.d_status);
-    else k_sort_ghist<4, true><<<g, kSortThreads, 0, s>>>(nullptr, nullptr, n, gh, xy, t.d_status);
+    if (full)
+        launch_dep(false, k_sort_ghist<0, true>, g, kSortThreads, 0, s, nullptr, nullptr, n, gh, xy, t.d_status);
+    else
+        launch_dep(false, k_sort_ghist<4, true>, g, kSortThreads, 0, s, nullptr, nullptr, n, gh, xy, t.d_status);
     int src = 0;
     const int p0 = full ? 0 : 4;
     for (int pass = p0; pass < 8; ++pass) {  // an even number of passes: the result is in buffers 0/1
         const int dst = 2 - src;
         if (pass == p0)  // the first pass forms the keys from the points
-            k_sort_scatter<true, true><<<g, kSortThreads, 0, s>>>(
-                nullptr, nullptr, nullptr, nullptr, t.d_keys[dst], t.d_vals[dst], t.d_keys[dst + 1], t.d_vals[dst + 1],
-                n, 8 * pass, T, nullptr, gh + pass * 256, stat + (size_t)pass * 2 * T * 256, tk + 2 * pass,
-                t.d_status, xy);
+            launch_dep(true, k_sort_scatter<true, true>, g, kSortThreads, 0, s,
+                       nullptr, nullptr, nullptr, nullptr, t.d_keys[dst], t.d_vals[dst], t.d_keys[dst + 1],
+                       t.d_vals[dst + 1], n, 8 * pass, T, nullptr, gh + pass * 256, stat + (size_t)pass * 2 * T * 256,
+                       tk + 2 * pass, t.d_status, xy);
         else
-            k_sort_scatter<true><<<g, kSortThreads, 0, s>>>(
-                t.d_keys[src], t.d_vals[src], t.d_keys[src + 1], t.d_vals[src + 1], t.d_keys[dst], t.d_vals[dst],
-                t.d_keys[dst + 1], t.d_vals[dst + 1], n, 8 * pass, T, nullptr, gh + pass * 256,
-                stat + (size_t)pass * 2 * T * 256, tk + 2 * pass, t.d_status);
+            launch_dep(true, k_sort_scatter<true>, g, kSortThreads, 0, s,
+                       t.d_keys[src], t.d_vals[src], t.d_keys[src + 1], t.d_vals[src + 1], t.d_keys[dst],
+                       t.d_vals[dst], t.d_keys[dst + 1], t.d_vals[dst + 1], n, 8 * pass, T, nullptr, gh + pass * 256,
+                       stat + (size_t)pass * 2 * T * 256, tk + 2 * pass, t.d_status, nullptr);
         FMM_CUDA(cudaGetLastError());
         src = dst;
     }
     *res = 0;
     if (!full) {  // the runs: values 0/1 -> 2/3
-        k_sort_runs<<<dim3(nblk(n, 256), 2), 256, 0, s>>>(t.d_keys[0], t.d_vals[0], t.d_keys[1], t.d_vals[1],
-                                                         t.d_vals[2], t.d_vals[3], n, side0, nz0, t.d_status);
+        launch_dep(true, k_sort_runs, dim3(nblk(n, 256), 2), 256, 0, s,
+                   t.d_keys[0], t.d_vals[0], t.d_keys[1], t.d_vals[1], t.d_vals[2], t.d_vals[3], n, side0, nz0,
+                   t.d_status);
         FMM_CUDA(cudaGetLastError());
         *res = 2;
     }
@@ -698,6 +704,7 @@ static fmm_status sort_coordinates(Tree& t, cudaStream_t s, const double2* xy, b
 // when its offset inside its segment is >= nzero of that segment.
 __global__ void k_mark(const int32_t* __restrict__ A, int n, const int32_t* __restrict__ start,
                        const int32_t* __restrict__ nzero, int K, uint8_t* side) {
+    pdl_entry();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int k = find_seg(start, K, i);
@@ -796,6 +803,7 @@ __global__ void __launch_bounds__(kPartThreads) k_part_fused(
     const int32_t* __restrict__ nzero, const int32_t* __restrict__ obefore, int K, int32_t* __restrict__ out,
     const int32_t* __restrict__ nstart, const int32_t* __restrict__ nnzero, int nK, uint8_t* __restrict__ side_next,
     int direct_next, unsigned long long* tstat, int T, unsigned* status) {
+    pdl_entry();
     __shared__ int wsum[32];
     __shared__ int sh_tile;
     __shared__ long long sh_excl;
@@ -872,10 +880,10 @@ static fmm_status partition(Tree& t, cudaStream_t s, int stage, const int32_t* A
     const int n = (int)t.n;
     const int T = nblk(n, kPartTile);
     const int grid = std::min(T, t.num_sms * 4);
-    k_part_fused<<<grid, kPartThreads, 0, s>>>(A, side, n, seg.d_start, seg.d_nzero, seg.d_obefore, seg.K, out,
-                                               next ? next->d_start : nullptr, next ? next->d_nzero : nullptr,
-                                               next ? next->K : 0, next ? side_next : nullptr, t.ninst == 1 ? 1 : 0,
-                                               t.d_part_stat + (size_t)stage * (T + 1), T, t.d_status);
+    launch_dep(true, k_part_fused, grid, kPartThreads, 0, s,
+               A, side, n, seg.d_start, seg.d_nzero, seg.d_obefore, seg.K, out, next ? next->d_start : nullptr,
+               next ? next->d_nzero : nullptr, next ? next->K : 0, next ? side_next : nullptr, t.ninst == 1 ? 1 : 0,
+               t.d_part_stat + (size_t)stage * (T + 1), T, t.d_status);
     FMM_CUDA(cudaGetLastError());
     return FMM_OK;
 }
@@ -890,6 +898,7 @@ __global__ void k_geom(const int32_t* __restrict__ ids, int cnt, const int32_t* 
                        const int32_t* __restrict__ bstart, const int32_t* __restrict__ bcount,
                        const int32_t* __restrict__ inst, const int64_t* __restrict__ inst_box_off, double2* center,
                        double* radius, double* rho, float4* chl, float* rho32, float* rad32, int is_root_level) {
+    pdl_entry();
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= cnt) return;
     const int b = ids[q];
@@ -1013,6 +1022,7 @@ __global__ void __launch_bounds__(kSubThreads) k_subtree(
     const int32_t* __restrict__ inst, const int64_t* __restrict__ inst_box_off, const int32_t* __restrict__ inst_levels,
     int32_t* __restrict__ loc, double2* center, double* radius, double* rho, float4* chl, float* rho32, float* rad32,
     unsigned* status) {
+    pdl_entry();
     __shared__ uint16_t buf[3][kSubMax];
     // per local id: its box (then half box) numbered within the subtree level, and during a split
     // 2 * that + the side it goes to
@@ -1119,6 +1129,7 @@ __global__ void k_target_slots(const int32_t* __restrict__ leaves, int nleaf, co
                                const int32_t* __restrict__ bcount, const int32_t* __restrict__ pslot,
                                const int32_t* __restrict__ Y, int n_src, int32_t* __restrict__ slot_of,
                                int32_t* __restrict__ nsrc) {
+    pdl_entry();
     const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (w >= nleaf) return;  // warp-uniform
@@ -1154,6 +1165,7 @@ __global__ void k_finalize(const int32_t* __restrict__ Y, int n, const double2* 
                            const double2* __restrict__ center, int32_t* perm, double2* pts, float4* pos4,
                            const int32_t* __restrict__ leaf_of, const int32_t* __restrict__ slot_of, float* posp32,
                            double2* posp64) {
+    pdl_entry();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int id = Y[i];
@@ -1194,6 +1206,7 @@ __global__ void k_lists_root(const int64_t* __restrict__ inst_box_off, int ninst
                              int32_t* sidx, int32_t* sowner, int32_t* woff, int32_t* nw,
                              unsigned long long* lvl_base, const int32_t* __restrict__ child0,
                              const int32_t* __restrict__ pslot, const int32_t* __restrict__ bcount, int2* srng) {
+    pdl_entry();
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b == 0) {
         lvl_base[0] = 0;             // strong entries of level 0 start at 0
@@ -1304,6 +1317,7 @@ __global__ void __launch_bounds__(kLThreads) k_lists_level(
     const float* __restrict__ rad32, const double2* __restrict__ center, const double* __restrict__ radius,
     double theta, unsigned long long* tstat, long long tiles_cap, long long scap, long long wcap,
     unsigned long long* need, unsigned* status) {
+    pdl_entry();
     __shared__ int ws[32];
     __shared__ long long sh_excl[2];
     __shared__ long long sh_tile;
@@ -1463,6 +1477,7 @@ __global__ void k_items(int nbox, const int32_t* __restrict__ child0, const int3
                         int2* box_m2l,
                         long long m2l_cap, int K, unsigned long long* rowctr, int32_t* rows, int2* box_tail,
                         unsigned* status, int item_sources) {
+    pdl_entry();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     // lists that overflowed or whose build gave up: no items (the counters stay zero)
     if (*((volatile unsigned*)status) & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW | ST_TIMEOUT | ST_INTERNAL)) return;
@@ -1523,6 +1538,7 @@ static_assert(kM2LItemPairsMax == 256, "k_m2l_rows: one thread per item length i
 __global__ void k_m2l_rows(int nbox, const int2* __restrict__ box_m2l, const int2* __restrict__ box_tail,
                            const unsigned long long* __restrict__ rowctr, long long m2l_cap, int32_t* rows,
                            unsigned long long* item_ctr, unsigned long long* need, unsigned* status) {
+    pdl_entry();
     __shared__ unsigned long long base[kM2LItemPairsMax];
     __shared__ int wsum[32];
     const unsigned st0 = *((volatile unsigned*)status);
@@ -1694,6 +1710,10 @@ fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s) {
     int src = 0;
     fmm_status st;
     const int lglob = std::min(t.l0, t.Lmax - 1);  // levels split by the global passes
+    // the zeroing comes first, so that the build's kernels follow one another directly (launch_dep)
+    if (lglob > 0)
+        FMM_CUDA(cudaMemsetAsync(t.d_part_stat, 0,
+                                 (size_t)2 * lglob * (nblk(n, kPartTile) + 1) * sizeof(unsigned long long), s));
     bool marked = false;                           // side flags of the first cut already written
     if (n < (1 << 30)) {  // onesweep passes (30-bit counts in the tile status words); keys formed in the first
         // the short sort (high halves + runs) for single trees, which also flags the root's x cut; a forest's
@@ -1723,17 +1743,15 @@ fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s) {
     int32_t* X2 = t.d_X2;
     int32_t* Y2 = t.d_Y2;
     const LevelList& L0 = t.level_boxes[0];
-    k_geom<<<nblk(L0.count, 128), 128, 0, s>>>(L0.d_ids, L0.count, X, Y, xy, t.d_bstart, t.d_bcount, t.d_inst,
-                                               t.d_inst_boxoff, t.d_center, t.d_radius, t.d_rho, t.d_chl, t.d_rho32,
-                                               t.d_rad32, 1);
+    launch_dep(true, k_geom, nblk(L0.count, 128), 128, 0, s,
+               L0.d_ids, L0.count, X, Y, xy, t.d_bstart, t.d_bcount, t.d_inst, t.d_inst_boxoff, t.d_center,
+               t.d_radius, t.d_rho, t.d_chl, t.d_rho32, t.d_rad32, 1);
     FMM_CUDA(cudaGetLastError());
     if (lglob > 0 && !marked) {  // flags of the first cut (x, level 0); later cuts get theirs from the stage before
         const SegTable& sx = t.seg_x[0];
-        k_mark<<<nblk(n, 256), 256, 0, s>>>(X, n, sx.d_start, sx.d_nzero, sx.K, t.d_sideX);
+        launch_dep(true, k_mark, nblk(n, 256), 256, 0, s,
+                   X, n, sx.d_start, sx.d_nzero, sx.K, t.d_sideX);
     }
-    if (lglob > 0)
-        FMM_CUDA(cudaMemsetAsync(t.d_part_stat, 0,
-                                 (size_t)2 * lglob * (nblk(n, kPartTile) + 1) * sizeof(unsigned long long), s));
     for (int l = 0; l < lglob; ++l) {
         const SegTable& sx = t.seg_x[l];
         const SegTable& sy = t.seg_y[l];
@@ -1745,27 +1763,28 @@ fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s) {
         if ((st = partition(t, s, 2 * l + 1, X, t.d_sideY, sy, X2, nxt, t.d_sideX))) return st;
         std::swap(X, X2);
         const LevelList& Ll = t.level_boxes[l + 1];
-        k_geom<<<nblk(Ll.count, 128), 128, 0, s>>>(Ll.d_ids, Ll.count, X, Y, xy, t.d_bstart, t.d_bcount, t.d_inst,
-                                                   t.d_inst_boxoff, t.d_center, t.d_radius, t.d_rho, t.d_chl,
-                                                   t.d_rho32, t.d_rad32, 0);
+        launch_dep(true, k_geom, nblk(Ll.count, 128), 128, 0, s,
+                   Ll.d_ids, Ll.count, X, Y, xy, t.d_bstart, t.d_bcount, t.d_inst, t.d_inst_boxoff, t.d_center,
+                   t.d_radius, t.d_rho, t.d_chl, t.d_rho32, t.d_rad32, 0);
         FMM_CUDA(cudaGetLastError());
     }
     if (lglob < t.Lmax - 1 && t.level_parents[lglob].count > 0) {
         // every remaining split inside one CTA per box of level l0
         const LevelList& Lp = t.level_parents[lglob];
-        k_subtree<<<Lp.count, kSubThreads, 0, s>>>(Lp.d_ids, Lp.count, lglob, X, Y, xy, t.d_bstart, t.d_bcount,
-                                                   t.d_inst, t.d_inst_boxoff, t.d_inst_levels, t.d_loc, t.d_center,
-                                                   t.d_radius, t.d_rho, t.d_chl, t.d_rho32, t.d_rad32, t.d_status);
+        launch_dep(true, k_subtree, Lp.count, kSubThreads, 0, s,
+                   Lp.d_ids, Lp.count, lglob, X, Y, xy, t.d_bstart, t.d_bcount, t.d_inst, t.d_inst_boxoff,
+                   t.d_inst_levels, t.d_loc, t.d_center, t.d_radius, t.d_rho, t.d_chl, t.d_rho32, t.d_rad32,
+                   t.d_status);
         FMM_CUDA(cudaGetLastError());
     }
     const bool f32 = t.path == FMM_PATH_FP32;
     if (t.n_src > 0)
-        k_target_slots<<<nblk(32 * t.nleaf, 128), 128, 0, s>>>(t.leaves.d_ids, (int)t.nleaf, t.d_bstart, t.d_bcount,
-                                                                t.d_pslot, Y, (int)t.n_src, t.d_slot_of, t.d_nsrc);
-    k_finalize<<<nblk(n, 256), 256, 0, s>>>(Y, n, xy, t.d_inst, t.d_inst_boxoff, t.d_center, t.d_perm, t.d_pts,
-                                            t.d_pos4, t.d_leaf_of, t.d_slot_of,
-                                            f32 ? static_cast<float*>(t.d_posp) : nullptr,
-                                            f32 ? nullptr : static_cast<double2*>(t.d_posp));
+        launch_dep(true, k_target_slots, nblk(32 * t.nleaf, 128), 128, 0, s,
+                   t.leaves.d_ids, (int)t.nleaf, t.d_bstart, t.d_bcount, t.d_pslot, Y, (int)t.n_src, t.d_slot_of,
+                   t.d_nsrc);
+    launch_dep(true, k_finalize, nblk(n, 256), 256, 0, s,
+               Y, n, xy, t.d_inst, t.d_inst_boxoff, t.d_center, t.d_perm, t.d_pts, t.d_pos4, t.d_leaf_of, t.d_slot_of,
+               f32 ? static_cast<float*>(t.d_posp) : nullptr, f32 ? nullptr : static_cast<double2*>(t.d_posp));
     FMM_CUDA(cudaGetLastError());
     return FMM_OK;
 }
@@ -1775,32 +1794,30 @@ fmm_status run_lists(Tree& t, cudaStream_t s) {
     unsigned long long* need = t.d_lvl_base + 2 * kMaxLevels;
     FMM_CUDA(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), s));
     FMM_CUDA(cudaMemsetAsync(need, 0, 6 * sizeof(unsigned long long), s));
-    // P2P sources of a leaf: its points, or with separate evaluation points its sources only
-    const int32_t* srccount = t.n_src > 0 ? t.d_nsrc : t.d_bcount;
-    k_lists_root<<<nblk(t.ninst, 128), 128, 0, s>>>(t.d_inst_boxoff, t.ninst, t.d_soff, t.d_ns, t.d_sidx, t.d_sowner,
-                                                    t.d_woff, t.d_nw, t.d_lvl_base, t.d_child0, t.d_pslot,
-                                                    srccount, t.d_srng);
     const long long tiles_cap = t.cand_cap / kLTile + 2;
     const size_t lstride = (size_t)(2 * tiles_cap + 1);  // status words + ticket of one level
-    const int grid = t.num_sms * 8;
     FMM_CUDA(cudaMemsetAsync(t.d_ltstat, 0, lstride * (size_t)std::max(t.Lmax - 1, 1) * sizeof(unsigned long long),
                              s));
-    for (int l = 1; l < t.Lmax; ++l) {
-        k_lists_level<<<grid, kLThreads, 0, s>>>(l, t.d_lvl_base, t.d_sowner, t.d_soff, t.d_ns, t.d_sidx, t.d_woff,
-                                                 t.d_nw, t.d_widx, t.d_child0, t.d_pslot, srccount, t.d_srng,
-                                                 t.d_chl, t.d_rad32, t.d_center, t.d_radius, t.theta,
-                                                 t.d_ltstat + lstride * (size_t)(l - 1), tiles_cap, t.scap_tot,
-                                                 t.wcap_tot, need, t.d_status);
-    }
     FMM_CUDA(cudaMemsetAsync(t.d_m2l_rowctr, 0, (kM2LItemPairsMax + 4) * sizeof(unsigned long long), s));
-    k_items<<<nblk(t.nbox, 128), 128, 0, s>>>((int)t.nbox, t.d_child0, t.d_bcount, t.d_soff, t.d_ns, t.d_woff,
-                                              t.d_nw, ctr,
-                                              t.d_p2p_items, t.d_p2p_rows, t.d_leaf_items, t.p2p_cap,
-                                              t.d_m2l_items, t.d_box_m2l,
-                                              t.m2l_cap, m2l_item_pairs(t), t.d_m2l_rowctr, t.d_m2l_rows,
-                                              t.d_box_tail, t.d_status, p2p_item_sources(t.n));
-    k_m2l_rows<<<nblk(t.nbox, 256), 256, 0, s>>>((int)t.nbox, t.d_box_m2l, t.d_box_tail, t.d_m2l_rowctr, t.m2l_cap,
-                                                 t.d_m2l_rows, ctr + 2, need, t.d_status);
+    // P2P sources of a leaf: its points, or with separate evaluation points its sources only
+    const int32_t* srccount = t.n_src > 0 ? t.d_nsrc : t.d_bcount;
+    launch_dep(false, k_lists_root, nblk(t.ninst, 128), 128, 0, s,
+               t.d_inst_boxoff, t.ninst, t.d_soff, t.d_ns, t.d_sidx, t.d_sowner, t.d_woff, t.d_nw, t.d_lvl_base,
+               t.d_child0, t.d_pslot, srccount, t.d_srng);
+    const int grid = t.num_sms * 8;
+    for (int l = 1; l < t.Lmax; ++l) {
+        launch_dep(true, k_lists_level, grid, kLThreads, 0, s,
+                   l, t.d_lvl_base, t.d_sowner, t.d_soff, t.d_ns, t.d_sidx, t.d_woff, t.d_nw, t.d_widx, t.d_child0,
+                   t.d_pslot, srccount, t.d_srng, t.d_chl, t.d_rad32, t.d_center, t.d_radius, t.theta,
+                   t.d_ltstat + lstride * (size_t)(l - 1), tiles_cap, t.scap_tot, t.wcap_tot, need, t.d_status);
+    }
+    launch_dep(true, k_items, nblk(t.nbox, 128), 128, 0, s,
+               (int)t.nbox, t.d_child0, t.d_bcount, t.d_soff, t.d_ns, t.d_woff, t.d_nw, ctr, t.d_p2p_items,
+               t.d_p2p_rows, t.d_leaf_items, t.p2p_cap, t.d_m2l_items, t.d_box_m2l, t.m2l_cap, m2l_item_pairs(t),
+               t.d_m2l_rowctr, t.d_m2l_rows, t.d_box_tail, t.d_status, p2p_item_sources(t.n));
+    launch_dep(true, k_m2l_rows, nblk(t.nbox, 256), 256, 0, s,
+               (int)t.nbox, t.d_box_m2l, t.d_box_tail, t.d_m2l_rowctr, t.m2l_cap, t.d_m2l_rows, ctr + 2, need,
+               t.d_status);
     FMM_CUDA(cudaGetLastError());
     return FMM_OK;
 }

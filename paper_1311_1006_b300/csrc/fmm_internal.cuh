@@ -23,6 +23,10 @@ __device__ __forceinline__ void pdl_entry() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
+// The wait alone: the next kernel is scheduled only as this one's CTAs exit.
+// The list passes take it, because the far-field stream's upward pass runs
+// beside them and waiting CTAs of the next list pass would hold its SM slots.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 template <typename... K, typename... A>
 inline cudaError_t launch_dep(bool dep, void (*k)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                               A&&... args) {

@@ -1206,7 +1206,7 @@ __global__ void k_lists_root(const int64_t* __restrict__ inst_box_off, int ninst
                              int32_t* sidx, int32_t* sowner, int32_t* woff, int32_t* nw,
                              unsigned long long* lvl_base, const int32_t* __restrict__ child0,
                              const int32_t* __restrict__ pslot, const int32_t* __restrict__ bcount, int2* srng) {
-    pdl_entry();
+    pdl_wait();
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b == 0) {
         lvl_base[0] = 0;             // strong entries of level 0 start at 0
@@ -1317,7 +1317,7 @@ __global__ void __launch_bounds__(kLThreads) k_lists_level(
     const float* __restrict__ rad32, const double2* __restrict__ center, const double* __restrict__ radius,
     double theta, unsigned long long* tstat, long long tiles_cap, long long scap, long long wcap,
     unsigned long long* need, unsigned* status) {
-    pdl_entry();
+    pdl_wait();
     __shared__ int ws[32];
     __shared__ long long sh_excl[2];
     __shared__ long long sh_tile;
@@ -1477,7 +1477,7 @@ __global__ void k_items(int nbox, const int32_t* __restrict__ child0, const int3
                         int2* box_m2l,
                         long long m2l_cap, int K, unsigned long long* rowctr, int32_t* rows, int2* box_tail,
                         unsigned* status, int item_sources) {
-    pdl_entry();
+    pdl_wait();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     // lists that overflowed or whose build gave up: no items (the counters stay zero)
     if (*((volatile unsigned*)status) & (ST_STRONG_OVERFLOW | ST_WEAK_OVERFLOW | ST_TIMEOUT | ST_INTERNAL)) return;
@@ -1538,7 +1538,7 @@ static_assert(kM2LItemPairsMax == 256, "k_m2l_rows: one thread per item length i
 __global__ void k_m2l_rows(int nbox, const int2* __restrict__ box_m2l, const int2* __restrict__ box_tail,
                            const unsigned long long* __restrict__ rowctr, long long m2l_cap, int32_t* rows,
                            unsigned long long* item_ctr, unsigned long long* need, unsigned* status) {
-    pdl_entry();
+    pdl_wait();
     __shared__ unsigned long long base[kM2LItemPairsMax];
     __shared__ int wsum[32];
     const unsigned st0 = *((volatile unsigned*)status);

@@ -698,6 +698,65 @@ static fmm_status sort_coordinates(Tree& t, cudaStream_t s, const double2* xy, b
     return FMM_OK;
 }
 
+// ================================================================ geometry
+
+// Box geometry from the first/last entries of the box's x- and y-lists:
+// centre = midpoint of the tight bounding box, radius = half its diagonal
+// (FP64 with explicit rounding, no contraction, so values are reproducible).
+// One level's boxes (ids[0..cnt)) with that level's lists X and Y.
+struct GeomArgs {
+    const int32_t* ids;
+    int cnt;
+    const int32_t* X;
+    const int32_t* Y;
+    const double2* xy;
+    const int32_t* bstart;
+    const int32_t* bcount;
+    const int32_t* inst;
+    const int64_t* inst_box_off;
+    double2* center;
+    double* radius;
+    double* rho;
+    float4* chl;
+    float* rho32;
+    float* rad32;
+    int is_root_level;
+};
+
+__device__ __forceinline__ void geom_box(const GeomArgs& g, int q) {
+    const int b = g.ids[q];
+    const int s = g.bstart[b], e = s + g.bcount[b] - 1;
+    const double x0 = g.xy[g.X[s]].x, x1 = g.xy[g.X[e]].x;
+    const double y0 = g.xy[g.Y[s]].y, y1 = g.xy[g.Y[e]].y;
+    const double cx = __dmul_rn(0.5, __dadd_rn(x0, x1));
+    const double cy = __dmul_rn(0.5, __dadd_rn(y0, y1));
+    const double dx = __dsub_rn(x1, x0), dy = __dsub_rn(y1, y0);
+    const double r = __dmul_rn(0.5, __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy))));
+    g.center[b] = make_double2(cx, cy);
+    g.radius[b] = r;
+    g.rad32[b] = __double2float_rn(r);
+    // Scale radius of the expansions: the bbox radius, floored at 2^-24 of the
+    // instance's root radius so that a box of coincident points still keeps a
+    // usable local-expansion derivative; rounded to FP32 so both precisions
+    // scale by the same number.
+    double ox = cx, oy = cy, rfloor = 0.0;
+    if (!g.is_root_level) {
+        const int root = (int)g.inst_box_off[g.inst[b]];
+        const double2 o = g.center[root];
+        ox = o.x;
+        oy = o.y;
+        rfloor = ldexp(g.radius[root], -24);
+    }
+    const double rs = r > rfloor ? r : rfloor;
+    const float r32 = rs >= 1e-30 ? __double2float_rn(rs) : 0.0f;
+    g.rho32[b] = r32;
+    g.rho[b] = (double)r32;
+    const double ex = __dsub_rn(cx, ox), ey = __dsub_rn(cy, oy);
+    const float hx = __double2float_rn(ex), hy = __double2float_rn(ey);
+    g.chl[b] = make_float4(hx, hy, __double2float_rn(__dsub_rn(ex, (double)hx)),
+                           __double2float_rn(__dsub_rn(ey, (double)hy)));
+}
+
 // ======================================================= segmented partition
 
 // Side flags of a contiguous cut: entry at position i of list A goes to side 1
@@ -802,7 +861,7 @@ __global__ void __launch_bounds__(kPartThreads) k_part_fused(
     const int32_t* __restrict__ A, const uint8_t* __restrict__ side, int n, const int32_t* __restrict__ start,
     const int32_t* __restrict__ nzero, const int32_t* __restrict__ obefore, int K, int32_t* __restrict__ out,
     const int32_t* __restrict__ nstart, const int32_t* __restrict__ nnzero, int nK, uint8_t* __restrict__ side_next,
-    int direct_next, unsigned long long* tstat, int T, unsigned* status) {
+    int direct_next, unsigned long long* tstat, int T, unsigned* status, GeomArgs geo) {
     pdl_entry();
     __shared__ int wsum[32];
     __shared__ int sh_tile;
@@ -869,69 +928,35 @@ __global__ void __launch_bounds__(kPartThreads) k_part_fused(
             P += f[j];
         }
     }
+    // the geometry of the level whose lists this stage reads (none: geo.cnt = 0), after the tiles, so that no
+    // tile waits on it; it takes the place of a launch between the stages
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < geo.cnt; q += gridDim.x * blockDim.x) geom_box(geo, q);
 }
 
 // One stage: partition A by side (segments of `seg`) into out; with `next`,
 // also the flags of the next stage's cut of out.
 // Stage `stage` uses its own region of tile status words (T + 1 each, zeroed
 // together before the first stage of a build).
+// geo: the geometry the stage's CTAs compute after their tiles (geo.cnt = 0: none).
 static fmm_status partition(Tree& t, cudaStream_t s, int stage, const int32_t* A, const uint8_t* side,
-                            const SegTable& seg, int32_t* out, const SegTable* next, uint8_t* side_next) {
+                            const SegTable& seg, int32_t* out, const SegTable* next, uint8_t* side_next,
+                            const GeomArgs& geo) {
     const int n = (int)t.n;
     const int T = nblk(n, kPartTile);
     const int grid = std::min(T, t.num_sms * 4);
     launch_dep(true, k_part_fused, grid, kPartThreads, 0, s,
                A, side, n, seg.d_start, seg.d_nzero, seg.d_obefore, seg.K, out, next ? next->d_start : nullptr,
                next ? next->d_nzero : nullptr, next ? next->K : 0, next ? side_next : nullptr, t.ninst == 1 ? 1 : 0,
-               t.d_part_stat + (size_t)stage * (T + 1), T, t.d_status);
+               t.d_part_stat + (size_t)stage * (T + 1), T, t.d_status, geo);
     FMM_CUDA(cudaGetLastError());
     return FMM_OK;
 }
 
-// ================================================================ geometry
-
-// Box geometry from the first/last entries of the box's x- and y-lists:
-// centre = midpoint of the tight bounding box, radius = half its diagonal
-// (FP64 with explicit rounding, no contraction, so values are reproducible).
-__global__ void k_geom(const int32_t* __restrict__ ids, int cnt, const int32_t* __restrict__ X,
-                       const int32_t* __restrict__ Y, const double2* __restrict__ xy,
-                       const int32_t* __restrict__ bstart, const int32_t* __restrict__ bcount,
-                       const int32_t* __restrict__ inst, const int64_t* __restrict__ inst_box_off, double2* center,
-                       double* radius, double* rho, float4* chl, float* rho32, float* rad32, int is_root_level) {
+// One thread per box of a level whose geometry no partition stage carries.
+__global__ void k_geom(GeomArgs g) {
     pdl_entry();
-    int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= cnt) return;
-    const int b = ids[q];
-    const int s = bstart[b], e = s + bcount[b] - 1;
-    const double x0 = xy[X[s]].x, x1 = xy[X[e]].x;
-    const double y0 = xy[Y[s]].y, y1 = xy[Y[e]].y;
-    const double cx = __dmul_rn(0.5, __dadd_rn(x0, x1));
-    const double cy = __dmul_rn(0.5, __dadd_rn(y0, y1));
-    const double dx = __dsub_rn(x1, x0), dy = __dsub_rn(y1, y0);
-    const double r = __dmul_rn(0.5, __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy))));
-    center[b] = make_double2(cx, cy);
-    radius[b] = r;
-    rad32[b] = __double2float_rn(r);
-    // Scale radius of the expansions: the bbox radius, floored at 2^-24 of the
-    // instance's root radius so that a box of coincident points still keeps a
-    // usable local-expansion derivative; rounded to FP32 so both precisions
-    // scale by the same number.
-    double ox = cx, oy = cy, rfloor = 0.0;
-    if (!is_root_level) {
-        const int root = (int)inst_box_off[inst[b]];
-        const double2 o = center[root];
-        ox = o.x;
-        oy = o.y;
-        rfloor = ldexp(radius[root], -24);
-    }
-    const double rs = r > rfloor ? r : rfloor;
-    const float r32 = rs >= 1e-30 ? __double2float_rn(rs) : 0.0f;
-    rho32[b] = r32;
-    rho[b] = (double)r32;
-    const double ex = __dsub_rn(cx, ox), ey = __dsub_rn(cy, oy);
-    const float hx = __double2float_rn(ex), hy = __double2float_rn(ey);
-    chl[b] = make_float4(hx, hy, __double2float_rn(__dsub_rn(ex, (double)hx)),
-                         __double2float_rn(__dsub_rn(ey, (double)hy)));
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < g.cnt) geom_box(g, q);
 }
 
 // ============================================== subtree splits in one CTA
@@ -1742,11 +1767,31 @@ fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s) {
     int32_t* Y = t.d_vals[src + 1];
     int32_t* X2 = t.d_X2;
     int32_t* Y2 = t.d_Y2;
-    const LevelList& L0 = t.level_boxes[0];
-    launch_dep(true, k_geom, nblk(L0.count, 128), 128, 0, s,
-               L0.d_ids, L0.count, X, Y, xy, t.d_bstart, t.d_bcount, t.d_inst, t.d_inst_boxoff, t.d_center,
-               t.d_radius, t.d_rho, t.d_chl, t.d_rho32, t.d_rad32, 1);
-    FMM_CUDA(cudaGetLastError());
+    // geometry of level l from its lists: carried by the stage that cuts level l in x (which reads Y and
+    // leaves X untouched); level lglob, which no global stage cuts, by k_geom
+    auto geometry = [&](int l, const int32_t* Xl, const int32_t* Yl) {
+        const LevelList& Ll = t.level_boxes[l];
+        GeomArgs g;
+        g.ids = Ll.d_ids;
+        g.cnt = (int)Ll.count;
+        g.X = Xl;
+        g.Y = Yl;
+        g.xy = xy;
+        g.bstart = t.d_bstart;
+        g.bcount = t.d_bcount;
+        g.inst = t.d_inst;
+        g.inst_box_off = t.d_inst_boxoff;
+        g.center = t.d_center;
+        g.radius = t.d_radius;
+        g.rho = t.d_rho;
+        g.chl = t.d_chl;
+        g.rho32 = t.d_rho32;
+        g.rad32 = t.d_rad32;
+        g.is_root_level = l == 0 ? 1 : 0;
+        return g;
+    };
+    GeomArgs none = geometry(0, X, Y);
+    none.cnt = 0;
     if (lglob > 0 && !marked) {  // flags of the first cut (x, level 0); later cuts get theirs from the stage before
         const SegTable& sx = t.seg_x[0];
         launch_dep(true, k_mark, nblk(n, 256), 256, 0, s,
@@ -1756,16 +1801,16 @@ fmm_status run_tree_build(Tree& t, const double* d_xy, cudaStream_t s) {
         const SegTable& sx = t.seg_x[l];
         const SegTable& sy = t.seg_y[l];
         // x-cut: Y partitioned by the x-side flags; the y-cut flags come from Y's new order
-        if ((st = partition(t, s, 2 * l, Y, t.d_sideX, sx, Y2, &sy, t.d_sideY))) return st;
+        if ((st = partition(t, s, 2 * l, Y, t.d_sideX, sx, Y2, &sy, t.d_sideY, geometry(l, X, Y)))) return st;
         std::swap(Y, Y2);
         // y-cut: X partitioned by the y-side flags; the next level's x-cut flags come from X's new order
         const SegTable* nxt = l + 1 < lglob ? &t.seg_x[l + 1] : nullptr;
-        if ((st = partition(t, s, 2 * l + 1, X, t.d_sideY, sy, X2, nxt, t.d_sideX))) return st;
+        if ((st = partition(t, s, 2 * l + 1, X, t.d_sideY, sy, X2, nxt, t.d_sideX, none))) return st;
         std::swap(X, X2);
-        const LevelList& Ll = t.level_boxes[l + 1];
-        launch_dep(true, k_geom, nblk(Ll.count, 128), 128, 0, s,
-                   Ll.d_ids, Ll.count, X, Y, xy, t.d_bstart, t.d_bcount, t.d_inst, t.d_inst_boxoff, t.d_center,
-                   t.d_radius, t.d_rho, t.d_chl, t.d_rho32, t.d_rad32, 0);
+    }
+    const GeomArgs gl = geometry(lglob, X, Y);
+    if (gl.cnt > 0) {
+        launch_dep(true, k_geom, nblk(gl.cnt, 128), 128, 0, s, gl);
         FMM_CUDA(cudaGetLastError());
     }
     if (lglob < t.Lmax - 1 && t.level_parents[lglob].count > 0) {

@@ -102,7 +102,7 @@ constexpr int kM2LTcRows = 128;  // work items (MMA rows) per CTA of the tensor-
 
 // Partition tile: 256 threads x 8 consecutive positions.
 constexpr int kPartThreads = 256;
-constexpr int kPartItems = 8;
+constexpr int kPartItems = 4;  // measured: 4 beats 8 (rebuild 1.062 -> 1.034 ms), 2, 3 and 6; 128 threads x 4 slower
 constexpr int kPartTile = kPartThreads * kPartItems;
 
 // Radix sort tile: 256 threads x 8 rounds.

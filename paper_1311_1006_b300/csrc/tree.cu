@@ -943,7 +943,7 @@ static fmm_status partition(Tree& t, cudaStream_t s, int stage, const int32_t* A
                             const GeomArgs& geo) {
     const int n = (int)t.n;
     const int T = nblk(n, kPartTile);
-    const int grid = std::min(T, t.num_sms * 4);
+    const int grid = std::min(T, t.num_sms * 8);  // a CTA per tile up to 8 per SM: more warps to hide the load chain
     launch_dep(true, k_part_fused, grid, kPartThreads, 0, s,
                A, side, n, seg.d_start, seg.d_nzero, seg.d_obefore, seg.K, out, next ? next->d_start : nullptr,
                next ? next->d_nzero : nullptr, next ? next->K : 0, next ? side_next : nullptr, t.ninst == 1 ? 1 : 0,

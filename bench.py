@@ -584,8 +584,8 @@ def run_gpu(args):
         phases = _phases(F.FMM_FLAG_TIMING)
         phases_alone = _phases(F.FMM_FLAG_TIMING | F.FMM_FLAG_SERIAL)
         tree.rebuild(X, flags=0)
-        build_ms = float(np.median(_timed_ms(lambda: tree.rebuild(X), 5, stream, flush)))
-        eval_ms = float(np.median(_timed_ms(lambda: tree.eval(G, out=phi), 5, stream, flush)))
+        build_ms = float(np.median(_timed_ms(lambda: tree.rebuild(X), 15, stream, flush)))
+        eval_ms = float(np.median(_timed_ms(lambda: tree.eval(G, out=phi), 15, stream, flush)))
 
         # --- accuracy on sampled points vs the exact sum (oracle) -----------------
         orc = None

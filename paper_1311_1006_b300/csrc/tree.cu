@@ -876,8 +876,7 @@ __global__ void __launch_bounds__(kPartThreads) k_part_fused(
     while (true) {
         if (threadIdx.x == 0) sh_tile = (int)atomicAdd(ticket, 1ull);
         __syncthreads();
-        const int t = sh_tile;
-        __syncthreads();
+        const int t = sh_tile;  // rewritten only after the scan's barriers of this tile
         if (t >= T) break;
         const int i0 = t * kPartTile + threadIdx.x * kPartItems;
         int f[kPartItems], a[kPartItems];
@@ -890,7 +889,7 @@ __global__ void __launch_bounds__(kPartThreads) k_part_fused(
             sum += f[j];
         }
         int total;
-        const int excl = block_excl_scan(sum, wsum, total);
+        const int excl = block_excl_scan_nb(sum, wsum, total);  // the barrier after the look-back closes it
         if (threadIdx.x < 32) {
             const unsigned long long pre = warp_lookback(tstat, t, (unsigned long long)total, status);
             if (threadIdx.x == 0) sh_excl = (long long)pre;
@@ -1461,34 +1460,52 @@ __global__ void __launch_bounds__(kLThreads) k_lists_level(
 // partial sums are added in item order later (deterministic).
 // int4 item = (box, list begin, list end, first item of the box or -1 when
 // the box has a single item).
-// One atomic per warp and counter: lanes reserve k0, k1, k2 entries from three
-// global counters; the scans come first, then lane 31's three atomics back to
-// back (their latencies overlap instead of adding up).
-__device__ __forceinline__ void warp_reserve3(unsigned long long* c0, int k0, unsigned long long* c1, int k1,
-                                              unsigned long long* c2, int k2, unsigned long long& b0,
-                                              unsigned long long& b1, unsigned long long& b2) {
-    const int lane = threadIdx.x & 31;
-    int i0 = k0, i1 = k1, i2 = k2;
+// One atomic per block and counter: the block's threads reserve k[q] entries
+// from the global counters c[q] (q < 5; a zero block total issues no atomic)
+// and get their first entries in b[q], in thread order.  Two block barriers.
+__device__ __forceinline__ void block_reserve5(unsigned long long* const (&c)[5], const int (&k)[5],
+                                               unsigned long long (&b)[5]) {
+    __shared__ int wtot[5][32];
+    __shared__ unsigned long long base[5];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) incl[q] = k[q];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const int y0 = __shfl_up_sync(0xffffffffu, i0, o);
-        const int y1 = __shfl_up_sync(0xffffffffu, i1, o);
-        const int y2 = __shfl_up_sync(0xffffffffu, i2, o);
-        if (lane >= o) {
-            i0 += y0;
-            i1 += y1;
-            i2 += y2;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const int y = __shfl_up_sync(0xffffffffu, incl[q], o);
+            if (lane >= o) incl[q] += y;
         }
     }
-    unsigned long long a0 = 0, a1 = 0, a2 = 0;
     if (lane == 31) {
-        if (i0 > 0) a0 = atomicAdd(c0, (unsigned long long)i0);
-        if (i1 > 0) a1 = atomicAdd(c1, (unsigned long long)i1);
-        if (i2 > 0) a2 = atomicAdd(c2, (unsigned long long)i2);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) wtot[q][w] = incl[q];
     }
-    b0 = __shfl_sync(0xffffffffu, a0, 31) + (unsigned long long)(i0 - k0);
-    b1 = __shfl_sync(0xffffffffu, a1, 31) + (unsigned long long)(i1 - k1);
-    b2 = __shfl_sync(0xffffffffu, a2, 31) + (unsigned long long)(i2 - k2);
+    __syncthreads();
+    if (w == 0) {
+        int tot[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            int v = lane < nw ? wtot[q][lane] : 0;
+            int x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane < nw) wtot[q][lane] = x - v;  // warps before this one
+            tot[q] = __shfl_sync(0xffffffffu, x, 31);
+        }
+        // lanes 0-4 issue the block's atomics side by side
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+            if (lane == q) base[q] = tot[q] > 0 ? atomicAdd(c[q], (unsigned long long)tot[q]) : 0ull;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 5; ++q) b[q] = base[q] + (unsigned long long)(wtot[q][w] + incl[q] - k[q]);
 }
 
 // M2L rows (the order in which the M2L kernels take the items): a box's full
@@ -1518,13 +1535,15 @@ __global__ void k_items(int nbox, const int32_t* __restrict__ child0, const int3
     const int km = (m + K - 1) / K;
     const int nfull = m / K, r = m - nfull * K;
     const int rank = r > 0 ? (int)atomicAdd(rowctr + r, 1ull) : 0;  // issued first: its latency overlaps the rest
-    unsigned long long bp, bm, bf, bh, bl, bz;
-    warp_reserve3(ctr + 2, kp, ctr + 3, km, rowctr + kM2LItemPairsMax, nfull, bp, bm, bf);
     // P2P row order: the full items of split leaves (the heavy ones) take rows from the front, every leaf's
     // last (or only) item takes a row from the back of the capacity
     const int kh = kp > 1 ? kp - 1 : 0, kl = kp > 0 ? 1 : 0;
-    warp_reserve3(rowctr + kM2LItemPairsMax + 1, kh, rowctr + kM2LItemPairsMax + 2, kl,
-                  rowctr + kM2LItemPairsMax + 3, 0, bh, bl, bz);
+    unsigned long long* const cs[5] = {ctr + 2, ctr + 3, rowctr + kM2LItemPairsMax, rowctr + kM2LItemPairsMax + 1,
+                                       rowctr + kM2LItemPairsMax + 2};
+    const int ks[5] = {kp, km, nfull, kh, kl};
+    unsigned long long bs[5];
+    block_reserve5(cs, ks, bs);
+    const unsigned long long bp = bs[0], bm = bs[1], bf = bs[2], bh = bs[3], bl = bs[4];
     // a box whose items do not fit gets (0, 0): the passes that read these tables stay inside the buffers
     if (leaf) {
         if ((long long)(bp + kp) > p2p_cap || (long long)(bh + kh + bl + kl) > p2p_cap) {

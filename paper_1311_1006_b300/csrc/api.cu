@@ -854,14 +854,15 @@ fmm_status fmm_get_tree_info(const fmm_tree* h, fmm_tree_info* out) {
     out->autotune_nlevels = t.tune.accepted;
     const int lv = t.Lmax - 1;
     const int lg = std::min(t.l0, lv);
-    // kernels per build: coordinate sort (see below), root geometry 1, first cut flags 1 (written by the
-    // short sort instead), per global level 2 partitions + geometry, subtree 1, finalize 1, lists root 1 + one
-    // pass per level, items 1, M2L row order 1; batched: instance keys 1 + 2 sort passes x 3.  Sort: digit
-    // counts + 4 passes + runs (short), counts + 8 passes (full), beyond 2^30 points keys + 8 x 3.
+    // kernels per build: coordinate sort (see below), first cut flags 1 (written by the short sort instead),
+    // per global level 2 partitions (the x cut also computes that level's geometry), the geometry of the last
+    // globally split level 1, subtree 1, finalize 1, lists root 1 + one pass per level, items 1, M2L row
+    // order 1; batched: instance keys 1 + 2 sort passes x 3.  Sort: digit counts + 4 passes + runs (short),
+    // counts + 8 passes (full), beyond 2^30 points keys + 8 x 3.
     const bool big = t.n >= (1 << 30), full = t.sort_full || t.ninst > 1;
     const int sortk = big ? 25 : (full ? 9 : 6);
     const int mark = lg > 0 && (big || full) ? 1 : 0;
-    out->launches_build = 5 + sortk + lv + 3 * lg + mark + (lg < lv ? 1 : 0) + (t.ninst > 1 ? 7 : 0);
+    out->launches_build = 5 + sortk + lv + 2 * lg + mark + (lg < lv ? 1 : 0) + (t.ninst > 1 ? 7 : 0);
     // per evaluation: gather, P2M, M2M per level, M2L, M2L partial sums, L2L per level (not the deepest on
     // the FP32 path), P2P, L2P (which adds the P2P partial sums of split leaves)
     out->launches_eval = 6 + 2 * lv - (fold_leaf_l2l(t) ? 1 : 0);

@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_ghist(const uint64_t* __r
                                                              const uint64_t* __restrict__ k1, int n,
                                                              unsigned* __restrict__ ghist,
                                                              const double2* __restrict__ xy, unsigned* status) {
-    pdl_entry();
+    pdl_wait();
     __shared__ unsigned h[8][256];
     const int s = blockIdx.y;
     const uint64_t* k = s ? k1 : k0;
@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t* _
                                                                const unsigned* __restrict__ ghist, unsigned* stat,
                                                                unsigned* ticket, unsigned* status,
                                                                const double2* __restrict__ xy = nullptr) {
-    pdl_entry();
+    pdl_wait();
     constexpr int W = kSortThreads / 32;
     __shared__ int whist[W][257];  // per-warp digit counts, then their exclusive prefix over warps
     __shared__ int base[256];      // global position of the tile's first key of each digit
@@ -605,7 +605,7 @@ __global__ void __launch_bounds__(256) k_sort_runs(const uint64_t* __restrict__ 
                                                    int32_t* __restrict__ o0, int32_t* __restrict__ o1, int n,
                                                    uint8_t* __restrict__ side0, const int32_t* __restrict__ nz0,
                                                    unsigned* status) {
-    pdl_entry();
+    pdl_wait();
     const uint64_t* key = blockIdx.y ? k1 : k0;
     const int32_t* val = blockIdx.y ? v1 : v0;
     int32_t* out = blockIdx.y ? o1 : o0;
@@ -763,7 +763,7 @@ __device__ __forceinline__ void geom_box(const GeomArgs& g, int q) {
 // when its offset inside its segment is >= nzero of that segment.
 __global__ void k_mark(const int32_t* __restrict__ A, int n, const int32_t* __restrict__ start,
                        const int32_t* __restrict__ nzero, int K, uint8_t* side) {
-    pdl_entry();
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int k = find_seg(start, K, i);
@@ -862,7 +862,7 @@ __global__ void __launch_bounds__(kPartThreads) k_part_fused(
     const int32_t* __restrict__ nzero, const int32_t* __restrict__ obefore, int K, int32_t* __restrict__ out,
     const int32_t* __restrict__ nstart, const int32_t* __restrict__ nnzero, int nK, uint8_t* __restrict__ side_next,
     int direct_next, unsigned long long* tstat, int T, unsigned* status, GeomArgs geo) {
-    pdl_entry();
+    pdl_wait();
     __shared__ int wsum[32];
     __shared__ int sh_tile;
     __shared__ long long sh_excl;
@@ -953,7 +953,7 @@ static fmm_status partition(Tree& t, cudaStream_t s, int stage, const int32_t* A
 
 // One thread per box of a level whose geometry no partition stage carries.
 __global__ void k_geom(GeomArgs g) {
-    pdl_entry();
+    pdl_wait();
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q < g.cnt) geom_box(g, q);
 }
@@ -1046,7 +1046,7 @@ __global__ void __launch_bounds__(kSubThreads) k_subtree(
     const int32_t* __restrict__ inst, const int64_t* __restrict__ inst_box_off, const int32_t* __restrict__ inst_levels,
     int32_t* __restrict__ loc, double2* center, double* radius, double* rho, float4* chl, float* rho32, float* rad32,
     unsigned* status) {
-    pdl_entry();
+    pdl_wait();
     __shared__ uint16_t buf[3][kSubMax];
     // per local id: its box (then half box) numbered within the subtree level, and during a split
     // 2 * that + the side it goes to
@@ -1153,7 +1153,7 @@ __global__ void k_target_slots(const int32_t* __restrict__ leaves, int nleaf, co
                                const int32_t* __restrict__ bcount, const int32_t* __restrict__ pslot,
                                const int32_t* __restrict__ Y, int n_src, int32_t* __restrict__ slot_of,
                                int32_t* __restrict__ nsrc) {
-    pdl_entry();
+    pdl_wait();
     const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (w >= nleaf) return;  // warp-uniform
@@ -1189,7 +1189,7 @@ __global__ void k_finalize(const int32_t* __restrict__ Y, int n, const double2* 
                            const double2* __restrict__ center, int32_t* perm, double2* pts, float4* pos4,
                            const int32_t* __restrict__ leaf_of, const int32_t* __restrict__ slot_of, float* posp32,
                            double2* posp64) {
-    pdl_entry();
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int id = Y[i];
